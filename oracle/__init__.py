@@ -1,0 +1,140 @@
+"""CPU oracle for the Cholesky J/K engine -- TEST INFRASTRUCTURE ONLY.
+
+A slow, obviously correct FP64-in / long-double-accumulate implementation of
+the paper's J/K build (Eq. 4, Sec. II.C) and its adjoint (Eq. 1, Sec. II.A),
+written in plain C (``jk_oracle.c``) and called here through ctypes.  Only
+``tests/``, ``__graft_entry__.smoke()`` and the cpu_baseline leg of
+``bench.py`` may import this package.  It shares no code with the CUDA path.
+
+Parity pins (tests/test_oracle.py): brute force through the explicit
+four-index tensor, closed forms (rank-1 factor, identity factor, elementary
+symmetric factor, D = I), the identities of the J/K maps (J depends only on
+D + D^T, K(D^T) = K(D)^T, symmetry, linearity, bra-ket invariance,
+self-adjointness, positivity of <D, J(D)>) and central finite differences
+of E for the adjoint.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+
+import numpy as np
+
+from . import build as _build
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = ct.CDLL(path)
+        dp = ct.POINTER(ct.c_double)
+        ip = ct.POINTER(ct.c_int)
+        L.jko_brute.argtypes = [ct.c_int, ct.c_int, dp, dp, dp, dp]
+        L.jko_build.argtypes = [ct.c_int, ct.c_int, dp, ct.c_int, ip, dp, dp, dp, dp]
+        L.jko_sample.argtypes = [ct.c_int, ct.c_int, dp, ct.c_int, ip, dp, dp,
+                                 ct.c_int, ip, ip, ip, dp, dp]
+        L.jko_adjoint.argtypes = [ct.c_int, ct.c_int, dp, ct.c_int, ip, dp, dp,
+                                  dp, dp, dp, dp, dp]
+        L.jko_energy.argtypes = [ct.c_int, ct.c_int, dp, ct.c_int, ip, dp, dp,
+                                 dp, dp, ct.POINTER(ct.c_longdouble)]
+        for f in (L.jko_brute, L.jko_build, L.jko_sample, L.jko_adjoint, L.jko_energy):
+            f.restype = ct.c_int
+        _lib = L
+    return _lib
+
+
+def _d(a):
+    if a is None:
+        return ct.POINTER(ct.c_double)()
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(ct.POINTER(ct.c_double))
+
+
+def _i(a):
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.int32))
+    return a, a.ctypes.data_as(ct.POINTER(ct.c_int))
+
+
+def _cat(blocks):
+    return np.ascontiguousarray(np.concatenate([np.asarray(b, np.float64).ravel() for b in blocks]))
+
+
+def _check(rc, name):
+    if rc != 0:
+        raise RuntimeError(f"oracle {name} failed with code {rc}")
+
+
+def brute(L: np.ndarray, D: np.ndarray):
+    """O1: (J, K) for one dense density through the explicit 4-index tensor."""
+    L = np.ascontiguousarray(L, np.float64)
+    D = np.ascontiguousarray(D, np.float64)
+    naux, n, _ = L.shape
+    J = np.empty((n, n)); K = np.empty((n, n))
+    _check(lib().jko_brute(n, naux, _d(L), _d(D), _d(J), _d(K)), "brute")
+    return J, K
+
+
+def build(L: np.ndarray, X: list, Y: list, want_j=True, want_k=True):
+    """O2: (J, K) as [nd][n][n] arrays for factored densities D_s = X_s Y_s^T."""
+    L = np.ascontiguousarray(L, np.float64)
+    naux, n, _ = L.shape
+    nd = len(X)
+    ks, kp = _i([x.shape[1] for x in X])
+    Xc, Yc = _cat(X), _cat(Y)
+    J = np.empty((nd, n, n)) if want_j else None
+    K = np.empty((nd, n, n)) if want_k else None
+    _check(lib().jko_build(n, naux, _d(L), nd, kp, _d(Xc), _d(Yc), _d(J), _d(K)), "build")
+    return J, K
+
+
+def sample(L: np.ndarray, X: list, Y: list, s, mu, nu):
+    """O2 at single entries: (J_s[mu,nu], K_s[mu,nu]) for index arrays s, mu, nu."""
+    L = np.ascontiguousarray(L, np.float64)
+    naux, n, _ = L.shape
+    nd = len(X)
+    ks, kp = _i([x.shape[1] for x in X])
+    Xc, Yc = _cat(X), _cat(Y)
+    sa, sp = _i(s); ma, mp = _i(mu); na, np_ = _i(nu)
+    Jo = np.empty(sa.size); Ko = np.empty(sa.size)
+    _check(lib().jko_sample(n, naux, _d(L), nd, kp, _d(Xc), _d(Yc), sa.size, sp, mp, np_,
+                            _d(Jo), _d(Ko)), "sample")
+    return Jo, Ko
+
+
+def adjoint(L: np.ndarray, X: list, Y: list, W=None, V=None, want_dl=True):
+    """O3: (dX list, dY list, dL [naux][n][n] or None) for
+    E = sum_s <W_s, K_s> + <V_s, J_s>."""
+    L = np.ascontiguousarray(L, np.float64)
+    naux, n, _ = L.shape
+    nd = len(X)
+    ks, kp = _i([x.shape[1] for x in X])
+    Xc, Yc = _cat(X), _cat(Y)
+    Wc = _cat(W) if W is not None else None
+    Vc = _cat(V) if V is not None else None
+    dX = np.empty(Xc.size); dY = np.empty(Yc.size)
+    dL = np.empty((naux, n, n)) if want_dl else None
+    _check(lib().jko_adjoint(n, naux, _d(L), nd, kp, _d(Xc), _d(Yc), _d(Wc), _d(Vc),
+                             _d(dX), _d(dY), _d(dL)), "adjoint")
+    outX, outY, off = [], [], 0
+    for k in ks:
+        outX.append(dX[off:off + n * k].reshape(n, k))
+        outY.append(dY[off:off + n * k].reshape(n, k))
+        off += n * k
+    return outX, outY, dL
+
+
+def energy(L: np.ndarray, X: list, Y: list, W=None, V=None) -> float:
+    """E = sum_s <W_s, K_s> + <V_s, J_s> from the O2 build."""
+    L = np.ascontiguousarray(L, np.float64)
+    naux, n, _ = L.shape
+    nd = len(X)
+    ks, kp = _i([x.shape[1] for x in X])
+    Xc, Yc = _cat(X), _cat(Y)
+    Wc = _cat(W) if W is not None else None
+    Vc = _cat(V) if V is not None else None
+    E = ct.c_longdouble(0)
+    _check(lib().jko_energy(n, naux, _d(L), nd, kp, _d(Xc), _d(Yc), _d(Wc), _d(Vc),
+                            ct.byref(E)), "energy")
+    return float(E.value)

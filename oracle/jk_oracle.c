@@ -1,0 +1,393 @@
+/*
+ * jk_oracle.c -- TEST INFRASTRUCTURE ONLY, not part of the product path.
+ *
+ * A plain, slow, obviously correct CPU reference for the Cholesky-decomposed
+ * Coulomb/exchange (J/K) build of the paper (Eq. 4, Sec. II.C) and for its
+ * adjoint (Eq. 1, Sec. II.A).  Only tests/, __graft_entry__.smoke() and the
+ * cpu_baseline leg of bench.py may load it.  It shares no source with the
+ * CUDA path.
+ *
+ * Precision: inputs and outputs are IEEE double; every product is formed and
+ * every sum is accumulated in long double (x87 extended, 64-bit significand),
+ * and each output is rounded to double exactly once.  The oracle's own error is
+ * therefore far below the 1e-12 relative / 1e-10 absolute parity gates.
+ *
+ * Conventions (all row-major):
+ *   L    [naux][n][n]     Cholesky vectors L^P, symmetric in (mu,nu)
+ *   X, Y per density s a block [n][k_s], blocks concatenated in s order
+ *   D    [n][n]           dense density (brute-force entry only)
+ *   J, K [nd][n][n]       outputs (bare J and K: no factor 2, no -1/2)
+ *   W, V [nd][n][n]       adjoint seeds (cotangents of K_s and J_s)
+ *
+ * Parallelism: OpenMP only over output rows; every sum runs in a fixed order,
+ * so results do not depend on the thread count.
+ */
+#include <stdlib.h>
+#include <string.h>
+
+typedef long double ld;
+
+#define IDX2(i, j, ld_) ((size_t)(i) * (size_t)(ld_) + (size_t)(j))
+
+/* ------------------------------------------------------------------------
+ * O1: brute force through the explicit four-index tensor.
+ * The CD representation (Sec. II.C): (mu nu|lam sig) = sum_P L^P_{mu nu} L^P_{lam sig}.
+ * Coulomb:  J_{mu nu} = sum_{lam sig} (mu nu|lam sig) D_{lam sig}
+ * Exchange: K_{mu nu} = sum_{lam sig} (mu lam|nu sig) D_{lam sig}
+ * (the textbook real-orbital definitions; Eq. 4 with W_R = D).
+ * Intended for n <= 24.
+ * ---------------------------------------------------------------------- */
+int jko_brute(int n, int naux, const double *L, const double *D,
+              double *J, double *K)
+{
+    if (n < 1 || naux < 1 || n > 32) return 1;
+    size_t n2 = (size_t)n * n;
+    ld *eri = (ld *)calloc(n2 * n2, sizeof(ld));
+    if (!eri) return 2;
+    for (int a = 0; a < n; a++)
+        for (int b = 0; b < n; b++)
+            for (int c = 0; c < n; c++)
+                for (int d = 0; d < n; d++) {
+                    ld s = 0.0L;
+                    for (int P = 0; P < naux; P++)
+                        s += (ld)L[(size_t)P * n2 + IDX2(a, b, n)] *
+                             (ld)L[(size_t)P * n2 + IDX2(c, d, n)];
+                    eri[IDX2(IDX2(a, b, n), IDX2(c, d, n), n2)] = s;
+                }
+    for (int mu = 0; mu < n; mu++)
+        for (int nu = 0; nu < n; nu++) {
+            ld j = 0.0L, k = 0.0L;
+            for (int lam = 0; lam < n; lam++)
+                for (int sig = 0; sig < n; sig++) {
+                    ld dls = (ld)D[IDX2(lam, sig, n)];
+                    j += eri[IDX2(IDX2(mu, nu, n), IDX2(lam, sig, n), n2)] * dls;
+                    k += eri[IDX2(IDX2(mu, lam, n), IDX2(nu, sig, n), n2)] * dls;
+                }
+            J[IDX2(mu, nu, n)] = (double)j;
+            K[IDX2(mu, nu, n)] = (double)k;
+        }
+    free(eri);
+    return 0;
+}
+
+/* T = L^P Z for one P: T[mu][i] = sum_lam L^P[mu][lam] Z[lam][i]. */
+static void panel(int n, int k, const double *LP, const double *Z, ld *T)
+{
+    #pragma omp parallel for schedule(static)
+    for (int mu = 0; mu < n; mu++) {
+        for (int i = 0; i < k; i++) {
+            ld s = 0.0L;
+            for (int lam = 0; lam < n; lam++)
+                s += (ld)LP[IDX2(mu, lam, n)] * (ld)Z[IDX2(lam, i, k)];
+            T[IDX2(mu, i, k)] = s;
+        }
+    }
+}
+
+/* <A, B> = sum_{ij} A_ij B_ij with B given in long double; fixed order. */
+static ld frob_dl(int n, const double *A, const ld *B)
+{
+    ld s = 0.0L;
+    for (size_t e = 0; e < (size_t)n * n; e++) s += (ld)A[e] * B[e];
+    return s;
+}
+
+static ld frob_dd(int n, const double *A, const double *B)
+{
+    ld s = 0.0L;
+    for (size_t e = 0; e < (size_t)n * n; e++) s += (ld)A[e] * (ld)B[e];
+    return s;
+}
+
+/* D = X Y^T in long double. */
+static void dense_density(int n, int k, const double *X, const double *Y, ld *D)
+{
+    #pragma omp parallel for schedule(static)
+    for (int lam = 0; lam < n; lam++)
+        for (int sig = 0; sig < n; sig++) {
+            ld s = 0.0L;
+            for (int i = 0; i < k; i++)
+                s += (ld)X[IDX2(lam, i, k)] * (ld)Y[IDX2(sig, i, k)];
+            D[IDX2(lam, sig, n)] = s;
+        }
+}
+
+/* ------------------------------------------------------------------------
+ * O2: the factored build, following the engine's statement of the problem:
+ *   gamma_{P,s} = sum_{lam sig} L^P_{lam sig} (X_s Y_s^T)_{lam sig}
+ *   J_s         = sum_P gamma_{P,s} L^P
+ *   K_s         = sum_P (L^P X_s)(L^P Y_s)^T        (= B_V^T B_U, Sec. II.C)
+ * J or K may be NULL.
+ * ---------------------------------------------------------------------- */
+int jko_build(int n, int naux, const double *L, int nd, const int *k,
+              const double *X, const double *Y, double *J, double *K)
+{
+    if (n < 1 || naux < 0 || nd < 0) return 1;
+    size_t n2 = (size_t)n * n;
+    int kmax = 1;
+    for (int s = 0; s < nd; s++) {
+        if (k[s] < 1) return 1;
+        if (k[s] > kmax) kmax = k[s];
+    }
+    ld *D = (ld *)malloc(n2 * sizeof(ld));
+    ld *Jacc = (ld *)malloc(n2 * sizeof(ld));
+    ld *Kacc = (ld *)malloc(n2 * sizeof(ld));
+    ld *TX = (ld *)malloc((size_t)n * kmax * sizeof(ld));
+    ld *TY = (ld *)malloc((size_t)n * kmax * sizeof(ld));
+    if (!D || !Jacc || !Kacc || !TX || !TY) {
+        free(D); free(Jacc); free(Kacc); free(TX); free(TY);
+        return 2;
+    }
+    size_t off = 0;
+    for (int s = 0; s < nd; s++) {
+        int ks = k[s];
+        const double *Xs = X + off, *Ys = Y + off;
+        off += (size_t)n * ks;
+        dense_density(n, ks, Xs, Ys, D);
+        memset(Jacc, 0, n2 * sizeof(ld));
+        memset(Kacc, 0, n2 * sizeof(ld));
+        for (int P = 0; P < naux; P++) {
+            const double *LP = L + (size_t)P * n2;
+            ld gamma = frob_dl(n, LP, D);
+            panel(n, ks, LP, Xs, TX);
+            panel(n, ks, LP, Ys, TY);
+            #pragma omp parallel for schedule(static)
+            for (int mu = 0; mu < n; mu++)
+                for (int nu = 0; nu < n; nu++) {
+                    ld kk = 0.0L;
+                    for (int i = 0; i < ks; i++)
+                        kk += TX[IDX2(mu, i, ks)] * TY[IDX2(nu, i, ks)];
+                    Kacc[IDX2(mu, nu, n)] += kk;
+                    Jacc[IDX2(mu, nu, n)] += gamma * (ld)LP[IDX2(mu, nu, n)];
+                }
+        }
+        for (size_t e = 0; e < n2; e++) {
+            if (J) J[(size_t)s * n2 + e] = (double)Jacc[e];
+            if (K) K[(size_t)s * n2 + e] = (double)Kacc[e];
+        }
+    }
+    free(D); free(Jacc); free(Kacc); free(TX); free(TY);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------
+ * O2 sampled: single entries J_s[mu][nu], K_s[mu][nu] for a list of
+ * (s, mu, nu), for sizes where the full build is too slow on the host.
+ *   J_s[mu][nu] = sum_P gamma_{P,s} L^P[mu][nu]
+ *   K_s[mu][nu] = sum_P sum_i (L^P[mu,:] . X_s[:,i]) (L^P[nu,:] . Y_s[:,i])
+ * ---------------------------------------------------------------------- */
+int jko_sample(int n, int naux, const double *L, int nd, const int *k,
+               const double *X, const double *Y, int nsamp, const int *ss,
+               const int *mus, const int *nus, double *Jout, double *Kout)
+{
+    if (n < 1 || naux < 0 || nd < 0 || nsamp < 0) return 1;
+    size_t n2 = (size_t)n * n;
+    size_t *offs = (size_t *)malloc((nd + 1) * sizeof(size_t));
+    int *need = (int *)calloc(nd > 0 ? nd : 1, sizeof(int));
+    ld *gamma = (ld *)calloc((size_t)(nd > 0 ? nd : 1) * (naux > 0 ? naux : 1), sizeof(ld));
+    ld *D = (ld *)malloc(n2 * sizeof(ld));
+    if (!offs || !need || !gamma || !D) {
+        free(offs); free(need); free(gamma); free(D);
+        return 2;
+    }
+    offs[0] = 0;
+    for (int s = 0; s < nd; s++) offs[s + 1] = offs[s] + (size_t)n * k[s];
+    for (int q = 0; q < nsamp; q++) {
+        if (ss[q] < 0 || ss[q] >= nd || mus[q] < 0 || mus[q] >= n ||
+            nus[q] < 0 || nus[q] >= n) {
+            free(offs); free(need); free(gamma); free(D);
+            return 1;
+        }
+        need[ss[q]] = 1;
+    }
+    for (int s = 0; s < nd; s++) {
+        if (!need[s]) continue;
+        dense_density(n, k[s], X + offs[s], Y + offs[s], D);
+        #pragma omp parallel for schedule(static)
+        for (int P = 0; P < naux; P++)
+            gamma[(size_t)s * naux + P] = frob_dl(n, L + (size_t)P * n2, D);
+    }
+    #pragma omp parallel for schedule(dynamic)
+    for (int q = 0; q < nsamp; q++) {
+        int s = ss[q], mu = mus[q], nu = nus[q], ks = k[s];
+        const double *Xs = X + offs[s], *Ys = Y + offs[s];
+        ld jv = 0.0L, kv = 0.0L;
+        for (int P = 0; P < naux; P++) {
+            const double *LP = L + (size_t)P * n2;
+            jv += gamma[(size_t)s * naux + P] * (ld)LP[IDX2(mu, nu, n)];
+            for (int i = 0; i < ks; i++) {
+                ld tx = 0.0L, ty = 0.0L;
+                for (int lam = 0; lam < n; lam++) {
+                    tx += (ld)LP[IDX2(mu, lam, n)] * (ld)Xs[IDX2(lam, i, ks)];
+                    ty += (ld)LP[IDX2(nu, lam, n)] * (ld)Ys[IDX2(lam, i, ks)];
+                }
+                kv += tx * ty;
+            }
+        }
+        if (Jout) Jout[q] = (double)jv;
+        if (Kout) Kout[q] = (double)kv;
+    }
+    free(offs); free(need); free(gamma); free(D);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------
+ * O3: the adjoint of E = sum_s <W_s, K_s> + <V_s, J_s> under the Frobenius
+ * pairing <A,B> = Tr A^T B (Eq. 1, Sec. II.A), written out by hand:
+ *
+ *   dE/dX_s = sum_P L^P W_s (L^P Y_s)   + J(V_s) Y_s
+ *   dE/dY_s = sum_P L^P W_s^T (L^P X_s) + J(V_s) X_s
+ *   G^P     = sum_s [ W_s (L^P Y_s) X_s^T + Y_s (L^P X_s)^T W_s
+ *                     + c_{P,s} X_s Y_s^T + gamma_{P,s} V_s ]
+ *   dE/dL^P = (G^P + G^P^T) / 2     (gradient on the symmetric subspace)
+ * with c_{P,s} = <V_s, L^P>, gamma_{P,s} = <L^P, X_s Y_s^T> and
+ * J(V) = sum_P <L^P, V> L^P.  W or V may be NULL (taken as zero); dL may be
+ * NULL (not formed).  dX, dY are [n][k_s] blocks concatenated like X.
+ * ---------------------------------------------------------------------- */
+int jko_adjoint(int n, int naux, const double *L, int nd, const int *k,
+                const double *X, const double *Y, const double *W,
+                const double *V, double *dX, double *dY, double *dL)
+{
+    if (n < 1 || naux < 0 || nd < 0) return 1;
+    size_t n2 = (size_t)n * n;
+    int kmax = 1;
+    size_t ktot = 0;
+    for (int s = 0; s < nd; s++) {
+        if (k[s] < 1) return 1;
+        if (k[s] > kmax) kmax = k[s];
+        ktot += (size_t)k[s];
+    }
+    size_t *offs = (size_t *)malloc((nd + 1) * sizeof(size_t));
+    ld *aX = (ld *)calloc((size_t)n * (ktot ? ktot : 1), sizeof(ld));
+    ld *aY = (ld *)calloc((size_t)n * (ktot ? ktot : 1), sizeof(ld));
+    ld *JV = (ld *)calloc(n2 * (nd ? nd : 1), sizeof(ld));
+    ld *TX = (ld *)malloc((size_t)n * kmax * sizeof(ld));
+    ld *TY = (ld *)malloc((size_t)n * kmax * sizeof(ld));
+    ld *U = (ld *)malloc((size_t)n * kmax * sizeof(ld));
+    ld *Vp = (ld *)malloc((size_t)n * kmax * sizeof(ld));
+    ld *G = (ld *)malloc(n2 * sizeof(ld));
+    ld *D = (ld *)malloc(n2 * (nd ? nd : 1) * sizeof(ld));
+    if (!offs || !aX || !aY || !JV || !TX || !TY || !U || !Vp || !G || !D) {
+        free(offs); free(aX); free(aY); free(JV); free(TX); free(TY);
+        free(U); free(Vp); free(G); free(D);
+        return 2;
+    }
+    offs[0] = 0;
+    for (int s = 0; s < nd; s++) offs[s + 1] = offs[s] + (size_t)n * k[s];
+    for (int s = 0; s < nd; s++)
+        dense_density(n, k[s], X + offs[s], Y + offs[s], D + (size_t)s * n2);
+
+    for (int P = 0; P < naux; P++) {
+        const double *LP = L + (size_t)P * n2;
+        memset(G, 0, n2 * sizeof(ld));
+        for (int s = 0; s < nd; s++) {
+            int ks = k[s];
+            const double *Xs = X + offs[s], *Ys = Y + offs[s];
+            const double *Ws = W ? W + (size_t)s * n2 : NULL;
+            const double *Vs = V ? V + (size_t)s * n2 : NULL;
+            ld gam = frob_dl(n, LP, D + (size_t)s * n2);
+            ld cps = Vs ? frob_dd(n, Vs, LP) : 0.0L;
+            if (Ws) {
+                panel(n, ks, LP, Xs, TX);
+                panel(n, ks, LP, Ys, TY);
+                /* U = W_s T_Y, Vp = W_s^T T_X */
+                #pragma omp parallel for schedule(static)
+                for (int mu = 0; mu < n; mu++)
+                    for (int i = 0; i < ks; i++) {
+                        ld u = 0.0L, v = 0.0L;
+                        for (int lam = 0; lam < n; lam++) {
+                            u += (ld)Ws[IDX2(mu, lam, n)] * TY[IDX2(lam, i, ks)];
+                            v += (ld)Ws[IDX2(lam, mu, n)] * TX[IDX2(lam, i, ks)];
+                        }
+                        U[IDX2(mu, i, ks)] = u;
+                        Vp[IDX2(mu, i, ks)] = v;
+                    }
+                /* dX_s += L^P U, dY_s += L^P Vp */
+                #pragma omp parallel for schedule(static)
+                for (int mu = 0; mu < n; mu++)
+                    for (int i = 0; i < ks; i++) {
+                        ld a = 0.0L, b = 0.0L;
+                        for (int lam = 0; lam < n; lam++) {
+                            a += (ld)LP[IDX2(mu, lam, n)] * U[IDX2(lam, i, ks)];
+                            b += (ld)LP[IDX2(mu, lam, n)] * Vp[IDX2(lam, i, ks)];
+                        }
+                        aX[offs[s] + IDX2(mu, i, ks)] += a;
+                        aY[offs[s] + IDX2(mu, i, ks)] += b;
+                    }
+            }
+            if (dL) {
+                #pragma omp parallel for schedule(static)
+                for (int mu = 0; mu < n; mu++)
+                    for (int nu = 0; nu < n; nu++) {
+                        ld g = 0.0L;
+                        if (Ws)
+                            for (int i = 0; i < ks; i++)
+                                g += U[IDX2(mu, i, ks)] * (ld)Xs[IDX2(nu, i, ks)] +
+                                     (ld)Ys[IDX2(mu, i, ks)] * Vp[IDX2(nu, i, ks)];
+                        g += cps * D[(size_t)s * n2 + IDX2(mu, nu, n)];
+                        if (Vs) g += gam * (ld)Vs[IDX2(mu, nu, n)];
+                        G[IDX2(mu, nu, n)] += g;
+                    }
+            }
+            if (Vs) {
+                ld *JVs = JV + (size_t)s * n2;
+                for (size_t e = 0; e < n2; e++) JVs[e] += cps * (ld)LP[e];
+            }
+        }
+        if (dL) {
+            double *dLP = dL + (size_t)P * n2;
+            for (int mu = 0; mu < n; mu++)
+                for (int nu = 0; nu < n; nu++)
+                    dLP[IDX2(mu, nu, n)] =
+                        (double)(0.5L * (G[IDX2(mu, nu, n)] + G[IDX2(nu, mu, n)]));
+        }
+    }
+    /* J(V_s) terms: dX_s += J(V_s) Y_s, dY_s += J(V_s) X_s */
+    if (V) {
+        for (int s = 0; s < nd; s++) {
+            int ks = k[s];
+            const double *Xs = X + offs[s], *Ys = Y + offs[s];
+            const ld *JVs = JV + (size_t)s * n2;
+            #pragma omp parallel for schedule(static)
+            for (int mu = 0; mu < n; mu++)
+                for (int i = 0; i < ks; i++) {
+                    ld a = 0.0L, b = 0.0L;
+                    for (int nu = 0; nu < n; nu++) {
+                        a += JVs[IDX2(mu, nu, n)] * (ld)Ys[IDX2(nu, i, ks)];
+                        b += JVs[IDX2(mu, nu, n)] * (ld)Xs[IDX2(nu, i, ks)];
+                    }
+                    aX[offs[s] + IDX2(mu, i, ks)] += a;
+                    aY[offs[s] + IDX2(mu, i, ks)] += b;
+                }
+        }
+    }
+    for (size_t e = 0; e < (size_t)n * ktot; e++) {
+        if (dX) dX[e] = (double)aX[e];
+        if (dY) dY[e] = (double)aY[e];
+    }
+    free(offs); free(aX); free(aY); free(JV); free(TX); free(TY);
+    free(U); free(Vp); free(G); free(D);
+    return 0;
+}
+
+/* E = sum_s <W_s, K_s> + <V_s, J_s>, evaluated from the O2 build in long
+ * double (for finite-difference checks of the adjoint). */
+int jko_energy(int n, int naux, const double *L, int nd, const int *k,
+               const double *X, const double *Y, const double *W,
+               const double *V, long double *E)
+{
+    size_t n2 = (size_t)n * n;
+    double *J = (double *)malloc(n2 * (nd ? nd : 1) * sizeof(double));
+    double *K = (double *)malloc(n2 * (nd ? nd : 1) * sizeof(double));
+    if (!J || !K) { free(J); free(K); return 2; }
+    int rc = jko_build(n, naux, L, nd, k, X, Y, J, K);
+    if (rc) { free(J); free(K); return rc; }
+    ld e = 0.0L;
+    for (int s = 0; s < nd; s++) {
+        if (W) e += frob_dd(n, W + (size_t)s * n2, K + (size_t)s * n2);
+        if (V) e += frob_dd(n, V + (size_t)s * n2, J + (size_t)s * n2);
+    }
+    *E = e;
+    free(J); free(K);
+    return 0;
+}
