@@ -1,0 +1,333 @@
+#!/usr/bin/env python
+"""Throughput of the Cholesky J/K engine on one B300 (or N replicas).
+
+One step = one full J/K build (panels, J metric dot, J back-contraction,
+K rank update, final FP64 reduction) for the multi-state workload:
+nbf = 400, naux = 2400, eight densities of width 40 (one symmetric ground
+density, seven non-symmetric transition densities), seeded synthetic inputs.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision split|fp64]
+                  [--impl ours|reference]
+
+Prints ONE JSON line on rank 0.  `value` is algorithmic TFLOP/s (FP64-
+equivalent work, slice products of the split path are cost, not counted) with
+all inputs resident in HBM; `e2e` is the same metric through the public API
+with pinned host inputs copied in and J/K copied out inside the timed region.
+Under torchrun every rank runs its own replica (the path has no exchange
+step); value = all ranks' work / the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Cholesky J/K TFLOP/s (% tensor peak), split-prec vs FP64 GPU at ≤1e-10 error"
+WORKLOAD = "multi-state nbf=400 naux=2400 tau=400, 8 densities k=40 (1 symmetric ground + 7 non-symmetric transition), FP64 in/out"
+
+# FP64 issue-rate peak of B300 for the plain engine's roofline: a dependent-
+# free FP64 FMA stream measured 1.20 TFLOP/s on this machine's B300 (148 SMs at
+# 2032 MHz, i.e. 2 FP64 FMA per clock per SM; nominal 1.25 TFLOP/s).
+FP64_PEAK_TFLOPS = 1.20
+
+
+def build_flops(n, naux, ks, sym):
+    """Algorithmic flops of one build: panels 2n^2kA per half-transform, rank
+    update 2n^2kA (n^2kA for a symmetric density), J back-contraction 2n^2A,
+    gamma from the panel 2nkA, per density."""
+    f = 0.0
+    for k, s in zip(ks, sym):
+        f += (3.0 if s else 6.0) * n * n * k * naux
+        f += 2.0 * n * n * naux + 2.0 * n * k * naux
+    return f
+
+
+def panel_rank_flops(n, naux, ks, sym):
+    return sum((3.0 if s else 6.0) * n * n * k * naux for k, s in zip(ks, sym))
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        smax = max((num(r[2]) for r in rows if num(r[2]) is not None), default=None)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": reasons, "samples": len(rows),
+                "power_w_max": max((num(r[3]) for r in rows if num(r[3]) is not None), default=None)}
+
+
+def dist_init():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl"
+        dist.init_process_group(backend=backend)
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world, device):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def cpu_baseline_sample(max_seconds=20.0):
+    """The oracle as it stands on a bounded sample of the workload: one
+    non-symmetric density (k=40) over the first `na` aux indices."""
+    import numpy as np
+    import oracle
+    from paper_2608_06536_b300 import inputs
+    n, tau = 400, 400.0
+    X, Y = inputs.transition_density(n, 40, 1, 0)
+    na = 2400
+    L = inputs.factor(n, na, tau, 0)
+    oracle.build(L[:2], [X], [Y])   # load + warm
+    t0 = time.perf_counter()
+    oracle.build(L, [X], [Y])
+    dt = time.perf_counter() - t0
+    flops = build_flops(n, na, [40], [False])
+    cores = len(os.sched_getaffinity(0))
+    omp = os.environ.get("OMP_NUM_THREADS")
+    return {"value": flops / dt / 1e12, "unit": "TFLOP/s", "cores": int(omp) if omp else cores,
+            "kind": "oracle",
+            "sample": f"1 non-symmetric density (k=40) x first {na} of 2400 aux indices, nbf=400; "
+                      f"{flops:.3g} algorithmic flop in {dt:.2f} s",
+            "seconds": dt}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    steps = []
+    for _ in range(args.warmup):
+        cpu_baseline_sample()
+    for _ in range(args.steps):
+        steps.append(cpu_baseline_sample())
+    v = statistics.median(s["value"] for s in steps)
+    sec = statistics.median(s["seconds"] for s in steps)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "TFLOP/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64 (long double accumulation)", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": steps[0]["sample"]},
+            "cpu_baseline": {k: steps[0][k] for k in ("unit", "cores", "kind", "sample")} | {"value": v},
+            "e2e": {"value": v, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, rank, world, local):
+    import numpy as np
+    import torch
+    from paper_2608_06536_b300 import inputs, jk
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    m = inputs.multi_state()
+    n, naux, ks, sym = m.n, m.naux, m.ks, m.sym
+    flops = build_flops(n, naux, ks, sym)
+    Ld = torch.from_numpy(m.L).to(dev)
+    Xd = [torch.from_numpy(x).to(dev) for x in m.X]
+    Yd = [torch.from_numpy(y).to(dev) for y in m.Y]
+    eng = jk.Engine(dev)
+    prec = args.precision
+    st = torch.cuda.current_stream(dev)
+
+    # warm-up (also sizes the arena)
+    for _ in range(args.warmup):
+        J, K = eng.build(Ld, Xd, Yd, sym, prec)
+    eng.sync_status()
+    torch.cuda.synchronize(dev)
+
+    # ---- device-resident timed region --------------------------------------
+    clocks = ClockSampler(local)
+    clocks.start()
+    eng.profile(True)
+    eng.profile_reset()
+    l0 = eng.launch_count()
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(args.steps):
+        J, K = eng.build(Ld, Xd, Yd, sym, prec, J=J, K=K)
+    e1.record(st)
+    torch.cuda.synchronize(dev)
+    barrier(world)
+    ms = e0.elapsed_time(e1) / args.steps
+    launches = eng.launch_count() - l0
+    prof = eng.profile_read()
+    eng.profile(False)
+    clk = clocks.stop()
+    eng.sync_status()
+    ms_max = max_over_ranks(ms, world, dev)
+    value = world * flops / (ms_max * 1e-3) / 1e12
+
+    # ---- end to end through the public API, host buffers ---------------------
+    Lh = torch.from_numpy(m.L).pin_memory()
+    Xh = [torch.from_numpy(x).pin_memory() for x in m.X]
+    Yh = [torch.from_numpy(y).pin_memory() for y in m.Y]
+    Jh = torch.empty((len(ks), n, n), dtype=torch.float64).pin_memory()
+    Kh = torch.empty((len(ks), n, n), dtype=torch.float64).pin_memory()
+    h2d = Lh.numel() * 8 + sum(x.numel() * 8 for x in Xh) + sum(y.numel() * 8 for y, s in zip(Yh, sym) if not s)
+    d2h = (Jh.numel() + Kh.numel()) * 8
+    e2e_steps = max(1, min(args.steps, 3))
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    e0.record(st)
+    for _ in range(e2e_steps):
+        Ld.copy_(Lh, non_blocking=True)
+        for a, b in zip(Xd, Xh):
+            a.copy_(b, non_blocking=True)
+        for a, b, s in zip(Yd, Yh, sym):
+            if not s:
+                a.copy_(b, non_blocking=True)
+        J, K = eng.build(Ld, Xd, Yd, sym, prec, J=J, K=K)
+        Jh.copy_(J, non_blocking=True)
+        Kh.copy_(K, non_blocking=True)
+    e1.record(st)
+    torch.cuda.synchronize(dev)
+    ms_e2e = max_over_ranks(e0.elapsed_time(e1) / e2e_steps, world, dev)
+    e2e = {"value": world * flops / (ms_e2e * 1e-3) / 1e12, "unit": "TFLOP/s",
+           "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "ms_per_step": ms_e2e}
+
+    # ---- roofline of the dominant kernel ------------------------------------
+    peaks, peak_src = load_peaks()
+    top = max(prof.items(), key=lambda kv: kv[1][0]) if prof else ("none", (0.0, 0))
+    top_name, (top_ms, top_cnt) = top
+    roofline = None
+    if top_name == "dgemm_fp64" and top_cnt:
+        alg = panel_rank_flops(n, naux, ks, sym) * args.steps
+        achieved = alg / (top_ms * 1e-3) / 1e12
+        roofline = {"kernel": top_name, "bound": "alu", "achieved": achieved,
+                    "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                    "peak_source": "FP64 FMA stream probe, 1.20 TFLOP/s (148 SM x 2 FMA/clk x 2032 MHz)",
+                    "traffic": None, "avg_launch_ms": top_ms / top_cnt,
+                    "share_of_step": top_ms / (ms * args.steps)}
+    elif top_name == "ozgemm_tcgen05" and top_cnt:
+        from paper_2608_06536_b300 import jk as _jk  # noqa: F401
+        issued = eng.last_issued_mma_flops * args.steps if hasattr(eng, "last_issued_mma_flops") else None
+        pk = peaks.get("bf16_tflops_sustained")
+        achieved = issued / (top_ms * 1e-3) / 1e12 if issued else None
+        roofline = {"kernel": top_name, "bound": "tensor", "achieved": achieved, "peak": pk,
+                    "unit": "TFLOP/s", "frac": (achieved / pk) if achieved else None,
+                    "peak_source": f"bf16_tflops_sustained ({peak_src})", "traffic": None,
+                    "avg_launch_ms": top_ms / top_cnt, "share_of_step": top_ms / (ms * args.steps)}
+
+    if rank != 0:
+        return
+    cpu = cpu_baseline_sample()
+    line = {
+        "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if prec == "fp64" else "bf16-slices/fp32-tmem/int64 -> f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "engine": prec, "nbf": n, "naux": naux, "nd": len(ks),
+                   "k": ks[0], "l2": "inputs larger than L2 (L = 3.07 GB FP64), no flush",
+                   "parallelism": f"replicas x{world}"},
+        "e2e": e2e,
+        "gpu_launches": int(launches),
+        "launches_per_step": launches / args.steps,
+        "kernels_ms": {k: v[0] / args.steps for k, v in prof.items()},
+        "roofline": roofline,
+        "cpu_baseline": {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")},
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["split", "fp64"], default="split")
+    args = ap.parse_args()
+    rank, world, local = dist_init()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

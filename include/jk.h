@@ -1,0 +1,159 @@
+/*
+ * jk.h -- C ABI of libjk.so, the B300 (sm_103a) Cholesky-decomposed
+ * Coulomb/exchange engine for non-symmetric densities.
+ *
+ * What it computes (the paper's statement of the problem, Eq. 4 and the
+ * energy-level CD build of Sec. II.C; bare J and K, no factor 2, no -1/2):
+ *
+ *   (mu nu|lam sig) = sum_P L^P_{mu nu} L^P_{lam sig}          CD integrals
+ *   D_s             = X_s Y_s^T                               factored density
+ *   gamma_{P,s}     = sum_{lam sig} L^P_{lam sig} (D_s)_{lam sig}
+ *   J_s             = sum_P gamma_{P,s} L^P
+ *   K_s             = sum_P (L^P X_s)(L^P Y_s)^T   (= B_V^T B_U with the
+ *                                                  half-transforms B_U, B_V)
+ *
+ * A symmetric density (D = X X^T) is the special case Y = X of the
+ * non-symmetric build (Sec. II.C).
+ *
+ * Conventions shared by every entry point:
+ *  - All arrays are row-major and live in DEVICE memory unless stated.
+ *    The caller owns every input, output and the workspace arena; the
+ *    library never calls cudaMalloc/cudaFree inside a build (the arena is
+ *    sub-allocated by bump, as the paper's engine does, Sec. IV).
+ *  - All work is enqueued asynchronously on the caller's stream
+ *    (a cudaStream_t passed as void*; NULL = legacy default stream).
+ *  - Outputs are overwritten, never accumulated into.
+ *  - Arguments are validated on the host before anything is launched; a
+ *    failing check returns a status and stores a message retrievable with
+ *    jk_last_error(); nothing is launched in that case.
+ *  - A handle must be used from one host thread and one stream at a time:
+ *    successive calls reuse the same arena.
+ *  - Pointers to double/float arrays must be 16-byte aligned
+ *    (JK_ERR_ARG otherwise).
+ *  - L^P is assumed symmetric in (mu, nu); this is not checked.
+ */
+#ifndef JK_H
+#define JK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    JK_OK = 0,
+    JK_ERR_ARG = 1,          /* NULL / misaligned pointer, bad enum value     */
+    JK_ERR_SHAPE = 2,        /* nbf, naux, k or counts out of range           */
+    JK_ERR_OOM = 3,          /* workspace arena too small for this call       */
+    JK_ERR_CUDA = 4,         /* a CUDA runtime call or launch failed          */
+    JK_ERR_TIMEOUT = 5,      /* a bounded device-side wait gave up            */
+    JK_ERR_UNSUPPORTED = 6   /* valid request this build does not implement   */
+} jk_status;
+
+typedef enum {
+    /* Plain FP64 engine: every product and sum in IEEE double. */
+    JK_FP64 = 0,
+    /* Split-precision engine: FP64 operands cut into BF16 slices (error-free
+     * splitting), slice products on tcgen05 tensor cores with FP32 TMEM
+     * accumulators kept exact, integer/FP64 recombination; FP64-accurate. */
+    JK_SPLIT_BF16 = 1
+} jk_precision;
+
+typedef struct jk_ctx *jk_handle;
+
+/* One Cholesky factor: L is [naux][nbf][nbf] FP64 on the device. */
+typedef struct {
+    int32_t nbf;
+    int32_t naux;
+    const double *L;
+} jk_factor;
+
+/* One factored density D = X Y^T.  X, Y are [nbf][k] FP64 on the device.
+ * symmetric != 0 means D = X X^T: Y is ignored (may be NULL). */
+typedef struct {
+    int32_t k;
+    int32_t symmetric;
+    const double *X;
+    const double *Y;
+} jk_density;
+
+/* Which entry point a workspace query is for. */
+typedef enum { JK_OP_BUILD = 0, JK_OP_ADJOINT = 1, JK_OP_BATCHED = 2 } jk_op;
+
+/* Create a handle over a caller-owned device arena of `bytes` bytes
+ * (256-byte aligned).  The arena must stay valid until jk_destroy. */
+jk_status jk_create(jk_handle *h, void *workspace, size_t bytes);
+jk_status jk_destroy(jk_handle h);
+
+/* Bytes of arena a call with these shapes needs (host-only, no GPU work).
+ * For JK_OP_BATCHED pass nmol factors and the concatenated densities, with
+ * nd_per_mol giving the split; otherwise nmol = 1 and nd_per_mol may be NULL. */
+jk_status jk_workspace_query(jk_op op, int32_t nmol, const jk_factor *f,
+                             const int32_t *nd_per_mol, int32_t nd,
+                             const jk_density *d, jk_precision p, size_t *bytes);
+
+/* jk_build: J_s and K_s for nd densities over one factor (Eq. 4, Sec. II.C).
+ *   J, K : [nd][nbf][nbf] FP64 outputs; either may be NULL (not formed).
+ * Status: JK_ERR_SHAPE if nbf < 1, naux < 1, nd < 1 or any k < 1;
+ *         JK_ERR_OOM if the arena is smaller than jk_workspace_query says. */
+jk_status jk_build(jk_handle h, const jk_factor *f, int32_t nd,
+                   const jk_density *d, double *J, double *K,
+                   jk_precision p, void *stream);
+
+/* jk_build_batched: many independent molecules (uneven nbf, naux, nd) in one
+ * call.  f[m] is molecule m's factor, nd_per_mol[m] its density count (host
+ * array), d the densities of all molecules concatenated in molecule order,
+ * J[i], K[i] (host arrays of device pointers, one per density in the same
+ * order) point to [nbf_m][nbf_m] FP64 outputs; J or K may be NULL. */
+jk_status jk_build_batched(jk_handle h, int32_t nmol, const jk_factor *f,
+                           const int32_t *nd_per_mol, const jk_density *d,
+                           double *const *J, double *const *K,
+                           jk_precision p, void *stream);
+
+/* jk_adjoint: gradients of E = sum_s <W_s, K_s> + <V_s, J_s> under the
+ * Frobenius pairing <A,B> = Tr A^T B (the self-adjoint form of Eq. 1, Sec. II.A):
+ *   dX_s = sum_P L^P W_s (L^P Y_s)   + J(V_s) Y_s
+ *   dY_s = sum_P L^P W_s^T (L^P X_s) + J(V_s) X_s
+ *   dL^P = sym( sum_s W_s (L^P Y_s) X_s^T + Y_s (L^P X_s)^T W_s
+ *               + <V_s, L^P> D_s + gamma_{P,s} V_s ),  sym(G) = (G + G^T)/2
+ * W, V : [nd][nbf][nbf] FP64 (either may be NULL = zero seeds).
+ * dX, dY : [nd] blocks of [nbf][k_s] FP64, concatenated in density order.
+ *          For a symmetric density Y = X, so dX receives dX_s + dY_s and the
+ *          dY block is written with zeros.
+ * dL : [naux][nbf][nbf] FP64, or NULL (not formed). */
+jk_status jk_adjoint(jk_handle h, const jk_factor *f, int32_t nd,
+                     const jk_density *d, const double *W, const double *V,
+                     double *dX, double *dY, double *dL,
+                     jk_precision p, void *stream);
+
+/* Wait for the stream and report any device-side error flag raised by this
+ * handle's kernels (e.g. JK_ERR_TIMEOUT from a bounded wait); clears it. */
+jk_status jk_sync_status(jk_handle h, void *stream);
+
+const char *jk_status_string(jk_status s);
+/* Message of the last failing call on this handle ("" if none). */
+const char *jk_last_error(jk_handle h);
+/* Library version string. */
+const char *jk_version(void);
+
+/* ---- instrumentation (does not change results) ---------------------------
+ * Kernels launched by this handle since creation or the last reset. */
+int64_t jk_launch_count(jk_handle h);
+/* on != 0: bracket every launch with CUDA events on the call's stream and
+ * accumulate per-kernel-kind device time.  Costs two event records per launch. */
+jk_status jk_profile_enable(jk_handle h, int32_t on);
+/* Zero the launch count and the accumulated times. */
+jk_status jk_profile_reset(jk_handle h);
+/* Number of kernel kinds and the name of kind i (NULL if out of range). */
+int32_t jk_profile_kinds(void);
+const char *jk_profile_kind_name(int32_t kind);
+/* Total device time (ms) and launches of one kind since the last reset;
+ * waits for the recorded events. */
+jk_status jk_profile_read(jk_handle h, int32_t kind, double *ms, int64_t *launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* JK_H */

@@ -1,0 +1,58 @@
+"""torch.autograd wrapper: J, K forward and the hand-written adjoint backward.
+
+Forward calls ``jk_build``; backward calls ``jk_adjoint`` with V = dE/dJ and
+W = dE/dK, so for E = sum_s <W_s, K_s> + <V_s, J_s> autograd returns exactly
+the library's adjoint (the self-adjoint form of Eq. 1, Sec. II.A).  The
+panels L^P X, L^P Y are recomputed in the backward pass, never stored.
+"""
+from __future__ import annotations
+
+import torch
+
+from . import jk as _jk
+
+
+class _JKFunction(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, engine, precision, sym, L, *xy):
+        nd = len(sym)
+        X = [xy[2 * s] for s in range(nd)]
+        Y = [xy[2 * s + 1] for s in range(nd)]
+        J, K = engine.build(L, X, Y, sym, precision)
+        ctx.engine, ctx.precision, ctx.sym = engine, precision, sym
+        ctx.save_for_backward(L, *xy)
+        return J, K
+
+    @staticmethod
+    def backward(ctx, gJ, gK):
+        L, *xy = ctx.saved_tensors
+        nd = len(ctx.sym)
+        X = [xy[2 * s] for s in range(nd)]
+        Y = [xy[2 * s + 1] for s in range(nd)]
+        want_dl = ctx.needs_input_grad[3]
+        dX, dY, dL = ctx.engine.adjoint(L, X, Y, ctx.sym, W=gK, V=gJ, want_dl=want_dl,
+                                        precision=ctx.precision)
+        grads = []
+        for s in range(nd):
+            if ctx.sym[s]:
+                # D = X X^T: the library folds both slots into dX.
+                grads += [dX[s], torch.zeros_like(dY[s])]
+            else:
+                grads += [dX[s], dY[s]]
+        return (None, None, None, dL if want_dl else None, *grads)
+
+
+def jk(L, X, Y=None, sym=None, precision="fp64", engine=None):
+    """Differentiable (J, K), each [nd][n][n], for D_s = X_s Y_s^T.
+
+    For a symmetric density pass Y_s = None (or sym[s] = True); its gradient
+    then arrives entirely on X_s.
+    """
+    nd = len(X)
+    sym = tuple(bool(sym[s]) if sym is not None else (Y is None or Y[s] is None) for s in range(nd))
+    Y = [X[s] if (sym[s] or Y is None or Y[s] is None) else Y[s] for s in range(nd)]
+    engine = engine if engine is not None else _jk.default_engine(L.device)
+    xy = []
+    for s in range(nd):
+        xy += [X[s], Y[s]]
+    return _JKFunction.apply(engine, precision, sym, L, *xy)

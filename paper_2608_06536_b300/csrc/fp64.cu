@@ -1,0 +1,520 @@
+// Plain FP64 engine: every product and every sum in IEEE double.
+//
+// This is the reference GPU engine the split-precision path is measured
+// against.  Data flow of one build (Sec. II.C, Eq. 4):
+//   Z      = [X_0 | Y_0 | X_1 | Y_1 | ...]             (nbf x ctot, packed)
+//   for each chunk of pc aux indices P:
+//     T^P  = L^P Z                                     panels (half-transforms)
+//     gamma_{P,s} = sum_{sig,i} T^P[sig][X_s col i] Y_s[sig][i]
+//     K_s += sum_{P in chunk} T^P_X (T^P_Y)^T          rank update, fixed order
+//   J_s = sum_P gamma_{P,s} L^P                         one L stream, all s
+// B300's FP64 units are few, so this engine is bound by FP64 issue rate, not
+// by HBM; it exists to be correct, deterministic and a fair baseline.
+#include <cstdarg>
+
+#include "jk_internal.h"
+
+namespace jk {
+
+// Generic operand addressing: element (row r, reduction index kk) of batch b
+// lives at p + b*sb + r*sr + (kk / kin)*sko + (kk % kin)*ski.  A two-level
+// reduction index lets one kernel sum over (P, i) pairs without repacking.
+struct GOp {
+    const double *p;
+    long long sb, sr, sko, ski;
+    int kin;
+};
+
+static GOp gop(const double *p, long long sb, long long sr, long long sko,
+               long long ski, int kin) {
+    GOp g;
+    g.p = p; g.sb = sb; g.sr = sr; g.sko = sko; g.ski = ski; g.kin = kin;
+    return g;
+}
+
+constexpr int GBM = 64, GBN = 64, GBK = 16;
+
+// C_b[m][n] = alpha * sum_kk A_b(m,kk) B_b(n,kk) + beta * C_b[m][n]
+// 64x64 tile per CTA, 256 threads, 4x4 outputs per thread; sums run in
+// increasing kk, so results are bit-reproducible for fixed shapes.
+__global__ void __launch_bounds__(256)
+dgemm_nt_kernel(int M, int N, int K, GOp A, GOp B, double *C, long long ldc,
+                long long scb, double alpha, double beta) {
+    __shared__ double As[GBK][GBM];
+    __shared__ double Bs[GBK][GBN];
+    const int b = blockIdx.z;
+    const int m0 = blockIdx.y * GBM, n0 = blockIdx.x * GBN;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const double *Ab = A.p + (long long)b * A.sb;
+    const double *Bb = B.p + (long long)b * B.sb;
+    double acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; i++)
+#pragma unroll
+        for (int j = 0; j < 4; j++) acc[i][j] = 0.0;
+
+    for (int k0 = 0; k0 < K; k0 += GBK) {
+        for (int e = threadIdx.x; e < GBM * GBK; e += 256) {
+            int r, c;
+            if (A.ski == 1) { r = e / GBK; c = e % GBK; } else { r = e % GBM; c = e / GBM; }
+            int m = m0 + r, kk = k0 + c;
+            double v = 0.0;
+            if (m < M && kk < K) {
+                int ko = kk / A.kin, ki = kk - ko * A.kin;
+                v = Ab[(long long)m * A.sr + (long long)ko * A.sko + (long long)ki * A.ski];
+            }
+            As[c][r] = v;
+        }
+        for (int e = threadIdx.x; e < GBN * GBK; e += 256) {
+            int r, c;
+            if (B.ski == 1) { r = e / GBK; c = e % GBK; } else { r = e % GBN; c = e / GBN; }
+            int nn = n0 + r, kk = k0 + c;
+            double v = 0.0;
+            if (nn < N && kk < K) {
+                int ko = kk / B.kin, ki = kk - ko * B.kin;
+                v = Bb[(long long)nn * B.sr + (long long)ko * B.sko + (long long)ki * B.ski];
+            }
+            Bs[c][r] = v;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int c = 0; c < GBK; c++) {
+            double a[4], bb[4];
+#pragma unroll
+            for (int i = 0; i < 4; i++) a[i] = As[c][ty + 16 * i];
+#pragma unroll
+            for (int j = 0; j < 4; j++) bb[j] = Bs[c][tx + 16 * j];
+#pragma unroll
+            for (int i = 0; i < 4; i++)
+#pragma unroll
+                for (int j = 0; j < 4; j++) acc[i][j] = fma(a[i], bb[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+    double *Cb = C + (long long)b * scb;
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+        int m = m0 + ty + 16 * i;
+        if (m >= M) continue;
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            int nn = n0 + tx + 16 * j;
+            if (nn >= N) continue;
+            double *c = Cb + (long long)m * ldc + nn;
+            double v = alpha * acc[i][j];
+            if (beta != 0.0) v = fma(beta, *c, v);
+            *c = v;
+        }
+    }
+}
+
+static jk_status dgemm(jk_ctx *h, int batch, int M, int N, int K, GOp A, GOp B,
+                       double *C, long long ldc, long long scb, double alpha,
+                       double beta, cudaStream_t st) {
+    if (M <= 0 || N <= 0 || batch <= 0) return JK_OK;
+    dim3 grid((N + GBN - 1) / GBN, (M + GBM - 1) / GBM, batch);
+    {
+        LaunchScope ls(h, KK_DGEMM, st);
+        dgemm_nt_kernel<<<grid, 256, 0, st>>>(M, N, K, A, B, C, ldc, scb, alpha, beta);
+    }
+    JK_LAUNCH_CHECK(h);
+    return JK_OK;
+}
+
+// Z[lam][off + i] = src[lam][i] for one density block.
+__global__ void pack_cols_kernel(const double *src, int n, int k, double *Z,
+                                 int ctot, int off) {
+    long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (e >= (long long)n * k) return;
+    int lam = (int)(e / k), i = (int)(e % k);
+    Z[(long long)lam * ctot + off + i] = src[e];
+}
+
+// Block-wide sum of one double per thread (256 threads), fixed order.
+__device__ __forceinline__ double block_sum_256(double v, double *red) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) red[w] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < 8; i++) t += red[i];
+    __syncthreads();
+    return t;
+}
+
+// gamma[s*ldg + P0 + p] = <L^{P0+p}, M_s> for dense n x n matrices M_s
+// (M = D_s for the Coulomb dot, M = V_s for the adjoint's <V_s, L^P>).
+// One CTA per (p, group of up to 4 densities); L^P is read once per group.
+__global__ void __launch_bounds__(256)
+frob_stream_kernel(const double *L, long long n2, const double *Mats, int nd,
+                   double *gamma, int ldg, int P0) {
+    __shared__ double red[8];
+    const int p = blockIdx.x;
+    const int s0 = blockIdx.y * 4;
+    const int ns = min(4, nd - s0);
+    const double *LP = L + (long long)(P0 + p) * n2;
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    for (long long e = threadIdx.x; e < n2; e += 256) {
+        double l = LP[e];
+#pragma unroll
+        for (int j = 0; j < 4; j++)
+            if (j < ns) acc[j] = fma(l, Mats[(long long)(s0 + j) * n2 + e], acc[j]);
+    }
+    for (int j = 0; j < ns; j++) {
+        double t = block_sum_256(acc[j], red);
+        if (threadIdx.x == 0) gamma[(long long)(s0 + j) * ldg + P0 + p] = t;
+    }
+}
+
+// gamma[s*ldg + P0 + p] = sum_{sig,i} T^p[sig][offX_s + i] * Y_s[sig][i]
+// (= <L^P, X_s Y_s^T>, from the panel already formed for K).
+struct DensTab {
+    const double *Y[kMaxDens];
+    int offX[kMaxDens];
+    int k[kMaxDens];
+};
+
+__global__ void __launch_bounds__(256)
+gamma_panel_kernel(const double *T, int n, int ctot, DensTab tab,
+                   double *gamma, int ldg, int P0) {
+    __shared__ double red[8];
+    const int p = blockIdx.x, s = blockIdx.y;
+    const int k = tab.k[s], off = tab.offX[s];
+    const double *Tp = T + (long long)p * n * ctot;
+    const double *Ys = tab.Y[s];
+    double acc = 0.0;
+    for (int e = threadIdx.x; e < n * k; e += 256) {
+        int sig = e / k, i = e - sig * k;
+        acc = fma(Tp[(long long)sig * ctot + off + i], Ys[e], acc);
+    }
+    double t = block_sum_256(acc, red);
+    if (threadIdx.x == 0) gamma[(long long)s * ldg + P0 + p] = t;
+}
+
+// Out_s[e] = sum_P g[s][P] L^P[e]: one pass over L for up to 8 densities.
+// Each thread owns two consecutive entries (16-byte loads); the sum over P
+// runs in increasing P.
+struct OutTab {
+    double *p[8];
+};
+
+template <int NS>
+__global__ void __launch_bounds__(256)
+jstream_kernel(const double *L, long long n2, int naux, const double *g,
+               int ldg, OutTab Out) {
+    long long e = 2 * (blockIdx.x * (long long)blockDim.x + threadIdx.x);
+    if (e >= n2) return;
+    const bool pair = (e + 1 < n2) && ((n2 & 1) == 0);
+    double a0[NS], a1[NS];
+#pragma unroll
+    for (int j = 0; j < NS; j++) { a0[j] = 0.0; a1[j] = 0.0; }
+    for (int P = 0; P < naux; P++) {
+        const double *LP = L + (long long)P * n2 + e;
+        double l0, l1 = 0.0;
+        if (pair) {
+            double2 v = __ldg(reinterpret_cast<const double2 *>(LP));
+            l0 = v.x; l1 = v.y;
+        } else {
+            l0 = __ldg(LP);
+            if (e + 1 < n2) l1 = __ldg(LP + 1);
+        }
+#pragma unroll
+        for (int j = 0; j < NS; j++) {
+            double gg = __ldg(g + (long long)j * ldg + P);
+            a0[j] = fma(gg, l0, a0[j]);
+            a1[j] = fma(gg, l1, a1[j]);
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < NS; j++) {
+        Out.p[j][e] = a0[j];
+        if (e + 1 < n2) Out.p[j][e + 1] = a1[j];
+    }
+}
+
+// Out[s] = sum_P g[s][P] L^P for s < nd (Out[s] are [n][n] device arrays).
+static jk_status jstream(jk_ctx *h, const double *L, int n, int naux,
+                         const double *g, int ldg, int nd, double *const *Out,
+                         cudaStream_t st) {
+    long long n2 = (long long)n * n;
+    int blocks = (int)((n2 / 2 + 1 + 255) / 256);
+    for (int s0 = 0; s0 < nd; s0 += 8) {
+        int ns = nd - s0 < 8 ? nd - s0 : 8;
+        const double *gs = g + (long long)s0 * ldg;
+        OutTab o;
+        for (int j = 0; j < 8; j++) o.p[j] = j < ns ? Out[s0 + j] : nullptr;
+        LaunchScope ls(h, KK_JSTREAM, st);
+        switch (ns) {
+#define JS(N) case N: jstream_kernel<N><<<blocks, 256, 0, st>>>(L, n2, naux, gs, ldg, o); break;
+            JS(1) JS(2) JS(3) JS(4) JS(5) JS(6) JS(7) JS(8)
+#undef JS
+        }
+        JK_LAUNCH_CHECK(h);
+    }
+    return JK_OK;
+}
+
+// G^p += sum_s c[s][P0+p] D_s + g[s][P0+p] V_s   (the J terms of dL)
+__global__ void gterms_kernel(double *G, long long n2, int pc, int nd,
+                              const double *D, const double *V, const double *c,
+                              const double *g, int ldg, int P0) {
+    long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    int p = blockIdx.y;
+    if (e >= n2) return;
+    double acc = G[(long long)p * n2 + e];
+    for (int s = 0; s < nd; s++) {
+        if (D) acc = fma(c[(long long)s * ldg + P0 + p], D[(long long)s * n2 + e], acc);
+        if (V) acc = fma(g[(long long)s * ldg + P0 + p], V[(long long)s * n2 + e], acc);
+    }
+    G[(long long)p * n2 + e] = acc;
+}
+
+// dL^P = (G^p + G^p^T) / 2
+__global__ void symmetrize_kernel(const double *G, int n, double *dL) {
+    long long n2 = (long long)n * n;
+    long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    int p = blockIdx.y;
+    if (e >= n2) return;
+    int mu = (int)(e / n), nu = (int)(e % n);
+    const double *Gp = G + (long long)p * n2;
+    dL[(long long)p * n2 + e] = 0.5 * (Gp[e] + Gp[(long long)nu * n + mu]);
+}
+
+// For symmetric densities (Y = X): dX += dY, dY = 0.
+__global__ void fold_sym_kernel(double *dX, double *dY, long long cnt) {
+    long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (e >= cnt) return;
+    dX[e] += dY[e];
+    dY[e] = 0.0;
+}
+
+static jk_status pack_z(jk_ctx *h, const Problem &pb, double *Z, cudaStream_t st) {
+    for (int s = 0; s < pb.nd; s++) {
+        long long cnt = (long long)pb.n * pb.k[s];
+        int blocks = (int)((cnt + 255) / 256);
+        { LaunchScope ls(h, KK_PACK, st);
+        pack_cols_kernel<<<blocks, 256, 0, st>>>(pb.X[s], pb.n, pb.k[s], Z, pb.ctot, pb.offX[s]); }
+        JK_LAUNCH_CHECK(h);
+        if (!pb.sym[s]) {
+            LaunchScope ls(h, KK_PACK, st);
+            pack_cols_kernel<<<blocks, 256, 0, st>>>(pb.Y[s], pb.n, pb.k[s], Z, pb.ctot, pb.offY[s]);
+            JK_LAUNCH_CHECK(h);
+        }
+    }
+    return JK_OK;
+}
+
+int fp64_default_pchunk(const Problem &pb) {
+    // Panel chunk of at most ~256 MB of FP64 (T^P for pc aux indices).
+    size_t per = (size_t)pb.n * (size_t)pb.ctot * 8;
+    size_t pc = (size_t)256 << 20;
+    pc = per ? pc / per : 1;
+    if (pc < 1) pc = 1;
+    if (pc > (size_t)pb.naux) pc = pb.naux;
+    return (int)pc;
+}
+
+size_t fp64_build_workspace(const Problem &pb, int pc) {
+    size_t n = pb.n, nd = pb.nd;
+    size_t b = 0;
+    b += align_up(n * pb.ctot * 8);                 // Z
+    b += align_up((size_t)pc * n * pb.ctot * 8);    // T chunk
+    b += align_up(nd * (size_t)pb.naux * 8);        // gamma
+    b += align_up(nd * n * n * 8);                  // dense D (J-only path)
+    return b;
+}
+
+jk_status fp64_build(jk_ctx *h, const Problem &pb, cudaStream_t st) {
+    const bool J = pb.wantJ, K = pb.wantK;
+    const int n = pb.n, naux = pb.naux, nd = pb.nd;
+    const long long n2 = (long long)n * n;
+    const int pc = fp64_default_pchunk(pb);
+    Arena &ar = h->arena;
+    double *Z = ar.take<double>((size_t)n * pb.ctot);
+    double *T = ar.take<double>((size_t)pc * n * pb.ctot);
+    double *gamma = ar.take<double>((size_t)nd * naux);
+    double *D = ar.take<double>((size_t)nd * n2);
+    if (!Z || !T || !gamma || !D)
+        return set_error(h, JK_ERR_OOM, "workspace too small for the FP64 build");
+
+    if (K) {
+        JK_TRY(pack_z(h, pb, Z, st));
+        DensTab tab;
+        for (int s = 0; s < nd; s++) {
+            tab.Y[s] = pb.sym[s] ? pb.X[s] : pb.Y[s];
+            tab.offX[s] = pb.offX[s];
+            tab.k[s] = pb.k[s];
+        }
+        for (int P0 = 0; P0 < naux; P0 += pc) {
+            const int np = naux - P0 < pc ? naux - P0 : pc;
+            // T[(p,mu)][c] = sum_lam L^{P0+p}[mu][lam] Z[lam][c]
+            JK_TRY(dgemm(h, 1, np * n, pb.ctot, n,
+                         gop(pb.L + (long long)P0 * n2, 0, n, 0, 1, n),
+                         gop(Z, 0, 1, 0, pb.ctot, n),
+                         T, pb.ctot, 0, 1.0, 0.0, st));
+            if (J) {
+                LaunchScope ls(h, KK_GAMMA, st);
+                gamma_panel_kernel<<<dim3(np, nd), 256, 0, st>>>(T, n, pb.ctot, tab, gamma, naux, P0);
+                JK_LAUNCH_CHECK(h);
+            }
+            // K_s (+)= sum_{p,i} T[p][mu][offX+i] T[p][nu][offY+i]
+            for (int s = 0; s < nd; s++) {
+                const long long sp = (long long)n * pb.ctot;
+                JK_TRY(dgemm(h, 1, n, n, np * pb.k[s],
+                             gop(T + pb.offX[s], 0, pb.ctot, sp, 1, pb.k[s]),
+                             gop(T + pb.offY[s], 0, pb.ctot, sp, 1, pb.k[s]),
+                             pb.K[s], n, 0, 1.0, P0 == 0 ? 0.0 : 1.0, st));
+            }
+        }
+    } else if (J) {
+        // J only: gamma from the dense densities D_s = X_s Y_s^T.
+        for (int s = 0; s < nd; s++) {
+            const double *Ys = pb.sym[s] ? pb.X[s] : pb.Y[s];
+            JK_TRY(dgemm(h, 1, n, n, pb.k[s], gop(pb.X[s], 0, pb.k[s], 0, 1, pb.k[s]),
+                         gop(Ys, 0, pb.k[s], 0, 1, pb.k[s]), D + (long long)s * n2, n, 0,
+                         1.0, 0.0, st));
+        }
+        { LaunchScope ls_f(h, KK_FROB, st);
+        frob_stream_kernel<<<dim3(naux, (nd + 3) / 4), 256, 0, st>>>(pb.L, n2, D, nd, gamma, naux, 0);
+        }
+        JK_LAUNCH_CHECK(h);
+    }
+    if (J) JK_TRY(jstream(h, pb.L, n, naux, gamma, naux, nd, pb.J, st));
+    return JK_OK;
+}
+
+size_t fp64_adjoint_workspace(const Problem &pb, int pc, bool want_dl) {
+    size_t n = pb.n, nd = pb.nd, A = pb.naux;
+    size_t b = 0;
+    b += align_up(n * pb.ctot * 8);                 // Z
+    b += align_up((size_t)pc * n * pb.ctot * 8);    // T chunk
+    b += 2 * align_up(nd * A * 8);                  // gamma, c
+    b += 2 * align_up(nd * n * n * 8);              // D, J(V)
+    b += 2 * align_up((size_t)pc * n * pb.kmax * 8);  // U, Vp
+    if (want_dl) b += align_up((size_t)pc * n * n * 8);  // G chunk
+    return b;
+}
+
+jk_status fp64_adjoint(jk_ctx *h, const Problem &pb, const double *W,
+                       const double *V, double *dX, double *dY, double *dL,
+                       cudaStream_t st) {
+    const int n = pb.n, naux = pb.naux, nd = pb.nd;
+    const long long n2 = (long long)n * n;
+    const int pc = fp64_default_pchunk(pb);
+    Arena &ar = h->arena;
+    double *Z = ar.take<double>((size_t)n * pb.ctot);
+    double *T = ar.take<double>((size_t)pc * n * pb.ctot);
+    double *gamma = ar.take<double>((size_t)nd * naux);
+    double *cps = ar.take<double>((size_t)nd * naux);
+    double *D = ar.take<double>((size_t)nd * n2);
+    double *JV = ar.take<double>((size_t)nd * n2);
+    double *U = ar.take<double>((size_t)pc * n * pb.kmax);
+    double *Vp = ar.take<double>((size_t)pc * n * pb.kmax);
+    double *G = dL ? ar.take<double>((size_t)pc * n2) : nullptr;
+    if (!Z || !T || !gamma || !cps || !D || !JV || !U || !Vp || (dL && !G))
+        return set_error(h, JK_ERR_OOM, "workspace too small for the FP64 adjoint");
+
+    // Offsets of each density's block in dX / dY.
+    long long boff[kMaxDens + 1];
+    boff[0] = 0;
+    for (int s = 0; s < nd; s++) boff[s + 1] = boff[s] + (long long)n * pb.k[s];
+    JK_CUDA_TRY(h, cudaMemsetAsync(dX, 0, boff[nd] * sizeof(double), st));
+    JK_CUDA_TRY(h, cudaMemsetAsync(dY, 0, boff[nd] * sizeof(double), st));
+
+    JK_TRY(pack_z(h, pb, Z, st));
+    for (int s = 0; s < nd; s++) {
+        const double *Ys = pb.sym[s] ? pb.X[s] : pb.Y[s];
+        JK_TRY(dgemm(h, 1, n, n, pb.k[s], gop(pb.X[s], 0, pb.k[s], 0, 1, pb.k[s]),
+                     gop(Ys, 0, pb.k[s], 0, 1, pb.k[s]), D + (long long)s * n2, n, 0,
+                     1.0, 0.0, st));
+    }
+    if (V) {
+        // c_{P,s} = <V_s, L^P>, J(V_s) = sum_P c_{P,s} L^P
+        { LaunchScope ls_f(h, KK_FROB, st);
+        frob_stream_kernel<<<dim3(naux, (nd + 3) / 4), 256, 0, st>>>(pb.L, n2, V, nd, cps, naux, 0);
+        }
+        JK_LAUNCH_CHECK(h);
+        double *jv[kMaxDens];
+        for (int s = 0; s < nd; s++) jv[s] = JV + (long long)s * n2;
+        JK_TRY(jstream(h, pb.L, n, naux, cps, naux, nd, jv, st));
+        if (dL) {
+            { LaunchScope ls_f(h, KK_FROB, st);
+            frob_stream_kernel<<<dim3(naux, (nd + 3) / 4), 256, 0, st>>>(pb.L, n2, D, nd, gamma, naux, 0);
+            }
+            JK_LAUNCH_CHECK(h);
+        }
+    }
+    const bool need_chunks = (W != nullptr) || (dL != nullptr);
+    for (int P0 = 0; need_chunks && P0 < naux; P0 += pc) {
+        const int np = naux - P0 < pc ? naux - P0 : pc;
+        const long long sp = (long long)n * pb.ctot;
+        if (W)
+            JK_TRY(dgemm(h, 1, np * n, pb.ctot, n,
+                         gop(pb.L + (long long)P0 * n2, 0, n, 0, 1, n),
+                         gop(Z, 0, 1, 0, pb.ctot, n), T, pb.ctot, 0, 1.0, 0.0, st));
+        if (dL) JK_CUDA_TRY(h, cudaMemsetAsync(G, 0, (size_t)np * n2 * sizeof(double), st));
+        for (int s = 0; W && s < nd; s++) {
+            const int k = pb.k[s];
+            const double *Ws = W + (long long)s * n2;
+            const double *Xs = pb.X[s];
+            const double *Ys = pb.sym[s] ? pb.X[s] : pb.Y[s];
+            const long long nk = (long long)n * k;
+            // U^p = W_s T_Y^p ; Vp^p = W_s^T T_X^p     (batched over p)
+            JK_TRY(dgemm(h, np, n, k, n, gop(Ws, 0, n, 0, 1, n),
+                         gop(T + pb.offY[s], sp, 1, 0, pb.ctot, n), U, k, nk, 1.0, 0.0, st));
+            JK_TRY(dgemm(h, np, n, k, n, gop(Ws, 0, 1, 0, n, n),
+                         gop(T + pb.offX[s], sp, 1, 0, pb.ctot, n), Vp, k, nk, 1.0, 0.0, st));
+            // dX_s += sum_{p,lam} L^p[mu][lam] U^p[lam][i]; dY_s likewise with Vp
+            JK_TRY(dgemm(h, 1, n, k, np * n, gop(pb.L + (long long)P0 * n2, 0, n, n2, 1, n),
+                         gop(U, 0, 1, nk, k, n), dX + boff[s], k, 0, 1.0, 1.0, st));
+            JK_TRY(dgemm(h, 1, n, k, np * n, gop(pb.L + (long long)P0 * n2, 0, n, n2, 1, n),
+                         gop(Vp, 0, 1, nk, k, n), dY + boff[s], k, 0, 1.0, 1.0, st));
+            if (dL) {
+                // G^p += U^p X_s^T + Y_s Vp^p^T
+                JK_TRY(dgemm(h, np, n, n, k, gop(U, nk, k, 0, 1, k), gop(Xs, 0, k, 0, 1, k),
+                             G, n, n2, 1.0, 1.0, st));
+                JK_TRY(dgemm(h, np, n, n, k, gop(Ys, 0, k, 0, 1, k), gop(Vp, nk, k, 0, 1, k),
+                             G, n, n2, 1.0, 1.0, st));
+            }
+        }
+        if (dL) {
+            dim3 g2((unsigned)((n2 + 255) / 256), np);
+            if (V) {
+                { LaunchScope ls_m(h, KK_MISC, st);
+                gterms_kernel<<<g2, 256, 0, st>>>(G, n2, np, nd, D, V, cps, gamma, naux, P0);
+                }
+                JK_LAUNCH_CHECK(h);
+            }
+            { LaunchScope ls_m(h, KK_MISC, st);
+            symmetrize_kernel<<<g2, 256, 0, st>>>(G, n, dL + (long long)P0 * n2);
+            }
+            JK_LAUNCH_CHECK(h);
+        }
+    }
+    if (V) {
+        for (int s = 0; s < nd; s++) {
+            const int k = pb.k[s];
+            const double *Xs = pb.X[s];
+            const double *Ys = pb.sym[s] ? pb.X[s] : pb.Y[s];
+            const double *JVs = JV + (long long)s * n2;
+            // dX_s += J(V_s) Y_s ; dY_s += J(V_s) X_s
+            JK_TRY(dgemm(h, 1, n, k, n, gop(JVs, 0, n, 0, 1, n), gop(Ys, 0, 1, 0, k, n),
+                         dX + boff[s], k, 0, 1.0, 1.0, st));
+            JK_TRY(dgemm(h, 1, n, k, n, gop(JVs, 0, n, 0, 1, n), gop(Xs, 0, 1, 0, k, n),
+                         dY + boff[s], k, 0, 1.0, 1.0, st));
+        }
+    }
+    for (int s = 0; s < nd; s++) {
+        if (!pb.sym[s]) continue;
+        long long cnt = boff[s + 1] - boff[s];
+        { LaunchScope ls_m(h, KK_MISC, st);
+        fold_sym_kernel<<<(unsigned)((cnt + 255) / 256), 256, 0, st>>>(dX + boff[s], dY + boff[s], cnt);
+        }
+        JK_LAUNCH_CHECK(h);
+    }
+    return JK_OK;
+}
+
+}  // namespace jk

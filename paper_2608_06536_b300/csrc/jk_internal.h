@@ -1,0 +1,153 @@
+// Internal declarations shared by the libjk.so translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "../../include/jk.h"
+
+namespace jk {
+
+constexpr size_t kArenaAlign = 256;
+constexpr int kMaxDens = 64;           // densities per molecule in one call
+
+inline size_t align_up(size_t x, size_t a = kArenaAlign) { return (x + a - 1) / a * a; }
+
+// Bump allocator over the caller's arena; reset at the start of every call.
+struct Arena {
+    char *base = nullptr;
+    size_t bytes = 0;
+    size_t off = 0;
+    size_t high = 0;
+    void reset(size_t start) { off = start; }
+    template <class T> T *take(size_t count) {
+        size_t need = align_up(count * sizeof(T));
+        if (off + need > bytes) return nullptr;
+        T *p = reinterpret_cast<T *>(base + off);
+        off += need;
+        if (off > high) high = off;
+        return p;
+    }
+};
+
+// Device-side status words at the start of the arena.
+struct DeviceFlags {
+    int error;        // JK_* code raised by a kernel (0 = none)
+    int where;        // kernel-specific detail
+    int pad[62];
+};
+
+// Kernel kinds for launch accounting / event timing.
+enum KernelKind {
+    KK_DGEMM = 0, KK_JSTREAM, KK_FROB, KK_GAMMA, KK_PACK, KK_MISC,
+    KK_SLICE, KK_OZGEMM, KK_OZREDUCE, KK_COUNT
+};
+
+struct Profiler {
+    bool on = false;
+    long long launches = 0;
+    struct Rec { int kind; cudaEvent_t a, b; };
+    std::vector<Rec> recs;
+    std::vector<cudaEvent_t> pool;
+    size_t used = 0;
+    double ms[KK_COUNT] = {};
+    long long cnt[KK_COUNT] = {};
+};
+
+}  // namespace jk
+
+struct jk_ctx {
+    jk::Arena arena;
+    jk::DeviceFlags *flags = nullptr;    // first bytes of the arena
+    std::string last_error;
+    int device = -1;
+    jk::Profiler prof;
+};
+
+namespace jk {
+
+// Per-call view of one molecule's problem after validation.
+struct Problem {
+    int n = 0, naux = 0, nd = 0;
+    const double *L = nullptr;
+    int k[kMaxDens];
+    int sym[kMaxDens];
+    const double *X[kMaxDens];
+    const double *Y[kMaxDens];
+    // Column layout of the panel matrix Z = [X_0 | Y_0 | X_1 | Y_1 | ...]
+    // (Y_s omitted for symmetric densities): offsets of X_s and Y_s in Z.
+    int offX[kMaxDens], offY[kMaxDens];
+    int ctot = 0;       // columns of Z
+    int ksum = 0;       // sum of k_s
+    int kmax = 0;
+    // Per-density outputs ([n][n] each); NULL entries are not formed.
+    double *J[kMaxDens];
+    double *K[kMaxDens];
+    bool wantJ = false, wantK = false;
+};
+
+jk_status set_error(jk_ctx *h, jk_status s, const char *fmt, ...);
+
+#define JK_CUDA_TRY(h, call)                                                   \
+    do {                                                                       \
+        cudaError_t e_ = (call);                                               \
+        if (e_ != cudaSuccess)                                                 \
+            return ::jk::set_error((h), JK_ERR_CUDA, "%s failed: %s (%s:%d)",  \
+                                   #call, cudaGetErrorString(e_), __FILE__,    \
+                                   __LINE__);                                  \
+    } while (0)
+
+#define JK_LAUNCH_CHECK(h)                                                     \
+    do {                                                                       \
+        cudaError_t e_ = cudaGetLastError();                                   \
+        if (e_ != cudaSuccess)                                                 \
+            return ::jk::set_error((h), JK_ERR_CUDA, "launch failed: %s (%s:%d)", \
+                                   cudaGetErrorString(e_), __FILE__, __LINE__); \
+    } while (0)
+
+#define JK_TRY(expr)                                                           \
+    do {                                                                       \
+        jk_status s_ = (expr);                                                 \
+        if (s_ != JK_OK) return s_;                                            \
+    } while (0)
+
+// ---- FP64 engine (fp64.cu) ------------------------------------------------
+size_t fp64_build_workspace(const Problem &pb, int pchunk);
+size_t fp64_adjoint_workspace(const Problem &pb, int pchunk, bool want_dl);
+int fp64_default_pchunk(const Problem &pb);
+jk_status fp64_build(jk_ctx *h, const Problem &pb, cudaStream_t st);
+jk_status fp64_adjoint(jk_ctx *h, const Problem &pb, const double *W,
+                       const double *V, double *dX, double *dY, double *dL,
+                       cudaStream_t st);
+
+// ---- split-precision engine (split.cu) -----------------------------------
+size_t split_build_workspace(const Problem &pb);
+size_t split_adjoint_workspace(const Problem &pb, bool want_dl);
+jk_status split_build(jk_ctx *h, const Problem &pb, cudaStream_t st);
+jk_status split_adjoint(jk_ctx *h, const Problem &pb, const double *W,
+                        const double *V, double *dX, double *dY, double *dL,
+                        cudaStream_t st);
+
+// ---- batched builds (batched.cu) ------------------------------------------
+jk_status batched_build(jk_ctx *h, int nmol, const Problem *pbs, jk_precision p,
+                        cudaStream_t st);
+
+// ---- batched builds (batched.cu) ------------------------------------------
+jk_status batched_build(jk_ctx *h, int nmol, const Problem *pbs, jk_precision p,
+                        cudaStream_t st);
+
+// Brackets one kernel launch: counts it and, when profiling is on, records
+// CUDA events before and after it on the launch stream.
+struct LaunchScope {
+    jk_ctx *h;
+    int kind;
+    cudaStream_t st;
+    cudaEvent_t b = nullptr;
+    LaunchScope(jk_ctx *h_, int kind_, cudaStream_t st_);
+    ~LaunchScope();
+};
+
+}  // namespace jk

@@ -1,0 +1,83 @@
+// Launch accounting and per-kernel-kind CUDA-event timing.
+#include "jk_internal.h"
+
+namespace jk {
+
+static const char *kKindNames[KK_COUNT] = {
+    "dgemm_fp64", "jstream_fp64", "frob_stream_fp64", "gamma_panel_fp64", "pack",
+    "misc", "slice", "ozgemm_tcgen05", "oz_reduce"};
+
+static cudaEvent_t take_event(Profiler &p) {
+    if (p.used == p.pool.size()) {
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+        p.pool.push_back(e);
+    }
+    return p.pool[p.used++];
+}
+
+LaunchScope::LaunchScope(jk_ctx *h_, int kind_, cudaStream_t st_) : h(h_), kind(kind_), st(st_) {
+    h->prof.launches++;
+    if (!h->prof.on) return;
+    cudaEvent_t a = take_event(h->prof);
+    b = take_event(h->prof);
+    if (!a || !b) { b = nullptr; return; }
+    cudaEventRecord(a, st);
+    h->prof.recs.push_back({kind, a, b});
+}
+
+LaunchScope::~LaunchScope() {
+    if (b) cudaEventRecord(b, st);
+}
+
+static void drain(jk_ctx *h) {
+    Profiler &p = h->prof;
+    for (auto &r : p.recs) {
+        float ms = 0.f;
+        if (cudaEventSynchronize(r.b) == cudaSuccess && cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+            p.ms[r.kind] += ms;
+            p.cnt[r.kind] += 1;
+        }
+        cudaGetLastError();
+    }
+    p.recs.clear();
+    p.used = 0;
+}
+
+}  // namespace jk
+
+using namespace jk;
+
+extern "C" {
+
+int64_t jk_launch_count(jk_handle h) { return h ? h->prof.launches : 0; }
+
+jk_status jk_profile_enable(jk_handle h, int32_t on) {
+    if (!h) return JK_ERR_ARG;
+    h->prof.on = on != 0;
+    return JK_OK;
+}
+
+jk_status jk_profile_reset(jk_handle h) {
+    if (!h) return JK_ERR_ARG;
+    drain(h);
+    h->prof.launches = 0;
+    for (int i = 0; i < KK_COUNT; i++) { h->prof.ms[i] = 0; h->prof.cnt[i] = 0; }
+    return JK_OK;
+}
+
+int32_t jk_profile_kinds(void) { return KK_COUNT; }
+
+const char *jk_profile_kind_name(int32_t kind) {
+    return (kind >= 0 && kind < KK_COUNT) ? kKindNames[kind] : nullptr;
+}
+
+jk_status jk_profile_read(jk_handle h, int32_t kind, double *ms, int64_t *launches) {
+    if (!h || kind < 0 || kind >= KK_COUNT) return JK_ERR_ARG;
+    drain(h);
+    if (ms) *ms = h->prof.ms[kind];
+    if (launches) *launches = h->prof.cnt[kind];
+    return JK_OK;
+}
+
+}  // extern "C"

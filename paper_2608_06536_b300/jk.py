@@ -1,0 +1,329 @@
+"""Thin ctypes binding of libjk.so (argument marshalling only).
+
+Every step of the J/K path runs in the library's CUDA kernels; this module
+only turns torch tensors into device pointers and sizes, owns the workspace
+arena (a torch byte tensor) and raises on a non-OK status.  There is no CPU
+fallback: without the compiled library the import of the engine fails.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+import threading
+
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libjk.so")
+
+JK_OK, JK_ERR_ARG, JK_ERR_SHAPE, JK_ERR_OOM, JK_ERR_CUDA, JK_ERR_TIMEOUT, JK_ERR_UNSUPPORTED = range(7)
+JK_FP64, JK_SPLIT_BF16 = 0, 1
+JK_OP_BUILD, JK_OP_ADJOINT, JK_OP_BATCHED = 0, 1, 2
+
+PRECISIONS = {"fp64": JK_FP64, "split": JK_SPLIT_BF16, "split_bf16": JK_SPLIT_BF16}
+
+
+class jk_factor(ct.Structure):
+    _fields_ = [("nbf", ct.c_int32), ("naux", ct.c_int32), ("L", ct.c_void_p)]
+
+
+class jk_density(ct.Structure):
+    _fields_ = [("k", ct.c_int32), ("symmetric", ct.c_int32),
+                ("X", ct.c_void_p), ("Y", ct.c_void_p)]
+
+
+class JKError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"jk status {status}: {msg}")
+        self.status = status
+
+
+_lib = None
+_lib_lock = threading.Lock()
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libjk.so and declare its C signatures (raises if it is missing)."""
+    global _lib
+    with _lib_lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            raise ImportError(f"libjk.so not built at {path}; run paper_2608_06536_b300/build.py")
+        L = ct.CDLL(path)
+        vp, sz = ct.c_void_p, ct.c_size_t
+        L.jk_create.argtypes = [ct.POINTER(vp), vp, sz]
+        L.jk_destroy.argtypes = [vp]
+        L.jk_workspace_query.argtypes = [ct.c_int, ct.c_int32, ct.POINTER(jk_factor),
+                                         ct.POINTER(ct.c_int32), ct.c_int32,
+                                         ct.POINTER(jk_density), ct.c_int, ct.POINTER(sz)]
+        L.jk_build.argtypes = [vp, ct.POINTER(jk_factor), ct.c_int32, ct.POINTER(jk_density),
+                               vp, vp, ct.c_int, vp]
+        L.jk_build_batched.argtypes = [vp, ct.c_int32, ct.POINTER(jk_factor),
+                                       ct.POINTER(ct.c_int32), ct.POINTER(jk_density),
+                                       ct.POINTER(vp), ct.POINTER(vp), ct.c_int, vp]
+        L.jk_adjoint.argtypes = [vp, ct.POINTER(jk_factor), ct.c_int32, ct.POINTER(jk_density),
+                                 vp, vp, vp, vp, vp, ct.c_int, vp]
+        L.jk_sync_status.argtypes = [vp, vp]
+        L.jk_status_string.argtypes = [ct.c_int]
+        L.jk_status_string.restype = ct.c_char_p
+        L.jk_last_error.argtypes = [vp]
+        L.jk_last_error.restype = ct.c_char_p
+        L.jk_version.restype = ct.c_char_p
+        L.jk_launch_count.argtypes = [vp]
+        L.jk_launch_count.restype = ct.c_int64
+        L.jk_profile_enable.argtypes = [vp, ct.c_int32]
+        L.jk_profile_reset.argtypes = [vp]
+        L.jk_profile_kinds.restype = ct.c_int32
+        L.jk_profile_kind_name.argtypes = [ct.c_int32]
+        L.jk_profile_kind_name.restype = ct.c_char_p
+        L.jk_profile_read.argtypes = [vp, ct.c_int32, ct.POINTER(ct.c_double), ct.POINTER(ct.c_int64)]
+        for f in (L.jk_profile_enable, L.jk_profile_reset, L.jk_profile_read):
+            f.restype = ct.c_int
+        for f in (L.jk_create, L.jk_destroy, L.jk_workspace_query, L.jk_build,
+                  L.jk_build_batched, L.jk_adjoint, L.jk_sync_status):
+            f.restype = ct.c_int
+        _lib = L
+        return L
+
+
+def _ptr(t):
+    return None if t is None else ct.c_void_p(t.data_ptr())
+
+
+def _dev_f64(t, device):
+    """Contiguous float64 tensor on `device` with a 16-byte aligned base."""
+    t = torch.as_tensor(t, dtype=torch.float64, device=device)
+    if not t.is_contiguous() or t.data_ptr() % 16:
+        t = t.contiguous().clone()
+    return t
+
+
+def _stream_ptr(stream):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ct.c_void_p(s.cuda_stream)
+
+
+class Densities:
+    """Factored densities D_s = X_s Y_s^T marshalled for the C ABI."""
+
+    def __init__(self, X, Y=None, sym=None, device=None):
+        nd = len(X)
+        sym = list(sym) if sym is not None else [False] * nd
+        Y = list(Y) if Y is not None else [None] * nd
+        self.X = [_dev_f64(x, device) for x in X]
+        self.Y = [None if (sym[s] or Y[s] is None) else _dev_f64(Y[s], device) for s in range(nd)]
+        self.sym = [bool(sym[s] or Y[s] is None) for s in range(nd)]
+        self.k = [int(x.shape[1]) for x in self.X]
+        self.n = int(self.X[0].shape[0])
+        arr = (jk_density * nd)()
+        for s in range(nd):
+            arr[s].k = self.k[s]
+            arr[s].symmetric = 1 if self.sym[s] else 0
+            arr[s].X = self.X[s].data_ptr()
+            arr[s].Y = self.Y[s].data_ptr() if self.Y[s] is not None else None
+        self.c = arr
+
+    def __len__(self):
+        return len(self.X)
+
+
+class Engine:
+    """One handle over a device workspace arena (grown on demand)."""
+
+    def __init__(self, device=None, workspace_bytes: int = 0):
+        self.lib = load_library()
+        dev = torch.device(device) if device is not None else torch.device("cuda")
+        if dev.type != "cuda":
+            raise ValueError("the J/K engine runs on a CUDA device only")
+        if dev.index is None:
+            dev = torch.device("cuda", torch.cuda.current_device())
+        self.device = dev
+        self._ws = None
+        self._h = ct.c_void_p()
+        if workspace_bytes:
+            self._ensure(workspace_bytes)
+
+    # -- arena ---------------------------------------------------------------
+    def _ensure(self, nbytes: int):
+        if self._ws is not None and self._ws.numel() >= nbytes:
+            return
+        self.close()
+        nbytes = max(int(nbytes), 1 << 20)
+        self._ws = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        h = ct.c_void_p()
+        self._check(self.lib.jk_create(ct.byref(h), ct.c_void_p(self._ws.data_ptr()), nbytes), None)
+        self._h = h
+        if getattr(self, "_profile_on", False):
+            self.lib.jk_profile_enable(self._h, 1)
+
+    def close(self):
+        if self._h:
+            self.lib.jk_destroy(self._h)
+            self._h = ct.c_void_p()
+        self._ws = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def workspace_bytes(self) -> int:
+        return 0 if self._ws is None else self._ws.numel()
+
+    def _check(self, status, h):
+        if status != JK_OK:
+            msg = self.lib.jk_last_error(h).decode() if h else ""
+            if not msg:
+                msg = self.lib.jk_status_string(status).decode()
+            raise JKError(status, msg)
+
+    def sync_status(self, stream=None):
+        self._check(self.lib.jk_sync_status(self._h, _stream_ptr(stream)), self._h)
+
+    # -- instrumentation -----------------------------------------------------
+    def launch_count(self) -> int:
+        return int(self.lib.jk_launch_count(self._h)) if self._h else 0
+
+    def profile(self, on: bool = True):
+        if self._h:
+            self._check(self.lib.jk_profile_enable(self._h, 1 if on else 0), self._h)
+        self._profile_on = on
+
+    def profile_reset(self):
+        if self._h:
+            self._check(self.lib.jk_profile_reset(self._h), self._h)
+
+    def profile_read(self) -> dict:
+        """{kind name: (total ms, launches)} since the last reset."""
+        out = {}
+        if not self._h:
+            return out
+        for kind in range(self.lib.jk_profile_kinds()):
+            ms, cnt = ct.c_double(), ct.c_int64()
+            self._check(self.lib.jk_profile_read(self._h, kind, ct.byref(ms), ct.byref(cnt)), self._h)
+            if cnt.value:
+                out[self.lib.jk_profile_kind_name(kind).decode()] = (ms.value, cnt.value)
+        return out
+
+    # -- queries -------------------------------------------------------------
+    def query(self, op, factors, dens_c, nd_per_mol, nd, precision) -> int:
+        nbytes = ct.c_size_t()
+        ndm = (ct.c_int32 * len(nd_per_mol))(*nd_per_mol) if nd_per_mol else None
+        st = self.lib.jk_workspace_query(op, len(factors), factors, ndm, nd, dens_c,
+                                         precision, ct.byref(nbytes))
+        self._check(st, None)
+        return nbytes.value
+
+    # -- entry points --------------------------------------------------------
+    def build(self, L, X, Y=None, sym=None, precision="fp64", want_j=True, want_k=True,
+              J=None, K=None, stream=None):
+        """J_s, K_s ([nd][n][n] float64) for D_s = X_s Y_s^T over factor L."""
+        p = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        L = _dev_f64(L, self.device)
+        dens = Densities(X, Y, sym, self.device)
+        naux, n = int(L.shape[0]), int(L.shape[1])
+        f = jk_factor(n, naux, L.data_ptr())
+        nd = len(dens)
+        self._ensure(self.query(JK_OP_BUILD, (jk_factor * 1)(f), dens.c, None, nd, p))
+        if want_j and J is None:
+            J = torch.empty((nd, n, n), dtype=torch.float64, device=self.device)
+        if want_k and K is None:
+            K = torch.empty((nd, n, n), dtype=torch.float64, device=self.device)
+        st = self.lib.jk_build(self._h, ct.byref(f), nd, dens.c, _ptr(J if want_j else None),
+                               _ptr(K if want_k else None), p, _stream_ptr(stream))
+        self._check(st, self._h)
+        return (J if want_j else None), (K if want_k else None)
+
+    def build_batched(self, mols, precision="fp64", want_j=True, want_k=True, stream=None):
+        """mols: list of (L, X list, Y list or None, sym list or None).
+        Returns per-molecule (J, K) lists of [nd_m][n_m][n_m] tensors."""
+        p = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        nmol = len(mols)
+        Ls, dens, outs = [], [], []
+        fac = (jk_factor * nmol)()
+        nd_per = []
+        for m, (L, X, Y, sym) in enumerate(mols):
+            L = _dev_f64(L, self.device)
+            d = Densities(X, Y, sym, self.device)
+            Ls.append(L); dens.append(d)
+            fac[m] = jk_factor(int(L.shape[1]), int(L.shape[0]), L.data_ptr())
+            nd_per.append(len(d))
+        ndt = sum(nd_per)
+        dall = (jk_density * ndt)()
+        i = 0
+        for d in dens:
+            for s in range(len(d)):
+                dall[i] = d.c[s]; i += 1
+        self._ensure(self.query(JK_OP_BATCHED, fac, dall, nd_per, ndt, p))
+        Jp = (ct.c_void_p * ndt)(); Kp = (ct.c_void_p * ndt)()
+        i = 0
+        for m, d in enumerate(dens):
+            n = d.n
+            Jm = torch.empty((len(d), n, n), dtype=torch.float64, device=self.device) if want_j else None
+            Km = torch.empty((len(d), n, n), dtype=torch.float64, device=self.device) if want_k else None
+            outs.append((Jm, Km))
+            for s in range(len(d)):
+                if want_j:
+                    Jp[i] = Jm[s].data_ptr()
+                if want_k:
+                    Kp[i] = Km[s].data_ptr()
+                i += 1
+        ndm = (ct.c_int32 * nmol)(*nd_per)
+        st = self.lib.jk_build_batched(self._h, nmol, fac, ndm, dall, Jp if want_j else None,
+                                       Kp if want_k else None, p, _stream_ptr(stream))
+        self._check(st, self._h)
+        return outs
+
+    def adjoint(self, L, X, Y=None, sym=None, W=None, V=None, want_dl=True,
+                precision="fp64", stream=None):
+        """(dX list, dY list, dL or None) for E = sum_s <W_s,K_s> + <V_s,J_s>."""
+        p = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        L = _dev_f64(L, self.device)
+        dens = Densities(X, Y, sym, self.device)
+        naux, n = int(L.shape[0]), int(L.shape[1])
+        f = jk_factor(n, naux, L.data_ptr())
+        nd = len(dens)
+        W = None if W is None else _dev_f64(W, self.device).reshape(nd, n, n)
+        V = None if V is None else _dev_f64(V, self.device).reshape(nd, n, n)
+        self._ensure(self.query(JK_OP_ADJOINT, (jk_factor * 1)(f), dens.c, None, nd, p))
+        tot = sum(n * k for k in dens.k)
+        dX = torch.empty(tot, dtype=torch.float64, device=self.device)
+        dY = torch.empty(tot, dtype=torch.float64, device=self.device)
+        dL = torch.empty((naux, n, n), dtype=torch.float64, device=self.device) if want_dl else None
+        st = self.lib.jk_adjoint(self._h, ct.byref(f), nd, dens.c, _ptr(W), _ptr(V), _ptr(dX),
+                                 _ptr(dY), _ptr(dL), p, _stream_ptr(stream))
+        self._check(st, self._h)
+        outX, outY, off = [], [], 0
+        for k in dens.k:
+            outX.append(dX[off:off + n * k].view(n, k))
+            outY.append(dY[off:off + n * k].view(n, k))
+            off += n * k
+        return outX, outY, dL
+
+
+_default = {}
+
+
+def default_engine(device=None) -> Engine:
+    dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+    key = (dev.type, dev.index)
+    if key not in _default:
+        _default[key] = Engine(dev)
+    return _default[key]
+
+
+def jk_build(L, X, Y=None, sym=None, precision="fp64", **kw):
+    return default_engine(L.device if torch.is_tensor(L) and L.is_cuda else None).build(
+        L, X, Y, sym, precision, **kw)
+
+
+def jk_build_batched(mols, precision="fp64", **kw):
+    return default_engine().build_batched(mols, precision, **kw)
+
+
+def jk_adjoint(L, X, Y=None, sym=None, W=None, V=None, precision="fp64", **kw):
+    return default_engine(L.device if torch.is_tensor(L) and L.is_cuda else None).adjoint(
+        L, X, Y, sym, W, V, precision=precision, **kw)

@@ -1,0 +1,101 @@
+"""Host-side checks of the C ABI (no GPU needed): the library loads, exports
+every entry point include/jk.h declares, and validates arguments before any
+device work."""
+import ctypes as ct
+import os
+import re
+
+import pytest
+
+from paper_2608_06536_b300 import build as pkg_build
+from paper_2608_06536_b300 import jk
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if not fn.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", fn)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names |= set(re.findall(r"\b(jk_[a-z0-9_]+)\s*\(", text))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    pkg_build.build()
+    return jk.load_library()
+
+
+def test_exports_every_declared_symbol(lib):
+    names = declared_symbols()
+    assert "jk_build" in names and "jk_build_batched" in names and "jk_adjoint" in names
+    raw = ct.CDLL(jk.LIB_PATH)
+    missing = [n for n in names if not hasattr(raw, n)]
+    assert not missing, missing
+
+
+def test_status_strings_and_version(lib):
+    assert lib.jk_status_string(jk.JK_OK) == b"ok"
+    assert lib.jk_status_string(jk.JK_ERR_OOM) == b"workspace arena too small"
+    assert lib.jk_version().startswith(b"jk-b300")
+
+
+def _one(n=10, naux=7, k=3, sym=0):
+    f = jk.jk_factor(n, naux, 0x1000)
+    d = (jk.jk_density * 1)()
+    d[0].k, d[0].symmetric, d[0].X, d[0].Y = k, sym, 0x2000, 0x3000
+    return f, d
+
+
+def test_workspace_query_host_only(lib):
+    f, d = _one()
+    nb = ct.c_size_t()
+    fa = (jk.jk_factor * 1)(f)
+    assert lib.jk_workspace_query(jk.JK_OP_BUILD, 1, fa, None, 1, d, jk.JK_FP64, ct.byref(nb)) == jk.JK_OK
+    small = nb.value
+    assert small > 0
+    f2, d2 = _one(n=100, naux=500, k=20)
+    fa2 = (jk.jk_factor * 1)(f2)
+    assert lib.jk_workspace_query(jk.JK_OP_BUILD, 1, fa2, None, 1, d2, jk.JK_FP64, ct.byref(nb)) == jk.JK_OK
+    assert nb.value > small
+    assert lib.jk_workspace_query(jk.JK_OP_ADJOINT, 1, fa2, None, 1, d2, jk.JK_FP64, ct.byref(nb)) == jk.JK_OK
+
+
+@pytest.mark.parametrize("n,naux,k", [(0, 5, 1), (5, 0, 1), (5, 5, 0), (5, 5, 100)])
+def test_workspace_query_rejects_bad_shapes(lib, n, naux, k):
+    f, d = _one(n, naux, k)
+    nb = ct.c_size_t()
+    fa = (jk.jk_factor * 1)(f)
+    assert lib.jk_workspace_query(jk.JK_OP_BUILD, 1, fa, None, 1, d, jk.JK_FP64, ct.byref(nb)) == jk.JK_ERR_SHAPE
+
+
+def test_workspace_query_rejects_bad_args(lib):
+    f, d = _one()
+    fa = (jk.jk_factor * 1)(f)
+    nb = ct.c_size_t()
+    assert lib.jk_workspace_query(jk.JK_OP_BUILD, 1, fa, None, 1, d, 7, ct.byref(nb)) == jk.JK_ERR_ARG
+    assert lib.jk_workspace_query(jk.JK_OP_BUILD, 1, fa, None, 1, d, jk.JK_FP64, None) == jk.JK_ERR_ARG
+    assert lib.jk_workspace_query(9, 1, fa, None, 1, d, jk.JK_FP64, ct.byref(nb)) == jk.JK_ERR_ARG
+    # batched: nd must equal the sum of nd_per_mol
+    ndm = (ct.c_int32 * 1)(1)
+    assert lib.jk_workspace_query(jk.JK_OP_BATCHED, 1, fa, ndm, 2, d, jk.JK_FP64, ct.byref(nb)) == jk.JK_ERR_SHAPE
+
+
+def test_create_rejects_bad_arena(lib):
+    h = ct.c_void_p()
+    assert lib.jk_create(None, None, 0) == jk.JK_ERR_ARG
+    assert lib.jk_create(ct.byref(h), None, 1 << 20) == jk.JK_ERR_ARG
+    assert lib.jk_create(ct.byref(h), ct.c_void_p(0x1001), 1 << 20) == jk.JK_ERR_ARG
+    assert not h.value
+
+
+def test_calls_on_null_handle(lib):
+    f, d = _one()
+    assert lib.jk_build(None, ct.byref(f), 1, d, None, None, 0, None) == jk.JK_ERR_ARG
+    assert lib.jk_adjoint(None, ct.byref(f), 1, d, None, None, None, None, None, 0, None) == jk.JK_ERR_ARG
+    assert lib.jk_sync_status(None, None) == jk.JK_ERR_ARG
+    assert lib.jk_last_error(None) == b""
