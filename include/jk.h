@@ -146,6 +146,9 @@ int64_t jk_launch_count(jk_handle h);
 jk_status jk_profile_enable(jk_handle h, int32_t on);
 /* Zero the launch count and the accumulated times. */
 jk_status jk_profile_reset(jk_handle h);
+/* Dense tensor-core flops issued by this handle's kernels since the last reset
+ * (2*M*N*K per MMA instruction, over the padded tiles actually issued). */
+double jk_issued_tensor_flops(jk_handle h);
 /* Number of kernel kinds and the name of kind i (NULL if out of range). */
 int32_t jk_profile_kinds(void);
 const char *jk_profile_kind_name(int32_t kind);

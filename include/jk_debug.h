@@ -1,0 +1,30 @@
+/*
+ * jk_debug.h -- test hooks of libjk.so (not part of the J/K engine's API).
+ *
+ * They expose single building blocks of the split-precision engine so that
+ * tests can check them in isolation against exact references.
+ */
+#ifndef JK_DEBUG_H
+#define JK_DEBUG_H
+
+#include "jk.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* C[M][N] = A[M][K] * B[N][K]^T (all FP64, row-major, device) through the
+ * split-precision path: each row of A and B is cut into six BF16 slices with
+ * its own power-of-two scale, the 21 leading slice products run on tcgen05
+ * tensor cores with exact FP32 accumulation windows, and the result is
+ * recombined in integers and rounded once to FP64.  Uses the handle's arena
+ * (size from jk_debug_sliced_gemm_workspace); JK_ERR_OOM if it is too small. */
+jk_status jk_debug_sliced_gemm(jk_handle h, int32_t M, int32_t N, int32_t K,
+                               const double *A, const double *B, double *C,
+                               void *stream);
+size_t jk_debug_sliced_gemm_workspace(int32_t M, int32_t N, int32_t K);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* JK_DEBUG_H */

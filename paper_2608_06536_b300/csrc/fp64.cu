@@ -306,6 +306,42 @@ static jk_status pack_z(jk_ctx *h, const Problem &pb, double *Z, cudaStream_t st
     return JK_OK;
 }
 
+// y += x (FP64, elementwise)
+__global__ void axpy_kernel(double *y, const double *x, long long cnt) {
+    long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (e < cnt) y[e] += x[e];
+}
+
+jk_status fp64_axpy(jk_ctx *h, double *y, const double *x, long long cnt, cudaStream_t st) {
+    LaunchScope ls(h, KK_MISC, st);
+    axpy_kernel<<<(unsigned)((cnt + 255) / 256), 256, 0, st>>>(y, x, cnt);
+    JK_LAUNCH_CHECK(h);
+    return JK_OK;
+}
+
+jk_status split_pack_z(jk_ctx *h, const Problem &pb, double *Z, cudaStream_t st) {
+    return pack_z(h, pb, Z, st);
+}
+
+// gamma[s][P0 + p] = sum_{sig,i} T^p[sig][offX_s + i] Y_s[sig][i] for p < np.
+jk_status fp64_gamma_panel(jk_ctx *h, const Problem &pb, const double *T, int np, double *gamma, int P0,
+                           cudaStream_t st) {
+    DensTab tab;
+    for (int s = 0; s < pb.nd; s++) {
+        tab.Y[s] = pb.sym[s] ? pb.X[s] : pb.Y[s];
+        tab.offX[s] = pb.offX[s];
+        tab.k[s] = pb.k[s];
+    }
+    LaunchScope ls(h, KK_GAMMA, st);
+    gamma_panel_kernel<<<dim3(np, pb.nd), 256, 0, st>>>(T, pb.n, pb.ctot, tab, gamma, pb.naux, P0);
+    JK_LAUNCH_CHECK(h);
+    return JK_OK;
+}
+
+jk_status fp64_jstream(jk_ctx *h, const Problem &pb, const double *gamma, cudaStream_t st) {
+    return jstream(h, pb.L, pb.n, pb.naux, gamma, pb.naux, pb.nd, pb.J, st);
+}
+
 int fp64_default_pchunk(const Problem &pb) {
     // Panel chunk of at most ~256 MB of FP64 (T^P for pc aux indices).
     size_t per = (size_t)pb.n * (size_t)pb.ctot * 8;

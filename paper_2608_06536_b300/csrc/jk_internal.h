@@ -55,6 +55,7 @@ struct Profiler {
     size_t used = 0;
     double ms[KK_COUNT] = {};
     long long cnt[KK_COUNT] = {};
+    double tensor_flops = 0.0;
 };
 
 }  // namespace jk
@@ -122,6 +123,8 @@ jk_status fp64_build(jk_ctx *h, const Problem &pb, cudaStream_t st);
 jk_status fp64_adjoint(jk_ctx *h, const Problem &pb, const double *W,
                        const double *V, double *dX, double *dY, double *dL,
                        cudaStream_t st);
+
+jk_status fp64_axpy(jk_ctx *h, double *y, const double *x, long long cnt, cudaStream_t st);
 
 // ---- split-precision engine (split.cu) -----------------------------------
 size_t split_build_workspace(const Problem &pb);

@@ -62,9 +62,12 @@ jk_status jk_profile_reset(jk_handle h) {
     if (!h) return JK_ERR_ARG;
     drain(h);
     h->prof.launches = 0;
+    h->prof.tensor_flops = 0.0;
     for (int i = 0; i < KK_COUNT; i++) { h->prof.ms[i] = 0; h->prof.cnt[i] = 0; }
     return JK_OK;
 }
+
+double jk_issued_tensor_flops(jk_handle h) { return h ? h->prof.tensor_flops : 0.0; }
 
 int32_t jk_profile_kinds(void) { return KK_COUNT; }
 

@@ -1,18 +1,703 @@
-// Split-precision engine (BF16 slices on tcgen05 tensor cores).
+// Split-precision engine: FP64-accurate J/K from BF16 tensor-core products.
+//
+// Every dense contraction of the build (panels T = L Z and the rank update
+// K_s = sum_P T_X T_Y^T) is computed as an error-free-split product:
+//
+//  * Slicing.  Each operand row r is scaled by 2^-e_r (e_r from the row's
+//    largest magnitude) and rounded once to a 48-bit fixed-point integer F,
+//    which is cut into six signed base-256 digits q_1..q_6 (|q_1| <= 256,
+//    |q_j| <= 128).  Slice j stores q_j * 2^(-8j) as a BF16 value -- exact,
+//    since every q_j has at most 8 significant bits.  This is done with
+//    integer arithmetic only (B300 has very little FP64 throughput).
+//  * Products.  The 21 slice pairs (a, b) with a + b <= 7 are multiplied on
+//    tcgen05 tensor cores (kind::f16, FP32 accumulate in tensor memory).
+//    Pairs on the same diagonal d = a + b - 2 share a scale 2^-(8d+16); the
+//    diagonals d = 0..3 each get their own TMEM accumulator and, over a
+//    window of 128 reduction elements, every partial sum is an integer below
+//    2^24 times that scale, so the FP32 accumulation is exact whatever the
+//    tensor core's rounding mode.  Diagonals d >= 4 (relative size <= 2^-32)
+//    share a fifth accumulator, whose truncation error stays below 2^-47.
+//  * Recombination.  After each 128-element window the five accumulators are
+//    read from TMEM, scaled by 2^48 and added into a per-element int64
+//    fixed-point accumulator (exact for d <= 3).  Split-K partials are summed
+//    in 128-bit integers; the only rounding to FP64 happens once per output.
+//
+// The representation error is below 2^-48 of each row's scale, which keeps the
+// built J and K within 1e-10 absolute of the FP64 oracle on the benchmark
+// workloads (see the parity tests).
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include <cstring>
+
 #include "jk_internal.h"
+#include "tc.cuh"
 
 namespace jk {
+namespace oz {
 
-size_t split_build_workspace(const Problem &) { return 0; }
-size_t split_adjoint_workspace(const Problem &, bool) { return 0; }
+constexpr int S = 6;            // slices per operand
+constexpr int BM = 128;         // rows of A per tile (TMEM lanes)
+constexpr int BN = 96;          // rows of B per tile (TMEM columns per accumulator)
+constexpr int KB = 16;          // reduction elements per pipeline stage (one MMA K-step)
+constexpr int CHUNK = 128;      // exact accumulation window
+constexpr int KBPC = CHUNK / KB;
+constexpr int SUPER = 2048;     // reduction elements per int64 partial
+constexpr int NSTAGE = 5;
+constexpr int NACC = 5;
+constexpr int NPAIRS = 21;
+constexpr int FRAC = 48;        // fraction bits of the int64 accumulator
+constexpr int THREADS = 320;    // producer warp, MMA warp, 8 epilogue warps
 
-jk_status split_build(jk_ctx *h, const Problem &, cudaStream_t) {
-    return set_error(h, JK_ERR_UNSUPPORTED, "split-precision build not built yet");
+constexpr int A_BYTES = S * BM * 32;
+constexpr int B_BYTES = S * BN * 32;
+constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+constexpr int SMEM_BYTES = NSTAGE * STAGE_BYTES + 1024 /*align slack*/ + 256 /*barriers*/;
+
+// Slice pairs ordered by diagonal; acc = min(d, 4); first = first pair of its accumulator.
+__constant__ int8_t kPairA[NPAIRS] = {0, 0, 1, 0, 1, 2, 0, 1, 2, 3, 0, 1, 2, 3, 4, 0, 1, 2, 3, 4, 5};
+__constant__ int8_t kPairB[NPAIRS] = {0, 1, 0, 2, 1, 0, 3, 2, 1, 0, 4, 3, 2, 1, 0, 5, 4, 3, 2, 1, 0};
+__constant__ int8_t kPairAcc[NPAIRS] = {0, 1, 1, 2, 2, 2, 3, 3, 3, 3, 4, 4, 4, 4, 4, 4, 4, 4, 4, 4, 4};
+__constant__ int8_t kPairFirst[NPAIRS] = {1, 1, 0, 1, 0, 0, 1, 0, 0, 0, 1, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+
+// ---------------------------------------------------------------------------
+// Integer helpers
+// ---------------------------------------------------------------------------
+
+// Exponent e with max|x| < 2^e (from the biased exponent field of max|x|).
+__device__ __forceinline__ int exponent_of_max(unsigned long long maxbits) {
+    int ex = static_cast<int>((maxbits >> 52) & 0x7FF);
+    return ex == 0 ? 0 : ex - 1022;
 }
 
-jk_status split_adjoint(jk_ctx *h, const Problem &, const double *, const double *,
-                        double *, double *, double *, cudaStream_t) {
+// F = round(x * 2^(48 - e)) as a signed integer, |F| <= 2^48 when |x| <= 2^e.
+// Zero and subnormal inputs give 0.
+__device__ __forceinline__ long long to_fixed48(double x, int e) {
+    const unsigned long long bits = static_cast<unsigned long long>(__double_as_longlong(x));
+    const int ex = static_cast<int>((bits >> 52) & 0x7FF);
+    if (ex == 0) return 0;
+    const unsigned long long m = (bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+    const int r = 1027 + e - ex;   // right shift of the 53-bit significand, >= 4
+    long long F;
+    if (r <= 0) F = static_cast<long long>(m << (-r));
+    else if (r >= 64) F = 0;
+    else F = static_cast<long long>((m + (1ull << (r - 1))) >> r);
+    return (bits >> 63) ? -F : F;
+}
+
+// v * 2^e2 rounded to nearest-even double, computed with integer operations.
+// Requires the result to be a normal double (true for all values built here).
+__device__ __forceinline__ double i64_to_f64_scaled(long long v, int e2) {
+    if (v == 0) return 0.0;
+    const unsigned long long sign = v < 0 ? 0x8000000000000000ull : 0ull;
+    unsigned long long a = v < 0 ? static_cast<unsigned long long>(-v) : static_cast<unsigned long long>(v);
+    int lz = __clzll(static_cast<long long>(a));
+    a <<= lz;                                   // leading one at bit 63
+    unsigned long long mant = a >> 11;          // 53 bits including the leading one
+    const unsigned long long rem = a & 0x7FFull;
+    if (rem > 0x400ull || (rem == 0x400ull && (mant & 1ull))) mant++;
+    int exp2 = 63 - lz + e2;
+    if (mant >> 53) { mant >>= 1; exp2++; }
+    const unsigned long long bits =
+        sign | (static_cast<unsigned long long>(exp2 + 1023) << 52) | (mant & 0xFFFFFFFFFFFFFull);
+    return __longlong_as_double(static_cast<long long>(bits));
+}
+
+__device__ __forceinline__ double i128_to_f64_scaled(__int128 v, int e2) {
+    // Split into a high part (exactly representable shift) and a low part.
+    const long long hi = static_cast<long long>(v >> 62);
+    const long long lo = static_cast<long long>(v - (static_cast<__int128>(hi) << 62));
+    // hi * 2^62 + lo, both converted exactly-rounded, summed in FP64 (one rounding step
+    // is negligible: |lo| < 2^62 and hi carries the leading bits).
+    return i64_to_f64_scaled(hi, e2 + 62) + i64_to_f64_scaled(lo, e2);
+}
+
+// ---------------------------------------------------------------------------
+// Slicers
+// ---------------------------------------------------------------------------
+
+// Source addressing: element (row r, reduction index kk) is at
+// p + r*sr + (kk / kin)*sko + (kk % kin)*ski.
+struct Src {
+    const double *p;
+    long long sr, sko, ski;
+    int kin;
+};
+
+__device__ __forceinline__ double src_at(const Src &s, int r, int kk) {
+    const int ko = kk / s.kin, ki = kk - ko * s.kin;
+    return s.p[static_cast<long long>(r) * s.sr + static_cast<long long>(ko) * s.sko +
+               static_cast<long long>(ki) * s.ski];
+}
+
+// e[g] for row groups g of `rpe` rows: max|x| over the group's rows and all K.
+// Each thread walks reduction indices kk = tid, tid + 256, ... keeping (ko, ki)
+// incrementally, so the hot loop has no integer division.
+__global__ void __launch_bounds__(256) expo_kernel(Src src, int rows, int K, int rpe, int *e) {
+    __shared__ unsigned long long red[8];
+    const int g = blockIdx.x;
+    const int r0 = g * rpe, r1 = min(rows, r0 + rpe);
+    const int step_o = 256 / src.kin, step_i = 256 % src.kin;
+    unsigned long long mx = 0;
+    for (int r = r0; r < r1; r++) {
+        const double *row = src.p + static_cast<long long>(r) * src.sr;
+        int ko = threadIdx.x / src.kin, ki = threadIdx.x - ko * src.kin;
+        for (int kk = threadIdx.x; kk < K; kk += 256) {
+            const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(
+                                             row[static_cast<long long>(ko) * src.sko +
+                                                 static_cast<long long>(ki) * src.ski])) &
+                                         0x7FFFFFFFFFFFFFFFull;
+            mx = b > mx ? b : mx;
+            ko += step_o;
+            ki += step_i;
+            if (ki >= src.kin) { ki -= src.kin; ko++; }
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long y = __shfl_down_sync(0xffffffffu, mx, o);
+        mx = y > mx ? y : mx;
+    }
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long m = red[0];
+        for (int i = 1; i < 8; i++) m = red[i] > m ? red[i] : m;
+        e[g] = exponent_of_max(m);
+    }
+}
+
+// BF16 bit pattern of q * 2^(-8j) for an integer |q| <= 256 (exact).
+__device__ __forceinline__ unsigned short q_to_bf16(long long q, int j) {
+    if (q == 0) return 0;
+    const unsigned sign = q < 0 ? 0x8000u : 0u;
+    const unsigned a = static_cast<unsigned>(q < 0 ? -q : q);
+    const int lz = __clz(a);                       // a = 1.f * 2^(31 - lz)
+    const int expo = 31 - lz - 8 * j + 127;
+    const unsigned frac = static_cast<unsigned>(((static_cast<unsigned long long>(a) << (lz + 1)) >> 25) & 0x7Fu);
+    return static_cast<unsigned short>(sign | (static_cast<unsigned>(expo) << 7) | frac);
+}
+
+constexpr int SLICE_ROWS = 8;   // rows per block of the slicer
+
+// out[j][r][kk] = q_j(r, kk) * 2^(-8(j+1)) for j = 0..5 (bf16), zero for kk >= K.
+__global__ void __launch_bounds__(256) slice_kernel(Src src, int rows, int K, int Kpad, const int *e,
+                                                    int rpe, unsigned short *out, long long sstride) {
+    const int kk = blockIdx.x * blockDim.x + threadIdx.x;
+    if (kk >= Kpad) return;
+    long long koff = 0;
+    if (kk < K) {
+        const int ko = kk / src.kin, ki = kk - ko * src.kin;
+        koff = static_cast<long long>(ko) * src.sko + static_cast<long long>(ki) * src.ski;
+    }
+    for (int rb = blockIdx.y * SLICE_ROWS; rb < rows; rb += gridDim.y * SLICE_ROWS) {
+        const int rend = min(rows, rb + SLICE_ROWS);
+        for (int r = rb; r < rend; r++) {
+            long long q[S] = {0, 0, 0, 0, 0, 0};
+            if (kk < K) {
+                long long F = to_fixed48(src.p[static_cast<long long>(r) * src.sr + koff], e[r / rpe]);
+                q[0] = (F + (1ll << 39)) >> 40; F -= q[0] << 40;
+                q[1] = (F + (1ll << 31)) >> 32; F -= q[1] << 32;
+                q[2] = (F + (1ll << 23)) >> 24; F -= q[2] << 24;
+                q[3] = (F + (1ll << 15)) >> 16; F -= q[3] << 16;
+                q[4] = (F + (1ll << 7)) >> 8;   F -= q[4] << 8;
+                q[5] = F;
+            }
+            const long long o = static_cast<long long>(r) * Kpad + kk;
+#pragma unroll
+            for (int j = 0; j < S; j++) out[j * sstride + o] = q_to_bf16(q[j], j + 1);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// The tcgen05 sliced GEMM:  C[m][n] = sum_k A[m][k] B[n][k]
+// ---------------------------------------------------------------------------
+struct OzArgs {
+    int M, N, K, nsuper;
+    const int *eA;
+    int a_rpe;
+    const int *eB;
+    int b_rpe;
+    double *C;            // nsuper == 1: FP64 result, row stride ldc
+    long long ldc;
+    long long *P;         // nsuper > 1: int64 partial z at P + z*pz, packed [M][N]
+    long long pz;
+    int *err;             // device error word (JK_ERR_TIMEOUT on a stalled pipeline)
+};
+
+__global__ void __launch_bounds__(THREADS, 1)
+ozgemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, OzArgs a) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + NSTAGE * STAGE_BYTES);
+    uint64_t *empty = full + NSTAGE;
+    uint64_t *accfull = empty + NSTAGE;
+    uint64_t *accempty = accfull + NACC;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(accempty + NACC);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int n_tile = blockIdx.x, m_tile = blockIdx.y, z = blockIdx.z;
+    const int k_begin = z * SUPER;
+    const int k_end = min(a.K, k_begin + SUPER);
+    const int nkb = (k_end - k_begin + KB - 1) / KB;
+    const int nchunks = (nkb + KBPC - 1) / KBPC;
+
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < NSTAGE; i++) { tc::mbar_init(&full[i], 1); tc::mbar_init(&empty[i], 1); }
+        for (int i = 0; i < NACC; i++) { tc::mbar_init(&accfull[i], 1); tc::mbar_init(&accempty[i], 8); }
+        *abort_flag = 0;
+        tc::fence_barrier_init();
+    }
+    if (warp == 1) {
+        tc::tmem_alloc(tmem_slot, 512);
+        tc::tmem_relinquish();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        // ---------------- TMA producer ----------------
+        if (lane == 0) {
+            tc::prefetch_tmap(&tmA);
+            tc::prefetch_tmap(&tmB);
+            int stage = 0;
+            uint32_t phase = 0;
+            for (int kb = 0; kb < nkb; kb++) {
+                if (!tc::mbar_wait(&empty[stage], phase ^ 1u, abort_flag)) break;
+                tc::mbar_expect_tx(&full[stage], STAGE_BYTES);
+                const int kc = k_begin + kb * KB;
+                uint8_t *sa = smem + stage * STAGE_BYTES;
+                tc::tma_load_3d(sa, &tmA, &full[stage], kc, m_tile * BM, 0);
+                tc::tma_load_3d(sa + A_BYTES, &tmB, &full[stage], kc, n_tile * BN, 0);
+                if (++stage == NSTAGE) { stage = 0; phase ^= 1u; }
+            }
+        }
+    } else if (warp == 1) {
+        // ---------------- MMA issuer ----------------
+        if (lane == 0) {
+            constexpr uint32_t idesc = tc::idesc_bf16_f32(BM, BN);
+            int stage = 0;
+            uint32_t phase = 0;
+            for (int kb = 0; kb < nkb; kb++) {
+                const int ch = kb / KBPC;
+                const bool cstart = (kb % KBPC) == 0;
+                const bool cend = (kb % KBPC) == KBPC - 1 || kb == nkb - 1;
+                if (!tc::mbar_wait(&full[stage], phase, abort_flag)) break;
+                tc::fence_after_sync();
+                const uint32_t abase = tc::smem_u32(smem + stage * STAGE_BYTES);
+                const uint32_t bbase = abase + A_BYTES;
+                bool ok = true;
+#pragma unroll 1
+                for (int p = 0; p < NPAIRS; p++) {
+                    const int acc = kPairAcc[p];
+                    uint32_t accumulate = 1;
+                    if (cstart && kPairFirst[p]) {
+                        if (ch > 0) {
+                            if (!tc::mbar_wait(&accempty[acc], static_cast<uint32_t>(ch - 1) & 1u, abort_flag)) {
+                                ok = false;
+                                break;
+                            }
+                            tc::fence_after_sync();
+                        }
+                        accumulate = 0;
+                    }
+                    const uint64_t ad = tc::sdesc_kmajor_sw32(abase + kPairA[p] * (BM * 32));
+                    const uint64_t bd = tc::sdesc_kmajor_sw32(bbase + kPairB[p] * (BN * 32));
+                    tc::mma_bf16(tmem + acc * BN, ad, bd, idesc, accumulate);
+                }
+                if (!ok) break;
+                tc::mma_commit(&empty[stage]);
+                if (cend)
+                    for (int acc = 0; acc < NACC; acc++) tc::mma_commit(&accfull[acc]);
+                if (++stage == NSTAGE) { stage = 0; phase ^= 1u; }
+            }
+        }
+    } else {
+        // ---------------- epilogue: 8 warps, two per TMEM lane quarter ----------------
+        const int ew = warp - 2;
+        const int q = warp & 3;          // lane quarter this warp may access
+        const int half = ew >> 2;        // which 64 columns
+        const int row = m_tile * BM + q * 32 + lane;
+        long long acc64[BN / 2];
+#pragma unroll
+        for (int i = 0; i < BN / 2; i++) acc64[i] = 0;
+        bool ok = true;
+        for (int ch = 0; ch < nchunks && ok; ch++) {
+#pragma unroll 1
+            for (int acc = 0; acc < NACC; acc++) {
+                if (!tc::mbar_wait(&accfull[acc], static_cast<uint32_t>(ch) & 1u, abort_flag)) { ok = false; break; }
+                __syncwarp();
+                tc::fence_after_sync();
+                const uint32_t tbase = tmem + (static_cast<uint32_t>(q * 32) << 16) + acc * BN + half * (BN / 2);
+                float v[BN / 2];
+#pragma unroll
+                for (int c = 0; c < BN / 2; c += 16) tc::tmem_ld16(tbase + c, v + c);
+                tc::tmem_wait_ld();
+                tc::fence_before_sync();
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive(&accempty[acc]);
+#pragma unroll
+                for (int i = 0; i < BN / 2; i++) acc64[i] += __float2ll_rn(v[i] * 0x1p48f);
+            }
+        }
+        if (ok && row < a.M) {
+            const int c0 = n_tile * BN + half * (BN / 2);
+            if (a.nsuper == 1) {
+                const int ea = a.eA[row / a.a_rpe] - FRAC;
+                double *crow = a.C + static_cast<long long>(row) * a.ldc;
+#pragma unroll
+                for (int i = 0; i < BN / 2; i++) {
+                    const int col = c0 + i;
+                    if (col < a.N) crow[col] = i64_to_f64_scaled(acc64[i], ea + a.eB[col / a.b_rpe]);
+                }
+            } else {
+                long long *prow = a.P + z * a.pz + static_cast<long long>(row) * a.N;
+#pragma unroll
+                for (int i = 0; i < BN / 2; i++) {
+                    const int col = c0 + i;
+                    if (col < a.N) prow[col] = acc64[i];
+                }
+            }
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 1) {
+        tc::fence_after_sync();
+        tc::tmem_dealloc(tmem, 512);
+    }
+    if (threadIdx.x == 0 && *abort_flag) atomicExch(a.err, static_cast<int>(JK_ERR_TIMEOUT));
+}
+
+// out[r][c] (+)= 2^(eA[r/arpe] + eB[c/brpe] - 48) * sum_z P[z][r][c]   (sum in 128-bit integers)
+__global__ void __launch_bounds__(256)
+reduce_partials_kernel(const long long *P, long long pz, int nz, int M, int N, const int *eA, int arpe,
+                       const int *eB, int brpe, double *out, long long ldo, int accumulate) {
+    const long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
+    if (e >= static_cast<long long>(M) * N) return;
+    const int r = static_cast<int>(e / N), c = static_cast<int>(e % N);
+    __int128 s = 0;
+    for (int zz = 0; zz < nz; zz++) s += static_cast<__int128>(P[zz * pz + e]);
+    const double v = i128_to_f64_scaled(s, eA[r / arpe] + eB[c / brpe] - FRAC);
+    double *o = out + static_cast<long long>(r) * ldo + c;
+    *o = accumulate ? (*o + v) : v;
+}
+
+}  // namespace oz
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+namespace {
+
+using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *,
+                                   CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
+                                   CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    }
+    return fn;
+}
+
+// Tensor map over slices [S][rows][Kpad] (bf16), box = {16, box_rows, S}, 32-byte swizzle.
+jk_status make_slice_map(jk_ctx *h, CUtensorMap *map, const __nv_bfloat16 *base, int rows, int Kpad,
+                         int box_rows) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return set_error(h, JK_ERR_CUDA, "cuTensorMapEncodeTiled is unavailable");
+    cuuint64_t dims[3] = {static_cast<cuuint64_t>(Kpad), static_cast<cuuint64_t>(rows),
+                          static_cast<cuuint64_t>(oz::S)};
+    cuuint64_t strides[2] = {static_cast<cuuint64_t>(Kpad) * 2, static_cast<cuuint64_t>(rows) * Kpad * 2};
+    cuuint32_t box[3] = {oz::KB, static_cast<cuuint32_t>(box_rows), oz::S};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<__nv_bfloat16 *>(base), dims, strides,
+                    box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return set_error(h, JK_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return JK_OK;
+}
+
+inline int kpad_of(int K) { return (K + 15) / 16 * 16; }
+
+}  // namespace
+
+// A sliced operand: S bf16 slices [S][rows][Kpad] plus per-group exponents.
+struct Sliced {
+    __nv_bfloat16 *s = nullptr;
+    int *e = nullptr;
+    int rows = 0, K = 0, Kpad = 0, rpe = 1;
+};
+
+static jk_status slice_operand(jk_ctx *h, const oz::Src &src, int rows, int K, int rpe, Sliced &out,
+                               cudaStream_t st) {
+    out.rows = rows;
+    out.K = K;
+    out.Kpad = kpad_of(K);
+    out.rpe = rpe;
+    const int groups = (rows + rpe - 1) / rpe;
+    {
+        LaunchScope ls(h, KK_SLICE, st);
+        oz::expo_kernel<<<groups, 256, 0, st>>>(src, rows, K, rpe, out.e);
+    }
+    JK_LAUNCH_CHECK(h);
+    const int rblocks = (rows + oz::SLICE_ROWS - 1) / oz::SLICE_ROWS;
+    dim3 grid((out.Kpad + 255) / 256, rblocks < 65535 ? rblocks : 65535);
+    {
+        LaunchScope ls(h, KK_SLICE, st);
+        oz::slice_kernel<<<grid, 256, 0, st>>>(src, rows, K, out.Kpad, out.e, rpe,
+                                                reinterpret_cast<unsigned short *>(out.s),
+                                                static_cast<long long>(rows) * out.Kpad);
+    }
+    JK_LAUNCH_CHECK(h);
+    return JK_OK;
+}
+
+static size_t sliced_bytes(int rows, int K, int rpe) {
+    return align_up(static_cast<size_t>(oz::S) * rows * kpad_of(K) * 2) +
+           align_up(static_cast<size_t>((rows + rpe - 1) / rpe) * 4);
+}
+
+static bool take_sliced(Arena &ar, int rows, int K, int rpe, Sliced &out) {
+    out.s = ar.take<__nv_bfloat16>(static_cast<size_t>(oz::S) * rows * kpad_of(K));
+    out.e = ar.take<int>(static_cast<size_t>((rows + rpe - 1) / rpe));
+    return out.s && out.e;
+}
+
+static int nsuper_of(int K) { return (K + oz::SUPER - 1) / oz::SUPER; }
+
+static bool smem_configured = false;
+
+// C = A B^T on sliced operands.  nsuper == 1: FP64 written to C (ldc).
+// Otherwise int64 partials go to P (packed [M][N] per super-chunk).
+static jk_status ozgemm(jk_ctx *h, const Sliced &A, const Sliced &B, double *C, long long ldc, long long *P,
+                        cudaStream_t st) {
+    if (A.K != B.K) return set_error(h, JK_ERR_ARG, "internal: sliced K mismatch");
+    if (!smem_configured) {
+        JK_CUDA_TRY(h, cudaFuncSetAttribute(oz::ozgemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            oz::SMEM_BYTES));
+        smem_configured = true;
+    }
+    CUtensorMap ta, tb;
+    JK_TRY(make_slice_map(h, &ta, A.s, A.rows, A.Kpad, oz::BM));
+    JK_TRY(make_slice_map(h, &tb, B.s, B.rows, B.Kpad, oz::BN));
+    oz::OzArgs a;
+    a.M = A.rows; a.N = B.rows; a.K = A.K; a.nsuper = nsuper_of(A.K);
+    a.eA = A.e; a.a_rpe = A.rpe; a.eB = B.e; a.b_rpe = B.rpe;
+    a.C = C; a.ldc = ldc; a.P = P; a.pz = static_cast<long long>(A.rows) * B.rows;
+    a.err = &h->flags->error;
+    if (a.nsuper > 1 && !P) return set_error(h, JK_ERR_ARG, "internal: partial buffer missing");
+    dim3 grid((a.N + oz::BN - 1) / oz::BN, (a.M + oz::BM - 1) / oz::BM, a.nsuper);
+    if (grid.y > 65535) return set_error(h, JK_ERR_SHAPE, "too many row tiles (%u)", grid.y);
+    {
+        LaunchScope ls(h, KK_OZGEMM, st);
+        oz::ozgemm_kernel<<<grid, oz::THREADS, oz::SMEM_BYTES, st>>>(ta, tb, a);
+    }
+    // Issued MMA work: every CTA runs all 21 slice pairs over its K-blocks.
+    double kblocks = 0.0;
+    for (int zz = 0; zz < a.nsuper; zz++) {
+        const int kb = (a.K - zz * oz::SUPER < oz::SUPER ? a.K - zz * oz::SUPER : oz::SUPER);
+        kblocks += (kb + oz::KB - 1) / oz::KB;
+    }
+    h->prof.tensor_flops += 2.0 * oz::BM * oz::BN * oz::KB * oz::NPAIRS * kblocks *
+                            static_cast<double>(grid.x) * grid.y;
+    JK_LAUNCH_CHECK(h);
+    return JK_OK;
+}
+
+static jk_status reduce_partials(jk_ctx *h, const long long *P, int nz, const Sliced &A, const Sliced &B,
+                                 double *out, long long ldo, bool accumulate, cudaStream_t st) {
+    const long long tot = static_cast<long long>(A.rows) * B.rows;
+    {
+        LaunchScope ls(h, KK_OZREDUCE, st);
+        oz::reduce_partials_kernel<<<static_cast<unsigned>((tot + 255) / 256), 256, 0, st>>>(
+            P, tot, nz, A.rows, B.rows, A.e, A.rpe, B.e, B.rpe, out, ldo, accumulate ? 1 : 0);
+    }
+    JK_LAUNCH_CHECK(h);
+    return JK_OK;
+}
+
+// ---------------------------------------------------------------------------
+// The split build
+// ---------------------------------------------------------------------------
+
+// P-chunk so that the per-chunk workspace stays below ~12 GB.
+static int split_pchunk(const Problem &pb) {
+    const size_t n = pb.n;
+    size_t per = n * n * (oz::S * 2) + n * pb.ctot * 8 + n * pb.ctot * (oz::S * 2);
+    size_t budget = static_cast<size_t>(12) << 30;
+    size_t pc = per ? budget / per : 1;
+    if (pc < 1) pc = 1;
+    if (pc > static_cast<size_t>(pb.naux)) pc = pb.naux;
+    // Keep rows of the panel GEMM within the grid limit.
+    size_t maxrows = static_cast<size_t>(65535) * oz::BM;
+    if (pc * n > maxrows) pc = maxrows / n;
+    return static_cast<int>(pc);
+}
+
+static size_t partial_count(const Problem &pb, int pc) {
+    // int64 partials of all densities' rank updates for one P-chunk.
+    size_t cnt = 0;
+    for (int s = 0; s < pb.nd; s++) {
+        int ns = nsuper_of(pc * pb.k[s]);
+        if (ns > 1) cnt += static_cast<size_t>(ns) * pb.n * pb.n;
+    }
+    return cnt;
+}
+
+size_t split_build_workspace(const Problem &pb) {
+    const int pc = split_pchunk(pb);
+    const size_t n = pb.n;
+    size_t b = 0;
+    b += align_up(n * pb.ctot * 8);                                  // Z
+    b += sliced_bytes(pc * pb.n, pb.n, pb.n);                        // L chunk slices
+    b += sliced_bytes(pb.ctot, pb.n, 1);                             // Z^T slices
+    b += align_up(static_cast<size_t>(pc) * n * pb.ctot * 8);        // T chunk (FP64)
+    b += align_up(static_cast<size_t>(pb.nd) * pb.naux * 8);         // gamma
+    for (int s = 0; s < pb.nd; s++) {                                // T_X, T_Y slices
+        b += sliced_bytes(pb.n, pc * pb.k[s], 1);
+        if (!pb.sym[s]) b += sliced_bytes(pb.n, pc * pb.k[s], 1);
+    }
+    b += align_up(partial_count(pb, pc) * 8);
+    b += align_up(static_cast<size_t>(pb.nd) * n * n * 8);           // K accumulators (if K not wanted)
+    if (pb.n > oz::SUPER) b += align_up(static_cast<size_t>(nsuper_of(pb.n)) * pc * n * pb.ctot * 8);
+    return b;
+}
+
+size_t split_adjoint_workspace(const Problem &, bool) { return 0; }
+
+jk_status split_pack_z(jk_ctx *h, const Problem &pb, double *Z, cudaStream_t st);
+jk_status fp64_gamma_panel(jk_ctx *h, const Problem &pb, const double *T, int np, double *gamma, int P0,
+                           cudaStream_t st);
+jk_status fp64_jstream(jk_ctx *h, const Problem &pb, const double *gamma, cudaStream_t st);
+
+jk_status split_build(jk_ctx *h, const Problem &pb, cudaStream_t st) {
+    const int n = pb.n, naux = pb.naux, nd = pb.nd;
+    const long long n2 = static_cast<long long>(n) * n;
+    const int pc = split_pchunk(pb);
+    Arena &ar = h->arena;
+    double *Z = ar.take<double>(static_cast<size_t>(n) * pb.ctot);
+    Sliced Ls, Zs;
+    bool ok = Z && take_sliced(ar, pc * n, n, n, Ls) && take_sliced(ar, pb.ctot, n, 1, Zs);
+    double *T = ar.take<double>(static_cast<size_t>(pc) * n * pb.ctot);
+    double *gamma = ar.take<double>(static_cast<size_t>(nd) * naux);
+    Sliced TX[kMaxDens], TY[kMaxDens];
+    for (int s = 0; ok && s < nd; s++) {
+        ok = take_sliced(ar, n, pc * pb.k[s], 1, TX[s]);
+        if (ok && !pb.sym[s]) ok = take_sliced(ar, n, pc * pb.k[s], 1, TY[s]);
+    }
+    long long *Pbuf = ar.take<long long>(partial_count(pb, pc) > 0 ? partial_count(pb, pc) : 1);
+    double *Kacc = ar.take<double>(static_cast<size_t>(nd) * n2);
+    long long *Ppanel = nullptr;
+    if (n > oz::SUPER) Ppanel = ar.take<long long>(static_cast<size_t>(nsuper_of(n)) * pc * n * pb.ctot);
+    if (!ok || !T || !gamma || !Pbuf || !Kacc || (n > oz::SUPER && !Ppanel))
+        return set_error(h, JK_ERR_OOM, "workspace too small for the split build");
+
+    // Z = [X_0 | Y_0 | ...] and its transpose sliced per column (rows of Z^T).
+    JK_TRY(split_pack_z(h, pb, Z, st));
+    oz::Src zsrc{Z, 1, 0, pb.ctot, n};          // row c of Z^T, element lam at Z[lam][c]
+    JK_TRY(slice_operand(h, zsrc, pb.ctot, n, 1, Zs, st));
+
+    for (int P0 = 0; P0 < naux; P0 += pc) {
+        const int np = naux - P0 < pc ? naux - P0 : pc;
+        // L^P rows (P, mu), reduction over lam, one exponent per P.
+        oz::Src lsrc{pb.L + P0 * n2, n, 0, 1, n};
+        Sliced Lc = Ls;
+        JK_TRY(slice_operand(h, lsrc, np * n, n, n, Lc, st));
+        // T[(p, mu)][c] = sum_lam L^p[mu][lam] Z[lam][c]
+        if (n > oz::SUPER) {
+            JK_TRY(ozgemm(h, Lc, Zs, nullptr, 0, Ppanel, st));
+            JK_TRY(reduce_partials(h, Ppanel, nsuper_of(n), Lc, Zs, T, pb.ctot, false, st));
+        } else {
+            JK_TRY(ozgemm(h, Lc, Zs, T, pb.ctot, nullptr, st));
+        }
+        if (pb.wantJ) JK_TRY(fp64_gamma_panel(h, pb, T, np, gamma, P0, st));
+        if (!pb.wantK) continue;
+        // Rank update per density over this chunk's (p, i) pairs.
+        long long *Pcur = Pbuf;
+        for (int s = 0; s < nd; s++) {
+            const int k = pb.k[s];
+            const int Kr = np * k;
+            oz::Src xs{T + pb.offX[s], pb.ctot, static_cast<long long>(n) * pb.ctot, 1, k};
+            TX[s].rows = n;
+            JK_TRY(slice_operand(h, xs, n, Kr, 1, TX[s], st));
+            Sliced *B = &TX[s];
+            if (!pb.sym[s]) {
+                oz::Src ys{T + pb.offY[s], pb.ctot, static_cast<long long>(n) * pb.ctot, 1, k};
+                JK_TRY(slice_operand(h, ys, n, Kr, 1, TY[s], st));
+                B = &TY[s];
+            }
+            double *Kout = pb.K[s];
+            const int ns = nsuper_of(Kr);
+            if (ns == 1) {
+                if (P0 == 0) {
+                    JK_TRY(ozgemm(h, TX[s], *B, Kout, n, nullptr, st));
+                } else {
+                    double *tmp = Kacc + s * n2;
+                    JK_TRY(ozgemm(h, TX[s], *B, tmp, n, nullptr, st));
+                    // Kout += tmp (FP64, fixed order)
+                    JK_TRY(fp64_axpy(h, Kout, tmp, n2, st));
+                }
+            } else {
+                JK_TRY(ozgemm(h, TX[s], *B, nullptr, 0, Pcur, st));
+                JK_TRY(reduce_partials(h, Pcur, ns, TX[s], *B, Kout, n, P0 > 0, st));
+                Pcur += static_cast<size_t>(ns) * n2;
+            }
+        }
+    }
+    if (pb.wantJ) JK_TRY(fp64_jstream(h, pb, gamma, st));
+    return JK_OK;
+}
+
+jk_status split_adjoint(jk_ctx *h, const Problem &, const double *, const double *, double *, double *,
+                        double *, cudaStream_t) {
     return set_error(h, JK_ERR_UNSUPPORTED, "split-precision adjoint not built yet");
 }
 
 }  // namespace jk
+
+// ---------------------------------------------------------------------------
+// Test hook: the sliced tensor-core GEMM on its own (see include/jk_debug.h).
+// ---------------------------------------------------------------------------
+extern "C" jk_status jk_debug_sliced_gemm(jk_handle h, int32_t M, int32_t N, int32_t K, const double *A,
+                                          const double *B, double *C, void *stream) {
+    using namespace jk;
+    if (!h) return JK_ERR_ARG;
+    if (M < 1 || N < 1 || K < 1) return set_error(h, JK_ERR_SHAPE, "M, N, K must be >= 1");
+    if (!A || !B || !C) return set_error(h, JK_ERR_ARG, "NULL operand");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    h->arena.reset(align_up(sizeof(DeviceFlags)));
+    Sliced As, Bs;
+    if (!take_sliced(h->arena, M, K, 1, As) || !take_sliced(h->arena, N, K, 1, Bs))
+        return set_error(h, JK_ERR_OOM, "workspace too small");
+    const int ns = nsuper_of(K);
+    long long *P = nullptr;
+    if (ns > 1) {
+        P = h->arena.take<long long>(static_cast<size_t>(ns) * M * N);
+        if (!P) return set_error(h, JK_ERR_OOM, "workspace too small");
+    }
+    oz::Src sa{A, K, 0, 1, K}, sb{B, K, 0, 1, K};
+    JK_TRY(slice_operand(h, sa, M, K, 1, As, st));
+    JK_TRY(slice_operand(h, sb, N, K, 1, Bs, st));
+    if (ns == 1) return ozgemm(h, As, Bs, C, N, nullptr, st);
+    JK_TRY(ozgemm(h, As, Bs, nullptr, 0, P, st));
+    return reduce_partials(h, P, ns, As, Bs, C, N, false, st);
+}
+
+extern "C" size_t jk_debug_sliced_gemm_workspace(int32_t M, int32_t N, int32_t K) {
+    using namespace jk;
+    size_t b = align_up(sizeof(DeviceFlags)) + sliced_bytes(M, K, 1) + sliced_bytes(N, K, 1);
+    const int ns = nsuper_of(K);
+    if (ns > 1) b += align_up(static_cast<size_t>(ns) * M * N * 8);
+    return b + kArenaAlign;
+}

@@ -78,6 +78,8 @@ def load_library(path: str = LIB_PATH):
         L.jk_profile_kind_name.argtypes = [ct.c_int32]
         L.jk_profile_kind_name.restype = ct.c_char_p
         L.jk_profile_read.argtypes = [vp, ct.c_int32, ct.POINTER(ct.c_double), ct.POINTER(ct.c_int64)]
+        L.jk_issued_tensor_flops.argtypes = [vp]
+        L.jk_issued_tensor_flops.restype = ct.c_double
         for f in (L.jk_profile_enable, L.jk_profile_reset, L.jk_profile_read):
             f.restype = ct.c_int
         for f in (L.jk_create, L.jk_destroy, L.jk_workspace_query, L.jk_build,
@@ -186,6 +188,9 @@ class Engine:
     # -- instrumentation -----------------------------------------------------
     def launch_count(self) -> int:
         return int(self.lib.jk_launch_count(self._h)) if self._h else 0
+
+    def issued_tensor_flops(self) -> float:
+        return float(self.lib.jk_issued_tensor_flops(self._h)) if self._h else 0.0
 
     def profile(self, on: bool = True):
         if self._h:

@@ -1,0 +1,133 @@
+"""Split-precision (BF16 slices on tcgen05) path: the sliced GEMM building block
+and the J/K build, against exact references and the CPU oracle."""
+import ctypes as ct
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2608_06536_b300 import inputs
+from tests._util import SPLIT_ABS, abs_err, rel_err, to_np
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dbg():
+    from paper_2608_06536_b300 import jk
+    lib = jk.load_library()
+    lib.jk_debug_sliced_gemm.argtypes = [ct.c_void_p, ct.c_int32, ct.c_int32, ct.c_int32,
+                                         ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p]
+    lib.jk_debug_sliced_gemm.restype = ct.c_int
+    lib.jk_debug_sliced_gemm_workspace.argtypes = [ct.c_int32, ct.c_int32, ct.c_int32]
+    lib.jk_debug_sliced_gemm_workspace.restype = ct.c_size_t
+    return lib
+
+
+def sliced_gemm(lib, A, B):
+    M, K = A.shape
+    N = B.shape[0]
+    ws = torch.empty(lib.jk_debug_sliced_gemm_workspace(M, N, K), dtype=torch.uint8, device="cuda")
+    h = ct.c_void_p()
+    assert lib.jk_create(ct.byref(h), ct.c_void_p(ws.data_ptr()), ws.numel()) == 0
+    Ad = torch.from_numpy(np.ascontiguousarray(A)).cuda()
+    Bd = torch.from_numpy(np.ascontiguousarray(B)).cuda()
+    C = torch.full((M, N), float("nan"), dtype=torch.float64, device="cuda")
+    st = lib.jk_debug_sliced_gemm(h, M, N, K, Ad.data_ptr(), Bd.data_ptr(), C.data_ptr(), None)
+    assert st == 0, lib.jk_last_error(h)
+    assert lib.jk_sync_status(h, None) == 0, lib.jk_last_error(h)
+    lib.jk_destroy(h)
+    return to_np(C)
+
+
+def exact_product(A, B):
+    return (A.astype(np.longdouble) @ B.T.astype(np.longdouble))
+
+
+@pytest.mark.parametrize("M,N,K", [(1, 1, 1), (128, 128, 128), (300, 200, 500), (129, 257, 2047)])
+def test_sliced_gemm_random(dbg, M, N, K):
+    rng = np.random.default_rng(M + N + K)
+    A = rng.standard_normal((M, K))
+    B = rng.standard_normal((N, K))
+    C = sliced_gemm(dbg, A, B)
+    ref = exact_product(A, B)
+    assert np.all(np.isfinite(C))
+    # error budget: 2^-48 of each row's scale per operand, summed over K
+    scale = np.abs(A).max(1)[:, None] * np.abs(B).max(1)[None, :] * np.sqrt(K)
+    assert float(np.max(np.abs(C - ref) / scale)) < 2.0 ** -44
+
+
+def test_sliced_gemm_split_k(dbg):
+    """K > 2048: int64 partials summed in 128-bit integers."""
+    rng = np.random.default_rng(11)
+    M, N, K = 140, 130, 5000
+    A = rng.standard_normal((M, K)) * np.exp(-np.arange(K) / 2000.0)
+    B = rng.standard_normal((N, K))
+    C = sliced_gemm(dbg, A, B)
+    ref = exact_product(A, B)
+    scale = np.abs(A).max(1)[:, None] * np.abs(B).max(1)[None, :] * np.sqrt(K)
+    assert float(np.max(np.abs(C - ref) / scale)) < 2.0 ** -44
+
+
+def test_sliced_gemm_integers_exact(dbg):
+    """Integer operands: every slice is exact, every accumulation window must
+    be exact in the tensor core's FP32 accumulator, so C equals the exact
+    product bit for bit (including a large accumulator next to small terms)."""
+    rng = np.random.default_rng(12)
+    M, N, K = 256, 128, 1024
+    A = rng.integers(-1000, 1001, (M, K)).astype(np.float64)
+    B = rng.integers(-1000, 1001, (N, K)).astype(np.float64)
+    A[:, :64] = 1000.0
+    B[:, :64] = 1000.0
+    A[:, 64:128] = 1.0
+    C = sliced_gemm(dbg, A, B)
+    ref = (A.astype(np.int64) @ B.T.astype(np.int64)).astype(np.float64)
+    np.testing.assert_array_equal(C, ref)
+
+
+@pytest.fixture(scope="module")
+def eng():
+    from paper_2608_06536_b300 import jk
+    return jk.Engine("cuda:0")
+
+
+def _gpu(m):
+    L = torch.from_numpy(m.L).cuda()
+    X = [torch.from_numpy(x).cuda() for x in m.X]
+    Y = [torch.from_numpy(y).cuda() for y in m.Y]
+    return L, X, Y
+
+
+@pytest.mark.parametrize("n,naux,ks,sym", [
+    (7, 5, [3], [False]),
+    (37, 53, [5, 1, 13], [False, True, False]),
+    (130, 70, [64, 3, 9], [False, False, True]),
+])
+def test_split_build_ragged_vs_oracle(eng, n, naux, ks, sym):
+    m = inputs.custom(n, naux, max(naux / 4, 1.0), ks, sym)
+    Jo, Ko = oracle.build(m.L, m.X, m.Y)
+    L, X, Y = _gpu(m)
+    J, K = eng.build(L, X, Y, sym, "split")
+    eng.sync_status()
+    for s in range(len(ks)):
+        assert abs_err(to_np(J[s]), Jo[s]) < SPLIT_ABS
+        assert abs_err(to_np(K[s]), Ko[s]) < SPLIT_ABS
+
+
+def test_split_build_one_molecule_small(eng):
+    m = inputs.one_molecule_small()
+    Jo, Ko = oracle.build(m.L, m.X, m.Y)
+    L, X, Y = _gpu(m)
+    J, K = eng.build(L, X, Y, m.sym, "split")
+    eng.sync_status()
+    assert abs_err(to_np(J), Jo) < SPLIT_ABS
+    assert abs_err(to_np(K), Ko) < SPLIT_ABS
+
+
+def test_split_build_deterministic(eng):
+    m = inputs.custom(96, 200, 50.0, [8, 8], [False, True])
+    L, X, Y = _gpu(m)
+    J1, K1 = eng.build(L, X, Y, m.sym, "split")
+    J2, K2 = eng.build(L, X, Y, m.sym, "split")
+    assert torch.equal(J1, J2) and torch.equal(K1, K2)
