@@ -128,6 +128,35 @@ jk_status jk_adjoint(jk_handle h, const jk_factor *f, int32_t nd,
                      double *dX, double *dY, double *dL,
                      jk_precision p, void *stream);
 
+/* ---- building without a caller arena -------------------------------------
+ * The paper has no counterpart of this entry point; it serves callers that
+ * cannot allocate device memory at all -- e.g. code running inside a CUDA
+ * graph stream capture (where cudaMalloc is illegal), plugins or callbacks
+ * whose host application forbids them to grow the device memory footprint,
+ * or tight loops where an allocation could synchronize the device.
+ *
+ * jk_build_noalloc computes exactly what jk_build(..., JK_FP64, ...) computes
+ * (plain FP64 engine; same kernels, so the same bits) without a handle or an
+ * arena: its workspace is one file-scope device array of
+ * JK_STATIC_SCRATCH_BYTES that every GPU which loads the library holds until
+ * the process exits.  It calls no cudaMalloc, cudaFree or other allocating
+ * routine.  The caller passes inputs and outputs as for jk_build.
+ *  - Returns JK_ERR_OOM, before launching anything, if the problem's FP64
+ *    workspace would exceed JK_STATIC_SCRATCH_BYTES (roughly: the panel
+ *    buffer naux*nbf*ctot*8 bytes, ctot = sum of X and Y widths, plus small
+ *    terms); use jk_build for larger problems.
+ *  - The first call on each device looks up the array's device address
+ *    (cudaGetSymbolAddress) with that device current; make that first call
+ *    before starting any stream capture.
+ *  - All calls on a device share the one array and it keeps the last call's
+ *    contents: calls whose work overlaps on the GPU (different streams, or
+ *    different host threads) race on it and must be serialized by the caller.
+ *  - Pointers are taken to be device memory (not checked); 16-byte alignment
+ *    and shapes are checked as in jk_build (JK_ERR_ARG / JK_ERR_SHAPE). */
+#define JK_STATIC_SCRATCH_BYTES ((size_t)32 << 20)
+jk_status jk_build_noalloc(const jk_factor *f, int32_t nd, const jk_density *d,
+                           double *J, double *K, void *stream);
+
 /* Wait for the stream and report any device-side error flag raised by this
  * handle's kernels (e.g. JK_ERR_TIMEOUT from a bounded wait); clears it. */
 jk_status jk_sync_status(jk_handle h, void *stream);
