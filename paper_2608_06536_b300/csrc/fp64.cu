@@ -177,7 +177,7 @@ struct DensTab {
 };
 
 __global__ void __launch_bounds__(256)
-gamma_panel_kernel(const double *T, int n, int ctot, DensTab tab,
+gamma_panel_kernel(const double *T, int n, long long ctot, DensTab tab,
                    double *gamma, int ldg, int P0) {
     __shared__ double red[8];
     const int p = blockIdx.x, s = blockIdx.y;
@@ -324,8 +324,8 @@ jk_status split_pack_z(jk_ctx *h, const Problem &pb, double *Z, cudaStream_t st)
 }
 
 // gamma[s][P0 + p] = sum_{sig,i} T^p[sig][offX_s + i] Y_s[sig][i] for p < np.
-jk_status fp64_gamma_panel(jk_ctx *h, const Problem &pb, const double *T, int np, double *gamma, int P0,
-                           cudaStream_t st) {
+jk_status fp64_gamma_panel(jk_ctx *h, const Problem &pb, const double *T, long long ldT, int np, double *gamma,
+                           int P0, cudaStream_t st) {
     DensTab tab;
     for (int s = 0; s < pb.nd; s++) {
         tab.Y[s] = pb.sym[s] ? pb.X[s] : pb.Y[s];
@@ -333,7 +333,7 @@ jk_status fp64_gamma_panel(jk_ctx *h, const Problem &pb, const double *T, int np
         tab.k[s] = pb.k[s];
     }
     LaunchScope ls(h, KK_GAMMA, st);
-    gamma_panel_kernel<<<dim3(np, pb.nd), 256, 0, st>>>(T, pb.n, pb.ctot, tab, gamma, pb.naux, P0);
+    gamma_panel_kernel<<<dim3(np, pb.nd), 256, 0, st>>>(T, pb.n, ldT, tab, gamma, pb.naux, P0);
     JK_LAUNCH_CHECK(h);
     return JK_OK;
 }

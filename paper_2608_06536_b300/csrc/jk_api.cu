@@ -133,6 +133,7 @@ jk_status jk_create(jk_handle *out, void *workspace, size_t bytes) {
     h->arena.bytes = bytes;
     h->flags = reinterpret_cast<DeviceFlags *>(workspace);
     if (cudaGetDevice(&h->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess ||
         cudaMemset(h->flags, 0, sizeof(DeviceFlags)) != cudaSuccess) {
         cudaGetLastError();
         delete h;

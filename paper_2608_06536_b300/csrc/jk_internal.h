@@ -65,6 +65,7 @@ struct jk_ctx {
     jk::DeviceFlags *flags = nullptr;    // first bytes of the arena
     std::string last_error;
     int device = -1;
+    int num_sms = 148;
     jk::Profiler prof;
 };
 

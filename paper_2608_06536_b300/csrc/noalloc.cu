@@ -113,6 +113,7 @@ extern "C" jk_status jk_build_noalloc(const jk_factor *f, int32_t nd, const jk_d
     ctx.flags = reinterpret_cast<DeviceFlags *>(base);
     ctx.arena.reset(head);
     cudaGetDevice(&ctx.device);
+    cudaDeviceGetAttribute(&ctx.num_sms, cudaDevAttrMultiProcessorCount, ctx.device);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (cudaMemsetAsync(base, 0, sizeof(DeviceFlags), s) != cudaSuccess) {
         cudaGetLastError();

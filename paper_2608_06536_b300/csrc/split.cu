@@ -16,10 +16,13 @@
 //    window of 128 reduction elements, every partial sum is an integer below
 //    2^24 times that scale, so the FP32 accumulation is exact whatever the
 //    tensor core's rounding mode.  Diagonals d >= 4 (relative size <= 2^-32)
-//    share a fifth accumulator, whose truncation error stays below 2^-47.
-//  * Recombination.  After each 128-element window the five accumulators are
-//    read from TMEM, scaled by 2^48 and added into a per-element int64
-//    fixed-point accumulator (exact for d <= 3).  Split-K partials are summed
+//    share a fifth accumulator that spans a whole tile (<= 2048 elements);
+//    its truncation error stays below 2^-45.  The window boundaries of the
+//    four exact accumulators are staggered so their drains do not coincide.
+//  * Recombination.  After each window an accumulator is
+//    read from TMEM, converted to 32-bit integers in their own units and
+//    shifted into a per-element int64 fixed-point accumulator with 48
+//    fraction bits (exact for d <= 3).  Split-K partials are summed
 //    in 128-bit integers; the only rounding to FP64 happens once per output.
 //
 // The representation error is below 2^-48 of each row's scale, which keeps the
@@ -43,7 +46,7 @@ constexpr int KB = 16;          // reduction elements per pipeline stage (one MM
 constexpr int CHUNK = 128;      // exact accumulation window
 constexpr int KBPC = CHUNK / KB;
 constexpr int SUPER = 2048;     // reduction elements per int64 partial
-constexpr int NSTAGE = 5;
+constexpr int NSTAGE = 3;
 constexpr int NACC = 5;
 constexpr int NPAIRS = 21;
 constexpr int FRAC = 48;        // fraction bits of the int64 accumulator
@@ -52,13 +55,14 @@ constexpr int THREADS = 320;    // producer warp, MMA warp, 8 epilogue warps
 constexpr int A_BYTES = S * BM * 32;
 constexpr int B_BYTES = S * BN * 32;
 constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
-constexpr int SMEM_BYTES = NSTAGE * STAGE_BYTES + 1024 /*align slack*/ + 256 /*barriers*/;
+// Output staging: each epilogue warp owns 32 rows x 48 columns of 64-bit words,
+// kept as three 32x16 blocks in the 128-byte swizzled layout of a TMA store.
+constexpr int OUT_COLS = BN / 2;
+constexpr int OUT_BLK = 16;                        // 64-bit words per 128-byte row
+constexpr int OUT_WARP_BYTES = 32 * OUT_COLS * 8;  // 12 KB
+constexpr int OUT_BYTES = 8 * OUT_WARP_BYTES;
+constexpr int SMEM_BYTES = NSTAGE * STAGE_BYTES + OUT_BYTES + 1024 /*align slack*/ + 256 /*barriers*/;
 
-// Slice pairs ordered by diagonal; acc = min(d, 4); first = first pair of its accumulator.
-__constant__ int8_t kPairA[NPAIRS] = {0, 0, 1, 0, 1, 2, 0, 1, 2, 3, 0, 1, 2, 3, 4, 0, 1, 2, 3, 4, 5};
-__constant__ int8_t kPairB[NPAIRS] = {0, 1, 0, 2, 1, 0, 3, 2, 1, 0, 4, 3, 2, 1, 0, 5, 4, 3, 2, 1, 0};
-__constant__ int8_t kPairAcc[NPAIRS] = {0, 1, 1, 2, 2, 2, 3, 3, 3, 3, 4, 4, 4, 4, 4, 4, 4, 4, 4, 4, 4};
-__constant__ int8_t kPairFirst[NPAIRS] = {1, 1, 0, 1, 0, 0, 1, 0, 0, 0, 1, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
 
 // ---------------------------------------------------------------------------
 // Integer helpers
@@ -221,16 +225,57 @@ struct OzArgs {
     int b_rpe;
     double *C;            // nsuper == 1: FP64 result, row stride ldc
     long long ldc;
-    long long *P;         // nsuper > 1: int64 partial z at P + z*pz, packed [M][N]
+    long long *P;         // nsuper > 1: int64 partial z at P + z*pz, rows of ldp words
     long long pz;
+    long long ldp;
+    int use_tma_store;    // output written through tmC (row stride even, 16-byte aligned)
     int *err;             // device error word (JK_ERR_TIMEOUT on a stalled pipeline)
 };
 
+// Accumulator windows.  Diagonal d <= 3 restarts every KBPC K-blocks, with
+// the boundary of accumulator d offset by WOFF[d] blocks so that the drains of
+// the four exact accumulators are spread over the window instead of all
+// landing at once.  The last accumulator (d >= 4, inexact) spans the tile.
+__host__ __device__ constexpr int woff(int d) { return d < 4 ? 2 * d : 0; }
+
+__device__ __forceinline__ bool win_start(int d, int kb) {
+    if (kb == 0) return true;
+    if (d == NACC - 1) return false;
+    return kb >= woff(d) && ((kb - woff(d)) % KBPC) == 0;
+}
+
+__device__ __forceinline__ bool win_end(int d, int kb, int nkb) {
+    return kb == nkb - 1 || win_start(d, kb + 1);
+}
+
+// Tile t of the launch: n-tile fastest (tiles sharing an A row block run side
+// by side and hit L2), then m-tile, then the split-K super-chunk z.
+struct TileCoord {
+    int n, m, z, kbeg, nkb;
+};
+
+__device__ __forceinline__ TileCoord tile_of(int t, int ntn, int ntm, int K) {
+    TileCoord c;
+    c.n = t % ntn;
+    c.m = (t / ntn) % ntm;
+    c.z = t / (ntn * ntm);
+    c.kbeg = c.z * SUPER;
+    const int kend = min(K, c.kbeg + SUPER);
+    c.nkb = (kend - c.kbeg + KB - 1) / KB;
+    return c;
+}
+
+// Persistent, warp-specialized sliced GEMM.  Warp 0 streams operand stages
+// with TMA, warp 1 issues the 21 slice-pair MMAs per stage, warps 2..9 drain
+// the five TMEM accumulators after every 128-element window into int64
+// registers and write the finished tile while the next tile's MMAs run.
 __global__ void __launch_bounds__(THREADS, 1)
-ozgemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, OzArgs a) {
+ozgemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+              const __grid_constant__ CUtensorMap tmC, OzArgs a) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    uint64_t *full = reinterpret_cast<uint64_t *>(smem + NSTAGE * STAGE_BYTES);
+    uint8_t *outbuf = smem + NSTAGE * STAGE_BYTES;
+    uint64_t *full = reinterpret_cast<uint64_t *>(outbuf + OUT_BYTES);
     uint64_t *empty = full + NSTAGE;
     uint64_t *accfull = empty + NSTAGE;
     uint64_t *accempty = accfull + NACC;
@@ -238,11 +283,8 @@ ozgemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int n_tile = blockIdx.x, m_tile = blockIdx.y, z = blockIdx.z;
-    const int k_begin = z * SUPER;
-    const int k_end = min(a.K, k_begin + SUPER);
-    const int nkb = (k_end - k_begin + KB - 1) / KB;
-    const int nchunks = (nkb + KBPC - 1) / KBPC;
+    const int ntn = (a.N + BN - 1) / BN, ntm = (a.M + BM - 1) / BM;
+    const int ntiles = ntn * ntm * a.nsuper;
 
     if (threadIdx.x == 0) {
         for (int i = 0; i < NSTAGE; i++) { tc::mbar_init(&full[i], 1); tc::mbar_init(&empty[i], 1); }
@@ -266,103 +308,180 @@ ozgemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
             tc::prefetch_tmap(&tmB);
             int stage = 0;
             uint32_t phase = 0;
-            for (int kb = 0; kb < nkb; kb++) {
-                if (!tc::mbar_wait(&empty[stage], phase ^ 1u, abort_flag)) break;
-                tc::mbar_expect_tx(&full[stage], STAGE_BYTES);
-                const int kc = k_begin + kb * KB;
-                uint8_t *sa = smem + stage * STAGE_BYTES;
-                tc::tma_load_3d(sa, &tmA, &full[stage], kc, m_tile * BM, 0);
-                tc::tma_load_3d(sa + A_BYTES, &tmB, &full[stage], kc, n_tile * BN, 0);
-                if (++stage == NSTAGE) { stage = 0; phase ^= 1u; }
+            bool ok = true;
+            for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+                const TileCoord tc_ = tile_of(t, ntn, ntm, a.K);
+                for (int kb = 0; kb < tc_.nkb; kb++) {
+                    if (!tc::mbar_wait(&empty[stage], phase ^ 1u, abort_flag)) { ok = false; break; }
+                    tc::mbar_expect_tx(&full[stage], STAGE_BYTES);
+                    const int kc = tc_.kbeg + kb * KB;
+                    uint8_t *sa = smem + stage * STAGE_BYTES;
+                    tc::tma_load_3d(sa, &tmA, &full[stage], kc, tc_.m * BM, 0);
+                    tc::tma_load_3d(sa + A_BYTES, &tmB, &full[stage], kc, tc_.n * BN, 0);
+                    if (++stage == NSTAGE) { stage = 0; phase ^= 1u; }
+                }
             }
         }
     } else if (warp == 1) {
         // ---------------- MMA issuer ----------------
         if (lane == 0) {
             constexpr uint32_t idesc = tc::idesc_bf16_f32(BM, BN);
+            // Pair tables as compile-time constants (the loop below is fully unrolled).
+            constexpr int PA[NPAIRS] = {0, 0, 1, 0, 1, 2, 0, 1, 2, 3, 0, 1, 2, 3, 4, 0, 1, 2, 3, 4, 5};
+            constexpr int PB[NPAIRS] = {0, 1, 0, 2, 1, 0, 3, 2, 1, 0, 4, 3, 2, 1, 0, 5, 4, 3, 2, 1, 0};
+            constexpr int PACC[NPAIRS] = {0, 1, 1, 2, 2, 2, 3, 3, 3, 3, 4, 4, 4, 4, 4, 4, 4, 4, 4, 4, 4};
+            constexpr int PFIRST[NPAIRS] = {1, 1, 0, 1, 0, 0, 1, 0, 0, 0, 1, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
             int stage = 0;
             uint32_t phase = 0;
-            for (int kb = 0; kb < nkb; kb++) {
-                const int ch = kb / KBPC;
-                const bool cstart = (kb % KBPC) == 0;
-                const bool cend = (kb % KBPC) == KBPC - 1 || kb == nkb - 1;
-                if (!tc::mbar_wait(&full[stage], phase, abort_flag)) break;
-                tc::fence_after_sync();
-                const uint32_t abase = tc::smem_u32(smem + stage * STAGE_BYTES);
-                const uint32_t bbase = abase + A_BYTES;
-                bool ok = true;
-#pragma unroll 1
-                for (int p = 0; p < NPAIRS; p++) {
-                    const int acc = kPairAcc[p];
-                    uint32_t accumulate = 1;
-                    if (cstart && kPairFirst[p]) {
-                        if (ch > 0) {
-                            if (!tc::mbar_wait(&accempty[acc], static_cast<uint32_t>(ch - 1) & 1u, abort_flag)) {
-                                ok = false;
-                                break;
+            int mcnt[NACC] = {0, 0, 0, 0, 0};   // windows completed per accumulator
+            bool ok = true;
+            for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+                const TileCoord tc_ = tile_of(t, ntn, ntm, a.K);
+                for (int kb = 0; kb < tc_.nkb; kb++) {
+                    if (!tc::mbar_wait(&full[stage], phase, abort_flag)) { ok = false; break; }
+                    tc::fence_after_sync();
+                    const uint64_t ad0 = tc::sdesc_kmajor_sw32(tc::smem_u32(smem + stage * STAGE_BYTES));
+                    const uint64_t bd0 = tc::sdesc_kmajor_sw32(tc::smem_u32(smem + stage * STAGE_BYTES + A_BYTES));
+#pragma unroll
+                    for (int p = 0; p < NPAIRS; p++) {
+                        uint32_t accumulate = 1;
+                        if (PFIRST[p] && win_start(PACC[p], kb)) {
+                            if (mcnt[PACC[p]] > 0) {
+                                if (!tc::mbar_wait(&accempty[PACC[p]], static_cast<uint32_t>(mcnt[PACC[p]] - 1) & 1u,
+                                                   abort_flag)) {
+                                    ok = false;
+                                    break;
+                                }
+                                tc::fence_after_sync();
                             }
-                            tc::fence_after_sync();
+                            accumulate = 0;
                         }
-                        accumulate = 0;
+                        // descriptor start address is in 16-byte units
+                        tc::mma_bf16(tmem + PACC[p] * BN, ad0 + static_cast<uint64_t>(PA[p] * (BM * 32 / 16)),
+                                     bd0 + static_cast<uint64_t>(PB[p] * (BN * 32 / 16)), idesc, accumulate);
                     }
-                    const uint64_t ad = tc::sdesc_kmajor_sw32(abase + kPairA[p] * (BM * 32));
-                    const uint64_t bd = tc::sdesc_kmajor_sw32(bbase + kPairB[p] * (BN * 32));
-                    tc::mma_bf16(tmem + acc * BN, ad, bd, idesc, accumulate);
+                    if (!ok) break;
+                    tc::mma_commit(&empty[stage]);
+#pragma unroll
+                    for (int d = 0; d < NACC; d++) {
+                        if (win_end(d, kb, tc_.nkb)) {
+                            tc::mma_commit(&accfull[d]);
+                            mcnt[d]++;
+                        }
+                    }
+                    if (++stage == NSTAGE) { stage = 0; phase ^= 1u; }
                 }
-                if (!ok) break;
-                tc::mma_commit(&empty[stage]);
-                if (cend)
-                    for (int acc = 0; acc < NACC; acc++) tc::mma_commit(&accfull[acc]);
-                if (++stage == NSTAGE) { stage = 0; phase ^= 1u; }
             }
         }
     } else {
         // ---------------- epilogue: 8 warps, two per TMEM lane quarter ----------------
         const int ew = warp - 2;
         const int q = warp & 3;          // lane quarter this warp may access
-        const int half = ew >> 2;        // which 64 columns
-        const int row = m_tile * BM + q * 32 + lane;
-        long long acc64[BN / 2];
-#pragma unroll
-        for (int i = 0; i < BN / 2; i++) acc64[i] = 0;
+        const int half = ew >> 2;        // which half of the tile's columns
+        int ecnt[NACC] = {0, 0, 0, 0, 0};
         bool ok = true;
-        for (int ch = 0; ch < nchunks && ok; ch++) {
-#pragma unroll 1
-            for (int acc = 0; acc < NACC; acc++) {
-                if (!tc::mbar_wait(&accfull[acc], static_cast<uint32_t>(ch) & 1u, abort_flag)) { ok = false; break; }
-                __syncwarp();
-                tc::fence_after_sync();
-                const uint32_t tbase = tmem + (static_cast<uint32_t>(q * 32) << 16) + acc * BN + half * (BN / 2);
-                float v[BN / 2];
+        for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+            const TileCoord tc_ = tile_of(t, ntn, ntm, a.K);
+            long long acc64[BN / 2];
 #pragma unroll
-                for (int c = 0; c < BN / 2; c += 16) tc::tmem_ld16(tbase + c, v + c);
-                tc::tmem_wait_ld();
-                tc::fence_before_sync();
-                __syncwarp();
-                if (lane == 0) tc::mbar_arrive(&accempty[acc]);
+            for (int i = 0; i < BN / 2; i++) acc64[i] = 0;
+            for (int kb = 0; kb < tc_.nkb && ok; kb++) {
 #pragma unroll
-                for (int i = 0; i < BN / 2; i++) acc64[i] += __float2ll_rn(v[i] * 0x1p48f);
+                for (int d = 0; d < NACC; d++) {
+                    if (!win_end(d, kb, tc_.nkb)) continue;
+                    if (!tc::mbar_wait(&accfull[d], static_cast<uint32_t>(ecnt[d]) & 1u, abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    ecnt[d]++;
+                    __syncwarp();
+                    tc::fence_after_sync();
+                    const uint32_t tbase = tmem + (static_cast<uint32_t>(q * 32) << 16) + d * BN + half * (BN / 2);
+                    float v[BN / 2];
+#pragma unroll
+                    for (int c = 0; c < BN / 2; c += 16) tc::tmem_ld16(tbase + c, v + c);
+                    tc::tmem_wait_ld();
+                    tc::fence_before_sync();
+                    __syncwarp();
+                    if (lane == 0) tc::mbar_arrive(&accempty[d]);
+                    // Accumulator d <= 3 holds integers in units of 2^-(8d+16) below 2^24;
+                    // the last one (spanning the tile) stays below 2^-20.  Scale to the
+                    // unit, convert with the FP32 add of 1.5*2^23 (exact below 2^22;
+                    // the rare larger value falls back to F2I), then shift into the
+                    // 2^-48 fixed point of acc64.  No 64-bit float conversions: those
+                    // run on the scarce FP64 pipe.
+                    const float unit = d < 4 ? __int_as_float((127 + 16 + 8 * d) << 23) : 0x1p48f;
+                    const int sh = d < 4 ? 32 - 8 * d : 0;
+#pragma unroll
+                    for (int i = 0; i < BN / 2; i++) {
+                        const float y = v[i] * unit;
+                        int xi = __float_as_int(y + 12582912.0f) - 0x4B400000;
+                        if (fabsf(y) > 4194304.0f) xi = __float2int_rn(y);
+                        acc64[i] += static_cast<long long>(xi) << sh;
+                    }
+                }
+            }
+            const int row = tc_.m * BM + q * 32 + lane;
+            if (!ok) break;
+            const int c0 = tc_.n * BN + half * OUT_COLS;
+            if (a.use_tma_store) {
+                // This warp's 32 x 48 block: lane = row, three swizzled 32 x 16 sub-blocks.
+                uint8_t *wbuf = outbuf + ew * OUT_WARP_BYTES;
+                if (lane == 0) tc::bulk_wait_read();   // previous tile's store has read the buffer
+                __syncwarp();
+                const int ea = a.nsuper == 1 && row < a.M ? a.eA[row / a.a_rpe] - FRAC : 0;
+#pragma unroll
+                for (int b = 0; b < OUT_COLS / OUT_BLK; b++) {
+                    uint8_t *blk = wbuf + b * (32 * OUT_BLK * 8);
+#pragma unroll
+                    for (int j = 0; j < OUT_BLK / 2; j++) {   // 16-byte chunks of this row
+                        const int i0 = b * OUT_BLK + 2 * j;
+                        long long w0 = acc64[i0], w1 = acc64[i0 + 1];
+                        if (a.nsuper == 1) {
+                            const int col = c0 + i0;
+                            const double d0 = col < a.N && row < a.M ? i64_to_f64_scaled(w0, ea + a.eB[col / a.b_rpe]) : 0.0;
+                            const double d1 = col + 1 < a.N && row < a.M ? i64_to_f64_scaled(w1, ea + a.eB[(col + 1) / a.b_rpe]) : 0.0;
+                            w0 = __double_as_longlong(d0);
+                            w1 = __double_as_longlong(d1);
+                        }
+                        const int chunk = j ^ (lane & 7);   // 128-byte swizzle
+                        longlong2 *dst = reinterpret_cast<longlong2 *>(blk + lane * 128 + chunk * 16);
+                        *dst = make_longlong2(w0, w1);
+                    }
+                }
+                tc::fence_proxy_async_smem();
+                __syncwarp();
+                if (lane == 0) {
+                    const int r0 = tc_.m * BM + q * 32;
+#pragma unroll
+                    for (int b = 0; b < OUT_COLS / OUT_BLK; b++) {
+                        const int cc = c0 + b * OUT_BLK;
+                        // rows of the partial for super-chunk z follow the M rows of z-1
+                        const int rr = a.nsuper == 1 ? r0 : r0 + tc_.z * static_cast<int>(a.pz / a.ldp);
+                        if (cc < a.N) tc::tma_store_2d(&tmC, wbuf + b * (32 * OUT_BLK * 8), cc, rr);
+                    }
+                    tc::bulk_commit();
+                }
+            } else if (row < a.M) {
+                if (a.nsuper == 1) {
+                    const int ea = a.eA[row / a.a_rpe] - FRAC;
+                    double *crow = a.C + static_cast<long long>(row) * a.ldc;
+#pragma unroll
+                    for (int i = 0; i < BN / 2; i++) {
+                        const int col = c0 + i;
+                        if (col < a.N) crow[col] = i64_to_f64_scaled(acc64[i], ea + a.eB[col / a.b_rpe]);
+                    }
+                } else {
+                    long long *prow = a.P + tc_.z * a.pz + static_cast<long long>(row) * a.ldp;
+#pragma unroll
+                    for (int i = 0; i < BN / 2; i++) {
+                        const int col = c0 + i;
+                        if (col < a.N) prow[col] = acc64[i];
+                    }
+                }
             }
         }
-        if (ok && row < a.M) {
-            const int c0 = n_tile * BN + half * (BN / 2);
-            if (a.nsuper == 1) {
-                const int ea = a.eA[row / a.a_rpe] - FRAC;
-                double *crow = a.C + static_cast<long long>(row) * a.ldc;
-#pragma unroll
-                for (int i = 0; i < BN / 2; i++) {
-                    const int col = c0 + i;
-                    if (col < a.N) crow[col] = i64_to_f64_scaled(acc64[i], ea + a.eB[col / a.b_rpe]);
-                }
-            } else {
-                long long *prow = a.P + z * a.pz + static_cast<long long>(row) * a.N;
-#pragma unroll
-                for (int i = 0; i < BN / 2; i++) {
-                    const int col = c0 + i;
-                    if (col < a.N) prow[col] = acc64[i];
-                }
-            }
-        }
+        if (a.use_tma_store && lane == 0) tc::bulk_wait_all();
     }
     tc::fence_before_sync();
     __syncthreads();
@@ -375,13 +494,14 @@ ozgemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
 
 // out[r][c] (+)= 2^(eA[r/arpe] + eB[c/brpe] - 48) * sum_z P[z][r][c]   (sum in 128-bit integers)
 __global__ void __launch_bounds__(256)
-reduce_partials_kernel(const long long *P, long long pz, int nz, int M, int N, const int *eA, int arpe,
-                       const int *eB, int brpe, double *out, long long ldo, int accumulate) {
+reduce_partials_kernel(const long long *P, long long pz, long long ldp, int nz, int M, int N, const int *eA,
+                       int arpe, const int *eB, int brpe, double *out, long long ldo, int accumulate) {
     const long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
     if (e >= static_cast<long long>(M) * N) return;
     const int r = static_cast<int>(e / N), c = static_cast<int>(e % N);
+    const long long off = static_cast<long long>(r) * ldp + c;
     __int128 s = 0;
-    for (int zz = 0; zz < nz; zz++) s += static_cast<__int128>(P[zz * pz + e]);
+    for (int zz = 0; zz < nz; zz++) s += static_cast<__int128>(P[zz * pz + off]);
     const double v = i128_to_f64_scaled(s, eA[r / arpe] + eB[c / brpe] - FRAC);
     double *o = out + static_cast<long long>(r) * ldo + c;
     *o = accumulate ? (*o + v) : v;
@@ -428,7 +548,28 @@ jk_status make_slice_map(jk_ctx *h, CUtensorMap *map, const __nv_bfloat16 *base,
     return JK_OK;
 }
 
+// Tensor map over a row-major matrix of 64-bit words (rows x cols, row stride
+// ld words, ld even), box = 16 words x 32 rows, 128-byte swizzle: the layout
+// the GEMM epilogue stages its output in.
+jk_status make_out_map(jk_ctx *h, CUtensorMap *map, void *base, long long rows, int cols, long long ld) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return set_error(h, JK_ERR_CUDA, "cuTensorMapEncodeTiled is unavailable");
+    cuuint64_t dims[2] = {static_cast<cuuint64_t>(cols), static_cast<cuuint64_t>(rows)};
+    cuuint64_t strides[1] = {static_cast<cuuint64_t>(ld) * 8};
+    cuuint32_t box[2] = {16, 32};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_INT64, 2, base, dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return set_error(h, JK_ERR_CUDA, "cuTensorMapEncodeTiled (output) failed (%d)", (int)r);
+    return JK_OK;
+}
+
 inline int kpad_of(int K) { return (K + 15) / 16 * 16; }
+inline long long even_ld(long long n) { return n + (n & 1); }
+// Rows reserved per split-K partial: M rounded up to whole row tiles, so a
+// tile's padding rows never land in the next partial.
+inline long long part_rows(long long M) { return (M + oz::BM - 1) / oz::BM * oz::BM; }
 
 }  // namespace
 
@@ -494,14 +635,28 @@ static jk_status ozgemm(jk_ctx *h, const Sliced &A, const Sliced &B, double *C, 
     oz::OzArgs a;
     a.M = A.rows; a.N = B.rows; a.K = A.K; a.nsuper = nsuper_of(A.K);
     a.eA = A.e; a.a_rpe = A.rpe; a.eB = B.e; a.b_rpe = B.rpe;
-    a.C = C; a.ldc = ldc; a.P = P; a.pz = static_cast<long long>(A.rows) * B.rows;
+    a.C = C; a.ldc = ldc; a.P = P;
+    a.ldp = even_ld(B.rows);
+    a.pz = part_rows(A.rows) * a.ldp;
     a.err = &h->flags->error;
     if (a.nsuper > 1 && !P) return set_error(h, JK_ERR_ARG, "internal: partial buffer missing");
-    dim3 grid((a.N + oz::BN - 1) / oz::BN, (a.M + oz::BM - 1) / oz::BM, a.nsuper);
-    if (grid.y > 65535) return set_error(h, JK_ERR_SHAPE, "too many row tiles (%u)", grid.y);
+    CUtensorMap tcm;
+    std::memset(&tcm, 0, sizeof tcm);
+    a.use_tma_store = 0;
+    if (a.nsuper > 1) {
+        JK_TRY(make_out_map(h, &tcm, P, static_cast<long long>(a.nsuper) * part_rows(a.M), a.N, a.ldp));
+        a.use_tma_store = 1;
+    } else if ((ldc % 2) == 0 && (reinterpret_cast<uintptr_t>(C) & 15u) == 0) {
+        JK_TRY(make_out_map(h, &tcm, C, a.M, a.N, ldc));
+        a.use_tma_store = 1;
+    }
+    const long long ntn = (a.N + oz::BN - 1) / oz::BN, ntm = (a.M + oz::BM - 1) / oz::BM;
+    const long long ntiles = ntn * ntm * a.nsuper;
+    if (ntiles > 0x7fffffffLL) return set_error(h, JK_ERR_SHAPE, "too many tiles (%lld)", ntiles);
+    const int grid = static_cast<int>(ntiles < h->num_sms ? ntiles : h->num_sms);
     {
         LaunchScope ls(h, KK_OZGEMM, st);
-        oz::ozgemm_kernel<<<grid, oz::THREADS, oz::SMEM_BYTES, st>>>(ta, tb, a);
+        oz::ozgemm_kernel<<<grid, oz::THREADS, oz::SMEM_BYTES, st>>>(ta, tb, tcm, a);
     }
     // Issued MMA work: every CTA runs all 21 slice pairs over its K-blocks.
     double kblocks = 0.0;
@@ -510,7 +665,7 @@ static jk_status ozgemm(jk_ctx *h, const Sliced &A, const Sliced &B, double *C, 
         kblocks += (kb + oz::KB - 1) / oz::KB;
     }
     h->prof.tensor_flops += 2.0 * oz::BM * oz::BN * oz::KB * oz::NPAIRS * kblocks *
-                            static_cast<double>(grid.x) * grid.y;
+                            static_cast<double>(ntn) * ntm;
     JK_LAUNCH_CHECK(h);
     return JK_OK;
 }
@@ -518,10 +673,12 @@ static jk_status ozgemm(jk_ctx *h, const Sliced &A, const Sliced &B, double *C, 
 static jk_status reduce_partials(jk_ctx *h, const long long *P, int nz, const Sliced &A, const Sliced &B,
                                  double *out, long long ldo, bool accumulate, cudaStream_t st) {
     const long long tot = static_cast<long long>(A.rows) * B.rows;
+    const long long ldp = even_ld(B.rows);
     {
         LaunchScope ls(h, KK_OZREDUCE, st);
         oz::reduce_partials_kernel<<<static_cast<unsigned>((tot + 255) / 256), 256, 0, st>>>(
-            P, tot, nz, A.rows, B.rows, A.e, A.rpe, B.e, B.rpe, out, ldo, accumulate ? 1 : 0);
+            P, part_rows(A.rows) * ldp, ldp, nz, A.rows, B.rows, A.e, A.rpe, B.e, B.rpe, out, ldo,
+            accumulate ? 1 : 0);
     }
     JK_LAUNCH_CHECK(h);
     return JK_OK;
@@ -550,7 +707,7 @@ static size_t partial_count(const Problem &pb, int pc) {
     size_t cnt = 0;
     for (int s = 0; s < pb.nd; s++) {
         int ns = nsuper_of(pc * pb.k[s]);
-        if (ns > 1) cnt += static_cast<size_t>(ns) * pb.n * pb.n;
+        if (ns > 1) cnt += static_cast<size_t>(ns) * part_rows(pb.n) * even_ld(pb.n);
     }
     return cnt;
 }
@@ -562,7 +719,7 @@ size_t split_build_workspace(const Problem &pb) {
     b += align_up(n * pb.ctot * 8);                                  // Z
     b += sliced_bytes(pc * pb.n, pb.n, pb.n);                        // L chunk slices
     b += sliced_bytes(pb.ctot, pb.n, 1);                             // Z^T slices
-    b += align_up(static_cast<size_t>(pc) * n * pb.ctot * 8);        // T chunk (FP64)
+    b += align_up(static_cast<size_t>(pc) * n * even_ld(pb.ctot) * 8);   // T chunk (FP64)
     b += align_up(static_cast<size_t>(pb.nd) * pb.naux * 8);         // gamma
     for (int s = 0; s < pb.nd; s++) {                                // T_X, T_Y slices
         b += sliced_bytes(pb.n, pc * pb.k[s], 1);
@@ -570,15 +727,16 @@ size_t split_build_workspace(const Problem &pb) {
     }
     b += align_up(partial_count(pb, pc) * 8);
     b += align_up(static_cast<size_t>(pb.nd) * n * n * 8);           // K accumulators (if K not wanted)
-    if (pb.n > oz::SUPER) b += align_up(static_cast<size_t>(nsuper_of(pb.n)) * pc * n * pb.ctot * 8);
+    if (pb.n > oz::SUPER)
+        b += align_up(static_cast<size_t>(nsuper_of(pb.n)) * part_rows(static_cast<long long>(pc) * n) * even_ld(pb.ctot) * 8);
     return b;
 }
 
 size_t split_adjoint_workspace(const Problem &, bool) { return 0; }
 
 jk_status split_pack_z(jk_ctx *h, const Problem &pb, double *Z, cudaStream_t st);
-jk_status fp64_gamma_panel(jk_ctx *h, const Problem &pb, const double *T, int np, double *gamma, int P0,
-                           cudaStream_t st);
+jk_status fp64_gamma_panel(jk_ctx *h, const Problem &pb, const double *T, long long ldT, int np, double *gamma,
+                           int P0, cudaStream_t st);
 jk_status fp64_jstream(jk_ctx *h, const Problem &pb, const double *gamma, cudaStream_t st);
 
 jk_status split_build(jk_ctx *h, const Problem &pb, cudaStream_t st) {
@@ -589,7 +747,8 @@ jk_status split_build(jk_ctx *h, const Problem &pb, cudaStream_t st) {
     double *Z = ar.take<double>(static_cast<size_t>(n) * pb.ctot);
     Sliced Ls, Zs;
     bool ok = Z && take_sliced(ar, pc * n, n, n, Ls) && take_sliced(ar, pb.ctot, n, 1, Zs);
-    double *T = ar.take<double>(static_cast<size_t>(pc) * n * pb.ctot);
+    const long long ldT = even_ld(pb.ctot);
+    double *T = ar.take<double>(static_cast<size_t>(pc) * n * ldT);
     double *gamma = ar.take<double>(static_cast<size_t>(nd) * naux);
     Sliced TX[kMaxDens], TY[kMaxDens];
     for (int s = 0; ok && s < nd; s++) {
@@ -599,7 +758,8 @@ jk_status split_build(jk_ctx *h, const Problem &pb, cudaStream_t st) {
     long long *Pbuf = ar.take<long long>(partial_count(pb, pc) > 0 ? partial_count(pb, pc) : 1);
     double *Kacc = ar.take<double>(static_cast<size_t>(nd) * n2);
     long long *Ppanel = nullptr;
-    if (n > oz::SUPER) Ppanel = ar.take<long long>(static_cast<size_t>(nsuper_of(n)) * pc * n * pb.ctot);
+    if (n > oz::SUPER)
+        Ppanel = ar.take<long long>(static_cast<size_t>(nsuper_of(n)) * part_rows(static_cast<long long>(pc) * n) * ldT);
     if (!ok || !T || !gamma || !Pbuf || !Kacc || (n > oz::SUPER && !Ppanel))
         return set_error(h, JK_ERR_OOM, "workspace too small for the split build");
 
@@ -617,23 +777,23 @@ jk_status split_build(jk_ctx *h, const Problem &pb, cudaStream_t st) {
         // T[(p, mu)][c] = sum_lam L^p[mu][lam] Z[lam][c]
         if (n > oz::SUPER) {
             JK_TRY(ozgemm(h, Lc, Zs, nullptr, 0, Ppanel, st));
-            JK_TRY(reduce_partials(h, Ppanel, nsuper_of(n), Lc, Zs, T, pb.ctot, false, st));
+            JK_TRY(reduce_partials(h, Ppanel, nsuper_of(n), Lc, Zs, T, ldT, false, st));
         } else {
-            JK_TRY(ozgemm(h, Lc, Zs, T, pb.ctot, nullptr, st));
+            JK_TRY(ozgemm(h, Lc, Zs, T, ldT, nullptr, st));
         }
-        if (pb.wantJ) JK_TRY(fp64_gamma_panel(h, pb, T, np, gamma, P0, st));
+        if (pb.wantJ) JK_TRY(fp64_gamma_panel(h, pb, T, ldT, np, gamma, P0, st));
         if (!pb.wantK) continue;
         // Rank update per density over this chunk's (p, i) pairs.
         long long *Pcur = Pbuf;
         for (int s = 0; s < nd; s++) {
             const int k = pb.k[s];
             const int Kr = np * k;
-            oz::Src xs{T + pb.offX[s], pb.ctot, static_cast<long long>(n) * pb.ctot, 1, k};
+            oz::Src xs{T + pb.offX[s], ldT, static_cast<long long>(n) * ldT, 1, k};
             TX[s].rows = n;
             JK_TRY(slice_operand(h, xs, n, Kr, 1, TX[s], st));
             Sliced *B = &TX[s];
             if (!pb.sym[s]) {
-                oz::Src ys{T + pb.offY[s], pb.ctot, static_cast<long long>(n) * pb.ctot, 1, k};
+                oz::Src ys{T + pb.offY[s], ldT, static_cast<long long>(n) * ldT, 1, k};
                 JK_TRY(slice_operand(h, ys, n, Kr, 1, TY[s], st));
                 B = &TY[s];
             }
@@ -651,7 +811,7 @@ jk_status split_build(jk_ctx *h, const Problem &pb, cudaStream_t st) {
             } else {
                 JK_TRY(ozgemm(h, TX[s], *B, nullptr, 0, Pcur, st));
                 JK_TRY(reduce_partials(h, Pcur, ns, TX[s], *B, Kout, n, P0 > 0, st));
-                Pcur += static_cast<size_t>(ns) * n2;
+                Pcur += static_cast<size_t>(ns) * part_rows(n) * even_ld(n);
             }
         }
     }
@@ -683,7 +843,7 @@ extern "C" jk_status jk_debug_sliced_gemm(jk_handle h, int32_t M, int32_t N, int
     const int ns = nsuper_of(K);
     long long *P = nullptr;
     if (ns > 1) {
-        P = h->arena.take<long long>(static_cast<size_t>(ns) * M * N);
+        P = h->arena.take<long long>(static_cast<size_t>(ns) * part_rows(M) * even_ld(N));
         if (!P) return set_error(h, JK_ERR_OOM, "workspace too small");
     }
     oz::Src sa{A, K, 0, 1, K}, sb{B, K, 0, 1, K};
@@ -698,6 +858,6 @@ extern "C" size_t jk_debug_sliced_gemm_workspace(int32_t M, int32_t N, int32_t K
     using namespace jk;
     size_t b = align_up(sizeof(DeviceFlags)) + sliced_bytes(M, K, 1) + sliced_bytes(N, K, 1);
     const int ns = nsuper_of(K);
-    if (ns > 1) b += align_up(static_cast<size_t>(ns) * M * N * 8);
+    if (ns > 1) b += align_up(static_cast<size_t>(ns) * part_rows(M) * even_ld(N) * 8);
     return b + kArenaAlign;
 }
