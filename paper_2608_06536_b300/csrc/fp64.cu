@@ -234,12 +234,47 @@ jstream_kernel(const double *L, long long n2, int naux, const double *g,
     }
 }
 
+// Symmetric form: L^P = L^P^T, so J = sum_P g_P L^P is symmetric and only the
+// n(n+1)/2 upper-triangle entries are formed (one per thread, consecutive
+// threads on consecutive columns of a row), then mirrored: half the FP64 work.
+template <int NS>
+__global__ void __launch_bounds__(64)
+jstream_sym_kernel(const double *L, int n, int naux, const double *g, int ldg, OutTab Out) {
+    const long long ntri = (long long)n * (n + 1) / 2;
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= ntri) return;
+    // row mu of the upper triangle starts at mu*n - mu*(mu-1)/2
+    const double nn = 2.0 * n + 1.0;
+    int mu = (int)((nn - sqrt(nn * nn - 8.0 * (double)t)) * 0.5);
+    if (mu < 0) mu = 0;
+    if (mu > n - 1) mu = n - 1;
+    while (mu > 0 && (long long)mu * n - (long long)mu * (mu - 1) / 2 > t) mu--;
+    while (mu < n - 1 && (long long)(mu + 1) * n - (long long)(mu + 1) * mu / 2 <= t) mu++;
+    const int nu = mu + (int)(t - ((long long)mu * n - (long long)mu * (mu - 1) / 2));
+    const long long n2 = (long long)n * n;
+    const long long e = (long long)mu * n + nu;
+    double a[NS];
+#pragma unroll
+    for (int j = 0; j < NS; j++) a[j] = 0.0;
+    const double *Lp = L + e;
+    for (int P = 0; P < naux; P++) {
+        const double l = __ldg(Lp + (long long)P * n2);
+#pragma unroll
+        for (int j = 0; j < NS; j++) a[j] = fma(__ldg(g + (long long)j * ldg + P), l, a[j]);
+    }
+#pragma unroll
+    for (int j = 0; j < NS; j++) {
+        Out.p[j][e] = a[j];
+        if (nu != mu) Out.p[j][(long long)nu * n + mu] = a[j];
+    }
+}
+
 // Out[s] = sum_P g[s][P] L^P for s < nd (Out[s] are [n][n] device arrays).
 static jk_status jstream(jk_ctx *h, const double *L, int n, int naux,
                          const double *g, int ldg, int nd, double *const *Out,
                          cudaStream_t st) {
-    long long n2 = (long long)n * n;
-    int blocks = (int)((n2 / 2 + 1 + 255) / 256);
+    const long long ntri = (long long)n * (n + 1) / 2;
+    const int blocks = (int)((ntri + 63) / 64);
     for (int s0 = 0; s0 < nd; s0 += 8) {
         int ns = nd - s0 < 8 ? nd - s0 : 8;
         const double *gs = g + (long long)s0 * ldg;
@@ -247,7 +282,7 @@ static jk_status jstream(jk_ctx *h, const double *L, int n, int naux,
         for (int j = 0; j < 8; j++) o.p[j] = j < ns ? Out[s0 + j] : nullptr;
         LaunchScope ls(h, KK_JSTREAM, st);
         switch (ns) {
-#define JS(N) case N: jstream_kernel<N><<<blocks, 256, 0, st>>>(L, n2, naux, gs, ldg, o); break;
+#define JS(N) case N: jstream_sym_kernel<N><<<blocks, 64, 0, st>>>(L, n, naux, gs, ldg, o); break;
             JS(1) JS(2) JS(3) JS(4) JS(5) JS(6) JS(7) JS(8)
 #undef JS
         }

@@ -171,15 +171,97 @@ __global__ void __launch_bounds__(256) expo_kernel(Src src, int rows, int K, int
     }
 }
 
-// BF16 bit pattern of q * 2^(-8j) for an integer |q| <= 256 (exact).
-__device__ __forceinline__ unsigned short q_to_bf16(long long q, int j) {
-    if (q == 0) return 0;
-    const unsigned sign = q < 0 ? 0x8000u : 0u;
-    const unsigned a = static_cast<unsigned>(q < 0 ? -q : q);
-    const int lz = __clz(a);                       // a = 1.f * 2^(31 - lz)
-    const int expo = 31 - lz - 8 * j + 127;
-    const unsigned frac = static_cast<unsigned>(((static_cast<unsigned long long>(a) << (lz + 1)) >> 25) & 0x7Fu);
-    return static_cast<unsigned short>(sign | (static_cast<unsigned>(expo) << 7) | frac);
+// Six balanced base-256 digits of F (|F| <= 2^48): F = sum_j q_j 2^(8(6-j)),
+// q_2..q_6 in [-128, 127], |q_1| <= 256.  32-bit integer arithmetic only.
+__device__ __forceinline__ void digits6(long long F, int q[S]) {
+    int lo = static_cast<int>(F & 0xFFFFFFll);        // [0, 2^24)
+    int hi = static_cast<int>(F >> 24);               // arithmetic shift
+    q[5] = ((lo + 128) & 255) - 128; lo = (lo - q[5]) >> 8;
+    q[4] = ((lo + 128) & 255) - 128; lo = (lo - q[4]) >> 8;
+    q[3] = ((lo + 128) & 255) - 128; lo = (lo - q[3]) >> 8;
+    hi += lo;
+    q[2] = ((hi + 128) & 255) - 128; hi = (hi - q[2]) >> 8;
+    q[1] = ((hi + 128) & 255) - 128; hi = (hi - q[1]) >> 8;
+    q[0] = hi;
+}
+
+// BF16 bits of q * 2^(-8(j+1)) for |q| <= 256: exact through FP32 (the integer
+// is formed with the 1.5*2^23 add, scaled by a power of two, and has at most
+// 8 significant bits, so the low half of the FP32 word is zero).
+__device__ __forceinline__ uint32_t qbf16(int q, float scale) {
+    const float f = (__int_as_float(0x4B400000 + q) - 12582912.0f) * scale;
+    return __float_as_uint(f) >> 16;
+}
+
+// Vector slicer: 4 consecutive reduction elements per thread.  Requires
+// src.ski == 1, src.kin % 4 == 0, K % 4 == 0 and 16-byte aligned pairs
+// (checked on the host).
+__global__ void __launch_bounds__(256) slice4_kernel(Src src, int rows, int K, int Kpad, const int *e, int rpe,
+                                                     uint2 *out, long long sstride4) {
+    const int kk = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
+    if (kk >= Kpad) return;
+    long long koff = 0;
+    if (kk < K) {
+        const int ko = kk / src.kin, ki = kk - ko * src.kin;
+        koff = static_cast<long long>(ko) * src.sko + ki;
+    }
+    for (int rb = blockIdx.y * 8; rb < rows; rb += gridDim.y * 8) {
+        const int rend = min(rows, rb + 8);
+        for (int r = rb; r < rend; r++) {
+            int q[4][S];
+            if (kk < K) {
+                const double2 *p2 = reinterpret_cast<const double2 *>(src.p + static_cast<long long>(r) * src.sr + koff);
+                const double2 a = p2[0], b = p2[1];
+                const int er = e[r / rpe];
+                digits6(to_fixed48(a.x, er), q[0]);
+                digits6(to_fixed48(a.y, er), q[1]);
+                digits6(to_fixed48(b.x, er), q[2]);
+                digits6(to_fixed48(b.y, er), q[3]);
+            } else {
+#pragma unroll
+                for (int i = 0; i < 4; i++)
+#pragma unroll
+                    for (int j = 0; j < S; j++) q[i][j] = 0;
+            }
+            const long long o = (static_cast<long long>(r) * Kpad + kk) >> 2;
+            float sc = 0.00390625f;
+#pragma unroll
+            for (int j = 0; j < S; j++) {
+                uint2 w;
+                w.x = qbf16(q[0][j], sc) | (qbf16(q[1][j], sc) << 16);
+                w.y = qbf16(q[2][j], sc) | (qbf16(q[3][j], sc) << 16);
+                out[j * sstride4 + o] = w;
+                sc *= 0.00390625f;
+            }
+        }
+    }
+}
+
+// e[g] for groups that are contiguous runs of `len` doubles starting at p + g*len
+// (len even, p 16-byte aligned): 16-byte loads.
+__global__ void __launch_bounds__(256) expo_flat_kernel(const double *p, long long len, int *e) {
+    __shared__ unsigned long long red[8];
+    const double2 *q = reinterpret_cast<const double2 *>(p + blockIdx.x * len);
+    unsigned long long mx = 0;
+    for (long long t = threadIdx.x; t < len / 2; t += 256) {
+        const double2 v = q[t];
+        const unsigned long long a = static_cast<unsigned long long>(__double_as_longlong(v.x)) & 0x7FFFFFFFFFFFFFFFull;
+        const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(v.y)) & 0x7FFFFFFFFFFFFFFFull;
+        mx = a > mx ? a : mx;
+        mx = b > mx ? b : mx;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long y = __shfl_down_sync(0xffffffffu, mx, o);
+        mx = y > mx ? y : mx;
+    }
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long m = red[0];
+        for (int i = 1; i < 8; i++) m = red[i] > m ? red[i] : m;
+        e[blockIdx.x] = exponent_of_max(m);
+    }
 }
 
 constexpr int SLICE_ROWS = 8;   // rows per block of the slicer
@@ -197,19 +279,15 @@ __global__ void __launch_bounds__(256) slice_kernel(Src src, int rows, int K, in
     for (int rb = blockIdx.y * SLICE_ROWS; rb < rows; rb += gridDim.y * SLICE_ROWS) {
         const int rend = min(rows, rb + SLICE_ROWS);
         for (int r = rb; r < rend; r++) {
-            long long q[S] = {0, 0, 0, 0, 0, 0};
-            if (kk < K) {
-                long long F = to_fixed48(src.p[static_cast<long long>(r) * src.sr + koff], e[r / rpe]);
-                q[0] = (F + (1ll << 39)) >> 40; F -= q[0] << 40;
-                q[1] = (F + (1ll << 31)) >> 32; F -= q[1] << 32;
-                q[2] = (F + (1ll << 23)) >> 24; F -= q[2] << 24;
-                q[3] = (F + (1ll << 15)) >> 16; F -= q[3] << 16;
-                q[4] = (F + (1ll << 7)) >> 8;   F -= q[4] << 8;
-                q[5] = F;
-            }
+            int q[S] = {0, 0, 0, 0, 0, 0};
+            if (kk < K) digits6(to_fixed48(src.p[static_cast<long long>(r) * src.sr + koff], e[r / rpe]), q);
             const long long o = static_cast<long long>(r) * Kpad + kk;
+            float sc = 0.00390625f;
 #pragma unroll
-            for (int j = 0; j < S; j++) out[j * sstride + o] = q_to_bf16(q[j], j + 1);
+            for (int j = 0; j < S; j++) {
+                out[j * sstride + o] = static_cast<unsigned short>(qbf16(q[j], sc));
+                sc *= 0.00390625f;
+            }
         }
     }
 }
@@ -587,18 +665,34 @@ static jk_status slice_operand(jk_ctx *h, const oz::Src &src, int rows, int K, i
     out.Kpad = kpad_of(K);
     out.rpe = rpe;
     const int groups = (rows + rpe - 1) / rpe;
+    const bool aligned = (reinterpret_cast<uintptr_t>(src.p) & 15u) == 0;
+    // A group of rows that is one contiguous run of doubles (e.g. one L^P).
+    const bool flat = aligned && src.ski == 1 && src.kin == K && src.sr == K &&
+                      ((static_cast<long long>(rpe) * K) % 2) == 0 && rows % rpe == 0;
     {
         LaunchScope ls(h, KK_SLICE, st);
-        oz::expo_kernel<<<groups, 256, 0, st>>>(src, rows, K, rpe, out.e);
+        if (flat)
+            oz::expo_flat_kernel<<<groups, 256, 0, st>>>(src.p, static_cast<long long>(rpe) * K, out.e);
+        else
+            oz::expo_kernel<<<groups, 256, 0, st>>>(src, rows, K, rpe, out.e);
     }
     JK_LAUNCH_CHECK(h);
+    const bool vec = aligned && src.ski == 1 && (src.kin % 4) == 0 && (K % 4) == 0 && (src.sr % 2) == 0 &&
+                     (src.sko % 2) == 0;
     const int rblocks = (rows + oz::SLICE_ROWS - 1) / oz::SLICE_ROWS;
-    dim3 grid((out.Kpad + 255) / 256, rblocks < 65535 ? rblocks : 65535);
     {
         LaunchScope ls(h, KK_SLICE, st);
-        oz::slice_kernel<<<grid, 256, 0, st>>>(src, rows, K, out.Kpad, out.e, rpe,
-                                                reinterpret_cast<unsigned short *>(out.s),
-                                                static_cast<long long>(rows) * out.Kpad);
+        if (vec) {
+            dim3 grid((out.Kpad / 4 + 255) / 256, rblocks < 65535 ? rblocks : 65535);
+            oz::slice4_kernel<<<grid, 256, 0, st>>>(src, rows, K, out.Kpad, out.e, rpe,
+                                                     reinterpret_cast<uint2 *>(out.s),
+                                                     static_cast<long long>(rows) * out.Kpad / 4);
+        } else {
+            dim3 grid((out.Kpad + 255) / 256, rblocks < 65535 ? rblocks : 65535);
+            oz::slice_kernel<<<grid, 256, 0, st>>>(src, rows, K, out.Kpad, out.e, rpe,
+                                                    reinterpret_cast<unsigned short *>(out.s),
+                                                    static_cast<long long>(rows) * out.Kpad);
+        }
     }
     JK_LAUNCH_CHECK(h);
     return JK_OK;
