@@ -11,14 +11,17 @@
 //    integer arithmetic only (B300 has very little FP64 throughput).
 //  * Products.  The 21 slice pairs (a, b) with a + b <= 7 are multiplied on
 //    tcgen05 tensor cores (kind::f16, FP32 accumulate in tensor memory).
-//    Pairs on the same diagonal d = a + b - 2 share a scale 2^-(8d+16); the
-//    diagonals d = 0..3 each get their own TMEM accumulator and, over a
-//    window of 128 reduction elements, every partial sum is an integer below
-//    2^24 times that scale, so the FP32 accumulation is exact whatever the
-//    tensor core's rounding mode.  Diagonals d >= 4 (relative size <= 2^-32)
-//    share a fifth accumulator that spans a whole tile (<= 2048 elements);
-//    its truncation error stays below 2^-45.  The window boundaries of the
-//    four exact accumulators are staggered so their drains do not coincide.
+//    Pairs on the same diagonal d = a + b - 2 share a scale 2^-(8d+16) and
+//    one TMEM accumulator per diagonal (six of 80 columns, laid out by d), so
+//    the pairs (a, b..b+m) of one A slice hit adjacent accumulators and run
+//    as ONE MMA with N = 80(m+1): 10 MMAs per K-step instead of 21.  Over a
+//    window of 128 reduction elements every partial sum of diagonals
+//    d = 0..3 is an integer below 2^24 times its scale, so the FP32
+//    accumulation is exact whatever the tensor core's rounding mode;
+//    diagonals 4 and 5 (relative size <= 2^-32) accumulate over a whole tile
+//    (<= 2048 elements) with truncation error below 2^-45.  The window
+//    boundaries of the exact accumulators are staggered so their drains do
+//    not coincide; the epilogue zeroes each drained accumulator.
 //  * Recombination.  After each window an accumulator is
 //    read from TMEM, converted to 32-bit integers in their own units and
 //    shifted into a per-element int64 fixed-point accumulator with 48
@@ -41,13 +44,13 @@ namespace oz {
 
 constexpr int S = 6;            // slices per operand
 constexpr int BM = 128;         // rows of A per tile (TMEM lanes)
-constexpr int BN = 96;          // rows of B per tile (TMEM columns per accumulator)
+constexpr int BN = 80;          // rows of B per tile (TMEM columns per accumulator)
 constexpr int KB = 16;          // reduction elements per pipeline stage (one MMA K-step)
 constexpr int CHUNK = 128;      // exact accumulation window
 constexpr int KBPC = CHUNK / KB;
 constexpr int SUPER = 2048;     // reduction elements per int64 partial
 constexpr int NSTAGE = 3;
-constexpr int NACC = 5;
+constexpr int NACC = 6;
 constexpr int NPAIRS = 21;
 constexpr int FRAC = 48;        // fraction bits of the int64 accumulator
 constexpr int THREADS = 320;    // producer warp, MMA warp, 8 epilogue warps
@@ -55,11 +58,11 @@ constexpr int THREADS = 320;    // producer warp, MMA warp, 8 epilogue warps
 constexpr int A_BYTES = S * BM * 32;
 constexpr int B_BYTES = S * BN * 32;
 constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
-// Output staging: each epilogue warp owns 32 rows x 48 columns of 64-bit words,
-// kept as three 32x16 blocks in the 128-byte swizzled layout of a TMA store.
+// Output staging: each epilogue warp owns 32 rows x 40 columns of 64-bit words,
+// kept as five 32x8 blocks in the 64-byte swizzled layout of a TMA store.
 constexpr int OUT_COLS = BN / 2;
-constexpr int OUT_BLK = 16;                        // 64-bit words per 128-byte row
-constexpr int OUT_WARP_BYTES = 32 * OUT_COLS * 8;  // 12 KB
+constexpr int OUT_BLK = 8;                         // 64-bit words per 64-byte row
+constexpr int OUT_WARP_BYTES = 32 * OUT_COLS * 8;  // 10 KB
 constexpr int OUT_BYTES = 8 * OUT_WARP_BYTES;
 constexpr int SMEM_BYTES = NSTAGE * STAGE_BYTES + OUT_BYTES + 1024 /*align slack*/ + 256 /*barriers*/;
 
@@ -310,21 +313,48 @@ struct OzArgs {
     int *err;             // device error word (JK_ERR_TIMEOUT on a stalled pipeline)
 };
 
-// Accumulator windows.  Diagonal d <= 3 restarts every KBPC K-blocks, with
-// the boundary of accumulator d offset by WOFF[d] blocks so that the drains of
-// the four exact accumulators are spread over the window instead of all
-// landing at once.  The last accumulator (d >= 4, inexact) spans the tile.
-__host__ __device__ constexpr int woff(int d) { return d < 4 ? 2 * d : 0; }
+// Accumulator windows.  Exactness bounds (|q_1| <= 256, |q_j| <= 128): one
+// reduction element adds at most 2^16 units to diagonals 0 and 1, and at most
+// 2^16 + 2^15 units to diagonals 2 and 3, so windows of 256 (d = 0, 1) and 128
+// (d = 2, 3) elements keep every partial sum below 2^24.  Window boundaries are
+// offset per accumulator so drains are spread over the K-blocks; accumulators
+// 4 and 5 (inexact) span the tile.
+__host__ __device__ constexpr int wper(int d) { return d < 2 ? 2 * KBPC : KBPC; }
+__host__ __device__ constexpr int woff(int d) { return d == 0 ? 0 : d == 1 ? KBPC : d == 2 ? 2 : 6; }
 
 __device__ __forceinline__ bool win_start(int d, int kb) {
     if (kb == 0) return true;
-    if (d == NACC - 1) return false;
-    return kb >= woff(d) && ((kb - woff(d)) % KBPC) == 0;
+    if (d >= 4) return false;
+    return kb >= woff(d) && ((kb - woff(d)) % wper(d)) == 0;
 }
 
 __device__ __forceinline__ bool win_end(int d, int kb, int nkb) {
     return kb == nkb - 1 || win_start(d, kb + 1);
 }
+
+// The same window pattern by residue r = kb mod 2*KBPC (compile-time inside the
+// unrolled K-block loop); tile starts and ends are added at run time.
+constexpr int WPERIOD = 2 * KBPC;
+__host__ __device__ constexpr bool ws_r(int d, int r) {
+    return d == 0 ? r == 0 : d == 1 ? r == KBPC : d == 2 ? (r % KBPC) == 2 : d == 3 ? (r % KBPC) == 6 : false;
+}
+__host__ __device__ constexpr unsigned ws_mask(int r) {
+    return (ws_r(0, r) ? 1u : 0u) | (ws_r(1, r) ? 2u : 0u) | (ws_r(2, r) ? 4u : 0u) | (ws_r(3, r) ? 8u : 0u);
+}
+__host__ __device__ constexpr unsigned we_mask(int r) { return ws_mask((r + 1) % WPERIOD); }
+
+// The 21 slice pairs as 10 merged MMAs: A slice a times B slices b0..b0+nb-1
+// into accumulators d0..d0+nb-1 (d = a + b).  Ordered so that MMAs touching
+// only the tile-long accumulators 4, 5 go first and the MMA touching
+// accumulator 0 goes last: the accumulator whose window just restarted is
+// needed as late as possible.
+constexpr int NMMA = 10;
+__host__ __device__ constexpr int mma_a(int i) { return i == 0 ? 0 : i == 1 ? 1 : i == 2 ? 2 : i == 3 ? 4 : i == 4 ? 5 : i == 5 ? 3 : i == 6 ? 2 : i == 7 ? 1 : 0; }
+__host__ __device__ constexpr int mma_b0(int i) { return i == 0 ? 4 : i == 1 ? 3 : i == 2 ? 3 : i == 8 ? 3 : 0; }
+__host__ __device__ constexpr int mma_nb(int i) { return i == 0 || i == 1 || i == 3 ? 2 : i == 2 || i == 4 || i == 8 ? 1 : 3; }
+__host__ __device__ constexpr int mma_d0(int i) { return mma_a(i) + mma_b0(i); }
+// Drain order at a tile end: the first MMAs of the next tile need 4, 5, then 3, 2, 1, 0.
+__host__ __device__ constexpr int drain_acc(int j) { return j == 0 ? 4 : j == 1 ? 5 : 3 - (j - 2); }
 
 // Tile t of the launch: n-tile fastest (tiles sharing an A row block run side
 // by side and hit L2), then m-tile, then the split-K super-chunk z.
@@ -403,51 +433,55 @@ ozgemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
     } else if (warp == 1) {
         // ---------------- MMA issuer ----------------
         if (lane == 0) {
-            constexpr uint32_t idesc = tc::idesc_bf16_f32(BM, BN);
-            // Pair tables as compile-time constants (the loop below is fully unrolled).
-            constexpr int PA[NPAIRS] = {0, 0, 1, 0, 1, 2, 0, 1, 2, 3, 0, 1, 2, 3, 4, 0, 1, 2, 3, 4, 5};
-            constexpr int PB[NPAIRS] = {0, 1, 0, 2, 1, 0, 3, 2, 1, 0, 4, 3, 2, 1, 0, 5, 4, 3, 2, 1, 0};
-            constexpr int PACC[NPAIRS] = {0, 1, 1, 2, 2, 2, 3, 3, 3, 3, 4, 4, 4, 4, 4, 4, 4, 4, 4, 4, 4};
-            constexpr int PFIRST[NPAIRS] = {1, 1, 0, 1, 0, 0, 1, 0, 0, 0, 1, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
             int stage = 0;
             uint32_t phase = 0;
-            int mcnt[NACC] = {0, 0, 0, 0, 0};   // windows completed per accumulator
+            int wcnt[NACC] = {0, 0, 0, 0, 0, 0};   // windows started per accumulator
             bool ok = true;
             for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
                 const TileCoord tc_ = tile_of(t, ntn, ntm, a.K);
-                for (int kb = 0; kb < tc_.nkb; kb++) {
-                    if (!tc::mbar_wait(&full[stage], phase, abort_flag)) { ok = false; break; }
-                    tc::fence_after_sync();
-                    const uint64_t ad0 = tc::sdesc_kmajor_sw32(tc::smem_u32(smem + stage * STAGE_BYTES));
-                    const uint64_t bd0 = tc::sdesc_kmajor_sw32(tc::smem_u32(smem + stage * STAGE_BYTES + A_BYTES));
+                for (int kb0 = 0; kb0 < tc_.nkb && ok; kb0 += WPERIOD) {
+                    // Unrolled over one window period: the window bookkeeping below is
+                    // compile-time except for the tile's first and last K-block.
 #pragma unroll
-                    for (int p = 0; p < NPAIRS; p++) {
-                        uint32_t accumulate = 1;
-                        if (PFIRST[p] && win_start(PACC[p], kb)) {
-                            if (mcnt[PACC[p]] > 0) {
-                                if (!tc::mbar_wait(&accempty[PACC[p]], static_cast<uint32_t>(mcnt[PACC[p]] - 1) & 1u,
-                                                   abort_flag)) {
-                                    ok = false;
-                                    break;
+                    for (int r = 0; r < WPERIOD; r++) {
+                        const int kb = kb0 + r;
+                        if (kb >= tc_.nkb) break;
+                        if (!tc::mbar_wait(&full[stage], phase, abort_flag)) { ok = false; break; }
+                        tc::fence_after_sync();
+                        unsigned pend = ws_mask(r) | (kb == 0 ? 0x3Fu : 0u);
+                        const uint64_t ad0 = tc::sdesc_kmajor_sw32(tc::smem_u32(smem + stage * STAGE_BYTES));
+                        const uint64_t bd0 = ad0 + static_cast<uint64_t>(A_BYTES / 16);
+#pragma unroll
+                        for (int i = 0; i < NMMA; i++) {
+                            const unsigned need = pend & (((1u << mma_nb(i)) - 1u) << mma_d0(i));
+                            if (need) {
+#pragma unroll
+                                for (int d = 0; d < NACC; d++) {
+                                    if (!(need & (1u << d))) continue;
+                                    // the epilogue has drained and zeroed accumulator d
+                                    if (!tc::mbar_wait(&accempty[d], static_cast<uint32_t>(wcnt[d]) & 1u, abort_flag)) {
+                                        ok = false;
+                                        break;
+                                    }
+                                    wcnt[d]++;
                                 }
+                                if (!ok) break;
+                                pend &= ~need;
                                 tc::fence_after_sync();
                             }
-                            accumulate = 0;
+                            // descriptor start address is in 16-byte units
+                            tc::mma_bf16(tmem + mma_d0(i) * BN, ad0 + static_cast<uint64_t>(mma_a(i) * (BM * 32 / 16)),
+                                         bd0 + static_cast<uint64_t>(mma_b0(i) * (BN * 32 / 16)),
+                                         tc::idesc_bf16_f32(BM, BN * mma_nb(i)), 1u);
                         }
-                        // descriptor start address is in 16-byte units
-                        tc::mma_bf16(tmem + PACC[p] * BN, ad0 + static_cast<uint64_t>(PA[p] * (BM * 32 / 16)),
-                                     bd0 + static_cast<uint64_t>(PB[p] * (BN * 32 / 16)), idesc, accumulate);
-                    }
-                    if (!ok) break;
-                    tc::mma_commit(&empty[stage]);
+                        if (!ok) break;
+                        tc::mma_commit(&empty[stage]);
+                        const unsigned ends = we_mask(r) | (kb == tc_.nkb - 1 ? 0x3Fu : 0u);
 #pragma unroll
-                    for (int d = 0; d < NACC; d++) {
-                        if (win_end(d, kb, tc_.nkb)) {
-                            tc::mma_commit(&accfull[d]);
-                            mcnt[d]++;
-                        }
+                        for (int d = 0; d < NACC; d++)
+                            if (ends & (1u << d)) tc::mma_commit(&accfull[d]);
+                        if (++stage == NSTAGE) { stage = 0; phase ^= 1u; }
                     }
-                    if (++stage == NSTAGE) { stage = 0; phase ^= 1u; }
                 }
             }
         }
@@ -456,7 +490,18 @@ ozgemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
         const int ew = warp - 2;
         const int q = warp & 3;          // lane quarter this warp may access
         const int half = ew >> 2;        // which half of the tile's columns
-        int ecnt[NACC] = {0, 0, 0, 0, 0};
+        const uint32_t tlane = tmem + (static_cast<uint32_t>(q * 32) << 16) + half * (BN / 2);
+        // Accumulators start at zero: clear this warp's share, then open them.
+#pragma unroll
+        for (int d = 0; d < NACC; d++)
+#pragma unroll
+            for (int c = 0; c < BN / 2; c += 8) tc::tmem_zero8(tlane + d * BN + c);
+        tc::tmem_wait_st();
+        tc::fence_before_sync();
+        __syncwarp();
+        if (lane == 0)
+            for (int d = 0; d < NACC; d++) tc::mbar_arrive(&accempty[d]);
+        int ecnt[NACC] = {0, 0, 0, 0, 0, 0};
         bool ok = true;
         for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
             const TileCoord tc_ = tile_of(t, ntn, ntm, a.K);
@@ -464,9 +509,12 @@ ozgemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
 #pragma unroll
             for (int i = 0; i < BN / 2; i++) acc64[i] = 0;
             for (int kb = 0; kb < tc_.nkb && ok; kb++) {
+                const unsigned ends = we_mask(kb % WPERIOD) | (kb == tc_.nkb - 1 ? 0x3Fu : 0u);
+                if (!ends) continue;
 #pragma unroll
-                for (int d = 0; d < NACC; d++) {
-                    if (!win_end(d, kb, tc_.nkb)) continue;
+                for (int j = 0; j < NACC; j++) {
+                    const int d = drain_acc(j);
+                    if (!(ends & (1u << d))) continue;
                     if (!tc::mbar_wait(&accfull[d], static_cast<uint32_t>(ecnt[d]) & 1u, abort_flag)) {
                         ok = false;
                         break;
@@ -474,28 +522,32 @@ ozgemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                     ecnt[d]++;
                     __syncwarp();
                     tc::fence_after_sync();
-                    const uint32_t tbase = tmem + (static_cast<uint32_t>(q * 32) << 16) + d * BN + half * (BN / 2);
                     float v[BN / 2];
 #pragma unroll
-                    for (int c = 0; c < BN / 2; c += 16) tc::tmem_ld16(tbase + c, v + c);
+                    for (int c = 0; c < BN / 2; c += 8) tc::tmem_ld8(tlane + d * BN + c, v + c);
                     tc::tmem_wait_ld();
+#pragma unroll
+                    for (int c = 0; c < BN / 2; c += 8) tc::tmem_zero8(tlane + d * BN + c);
+                    tc::tmem_wait_st();
                     tc::fence_before_sync();
                     __syncwarp();
                     if (lane == 0) tc::mbar_arrive(&accempty[d]);
                     // Accumulator d <= 3 holds integers in units of 2^-(8d+16) below 2^24;
-                    // the last one (spanning the tile) stays below 2^-20.  Scale to the
-                    // unit, convert with the FP32 add of 1.5*2^23 (exact below 2^22;
-                    // the rare larger value falls back to F2I), then shift into the
-                    // 2^-48 fixed point of acc64.  No 64-bit float conversions: those
-                    // run on the scarce FP64 pipe.
+                    // accumulators 4, 5 (spanning the tile) stay below 2^-20.  Scale to
+                    // the unit and convert with one FFMA against 1.5*2^23 (exact below
+                    // 2^22; the rare larger value falls back to F2I), then add into the
+                    // 2^-48 fixed point of acc64 (a high-word add for d = 0, a 32x32->64
+                    // multiply-add otherwise).  No 64-bit float conversions: those run
+                    // on the scarce FP64 pipe.
                     const float unit = d < 4 ? __int_as_float((127 + 16 + 8 * d) << 23) : 0x1p48f;
-                    const int sh = d < 4 ? 32 - 8 * d : 0;
+                    const float vmax = d < 4 ? __int_as_float((127 + 22 - 16 - 8 * d) << 23) : 0x1p-26f;
 #pragma unroll
                     for (int i = 0; i < BN / 2; i++) {
-                        const float y = v[i] * unit;
-                        int xi = __float_as_int(y + 12582912.0f) - 0x4B400000;
-                        if (fabsf(y) > 4194304.0f) xi = __float2int_rn(y);
-                        acc64[i] += static_cast<long long>(xi) << sh;
+                        int xi = __float_as_int(__fmaf_rn(v[i], unit, 12582912.0f)) - 0x4B400000;
+                        if (fabsf(v[i]) > vmax) xi = __float2int_rn(v[i] * unit);
+                        if (d == 0) acc64[i] += static_cast<long long>(xi) << 32;
+                        else if (d < 4) acc64[i] += static_cast<long long>(xi) * static_cast<long long>(1 << (32 - 8 * d));
+                        else acc64[i] += static_cast<long long>(xi);
                     }
                 }
             }
@@ -522,8 +574,8 @@ ozgemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                             w0 = __double_as_longlong(d0);
                             w1 = __double_as_longlong(d1);
                         }
-                        const int chunk = j ^ (lane & 7);   // 128-byte swizzle
-                        longlong2 *dst = reinterpret_cast<longlong2 *>(blk + lane * 128 + chunk * 16);
+                        const int chunk = j ^ ((lane >> 1) & 3);   // 64-byte swizzle
+                        longlong2 *dst = reinterpret_cast<longlong2 *>(blk + lane * 64 + chunk * 16);
                         *dst = make_longlong2(w0, w1);
                     }
                 }
@@ -627,17 +679,17 @@ jk_status make_slice_map(jk_ctx *h, CUtensorMap *map, const __nv_bfloat16 *base,
 }
 
 // Tensor map over a row-major matrix of 64-bit words (rows x cols, row stride
-// ld words, ld even), box = 16 words x 32 rows, 128-byte swizzle: the layout
+// ld words, ld even), box = 8 words x 32 rows, 64-byte swizzle: the layout
 // the GEMM epilogue stages its output in.
 jk_status make_out_map(jk_ctx *h, CUtensorMap *map, void *base, long long rows, int cols, long long ld) {
     EncodeTiledFn fn = encode_fn();
     if (!fn) return set_error(h, JK_ERR_CUDA, "cuTensorMapEncodeTiled is unavailable");
     cuuint64_t dims[2] = {static_cast<cuuint64_t>(cols), static_cast<cuuint64_t>(rows)};
     cuuint64_t strides[1] = {static_cast<cuuint64_t>(ld) * 8};
-    cuuint32_t box[2] = {16, 32};
+    cuuint32_t box[2] = {oz::OUT_BLK, 32};
     cuuint32_t estr[2] = {1, 1};
     CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_INT64, 2, base, dims, strides, box, estr,
-                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_NONE,
                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return set_error(h, JK_ERR_CUDA, "cuTensorMapEncodeTiled (output) failed (%d)", (int)r);
     return JK_OK;
