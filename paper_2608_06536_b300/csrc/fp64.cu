@@ -373,6 +373,24 @@ jk_status fp64_gamma_panel(jk_ctx *h, const Problem &pb, const double *T, long l
     return JK_OK;
 }
 
+// out[s*naux + P] = <L^P, M_s> for dense n x n matrices M_s (s < nd).
+jk_status fp64_frob_all(jk_ctx *h, const double *L, int n, int naux, const double *Mats, int nd, double *out,
+                        cudaStream_t st) {
+    const long long n2 = (long long)n * n;
+    LaunchScope ls(h, KK_FROB, st);
+    frob_stream_kernel<<<dim3(naux, (nd + 3) / 4), 256, 0, st>>>(L, n2, Mats, nd, out, naux, 0);
+    JK_LAUNCH_CHECK(h);
+    return JK_OK;
+}
+
+// out[s] = sum_P g[s*naux + P] L^P (dense [nd][n][n] output).
+jk_status fp64_jstream_dense(jk_ctx *h, const double *L, int n, int naux, const double *g, int nd, double *out,
+                             cudaStream_t st) {
+    double *ptrs[kMaxDens];
+    for (int s = 0; s < nd; s++) ptrs[s] = out + (long long)s * n * n;
+    return jstream(h, L, n, naux, g, naux, nd, ptrs, st);
+}
+
 jk_status fp64_jstream(jk_ctx *h, const Problem &pb, const double *gamma, cudaStream_t st) {
     return jstream(h, pb.L, pb.n, pb.naux, gamma, pb.naux, pb.nd, pb.J, st);
 }

@@ -34,7 +34,9 @@
 #include <cuda.h>
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cstring>
+#include <type_traits>
 
 #include "jk_internal.h"
 #include "tc.cuh"
@@ -72,9 +74,11 @@ constexpr int SMEM_BYTES = NSTAGE * STAGE_BYTES + OUT_BYTES + 1024 /*align slack
 // ---------------------------------------------------------------------------
 
 // Exponent e with max|x| < 2^e (from the biased exponent field of max|x|).
+// An all-zero group gets a very small exponent so it never sets the scale
+// when partial sums are aligned.
 __device__ __forceinline__ int exponent_of_max(unsigned long long maxbits) {
     int ex = static_cast<int>((maxbits >> 52) & 0x7FF);
-    return ex == 0 ? 0 : ex - 1022;
+    return ex == 0 ? -1000 : ex - 1022;
 }
 
 // F = round(x * 2^(48 - e)) as a signed integer, |F| <= 2^48 when |x| <= 2^e.
@@ -124,32 +128,36 @@ __device__ __forceinline__ double i128_to_f64_scaled(__int128 v, int e2) {
 // ---------------------------------------------------------------------------
 
 // Source addressing: element (row r, reduction index kk) is at
-// p + r*sr + (kk / kin)*sko + (kk % kin)*ski.
+// p + (r / rin)*sr + (r % rin)*sri + (kk / kin)*sko + (kk % kin)*ski
+// (two-level row and reduction indices, e.g. rows (P, i) or K = (P, lam)).
 struct Src {
     const double *p;
     long long sr, sko, ski;
     int kin;
+    int rin = 1;
+    long long sri = 0;
 };
 
-__device__ __forceinline__ double src_at(const Src &s, int r, int kk) {
-    const int ko = kk / s.kin, ki = kk - ko * s.kin;
-    return s.p[static_cast<long long>(r) * s.sr + static_cast<long long>(ko) * s.sko +
-               static_cast<long long>(ki) * s.ski];
+__device__ __forceinline__ const double *src_row(const Src &s, int r) {
+    const int ro = r / s.rin, ri = r - ro * s.rin;
+    return s.p + static_cast<long long>(ro) * s.sr + static_cast<long long>(ri) * s.sri;
 }
 
-// e[g] for row groups g of `rpe` rows: max|x| over the group's rows and all K.
-// Each thread walks reduction indices kk = tid, tid + 256, ... keeping (ko, ki)
-// incrementally, so the hot loop has no integer division.
+// e[g * gridDim.y + z] for row groups g of `rpe` rows and super-chunks z of
+// the reduction index: max|x| over the group's rows and kk in
+// [z*SUPER, (z+1)*SUPER).  Each thread walks kk = k0 + tid, + 256, ... keeping
+// (ko, ki) incrementally, so the hot loop has no integer division.
 __global__ void __launch_bounds__(256) expo_kernel(Src src, int rows, int K, int rpe, int *e) {
     __shared__ unsigned long long red[8];
-    const int g = blockIdx.x;
+    const int g = blockIdx.x, z = blockIdx.y;
     const int r0 = g * rpe, r1 = min(rows, r0 + rpe);
+    const int k0 = z * SUPER, k1 = min(K, k0 + SUPER);
     const int step_o = 256 / src.kin, step_i = 256 % src.kin;
     unsigned long long mx = 0;
     for (int r = r0; r < r1; r++) {
-        const double *row = src.p + static_cast<long long>(r) * src.sr;
-        int ko = threadIdx.x / src.kin, ki = threadIdx.x - ko * src.kin;
-        for (int kk = threadIdx.x; kk < K; kk += 256) {
+        const double *row = src_row(src, r);
+        int ko = (k0 + threadIdx.x) / src.kin, ki = k0 + threadIdx.x - ko * src.kin;
+        for (int kk = k0 + threadIdx.x; kk < k1; kk += 256) {
             const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(
                                              row[static_cast<long long>(ko) * src.sko +
                                                  static_cast<long long>(ki) * src.ski])) &
@@ -170,7 +178,7 @@ __global__ void __launch_bounds__(256) expo_kernel(Src src, int rows, int K, int
     if (threadIdx.x == 0) {
         unsigned long long m = red[0];
         for (int i = 1; i < 8; i++) m = red[i] > m ? red[i] : m;
-        e[g] = exponent_of_max(m);
+        e[g * gridDim.y + z] = exponent_of_max(m);
     }
 }
 
@@ -200,7 +208,7 @@ __device__ __forceinline__ uint32_t qbf16(int q, float scale) {
 // src.ski == 1, src.kin % 4 == 0, K % 4 == 0 and 16-byte aligned pairs
 // (checked on the host).
 __global__ void __launch_bounds__(256) slice4_kernel(Src src, int rows, int K, int Kpad, const int *e, int rpe,
-                                                     uint2 *out, long long sstride4) {
+                                                     int nsc, uint2 *out, long long sstride4) {
     const int kk = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
     if (kk >= Kpad) return;
     long long koff = 0;
@@ -213,9 +221,9 @@ __global__ void __launch_bounds__(256) slice4_kernel(Src src, int rows, int K, i
         for (int r = rb; r < rend; r++) {
             int q[4][S];
             if (kk < K) {
-                const double2 *p2 = reinterpret_cast<const double2 *>(src.p + static_cast<long long>(r) * src.sr + koff);
+                const double2 *p2 = reinterpret_cast<const double2 *>(src_row(src, r) + koff);
                 const double2 a = p2[0], b = p2[1];
-                const int er = e[r / rpe];
+                const int er = e[(r / rpe) * nsc + kk / SUPER];
                 digits6(to_fixed48(a.x, er), q[0]);
                 digits6(to_fixed48(a.y, er), q[1]);
                 digits6(to_fixed48(b.x, er), q[2]);
@@ -271,7 +279,7 @@ constexpr int SLICE_ROWS = 8;   // rows per block of the slicer
 
 // out[j][r][kk] = q_j(r, kk) * 2^(-8(j+1)) for j = 0..5 (bf16), zero for kk >= K.
 __global__ void __launch_bounds__(256) slice_kernel(Src src, int rows, int K, int Kpad, const int *e,
-                                                    int rpe, unsigned short *out, long long sstride) {
+                                                    int rpe, int nsc, unsigned short *out, long long sstride) {
     const int kk = blockIdx.x * blockDim.x + threadIdx.x;
     if (kk >= Kpad) return;
     long long koff = 0;
@@ -283,7 +291,7 @@ __global__ void __launch_bounds__(256) slice_kernel(Src src, int rows, int K, in
         const int rend = min(rows, rb + SLICE_ROWS);
         for (int r = rb; r < rend; r++) {
             int q[S] = {0, 0, 0, 0, 0, 0};
-            if (kk < K) digits6(to_fixed48(src.p[static_cast<long long>(r) * src.sr + koff], e[r / rpe]), q);
+            if (kk < K) digits6(to_fixed48(src_row(src, r)[koff], e[(r / rpe) * nsc + kk / SUPER]), q);
             const long long o = static_cast<long long>(r) * Kpad + kk;
             float sc = 0.00390625f;
 #pragma unroll
@@ -559,7 +567,7 @@ ozgemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                 uint8_t *wbuf = outbuf + ew * OUT_WARP_BYTES;
                 if (lane == 0) tc::bulk_wait_read();   // previous tile's store has read the buffer
                 __syncwarp();
-                const int ea = a.nsuper == 1 && row < a.M ? a.eA[row / a.a_rpe] - FRAC : 0;
+                const int ea = a.nsuper == 1 && row < a.M ? a.eA[row / a.a_rpe] - FRAC : 0;   // z = 0
 #pragma unroll
                 for (int b = 0; b < OUT_COLS / OUT_BLK; b++) {
                     uint8_t *blk = wbuf + b * (32 * OUT_BLK * 8);
@@ -622,7 +630,9 @@ ozgemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
     if (threadIdx.x == 0 && *abort_flag) atomicExch(a.err, static_cast<int>(JK_ERR_TIMEOUT));
 }
 
-// out[r][c] (+)= 2^(eA[r/arpe] + eB[c/brpe] - 48) * sum_z P[z][r][c]   (sum in 128-bit integers)
+// out[r][c] (+)= sum_z P[z][r][c] 2^(eA[r/arpe][z] + eB[c/brpe][z] - 48).  The
+// partials are aligned to the largest scale by 128-bit shifts (52 guard bits)
+// and summed exactly; one rounding to FP64 at the end.
 __global__ void __launch_bounds__(256)
 reduce_partials_kernel(const long long *P, long long pz, long long ldp, int nz, int M, int N, const int *eA,
                        int arpe, const int *eB, int brpe, double *out, long long ldo, int accumulate) {
@@ -630,9 +640,16 @@ reduce_partials_kernel(const long long *P, long long pz, long long ldp, int nz, 
     if (e >= static_cast<long long>(M) * N) return;
     const int r = static_cast<int>(e / N), c = static_cast<int>(e % N);
     const long long off = static_cast<long long>(r) * ldp + c;
+    const int *ea = eA + static_cast<long long>(r / arpe) * nz;
+    const int *eb = eB + static_cast<long long>(c / brpe) * nz;
+    int emax = -(1 << 30);
+    for (int zz = 0; zz < nz; zz++) emax = max(emax, ea[zz] + eb[zz]);
     __int128 s = 0;
-    for (int zz = 0; zz < nz; zz++) s += static_cast<__int128>(P[zz * pz + off]);
-    const double v = i128_to_f64_scaled(s, eA[r / arpe] + eB[c / brpe] - FRAC);
+    for (int zz = 0; zz < nz; zz++) {
+        const int d = emax - (ea[zz] + eb[zz]);
+        if (d < 100) s += (static_cast<__int128>(P[zz * pz + off]) << 52) >> d;
+    }
+    const double v = i128_to_f64_scaled(s, emax - FRAC - 52);
     double *o = out + static_cast<long long>(r) * ldo + c;
     *o = accumulate ? (*o + v) : v;
 }
@@ -717,31 +734,32 @@ static jk_status slice_operand(jk_ctx *h, const oz::Src &src, int rows, int K, i
     out.Kpad = kpad_of(K);
     out.rpe = rpe;
     const int groups = (rows + rpe - 1) / rpe;
+    const int nsc = (K + oz::SUPER - 1) / oz::SUPER;   // one exponent per row group and super-chunk
     const bool aligned = (reinterpret_cast<uintptr_t>(src.p) & 15u) == 0;
     // A group of rows that is one contiguous run of doubles (e.g. one L^P).
-    const bool flat = aligned && src.ski == 1 && src.kin == K && src.sr == K &&
+    const bool flat = nsc == 1 && aligned && src.rin == 1 && src.ski == 1 && src.kin == K && src.sr == K &&
                       ((static_cast<long long>(rpe) * K) % 2) == 0 && rows % rpe == 0;
     {
         LaunchScope ls(h, KK_SLICE, st);
         if (flat)
             oz::expo_flat_kernel<<<groups, 256, 0, st>>>(src.p, static_cast<long long>(rpe) * K, out.e);
         else
-            oz::expo_kernel<<<groups, 256, 0, st>>>(src, rows, K, rpe, out.e);
+            oz::expo_kernel<<<dim3(groups, nsc), 256, 0, st>>>(src, rows, K, rpe, out.e);
     }
     JK_LAUNCH_CHECK(h);
     const bool vec = aligned && src.ski == 1 && (src.kin % 4) == 0 && (K % 4) == 0 && (src.sr % 2) == 0 &&
-                     (src.sko % 2) == 0;
+                     (src.sri % 2) == 0 && (src.sko % 2) == 0;
     const int rblocks = (rows + oz::SLICE_ROWS - 1) / oz::SLICE_ROWS;
     {
         LaunchScope ls(h, KK_SLICE, st);
         if (vec) {
             dim3 grid((out.Kpad / 4 + 255) / 256, rblocks < 65535 ? rblocks : 65535);
-            oz::slice4_kernel<<<grid, 256, 0, st>>>(src, rows, K, out.Kpad, out.e, rpe,
+            oz::slice4_kernel<<<grid, 256, 0, st>>>(src, rows, K, out.Kpad, out.e, rpe, nsc,
                                                      reinterpret_cast<uint2 *>(out.s),
                                                      static_cast<long long>(rows) * out.Kpad / 4);
         } else {
             dim3 grid((out.Kpad + 255) / 256, rblocks < 65535 ? rblocks : 65535);
-            oz::slice_kernel<<<grid, 256, 0, st>>>(src, rows, K, out.Kpad, out.e, rpe,
+            oz::slice_kernel<<<grid, 256, 0, st>>>(src, rows, K, out.Kpad, out.e, rpe, nsc,
                                                     reinterpret_cast<unsigned short *>(out.s),
                                                     static_cast<long long>(rows) * out.Kpad);
         }
@@ -751,13 +769,14 @@ static jk_status slice_operand(jk_ctx *h, const oz::Src &src, int rows, int K, i
 }
 
 static size_t sliced_bytes(int rows, int K, int rpe) {
+    const size_t nsc = (K + oz::SUPER - 1) / oz::SUPER;
     return align_up(static_cast<size_t>(oz::S) * rows * kpad_of(K) * 2) +
-           align_up(static_cast<size_t>((rows + rpe - 1) / rpe) * 4);
+           align_up(static_cast<size_t>((rows + rpe - 1) / rpe) * nsc * 4);
 }
 
 static bool take_sliced(Arena &ar, int rows, int K, int rpe, Sliced &out) {
     out.s = ar.take<__nv_bfloat16>(static_cast<size_t>(oz::S) * rows * kpad_of(K));
-    out.e = ar.take<int>(static_cast<size_t>((rows + rpe - 1) / rpe));
+    out.e = ar.take<int>(static_cast<size_t>((rows + rpe - 1) / rpe) * ((K + oz::SUPER - 1) / oz::SUPER));
     return out.s && out.e;
 }
 
@@ -878,7 +897,6 @@ size_t split_build_workspace(const Problem &pb) {
     return b;
 }
 
-size_t split_adjoint_workspace(const Problem &, bool) { return 0; }
 
 jk_status split_pack_z(jk_ctx *h, const Problem &pb, double *Z, cudaStream_t st);
 jk_status fp64_gamma_panel(jk_ctx *h, const Problem &pb, const double *T, long long ldT, int np, double *gamma,
@@ -965,9 +983,317 @@ jk_status split_build(jk_ctx *h, const Problem &pb, cudaStream_t st) {
     return JK_OK;
 }
 
-jk_status split_adjoint(jk_ctx *h, const Problem &, const double *, const double *, double *, double *,
-                        double *, cudaStream_t) {
-    return set_error(h, JK_ERR_UNSUPPORTED, "split-precision adjoint not built yet");
+// ---------------------------------------------------------------------------
+// The split adjoint
+// ---------------------------------------------------------------------------
+namespace {
+
+// AG[(p, mu)][col] for one density: [U^p[mu][i] | Vp^p[mu][i] | c_{P0+p,s} X[mu][i]]
+// at columns off, off + k, off + 2k (U, Vp laid out [mu][(p, i)]).
+__global__ void pack_ag_kernel(double *AG, long long ldag, int off, const double *U, const double *Vp,
+                               const double *X, const double *cps, int P0, int n, int k, int np) {
+    const long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
+    const long long tot = static_cast<long long>(np) * n * k;
+    if (e >= tot) return;
+    const int i = static_cast<int>(e % k);
+    const long long pm = e / k;
+    const int mu = static_cast<int>(pm % n), p = static_cast<int>(pm / n);
+    double *row = AG + pm * ldag + off;
+    const long long uo = static_cast<long long>(mu) * np * k + static_cast<long long>(p) * k + i;
+    row[i] = U ? U[uo] : 0.0;
+    row[k + i] = Vp ? Vp[uo] : 0.0;
+    row[2 * k + i] = cps ? cps[P0 + p] * X[static_cast<long long>(mu) * k + i] : 0.0;
+}
+
+// BG[nu][col] = [X[nu][i] | Y[nu][i] | Y[nu][i]] at off, off + k, off + 2k.
+__global__ void pack_bg_kernel(double *BG, long long ldbg, int off, const double *X, const double *Y, int n, int k) {
+    const long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
+    if (e >= static_cast<long long>(n) * k) return;
+    const int nu = static_cast<int>(e / k), i = static_cast<int>(e % k);
+    double *row = BG + static_cast<long long>(nu) * ldbg + off;
+    row[i] = X[e];
+    row[k + i] = Y[e];
+    row[2 * k + i] = Y[e];
+}
+
+// dL^{P0+p} = (G^p + G^p^T)/2 + (GV^p + GV^p^T)/2   (GV may be NULL)
+__global__ void sym_dl_kernel(const double *G, const double *GV, int n, double *dL) {
+    const long long n2 = static_cast<long long>(n) * n;
+    const long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
+    const int p = blockIdx.y;
+    if (e >= n2) return;
+    const int mu = static_cast<int>(e / n), nu = static_cast<int>(e % n);
+    const long long t = static_cast<long long>(nu) * n + mu;
+    const double *Gp = G + p * n2;
+    double v = 0.5 * (Gp[e] + Gp[t]);
+    if (GV) {
+        const double *Vp = GV + p * n2;
+        v += 0.5 * (Vp[e] + Vp[t]);
+    }
+    dL[p * n2 + e] = v;
+}
+
+__global__ void fold_sym_split_kernel(double *dX, double *dY, long long cnt) {
+    const long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
+    if (e >= cnt) return;
+    dX[e] += dY[e];
+    dY[e] = 0.0;
+}
+
+}  // namespace
+
+jk_status fp64_frob_all(jk_ctx *h, const double *L, int n, int naux, const double *Mats, int nd, double *out,
+                        cudaStream_t st);
+jk_status fp64_jstream_dense(jk_ctx *h, const double *L, int n, int naux, const double *g, int nd, double *out,
+                             cudaStream_t st);
+
+// out (+)= A B^T on sliced operands, FP64 out with row stride ldo.  Uses P (int64
+// partials) when K spans several super-chunks, else tmp when accumulating.
+static jk_status gemm_into(jk_ctx *h, const Sliced &A, const Sliced &B, double *out, long long ldo, bool accumulate,
+                           long long *P, double *tmp, cudaStream_t st) {
+    const int ns = nsuper_of(A.K);
+    if (ns > 1) {
+        JK_TRY(ozgemm(h, A, B, nullptr, 0, P, st));
+        return reduce_partials(h, P, ns, A, B, out, ldo, accumulate, st);
+    }
+    if (!accumulate) return ozgemm(h, A, B, out, ldo, nullptr, st);
+    if (ldo != B.rows) return set_error(h, JK_ERR_ARG, "internal: accumulate needs packed output");
+    JK_TRY(ozgemm(h, A, B, tmp, B.rows, nullptr, st));
+    return fp64_axpy(h, out, tmp, static_cast<long long>(A.rows) * B.rows, st);
+}
+
+// Aux-index chunk of the split adjoint so that its workspace stays near 8 GB.
+static int split_adj_pchunk(const Problem &pb) {
+    const size_t n = pb.n, ctot = pb.ctot, ks3 = 3 * static_cast<size_t>(pb.ksum);
+    size_t per = n * n * 12 * 2                  // L slices: panel layout and row-mu layout
+                 + n * even_ld(ctot) * 8         // T
+                 + 2 * pb.kmax * n * 12          // T_X, T_Y as B operands
+                 + 2 * n * pb.kmax * 8 + pb.kmax * n * 12 * 2   // U, Vp and their slices
+                 + n * ks3 * (8 + 12)            // AG and its slices
+                 + n * n * 8 * 2;                // G, GV
+    size_t budget = static_cast<size_t>(8) << 30;
+    size_t pc = per ? budget / per : 1;
+    if (pc < 1) pc = 1;
+    if (pc > static_cast<size_t>(pb.naux)) pc = pb.naux;
+    size_t maxrows = static_cast<size_t>(65535) * oz::BM;
+    if (pc * n > maxrows) pc = maxrows / n;
+    return static_cast<int>(pc);
+}
+
+struct AdjBufs {
+    double *Z, *T, *gam, *cps, *JV, *U, *Vp, *AG, *BG, *G, *GV, *tmp;
+    long long *P;
+    Sliced Zs, Ls, Lm, Ws[kMaxDens], WTs[kMaxDens], TXb, TYb, Ub, Vpb, AGs, BGs, Gam, Vs, JVs, Xt, Yt;
+};
+
+static size_t adj_partials(const Problem &pb, int pc) {
+    const size_t n = pb.n;
+    size_t m = 0;
+    // dX / dY over K = pc*n, and the panel when n > SUPER
+    m = std::max<size_t>(m, static_cast<size_t>(nsuper_of(pc * pb.n)) * part_rows(n) * even_ld(pb.kmax));
+    if (pb.n > oz::SUPER)
+        m = std::max<size_t>(m, static_cast<size_t>(nsuper_of(pb.n)) * part_rows(static_cast<long long>(pc) * n) *
+                                    even_ld(pb.ctot));
+    return m ? m : 1;
+}
+
+static bool adj_take(Arena &ar, const Problem &pb, int pc, bool W, bool V, bool dl, AdjBufs &b) {
+    const int n = pb.n, nd = pb.nd, kmax = pb.kmax, ks3 = 3 * pb.ksum;
+    const long long n2 = static_cast<long long>(n) * n;
+    bool ok = true;
+    auto tk = [&](auto *&ptr, size_t cnt) {
+        using T = std::remove_reference_t<decltype(*ptr)>;
+        ptr = ar.take<T>(cnt ? cnt : 1);
+        ok = ok && ptr;
+    };
+    tk(b.Z, static_cast<size_t>(n) * pb.ctot);
+    tk(b.T, static_cast<size_t>(pc) * n * even_ld(pb.ctot));
+    tk(b.gam, static_cast<size_t>(nd) * pb.naux);
+    tk(b.cps, static_cast<size_t>(nd) * pb.naux);
+    tk(b.JV, V ? static_cast<size_t>(nd) * n2 : 1);
+    tk(b.U, static_cast<size_t>(n) * pc * kmax);
+    tk(b.Vp, static_cast<size_t>(n) * pc * kmax);
+    tk(b.AG, dl ? static_cast<size_t>(pc) * n * ks3 : 1);
+    tk(b.BG, dl ? static_cast<size_t>(n) * ks3 : 1);
+    tk(b.G, dl ? static_cast<size_t>(pc) * n2 : 1);
+    tk(b.GV, dl && V ? static_cast<size_t>(pc) * n2 : 1);
+    tk(b.tmp, static_cast<size_t>(n) * std::max(kmax, 1));
+    tk(b.P, adj_partials(pb, pc));
+    ok = ok && take_sliced(ar, pb.ctot, n, 1, b.Zs) && take_sliced(ar, pc * n, n, n, b.Ls) &&
+         take_sliced(ar, n, pc * n, 1, b.Lm);
+    for (int s = 0; ok && W && s < nd; s++)
+        ok = take_sliced(ar, n, n, 1, b.Ws[s]) && take_sliced(ar, n, n, 1, b.WTs[s]);
+    ok = ok && take_sliced(ar, pc * kmax, n, 1, b.TXb) && take_sliced(ar, pc * kmax, n, 1, b.TYb) &&
+         take_sliced(ar, kmax, pc * n, 1, b.Ub) && take_sliced(ar, kmax, pc * n, 1, b.Vpb);
+    if (ok && dl) ok = take_sliced(ar, pc * n, ks3, 1, b.AGs) && take_sliced(ar, n, ks3, 1, b.BGs);
+    if (ok && dl && V) ok = take_sliced(ar, pc, nd, 1, b.Gam) && take_sliced(ar, static_cast<int>(n2), nd, 1, b.Vs);
+    if (ok && V) ok = take_sliced(ar, static_cast<int>(n2 / n) * nd, n, 1, b.JVs) &&
+                      take_sliced(ar, kmax, n, 1, b.Xt) && take_sliced(ar, kmax, n, 1, b.Yt);
+    return ok;
+}
+
+size_t split_adjoint_workspace(const Problem &pb, bool want_dl) {
+    // Measure with a dry-run arena (no device memory touched).
+    Arena ar;
+    ar.base = reinterpret_cast<char *>(static_cast<uintptr_t>(1) << 40);
+    ar.bytes = static_cast<size_t>(1) << 62;
+    ar.reset(0);
+    AdjBufs b;
+    adj_take(ar, pb, split_adj_pchunk(pb), true, true, want_dl, b);
+    return ar.high + 4096;
+}
+
+jk_status split_pack_z(jk_ctx *h, const Problem &pb, double *Z, cudaStream_t st);
+
+jk_status split_adjoint(jk_ctx *h, const Problem &pb, const double *W, const double *V, double *dX, double *dY,
+                        double *dL, cudaStream_t st) {
+    const int n = pb.n, naux = pb.naux, nd = pb.nd;
+    const long long n2 = static_cast<long long>(n) * n;
+    const int pc = split_adj_pchunk(pb);
+    const bool wantW = W != nullptr, wantV = V != nullptr, wantL = dL != nullptr;
+    AdjBufs b;
+    if (!adj_take(h->arena, pb, pc, wantW, wantV, wantL, b))
+        return set_error(h, JK_ERR_OOM, "workspace too small for the split adjoint");
+    const long long ldT = even_ld(pb.ctot);
+    const int ks3 = 3 * pb.ksum;
+
+    long long boff[kMaxDens + 1];
+    boff[0] = 0;
+    for (int s = 0; s < nd; s++) boff[s + 1] = boff[s] + static_cast<long long>(n) * pb.k[s];
+    JK_CUDA_TRY(h, cudaMemsetAsync(dX, 0, boff[nd] * sizeof(double), st));
+    JK_CUDA_TRY(h, cudaMemsetAsync(dY, 0, boff[nd] * sizeof(double), st));
+
+    JK_TRY(split_pack_z(h, pb, b.Z, st));
+    oz::Src zsrc{b.Z, 1, 0, pb.ctot, n};
+    JK_TRY(slice_operand(h, zsrc, pb.ctot, n, 1, b.Zs, st));
+    if (wantV) {
+        // c_{P,s} = <V_s, L^P> and J(V_s) = sum_P c_{P,s} L^P in FP64
+        JK_TRY(fp64_frob_all(h, pb.L, n, naux, V, nd, b.cps, st));
+        JK_TRY(fp64_jstream_dense(h, pb.L, n, naux, b.cps, nd, b.JV, st));
+    }
+    if (wantW) {
+        for (int s = 0; s < nd; s++) {
+            const double *Wsd = W + s * n2;
+            oz::Src ws{Wsd, n, 0, 1, n};          // rows mu, K = lam: W[mu][lam]
+            oz::Src wt{Wsd, 1, 0, n, n};          // rows mu, K = lam: W[lam][mu]
+            JK_TRY(slice_operand(h, ws, n, n, 1, b.Ws[s], st));
+            JK_TRY(slice_operand(h, wt, n, n, 1, b.WTs[s], st));
+        }
+    }
+    if (wantL) {
+        int off = 0;
+        for (int s = 0; s < nd; s++) {
+            const int k = pb.k[s];
+            const double *Ys = pb.sym[s] ? pb.X[s] : pb.Y[s];
+            {
+                LaunchScope ls(h, KK_PACK, st);
+                pack_bg_kernel<<<static_cast<unsigned>((static_cast<long long>(n) * k + 255) / 256), 256, 0, st>>>(
+                    b.BG, ks3, off, pb.X[s], Ys, n, k);
+            }
+            JK_LAUNCH_CHECK(h);
+            off += 3 * k;
+        }
+        oz::Src bgs{b.BG, ks3, 0, 1, ks3};
+        JK_TRY(slice_operand(h, bgs, n, ks3, 1, b.BGs, st));
+        if (wantV) {
+            oz::Src vsrc{V, 1, 0, n2, nd};        // rows (mu nu), K = s: V[s][mu nu]
+            JK_TRY(slice_operand(h, vsrc, static_cast<int>(n2), nd, 1, b.Vs, st));
+        }
+    }
+
+    for (int P0 = 0; P0 < naux; P0 += pc) {
+        const int np = naux - P0 < pc ? naux - P0 : pc;
+        // Panels T^p = L^p Z (the half-transforms), as in the build
+        oz::Src lsrc{pb.L + P0 * n2, n, 0, 1, n};
+        JK_TRY(slice_operand(h, lsrc, np * n, n, n, b.Ls, st));
+        if (n > oz::SUPER) {
+            JK_TRY(ozgemm(h, b.Ls, b.Zs, nullptr, 0, b.P, st));
+            JK_TRY(reduce_partials(h, b.P, nsuper_of(n), b.Ls, b.Zs, b.T, ldT, false, st));
+        } else {
+            JK_TRY(ozgemm(h, b.Ls, b.Zs, b.T, ldT, nullptr, st));
+        }
+        if (wantV && wantL) JK_TRY(fp64_gamma_panel(h, pb, b.T, ldT, np, b.gam, P0, st));
+        if (wantW) {
+            // L with rows mu and reduction over (p, lam), for dX and dY
+            oz::Src lm{pb.L + P0 * n2, n, n2, 1, n};
+            JK_TRY(slice_operand(h, lm, n, np * n, 1, b.Lm, st));
+        }
+        for (int s = 0; s < nd; s++) {
+            const int k = pb.k[s];
+            const long long npk = static_cast<long long>(np) * k;
+            if (wantW) {
+                // U_s = W_s T_Y^T, Vp_s = W_s^T T_X^T: rows mu, columns (p, i)
+                oz::Src ty{b.T + pb.offY[s], static_cast<long long>(n) * ldT, 0, ldT, n, k, 1};
+                oz::Src tx{b.T + pb.offX[s], static_cast<long long>(n) * ldT, 0, ldT, n, k, 1};
+                JK_TRY(slice_operand(h, ty, static_cast<int>(npk), n, 1, b.TYb, st));
+                JK_TRY(slice_operand(h, tx, static_cast<int>(npk), n, 1, b.TXb, st));
+                JK_TRY(ozgemm(h, b.Ws[s], b.TYb, b.U, npk, nullptr, st));
+                JK_TRY(ozgemm(h, b.WTs[s], b.TXb, b.Vp, npk, nullptr, st));
+                // dX_s += sum_{p,lam} L^p[mu][lam] U[lam][(p,i)] ; dY_s likewise with Vp
+                oz::Src us{b.U, 1, k, npk, n};
+                oz::Src vs{b.Vp, 1, k, npk, n};
+                JK_TRY(slice_operand(h, us, k, np * n, 1, b.Ub, st));
+                JK_TRY(slice_operand(h, vs, k, np * n, 1, b.Vpb, st));
+                JK_TRY(gemm_into(h, b.Lm, b.Ub, dX + boff[s], k, P0 > 0, b.P, b.tmp, st));
+                JK_TRY(gemm_into(h, b.Lm, b.Vpb, dY + boff[s], k, P0 > 0, b.P, b.tmp, st));
+            }
+            if (wantL) {
+                int off = 0;
+                for (int t = 0; t < s; t++) off += 3 * pb.k[t];
+                {
+                    LaunchScope ls(h, KK_PACK, st);
+                    pack_ag_kernel<<<static_cast<unsigned>((static_cast<long long>(np) * n * k + 255) / 256), 256, 0,
+                                     st>>>(b.AG, ks3, off, wantW ? b.U : nullptr, wantW ? b.Vp : nullptr, pb.X[s],
+                                           wantV ? b.cps + static_cast<long long>(s) * naux : nullptr, P0, n, k, np);
+                }
+                JK_LAUNCH_CHECK(h);
+            }
+        }
+        if (wantL) {
+            // G[(p,mu)][nu] = sum_s U X^T + Vp Y^T + c X Y^T  (sym(Vp Y^T) = sym(Y Vp^T))
+            oz::Src ags{b.AG, ks3, 0, 1, ks3};
+            JK_TRY(slice_operand(h, ags, np * n, ks3, 1, b.AGs, st));
+            JK_TRY(ozgemm(h, b.AGs, b.BGs, b.G, n, nullptr, st));
+            const double *GV = nullptr;
+            if (wantV) {
+                // GV[p][(mu nu)] = sum_s gamma_{P0+p,s} V_s[mu nu]
+                oz::Src gsrc{b.gam + P0, 1, 0, naux, nd};
+                JK_TRY(slice_operand(h, gsrc, np, nd, 1, b.Gam, st));
+                JK_TRY(ozgemm(h, b.Gam, b.Vs, b.GV, n2, nullptr, st));
+                GV = b.GV;
+            }
+            {
+                LaunchScope ls(h, KK_MISC, st);
+                sym_dl_kernel<<<dim3(static_cast<unsigned>((n2 + 255) / 256), np), 256, 0, st>>>(b.G, GV, n,
+                                                                                                 dL + P0 * n2);
+            }
+            JK_LAUNCH_CHECK(h);
+        }
+    }
+    if (wantV) {
+        // dX_s += J(V_s) Y_s, dY_s += J(V_s) X_s
+        for (int s = 0; s < nd; s++) {
+            const int k = pb.k[s];
+            const double *Ys = pb.sym[s] ? pb.X[s] : pb.Y[s];
+            oz::Src jv{b.JV + s * n2, n, 0, 1, n};
+            Sliced Jvs = b.JVs;
+            JK_TRY(slice_operand(h, jv, n, n, 1, Jvs, st));
+            oz::Src yt{Ys, 1, 0, k, n};
+            oz::Src xt{pb.X[s], 1, 0, k, n};
+            JK_TRY(slice_operand(h, yt, k, n, 1, b.Yt, st));
+            JK_TRY(slice_operand(h, xt, k, n, 1, b.Xt, st));
+            JK_TRY(gemm_into(h, Jvs, b.Yt, dX + boff[s], k, true, b.P, b.tmp, st));
+            JK_TRY(gemm_into(h, Jvs, b.Xt, dY + boff[s], k, true, b.P, b.tmp, st));
+        }
+    }
+    for (int s = 0; s < nd; s++) {
+        if (!pb.sym[s]) continue;
+        const long long cnt = boff[s + 1] - boff[s];
+        LaunchScope ls(h, KK_MISC, st);
+        fold_sym_split_kernel<<<static_cast<unsigned>((cnt + 255) / 256), 256, 0, st>>>(dX + boff[s], dY + boff[s], cnt);
+        JK_LAUNCH_CHECK(h);
+    }
+    return JK_OK;
 }
 
 }  // namespace jk

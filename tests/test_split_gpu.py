@@ -131,3 +131,65 @@ def test_split_build_deterministic(eng):
     J1, K1 = eng.build(L, X, Y, m.sym, "split")
     J2, K2 = eng.build(L, X, Y, m.sym, "split")
     assert torch.equal(J1, J2) and torch.equal(K1, K2)
+
+
+# ------------------------------------------------------------------ adjoint
+
+@pytest.mark.parametrize("n,naux,ks,sym", [
+    (9, 6, [2, 3], [False, False]),
+    (33, 41, [4, 5], [True, False]),
+    (70, 150, [8, 16, 3], [False, False, True]),
+])
+def test_split_adjoint_vs_oracle(eng, n, naux, ks, sym):
+    m = inputs.custom(n, naux, max(naux / 5, 1.0), ks, sym)
+    rng = np.random.default_rng(3)
+    W = [rng.standard_normal((n, n)) for _ in ks]
+    V = [rng.standard_normal((n, n)) for _ in ks]
+    dXo, dYo, dLo = oracle.adjoint(m.L, m.X, m.Y, W, V)
+    L, X, Y = _gpu(m)
+    dX, dY, dL = eng.adjoint(L, X, Y, m.sym, torch.tensor(np.array(W)).cuda(),
+                             torch.tensor(np.array(V)).cuda(), precision="split")
+    eng.sync_status()
+    assert abs_err(to_np(dL), dLo) < SPLIT_ABS
+    for s in range(len(ks)):
+        if sym[s]:
+            assert abs_err(to_np(dX[s]), dXo[s] + dYo[s]) < SPLIT_ABS
+            assert np.all(to_np(dY[s]) == 0)
+        else:
+            assert abs_err(to_np(dX[s]), dXo[s]) < SPLIT_ABS
+            assert abs_err(to_np(dY[s]), dYo[s]) < SPLIT_ABS
+
+
+def test_split_adjoint_partial_seeds(eng):
+    n = 21
+    m = inputs.custom(n, 13, 5.0, [3], [False])
+    rng = np.random.default_rng(4)
+    W = [rng.standard_normal((n, n))]
+    L, X, Y = _gpu(m)
+    Wt = torch.tensor(np.array(W)).cuda()
+    dXo, dYo, dLo = oracle.adjoint(m.L, m.X, m.Y, W, None)
+    dX, dY, dL = eng.adjoint(L, X, Y, m.sym, Wt, None, precision="split")
+    assert abs_err(to_np(dX[0]), dXo[0]) < SPLIT_ABS and abs_err(to_np(dL), dLo) < SPLIT_ABS
+    dXo, dYo, dLo = oracle.adjoint(m.L, m.X, m.Y, None, W)
+    dX, dY, dL = eng.adjoint(L, X, Y, m.sym, None, Wt, precision="split")
+    assert abs_err(to_np(dY[0]), dYo[0]) < SPLIT_ABS and abs_err(to_np(dL), dLo) < SPLIT_ABS
+    dX, dY, dL = eng.adjoint(L, X, Y, m.sym, Wt, Wt, want_dl=False, precision="split")
+    assert dL is None
+
+
+def test_split_autograd_matches_fp64(eng):
+    from paper_2608_06536_b300.autograd import jk as jk_fn
+    n, naux = 40, 60
+    m = inputs.custom(n, naux, 12.0, [5, 4], [False, True])
+    rng = np.random.default_rng(6)
+    Wn = rng.standard_normal((2, n, n)); Vn = rng.standard_normal((2, n, n))
+    grads = {}
+    for prec in ("fp64", "split"):
+        L = torch.tensor(m.L, device="cuda", requires_grad=True)
+        X = [torch.tensor(x, device="cuda", requires_grad=True) for x in m.X]
+        Y = [torch.tensor(m.Y[0], device="cuda", requires_grad=True), None]
+        J, K = jk_fn(L, X, Y, precision=prec, engine=eng)
+        E = (torch.tensor(Wn, device="cuda") * K).sum() + (torch.tensor(Vn, device="cuda") * J).sum()
+        grads[prec] = [to_np(g) for g in torch.autograd.grad(E, [L, X[0], X[1], Y[0]])]
+    for a, b in zip(grads["fp64"], grads["split"]):
+        assert abs_err(b, a) < SPLIT_ABS
