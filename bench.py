@@ -51,6 +51,16 @@ def build_flops(n, naux, ks, sym):
     return f
 
 
+# DRAM bytes of the sliced GEMM measured by ncu (dram__bytes_read.sum +
+# dram__bytes_write.sum) on the profile case (nbf=400, naux=600, 8 densities
+# k=40; summary in profiles/ozgemm_tcgen05_profile_case.md): the panel launch
+# moved 2.289 GB for 600 aux indices and the rank update of one density set
+# 0.126 GB per operand for 600 aux indices.  Both grow in proportion to naux,
+# which is how they are scaled to the full multi-state launches.
+OZ_PANEL_BYTES_PER_P = 2.289e9 / 600
+OZ_RANK_BYTES_PER_P_OPERAND = 0.126e9 / 600
+
+
 def panel_rank_flops(n, naux, ks, sym):
     return sum((3.0 if s else 6.0) * n * n * k * naux for k, s in zip(ks, sym))
 
@@ -146,26 +156,31 @@ def max_over_ranks(x, world, device):
     return float(t.item())
 
 
-def cpu_baseline_sample(max_seconds=20.0):
-    """The oracle as it stands on a bounded sample of the workload: one
-    non-symmetric density (k=40) over the first `na` aux indices."""
-    import numpy as np
+_CPU_SAMPLE = {}
+
+
+def cpu_baseline_sample(L=None):
+    """The oracle as it stands on a bounded sample of the workload: three of
+    the seven non-symmetric densities (k=40) over all 2400 aux indices."""
     import oracle
     from paper_2608_06536_b300 import inputs
-    n, tau = 400, 400.0
-    X, Y = inputs.transition_density(n, 40, 1, 0)
-    na = 2400
-    L = inputs.factor(n, na, tau, 0)
-    oracle.build(L[:2], [X], [Y])   # load + warm
+    n, tau, na, nds = 400, 400.0, 2400, 3
+    if "L" not in _CPU_SAMPLE:
+        _CPU_SAMPLE["L"] = L if L is not None else inputs.factor(n, na, tau, 0)
+        _CPU_SAMPLE["XY"] = [inputs.transition_density(n, 40, s, 0) for s in range(1, 1 + nds)]
+    L = _CPU_SAMPLE["L"]
+    X = [xy[0] for xy in _CPU_SAMPLE["XY"]]
+    Y = [xy[1] for xy in _CPU_SAMPLE["XY"]]
+    oracle.build(L[:2], X[:1], Y[:1])   # load + warm
     t0 = time.perf_counter()
-    oracle.build(L, [X], [Y])
+    oracle.build(L, X, Y)
     dt = time.perf_counter() - t0
-    flops = build_flops(n, na, [40], [False])
+    flops = build_flops(n, na, [40] * nds, [False] * nds)
     cores = len(os.sched_getaffinity(0))
     omp = os.environ.get("OMP_NUM_THREADS")
     return {"value": flops / dt / 1e12, "unit": "TFLOP/s", "cores": int(omp) if omp else cores,
             "kind": "oracle",
-            "sample": f"1 non-symmetric density (k=40) x first {na} of 2400 aux indices, nbf=400; "
+            "sample": f"{nds} of the 7 non-symmetric densities (k=40) x all {na} aux indices, nbf=400; "
                       f"{flops:.3g} algorithmic flop in {dt:.2f} s",
             "seconds": dt}
 
@@ -295,6 +310,11 @@ def run_ours(args, rank, world, local):
                     "share_of_step": top_ms / (ms * args.steps)}
     elif top_name == "ozgemm_tcgen05" and top_cnt:
         pk = peaks.get("bf16_tflops_sustained")
+        traffic = None
+        if args.case == "multi_state":
+            operands = sum(1 if s_ else 2 for s_ in sym)
+            per_step = OZ_PANEL_BYTES_PER_P * naux + OZ_RANK_BYTES_PER_P_OPERAND * naux * operands
+            traffic = per_step * args.steps / top_cnt
         achieved = issued / (top_ms * 1e-3) / 1e12 if issued else None
         alg = panel_rank_flops(n, naux, ks, sym) * args.steps
         roofline = {"kernel": top_name, "bound": "tensor", "achieved": achieved, "peak": pk,
@@ -302,12 +322,14 @@ def run_ours(args, rank, world, local):
                     "peak_source": f"bf16_tflops_sustained of {peak_src} (MEASURED_PEAKS)",
                     "achieved_counts": "dense BF16 MMA flops issued (21 slice pairs over padded tiles)",
                     "algorithmic_fp64_equiv_tflops": alg / (top_ms * 1e-3) / 1e12,
-                    "traffic": None, "avg_launch_ms": top_ms / top_cnt,
+                    "traffic": traffic,
+                    "traffic_note": "DRAM bytes per launch, ncu capture of the profile case scaled by naux",
+                    "avg_launch_ms": top_ms / top_cnt,
                     "share_of_step": top_ms / (ms * args.steps)}
 
     if rank != 0:
         return
-    cpu = cpu_baseline_sample()
+    cpu = cpu_baseline_sample(m.L)
     line = {
         "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
