@@ -157,6 +157,13 @@ jk_status jk_adjoint(jk_handle h, const jk_factor *f, int32_t nd,
 jk_status jk_build_noalloc(const jk_factor *f, int32_t nd, const jk_density *d,
                            double *J, double *K, void *stream);
 
+/* Handle options.  JK_OPT_AUX_CHUNK: at most this many aux indices P per
+ * internal chunk (0 = automatic, chosen from the workspace budget).  Chunking
+ * over P is a pure memory knob (the paper's aux-index blocking, Table
+ * "precision", Sec. V.F): FP64 results change only by summation order. */
+typedef enum { JK_OPT_AUX_CHUNK = 0 } jk_option;
+jk_status jk_set_option(jk_handle h, jk_option opt, int64_t value);
+
 /* Wait for the stream and report any device-side error flag raised by this
  * handle's kernels (e.g. JK_ERR_TIMEOUT from a bounded wait); clears it. */
 jk_status jk_sync_status(jk_handle h, void *stream);

@@ -402,6 +402,7 @@ int fp64_default_pchunk(const Problem &pb) {
     pc = per ? pc / per : 1;
     if (pc < 1) pc = 1;
     if (pc > (size_t)pb.naux) pc = pb.naux;
+    if (pb.aux_chunk > 0 && pc > (size_t)pb.aux_chunk) pc = pb.aux_chunk;
     return (int)pc;
 }
 

@@ -85,6 +85,10 @@ static jk_status make_problem(jk_ctx *h, const jk_factor *f, int nd,
 
 static size_t flags_bytes() { return align_up(sizeof(DeviceFlags)); }
 
+static void apply_options(jk_ctx *h, Problem &pb) {
+    if (h) pb.aux_chunk = h->aux_chunk;
+}
+
 static jk_status check_out(jk_ctx *h, const void *p, const char *what) {
     if (!p) return JK_OK;
     if (!aligned16(p)) return set_error(h, JK_ERR_ARG, "%s is not 16-byte aligned", what);
@@ -157,15 +161,16 @@ jk_status jk_workspace_query(jk_op op, int32_t nmol, const jk_factor *f,
     if (op == JK_OP_BATCHED) {
         if (nmol < 1 || !nd_per_mol) return JK_ERR_SHAPE;
         int off = 0;
+        std::vector<Problem> pbs(nmol);
         for (int m = 0; m < nmol; m++) {
-            Problem pb;
-            jk_status s = make_problem(nullptr, &f[m], nd_per_mol[m], d + off, false, pb);
+            jk_status s = make_problem(nullptr, &f[m], nd_per_mol[m], d + off, false, pbs[m]);
             if (s != JK_OK) return s;
-            size_t b = build_bytes(pb, p);
+            size_t b = build_bytes(pbs[m], p);
             if (b > need) need = b;
             off += nd_per_mol[m];
         }
         if (off != nd) return JK_ERR_SHAPE;
+        if (p == JK_SPLIT_BF16) need = split_batched_workspace(nmol, pbs.data());
     } else if (op == JK_OP_BUILD || op == JK_OP_ADJOINT) {
         Problem pb;
         jk_status s = make_problem(nullptr, f, nd, d, false, pb);
@@ -185,6 +190,7 @@ jk_status jk_build(jk_handle h, const jk_factor *f, int32_t nd, const jk_density
         return set_error(h, JK_ERR_ARG, "unknown precision %d", (int)p);
     Problem pb;
     JK_TRY(make_problem(h, f, nd, d, true, pb));
+    apply_options(h, pb);
     JK_TRY(check_out(h, J, "J"));
     JK_TRY(check_out(h, K, "K"));
     if (!J && !K) return JK_OK;
@@ -218,6 +224,7 @@ jk_status jk_build_batched(jk_handle h, int32_t nmol, const jk_factor *f,
     for (int m = 0; m < nmol; m++) {
         Problem &pb = pbs[m];
         JK_TRY(make_problem(h, &f[m], nd_per_mol[m], d + off, true, pb));
+        apply_options(h, pb);
         pb.wantJ = J != nullptr;
         pb.wantK = K != nullptr;
         for (int s = 0; s < nd_per_mol[m]; s++) {
@@ -228,7 +235,7 @@ jk_status jk_build_batched(jk_handle h, int32_t nmol, const jk_factor *f,
             JK_TRY(check_out(h, pb.J[s], "J[i]"));
             JK_TRY(check_out(h, pb.K[s], "K[i]"));
         }
-        if (h->arena.bytes < flags_bytes() + build_bytes(pb, p))
+        if (p == JK_FP64 && h->arena.bytes < flags_bytes() + build_bytes(pb, p))
             return set_error(h, JK_ERR_OOM, "arena too small for molecule %d", m);
         off += nd_per_mol[m];
     }
@@ -244,6 +251,7 @@ jk_status jk_adjoint(jk_handle h, const jk_factor *f, int32_t nd, const jk_densi
         return set_error(h, JK_ERR_ARG, "unknown precision %d", (int)p);
     Problem pb;
     JK_TRY(make_problem(h, f, nd, d, true, pb));
+    apply_options(h, pb);
     if (!dX || !dY) return set_error(h, JK_ERR_ARG, "dX and dY are required");
     JK_TRY(check_out(h, dX, "dX"));
     JK_TRY(check_out(h, dY, "dY"));
@@ -257,6 +265,16 @@ jk_status jk_adjoint(jk_handle h, const jk_factor *f, int32_t nd, const jk_densi
                          h->arena.bytes, need);
     return p == JK_FP64 ? fp64_adjoint(h, pb, W, V, dX, dY, dL, st)
                         : split_adjoint(h, pb, W, V, dX, dY, dL, st);
+}
+
+jk_status jk_set_option(jk_handle h, jk_option opt, int64_t value) {
+    if (!h) return JK_ERR_ARG;
+    if (opt == JK_OPT_AUX_CHUNK) {
+        if (value < 0 || value > (1 << 30)) return set_error(h, JK_ERR_ARG, "aux chunk out of range");
+        h->aux_chunk = static_cast<int>(value);
+        return JK_OK;
+    }
+    return set_error(h, JK_ERR_ARG, "unknown option %d", (int)opt);
 }
 
 jk_status jk_sync_status(jk_handle h, void *stream) {

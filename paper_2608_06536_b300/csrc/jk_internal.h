@@ -66,6 +66,7 @@ struct jk_ctx {
     std::string last_error;
     int device = -1;
     int num_sms = 148;
+    int aux_chunk = 0;
     jk::Profiler prof;
 };
 
@@ -89,6 +90,7 @@ struct Problem {
     double *J[kMaxDens];
     double *K[kMaxDens];
     bool wantJ = false, wantK = false;
+    int aux_chunk = 0;   // at most this many aux indices per chunk (0 = automatic)
 };
 
 jk_status set_error(jk_ctx *h, jk_status s, const char *fmt, ...);
@@ -135,9 +137,15 @@ jk_status split_adjoint(jk_ctx *h, const Problem &pb, const double *W,
                         const double *V, double *dX, double *dY, double *dL,
                         cudaStream_t st);
 
+size_t split_batched_workspace(int nmol, const Problem *pbs);
+jk_status split_batched(jk_ctx *h, int nmol, const Problem *pbs, cudaStream_t st);
+
 // ---- batched builds (batched.cu) ------------------------------------------
 jk_status batched_build(jk_ctx *h, int nmol, const Problem *pbs, jk_precision p,
                         cudaStream_t st);
+
+size_t split_batched_workspace(int nmol, const Problem *pbs);
+jk_status split_batched(jk_ctx *h, int nmol, const Problem *pbs, cudaStream_t st);
 
 // ---- batched builds (batched.cu) ------------------------------------------
 jk_status batched_build(jk_ctx *h, int nmol, const Problem *pbs, jk_precision p,

@@ -37,6 +37,7 @@
 #include <algorithm>
 #include <cstring>
 #include <type_traits>
+#include <vector>
 
 #include "jk_internal.h"
 #include "tc.cuh"
@@ -364,6 +365,29 @@ __host__ __device__ constexpr int mma_d0(int i) { return mma_a(i) + mma_b0(i); }
 // Drain order at a tile end: the first MMAs of the next tile need 4, 5, then 3, 2, 1, 0.
 __host__ __device__ constexpr int drain_acc(int j) { return j == 0 ? 4 : j == 1 ? 5 : 3 - (j - 2); }
 
+// One GEMM of a launch.  A launch carries up to MAXG of them (uneven shapes
+// from many molecules and densities) in its parameter space, so a whole
+// batched build is a handful of persistent launches with no device-side
+// descriptor tables (and stays capturable in a CUDA graph).
+struct OzProb {
+    CUtensorMap tmA, tmB, tmC;
+    OzArgs a;
+    int tile0;          // first launch-wide tile index of this problem
+    int ntn, ntm;
+};
+constexpr int MAXG = 32;
+struct OzGroup {
+    OzProb p[MAXG];
+    int nprob;
+    int ntiles;
+};
+
+__device__ __forceinline__ int prob_of(const OzGroup &g, int t) {
+    int i = 0;
+    while (i + 1 < g.nprob && g.p[i + 1].tile0 <= t) ++i;
+    return i;
+}
+
 // Tile t of the launch: n-tile fastest (tiles sharing an A row block run side
 // by side and hit L2), then m-tile, then the split-K super-chunk z.
 struct TileCoord {
@@ -386,8 +410,7 @@ __device__ __forceinline__ TileCoord tile_of(int t, int ntn, int ntm, int K) {
 // the five TMEM accumulators after every 128-element window into int64
 // registers and write the finished tile while the next tile's MMAs run.
 __global__ void __launch_bounds__(THREADS, 1)
-ozgemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-              const __grid_constant__ CUtensorMap tmC, OzArgs a) {
+ozgemm_kernel(const __grid_constant__ OzGroup g) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint8_t *outbuf = smem + NSTAGE * STAGE_BYTES;
@@ -399,8 +422,7 @@ ozgemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int ntn = (a.N + BN - 1) / BN, ntm = (a.M + BM - 1) / BM;
-    const int ntiles = ntn * ntm * a.nsuper;
+    const int ntiles = g.ntiles;
 
     if (threadIdx.x == 0) {
         for (int i = 0; i < NSTAGE; i++) { tc::mbar_init(&full[i], 1); tc::mbar_init(&empty[i], 1); }
@@ -420,20 +442,26 @@ ozgemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
     if (warp == 0) {
         // ---------------- TMA producer ----------------
         if (lane == 0) {
-            tc::prefetch_tmap(&tmA);
-            tc::prefetch_tmap(&tmB);
+            int last = -1;
             int stage = 0;
             uint32_t phase = 0;
             bool ok = true;
             for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-                const TileCoord tc_ = tile_of(t, ntn, ntm, a.K);
+                const int pi = prob_of(g, t);
+                const OzProb &pr = g.p[pi];
+                if (pi != last) {
+                    tc::prefetch_tmap(&pr.tmA);
+                    tc::prefetch_tmap(&pr.tmB);
+                    last = pi;
+                }
+                const TileCoord tc_ = tile_of(t - pr.tile0, pr.ntn, pr.ntm, pr.a.K);
                 for (int kb = 0; kb < tc_.nkb; kb++) {
                     if (!tc::mbar_wait(&empty[stage], phase ^ 1u, abort_flag)) { ok = false; break; }
                     tc::mbar_expect_tx(&full[stage], STAGE_BYTES);
                     const int kc = tc_.kbeg + kb * KB;
                     uint8_t *sa = smem + stage * STAGE_BYTES;
-                    tc::tma_load_3d(sa, &tmA, &full[stage], kc, tc_.m * BM, 0);
-                    tc::tma_load_3d(sa + A_BYTES, &tmB, &full[stage], kc, tc_.n * BN, 0);
+                    tc::tma_load_3d(sa, &pr.tmA, &full[stage], kc, tc_.m * BM, 0);
+                    tc::tma_load_3d(sa + A_BYTES, &pr.tmB, &full[stage], kc, tc_.n * BN, 0);
                     if (++stage == NSTAGE) { stage = 0; phase ^= 1u; }
                 }
             }
@@ -446,7 +474,8 @@ ozgemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
             int wcnt[NACC] = {0, 0, 0, 0, 0, 0};   // windows started per accumulator
             bool ok = true;
             for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-                const TileCoord tc_ = tile_of(t, ntn, ntm, a.K);
+                const OzProb &pr = g.p[prob_of(g, t)];
+                const TileCoord tc_ = tile_of(t - pr.tile0, pr.ntn, pr.ntm, pr.a.K);
                 for (int kb0 = 0; kb0 < tc_.nkb && ok; kb0 += WPERIOD) {
                     // Unrolled over one window period: the window bookkeeping below is
                     // compile-time except for the tile's first and last K-block.
@@ -512,7 +541,9 @@ ozgemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
         int ecnt[NACC] = {0, 0, 0, 0, 0, 0};
         bool ok = true;
         for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-            const TileCoord tc_ = tile_of(t, ntn, ntm, a.K);
+            const OzProb &pr = g.p[prob_of(g, t)];
+            const OzArgs &a = pr.a;
+            const TileCoord tc_ = tile_of(t - pr.tile0, pr.ntn, pr.ntm, a.K);
             long long acc64[BN / 2];
 #pragma unroll
             for (int i = 0; i < BN / 2; i++) acc64[i] = 0;
@@ -596,7 +627,7 @@ ozgemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                         const int cc = c0 + b * OUT_BLK;
                         // rows of the partial for super-chunk z follow the M rows of z-1
                         const int rr = a.nsuper == 1 ? r0 : r0 + tc_.z * static_cast<int>(a.pz / a.ldp);
-                        if (cc < a.N) tc::tma_store_2d(&tmC, wbuf + b * (32 * OUT_BLK * 8), cc, rr);
+                        if (cc < a.N) tc::tma_store_2d(&pr.tmC, wbuf + b * (32 * OUT_BLK * 8), cc, rr);
                     }
                     tc::bulk_commit();
                 }
@@ -619,7 +650,7 @@ ozgemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                 }
             }
         }
-        if (a.use_tma_store && lane == 0) tc::bulk_wait_all();
+        if (lane == 0) tc::bulk_wait_all();
     }
     tc::fence_before_sync();
     __syncthreads();
@@ -627,7 +658,7 @@ ozgemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
         tc::fence_after_sync();
         tc::tmem_dealloc(tmem, 512);
     }
-    if (threadIdx.x == 0 && *abort_flag) atomicExch(a.err, static_cast<int>(JK_ERR_TIMEOUT));
+    if (threadIdx.x == 0 && *abort_flag) atomicExch(g.p[0].a.err, static_cast<int>(JK_ERR_TIMEOUT));
 }
 
 // out[r][c] (+)= sum_z P[z][r][c] 2^(eA[r/arpe][z] + eB[c/brpe][z] - 48).  The
@@ -782,22 +813,15 @@ static bool take_sliced(Arena &ar, int rows, int K, int rpe, Sliced &out) {
 
 static int nsuper_of(int K) { return (K + oz::SUPER - 1) / oz::SUPER; }
 
-static bool smem_configured = false;
-
-// C = A B^T on sliced operands.  nsuper == 1: FP64 written to C (ldc).
-// Otherwise int64 partials go to P (packed [M][N] per super-chunk).
-static jk_status ozgemm(jk_ctx *h, const Sliced &A, const Sliced &B, double *C, long long ldc, long long *P,
-                        cudaStream_t st) {
+// Fill one GEMM problem C = A B^T on sliced operands.  nsuper == 1: FP64 written
+// to C (row stride ldc); otherwise int64 partials go to P (padded row blocks).
+static jk_status oz_problem(jk_ctx *h, const Sliced &A, const Sliced &B, double *C, long long ldc, long long *P,
+                            oz::OzProb &pr) {
     if (A.K != B.K) return set_error(h, JK_ERR_ARG, "internal: sliced K mismatch");
-    if (!smem_configured) {
-        JK_CUDA_TRY(h, cudaFuncSetAttribute(oz::ozgemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            oz::SMEM_BYTES));
-        smem_configured = true;
-    }
-    CUtensorMap ta, tb;
-    JK_TRY(make_slice_map(h, &ta, A.s, A.rows, A.Kpad, oz::BM));
-    JK_TRY(make_slice_map(h, &tb, B.s, B.rows, B.Kpad, oz::BN));
-    oz::OzArgs a;
+    std::memset(&pr, 0, sizeof pr);
+    JK_TRY(make_slice_map(h, &pr.tmA, A.s, A.rows, A.Kpad, oz::BM));
+    JK_TRY(make_slice_map(h, &pr.tmB, B.s, B.rows, B.Kpad, oz::BN));
+    oz::OzArgs &a = pr.a;
     a.M = A.rows; a.N = B.rows; a.K = A.K; a.nsuper = nsuper_of(A.K);
     a.eA = A.e; a.a_rpe = A.rpe; a.eB = B.e; a.b_rpe = B.rpe;
     a.C = C; a.ldc = ldc; a.P = P;
@@ -805,34 +829,65 @@ static jk_status ozgemm(jk_ctx *h, const Sliced &A, const Sliced &B, double *C, 
     a.pz = part_rows(A.rows) * a.ldp;
     a.err = &h->flags->error;
     if (a.nsuper > 1 && !P) return set_error(h, JK_ERR_ARG, "internal: partial buffer missing");
-    CUtensorMap tcm;
-    std::memset(&tcm, 0, sizeof tcm);
     a.use_tma_store = 0;
     if (a.nsuper > 1) {
-        JK_TRY(make_out_map(h, &tcm, P, static_cast<long long>(a.nsuper) * part_rows(a.M), a.N, a.ldp));
+        JK_TRY(make_out_map(h, &pr.tmC, P, static_cast<long long>(a.nsuper) * part_rows(a.M), a.N, a.ldp));
         a.use_tma_store = 1;
     } else if ((ldc % 2) == 0 && (reinterpret_cast<uintptr_t>(C) & 15u) == 0) {
-        JK_TRY(make_out_map(h, &tcm, C, a.M, a.N, ldc));
+        JK_TRY(make_out_map(h, &pr.tmC, C, a.M, a.N, ldc));
         a.use_tma_store = 1;
     }
     const long long ntn = (a.N + oz::BN - 1) / oz::BN, ntm = (a.M + oz::BM - 1) / oz::BM;
-    const long long ntiles = ntn * ntm * a.nsuper;
-    if (ntiles > 0x7fffffffLL) return set_error(h, JK_ERR_SHAPE, "too many tiles (%lld)", ntiles);
-    const int grid = static_cast<int>(ntiles < h->num_sms ? ntiles : h->num_sms);
-    {
-        LaunchScope ls(h, KK_OZGEMM, st);
-        oz::ozgemm_kernel<<<grid, oz::THREADS, oz::SMEM_BYTES, st>>>(ta, tb, tcm, a);
-    }
-    // Issued MMA work: every CTA runs all 21 slice pairs over its K-blocks.
+    if (ntn * ntm * a.nsuper > 0x3fffffffLL) return set_error(h, JK_ERR_SHAPE, "too many tiles");
+    pr.ntn = static_cast<int>(ntn);
+    pr.ntm = static_cast<int>(ntm);
+    // Issued MMA work: every tile runs all 21 slice pairs over its K-blocks.
     double kblocks = 0.0;
     for (int zz = 0; zz < a.nsuper; zz++) {
         const int kb = (a.K - zz * oz::SUPER < oz::SUPER ? a.K - zz * oz::SUPER : oz::SUPER);
         kblocks += (kb + oz::KB - 1) / oz::KB;
     }
-    h->prof.tensor_flops += 2.0 * oz::BM * oz::BN * oz::KB * oz::NPAIRS * kblocks *
-                            static_cast<double>(ntn) * ntm;
-    JK_LAUNCH_CHECK(h);
+    h->prof.tensor_flops += 2.0 * oz::BM * oz::BN * oz::KB * oz::NPAIRS * kblocks * static_cast<double>(ntn) * ntm;
     return JK_OK;
+}
+
+static bool smem_configured = false;
+
+// Launch a list of problems: persistent grid, up to MAXG problems per launch.
+static jk_status oz_launch(jk_ctx *h, const std::vector<oz::OzProb> &probs, cudaStream_t st) {
+    if (!smem_configured) {
+        JK_CUDA_TRY(h, cudaFuncSetAttribute(oz::ozgemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            oz::SMEM_BYTES));
+        smem_configured = true;
+    }
+    static thread_local oz::OzGroup grp;   // 16 KB of launch parameters, built on the host
+    for (size_t i0 = 0; i0 < probs.size(); i0 += oz::MAXG) {
+        const int np = static_cast<int>(std::min<size_t>(oz::MAXG, probs.size() - i0));
+        long long tiles = 0;
+        for (int i = 0; i < np; i++) {
+            grp.p[i] = probs[i0 + i];
+            grp.p[i].tile0 = static_cast<int>(tiles);
+            tiles += static_cast<long long>(grp.p[i].ntn) * grp.p[i].ntm * grp.p[i].a.nsuper;
+        }
+        if (tiles > 0x7fffffffLL) return set_error(h, JK_ERR_SHAPE, "too many tiles in one launch");
+        grp.nprob = np;
+        grp.ntiles = static_cast<int>(tiles);
+        const int grid = static_cast<int>(tiles < h->num_sms ? tiles : h->num_sms);
+        {
+            LaunchScope ls(h, KK_OZGEMM, st);
+            oz::ozgemm_kernel<<<grid, oz::THREADS, oz::SMEM_BYTES, st>>>(grp);
+        }
+        JK_LAUNCH_CHECK(h);
+    }
+    return JK_OK;
+}
+
+// C = A B^T on sliced operands (one problem, one launch).
+static jk_status ozgemm(jk_ctx *h, const Sliced &A, const Sliced &B, double *C, long long ldc, long long *P,
+                        cudaStream_t st) {
+    std::vector<oz::OzProb> v(1);
+    JK_TRY(oz_problem(h, A, B, C, ldc, P, v[0]));
+    return oz_launch(h, v, st);
 }
 
 static jk_status reduce_partials(jk_ctx *h, const long long *P, int nz, const Sliced &A, const Sliced &B,
@@ -864,6 +919,7 @@ static int split_pchunk(const Problem &pb) {
     // Keep rows of the panel GEMM within the grid limit.
     size_t maxrows = static_cast<size_t>(65535) * oz::BM;
     if (pc * n > maxrows) pc = maxrows / n;
+    if (pb.aux_chunk > 0 && pc > static_cast<size_t>(pb.aux_chunk)) pc = pb.aux_chunk;
     return static_cast<int>(pc);
 }
 
@@ -1077,6 +1133,7 @@ static int split_adj_pchunk(const Problem &pb) {
     if (pc > static_cast<size_t>(pb.naux)) pc = pb.naux;
     size_t maxrows = static_cast<size_t>(65535) * oz::BM;
     if (pc * n > maxrows) pc = maxrows / n;
+    if (pb.aux_chunk > 0 && pc > static_cast<size_t>(pb.aux_chunk)) pc = pb.aux_chunk;
     return static_cast<int>(pc);
 }
 
@@ -1144,6 +1201,194 @@ size_t split_adjoint_workspace(const Problem &pb, bool want_dl) {
 }
 
 jk_status split_pack_z(jk_ctx *h, const Problem &pb, double *Z, cudaStream_t st);
+
+// ---------------------------------------------------------------------------
+// Batched split build: many molecules, grouped launches
+// ---------------------------------------------------------------------------
+namespace {
+
+struct MolBufs {
+    double *Z = nullptr, *gamma = nullptr;
+    Sliced Zs;
+    int pc = 0;
+};
+
+struct ItemBufs {
+    int mol = 0, P0 = 0, np = 0;
+    Sliced Ls, TX[kMaxDens], TY[kMaxDens];
+    double *T = nullptr, *tmp = nullptr;
+    long long *P = nullptr;
+};
+
+size_t item_bytes(const Problem &pb, int pc) {
+    const size_t n = pb.n;
+    size_t b = sliced_bytes(pc * pb.n, pb.n, pb.n) + align_up(static_cast<size_t>(pc) * n * even_ld(pb.ctot) * 8);
+    for (int s = 0; s < pb.nd; s++) {
+        b += sliced_bytes(pb.n, pc * pb.k[s], 1);
+        if (!pb.sym[s]) b += sliced_bytes(pb.n, pc * pb.k[s], 1);
+    }
+    b += align_up(partial_count(pb, pc) * 8 + 8);
+    b += align_up(static_cast<size_t>(pb.nd) * n * n * 8);   // per-density tmp for chunk accumulation
+    return b + 16 * kArenaAlign;
+}
+
+size_t mol_bytes(const Problem &pb) {
+    return align_up(static_cast<size_t>(pb.n) * pb.ctot * 8) + sliced_bytes(pb.ctot, pb.n, 1) +
+           align_up(static_cast<size_t>(pb.nd) * pb.naux * 8) + 4 * kArenaAlign;
+}
+
+bool take_item(Arena &ar, const Problem &pb, int pc, ItemBufs &it) {
+    const int n = pb.n;
+    bool ok = take_sliced(ar, pc * n, n, n, it.Ls);
+    it.T = ar.take<double>(static_cast<size_t>(pc) * n * even_ld(pb.ctot));
+    ok = ok && it.T;
+    for (int s = 0; ok && s < pb.nd; s++) {
+        ok = take_sliced(ar, n, pc * pb.k[s], 1, it.TX[s]);
+        if (ok && !pb.sym[s]) ok = take_sliced(ar, n, pc * pb.k[s], 1, it.TY[s]);
+    }
+    it.P = ar.take<long long>(partial_count(pb, pc) + 1);
+    it.tmp = ar.take<double>(static_cast<size_t>(pb.nd) * n * n);
+    return ok && it.P && it.tmp;
+}
+
+}  // namespace
+
+size_t split_batched_workspace(int nmol, const Problem *pbs) {
+    size_t mols = 0, maxitem = 0, items = 0;
+    for (int m = 0; m < nmol; m++) {
+        const Problem &pb = pbs[m];
+        mols += mol_bytes(pb);
+        const int pc = split_pchunk(pb);
+        const size_t ib = item_bytes(pb, pc);
+        maxitem = std::max(maxitem, ib);
+        items += ib * ((pb.naux + pc - 1) / pc);
+    }
+    // enough for every molecule's persistent buffers and at least the largest
+    // work item; more (up to everything, capped at 24 GB) lets waves hold more items
+    const size_t cap = static_cast<size_t>(24) << 30;
+    return mols + std::max(maxitem, std::min(items, cap));
+}
+
+jk_status split_batched(jk_ctx *h, int nmol, const Problem *pbs, cudaStream_t st) {
+    Arena &ar = h->arena;
+    std::vector<MolBufs> mb(nmol);
+    // Persistent per-molecule buffers: packed Z and its slices, gamma.
+    for (int m = 0; m < nmol; m++) {
+        const Problem &pb = pbs[m];
+        mb[m].Z = ar.take<double>(static_cast<size_t>(pb.n) * pb.ctot);
+        mb[m].gamma = ar.take<double>(static_cast<size_t>(pb.nd) * pb.naux);
+        if (!mb[m].Z || !mb[m].gamma || !take_sliced(ar, pb.ctot, pb.n, 1, mb[m].Zs))
+            return set_error(h, JK_ERR_OOM, "workspace too small for the batched build");
+        mb[m].pc = split_pchunk(pb);
+        JK_TRY(split_pack_z(h, pb, mb[m].Z, st));
+        oz::Src zsrc{mb[m].Z, 1, 0, pb.ctot, pb.n};
+        JK_TRY(slice_operand(h, zsrc, pb.ctot, pb.n, 1, mb[m].Zs, st));
+    }
+    const size_t persist = ar.off;
+    // Work items (molecule, aux chunk) in order.
+    std::vector<std::pair<int, int>> work;
+    for (int m = 0; m < nmol; m++)
+        for (int P0 = 0; P0 < pbs[m].naux; P0 += mb[m].pc) work.push_back({m, P0});
+    size_t w0 = 0;
+    while (w0 < work.size()) {
+        ar.reset(persist);
+        std::vector<ItemBufs> items;
+        std::vector<char> inwave(nmol, 0);
+        size_t w1 = w0;
+        while (w1 < work.size()) {
+            const int m = work[w1].first;
+            if (inwave[m]) break;                 // one chunk per molecule per wave
+            const Problem &pb = pbs[m];
+            const size_t save = ar.off;
+            ItemBufs it;
+            it.mol = m;
+            it.P0 = work[w1].second;
+            it.np = std::min(mb[m].pc, pb.naux - it.P0);
+            if (!take_item(ar, pb, mb[m].pc, it)) {
+                ar.off = save;
+                break;
+            }
+            items.push_back(it);
+            inwave[m] = 1;
+            ++w1;
+        }
+        if (items.empty()) return set_error(h, JK_ERR_OOM, "workspace too small for one batched work item");
+        // 1. slice the factor chunks
+        for (auto &it : items) {
+            const Problem &pb = pbs[it.mol];
+            const long long n2 = static_cast<long long>(pb.n) * pb.n;
+            oz::Src lsrc{pb.L + it.P0 * n2, pb.n, 0, 1, pb.n};
+            JK_TRY(slice_operand(h, lsrc, it.np * pb.n, pb.n, pb.n, it.Ls, st));
+        }
+        // 2. all panels of the wave: grouped persistent launches
+        std::vector<oz::OzProb> probs;
+        for (auto &it : items) {
+            const Problem &pb = pbs[it.mol];
+            probs.emplace_back();
+            if (pb.n > oz::SUPER) return set_error(h, JK_ERR_UNSUPPORTED, "batched build needs nbf <= 2048");
+            JK_TRY(oz_problem(h, it.Ls, mb[it.mol].Zs, it.T, even_ld(pb.ctot), nullptr, probs.back()));
+        }
+        JK_TRY(oz_launch(h, probs, st));
+        // 3. gamma and rank-update operands
+        for (auto &it : items) {
+            const Problem &pb = pbs[it.mol];
+            const long long ldT = even_ld(pb.ctot);
+            if (pb.wantJ) JK_TRY(fp64_gamma_panel(h, pb, it.T, ldT, it.np, mb[it.mol].gamma, it.P0, st));
+            if (!pb.wantK) continue;
+            for (int s = 0; s < pb.nd; s++) {
+                const int k = pb.k[s], Kr = it.np * k;
+                oz::Src xs{it.T + pb.offX[s], ldT, static_cast<long long>(pb.n) * ldT, 1, k};
+                JK_TRY(slice_operand(h, xs, pb.n, Kr, 1, it.TX[s], st));
+                if (!pb.sym[s]) {
+                    oz::Src ys{it.T + pb.offY[s], ldT, static_cast<long long>(pb.n) * ldT, 1, k};
+                    JK_TRY(slice_operand(h, ys, pb.n, Kr, 1, it.TY[s], st));
+                }
+            }
+        }
+        // 4. every rank update of the wave: grouped persistent launches
+        probs.clear();
+        struct Red { const ItemBufs *it; int s; long long *P; double *tmp; };
+        std::vector<Red> reds;
+        for (auto &it : items) {
+            const Problem &pb = pbs[it.mol];
+            if (!pb.wantK) continue;
+            const long long n2 = static_cast<long long>(pb.n) * pb.n;
+            long long *Pcur = it.P;
+            for (int s = 0; s < pb.nd; s++) {
+                const Sliced &B = pb.sym[s] ? it.TX[s] : it.TY[s];
+                const int ns = nsuper_of(it.np * pb.k[s]);
+                probs.emplace_back();
+                if (ns == 1) {
+                    double *out = it.P0 == 0 ? pb.K[s] : it.tmp + s * n2;
+                    JK_TRY(oz_problem(h, it.TX[s], B, out, pb.n, nullptr, probs.back()));
+                    if (it.P0 > 0) reds.push_back({&it, s, nullptr, it.tmp + s * n2});
+                } else {
+                    JK_TRY(oz_problem(h, it.TX[s], B, nullptr, 0, Pcur, probs.back()));
+                    reds.push_back({&it, s, Pcur, nullptr});
+                    Pcur += static_cast<size_t>(ns) * part_rows(pb.n) * even_ld(pb.n);
+                }
+            }
+        }
+        JK_TRY(oz_launch(h, probs, st));
+        // 5. reductions into K
+        for (auto &r : reds) {
+            const Problem &pb = pbs[r.it->mol];
+            const long long n2 = static_cast<long long>(pb.n) * pb.n;
+            const Sliced &B = pb.sym[r.s] ? r.it->TX[r.s] : r.it->TY[r.s];
+            if (r.P) {
+                JK_TRY(reduce_partials(h, r.P, nsuper_of(r.it->np * pb.k[r.s]), r.it->TX[r.s], B, pb.K[r.s], pb.n,
+                                       r.it->P0 > 0, st));
+            } else {
+                JK_TRY(fp64_axpy(h, pb.K[r.s], r.tmp, n2, st));
+            }
+        }
+        w0 = w1;
+    }
+    // J back-contraction per molecule (FP64)
+    for (int m = 0; m < nmol; m++)
+        if (pbs[m].wantJ) JK_TRY(fp64_jstream(h, pbs[m], mb[m].gamma, st));
+    return JK_OK;
+}
 
 jk_status split_adjoint(jk_ctx *h, const Problem &pb, const double *W, const double *V, double *dX, double *dY,
                         double *dL, cudaStream_t st) {

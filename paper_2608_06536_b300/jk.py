@@ -65,6 +65,8 @@ def load_library(path: str = LIB_PATH):
         L.jk_adjoint.argtypes = [vp, ct.POINTER(jk_factor), ct.c_int32, ct.POINTER(jk_density),
                                  vp, vp, vp, vp, vp, ct.c_int, vp]
         L.jk_sync_status.argtypes = [vp, vp]
+        L.jk_set_option.argtypes = [vp, ct.c_int, ct.c_int64]
+        L.jk_set_option.restype = ct.c_int
         L.jk_status_string.argtypes = [ct.c_int]
         L.jk_status_string.restype = ct.c_char_p
         L.jk_last_error.argtypes = [vp]
@@ -158,6 +160,8 @@ class Engine:
         self._h = h
         if getattr(self, "_profile_on", False):
             self.lib.jk_profile_enable(self._h, 1)
+        if getattr(self, "_aux_chunk", 0):
+            self.lib.jk_set_option(self._h, 0, self._aux_chunk)
 
     def close(self):
         if self._h:
@@ -184,6 +188,13 @@ class Engine:
 
     def sync_status(self, stream=None):
         self._check(self.lib.jk_sync_status(self._h, _stream_ptr(stream)), self._h)
+
+    # -- options ---------------------------------------------------------------
+    def set_aux_chunk(self, naux_per_chunk: int):
+        """At most this many aux indices per internal chunk (0 = automatic)."""
+        self._aux_chunk = int(naux_per_chunk)
+        if self._h:
+            self._check(self.lib.jk_set_option(self._h, 0, self._aux_chunk), self._h)
 
     # -- instrumentation -----------------------------------------------------
     def launch_count(self) -> int:
