@@ -541,9 +541,13 @@ ozgemm_kernel(const __grid_constant__ OzGroup g) {
         int ecnt[NACC] = {0, 0, 0, 0, 0, 0};
         bool ok = true;
         for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-            const OzProb &pr = g.p[prob_of(g, t)];
-            const OzArgs &a = pr.a;
-            const TileCoord tc_ = tile_of(t - pr.tile0, pr.ntn, pr.ntm, a.K);
+            // Copy the tile's problem out of parameter space once: the stores
+            // below go through generic pointers and would otherwise force a
+            // reload of every field per element.
+            const int pi = prob_of(g, t);
+            const OzArgs a = g.p[pi].a;
+            const CUtensorMap *tmC = &g.p[pi].tmC;
+            const TileCoord tc_ = tile_of(t - g.p[pi].tile0, g.p[pi].ntn, g.p[pi].ntm, a.K);
             long long acc64[BN / 2];
 #pragma unroll
             for (int i = 0; i < BN / 2; i++) acc64[i] = 0;
@@ -627,7 +631,7 @@ ozgemm_kernel(const __grid_constant__ OzGroup g) {
                         const int cc = c0 + b * OUT_BLK;
                         // rows of the partial for super-chunk z follow the M rows of z-1
                         const int rr = a.nsuper == 1 ? r0 : r0 + tc_.z * static_cast<int>(a.pz / a.ldp);
-                        if (cc < a.N) tc::tma_store_2d(&pr.tmC, wbuf + b * (32 * OUT_BLK * 8), cc, rr);
+                        if (cc < a.N) tc::tma_store_2d(tmC, wbuf + b * (32 * OUT_BLK * 8), cc, rr);
                     }
                     tc::bulk_commit();
                 }
