@@ -28,8 +28,11 @@
  *    jk_last_error(); nothing is launched in that case.
  *  - A handle must be used from one host thread and one stream at a time:
  *    successive calls reuse the same arena.
- *  - Pointers to double/float arrays must be 16-byte aligned
- *    (JK_ERR_ARG otherwise).
+ *  - Input arrays (L, X, Y, W, V) must be 16-byte aligned; output arrays
+ *    (J, K, dX, dY, dL) need only the natural 8-byte alignment of double
+ *    (JK_ERR_ARG otherwise).  Outputs that are 16-byte aligned with an even
+ *    row length take the bulk-store (TMA) path; others are written with
+ *    plain stores.
  *  - L^P is assumed symmetric in (mu, nu); this is not checked.
  */
 #ifndef JK_H
@@ -89,10 +92,16 @@ jk_status jk_destroy(jk_handle h);
 
 /* Bytes of arena a call with these shapes needs (host-only, no GPU work).
  * For JK_OP_BATCHED pass nmol factors and the concatenated densities, with
- * nd_per_mol giving the split; otherwise nmol = 1 and nd_per_mol may be NULL. */
+ * nd_per_mol giving the split; otherwise nmol = 1 and nd_per_mol may be NULL.
+ * Without a handle the answer covers both the default configuration and a
+ * tuned one cached for these shapes (see jk_autotune); the _handle form
+ * answers for the configuration that handle's options select. */
 jk_status jk_workspace_query(jk_op op, int32_t nmol, const jk_factor *f,
                              const int32_t *nd_per_mol, int32_t nd,
                              const jk_density *d, jk_precision p, size_t *bytes);
+jk_status jk_workspace_query_handle(jk_handle h, jk_op op, int32_t nmol, const jk_factor *f,
+                                    const int32_t *nd_per_mol, int32_t nd,
+                                    const jk_density *d, jk_precision p, size_t *bytes);
 
 /* jk_build: J_s and K_s for nd densities over one factor (Eq. 4, Sec. II.C).
  *   J, K : [nd][nbf][nbf] FP64 outputs; either may be NULL (not formed).
@@ -157,12 +166,64 @@ jk_status jk_adjoint(jk_handle h, const jk_factor *f, int32_t nd,
 jk_status jk_build_noalloc(const jk_factor *f, int32_t nd, const jk_density *d,
                            double *J, double *K, void *stream);
 
-/* Handle options.  JK_OPT_AUX_CHUNK: at most this many aux indices P per
- * internal chunk (0 = automatic, chosen from the workspace budget).  Chunking
+/* Handle options.  JK_OPT_AUX_CHUNK: this many aux indices P per internal
+ * chunk, the last one smaller (0 = automatic, chosen from a workspace budget;
+ * a larger chunk needs a larger workspace, see jk_workspace_query).  Chunking
  * over P is a pure memory knob (the paper's aux-index blocking, Table
  * "precision", Sec. V.F): FP64 results change only by summation order. */
-typedef enum { JK_OPT_AUX_CHUNK = 0 } jk_option;
+typedef enum {
+    JK_OPT_AUX_CHUNK = 0,   /* >= 0; 0 = automatic                                */
+    JK_OPT_SCHEDULE = 1,    /* -1 = tuned/default, 0 = per-density launches,
+                               1 = grouped persistent launches (split precision)  */
+    JK_OPT_RASTER = 2,      /* -1 = tuned/default, 0 = n-tile fastest,
+                               1 = m-tile fastest (tile order of the sliced GEMM) */
+    JK_OPT_USE_TUNED = 3    /* 1 (default) = apply autotuned configurations,
+                               0 = ignore them                                    */
+} jk_option;
+/* Options set explicitly on a handle override tuned configurations. */
 jk_status jk_set_option(jk_handle h, jk_option opt, int64_t value);
+
+/* ---------------------------------------------------------------------------
+ * Autotuner.  A configuration is the set of run-time choices a build makes
+ * (aux-index chunk, launch schedule, GEMM tile order).  jk_autotune times the
+ * candidate configurations of one problem with CUDA events on `stream` (it
+ * synchronizes the stream, so it must not be called during stream capture),
+ * keeps the fastest in a process-wide cache keyed by a shape bucket (op,
+ * precision, SM count, nbf, naux, densities, total width, molecules) and
+ * returns it.  Later jk_build / jk_build_batched calls whose shapes fall in a
+ * cached bucket use that configuration (unless the handle sets the option
+ * explicitly or JK_OPT_USE_TUNED is 0); jk_workspace_query accounts for it.
+ * Candidates that do not fit the handle's arena are skipped.  J and K are
+ * overwritten with the result of the last candidate run (all candidates agree
+ * to the precision's tolerance).  reps >= 1 timed builds per candidate.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+    int32_t aux_chunk;   /* aux indices per chunk, 0 = automatic */
+    int32_t schedule;    /* 0 per-density launches, 1 grouped persistent launches */
+    int32_t raster;      /* 0 n-tile fastest, 1 m-tile fastest */
+} jk_tune_config;
+
+jk_status jk_autotune(jk_handle h, const jk_factor *f, int32_t nd, const jk_density *d,
+                      double *J, double *K, jk_precision p, void *stream, int32_t reps,
+                      jk_tune_config *best, double *best_ms);
+jk_status jk_autotune_batched(jk_handle h, int32_t nmol, const jk_factor *f,
+                              const int32_t *nd_per_mol, const jk_density *d,
+                              double *const *J, double *const *K, jk_precision p,
+                              void *stream, int32_t reps, jk_tune_config *best,
+                              double *best_ms);
+/* Cached configuration for a problem's bucket (host only: pointers are not
+ * dereferenced or checked).  JK_OK if found, JK_ERR_UNSUPPORTED if not. */
+jk_status jk_tune_lookup(jk_op op, int32_t nmol, const jk_factor *f, const int32_t *nd_per_mol,
+                         int32_t nd, const jk_density *d, jk_precision p, int32_t num_sms,
+                         jk_tune_config *cfg);
+/* The cache as text, one entry per line, for saving between processes.
+ * export: writes at most cap bytes (NUL-terminated) and the full length
+ * (without the NUL) to *len; import merges lines (later entries win) and
+ * returns JK_ERR_ARG on a malformed line (entries before it are kept);
+ * clear empties the cache. */
+jk_status jk_tune_export(char *buf, size_t cap, size_t *len);
+jk_status jk_tune_import(const char *text);
+jk_status jk_tune_clear(void);
 
 /* Wait for the stream and report any device-side error flag raised by this
  * handle's kernels (e.g. JK_ERR_TIMEOUT from a bounded wait); clears it. */

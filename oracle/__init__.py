@@ -37,9 +37,12 @@ def lib():
                                  ct.c_int, ip, ip, ip, dp, dp]
         L.jko_adjoint.argtypes = [ct.c_int, ct.c_int, dp, ct.c_int, ip, dp, dp,
                                   dp, dp, dp, dp, dp]
+        L.jko_adjoint_sample.argtypes = [ct.c_int, ct.c_int, dp, ct.c_int, ip, dp, dp, dp, dp,
+                                         ct.c_int, ip, ip, ip, dp, dp, ct.c_int, ip, ip, ip, dp]
         L.jko_energy.argtypes = [ct.c_int, ct.c_int, dp, ct.c_int, ip, dp, dp,
                                  dp, dp, ct.POINTER(ct.c_longdouble)]
-        for f in (L.jko_brute, L.jko_build, L.jko_sample, L.jko_adjoint, L.jko_energy):
+        for f in (L.jko_brute, L.jko_build, L.jko_sample, L.jko_adjoint, L.jko_adjoint_sample,
+                  L.jko_energy):
             f.restype = ct.c_int
         _lib = L
     return _lib
@@ -123,6 +126,28 @@ def adjoint(L: np.ndarray, X: list, Y: list, W=None, V=None, want_dl=True):
         outY.append(dY[off:off + n * k].reshape(n, k))
         off += n * k
     return outX, outY, dL
+
+
+def adjoint_sample(L: np.ndarray, X: list, Y: list, W=None, V=None, xsamp=None, lsamp=None):
+    """O3 at single entries.  ``xsamp`` = (s, mu, i) index arrays for dX_s[mu,i]
+    and dY_s[mu,i]; ``lsamp`` = (P, mu, nu) for dL^P[mu,nu].  Returns
+    (dX values, dY values, dL values)."""
+    L = np.ascontiguousarray(L, np.float64)
+    naux, n, _ = L.shape
+    nd = len(X)
+    ks, kp = _i([x.shape[1] for x in X])
+    Xc, Yc = _cat(X), _cat(Y)
+    Wc = _cat(W) if W is not None else None
+    Vc = _cat(V) if V is not None else None
+    xs, xmu, xi = xsamp if xsamp is not None else ([], [], [])
+    lP, lmu, lnu = lsamp if lsamp is not None else ([], [], [])
+    (xa, xp), (ma, mp), (ia, ip_) = _i(xs), _i(xmu), _i(xi)
+    (pa, pp), (la, lp), (na, np_) = _i(lP), _i(lmu), _i(lnu)
+    dX = np.empty(max(xa.size, 1)); dY = np.empty(max(xa.size, 1)); dL = np.empty(max(pa.size, 1))
+    _check(lib().jko_adjoint_sample(n, naux, _d(L), nd, kp, _d(Xc), _d(Yc), _d(Wc), _d(Vc),
+                                    xa.size, xp, mp, ip_, _d(dX), _d(dY), pa.size, pp, lp, np_,
+                                    _d(dL)), "adjoint_sample")
+    return dX[:xa.size], dY[:xa.size], dL[:pa.size]
 
 
 def energy(L: np.ndarray, X: list, Y: list, W=None, V=None) -> float:

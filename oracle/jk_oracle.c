@@ -370,6 +370,162 @@ int jko_adjoint(int n, int naux, const double *L, int nd, const int *k,
     return 0;
 }
 
+/* ------------------------------------------------------------------------
+ * O3 sampled: the adjoint formulas above at single entries, for sizes where
+ * the full adjoint is too slow on the host.
+ *   dX_s[mu][i] = sum_P (L^P W_s L^P Y_s)[mu][i] + (J(V_s) Y_s)[mu][i]
+ *   dY_s[mu][i] = sum_P (L^P W_s^T L^P X_s)[mu][i] + (J(V_s) X_s)[mu][i]
+ *   dL^P[mu][nu] = (G^P[mu][nu] + G^P[nu][mu]) / 2, G^P as in O3.
+ * Each dX/dY entry is evaluated right to left (a column of L^P Y_s, then
+ * W_s times it, then row mu of L^P); each dL entry forms the panels of its P.
+ * W or V may be NULL (zero).  Samples: (xs, xmu, xi) for dX and dY, and
+ * (lP, lmu, lnu) for dL; either list may be empty.
+ * ---------------------------------------------------------------------- */
+int jko_adjoint_sample(int n, int naux, const double *L, int nd, const int *k,
+                       const double *X, const double *Y, const double *W,
+                       const double *V, int nx, const int *xs, const int *xmu,
+                       const int *xi, double *dXout, double *dYout, int nl,
+                       const int *lP, const int *lmu, const int *lnu,
+                       double *dLout)
+{
+    if (n < 1 || naux < 0 || nd < 0 || nx < 0 || nl < 0) return 1;
+    size_t n2 = (size_t)n * n;
+    size_t *offs = (size_t *)malloc((nd + 1) * sizeof(size_t));
+    ld *c = (ld *)calloc((size_t)(nd ? nd : 1) * (naux ? naux : 1), sizeof(ld));
+    int *needc = (int *)calloc(nd ? nd : 1, sizeof(int));
+    if (!offs || !c || !needc) { free(offs); free(c); free(needc); return 2; }
+    offs[0] = 0;
+    for (int s = 0; s < nd; s++) {
+        if (k[s] < 1) { free(offs); free(c); free(needc); return 1; }
+        offs[s + 1] = offs[s] + (size_t)n * k[s];
+    }
+    for (int q = 0; q < nx; q++)
+        if (xs[q] < 0 || xs[q] >= nd || xmu[q] < 0 || xmu[q] >= n || xi[q] < 0 || xi[q] >= k[xs[q]]) {
+            free(offs); free(c); free(needc); return 1;
+        }
+    for (int q = 0; q < nl; q++)
+        if (lP[q] < 0 || lP[q] >= naux || lmu[q] < 0 || lmu[q] >= n || lnu[q] < 0 || lnu[q] >= n) {
+            free(offs); free(c); free(needc); return 1;
+        }
+    /* c_{P,s} = <V_s, L^P> for the densities the dX/dY samples touch */
+    if (V) {
+        for (int q = 0; q < nx; q++) needc[xs[q]] = 1;
+        for (int s = 0; s < nd; s++) {
+            if (!needc[s]) continue;
+            #pragma omp parallel for schedule(static)
+            for (int P = 0; P < naux; P++)
+                c[(size_t)s * naux + P] = frob_dd(n, V + (size_t)s * n2, L + (size_t)P * n2);
+        }
+    }
+    int fail = 0;
+    #pragma omp parallel for schedule(dynamic)
+    for (int q = 0; q < nx; q++) {
+        int s = xs[q], mu = xmu[q], i = xi[q], ks = k[s];
+        const double *Xs = X + offs[s], *Ys = Y + offs[s];
+        const double *Ws = W ? W + (size_t)s * n2 : NULL;
+        ld *ty = (ld *)malloc(n * sizeof(ld)), *tx = (ld *)malloc(n * sizeof(ld));
+        ld *u = (ld *)malloc(n * sizeof(ld)), *v = (ld *)malloc(n * sizeof(ld));
+        if (!ty || !tx || !u || !v) {
+            free(ty); free(tx); free(u); free(v);
+            #pragma omp atomic write
+            fail = 1;
+            continue;
+        }
+        ld ax = 0.0L, ay = 0.0L;
+        for (int P = 0; P < naux; P++) {
+            const double *LP = L + (size_t)P * n2;
+            if (Ws) {
+                /* columns i of L^P Y_s and L^P X_s */
+                for (int rho = 0; rho < n; rho++) {
+                    ld a = 0.0L, b = 0.0L;
+                    for (int sig = 0; sig < n; sig++) {
+                        a += (ld)LP[IDX2(rho, sig, n)] * (ld)Ys[IDX2(sig, i, ks)];
+                        b += (ld)LP[IDX2(rho, sig, n)] * (ld)Xs[IDX2(sig, i, ks)];
+                    }
+                    ty[rho] = a;
+                    tx[rho] = b;
+                }
+                /* u = W_s ty, v = W_s^T tx */
+                for (int lam = 0; lam < n; lam++) {
+                    ld a = 0.0L, b = 0.0L;
+                    for (int rho = 0; rho < n; rho++) {
+                        a += (ld)Ws[IDX2(lam, rho, n)] * ty[rho];
+                        b += (ld)Ws[IDX2(rho, lam, n)] * tx[rho];
+                    }
+                    u[lam] = a;
+                    v[lam] = b;
+                }
+                for (int lam = 0; lam < n; lam++) {
+                    ax += (ld)LP[IDX2(mu, lam, n)] * u[lam];
+                    ay += (ld)LP[IDX2(mu, lam, n)] * v[lam];
+                }
+            }
+            if (V) {
+                /* (J(V_s) Y_s)[mu][i] = sum_P c_{P,s} (L^P Y_s)[mu][i] */
+                ld py = 0.0L, px = 0.0L;
+                for (int nu = 0; nu < n; nu++) {
+                    py += (ld)LP[IDX2(mu, nu, n)] * (ld)Ys[IDX2(nu, i, ks)];
+                    px += (ld)LP[IDX2(mu, nu, n)] * (ld)Xs[IDX2(nu, i, ks)];
+                }
+                ax += c[(size_t)s * naux + P] * py;
+                ay += c[(size_t)s * naux + P] * px;
+            }
+        }
+        if (dXout) dXout[q] = (double)ax;
+        if (dYout) dYout[q] = (double)ay;
+        free(ty); free(tx); free(u); free(v);
+    }
+    /* dL entries: G^P[a][b] = sum_s [U[a,:].X_s[b,:] + Y_s[a,:].Vp[b,:]
+     *                                + c_{P,s} D_s[a][b] + gamma_{P,s} V_s[a][b]]
+     * with U = W_s (L^P Y_s), Vp = W_s^T (L^P X_s). */
+    #pragma omp parallel for schedule(dynamic)
+    for (int q = 0; q < nl; q++) {
+        int P = lP[q], mu = lmu[q], nu = lnu[q];
+        const double *LP = L + (size_t)P * n2;
+        ld g = 0.0L;
+        for (int s = 0; s < nd; s++) {
+            int ks = k[s];
+            const double *Xs = X + offs[s], *Ys = Y + offs[s];
+            const double *Ws = W ? W + (size_t)s * n2 : NULL;
+            const double *Vs = V ? V + (size_t)s * n2 : NULL;
+            ld gam = 0.0L, cps = Vs ? frob_dd(n, Vs, LP) : 0.0L;
+            for (int lam = 0; lam < n; lam++)
+                for (int sig = 0; sig < n; sig++) {
+                    ld d = 0.0L;
+                    for (int i = 0; i < ks; i++) d += (ld)Xs[IDX2(lam, i, ks)] * (ld)Ys[IDX2(sig, i, ks)];
+                    gam += (ld)LP[IDX2(lam, sig, n)] * d;
+                }
+            for (int pass = 0; pass < 2; pass++) {   /* G[mu][nu], then G[nu][mu] */
+                int a = pass ? nu : mu, b = pass ? mu : nu;
+                ld Dab = 0.0L;
+                for (int i = 0; i < ks; i++) Dab += (ld)Xs[IDX2(a, i, ks)] * (ld)Ys[IDX2(b, i, ks)];
+                ld term = cps * Dab + (Vs ? gam * (ld)Vs[IDX2(a, b, n)] : 0.0L);
+                if (Ws) {
+                    for (int i = 0; i < ks; i++) {
+                        /* U[a][i] = sum_lam W[a][lam] (L^P Y_s)[lam][i];
+                         * Vp[b][i] = sum_lam W[lam][b] (L^P X_s)[lam][i] */
+                        ld ua = 0.0L, vb = 0.0L;
+                        for (int lam = 0; lam < n; lam++) {
+                            ld tyl = 0.0L, txl = 0.0L;
+                            for (int sig = 0; sig < n; sig++) {
+                                tyl += (ld)LP[IDX2(lam, sig, n)] * (ld)Ys[IDX2(sig, i, ks)];
+                                txl += (ld)LP[IDX2(lam, sig, n)] * (ld)Xs[IDX2(sig, i, ks)];
+                            }
+                            ua += (ld)Ws[IDX2(a, lam, n)] * tyl;
+                            vb += (ld)Ws[IDX2(lam, b, n)] * txl;
+                        }
+                        term += ua * (ld)Xs[IDX2(b, i, ks)] + (ld)Ys[IDX2(a, i, ks)] * vb;
+                    }
+                }
+                g += term;
+            }
+        }
+        if (dLout) dLout[q] = (double)(0.5L * g);
+    }
+    free(offs); free(c); free(needc);
+    return fail ? 2 : 0;
+}
+
 /* E = sum_s <W_s, K_s> + <V_s, J_s>, evaluated from the O2 build in long
  * double (for finite-difference checks of the adjoint). */
 int jko_energy(int n, int naux, const double *L, int nd, const int *k,

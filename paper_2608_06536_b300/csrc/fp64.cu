@@ -354,6 +354,13 @@ jk_status fp64_axpy(jk_ctx *h, double *y, const double *x, long long cnt, cudaSt
     return JK_OK;
 }
 
+// C[m][n] = sum_kk A[m*a_sr + kk*a_sk] B[n*b_sr + kk*b_sk] + beta C[m][n], in FP64.
+jk_status fp64_gemm_nt(jk_ctx *h, int M, int N, int K, const double *A, long long a_sr, long long a_sk,
+                       const double *B, long long b_sr, long long b_sk, double *C, long long ldc, double beta,
+                       cudaStream_t st) {
+    return dgemm(h, 1, M, N, K, gop(A, 0, a_sr, 0, a_sk, K), gop(B, 0, b_sr, 0, b_sk, K), C, ldc, 0, 1.0, beta, st);
+}
+
 jk_status split_pack_z(jk_ctx *h, const Problem &pb, double *Z, cudaStream_t st) {
     return pack_z(h, pb, Z, st);
 }
@@ -401,8 +408,8 @@ int fp64_default_pchunk(const Problem &pb) {
     size_t pc = (size_t)256 << 20;
     pc = per ? pc / per : 1;
     if (pc < 1) pc = 1;
+    if (pb.aux_chunk > 0) pc = pb.aux_chunk;       // explicit or tuned chunk
     if (pc > (size_t)pb.naux) pc = pb.naux;
-    if (pb.aux_chunk > 0 && pc > (size_t)pb.aux_chunk) pc = pb.aux_chunk;
     return (int)pc;
 }
 

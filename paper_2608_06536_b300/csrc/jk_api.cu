@@ -1,4 +1,6 @@
 // C ABI of libjk.so: handle, arena, validation and dispatch (see include/jk.h).
+#include <algorithm>
+#include <cmath>
 #include <cstdarg>
 #include <cstring>
 #include <new>
@@ -20,6 +22,7 @@ jk_status set_error(jk_ctx *h, jk_status s, const char *fmt, ...) {
 }
 
 static bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+static bool aligned8(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 7u) == 0; }
 
 // True if p is memory the current device can read (device or managed).
 static bool device_readable(const void *p) {
@@ -85,11 +88,46 @@ static jk_status make_problem(jk_ctx *h, const jk_factor *f, int nd,
 
 static size_t flags_bytes() { return align_up(sizeof(DeviceFlags)); }
 
-static void apply_options(jk_ctx *h, Problem &pb) {
-    if (h) pb.aux_chunk = h->aux_chunk;
+// Effective run-time configuration of a call: the tuned entry of its shape
+// bucket (when allowed), overridden by options set explicitly on the handle.
+static jk_tune_config resolve_config(const jk_ctx *h, jk_op op, jk_precision p, int sms, int nmol,
+                                     const Problem *pbs) {
+    jk_tune_config c{0, 0, 0};
+    if (!h || h->use_tuned) {
+        jk_tune_config t;
+        if (tune_lookup(tune_key(op, p, sms, nmol, pbs), t)) c = t;
+    }
+    if (h) {
+        if (h->aux_chunk >= 0) c.aux_chunk = h->aux_chunk;
+        if (h->schedule >= 0) c.schedule = h->schedule;
+        if (h->raster >= 0) c.raster = h->raster;
+    }
+    return c;
+}
+
+static void apply_config(Problem &pb, const jk_tune_config &c) {
+    pb.aux_chunk = c.aux_chunk;
+    pb.schedule = c.schedule;
+}
+
+static int current_sms() {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return sms;
 }
 
 static jk_status check_out(jk_ctx *h, const void *p, const char *what) {
+    if (!p) return JK_OK;
+    if (!aligned8(p)) return set_error(h, JK_ERR_ARG, "%s is not 8-byte aligned", what);
+    if (!device_readable(p)) return set_error(h, JK_ERR_ARG, "%s is not device memory", what);
+    return JK_OK;
+}
+
+static jk_status check_in(jk_ctx *h, const void *p, const char *what) {
     if (!p) return JK_OK;
     if (!aligned16(p)) return set_error(h, JK_ERR_ARG, "%s is not 16-byte aligned", what);
     if (!device_readable(p)) return set_error(h, JK_ERR_ARG, "%s is not device memory", what);
@@ -109,8 +147,21 @@ static jk_status begin_call(jk_ctx *h) {
 }
 
 static size_t build_bytes(const Problem &pb, jk_precision p) {
-    return p == JK_FP64 ? fp64_build_workspace(pb, fp64_default_pchunk(pb))
-                        : split_build_workspace(pb);
+    if (p == JK_FP64) return fp64_build_workspace(pb, fp64_default_pchunk(pb));
+    return pb.schedule == 1 ? split_batched_workspace(1, &pb) : split_build_workspace(pb);
+}
+
+static size_t batched_bytes(int nmol, const Problem *pbs, jk_precision p) {
+    if (p == JK_SPLIT_BF16) return split_batched_workspace(nmol, pbs);
+    size_t need = 0;
+    for (int m = 0; m < nmol; m++) need = std::max(need, build_bytes(pbs[m], p));
+    return need;
+}
+
+static jk_status run_build(jk_ctx *h, const Problem &pb, jk_precision p, cudaStream_t st) {
+    h->arena.reset(flags_bytes());
+    if (p == JK_FP64) return fp64_build(h, pb, st);
+    return pb.schedule == 1 ? split_batched(h, 1, &pb, st) : split_build(h, pb, st);
 }
 
 static size_t adjoint_bytes(const Problem &pb, jk_precision p, bool want_dl) {
@@ -152,52 +203,16 @@ jk_status jk_destroy(jk_handle h) {
     return JK_OK;
 }
 
-jk_status jk_workspace_query(jk_op op, int32_t nmol, const jk_factor *f,
-                             const int32_t *nd_per_mol, int32_t nd,
-                             const jk_density *d, jk_precision p, size_t *bytes) {
-    if (!bytes || !f || !d) return JK_ERR_ARG;
-    if (p != JK_FP64 && p != JK_SPLIT_BF16) return JK_ERR_ARG;
-    size_t need = 0;
-    if (op == JK_OP_BATCHED) {
-        if (nmol < 1 || !nd_per_mol) return JK_ERR_SHAPE;
-        int off = 0;
-        std::vector<Problem> pbs(nmol);
-        for (int m = 0; m < nmol; m++) {
-            jk_status s = make_problem(nullptr, &f[m], nd_per_mol[m], d + off, false, pbs[m]);
-            if (s != JK_OK) return s;
-            size_t b = build_bytes(pbs[m], p);
-            if (b > need) need = b;
-            off += nd_per_mol[m];
-        }
-        if (off != nd) return JK_ERR_SHAPE;
-        if (p == JK_SPLIT_BF16) need = split_batched_workspace(nmol, pbs.data());
-    } else if (op == JK_OP_BUILD || op == JK_OP_ADJOINT) {
-        Problem pb;
-        jk_status s = make_problem(nullptr, f, nd, d, false, pb);
-        if (s != JK_OK) return s;
-        need = op == JK_OP_BUILD ? build_bytes(pb, p) : adjoint_bytes(pb, p, true);
-    } else {
-        return JK_ERR_ARG;
-    }
-    *bytes = need + flags_bytes() + kArenaAlign;
-    return JK_OK;
-}
+}  // extern "C"
 
-jk_status jk_build(jk_handle h, const jk_factor *f, int32_t nd, const jk_density *d,
-                   double *J, double *K, jk_precision p, void *stream) {
-    JK_TRY(begin_call(h));
-    if (p != JK_FP64 && p != JK_SPLIT_BF16)
-        return set_error(h, JK_ERR_ARG, "unknown precision %d", (int)p);
-    Problem pb;
+namespace jk {
+
+// Validation shared by jk_build and jk_autotune: the problem and its outputs.
+static jk_status prepare_build(jk_ctx *h, const jk_factor *f, int32_t nd, const jk_density *d, double *J,
+                               double *K, Problem &pb) {
     JK_TRY(make_problem(h, f, nd, d, true, pb));
-    apply_options(h, pb);
     JK_TRY(check_out(h, J, "J"));
     JK_TRY(check_out(h, K, "K"));
-    if (!J && !K) return JK_OK;
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    if (h->arena.bytes < flags_bytes() + build_bytes(pb, p))
-        return set_error(h, JK_ERR_OOM, "arena has %zu bytes, this build needs %zu",
-                         h->arena.bytes, flags_bytes() + build_bytes(pb, p));
     const long long n2 = (long long)pb.n * pb.n;
     pb.wantJ = J != nullptr;
     pb.wantK = K != nullptr;
@@ -205,26 +220,20 @@ jk_status jk_build(jk_handle h, const jk_factor *f, int32_t nd, const jk_density
         pb.J[s] = J ? J + s * n2 : nullptr;
         pb.K[s] = K ? K + s * n2 : nullptr;
     }
-    return p == JK_FP64 ? fp64_build(h, pb, st) : split_build(h, pb, st);
+    return JK_OK;
 }
 
-jk_status jk_build_batched(jk_handle h, int32_t nmol, const jk_factor *f,
-                           const int32_t *nd_per_mol, const jk_density *d,
-                           double *const *J, double *const *K, jk_precision p,
-                           void *stream) {
-    JK_TRY(begin_call(h));
-    if (p != JK_FP64 && p != JK_SPLIT_BF16)
-        return set_error(h, JK_ERR_ARG, "unknown precision %d", (int)p);
+// Validation shared by jk_build_batched and jk_autotune_batched.
+static jk_status prepare_batched(jk_ctx *h, int32_t nmol, const jk_factor *f, const int32_t *nd_per_mol,
+                                 const jk_density *d, double *const *J, double *const *K,
+                                 std::vector<Problem> &pbs) {
     if (nmol < 1 || !f || !nd_per_mol || !d)
         return set_error(h, JK_ERR_SHAPE, "nmol=%d or a NULL array", nmol);
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    // Validate everything before launching anything.
-    std::vector<Problem> pbs(nmol);
+    pbs.resize(nmol);
     int off = 0;
     for (int m = 0; m < nmol; m++) {
         Problem &pb = pbs[m];
         JK_TRY(make_problem(h, &f[m], nd_per_mol[m], d + off, true, pb));
-        apply_options(h, pb);
         pb.wantJ = J != nullptr;
         pb.wantK = K != nullptr;
         for (int s = 0; s < nd_per_mol[m]; s++) {
@@ -235,12 +244,275 @@ jk_status jk_build_batched(jk_handle h, int32_t nmol, const jk_factor *f,
             JK_TRY(check_out(h, pb.J[s], "J[i]"));
             JK_TRY(check_out(h, pb.K[s], "K[i]"));
         }
-        if (p == JK_FP64 && h->arena.bytes < flags_bytes() + build_bytes(pb, p))
-            return set_error(h, JK_ERR_OOM, "arena too small for molecule %d", m);
         off += nd_per_mol[m];
     }
+    return JK_OK;
+}
+
+// Times each candidate configuration (one warm-up build, then reps builds
+// between two events on the stream) and keeps the fastest.  A device error
+// flag raised by any candidate ends the search with that status.
+template <class Fits, class Run>
+static jk_status time_candidates(jk_ctx *h, const std::vector<jk_tune_config> &cands, int reps, cudaStream_t st,
+                                 Fits fits, Run run, jk_tune_config &best, double &best_ms) {
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    JK_CUDA_TRY(h, cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return set_error(h, JK_ERR_CUDA, "cudaEventCreate failed");
+    }
+    jk_status rc = JK_OK;
+    bool any = false;
+    best_ms = INFINITY;
+    for (const auto &c : cands) {
+        if (!fits(c)) continue;
+        if ((rc = run(c)) != JK_OK) break;
+        if (cudaEventRecord(e0, st) != cudaSuccess) { rc = set_error(h, JK_ERR_CUDA, "event record failed"); break; }
+        for (int r = 0; r < reps && rc == JK_OK; r++) rc = run(c);
+        if (rc != JK_OK) break;
+        float ms = 0.f;
+        if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+            cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+            rc = set_error(h, JK_ERR_CUDA, "event timing failed: %s", cudaGetErrorString(cudaGetLastError()));
+            break;
+        }
+        DeviceFlags fl;
+        if (cudaMemcpy(&fl, h->flags, sizeof fl, cudaMemcpyDeviceToHost) != cudaSuccess) {
+            rc = set_error(h, JK_ERR_CUDA, "reading the device flags failed");
+            break;
+        }
+        if (fl.error != 0) {
+            cudaMemset(h->flags, 0, sizeof(DeviceFlags));
+            rc = set_error(h, static_cast<jk_status>(fl.error), "device reported status %d while tuning", fl.error);
+            break;
+        }
+        const double per = ms / reps;
+        if (per < best_ms) {
+            best_ms = per;
+            best = c;
+        }
+        any = true;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != JK_OK) return rc;
+    if (!any) return set_error(h, JK_ERR_OOM, "no candidate configuration fits the arena");
+    return JK_OK;
+}
+
+// Aux-chunk candidates around the automatic choice pc0 (0 = automatic),
+// deduplicated by the chunk they produce.
+static std::vector<int> chunk_candidates(int pc0, int naux_max) {
+    std::vector<int> out{0};
+    std::vector<int> seen{std::min(pc0, naux_max)};
+    for (int v : {2 * pc0, pc0 / 2, pc0 / 4}) {
+        if (v < 1) continue;
+        const int eff = std::min(v, naux_max);
+        if (std::find(seen.begin(), seen.end(), eff) != seen.end()) continue;
+        seen.push_back(eff);
+        out.push_back(v);
+    }
+    return out;
+}
+
+// Workspace of a call under the configuration the handle would use (h may be
+// NULL: then the larger of the default and the tuned configuration).
+static jk_status query_impl(const jk_ctx *h, jk_op op, int32_t nmol, const jk_factor *f,
+                            const int32_t *nd_per_mol, int32_t nd, const jk_density *d, jk_precision p,
+                            size_t *bytes) {
+    if (!bytes || !f || !d) return JK_ERR_ARG;
+    if (p != JK_FP64 && p != JK_SPLIT_BF16) return JK_ERR_ARG;
+    const int sms = h ? h->num_sms : current_sms();
+    size_t need = 0;
+    std::vector<Problem> pbs;
+    if (op == JK_OP_BATCHED) {
+        if (nmol < 1 || !nd_per_mol) return JK_ERR_SHAPE;
+        pbs.resize(nmol);
+        int off = 0;
+        for (int m = 0; m < nmol; m++) {
+            jk_status s = make_problem(nullptr, &f[m], nd_per_mol[m], d + off, false, pbs[m]);
+            if (s != JK_OK) return s;
+            off += nd_per_mol[m];
+        }
+        if (off != nd) return JK_ERR_SHAPE;
+    } else if (op == JK_OP_BUILD || op == JK_OP_ADJOINT) {
+        pbs.resize(1);
+        jk_status s = make_problem(nullptr, f, nd, d, false, pbs[0]);
+        if (s != JK_OK) return s;
+        nmol = 1;
+    } else {
+        return JK_ERR_ARG;
+    }
+    const jk_tune_config cfgs[2] = {resolve_config(h, op, p, sms, nmol, pbs.data()), jk_tune_config{0, 0, 0}};
+    for (int v = 0; v < (h ? 1 : 2); v++) {
+        for (auto &pb : pbs) apply_config(pb, cfgs[v]);
+        size_t b = op == JK_OP_BATCHED ? batched_bytes(nmol, pbs.data(), p)
+                   : op == JK_OP_BUILD ? build_bytes(pbs[0], p)
+                                       : adjoint_bytes(pbs[0], p, true);
+        need = std::max(need, b);
+    }
+    *bytes = need + flags_bytes() + kArenaAlign;
+    return JK_OK;
+}
+
+}  // namespace jk
+
+extern "C" {
+
+jk_status jk_workspace_query(jk_op op, int32_t nmol, const jk_factor *f,
+                             const int32_t *nd_per_mol, int32_t nd,
+                             const jk_density *d, jk_precision p, size_t *bytes) {
+    return query_impl(nullptr, op, nmol, f, nd_per_mol, nd, d, p, bytes);
+}
+
+jk_status jk_workspace_query_handle(jk_handle h, jk_op op, int32_t nmol, const jk_factor *f,
+                                    const int32_t *nd_per_mol, int32_t nd, const jk_density *d,
+                                    jk_precision p, size_t *bytes) {
+    if (!h) return JK_ERR_ARG;
+    return query_impl(h, op, nmol, f, nd_per_mol, nd, d, p, bytes);
+}
+
+jk_status jk_build(jk_handle h, const jk_factor *f, int32_t nd, const jk_density *d,
+                   double *J, double *K, jk_precision p, void *stream) {
+    JK_TRY(begin_call(h));
+    if (p != JK_FP64 && p != JK_SPLIT_BF16)
+        return set_error(h, JK_ERR_ARG, "unknown precision %d", (int)p);
+    Problem pb;
+    JK_TRY(prepare_build(h, f, nd, d, J, K, pb));
+    if (!J && !K) return JK_OK;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const jk_tune_config c = resolve_config(h, JK_OP_BUILD, p, h->num_sms, 1, &pb);
+    apply_config(pb, c);
+    h->cur_raster = c.raster;
+    if (h->arena.bytes < flags_bytes() + build_bytes(pb, p))
+        return set_error(h, JK_ERR_OOM, "arena has %zu bytes, this build needs %zu",
+                         h->arena.bytes, flags_bytes() + build_bytes(pb, p));
+    return run_build(h, pb, p, st);
+}
+
+jk_status jk_build_batched(jk_handle h, int32_t nmol, const jk_factor *f,
+                           const int32_t *nd_per_mol, const jk_density *d,
+                           double *const *J, double *const *K, jk_precision p,
+                           void *stream) {
+    JK_TRY(begin_call(h));
+    if (p != JK_FP64 && p != JK_SPLIT_BF16)
+        return set_error(h, JK_ERR_ARG, "unknown precision %d", (int)p);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // Validate everything before launching anything.
+    std::vector<Problem> pbs;
+    JK_TRY(prepare_batched(h, nmol, f, nd_per_mol, d, J, K, pbs));
+    const jk_tune_config c = resolve_config(h, JK_OP_BATCHED, p, h->num_sms, nmol, pbs.data());
+    for (auto &pb : pbs) apply_config(pb, c);
+    h->cur_raster = c.raster;
+    if (h->arena.bytes < flags_bytes() + batched_bytes(nmol, pbs.data(), p))
+        return set_error(h, JK_ERR_OOM, "arena has %zu bytes, this batched build needs %zu", h->arena.bytes,
+                         flags_bytes() + batched_bytes(nmol, pbs.data(), p));
     if (!J && !K) return JK_OK;
     return batched_build(h, nmol, pbs.data(), p, st);
+}
+
+jk_status jk_autotune(jk_handle h, const jk_factor *f, int32_t nd, const jk_density *d,
+                      double *J, double *K, jk_precision p, void *stream, int32_t reps,
+                      jk_tune_config *best, double *best_ms) {
+    JK_TRY(begin_call(h));
+    if (p != JK_FP64 && p != JK_SPLIT_BF16)
+        return set_error(h, JK_ERR_ARG, "unknown precision %d", (int)p);
+    if (reps < 1) return set_error(h, JK_ERR_ARG, "reps=%d must be >= 1", reps);
+    Problem pb;
+    JK_TRY(prepare_build(h, f, nd, d, J, K, pb));
+    if (!J && !K) return set_error(h, JK_ERR_ARG, "J and K are both NULL");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int pc0 = p == JK_FP64 ? [&] { Problem q = pb; q.aux_chunk = 0; return fp64_default_pchunk(q); }()
+                                 : split_auto_pchunk(pb);
+    std::vector<jk_tune_config> cands;
+    for (int ch : chunk_candidates(pc0, pb.naux))
+        for (int sc = 0; sc < (p == JK_FP64 ? 1 : 2); sc++)
+            for (int ra = 0; ra < (p == JK_FP64 ? 1 : 2); ra++) cands.push_back(jk_tune_config{ch, sc, ra});
+    auto fits = [&](const jk_tune_config &c) {
+        Problem q = pb;
+        apply_config(q, c);
+        return h->arena.bytes >= flags_bytes() + build_bytes(q, p);
+    };
+    auto run = [&](const jk_tune_config &c) {
+        Problem q = pb;
+        apply_config(q, c);
+        h->cur_raster = c.raster;
+        return run_build(h, q, p, st);
+    };
+    jk_tune_config bc{0, 0, 0};
+    double bms = 0.0;
+    JK_TRY(time_candidates(h, cands, reps, st, fits, run, bc, bms));
+    tune_store(tune_key(JK_OP_BUILD, p, h->num_sms, 1, &pb), bc, bms);
+    if (best) *best = bc;
+    if (best_ms) *best_ms = bms;
+    return JK_OK;
+}
+
+jk_status jk_autotune_batched(jk_handle h, int32_t nmol, const jk_factor *f,
+                              const int32_t *nd_per_mol, const jk_density *d,
+                              double *const *J, double *const *K, jk_precision p,
+                              void *stream, int32_t reps, jk_tune_config *best,
+                              double *best_ms) {
+    JK_TRY(begin_call(h));
+    if (p != JK_FP64 && p != JK_SPLIT_BF16)
+        return set_error(h, JK_ERR_ARG, "unknown precision %d", (int)p);
+    if (reps < 1) return set_error(h, JK_ERR_ARG, "reps=%d must be >= 1", reps);
+    std::vector<Problem> pbs;
+    JK_TRY(prepare_batched(h, nmol, f, nd_per_mol, d, J, K, pbs));
+    if (!J && !K) return set_error(h, JK_ERR_ARG, "J and K are both NULL");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int pc0 = 1 << 30, naux_max = 0;
+    for (auto &pb : pbs) {
+        Problem q = pb;
+        q.aux_chunk = 0;
+        pc0 = std::min(pc0, p == JK_FP64 ? fp64_default_pchunk(q) : split_auto_pchunk(q));
+        naux_max = std::max(naux_max, pb.naux);
+    }
+    std::vector<jk_tune_config> cands;
+    for (int ch : chunk_candidates(pc0, naux_max))
+        for (int ra = 0; ra < (p == JK_FP64 ? 1 : 2); ra++) cands.push_back(jk_tune_config{ch, 1, ra});
+    auto fits = [&](const jk_tune_config &c) {
+        std::vector<Problem> q = pbs;
+        for (auto &pb : q) apply_config(pb, c);
+        return h->arena.bytes >= flags_bytes() + batched_bytes(nmol, q.data(), p);
+    };
+    auto run = [&](const jk_tune_config &c) {
+        std::vector<Problem> q = pbs;
+        for (auto &pb : q) apply_config(pb, c);
+        h->cur_raster = c.raster;
+        return batched_build(h, nmol, q.data(), p, st);
+    };
+    jk_tune_config bc{0, 1, 0};
+    double bms = 0.0;
+    JK_TRY(time_candidates(h, cands, reps, st, fits, run, bc, bms));
+    tune_store(tune_key(JK_OP_BATCHED, p, h->num_sms, nmol, pbs.data()), bc, bms);
+    if (best) *best = bc;
+    if (best_ms) *best_ms = bms;
+    return JK_OK;
+}
+
+jk_status jk_tune_lookup(jk_op op, int32_t nmol, const jk_factor *f, const int32_t *nd_per_mol,
+                         int32_t nd, const jk_density *d, jk_precision p, int32_t num_sms,
+                         jk_tune_config *cfg) {
+    if (!f || !d || !cfg) return JK_ERR_ARG;
+    std::vector<Problem> pbs;
+    if (op == JK_OP_BATCHED) {
+        if (nmol < 1 || !nd_per_mol) return JK_ERR_SHAPE;
+        pbs.resize(nmol);
+        int off = 0;
+        for (int m = 0; m < nmol; m++) {
+            JK_TRY(make_problem(nullptr, &f[m], nd_per_mol[m], d + off, false, pbs[m]));
+            off += nd_per_mol[m];
+        }
+        if (off != nd) return JK_ERR_SHAPE;
+    } else if (op == JK_OP_BUILD) {
+        pbs.resize(1);
+        JK_TRY(make_problem(nullptr, f, nd, d, false, pbs[0]));
+        nmol = 1;
+    } else {
+        return JK_ERR_ARG;
+    }
+    return tune_lookup(tune_key(op, p, num_sms, nmol, pbs.data()), *cfg) ? JK_OK : JK_ERR_UNSUPPORTED;
 }
 
 jk_status jk_adjoint(jk_handle h, const jk_factor *f, int32_t nd, const jk_density *d,
@@ -251,13 +523,14 @@ jk_status jk_adjoint(jk_handle h, const jk_factor *f, int32_t nd, const jk_densi
         return set_error(h, JK_ERR_ARG, "unknown precision %d", (int)p);
     Problem pb;
     JK_TRY(make_problem(h, f, nd, d, true, pb));
-    apply_options(h, pb);
+    if (h->aux_chunk >= 0) pb.aux_chunk = h->aux_chunk;
+    h->cur_raster = h->raster >= 0 ? h->raster : 0;
     if (!dX || !dY) return set_error(h, JK_ERR_ARG, "dX and dY are required");
     JK_TRY(check_out(h, dX, "dX"));
     JK_TRY(check_out(h, dY, "dY"));
     JK_TRY(check_out(h, dL, "dL"));
-    JK_TRY(check_out(h, W, "W"));
-    JK_TRY(check_out(h, V, "V"));
+    JK_TRY(check_in(h, W, "W"));
+    JK_TRY(check_in(h, V, "V"));
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     size_t need = flags_bytes() + adjoint_bytes(pb, p, dL != nullptr);
     if (h->arena.bytes < need)
@@ -270,8 +543,18 @@ jk_status jk_adjoint(jk_handle h, const jk_factor *f, int32_t nd, const jk_densi
 jk_status jk_set_option(jk_handle h, jk_option opt, int64_t value) {
     if (!h) return JK_ERR_ARG;
     if (opt == JK_OPT_AUX_CHUNK) {
-        if (value < 0 || value > (1 << 30)) return set_error(h, JK_ERR_ARG, "aux chunk out of range");
+        if (value < -1 || value > (1 << 30)) return set_error(h, JK_ERR_ARG, "aux chunk out of range");
         h->aux_chunk = static_cast<int>(value);
+        return JK_OK;
+    }
+    if (opt == JK_OPT_SCHEDULE || opt == JK_OPT_RASTER) {
+        if (value < -1 || value > 1) return set_error(h, JK_ERR_ARG, "option %d takes -1, 0 or 1", (int)opt);
+        (opt == JK_OPT_SCHEDULE ? h->schedule : h->raster) = static_cast<int>(value);
+        return JK_OK;
+    }
+    if (opt == JK_OPT_USE_TUNED) {
+        if (value != 0 && value != 1) return set_error(h, JK_ERR_ARG, "JK_OPT_USE_TUNED takes 0 or 1");
+        h->use_tuned = static_cast<int>(value);
         return JK_OK;
     }
     return set_error(h, JK_ERR_ARG, "unknown option %d", (int)opt);

@@ -66,7 +66,11 @@ struct jk_ctx {
     std::string last_error;
     int device = -1;
     int num_sms = 148;
-    int aux_chunk = 0;
+    int aux_chunk = -1;      // explicit options (JK_OPT_*); -1 = not set
+    int schedule = -1;
+    int raster = -1;
+    int use_tuned = 1;
+    int cur_raster = 0;      // tile order in effect for the running call
     jk::Profiler prof;
 };
 
@@ -91,6 +95,7 @@ struct Problem {
     double *K[kMaxDens];
     bool wantJ = false, wantK = false;
     int aux_chunk = 0;   // at most this many aux indices per chunk (0 = automatic)
+    int schedule = 0;    // split precision: 0 per-density launches, 1 grouped launches
 };
 
 jk_status set_error(jk_ctx *h, jk_status s, const char *fmt, ...);
@@ -138,18 +143,13 @@ jk_status split_adjoint(jk_ctx *h, const Problem &pb, const double *W,
                         cudaStream_t st);
 
 size_t split_batched_workspace(int nmol, const Problem *pbs);
+int split_auto_pchunk(const Problem &pb);   // aux chunk chosen from the workspace budget
 jk_status split_batched(jk_ctx *h, int nmol, const Problem *pbs, cudaStream_t st);
 
 // ---- batched builds (batched.cu) ------------------------------------------
 jk_status batched_build(jk_ctx *h, int nmol, const Problem *pbs, jk_precision p,
                         cudaStream_t st);
 
-size_t split_batched_workspace(int nmol, const Problem *pbs);
-jk_status split_batched(jk_ctx *h, int nmol, const Problem *pbs, cudaStream_t st);
-
-// ---- batched builds (batched.cu) ------------------------------------------
-jk_status batched_build(jk_ctx *h, int nmol, const Problem *pbs, jk_precision p,
-                        cudaStream_t st);
 
 // Brackets one kernel launch: counts it and, when profiling is on, records
 // CUDA events before and after it on the launch stream.
@@ -161,5 +161,14 @@ struct LaunchScope {
     LaunchScope(jk_ctx *h_, int kind_, cudaStream_t st_);
     ~LaunchScope();
 };
+
+// ---- autotuner (tune.cu) ----------------------------------------------------
+struct TuneKey {
+    int op, prec, sms, nmol, nb, nauxb, nd, ksumb;
+    bool operator<(const TuneKey &o) const;
+};
+TuneKey tune_key(jk_op op, jk_precision p, int sms, int nmol, const Problem *pbs);
+bool tune_lookup(const TuneKey &k, jk_tune_config &cfg);
+void tune_store(const TuneKey &k, const jk_tune_config &cfg, double ms);
 
 }  // namespace jk

@@ -380,6 +380,7 @@ struct OzGroup {
     OzProb p[MAXG];
     int nprob;
     int ntiles;
+    int raster;         // 0: n-tile fastest, 1: m-tile fastest
 };
 
 __device__ __forceinline__ int prob_of(const OzGroup &g, int t) {
@@ -388,16 +389,22 @@ __device__ __forceinline__ int prob_of(const OzGroup &g, int t) {
     return i;
 }
 
-// Tile t of the launch: n-tile fastest (tiles sharing an A row block run side
-// by side and hit L2), then m-tile, then the split-K super-chunk z.
+// Tile t of a problem: raster 0 runs the n-tiles of one A row block side by
+// side (they share the A tile in L2), raster 1 the m-tiles of one B column
+// block; the split-K super-chunk z varies slowest.
 struct TileCoord {
     int n, m, z, kbeg, nkb;
 };
 
-__device__ __forceinline__ TileCoord tile_of(int t, int ntn, int ntm, int K) {
+__device__ __forceinline__ TileCoord tile_of(int t, int ntn, int ntm, int K, int raster) {
     TileCoord c;
-    c.n = t % ntn;
-    c.m = (t / ntn) % ntm;
+    if (raster == 0) {
+        c.n = t % ntn;
+        c.m = (t / ntn) % ntm;
+    } else {
+        c.m = t % ntm;
+        c.n = (t / ntm) % ntn;
+    }
     c.z = t / (ntn * ntm);
     c.kbeg = c.z * SUPER;
     const int kend = min(K, c.kbeg + SUPER);
@@ -454,7 +461,7 @@ ozgemm_kernel(const __grid_constant__ OzGroup g) {
                     tc::prefetch_tmap(&pr.tmB);
                     last = pi;
                 }
-                const TileCoord tc_ = tile_of(t - pr.tile0, pr.ntn, pr.ntm, pr.a.K);
+                const TileCoord tc_ = tile_of(t - pr.tile0, pr.ntn, pr.ntm, pr.a.K, g.raster);
                 for (int kb = 0; kb < tc_.nkb; kb++) {
                     if (!tc::mbar_wait(&empty[stage], phase ^ 1u, abort_flag)) { ok = false; break; }
                     tc::mbar_expect_tx(&full[stage], STAGE_BYTES);
@@ -475,7 +482,7 @@ ozgemm_kernel(const __grid_constant__ OzGroup g) {
             bool ok = true;
             for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
                 const OzProb &pr = g.p[prob_of(g, t)];
-                const TileCoord tc_ = tile_of(t - pr.tile0, pr.ntn, pr.ntm, pr.a.K);
+                const TileCoord tc_ = tile_of(t - pr.tile0, pr.ntn, pr.ntm, pr.a.K, g.raster);
                 for (int kb0 = 0; kb0 < tc_.nkb && ok; kb0 += WPERIOD) {
                     // Unrolled over one window period: the window bookkeeping below is
                     // compile-time except for the tile's first and last K-block.
@@ -547,7 +554,7 @@ ozgemm_kernel(const __grid_constant__ OzGroup g) {
             const int pi = prob_of(g, t);
             const OzArgs a = g.p[pi].a;
             const CUtensorMap *tmC = &g.p[pi].tmC;
-            const TileCoord tc_ = tile_of(t - g.p[pi].tile0, g.p[pi].ntn, g.p[pi].ntm, a.K);
+            const TileCoord tc_ = tile_of(t - g.p[pi].tile0, g.p[pi].ntn, g.p[pi].ntm, a.K, g.raster);
             long long acc64[BN / 2];
 #pragma unroll
             for (int i = 0; i < BN / 2; i++) acc64[i] = 0;
@@ -876,6 +883,7 @@ static jk_status oz_launch(jk_ctx *h, const std::vector<oz::OzProb> &probs, cuda
         if (tiles > 0x7fffffffLL) return set_error(h, JK_ERR_SHAPE, "too many tiles in one launch");
         grp.nprob = np;
         grp.ntiles = static_cast<int>(tiles);
+        grp.raster = h->cur_raster;
         const int grid = static_cast<int>(tiles < h->num_sms ? tiles : h->num_sms);
         {
             LaunchScope ls(h, KK_OZGEMM, st);
@@ -919,12 +927,18 @@ static int split_pchunk(const Problem &pb) {
     size_t budget = static_cast<size_t>(12) << 30;
     size_t pc = per ? budget / per : 1;
     if (pc < 1) pc = 1;
+    if (pb.aux_chunk > 0) pc = pb.aux_chunk;       // explicit or tuned chunk
     if (pc > static_cast<size_t>(pb.naux)) pc = pb.naux;
     // Keep rows of the panel GEMM within the grid limit.
     size_t maxrows = static_cast<size_t>(65535) * oz::BM;
     if (pc * n > maxrows) pc = maxrows / n;
-    if (pb.aux_chunk > 0 && pc > static_cast<size_t>(pb.aux_chunk)) pc = pb.aux_chunk;
     return static_cast<int>(pc);
+}
+
+int split_auto_pchunk(const Problem &pb) {
+    Problem q = pb;
+    q.aux_chunk = 0;
+    return split_pchunk(q);
 }
 
 static size_t partial_count(const Problem &pb, int pc) {
@@ -1106,6 +1120,9 @@ jk_status fp64_frob_all(jk_ctx *h, const double *L, int n, int naux, const doubl
                         cudaStream_t st);
 jk_status fp64_jstream_dense(jk_ctx *h, const double *L, int n, int naux, const double *g, int nd, double *out,
                              cudaStream_t st);
+jk_status fp64_gemm_nt(jk_ctx *h, int M, int N, int K, const double *A, long long a_sr, long long a_sk,
+                       const double *B, long long b_sr, long long b_sk, double *C, long long ldc, double beta,
+                       cudaStream_t st);
 
 // out (+)= A B^T on sliced operands, FP64 out with row stride ldo.  Uses P (int64
 // partials) when K spans several super-chunks, else tmp when accumulating.
@@ -1134,17 +1151,17 @@ static int split_adj_pchunk(const Problem &pb) {
     size_t budget = static_cast<size_t>(8) << 30;
     size_t pc = per ? budget / per : 1;
     if (pc < 1) pc = 1;
+    if (pb.aux_chunk > 0) pc = pb.aux_chunk;       // explicit chunk
     if (pc > static_cast<size_t>(pb.naux)) pc = pb.naux;
     size_t maxrows = static_cast<size_t>(65535) * oz::BM;
     if (pc * n > maxrows) pc = maxrows / n;
-    if (pb.aux_chunk > 0 && pc > static_cast<size_t>(pb.aux_chunk)) pc = pb.aux_chunk;
     return static_cast<int>(pc);
 }
 
 struct AdjBufs {
     double *Z, *T, *gam, *cps, *JV, *U, *Vp, *AG, *BG, *G, *GV, *tmp;
     long long *P;
-    Sliced Zs, Ls, Lm, Ws[kMaxDens], WTs[kMaxDens], TXb, TYb, Ub, Vpb, AGs, BGs, Gam, Vs, JVs, Xt, Yt;
+    Sliced Zs, Ls, Lm, Ws[kMaxDens], WTs[kMaxDens], TXb, TYb, Ub, Vpb, AGs, BGs, Gam, Vs;
 };
 
 static size_t adj_partials(const Problem &pb, int pc) {
@@ -1188,8 +1205,6 @@ static bool adj_take(Arena &ar, const Problem &pb, int pc, bool W, bool V, bool 
          take_sliced(ar, kmax, pc * n, 1, b.Ub) && take_sliced(ar, kmax, pc * n, 1, b.Vpb);
     if (ok && dl) ok = take_sliced(ar, pc * n, ks3, 1, b.AGs) && take_sliced(ar, n, ks3, 1, b.BGs);
     if (ok && dl && V) ok = take_sliced(ar, pc, nd, 1, b.Gam) && take_sliced(ar, static_cast<int>(n2), nd, 1, b.Vs);
-    if (ok && V) ok = take_sliced(ar, static_cast<int>(n2 / n) * nd, n, 1, b.JVs) &&
-                      take_sliced(ar, kmax, n, 1, b.Xt) && take_sliced(ar, kmax, n, 1, b.Yt);
     return ok;
 }
 
@@ -1520,19 +1535,13 @@ jk_status split_adjoint(jk_ctx *h, const Problem &pb, const double *W, const dou
         }
     }
     if (wantV) {
-        // dX_s += J(V_s) Y_s, dY_s += J(V_s) X_s
+        // dX_s += J(V_s) Y_s, dY_s += J(V_s) X_s: small (n x n by n x k) FP64 products,
+        // so every J term of the adjoint stays in FP64 end to end.
         for (int s = 0; s < nd; s++) {
             const int k = pb.k[s];
             const double *Ys = pb.sym[s] ? pb.X[s] : pb.Y[s];
-            oz::Src jv{b.JV + s * n2, n, 0, 1, n};
-            Sliced Jvs = b.JVs;
-            JK_TRY(slice_operand(h, jv, n, n, 1, Jvs, st));
-            oz::Src yt{Ys, 1, 0, k, n};
-            oz::Src xt{pb.X[s], 1, 0, k, n};
-            JK_TRY(slice_operand(h, yt, k, n, 1, b.Yt, st));
-            JK_TRY(slice_operand(h, xt, k, n, 1, b.Xt, st));
-            JK_TRY(gemm_into(h, Jvs, b.Yt, dX + boff[s], k, true, b.P, b.tmp, st));
-            JK_TRY(gemm_into(h, Jvs, b.Xt, dY + boff[s], k, true, b.P, b.tmp, st));
+            JK_TRY(fp64_gemm_nt(h, n, k, n, b.JV + s * n2, n, 1, Ys, 1, k, dX + boff[s], k, 1.0, st));
+            JK_TRY(fp64_gemm_nt(h, n, k, n, b.JV + s * n2, n, 1, pb.X[s], 1, k, dY + boff[s], k, 1.0, st));
         }
     }
     for (int s = 0; s < nd; s++) {

@@ -19,6 +19,11 @@ shapes stand in for them, with nbf spanning the paper's 236-472 AO range):
 * Uneven batch: molecule sizes nbf ~ U{100..600}, densities per molecule
   ~ U{1..16} from stream ``[seed, 0]``; molecule m then uses seed
   ``seed * 1000 + m`` for its own factor and densities.
+* Factors too large to draw on the host in reasonable time (the 40 GB
+  single molecule, the 208 GB uneven batch, the 10 GB adjoint case) are drawn
+  on the device by ``factor_device``: the same symmetric N(0,1) * exp(-P/tau)
+  recipe, with torch's Philox generator seeded from ``[seed, 1]``.  Tests
+  that check such a factor against the CPU code copy it back to the host.
 """
 from __future__ import annotations
 
@@ -44,6 +49,27 @@ def factor(n: int, naux: int, tau: float, seed: int = 0, P0: int = 0) -> np.ndar
     L = np.empty((naux, n, n), dtype=np.float64)
     for j in range(naux):
         L[j] = factor_slice(n, P0 + j, tau, seed)
+    return L
+
+
+def factor_device(n: int, naux: int, tau: float, seed: int = 0, device="cuda",
+                  block: int = 64):
+    """L^P for P = 0 .. naux-1 drawn on the device as [naux][n][n] float64:
+    an n x n N(0,1) draw per P whose upper triangle (with the diagonal) is
+    kept and mirrored, scaled by exp(-P/tau).  Deterministic for a given
+    (n, naux, tau, seed) and block size."""
+    import torch
+    state = np.random.SeedSequence([seed, 1]).generate_state(2, dtype=np.uint32)
+    g = torch.Generator(device=device)
+    g.manual_seed(int(state[0]) << 32 | int(state[1]))
+    L = torch.empty((naux, n, n), dtype=torch.float64, device=device)
+    upper = torch.ones((n, n), dtype=torch.bool, device=device).triu_()
+    for P0 in range(0, naux, block):
+        b = min(block, naux - P0)
+        R = torch.randn((b, n, n), dtype=torch.float64, device=device, generator=g)
+        R = torch.where(upper, R, R.transpose(1, 2))
+        scale = torch.exp(-torch.arange(P0, P0 + b, dtype=torch.float64, device=device) / tau)
+        L[P0:P0 + b] = R * scale[:, None, None]
     return L
 
 

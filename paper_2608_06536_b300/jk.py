@@ -32,6 +32,16 @@ class jk_density(ct.Structure):
                 ("X", ct.c_void_p), ("Y", ct.c_void_p)]
 
 
+class jk_tune_config(ct.Structure):
+    _fields_ = [("aux_chunk", ct.c_int32), ("schedule", ct.c_int32), ("raster", ct.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {"aux_chunk": self.aux_chunk, "schedule": self.schedule, "raster": self.raster}
+
+
+OPTIONS = {"aux_chunk": 0, "schedule": 1, "raster": 2, "use_tuned": 3}
+
+
 class JKError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"jk status {status}: {msg}")
@@ -64,6 +74,23 @@ def load_library(path: str = LIB_PATH):
                                        ct.POINTER(vp), ct.POINTER(vp), ct.c_int, vp]
         L.jk_adjoint.argtypes = [vp, ct.POINTER(jk_factor), ct.c_int32, ct.POINTER(jk_density),
                                  vp, vp, vp, vp, vp, ct.c_int, vp]
+        L.jk_workspace_query_handle.argtypes = [vp, ct.c_int, ct.c_int32, ct.POINTER(jk_factor),
+                                                ct.POINTER(ct.c_int32), ct.c_int32,
+                                                ct.POINTER(jk_density), ct.c_int, ct.POINTER(sz)]
+        L.jk_autotune.argtypes = [vp, ct.POINTER(jk_factor), ct.c_int32, ct.POINTER(jk_density),
+                                  vp, vp, ct.c_int, vp, ct.c_int32, ct.POINTER(jk_tune_config),
+                                  ct.POINTER(ct.c_double)]
+        L.jk_autotune_batched.argtypes = [vp, ct.c_int32, ct.POINTER(jk_factor), ct.POINTER(ct.c_int32),
+                                          ct.POINTER(jk_density), ct.POINTER(vp), ct.POINTER(vp), ct.c_int,
+                                          vp, ct.c_int32, ct.POINTER(jk_tune_config), ct.POINTER(ct.c_double)]
+        L.jk_tune_lookup.argtypes = [ct.c_int, ct.c_int32, ct.POINTER(jk_factor), ct.POINTER(ct.c_int32),
+                                     ct.c_int32, ct.POINTER(jk_density), ct.c_int, ct.c_int32,
+                                     ct.POINTER(jk_tune_config)]
+        L.jk_tune_export.argtypes = [ct.c_char_p, sz, ct.POINTER(sz)]
+        L.jk_tune_import.argtypes = [ct.c_char_p]
+        for f in (L.jk_workspace_query_handle, L.jk_autotune, L.jk_autotune_batched, L.jk_tune_lookup,
+                  L.jk_tune_export, L.jk_tune_import, L.jk_tune_clear):
+            f.restype = ct.c_int
         L.jk_sync_status.argtypes = [vp, vp]
         L.jk_set_option.argtypes = [vp, ct.c_int, ct.c_int64]
         L.jk_set_option.restype = ct.c_int
@@ -145,6 +172,7 @@ class Engine:
         self.device = dev
         self._ws = None
         self._h = ct.c_void_p()
+        self._opts = {}
         if workspace_bytes:
             self._ensure(workspace_bytes)
 
@@ -160,8 +188,8 @@ class Engine:
         self._h = h
         if getattr(self, "_profile_on", False):
             self.lib.jk_profile_enable(self._h, 1)
-        if getattr(self, "_aux_chunk", 0):
-            self.lib.jk_set_option(self._h, 0, self._aux_chunk)
+        for code, value in self._opts.items():
+            self._check(self.lib.jk_set_option(self._h, code, value), self._h)
 
     def close(self):
         if self._h:
@@ -190,11 +218,18 @@ class Engine:
         self._check(self.lib.jk_sync_status(self._h, _stream_ptr(stream)), self._h)
 
     # -- options ---------------------------------------------------------------
-    def set_aux_chunk(self, naux_per_chunk: int):
-        """At most this many aux indices per internal chunk (0 = automatic)."""
-        self._aux_chunk = int(naux_per_chunk)
+    def set_option(self, name: str, value: int):
+        """Handle option (JK_OPT_*): "aux_chunk" (>= 0, 0 = automatic, -1 =
+        tuned/default), "schedule" and "raster" (-1 = tuned/default, 0, 1),
+        "use_tuned" (0 or 1).  Kept across arena growth."""
+        code = OPTIONS[name]
+        self._opts[code] = int(value)
         if self._h:
-            self._check(self.lib.jk_set_option(self._h, 0, self._aux_chunk), self._h)
+            self._check(self.lib.jk_set_option(self._h, code, int(value)), self._h)
+
+    def set_aux_chunk(self, naux_per_chunk: int):
+        """This many aux indices per internal chunk (0 = automatic)."""
+        self.set_option("aux_chunk", naux_per_chunk)
 
     # -- instrumentation -----------------------------------------------------
     def launch_count(self) -> int:
@@ -226,10 +261,13 @@ class Engine:
 
     # -- queries -------------------------------------------------------------
     def query(self, op, factors, dens_c, nd_per_mol, nd, precision) -> int:
+        """Arena bytes for a call under this handle's options and tuned configs."""
+        if not self._h:
+            self._ensure(1 << 20)
         nbytes = ct.c_size_t()
         ndm = (ct.c_int32 * len(nd_per_mol))(*nd_per_mol) if nd_per_mol else None
-        st = self.lib.jk_workspace_query(op, len(factors), factors, ndm, nd, dens_c,
-                                         precision, ct.byref(nbytes))
+        st = self.lib.jk_workspace_query_handle(self._h, op, len(factors), factors, ndm, nd, dens_c,
+                                                precision, ct.byref(nbytes))
         self._check(st, None)
         return nbytes.value
 
@@ -253,12 +291,58 @@ class Engine:
         self._check(st, self._h)
         return (J if want_j else None), (K if want_k else None)
 
-    def build_batched(self, mols, precision="fp64", want_j=True, want_k=True, stream=None):
-        """mols: list of (L, X list, Y list or None, sym list or None).
-        Returns per-molecule (J, K) lists of [nd_m][n_m][n_m] tensors."""
+    def autotune(self, L, X, Y=None, sym=None, precision="split", reps: int = 3, stream=None):
+        """Time the candidate configurations of this build and cache the
+        fastest for its shape bucket; returns (config dict, ms per build)."""
         p = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        L = _dev_f64(L, self.device)
+        dens = Densities(X, Y, sym, self.device)
+        naux, n = int(L.shape[0]), int(L.shape[1])
+        f = jk_factor(n, naux, L.data_ptr())
+        nd = len(dens)
+        self._ensure(self._tune_bytes(JK_OP_BUILD, (jk_factor * 1)(f), dens.c, None, nd, p))
+        J = torch.empty((nd, n, n), dtype=torch.float64, device=self.device)
+        K = torch.empty((nd, n, n), dtype=torch.float64, device=self.device)
+        cfg, ms = jk_tune_config(), ct.c_double()
+        st = self.lib.jk_autotune(self._h, ct.byref(f), nd, dens.c, _ptr(J), _ptr(K), p,
+                                  _stream_ptr(stream), int(reps), ct.byref(cfg), ct.byref(ms))
+        self._check(st, self._h)
+        return cfg.as_dict(), ms.value
+
+    def autotune_batched(self, mols, precision="split", reps: int = 3, stream=None):
+        """As autotune, for a batched build over `mols` (see build_batched)."""
+        p = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        fac, dall, nd_per, keep, outs = self._marshal_batched(mols)
+        ndt = sum(nd_per)
+        self._ensure(self._tune_bytes(JK_OP_BATCHED, fac, dall, nd_per, ndt, p))
+        Jp, Kp, _ = self._batched_outputs(keep[1], True, True)
+        ndm = (ct.c_int32 * len(mols))(*nd_per)
+        cfg, ms = jk_tune_config(), ct.c_double()
+        st = self.lib.jk_autotune_batched(self._h, len(mols), fac, ndm, dall, Jp, Kp, p, _stream_ptr(stream),
+                                          int(reps), ct.byref(cfg), ct.byref(ms))
+        self._check(st, self._h)
+        return cfg.as_dict(), ms.value
+
+    def _tune_bytes(self, op, factors, dens_c, nd_per_mol, nd, p) -> int:
+        """Arena for the largest candidate of an autotune: the automatic
+        configuration at twice its aux chunk, and the grouped schedule."""
+        saved = dict(self._opts)
+        need = self.query(op, factors, dens_c, nd_per_mol, nd, p)
+        try:
+            for sched in ((0, 1) if op == JK_OP_BUILD else (1,)):
+                self.set_option("schedule", sched)
+                self.set_option("aux_chunk", 0)
+                need = max(need, self.query(op, factors, dens_c, nd_per_mol, nd, p))
+        finally:
+            self._opts = saved
+            if self._h:
+                for code in range(len(OPTIONS)):
+                    self.lib.jk_set_option(self._h, code, saved.get(code, 1 if code == 3 else -1))
+        return int(need * 2)
+
+    def _marshal_batched(self, mols):
         nmol = len(mols)
-        Ls, dens, outs = [], [], []
+        Ls, dens = [], []
         fac = (jk_factor * nmol)()
         nd_per = []
         for m, (L, X, Y, sym) in enumerate(mols):
@@ -273,10 +357,13 @@ class Engine:
         for d in dens:
             for s in range(len(d)):
                 dall[i] = d.c[s]; i += 1
-        self._ensure(self.query(JK_OP_BATCHED, fac, dall, nd_per, ndt, p))
+        return fac, dall, nd_per, (Ls, dens), None
+
+    def _batched_outputs(self, dens, want_j, want_k):
+        ndt = sum(len(d) for d in dens)
         Jp = (ct.c_void_p * ndt)(); Kp = (ct.c_void_p * ndt)()
-        i = 0
-        for m, d in enumerate(dens):
+        outs, i = [], 0
+        for d in dens:
             n = d.n
             Jm = torch.empty((len(d), n, n), dtype=torch.float64, device=self.device) if want_j else None
             Km = torch.empty((len(d), n, n), dtype=torch.float64, device=self.device) if want_k else None
@@ -287,8 +374,18 @@ class Engine:
                 if want_k:
                     Kp[i] = Km[s].data_ptr()
                 i += 1
-        ndm = (ct.c_int32 * nmol)(*nd_per)
-        st = self.lib.jk_build_batched(self._h, nmol, fac, ndm, dall, Jp if want_j else None,
+        return Jp, Kp, outs
+
+    def build_batched(self, mols, precision="fp64", want_j=True, want_k=True, stream=None):
+        """mols: list of (L, X list, Y list or None, sym list or None).
+        Returns per-molecule (J, K) lists of [nd_m][n_m][n_m] tensors."""
+        p = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        fac, dall, nd_per, keep, _ = self._marshal_batched(mols)
+        ndt = sum(nd_per)
+        self._ensure(self.query(JK_OP_BATCHED, fac, dall, nd_per, ndt, p))
+        Jp, Kp, outs = self._batched_outputs(keep[1], want_j, want_k)
+        ndm = (ct.c_int32 * len(mols))(*nd_per)
+        st = self.lib.jk_build_batched(self._h, len(mols), fac, ndm, dall, Jp if want_j else None,
                                        Kp if want_k else None, p, _stream_ptr(stream))
         self._check(st, self._h)
         return outs
@@ -343,3 +440,25 @@ def jk_build_batched(mols, precision="fp64", **kw):
 def jk_adjoint(L, X, Y=None, sym=None, W=None, V=None, precision="fp64", **kw):
     return default_engine(L.device if torch.is_tensor(L) and L.is_cuda else None).adjoint(
         L, X, Y, sym, W, V, precision=precision, **kw)
+
+
+def tune_export() -> str:
+    """The process-wide autotuner cache as text (one entry per line)."""
+    lib = load_library()
+    n = ct.c_size_t()
+    lib.jk_tune_export(None, 0, ct.byref(n))
+    buf = ct.create_string_buffer(n.value + 1)
+    lib.jk_tune_export(buf, n.value + 1, ct.byref(n))
+    return buf.value.decode()
+
+
+def tune_import(text: str):
+    """Merge cache entries produced by tune_export (raises on a bad line)."""
+    st = load_library().jk_tune_import(text.encode())
+    if st != JK_OK:
+        raise JKError(st, "malformed autotuner cache text")
+
+
+def tune_clear():
+    load_library().jk_tune_clear()
+

@@ -147,3 +147,28 @@ def test_fp64_batched_uneven_vs_oracle(eng):
     for m, (J, K) in zip(mols, outs):
         Jo, Ko = oracle.build(m.L, m.X, m.Y)
         assert rel_err(to_np(J), Jo) < FP64_REL and rel_err(to_np(K), Ko) < FP64_REL
+
+
+@pytest.mark.parametrize("precision", ["fp64", "split"])
+def test_outputs_at_odd_offsets(eng, precision):
+    """Outputs need only double alignment: odd nbf makes every other density's
+    J_s, K_s start 8 bytes off a 16-byte boundary (batched), and a single
+    build may write into a view that starts one double into a buffer."""
+    mols = _mols([(37, 80, [3, 4, 2], [False, True, False]), (21, 40, [2, 2], [False, False])], seed0=60)
+    args = [(*_gpu(m), m.sym) for m in mols]
+    outs = eng.build_batched(args, precision)
+    eng.sync_status()
+    tol = (lambda a, b: rel_err(a, b) < FP64_REL) if precision == "fp64" else (lambda a, b: abs_err(a, b) < SPLIT_ABS)
+    for m, (J, K) in zip(mols, outs):
+        Jo, Ko = oracle.build(m.L, m.X, m.Y)
+        assert tol(to_np(J), Jo) and tol(to_np(K), Ko)
+    m = mols[0]
+    L, X, Y = _gpu(m)
+    buf = torch.full((2 * m.nd * m.n * m.n + 1,), float("nan"), dtype=torch.float64, device="cuda")
+    J = buf[1:1 + m.nd * m.n * m.n].view(m.nd, m.n, m.n)
+    K = buf[1 + m.nd * m.n * m.n:].view(m.nd, m.n, m.n)
+    eng.build(L, X, Y, m.sym, precision, J=J, K=K)
+    eng.sync_status()
+    Jo, Ko = oracle.build(m.L, m.X, m.Y)
+    assert tol(to_np(J), Jo) and tol(to_np(K), Ko)
+    assert torch.isnan(buf[0])

@@ -206,9 +206,12 @@ def test_errors_are_reported_before_launch(eng):
     # arena too small -> OOM, outputs untouched
     st = lib.jk_build(h, ct.byref(f), 1, d, ct.c_void_p(J.data_ptr()), None, jk.JK_FP64, None)
     assert st == jk.JK_ERR_OOM and b"arena" in lib.jk_last_error(h)
-    # misaligned output
-    st = lib.jk_build(h, ct.byref(f), 1, d, ct.c_void_p(J.data_ptr() + 8), None, jk.JK_FP64, None)
-    assert st == jk.JK_ERR_ARG
+    # output not aligned to a double; input not aligned to 16 bytes
+    st = lib.jk_build(h, ct.byref(f), 1, d, ct.c_void_p(J.data_ptr() + 4), None, jk.JK_FP64, None)
+    assert st == jk.JK_ERR_ARG and b"aligned" in lib.jk_last_error(h)
+    f8 = jk.jk_factor(30, 20, L.data_ptr() + 8)
+    st = lib.jk_build(h, ct.byref(f8), 1, d, ct.c_void_p(J.data_ptr()), None, jk.JK_FP64, None)
+    assert st == jk.JK_ERR_ARG and b"aligned" in lib.jk_last_error(h)
     # host pointer as factor
     hostL = np.zeros(30 * 30 * 20)
     f2 = jk.jk_factor(30, 20, hostL.ctypes.data)

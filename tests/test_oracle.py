@@ -87,6 +87,26 @@ def test_sampled_matches_full():
     assert rel(Ks, K[s, mu, nu]) < 1e-14
 
 
+@pytest.mark.parametrize("withW,withV", [(True, True), (True, False), (False, True)])
+def test_sampled_adjoint_matches_full(withW, withV):
+    """The entry-by-entry adjoint evaluates the same formulas as the full one
+    in a different order (right to left per entry); the full adjoint is pinned
+    by finite differences below."""
+    n, naux = 11, 7
+    m = inputs.custom(n, naux, 3.0, [3, 4], [False, True])
+    rng = np.random.default_rng(9)
+    W = [rng.standard_normal((n, n)) for _ in range(2)] if withW else None
+    V = [rng.standard_normal((n, n)) for _ in range(2)] if withV else None
+    dX, dY, dL = oracle.adjoint(m.L, m.X, m.Y, W, V)
+    s = rng.integers(0, 2, 30); mu = rng.integers(0, n, 30); i = rng.integers(0, 3, 30)
+    P = rng.integers(0, naux, 30); a = rng.integers(0, n, 30); b = rng.integers(0, n, 30)
+    sx, sy, sl = oracle.adjoint_sample(m.L, m.X, m.Y, W, V, (s, mu, i), (P, a, b))
+    ex = np.array([dX[q][mu_, i_] for q, mu_, i_ in zip(s, mu, i)])
+    ey = np.array([dY[q][mu_, i_] for q, mu_, i_ in zip(s, mu, i)])
+    assert rel(sx, ex) < 1e-14 and rel(sy, ey) < 1e-14
+    assert rel(sl, dL[P, a, b]) < 1e-14
+
+
 # ----------------------------------------------------------- closed forms
 
 def test_rank_one_factor():
