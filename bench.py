@@ -53,12 +53,14 @@ def build_flops(n, naux, ks, sym):
 
 # DRAM bytes of the sliced GEMM measured by ncu (dram__bytes_read.sum +
 # dram__bytes_write.sum) on the profile case (nbf=400, naux=600, 8 densities
-# k=40; summary in profiles/ozgemm_tcgen05_profile_case.md): the panel launch
-# moved 2.289 GB for 600 aux indices and the rank update of one density set
-# 0.126 GB per operand for 600 aux indices.  Both grow in proportion to naux,
-# which is how they are scaled to the full multi-state launches.
-OZ_PANEL_BYTES_PER_P = 2.289e9 / 600
-OZ_RANK_BYTES_PER_P_OPERAND = 0.126e9 / 600
+# k=40; summary in profiles/ozgemm_tcgen05_profile_case.md) in the tuned
+# configuration (one aux chunk, grouped schedule: one panel launch and one
+# rank-update launch per build): the panel launch moved 2.268 GB and the
+# grouped rank-update launch 2.029 GB for 600 aux indices.  Both grow in
+# proportion to naux, which is how they are scaled to the full multi-state
+# launches.
+OZ_PANEL_BYTES_PER_P = 2.268e9 / 600
+OZ_RANK_BYTES_PER_P = 2.029e9 / 600
 
 
 def panel_rank_flops(n, naux, ks, sym):
@@ -229,7 +231,12 @@ def run_ours(args, rank, world, local):
     # autotune (untimed): the fastest run-time configuration for this shape is
     # cached and every build below uses it
     tuned = None
-    if args.tune:
+    if args.config:
+        # a fixed configuration (for profiling runs): no tuning
+        for name, v in zip(("aux_chunk", "schedule", "raster", "cluster"), args.config.split(",")):
+            eng.set_option(name, int(v))
+        tuned = {"fixed": args.config}
+    elif args.tune:
         cfg, tms = eng.autotune(Ld, Xd, Yd, sym, prec, reps=1 if prec == "fp64" else 2)
         tuned = dict(cfg, ms=tms)
     # warm-up (also sizes the arena)
@@ -318,8 +325,7 @@ def run_ours(args, rank, world, local):
         pk = peaks.get("bf16_tflops_sustained")
         traffic = None
         if args.case == "multi_state":
-            operands = sum(1 if s_ else 2 for s_ in sym)
-            per_step = OZ_PANEL_BYTES_PER_P * naux + OZ_RANK_BYTES_PER_P_OPERAND * naux * operands
+            per_step = (OZ_PANEL_BYTES_PER_P + OZ_RANK_BYTES_PER_P) * naux
             traffic = per_step * args.steps / top_cnt
         achieved = issued / (top_ms * 1e-3) / 1e12 if issued else None
         alg = panel_rank_flops(n, naux, ks, sym) * args.steps
@@ -367,6 +373,8 @@ def main():
                     help="profile: nbf=400, naux=600 variant for ncu captures")
     ap.add_argument("--no-tune", dest="tune", action="store_false",
                     help="skip the autotuner (default configuration)")
+    ap.add_argument("--config", default="",
+                    help="fixed run-time configuration aux_chunk,schedule,raster,cluster (skips the autotuner)")
     ap.add_argument("--quick", action="store_true",
                     help="device-resident timing only (no e2e, no CPU baseline)")
     args = ap.parse_args()

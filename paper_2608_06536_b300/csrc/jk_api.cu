@@ -88,11 +88,14 @@ static jk_status make_problem(jk_ctx *h, const jk_factor *f, int nd,
 
 static size_t flags_bytes() { return align_up(sizeof(DeviceFlags)); }
 
+// Without a tuned entry: one CTA per tile (clusters are a tuning candidate).
+constexpr int kDefaultCluster = 0;
+
 // Effective run-time configuration of a call: the tuned entry of its shape
 // bucket (when allowed), overridden by options set explicitly on the handle.
 static jk_tune_config resolve_config(const jk_ctx *h, jk_op op, jk_precision p, int sms, int nmol,
                                      const Problem *pbs) {
-    jk_tune_config c{0, 0, 0};
+    jk_tune_config c{0, 0, 0, kDefaultCluster};
     if (!h || h->use_tuned) {
         jk_tune_config t;
         if (tune_lookup(tune_key(op, p, sms, nmol, pbs), t)) c = t;
@@ -101,6 +104,7 @@ static jk_tune_config resolve_config(const jk_ctx *h, jk_op op, jk_precision p, 
         if (h->aux_chunk >= 0) c.aux_chunk = h->aux_chunk;
         if (h->schedule >= 0) c.schedule = h->schedule;
         if (h->raster >= 0) c.raster = h->raster;
+        if (h->cluster >= 0) c.cluster = h->cluster;
     }
     return c;
 }
@@ -343,7 +347,8 @@ static jk_status query_impl(const jk_ctx *h, jk_op op, int32_t nmol, const jk_fa
     } else {
         return JK_ERR_ARG;
     }
-    const jk_tune_config cfgs[2] = {resolve_config(h, op, p, sms, nmol, pbs.data()), jk_tune_config{0, 0, 0}};
+    const jk_tune_config cfgs[2] = {resolve_config(h, op, p, sms, nmol, pbs.data()),
+                                    jk_tune_config{0, 0, 0, kDefaultCluster}};
     for (int v = 0; v < (h ? 1 : 2); v++) {
         for (auto &pb : pbs) apply_config(pb, cfgs[v]);
         size_t b = op == JK_OP_BATCHED ? batched_bytes(nmol, pbs.data(), p)
@@ -384,6 +389,7 @@ jk_status jk_build(jk_handle h, const jk_factor *f, int32_t nd, const jk_density
     const jk_tune_config c = resolve_config(h, JK_OP_BUILD, p, h->num_sms, 1, &pb);
     apply_config(pb, c);
     h->cur_raster = c.raster;
+    h->cur_cluster = c.cluster;
     if (h->arena.bytes < flags_bytes() + build_bytes(pb, p))
         return set_error(h, JK_ERR_OOM, "arena has %zu bytes, this build needs %zu",
                          h->arena.bytes, flags_bytes() + build_bytes(pb, p));
@@ -404,6 +410,7 @@ jk_status jk_build_batched(jk_handle h, int32_t nmol, const jk_factor *f,
     const jk_tune_config c = resolve_config(h, JK_OP_BATCHED, p, h->num_sms, nmol, pbs.data());
     for (auto &pb : pbs) apply_config(pb, c);
     h->cur_raster = c.raster;
+    h->cur_cluster = c.cluster;
     if (h->arena.bytes < flags_bytes() + batched_bytes(nmol, pbs.data(), p))
         return set_error(h, JK_ERR_OOM, "arena has %zu bytes, this batched build needs %zu", h->arena.bytes,
                          flags_bytes() + batched_bytes(nmol, pbs.data(), p));
@@ -427,7 +434,9 @@ jk_status jk_autotune(jk_handle h, const jk_factor *f, int32_t nd, const jk_dens
     std::vector<jk_tune_config> cands;
     for (int ch : chunk_candidates(pc0, pb.naux))
         for (int sc = 0; sc < (p == JK_FP64 ? 1 : 2); sc++)
-            for (int ra = 0; ra < (p == JK_FP64 ? 1 : 2); ra++) cands.push_back(jk_tune_config{ch, sc, ra});
+            for (int ra = 0; ra < (p == JK_FP64 ? 1 : 2); ra++)
+                for (int cl = 0; cl < (p == JK_FP64 ? 1 : 2); cl++)
+                    cands.push_back(jk_tune_config{ch, sc, ra, p == JK_FP64 ? kDefaultCluster : cl});
     auto fits = [&](const jk_tune_config &c) {
         Problem q = pb;
         apply_config(q, c);
@@ -437,9 +446,10 @@ jk_status jk_autotune(jk_handle h, const jk_factor *f, int32_t nd, const jk_dens
         Problem q = pb;
         apply_config(q, c);
         h->cur_raster = c.raster;
+        h->cur_cluster = c.cluster;
         return run_build(h, q, p, st);
     };
-    jk_tune_config bc{0, 0, 0};
+    jk_tune_config bc{0, 0, 0, kDefaultCluster};
     double bms = 0.0;
     JK_TRY(time_candidates(h, cands, reps, st, fits, run, bc, bms));
     tune_store(tune_key(JK_OP_BUILD, p, h->num_sms, 1, &pb), bc, bms);
@@ -470,7 +480,9 @@ jk_status jk_autotune_batched(jk_handle h, int32_t nmol, const jk_factor *f,
     }
     std::vector<jk_tune_config> cands;
     for (int ch : chunk_candidates(pc0, naux_max))
-        for (int ra = 0; ra < (p == JK_FP64 ? 1 : 2); ra++) cands.push_back(jk_tune_config{ch, 1, ra});
+        for (int ra = 0; ra < (p == JK_FP64 ? 1 : 2); ra++)
+            for (int cl = 0; cl < (p == JK_FP64 ? 1 : 2); cl++)
+                cands.push_back(jk_tune_config{ch, 1, ra, p == JK_FP64 ? kDefaultCluster : cl});
     auto fits = [&](const jk_tune_config &c) {
         std::vector<Problem> q = pbs;
         for (auto &pb : q) apply_config(pb, c);
@@ -480,9 +492,10 @@ jk_status jk_autotune_batched(jk_handle h, int32_t nmol, const jk_factor *f,
         std::vector<Problem> q = pbs;
         for (auto &pb : q) apply_config(pb, c);
         h->cur_raster = c.raster;
+        h->cur_cluster = c.cluster;
         return batched_build(h, nmol, q.data(), p, st);
     };
-    jk_tune_config bc{0, 1, 0};
+    jk_tune_config bc{0, 1, 0, kDefaultCluster};
     double bms = 0.0;
     JK_TRY(time_candidates(h, cands, reps, st, fits, run, bc, bms));
     tune_store(tune_key(JK_OP_BATCHED, p, h->num_sms, nmol, pbs.data()), bc, bms);
@@ -525,6 +538,7 @@ jk_status jk_adjoint(jk_handle h, const jk_factor *f, int32_t nd, const jk_densi
     JK_TRY(make_problem(h, f, nd, d, true, pb));
     if (h->aux_chunk >= 0) pb.aux_chunk = h->aux_chunk;
     h->cur_raster = h->raster >= 0 ? h->raster : 0;
+    h->cur_cluster = h->cluster >= 0 ? h->cluster : kDefaultCluster;
     if (!dX || !dY) return set_error(h, JK_ERR_ARG, "dX and dY are required");
     JK_TRY(check_out(h, dX, "dX"));
     JK_TRY(check_out(h, dY, "dY"));
@@ -547,9 +561,10 @@ jk_status jk_set_option(jk_handle h, jk_option opt, int64_t value) {
         h->aux_chunk = static_cast<int>(value);
         return JK_OK;
     }
-    if (opt == JK_OPT_SCHEDULE || opt == JK_OPT_RASTER) {
+    if (opt == JK_OPT_SCHEDULE || opt == JK_OPT_RASTER || opt == JK_OPT_CLUSTER) {
         if (value < -1 || value > 1) return set_error(h, JK_ERR_ARG, "option %d takes -1, 0 or 1", (int)opt);
-        (opt == JK_OPT_SCHEDULE ? h->schedule : h->raster) = static_cast<int>(value);
+        (opt == JK_OPT_SCHEDULE ? h->schedule : opt == JK_OPT_RASTER ? h->raster : h->cluster) =
+            static_cast<int>(value);
         return JK_OK;
     }
     if (opt == JK_OPT_USE_TUNED) {

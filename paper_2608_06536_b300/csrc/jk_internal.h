@@ -69,8 +69,11 @@ struct jk_ctx {
     int aux_chunk = -1;      // explicit options (JK_OPT_*); -1 = not set
     int schedule = -1;
     int raster = -1;
+    int cluster = -1;
     int use_tuned = 1;
     int cur_raster = 0;      // tile order in effect for the running call
+    int cur_cluster = 0;     // 2-CTA clustered sliced GEMM in effect for the running call
+    int max_clusters = 0;    // resident 2-CTA clusters of the sliced GEMM (0 = not yet queried)
     jk::Profiler prof;
 };
 

@@ -351,6 +351,15 @@ __host__ __device__ constexpr unsigned ws_mask(int r) {
     return (ws_r(0, r) ? 1u : 0u) | (ws_r(1, r) ? 2u : 0u) | (ws_r(2, r) ? 4u : 0u) | (ws_r(3, r) ? 8u : 0u);
 }
 __host__ __device__ constexpr unsigned we_mask(int r) { return ws_mask((r + 1) % WPERIOD); }
+// The same masks as 16 nibbles of one constant, for run-time r.
+__host__ __device__ constexpr unsigned long long ws_table() {
+    unsigned long long t = 0;
+    for (int r = 0; r < WPERIOD; r++) t |= static_cast<unsigned long long>(ws_mask(r)) << (4 * r);
+    return t;
+}
+static_assert(WPERIOD == 16, "one nibble per residue");
+__device__ __forceinline__ unsigned ws_mask_rt(int r) { return static_cast<unsigned>(ws_table() >> (4 * r)) & 0xFu; }
+__device__ __forceinline__ unsigned we_mask_rt(int r) { return ws_mask_rt((r + 1) & (WPERIOD - 1)); }
 
 // The 21 slice pairs as 10 merged MMAs: A slice a times B slices b0..b0+nb-1
 // into accumulators d0..d0+nb-1 (d = a + b).  Ordered so that MMAs touching
@@ -371,15 +380,18 @@ __host__ __device__ constexpr int drain_acc(int j) { return j == 0 ? 4 : j == 1 
 // descriptor tables (and stays capturable in a CUDA graph).
 struct OzProb {
     CUtensorMap tmA, tmB, tmC;
+    CUtensorMap tmS;    // clustered launches: three slice planes of the shared operand
     OzArgs a;
-    int tile0;          // first launch-wide tile index of this problem
-    int ntn, ntm;
+    int tile0;          // first launch-wide work unit of this problem
+    int ntn, ntm;       // output tiles along N and M
+    int un, um;         // work units along N and M (tiles, or tile pairs along pair_n ? N : M)
+    int pair_n;         // clustered: the two CTAs take adjacent n-tiles (share A) or m-tiles (share B)
 };
 constexpr int MAXG = 32;
 struct OzGroup {
     OzProb p[MAXG];
     int nprob;
-    int ntiles;
+    int nunits;         // work units of the launch (tiles, or tile pairs for 2-CTA clusters)
     int raster;         // 0: n-tile fastest, 1: m-tile fastest
 };
 
@@ -389,23 +401,37 @@ __device__ __forceinline__ int prob_of(const OzGroup &g, int t) {
     return i;
 }
 
-// Tile t of a problem: raster 0 runs the n-tiles of one A row block side by
-// side (they share the A tile in L2), raster 1 the m-tiles of one B column
-// block; the split-K super-chunk z varies slowest.
+// Work unit u of a problem: raster 0 runs the n-units of one A row block side
+// by side (they share the A tile in L2), raster 1 the m-units of one B column
+// block; the split-K super-chunk z varies slowest.  In a 2-CTA cluster a unit
+// is a pair of tiles, adjacent along N (pair_n: both need the same A tile) or
+// along M (both need the same B tile); CTA rank r takes tile 2i + r.  A pair
+// member past the last tile (odd tile count) is virtual: it loads its half of
+// the shared operand for its partner and stores nothing.
 struct TileCoord {
     int n, m, z, kbeg, nkb;
+    bool virt;
 };
 
-__device__ __forceinline__ TileCoord tile_of(int t, int ntn, int ntm, int K, int raster) {
+__device__ __forceinline__ TileCoord tile_of(const OzProb &pr, int u, int raster, bool cl, int crank) {
     TileCoord c;
+    int cn, cm;
     if (raster == 0) {
-        c.n = t % ntn;
-        c.m = (t / ntn) % ntm;
+        cn = u % pr.un;
+        cm = (u / pr.un) % pr.um;
     } else {
-        c.m = t % ntm;
-        c.n = (t / ntm) % ntn;
+        cm = u % pr.um;
+        cn = (u / pr.um) % pr.un;
     }
-    c.z = t / (ntn * ntm);
+    c.n = cn;
+    c.m = cm;
+    if (cl) {
+        if (pr.pair_n) c.n = 2 * cn + crank;
+        else c.m = 2 * cm + crank;
+    }
+    c.virt = c.n >= pr.ntn || c.m >= pr.ntm;
+    c.z = u / (pr.un * pr.um);
+    const int K = pr.a.K;
     c.kbeg = c.z * SUPER;
     const int kend = min(K, c.kbeg + SUPER);
     c.nkb = (kend - c.kbeg + KB - 1) / KB;
@@ -414,8 +440,18 @@ __device__ __forceinline__ TileCoord tile_of(int t, int ntn, int ntm, int K, int
 
 // Persistent, warp-specialized sliced GEMM.  Warp 0 streams operand stages
 // with TMA, warp 1 issues the 21 slice-pair MMAs per stage, warps 2..9 drain
-// the five TMEM accumulators after every 128-element window into int64
-// registers and write the finished tile while the next tile's MMAs run.
+// the six TMEM accumulators after every window into int64 registers and write
+// the finished tile while the next tile's MMAs run.
+//
+// CL = true: 2-CTA clusters.  The two CTAs compute tiles that share one
+// operand tile; each loads three of its six slice planes once and multicasts
+// them into both CTAs, which halves that operand's TMA traffic (the kernel is
+// bound by the TMA's row rate on 32-byte rows).  A stage is refilled only
+// after both CTAs' MMAs have read it: each MMA issuer's commit arrives on the
+// stage's empty barrier in both CTAs.
+constexpr int A_HALF = A_BYTES / 2, B_HALF = B_BYTES / 2;
+
+template <bool CL>
 __global__ void __launch_bounds__(THREADS, 1)
 ozgemm_kernel(const __grid_constant__ OzGroup g) {
     extern __shared__ uint8_t smem_raw[];
@@ -429,10 +465,13 @@ ozgemm_kernel(const __grid_constant__ OzGroup g) {
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int ntiles = g.ntiles;
+    const int nunits = g.nunits;
+    const int crank = CL ? static_cast<int>(tc::cluster_ctarank()) : 0;
+    const int u0 = CL ? static_cast<int>(tc::cluster_id_x()) : static_cast<int>(blockIdx.x);
+    const int ustep = CL ? static_cast<int>(tc::cluster_count_x()) : static_cast<int>(gridDim.x);
 
     if (threadIdx.x == 0) {
-        for (int i = 0; i < NSTAGE; i++) { tc::mbar_init(&full[i], 1); tc::mbar_init(&empty[i], 1); }
+        for (int i = 0; i < NSTAGE; i++) { tc::mbar_init(&full[i], 1); tc::mbar_init(&empty[i], CL ? 2 : 1); }
         for (int i = 0; i < NACC; i++) { tc::mbar_init(&accfull[i], 1); tc::mbar_init(&accempty[i], 8); }
         *abort_flag = 0;
         tc::fence_barrier_init();
@@ -443,6 +482,8 @@ ozgemm_kernel(const __grid_constant__ OzGroup g) {
     }
     tc::fence_before_sync();
     __syncthreads();
+    // the peer's barriers must be initialized before anything is multicast into it
+    if (CL) tc::cluster_sync();
     tc::fence_after_sync();
     const uint32_t tmem = *tmem_slot;
 
@@ -453,24 +494,48 @@ ozgemm_kernel(const __grid_constant__ OzGroup g) {
             int stage = 0;
             uint32_t phase = 0;
             bool ok = true;
-            for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-                const int pi = prob_of(g, t);
+            for (int u = u0; u < nunits && ok; u += ustep) {
+                const int pi = prob_of(g, u);
                 const OzProb &pr = g.p[pi];
                 if (pi != last) {
                     tc::prefetch_tmap(&pr.tmA);
                     tc::prefetch_tmap(&pr.tmB);
+                    if (CL) tc::prefetch_tmap(&pr.tmS);
                     last = pi;
                 }
-                const TileCoord tc_ = tile_of(t - pr.tile0, pr.ntn, pr.ntm, pr.a.K, g.raster);
+                const TileCoord tc_ = tile_of(pr, u - pr.tile0, g.raster, CL, crank);
+                // bytes landing in this CTA per stage: both operands, less the
+                // unshared one when this CTA's tile is virtual
+                const uint32_t own = pr.pair_n ? B_BYTES : A_BYTES;
+                const uint32_t bytes = STAGE_BYTES - (tc_.virt ? own : 0u);
                 for (int kb = 0; kb < tc_.nkb; kb++) {
                     if (!tc::mbar_wait(&empty[stage], phase ^ 1u, abort_flag)) { ok = false; break; }
-                    tc::mbar_expect_tx(&full[stage], STAGE_BYTES);
                     const int kc = tc_.kbeg + kb * KB;
                     uint8_t *sa = smem + stage * STAGE_BYTES;
-                    tc::tma_load_3d(sa, &pr.tmA, &full[stage], kc, tc_.m * BM, 0);
-                    tc::tma_load_3d(sa + A_BYTES, &pr.tmB, &full[stage], kc, tc_.n * BN, 0);
+                    if (!CL) {
+                        tc::mbar_expect_tx(&full[stage], STAGE_BYTES);
+                        tc::tma_load_3d(sa, &pr.tmA, &full[stage], kc, tc_.m * BM, 0);
+                        tc::tma_load_3d(sa + A_BYTES, &pr.tmB, &full[stage], kc, tc_.n * BN, 0);
+                    } else {
+                        tc::mbar_expect_tx(&full[stage], bytes);
+                        if (pr.pair_n) {
+                            tc::tma_load_3d_mc(sa + crank * A_HALF, &pr.tmS, &full[stage], kc, tc_.m * BM,
+                                               3 * crank, 0x3);
+                            if (!tc_.virt) tc::tma_load_3d(sa + A_BYTES, &pr.tmB, &full[stage], kc, tc_.n * BN, 0);
+                        } else {
+                            tc::tma_load_3d_mc(sa + A_BYTES + crank * B_HALF, &pr.tmS, &full[stage], kc,
+                                               tc_.n * BN, 3 * crank, 0x3);
+                            if (!tc_.virt) tc::tma_load_3d(sa, &pr.tmA, &full[stage], kc, tc_.m * BM, 0);
+                        }
+                    }
                     if (++stage == NSTAGE) { stage = 0; phase ^= 1u; }
                 }
+            }
+            // Tail: wait until the last fill of every stage has been consumed by
+            // both CTAs, so no arrival from the peer is still on its way here.
+            for (int i = 0; i < NSTAGE && ok; i++) {
+                if (!tc::mbar_wait(&empty[stage], phase ^ 1u, abort_flag)) break;
+                if (++stage == NSTAGE) { stage = 0; phase ^= 1u; }
             }
         }
     } else if (warp == 1) {
@@ -480,19 +545,23 @@ ozgemm_kernel(const __grid_constant__ OzGroup g) {
             uint32_t phase = 0;
             int wcnt[NACC] = {0, 0, 0, 0, 0, 0};   // windows started per accumulator
             bool ok = true;
-            for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-                const OzProb &pr = g.p[prob_of(g, t)];
-                const TileCoord tc_ = tile_of(t - pr.tile0, pr.ntn, pr.ntm, pr.a.K, g.raster);
+            for (int u = u0; u < nunits && ok; u += ustep) {
+                const OzProb &pr = g.p[prob_of(g, u)];
+                const TileCoord tc_ = tile_of(pr, u - pr.tile0, g.raster, CL, crank);
                 for (int kb0 = 0; kb0 < tc_.nkb && ok; kb0 += WPERIOD) {
                     // Unrolled over one window period: the window bookkeeping below is
-                    // compile-time except for the tile's first and last K-block.
+                    // compile-time except for the tile's first and last K-block.  The
+                    // waits' polling loops are out of line, which keeps this single
+                    // thread's code small enough for the instruction cache.
 #pragma unroll
                     for (int r = 0; r < WPERIOD; r++) {
                         const int kb = kb0 + r;
                         if (kb >= tc_.nkb) break;
                         if (!tc::mbar_wait(&full[stage], phase, abort_flag)) { ok = false; break; }
                         tc::fence_after_sync();
-                        unsigned pend = ws_mask(r) | (kb == 0 ? 0x3Fu : 0u);
+                        // window starts are compile-time per r; the tile start (r = 0 of the
+                        // first period) opens all six
+                        unsigned pend = ws_mask(r) | ((r == 0 && kb0 == 0) ? 0x3Fu : 0u);
                         const uint64_t ad0 = tc::sdesc_kmajor_sw32(tc::smem_u32(smem + stage * STAGE_BYTES));
                         const uint64_t bd0 = ad0 + static_cast<uint64_t>(A_BYTES / 16);
 #pragma unroll
@@ -519,7 +588,8 @@ ozgemm_kernel(const __grid_constant__ OzGroup g) {
                                          tc::idesc_bf16_f32(BM, BN * mma_nb(i)), 1u);
                         }
                         if (!ok) break;
-                        tc::mma_commit(&empty[stage]);
+                        if (CL) tc::mma_commit_mc(&empty[stage], 0x3);
+                        else tc::mma_commit(&empty[stage]);
                         const unsigned ends = we_mask(r) | (kb == tc_.nkb - 1 ? 0x3Fu : 0u);
 #pragma unroll
                         for (int d = 0; d < NACC; d++)
@@ -545,31 +615,33 @@ ozgemm_kernel(const __grid_constant__ OzGroup g) {
         __syncwarp();
         if (lane == 0)
             for (int d = 0; d < NACC; d++) tc::mbar_arrive(&accempty[d]);
-        int ecnt[NACC] = {0, 0, 0, 0, 0, 0};
+        uint32_t epar = 0;   // bit d: parity of the windows drained from accumulator d
         bool ok = true;
-        for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+        for (int u = u0; u < nunits && ok; u += ustep) {
             // Copy the tile's problem out of parameter space once: the stores
             // below go through generic pointers and would otherwise force a
             // reload of every field per element.
-            const int pi = prob_of(g, t);
+            const int pi = prob_of(g, u);
             const OzArgs a = g.p[pi].a;
             const CUtensorMap *tmC = &g.p[pi].tmC;
-            const TileCoord tc_ = tile_of(t - g.p[pi].tile0, g.p[pi].ntn, g.p[pi].ntm, a.K, g.raster);
+            const TileCoord tc_ = tile_of(g.p[pi], u - g.p[pi].tile0, g.raster, CL, crank);
             long long acc64[BN / 2];
 #pragma unroll
             for (int i = 0; i < BN / 2; i++) acc64[i] = 0;
             for (int kb = 0; kb < tc_.nkb && ok; kb++) {
-                const unsigned ends = we_mask(kb % WPERIOD) | (kb == tc_.nkb - 1 ? 0x3Fu : 0u);
+                const unsigned ends = we_mask_rt(kb & (WPERIOD - 1)) | (kb == tc_.nkb - 1 ? 0x3Fu : 0u);
                 if (!ends) continue;
-#pragma unroll
+                // one copy of the drain-and-convert code for all six accumulators
+                // (per-accumulator unrolled copies cost instruction-cache misses)
+#pragma unroll 1
                 for (int j = 0; j < NACC; j++) {
                     const int d = drain_acc(j);
                     if (!(ends & (1u << d))) continue;
-                    if (!tc::mbar_wait(&accfull[d], static_cast<uint32_t>(ecnt[d]) & 1u, abort_flag)) {
+                    if (!tc::mbar_wait(&accfull[d], (epar >> d) & 1u, abort_flag)) {
                         ok = false;
                         break;
                     }
-                    ecnt[d]++;
+                    epar ^= 1u << d;
                     __syncwarp();
                     tc::fence_after_sync();
                     float v[BN / 2];
@@ -586,23 +658,23 @@ ozgemm_kernel(const __grid_constant__ OzGroup g) {
                     // accumulators 4, 5 (spanning the tile) stay below 2^-20.  Scale to
                     // the unit and convert with one FFMA against 1.5*2^23 (exact below
                     // 2^22; the rare larger value falls back to F2I), then add into the
-                    // 2^-48 fixed point of acc64 (a high-word add for d = 0, a 32x32->64
-                    // multiply-add otherwise).  No 64-bit float conversions: those run
-                    // on the scarce FP64 pipe.
+                    // 2^-48 fixed point of acc64 (shifted by 32 - 8d for the exact
+                    // diagonals).  No 64-bit float conversions: those run on the scarce
+                    // FP64 pipe.
                     const float unit = d < 4 ? __int_as_float((127 + 16 + 8 * d) << 23) : 0x1p48f;
                     const float vmax = d < 4 ? __int_as_float((127 + 22 - 16 - 8 * d) << 23) : 0x1p-26f;
+                    const int sh = d < 4 ? 32 - 8 * d : 0;
 #pragma unroll
                     for (int i = 0; i < BN / 2; i++) {
                         int xi = __float_as_int(__fmaf_rn(v[i], unit, 12582912.0f)) - 0x4B400000;
                         if (fabsf(v[i]) > vmax) xi = __float2int_rn(v[i] * unit);
-                        if (d == 0) acc64[i] += static_cast<long long>(xi) << 32;
-                        else if (d < 4) acc64[i] += static_cast<long long>(xi) * static_cast<long long>(1 << (32 - 8 * d));
-                        else acc64[i] += static_cast<long long>(xi);
+                        acc64[i] += static_cast<long long>(static_cast<unsigned long long>(static_cast<long long>(xi)) << sh);
                     }
                 }
             }
             const int row = tc_.m * BM + q * 32 + lane;
             if (!ok) break;
+            if (tc_.virt) continue;   // a virtual pair member: accumulators drained, nothing stored
             const int c0 = tc_.n * BN + half * OUT_COLS;
             if (a.use_tma_store) {
                 // This warp's 32 x 48 block: lane = row, three swizzled 32 x 16 sub-blocks.
@@ -665,6 +737,16 @@ ozgemm_kernel(const __grid_constant__ OzGroup g) {
     }
     tc::fence_before_sync();
     __syncthreads();
+    if (CL) {
+        // Neither CTA leaves while the other may still address its shared memory.
+        tc::cluster_sync();
+        if (*abort_flag) {
+            // an abandoned pipeline may still have copies in flight: let them land
+            const unsigned long long t0 = tc::globaltimer();
+            while (tc::globaltimer() - t0 < 2000000ull) {
+            }
+        }
+    }
     if (warp == 1) {
         tc::fence_after_sync();
         tc::tmem_dealloc(tmem, 512);
@@ -722,13 +804,13 @@ EncodeTiledFn encode_fn() {
 
 // Tensor map over slices [S][rows][Kpad] (bf16), box = {16, box_rows, S}, 32-byte swizzle.
 jk_status make_slice_map(jk_ctx *h, CUtensorMap *map, const __nv_bfloat16 *base, int rows, int Kpad,
-                         int box_rows) {
+                         int box_rows, int box_planes = oz::S) {
     EncodeTiledFn fn = encode_fn();
     if (!fn) return set_error(h, JK_ERR_CUDA, "cuTensorMapEncodeTiled is unavailable");
     cuuint64_t dims[3] = {static_cast<cuuint64_t>(Kpad), static_cast<cuuint64_t>(rows),
                           static_cast<cuuint64_t>(oz::S)};
     cuuint64_t strides[2] = {static_cast<cuuint64_t>(Kpad) * 2, static_cast<cuuint64_t>(rows) * Kpad * 2};
-    cuuint32_t box[3] = {oz::KB, static_cast<cuuint32_t>(box_rows), oz::S};
+    cuuint32_t box[3] = {oz::KB, static_cast<cuuint32_t>(box_rows), static_cast<cuuint32_t>(box_planes)};
     cuuint32_t estr[3] = {1, 1, 1};
     CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<__nv_bfloat16 *>(base), dims, strides,
                     box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B,
@@ -852,42 +934,84 @@ static jk_status oz_problem(jk_ctx *h, const Sliced &A, const Sliced &B, double 
     if (ntn * ntm * a.nsuper > 0x3fffffffLL) return set_error(h, JK_ERR_SHAPE, "too many tiles");
     pr.ntn = static_cast<int>(ntn);
     pr.ntm = static_cast<int>(ntm);
-    // Issued MMA work: every tile runs all 21 slice pairs over its K-blocks.
+    pr.un = pr.ntn;
+    pr.um = pr.ntm;
+    pr.pair_n = 1;
+    if (h->cur_cluster) {
+        // Pair the tiles along the dimension that moves fewer TMA rows per K-step
+        // (shared operand halved), counting the padding of an odd tile count.
+        const double rows_n = (oz::S * oz::BM / 2 + oz::S * oz::BN) * (2.0 * ((ntn + 1) / 2) / ntn);
+        const double rows_m = (oz::S * oz::BM + oz::S * oz::BN / 2) * (2.0 * ((ntm + 1) / 2) / ntm);
+        pr.pair_n = rows_n <= rows_m ? 1 : 0;
+        if (pr.pair_n) pr.un = static_cast<int>((ntn + 1) / 2);
+        else pr.um = static_cast<int>((ntm + 1) / 2);
+        if (pr.pair_n) JK_TRY(make_slice_map(h, &pr.tmS, A.s, A.rows, A.Kpad, oz::BM, oz::S / 2));
+        else JK_TRY(make_slice_map(h, &pr.tmS, B.s, B.rows, B.Kpad, oz::BN, oz::S / 2));
+    }
+    // Issued MMA work: every tile (virtual pair members included) runs all 21
+    // slice pairs over its K-blocks.
+    const double tiles = h->cur_cluster ? 2.0 * pr.un * pr.um : static_cast<double>(ntn) * ntm;
     double kblocks = 0.0;
     for (int zz = 0; zz < a.nsuper; zz++) {
         const int kb = (a.K - zz * oz::SUPER < oz::SUPER ? a.K - zz * oz::SUPER : oz::SUPER);
         kblocks += (kb + oz::KB - 1) / oz::KB;
     }
-    h->prof.tensor_flops += 2.0 * oz::BM * oz::BN * oz::KB * oz::NPAIRS * kblocks * static_cast<double>(ntn) * ntm;
+    h->prof.tensor_flops += 2.0 * oz::BM * oz::BN * oz::KB * oz::NPAIRS * kblocks * tiles;
     return JK_OK;
 }
 
-static bool smem_configured = false;
-
 // Launch a list of problems: persistent grid, up to MAXG problems per launch.
+// Clustered (h->cur_cluster): 2-CTA clusters, as many as can be resident.
 static jk_status oz_launch(jk_ctx *h, const std::vector<oz::OzProb> &probs, cudaStream_t st) {
+    static bool smem_configured = false;
+    int &max_clusters = h->max_clusters;
     if (!smem_configured) {
-        JK_CUDA_TRY(h, cudaFuncSetAttribute(oz::ozgemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        JK_CUDA_TRY(h, cudaFuncSetAttribute(oz::ozgemm_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            oz::SMEM_BYTES));
+        JK_CUDA_TRY(h, cudaFuncSetAttribute(oz::ozgemm_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             oz::SMEM_BYTES));
         smem_configured = true;
     }
-    static thread_local oz::OzGroup grp;   // 16 KB of launch parameters, built on the host
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.blockDim = dim3(oz::THREADS);
+    cfg.dynamicSmemBytes = oz::SMEM_BYTES;
+    cfg.stream = st;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (h->cur_cluster && max_clusters == 0) {
+        cfg.gridDim = dim3(2 * h->num_sms);
+        int n = 0;
+        JK_CUDA_TRY(h, cudaOccupancyMaxActiveClusters(&n, oz::ozgemm_kernel<true>, &cfg));
+        if (n < 1) return set_error(h, JK_ERR_UNSUPPORTED, "no 2-CTA cluster of the sliced GEMM fits an SM pair");
+        max_clusters = n;
+    }
+    static thread_local oz::OzGroup grp;   // ~20 KB of launch parameters, built on the host
     for (size_t i0 = 0; i0 < probs.size(); i0 += oz::MAXG) {
         const int np = static_cast<int>(std::min<size_t>(oz::MAXG, probs.size() - i0));
-        long long tiles = 0;
+        long long units = 0;
         for (int i = 0; i < np; i++) {
             grp.p[i] = probs[i0 + i];
-            grp.p[i].tile0 = static_cast<int>(tiles);
-            tiles += static_cast<long long>(grp.p[i].ntn) * grp.p[i].ntm * grp.p[i].a.nsuper;
+            grp.p[i].tile0 = static_cast<int>(units);
+            units += static_cast<long long>(grp.p[i].un) * grp.p[i].um * grp.p[i].a.nsuper;
         }
-        if (tiles > 0x7fffffffLL) return set_error(h, JK_ERR_SHAPE, "too many tiles in one launch");
+        if (units > 0x7fffffffLL) return set_error(h, JK_ERR_SHAPE, "too many tiles in one launch");
         grp.nprob = np;
-        grp.ntiles = static_cast<int>(tiles);
+        grp.nunits = static_cast<int>(units);
         grp.raster = h->cur_raster;
-        const int grid = static_cast<int>(tiles < h->num_sms ? tiles : h->num_sms);
-        {
+        if (h->cur_cluster) {
+            const long long ncl = units < max_clusters ? units : max_clusters;
+            cfg.gridDim = dim3(static_cast<unsigned>(2 * ncl));
             LaunchScope ls(h, KK_OZGEMM, st);
-            oz::ozgemm_kernel<<<grid, oz::THREADS, oz::SMEM_BYTES, st>>>(grp);
+            JK_CUDA_TRY(h, cudaLaunchKernelEx(&cfg, oz::ozgemm_kernel<true>, grp));
+        } else {
+            const int grid = static_cast<int>(units < h->num_sms ? units : h->num_sms);
+            LaunchScope ls(h, KK_OZGEMM, st);
+            oz::ozgemm_kernel<false><<<grid, oz::THREADS, oz::SMEM_BYTES, st>>>(grp);
         }
         JK_LAUNCH_CHECK(h);
     }
@@ -1567,6 +1691,9 @@ extern "C" jk_status jk_debug_sliced_gemm(jk_handle h, int32_t M, int32_t N, int
     if (!A || !B || !C) return set_error(h, JK_ERR_ARG, "NULL operand");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     h->arena.reset(align_up(sizeof(DeviceFlags)));
+    // tile order and clustering: the handle's explicit options, else the defaults
+    h->cur_raster = h->raster >= 0 ? h->raster : 0;
+    h->cur_cluster = h->cluster >= 0 ? h->cluster : 0;
     Sliced As, Bs;
     if (!take_sliced(h->arena, M, K, 1, As) || !take_sliced(h->arena, N, K, 1, Bs))
         return set_error(h, JK_ERR_OOM, "workspace too small");

@@ -33,13 +33,15 @@ class jk_density(ct.Structure):
 
 
 class jk_tune_config(ct.Structure):
-    _fields_ = [("aux_chunk", ct.c_int32), ("schedule", ct.c_int32), ("raster", ct.c_int32)]
+    _fields_ = [("aux_chunk", ct.c_int32), ("schedule", ct.c_int32), ("raster", ct.c_int32),
+                ("cluster", ct.c_int32)]
 
     def as_dict(self) -> dict:
-        return {"aux_chunk": self.aux_chunk, "schedule": self.schedule, "raster": self.raster}
+        return {"aux_chunk": self.aux_chunk, "schedule": self.schedule, "raster": self.raster,
+                "cluster": self.cluster}
 
 
-OPTIONS = {"aux_chunk": 0, "schedule": 1, "raster": 2, "use_tuned": 3}
+OPTIONS = {"aux_chunk": 0, "schedule": 1, "raster": 2, "use_tuned": 3, "cluster": 4}
 
 
 class JKError(RuntimeError):
