@@ -628,6 +628,17 @@ ozgemm_kernel(const __grid_constant__ OzGroup g) {
             long long acc64[BN / 2];
 #pragma unroll
             for (int i = 0; i < BN / 2; i++) acc64[i] = 0;
+            // Exponents of this warp's output rows and columns, fetched now so that
+            // their latency hides under the tile's MMAs: lane l holds the column
+            // exponents of columns l and 32 + l of its 40 (shared by shuffles).
+            const int c0 = tc_.n * BN + half * OUT_COLS;
+            const int row = tc_.m * BM + q * 32 + lane;
+            int ea = 0, eb_lo = 0, eb_hi = 0;
+            if (a.nsuper == 1) {
+                if (row < a.M) ea = a.eA[row / a.a_rpe] - FRAC;
+                if (c0 + lane < a.N) eb_lo = a.eB[(c0 + lane) / a.b_rpe];
+                if (lane < OUT_COLS - 32 && c0 + 32 + lane < a.N) eb_hi = a.eB[(c0 + 32 + lane) / a.b_rpe];
+            }
             for (int kb = 0; kb < tc_.nkb && ok; kb++) {
                 const unsigned ends = we_mask_rt(kb & (WPERIOD - 1)) | (kb == tc_.nkb - 1 ? 0x3Fu : 0u);
                 if (!ends) continue;
@@ -645,11 +656,14 @@ ozgemm_kernel(const __grid_constant__ OzGroup g) {
                     __syncwarp();
                     tc::fence_after_sync();
                     float v[BN / 2];
-#pragma unroll
-                    for (int c = 0; c < BN / 2; c += 8) tc::tmem_ld8(tlane + d * BN + c, v + c);
+                    static_assert(BN / 2 == 40, "drain shapes: 16 + 16 + 8 columns");
+                    tc::tmem_ld16(tlane + d * BN, v);
+                    tc::tmem_ld16(tlane + d * BN + 16, v + 16);
+                    tc::tmem_ld8(tlane + d * BN + 32, v + 32);
                     tc::tmem_wait_ld();
-#pragma unroll
-                    for (int c = 0; c < BN / 2; c += 8) tc::tmem_zero8(tlane + d * BN + c);
+                    tc::tmem_zero16(tlane + d * BN);
+                    tc::tmem_zero16(tlane + d * BN + 16);
+                    tc::tmem_zero8(tlane + d * BN + 32);
                     tc::tmem_wait_st();
                     tc::fence_before_sync();
                     __syncwarp();
@@ -672,16 +686,13 @@ ozgemm_kernel(const __grid_constant__ OzGroup g) {
                     }
                 }
             }
-            const int row = tc_.m * BM + q * 32 + lane;
             if (!ok) break;
             if (tc_.virt) continue;   // a virtual pair member: accumulators drained, nothing stored
-            const int c0 = tc_.n * BN + half * OUT_COLS;
             if (a.use_tma_store) {
                 // This warp's 32 x 48 block: lane = row, three swizzled 32 x 16 sub-blocks.
                 uint8_t *wbuf = outbuf + ew * OUT_WARP_BYTES;
                 if (lane == 0) tc::bulk_wait_read();   // previous tile's store has read the buffer
                 __syncwarp();
-                const int ea = a.nsuper == 1 && row < a.M ? a.eA[row / a.a_rpe] - FRAC : 0;   // z = 0
 #pragma unroll
                 for (int b = 0; b < OUT_COLS / OUT_BLK; b++) {
                     uint8_t *blk = wbuf + b * (32 * OUT_BLK * 8);
@@ -691,8 +702,10 @@ ozgemm_kernel(const __grid_constant__ OzGroup g) {
                         long long w0 = acc64[i0], w1 = acc64[i0 + 1];
                         if (a.nsuper == 1) {
                             const int col = c0 + i0;
-                            const double d0 = col < a.N && row < a.M ? i64_to_f64_scaled(w0, ea + a.eB[col / a.b_rpe]) : 0.0;
-                            const double d1 = col + 1 < a.N && row < a.M ? i64_to_f64_scaled(w1, ea + a.eB[(col + 1) / a.b_rpe]) : 0.0;
+                            const int eb0 = __shfl_sync(0xffffffffu, i0 < 32 ? eb_lo : eb_hi, i0 & 31);
+                            const int eb1 = __shfl_sync(0xffffffffu, i0 + 1 < 32 ? eb_lo : eb_hi, (i0 + 1) & 31);
+                            const double d0 = col < a.N && row < a.M ? i64_to_f64_scaled(w0, ea + eb0) : 0.0;
+                            const double d1 = col + 1 < a.N && row < a.M ? i64_to_f64_scaled(w1, ea + eb1) : 0.0;
                             w0 = __double_as_longlong(d0);
                             w1 = __double_as_longlong(d1);
                         }
