@@ -289,24 +289,24 @@ def run_ours(args, rank, world, local):
     h2d = Lh.numel() * 8 + sum(x.numel() * 8 for x in Xh) + sum(y.numel() * 8 for y, s in zip(Yh, sym) if not s)
     d2h = (Jh.numel() + Kh.numel()) * 8
     e2e_steps = max(1, min(args.steps, 3))
+    # jk_build_host: the library streams the factor to the device in aux chunks
+    # on its own copy stream, overlapped with the build of the previous chunk;
+    # densities up and J, K down on the caller's stream.  One untimed call sizes
+    # the arena.
+    eng.build_host(Lh, Xh, Yh, sym, prec, J=Jh, K=Kh, stream=st)
     barrier(world)
     torch.cuda.synchronize(dev)
     e0.record(st)
     for _ in range(e2e_steps):
-        Ld.copy_(Lh, non_blocking=True)
-        for a, b in zip(Xd, Xh):
-            a.copy_(b, non_blocking=True)
-        for a, b, s in zip(Yd, Yh, sym):
-            if not s:
-                a.copy_(b, non_blocking=True)
-        J, K = eng.build(Ld, Xd, Yd, sym, prec, J=J, K=K)
-        Jh.copy_(J, non_blocking=True)
-        Kh.copy_(K, non_blocking=True)
+        eng.build_host(Lh, Xh, Yh, sym, prec, J=Jh, K=Kh, stream=st, sync=False)
     e1.record(st)
     torch.cuda.synchronize(dev)
+    eng.sync_status(st)
     ms_e2e = max_over_ranks(e0.elapsed_time(e1) / e2e_steps, world, dev)
     e2e = {"value": world * flops / (ms_e2e * 1e-3) / 1e12, "unit": "TFLOP/s",
-           "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "ms_per_step": ms_e2e}
+           "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "ms_per_step": ms_e2e,
+           "path": "jk_build_host: pinned host inputs and outputs, factor streamed in aux chunks "
+                   "overlapped with the build"}
 
     # ---- roofline of the dominant kernel ------------------------------------
     peaks, peak_src = load_peaks()

@@ -83,7 +83,7 @@ typedef struct {
 } jk_density;
 
 /* Which entry point a workspace query is for. */
-typedef enum { JK_OP_BUILD = 0, JK_OP_ADJOINT = 1, JK_OP_BATCHED = 2 } jk_op;
+typedef enum { JK_OP_BUILD = 0, JK_OP_ADJOINT = 1, JK_OP_BATCHED = 2, JK_OP_BUILD_HOST = 3 } jk_op;
 
 /* Create a handle over a caller-owned device arena of `bytes` bytes
  * (256-byte aligned).  The arena must stay valid until jk_destroy. */
@@ -110,6 +110,20 @@ jk_status jk_workspace_query_handle(jk_handle h, jk_op op, int32_t nmol, const j
 jk_status jk_build(jk_handle h, const jk_factor *f, int32_t nd,
                    const jk_density *d, double *J, double *K,
                    jk_precision p, void *stream);
+
+/* jk_build_host: jk_build with every array in host memory (factor, densities
+ * and outputs; page-locked memory gives full copy speed and asynchrony).  The
+ * factor, the bulk of the input (naux x nbf^2 doubles), is streamed to the
+ * device in aux-index chunks on an internal copy stream, double-buffered and
+ * overlapped with the build of the previous chunk on `stream`; J and K are
+ * summed over the chunks in FP64 on the device (the build is linear in the
+ * aux-index range) and copied back to the host at the end.  All work is
+ * ordered on `stream` (the copy stream forks from and joins it), so the call
+ * returns before the results are in host memory: synchronize `stream` (or
+ * call jk_sync_status) before reading J, K.  Arena: jk_workspace_query with
+ * JK_OP_BUILD_HOST.  Status as jk_build; host pointers are not checked. */
+jk_status jk_build_host(jk_handle h, const jk_factor *f, int32_t nd, const jk_density *d,
+                        double *J, double *K, jk_precision p, void *stream);
 
 /* jk_build_batched: many independent molecules (uneven nbf, naux, nd) in one
  * call.  f[m] is molecule m's factor, nd_per_mol[m] its density count (host
@@ -179,8 +193,10 @@ typedef enum {
                                1 = m-tile fastest (tile order of the sliced GEMM) */
     JK_OPT_USE_TUNED = 3,   /* 1 (default) = apply autotuned configurations,
                                0 = ignore them                                    */
-    JK_OPT_CLUSTER = 4      /* -1 = tuned/default, 0 = one CTA per tile, 1 = 2-CTA
+    JK_OPT_CLUSTER = 4,     /* -1 = tuned/default, 0 = one CTA per tile, 1 = 2-CTA
                                clusters sharing an operand tile by TMA multicast  */
+    JK_OPT_HOST_CHUNK = 5   /* jk_build_host: aux indices per streamed chunk of
+                               the factor, 0 = automatic (about 12 chunks)         */
 } jk_option;
 /* Options set explicitly on a handle override tuned configurations. */
 jk_status jk_set_option(jk_handle h, jk_option opt, int64_t value);

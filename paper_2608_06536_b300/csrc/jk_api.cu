@@ -173,6 +173,175 @@ static size_t adjoint_bytes(const Problem &pb, jk_precision p, bool want_dl) {
                         : split_adjoint_workspace(pb, want_dl);
 }
 
+// ---- host-resident inputs (jk_build_host) ----------------------------------
+// The factor streams to the device in chunks of aux indices; each chunk is an
+// ordinary build over its P-range (J and K are sums over P), summed on the
+// device in FP64 in chunk order.
+
+static int host_chunk_of(const jk_ctx *h, const Problem &pb) {
+    long long c = h && h->host_chunk > 0 ? h->host_chunk : (pb.naux + 11) / 12;
+    if (c < 16) c = 16;
+    if (c > pb.naux) c = pb.naux;
+    return static_cast<int>(c);
+}
+
+// Device buffers of a host build that live across its chunks.
+struct HostBufs {
+    double *XY = nullptr;          // X_s (and Y_s) packed density by density
+    double *J = nullptr, *K = nullptr, *Jc = nullptr, *Kc = nullptr;
+    double *stage[2] = {nullptr, nullptr};
+};
+
+static size_t host_xy_count(const Problem &pb) {
+    size_t c = 0;
+    for (int s = 0; s < pb.nd; s++) c += static_cast<size_t>(pb.n) * pb.k[s] * (pb.sym[s] ? 1 : 2);
+    return c;
+}
+
+static size_t host_persist_bytes(const Problem &pb, int chunk, bool wantJ, bool wantK) {
+    const size_t nn = static_cast<size_t>(pb.nd) * pb.n * pb.n * 8;
+    return align_up(host_xy_count(pb) * 8) + (wantJ ? 2 * align_up(nn) : 0) + (wantK ? 2 * align_up(nn) : 0) +
+           2 * align_up(static_cast<size_t>(chunk) * pb.n * pb.n * 8) + 8 * kArenaAlign;
+}
+
+// The per-chunk problem: device copies of the densities, a staging factor.
+static Problem host_chunk_problem(const Problem &pb, const HostBufs &b, int np, int buf) {
+    Problem q = pb;
+    q.naux = np;
+    q.L = b.stage[buf];
+    size_t off = 0;
+    for (int s = 0; s < pb.nd; s++) {
+        const size_t cnt = static_cast<size_t>(pb.n) * pb.k[s];
+        q.X[s] = b.XY + off;
+        off += cnt;
+        if (pb.sym[s]) {
+            q.Y[s] = q.X[s];
+        } else {
+            q.Y[s] = b.XY + off;
+            off += cnt;
+        }
+    }
+    const long long n2 = static_cast<long long>(pb.n) * pb.n;
+    for (int s = 0; s < pb.nd; s++) {
+        q.J[s] = pb.wantJ ? b.Jc + s * n2 : nullptr;
+        q.K[s] = pb.wantK ? b.Kc + s * n2 : nullptr;
+    }
+    return q;
+}
+
+// Configuration of the chunk builds: tuned for the chunk shape, else the
+// grouped schedule (one launch per phase for all densities of the chunk).
+static jk_tune_config host_config(const jk_ctx *h, jk_precision p, const Problem &q) {
+    jk_tune_config c{0, 1, 0, kDefaultCluster};
+    jk_tune_config t;
+    if (h->use_tuned && tune_lookup(tune_key(JK_OP_BUILD, p, h->num_sms, 1, &q), t)) c = t;
+    if (h->aux_chunk >= 0) c.aux_chunk = h->aux_chunk;
+    if (h->schedule >= 0) c.schedule = h->schedule;
+    if (h->raster >= 0) c.raster = h->raster;
+    if (h->cluster >= 0) c.cluster = h->cluster;
+    return c;
+}
+
+static size_t host_build_bytes(const jk_ctx *h, const Problem &pb, jk_precision p) {
+    const int chunk = host_chunk_of(h, pb);
+    Problem q = pb;
+    q.naux = chunk;
+    jk_tune_config c{0, 1, 0, kDefaultCluster};
+    if (h) c = host_config(h, p, q);
+    apply_config(q, c);
+    return host_persist_bytes(pb, chunk, true, true) + build_bytes(q, p);
+}
+
+static jk_status ensure_copy_stream(jk_ctx *h) {
+    if (h->copy_stream) return JK_OK;
+    JK_CUDA_TRY(h, cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking));
+    JK_CUDA_TRY(h, cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+    for (int i = 0; i < 2; i++) {
+        JK_CUDA_TRY(h, cudaEventCreateWithFlags(&h->ev_up[i], cudaEventDisableTiming));
+        JK_CUDA_TRY(h, cudaEventCreateWithFlags(&h->ev_used[i], cudaEventDisableTiming));
+    }
+    return JK_OK;
+}
+
+static jk_status host_build(jk_ctx *h, const Problem &pb, const jk_density *d, double *J, double *K,
+                            jk_precision p, cudaStream_t st) {
+    const int n = pb.n, naux = pb.naux, nd = pb.nd;
+    const long long n2 = static_cast<long long>(n) * n;
+    const size_t nn = static_cast<size_t>(nd) * n2;
+    const int chunk = host_chunk_of(h, pb);
+    Arena &ar = h->arena;
+    HostBufs b;
+    b.XY = ar.take<double>(host_xy_count(pb));
+    bool ok = b.XY != nullptr;
+    if (pb.wantJ) {
+        b.J = ar.take<double>(nn);
+        b.Jc = ar.take<double>(nn);
+        ok = ok && b.J && b.Jc;
+    }
+    if (pb.wantK) {
+        b.K = ar.take<double>(nn);
+        b.Kc = ar.take<double>(nn);
+        ok = ok && b.K && b.Kc;
+    }
+    for (int i = 0; i < 2; i++) {
+        b.stage[i] = ar.take<double>(static_cast<size_t>(chunk) * n2);
+        ok = ok && b.stage[i];
+    }
+    if (!ok) return set_error(h, JK_ERR_OOM, "arena too small for the host build's staging buffers");
+    Problem q = host_chunk_problem(pb, b, chunk, 0);
+    const jk_tune_config cfg = host_config(h, p, q);
+    apply_config(q, cfg);
+    if (ar.off + build_bytes(q, p) > ar.bytes)
+        return set_error(h, JK_ERR_OOM, "arena has %zu bytes, this host build needs %zu", ar.bytes,
+                         ar.off + build_bytes(q, p));
+    JK_TRY(ensure_copy_stream(h));
+    h->cur_raster = cfg.raster;
+    h->cur_cluster = cfg.cluster;
+
+    // densities up, accumulators cleared (on the caller's stream)
+    size_t off = 0;
+    for (int s = 0; s < nd; s++) {
+        const size_t cnt = static_cast<size_t>(n) * pb.k[s];
+        JK_CUDA_TRY(h, cudaMemcpyAsync(b.XY + off, d[s].X, cnt * 8, cudaMemcpyHostToDevice, st));
+        off += cnt;
+        if (!pb.sym[s]) {
+            JK_CUDA_TRY(h, cudaMemcpyAsync(b.XY + off, d[s].Y, cnt * 8, cudaMemcpyHostToDevice, st));
+            off += cnt;
+        }
+    }
+    if (pb.wantJ) JK_CUDA_TRY(h, cudaMemsetAsync(b.J, 0, nn * 8, st));
+    if (pb.wantK) JK_CUDA_TRY(h, cudaMemsetAsync(b.K, 0, nn * 8, st));
+    // the copy stream forks from the caller's stream ...
+    JK_CUDA_TRY(h, cudaEventRecord(h->ev_fork, st));
+    JK_CUDA_TRY(h, cudaStreamWaitEvent(h->copy_stream, h->ev_fork, 0));
+    struct FloorGuard {
+        Arena &a;
+        ~FloorGuard() { a.floor = 0; }
+    } guard{ar};
+    ar.floor = ar.off;
+    int c = 0;
+    for (int P0 = 0; P0 < naux; P0 += chunk, c++) {
+        const int np = naux - P0 < chunk ? naux - P0 : chunk;
+        const int buf = c & 1;
+        // ... uploads chunk c once the build of chunk c - 2 has released its buffer ...
+        if (c >= 2) JK_CUDA_TRY(h, cudaStreamWaitEvent(h->copy_stream, h->ev_used[buf], 0));
+        JK_CUDA_TRY(h, cudaMemcpyAsync(b.stage[buf], pb.L + P0 * n2, static_cast<size_t>(np) * n2 * 8,
+                                       cudaMemcpyHostToDevice, h->copy_stream));
+        JK_CUDA_TRY(h, cudaEventRecord(h->ev_up[buf], h->copy_stream));
+        // ... and every chunk's build waits for its upload (which also joins the streams)
+        JK_CUDA_TRY(h, cudaStreamWaitEvent(st, h->ev_up[buf], 0));
+        Problem qc = host_chunk_problem(pb, b, np, buf);
+        apply_config(qc, cfg);
+        JK_TRY(run_build(h, qc, p, st));
+        if (pb.wantJ) JK_TRY(fp64_axpy(h, b.J, b.Jc, static_cast<long long>(nn), st));
+        if (pb.wantK) JK_TRY(fp64_axpy(h, b.K, b.Kc, static_cast<long long>(nn), st));
+        JK_CUDA_TRY(h, cudaEventRecord(h->ev_used[buf], st));
+    }
+    if (pb.wantJ) JK_CUDA_TRY(h, cudaMemcpyAsync(J, b.J, nn * 8, cudaMemcpyDeviceToHost, st));
+    if (pb.wantK) JK_CUDA_TRY(h, cudaMemcpyAsync(K, b.K, nn * 8, cudaMemcpyDeviceToHost, st));
+    return JK_OK;
+}
+
 }  // namespace jk
 
 using namespace jk;
@@ -203,6 +372,16 @@ jk_status jk_create(jk_handle *out, void *workspace, size_t bytes) {
 }
 
 jk_status jk_destroy(jk_handle h) {
+    if (!h) return JK_OK;
+    if (h->copy_stream) {
+        cudaStreamSynchronize(h->copy_stream);
+        cudaStreamDestroy(h->copy_stream);
+        cudaEventDestroy(h->ev_fork);
+        for (int i = 0; i < 2; i++) {
+            cudaEventDestroy(h->ev_up[i]);
+            cudaEventDestroy(h->ev_used[i]);
+        }
+    }
     delete h;
     return JK_OK;
 }
@@ -339,11 +518,15 @@ static jk_status query_impl(const jk_ctx *h, jk_op op, int32_t nmol, const jk_fa
             off += nd_per_mol[m];
         }
         if (off != nd) return JK_ERR_SHAPE;
-    } else if (op == JK_OP_BUILD || op == JK_OP_ADJOINT) {
+    } else if (op == JK_OP_BUILD || op == JK_OP_ADJOINT || op == JK_OP_BUILD_HOST) {
         pbs.resize(1);
         jk_status s = make_problem(nullptr, f, nd, d, false, pbs[0]);
         if (s != JK_OK) return s;
         nmol = 1;
+        if (op == JK_OP_BUILD_HOST) {
+            *bytes = host_build_bytes(h, pbs[0], p) + flags_bytes() + kArenaAlign;
+            return JK_OK;
+        }
     } else {
         return JK_ERR_ARG;
     }
@@ -394,6 +577,23 @@ jk_status jk_build(jk_handle h, const jk_factor *f, int32_t nd, const jk_density
         return set_error(h, JK_ERR_OOM, "arena has %zu bytes, this build needs %zu",
                          h->arena.bytes, flags_bytes() + build_bytes(pb, p));
     return run_build(h, pb, p, st);
+}
+
+jk_status jk_build_host(jk_handle h, const jk_factor *f, int32_t nd, const jk_density *d,
+                        double *J, double *K, jk_precision p, void *stream) {
+    JK_TRY(begin_call(h));
+    if (p != JK_FP64 && p != JK_SPLIT_BF16)
+        return set_error(h, JK_ERR_ARG, "unknown precision %d", (int)p);
+    Problem pb;
+    JK_TRY(make_problem(h, f, nd, d, false, pb));
+    if (!f->L) return set_error(h, JK_ERR_ARG, "factor L is NULL");
+    for (int s = 0; s < nd; s++)
+        if (!d[s].X || (!d[s].symmetric && !d[s].Y))
+            return set_error(h, JK_ERR_ARG, "density %d: X or Y is NULL", s);
+    if (!J && !K) return JK_OK;
+    pb.wantJ = J != nullptr;
+    pb.wantK = K != nullptr;
+    return host_build(h, pb, d, J, K, p, static_cast<cudaStream_t>(stream));
 }
 
 jk_status jk_build_batched(jk_handle h, int32_t nmol, const jk_factor *f,
@@ -565,6 +765,11 @@ jk_status jk_set_option(jk_handle h, jk_option opt, int64_t value) {
         if (value < -1 || value > 1) return set_error(h, JK_ERR_ARG, "option %d takes -1, 0 or 1", (int)opt);
         (opt == JK_OPT_SCHEDULE ? h->schedule : opt == JK_OPT_RASTER ? h->raster : h->cluster) =
             static_cast<int>(value);
+        return JK_OK;
+    }
+    if (opt == JK_OPT_HOST_CHUNK) {
+        if (value < 0 || value > (1 << 30)) return set_error(h, JK_ERR_ARG, "host chunk out of range");
+        h->host_chunk = static_cast<int>(value);
         return JK_OK;
     }
     if (opt == JK_OPT_USE_TUNED) {

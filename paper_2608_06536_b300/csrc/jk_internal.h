@@ -22,7 +22,8 @@ struct Arena {
     size_t bytes = 0;
     size_t off = 0;
     size_t high = 0;
-    void reset(size_t start) { off = start; }
+    size_t floor = 0;    // buffers below this offset outlive the inner calls that reset the arena
+    void reset(size_t start) { off = start > floor ? start : floor; }
     template <class T> T *take(size_t count) {
         size_t need = align_up(count * sizeof(T));
         if (off + need > bytes) return nullptr;
@@ -74,6 +75,9 @@ struct jk_ctx {
     int cur_raster = 0;      // tile order in effect for the running call
     int cur_cluster = 0;     // 2-CTA clustered sliced GEMM in effect for the running call
     int max_clusters = 0;    // resident 2-CTA clusters of the sliced GEMM (0 = not yet queried)
+    int host_chunk = 0;      // aux indices per streamed chunk of a host-resident factor (0 = automatic)
+    cudaStream_t copy_stream = nullptr;   // host builds: uploads of the factor, created on first use
+    cudaEvent_t ev_fork = nullptr, ev_up[2] = {nullptr, nullptr}, ev_used[2] = {nullptr, nullptr};
     jk::Profiler prof;
 };
 

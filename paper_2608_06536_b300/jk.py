@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(HERE, "libjk.so")
 
 JK_OK, JK_ERR_ARG, JK_ERR_SHAPE, JK_ERR_OOM, JK_ERR_CUDA, JK_ERR_TIMEOUT, JK_ERR_UNSUPPORTED = range(7)
 JK_FP64, JK_SPLIT_BF16 = 0, 1
-JK_OP_BUILD, JK_OP_ADJOINT, JK_OP_BATCHED = 0, 1, 2
+JK_OP_BUILD, JK_OP_ADJOINT, JK_OP_BATCHED, JK_OP_BUILD_HOST = 0, 1, 2, 3
 
 PRECISIONS = {"fp64": JK_FP64, "split": JK_SPLIT_BF16, "split_bf16": JK_SPLIT_BF16}
 
@@ -41,7 +41,7 @@ class jk_tune_config(ct.Structure):
                 "cluster": self.cluster}
 
 
-OPTIONS = {"aux_chunk": 0, "schedule": 1, "raster": 2, "use_tuned": 3, "cluster": 4}
+OPTIONS = {"aux_chunk": 0, "schedule": 1, "raster": 2, "use_tuned": 3, "cluster": 4, "host_chunk": 5}
 
 
 class JKError(RuntimeError):
@@ -71,6 +71,9 @@ def load_library(path: str = LIB_PATH):
                                          ct.POINTER(jk_density), ct.c_int, ct.POINTER(sz)]
         L.jk_build.argtypes = [vp, ct.POINTER(jk_factor), ct.c_int32, ct.POINTER(jk_density),
                                vp, vp, ct.c_int, vp]
+        L.jk_build_host.argtypes = [vp, ct.POINTER(jk_factor), ct.c_int32, ct.POINTER(jk_density),
+                                    vp, vp, ct.c_int, vp]
+        L.jk_build_host.restype = ct.c_int
         L.jk_build_batched.argtypes = [vp, ct.c_int32, ct.POINTER(jk_factor),
                                        ct.POINTER(ct.c_int32), ct.POINTER(jk_density),
                                        ct.POINTER(vp), ct.POINTER(vp), ct.c_int, vp]
@@ -130,6 +133,14 @@ def _dev_f64(t, device):
     if not t.is_contiguous() or t.data_ptr() % 16:
         t = t.contiguous().clone()
     return t
+
+
+def _host_f64(t):
+    """Contiguous float64 CPU tensor (pinned inputs keep their pinning)."""
+    t = torch.as_tensor(t, dtype=torch.float64)
+    if t.device.type != "cpu":
+        raise ValueError("build_host takes host (CPU) tensors")
+    return t.contiguous()
 
 
 def _stream_ptr(stream):
@@ -293,6 +304,40 @@ class Engine:
         self._check(st, self._h)
         return (J if want_j else None), (K if want_k else None)
 
+    def build_host(self, L, X, Y=None, sym=None, precision="split", want_j=True, want_k=True,
+                   J=None, K=None, stream=None, sync=True):
+        """J, K for host-resident inputs (CPU float64 tensors, ideally pinned):
+        the factor streams to the device chunk by chunk, overlapped with the
+        build; J, K ([nd][n][n], CPU) are written at the end of the stream's
+        work (sync=True waits for it)."""
+        p = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        L = _host_f64(L)
+        X = [_host_f64(x) for x in X]
+        nd = len(X)
+        sym = list(sym) if sym is not None else [False] * nd
+        Y = list(Y) if Y is not None else [None] * nd
+        Y = [None if (sym[s] or Y[s] is None) else _host_f64(Y[s]) for s in range(nd)]
+        symf = [sym[s] or Y[s] is None for s in range(nd)]
+        naux, n = int(L.shape[0]), int(L.shape[1])
+        f = jk_factor(n, naux, L.data_ptr())
+        dens = (jk_density * nd)()
+        for s in range(nd):
+            dens[s].k = int(X[s].shape[1])
+            dens[s].symmetric = 1 if symf[s] else 0
+            dens[s].X = X[s].data_ptr()
+            dens[s].Y = Y[s].data_ptr() if Y[s] is not None else None
+        self._ensure(self.query(JK_OP_BUILD_HOST, (jk_factor * 1)(f), dens, None, nd, p))
+        if want_j and J is None:
+            J = torch.empty((nd, n, n), dtype=torch.float64).pin_memory()
+        if want_k and K is None:
+            K = torch.empty((nd, n, n), dtype=torch.float64).pin_memory()
+        st = self.lib.jk_build_host(self._h, ct.byref(f), nd, dens, _ptr(J if want_j else None),
+                                    _ptr(K if want_k else None), p, _stream_ptr(stream))
+        self._check(st, self._h)
+        if sync:
+            self.sync_status(stream)
+        return (J if want_j else None), (K if want_k else None)
+
     def autotune(self, L, X, Y=None, sym=None, precision="split", reps: int = 3, stream=None):
         """Time the candidate configurations of this build and cache the
         fastest for its shape bucket; returns (config dict, ms per build)."""
@@ -339,7 +384,7 @@ class Engine:
             self._opts = saved
             if self._h:
                 for code in range(len(OPTIONS)):
-                    self.lib.jk_set_option(self._h, code, saved.get(code, 1 if code == 3 else -1))
+                    self.lib.jk_set_option(self._h, code, saved.get(code, 1 if code == 3 else 0 if code == 5 else -1))
         return int(need * 2)
 
     def _marshal_batched(self, mols):
