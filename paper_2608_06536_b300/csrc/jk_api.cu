@@ -373,6 +373,12 @@ jk_status jk_create(jk_handle *out, void *workspace, size_t bytes) {
 
 jk_status jk_destroy(jk_handle h) {
     if (!h) return JK_OK;
+    if (h->aux_stream) {
+        cudaStreamSynchronize(h->aux_stream);
+        cudaStreamDestroy(h->aux_stream);
+        cudaEventDestroy(h->ev_jfork);
+        cudaEventDestroy(h->ev_jdone);
+    }
     if (h->copy_stream) {
         cudaStreamSynchronize(h->copy_stream);
         cudaStreamDestroy(h->copy_stream);

@@ -78,6 +78,8 @@ struct jk_ctx {
     int host_chunk = 0;      // aux indices per streamed chunk of a host-resident factor (0 = automatic)
     cudaStream_t copy_stream = nullptr;   // host builds: uploads of the factor, created on first use
     cudaEvent_t ev_fork = nullptr, ev_up[2] = {nullptr, nullptr}, ev_used[2] = {nullptr, nullptr};
+    cudaStream_t aux_stream = nullptr;    // FP64 J streams overlapped with the rank updates
+    cudaEvent_t ev_jfork = nullptr, ev_jdone = nullptr;
     jk::Profiler prof;
 };
 

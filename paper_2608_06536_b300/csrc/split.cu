@@ -1114,6 +1114,27 @@ jk_status fp64_gamma_panel(jk_ctx *h, const Problem &pb, const double *T, long l
                            int P0, cudaStream_t st);
 jk_status fp64_jstream(jk_ctx *h, const Problem &pb, const double *gamma, cudaStream_t st);
 
+// The FP64 J back-contraction needs only the factor and gamma, and runs on the
+// FP64 pipe: it is forked onto a second stream as soon as gamma is complete
+// and overlaps the rank updates on the tensor pipe (join at the end of the
+// build, so the call stays ordered on the caller's stream).
+static jk_status fork_jstream(jk_ctx *h, cudaStream_t st) {
+    if (!h->aux_stream) {
+        JK_CUDA_TRY(h, cudaStreamCreateWithFlags(&h->aux_stream, cudaStreamNonBlocking));
+        JK_CUDA_TRY(h, cudaEventCreateWithFlags(&h->ev_jfork, cudaEventDisableTiming));
+        JK_CUDA_TRY(h, cudaEventCreateWithFlags(&h->ev_jdone, cudaEventDisableTiming));
+    }
+    JK_CUDA_TRY(h, cudaEventRecord(h->ev_jfork, st));
+    JK_CUDA_TRY(h, cudaStreamWaitEvent(h->aux_stream, h->ev_jfork, 0));
+    return JK_OK;
+}
+
+static jk_status join_jstream(jk_ctx *h, cudaStream_t st) {
+    JK_CUDA_TRY(h, cudaEventRecord(h->ev_jdone, h->aux_stream));
+    JK_CUDA_TRY(h, cudaStreamWaitEvent(st, h->ev_jdone, 0));
+    return JK_OK;
+}
+
 jk_status split_build(jk_ctx *h, const Problem &pb, cudaStream_t st) {
     const int n = pb.n, naux = pb.naux, nd = pb.nd;
     const long long n2 = static_cast<long long>(n) * n;
@@ -1157,6 +1178,10 @@ jk_status split_build(jk_ctx *h, const Problem &pb, cudaStream_t st) {
             JK_TRY(ozgemm(h, Lc, Zs, T, ldT, nullptr, st));
         }
         if (pb.wantJ) JK_TRY(fp64_gamma_panel(h, pb, T, ldT, np, gamma, P0, st));
+        if (pb.wantJ && P0 + np >= naux) {
+            JK_TRY(fork_jstream(h, st));
+            JK_TRY(fp64_jstream(h, pb, gamma, h->aux_stream));
+        }
         if (!pb.wantK) continue;
         // Rank update per density over this chunk's (p, i) pairs.
         long long *Pcur = Pbuf;
@@ -1190,7 +1215,7 @@ jk_status split_build(jk_ctx *h, const Problem &pb, cudaStream_t st) {
             }
         }
     }
-    if (pb.wantJ) JK_TRY(fp64_jstream(h, pb, gamma, st));
+    if (pb.wantJ) JK_TRY(join_jstream(h, st));
     return JK_OK;
 }
 
@@ -1441,6 +1466,7 @@ jk_status split_batched(jk_ctx *h, int nmol, const Problem *pbs, cudaStream_t st
         JK_TRY(slice_operand(h, zsrc, pb.ctot, pb.n, 1, mb[m].Zs, st));
     }
     const size_t persist = ar.off;
+    bool forked = false;   // J streams running on the second stream
     // Work items (molecule, aux chunk) in order.
     std::vector<std::pair<int, int>> work;
     for (int m = 0; m < nmol; m++)
@@ -1485,11 +1511,25 @@ jk_status split_batched(jk_ctx *h, int nmol, const Problem *pbs, cudaStream_t st
             JK_TRY(oz_problem(h, it.Ls, mb[it.mol].Zs, it.T, even_ld(pb.ctot), nullptr, probs.back()));
         }
         JK_TRY(oz_launch(h, probs, st));
-        // 3. gamma and rank-update operands
+        // 3. gamma; the J streams of molecules whose last chunk this is go to the
+        // second stream; then the rank-update operands
+        bool fork = false;
+        for (auto &it : items) {
+            const Problem &pb = pbs[it.mol];
+            if (!pb.wantJ) continue;
+            JK_TRY(fp64_gamma_panel(h, pb, it.T, even_ld(pb.ctot), it.np, mb[it.mol].gamma, it.P0, st));
+            fork = fork || it.P0 + it.np >= pb.naux;
+        }
+        if (fork) {
+            JK_TRY(fork_jstream(h, st));
+            forked = true;
+            for (auto &it : items)
+                if (pbs[it.mol].wantJ && it.P0 + it.np >= pbs[it.mol].naux)
+                    JK_TRY(fp64_jstream(h, pbs[it.mol], mb[it.mol].gamma, h->aux_stream));
+        }
         for (auto &it : items) {
             const Problem &pb = pbs[it.mol];
             const long long ldT = even_ld(pb.ctot);
-            if (pb.wantJ) JK_TRY(fp64_gamma_panel(h, pb, it.T, ldT, it.np, mb[it.mol].gamma, it.P0, st));
             if (!pb.wantK) continue;
             for (int s = 0; s < pb.nd; s++) {
                 const int k = pb.k[s], Kr = it.np * k;
@@ -1540,9 +1580,7 @@ jk_status split_batched(jk_ctx *h, int nmol, const Problem *pbs, cudaStream_t st
         }
         w0 = w1;
     }
-    // J back-contraction per molecule (FP64)
-    for (int m = 0; m < nmol; m++)
-        if (pbs[m].wantJ) JK_TRY(fp64_jstream(h, pbs[m], mb[m].gamma, st));
+    if (forked) JK_TRY(join_jstream(h, st));
     return JK_OK;
 }
 
