@@ -132,13 +132,16 @@ class ClockSampler:
 
 
 def dist_init():
+    """Replicas: one process per GPU (RANK / WORLD_SIZE / MASTER_* from the
+    launcher).  NCCL between GPUs; gloo where no GPU is visible (CPU tests of
+    the multi-process logic)."""
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world > 1:
+        import torch
         import torch.distributed as dist
-        backend = "nccl"
-        dist.init_process_group(backend=backend)
+        dist.init_process_group(backend="nccl" if torch.cuda.is_available() else "gloo")
     return rank, world, local
 
 
@@ -148,14 +151,23 @@ def barrier(world):
         dist.barrier()
 
 
-def max_over_ranks(x, world, device):
+def max_over_ranks(x, world, device=None):
+    """The slowest rank's time: the whole job finishes when it does."""
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
+    if dist.get_backend() == "gloo":
+        device = "cpu"
     t = torch.tensor([x], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def job_tflops(flops_per_rank, ms_max, world):
+    """Whole-job throughput of `world` replicas that each did flops_per_rank
+    in at most ms_max milliseconds (weak scaling)."""
+    return world * flops_per_rank / (ms_max * 1e-3) / 1e12
 
 
 _CPU_SAMPLE = {}
@@ -269,7 +281,7 @@ def run_ours(args, rank, world, local):
     clk = clocks.stop()
     eng.sync_status()
     ms_max = max_over_ranks(ms, world, dev)
-    value = world * flops / (ms_max * 1e-3) / 1e12
+    value = job_tflops(flops, ms_max, world)
 
     if args.quick:
         if rank == 0:
@@ -303,7 +315,7 @@ def run_ours(args, rank, world, local):
     torch.cuda.synchronize(dev)
     eng.sync_status(st)
     ms_e2e = max_over_ranks(e0.elapsed_time(e1) / e2e_steps, world, dev)
-    e2e = {"value": world * flops / (ms_e2e * 1e-3) / 1e12, "unit": "TFLOP/s",
+    e2e = {"value": job_tflops(flops, ms_e2e, world), "unit": "TFLOP/s",
            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "ms_per_step": ms_e2e,
            "path": "jk_build_host: pinned host inputs and outputs, factor streamed in aux chunks "
                    "overlapped with the build"}
