@@ -33,6 +33,7 @@ static GOp gop(const double *p, long long sb, long long sr, long long sko,
 }
 
 constexpr int GBM = 64, GBN = 64, GBK = 16;
+constexpr int kMaxRankSplit = 8;   // most aux-index groups one FP64 rank update is split into
 
 // C_b[m][n] = alpha * sum_kk A_b(m,kk) B_b(n,kk) + beta * C_b[m][n]
 // 64x64 tile per CTA, 256 threads, 4x4 outputs per thread; sums run in
@@ -420,7 +421,54 @@ size_t fp64_build_workspace(const Problem &pb, int pc) {
     b += align_up((size_t)pc * n * pb.ctot * 8);    // T chunk
     b += align_up(nd * (size_t)pb.naux * 8);        // gamma
     b += align_up(nd * n * n * 8);                  // dense D (J-only path)
+    b += align_up((size_t)kMaxRankSplit * n * n * 8);   // split rank-update partials
     return b;
+}
+
+// out[e] = (accumulate ? out[e] : 0) + sum_b part[b][e], b in increasing order.
+__global__ void sum_parts_kernel(double *out, const double *part, int nb, long long cnt, int accumulate) {
+    const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (e >= cnt) return;
+    double acc = accumulate ? out[e] : 0.0;
+    for (int b = 0; b < nb; b++) acc += part[(long long)b * cnt + e];
+    out[e] = acc;
+}
+
+// Split of an n x n rank update over the chunk's aux indices so that its few
+// 64 x 64 output tiles still fill the GPU.
+static int rank_splits(const jk_ctx *h, int n, int np) {
+    const int tiles = ((n + GBN - 1) / GBN) * ((n + GBM - 1) / GBM);
+    int ns = (h->num_sms + tiles - 1) / tiles;
+    if (ns > kMaxRankSplit) ns = kMaxRankSplit;
+    if (ns > np) ns = np;
+    return ns < 1 ? 1 : ns;
+}
+
+// K_s (+)= sum over the chunk's (p, i) of T[p][mu][offX+i] T[p][nu][offY+i]:
+// partial products over groups of p (one batched launch, plus one for a
+// remainder), then their sum into K_s in a fixed order.
+static jk_status rank_update_fp64(jk_ctx *h, const Problem &pb, const double *T, int np, int s, bool accumulate,
+                                  double *part, cudaStream_t st) {
+    const int n = pb.n, k = pb.k[s];
+    const long long n2 = (long long)n * n, sp = (long long)n * pb.ctot;
+    const int ns = rank_splits(h, n, np);
+    const int pbs = (np + ns - 1) / ns;
+    const int nfull = np / pbs, rem = np - nfull * pbs;
+    if (nfull > 0)
+        JK_TRY(dgemm(h, nfull, n, n, pbs * k, gop(T + pb.offX[s], pbs * sp, pb.ctot, sp, 1, k),
+                     gop(T + pb.offY[s], pbs * sp, pb.ctot, sp, 1, k), part, n, n2, 1.0, 0.0, st));
+    if (rem > 0) {
+        const long long b0 = (long long)nfull * pbs * sp;
+        JK_TRY(dgemm(h, 1, n, n, rem * k, gop(T + pb.offX[s] + b0, 0, pb.ctot, sp, 1, k),
+                     gop(T + pb.offY[s] + b0, 0, pb.ctot, sp, 1, k), part + nfull * n2, n, 0, 1.0, 0.0, st));
+    }
+    {
+        LaunchScope ls(h, KK_MISC, st);
+        sum_parts_kernel<<<(unsigned)((n2 + 255) / 256), 256, 0, st>>>(pb.K[s], part, nfull + (rem > 0), n2,
+                                                                      accumulate ? 1 : 0);
+    }
+    JK_LAUNCH_CHECK(h);
+    return JK_OK;
 }
 
 jk_status fp64_build(jk_ctx *h, const Problem &pb, cudaStream_t st) {
@@ -433,7 +481,8 @@ jk_status fp64_build(jk_ctx *h, const Problem &pb, cudaStream_t st) {
     double *T = ar.take<double>((size_t)pc * n * pb.ctot);
     double *gamma = ar.take<double>((size_t)nd * naux);
     double *D = ar.take<double>((size_t)nd * n2);
-    if (!Z || !T || !gamma || !D)
+    double *part = ar.take<double>((size_t)kMaxRankSplit * n2);
+    if (!Z || !T || !gamma || !D || !part)
         return set_error(h, JK_ERR_OOM, "workspace too small for the FP64 build");
 
     if (K) {
@@ -457,13 +506,7 @@ jk_status fp64_build(jk_ctx *h, const Problem &pb, cudaStream_t st) {
                 JK_LAUNCH_CHECK(h);
             }
             // K_s (+)= sum_{p,i} T[p][mu][offX+i] T[p][nu][offY+i]
-            for (int s = 0; s < nd; s++) {
-                const long long sp = (long long)n * pb.ctot;
-                JK_TRY(dgemm(h, 1, n, n, np * pb.k[s],
-                             gop(T + pb.offX[s], 0, pb.ctot, sp, 1, pb.k[s]),
-                             gop(T + pb.offY[s], 0, pb.ctot, sp, 1, pb.k[s]),
-                             pb.K[s], n, 0, 1.0, P0 == 0 ? 0.0 : 1.0, st));
-            }
+            for (int s = 0; s < nd; s++) JK_TRY(rank_update_fp64(h, pb, T, np, s, P0 > 0, part, st));
         }
     } else if (J) {
         // J only: gamma from the dense densities D_s = X_s Y_s^T.
