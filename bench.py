@@ -374,6 +374,79 @@ def run_ours(args, rank, world, local):
     print(json.dumps(line), flush=True)
 
 
+def adjoint_flops(n, naux, ks, sym):
+    """Algorithmic flops of the adjoint: 12 n^2 k naux (dX, dY with the panels
+    recomputed) + 4 n^2 k naux (dL outer products) + 4 n^2 naux (J terms) per
+    density."""
+    return sum(12.0 * n * n * k * naux + 4.0 * n * n * k * naux + 4.0 * n * n * naux for k in ks)
+
+
+def run_extra_case(args, rank, local):
+    """Reported beside the headline workload (not the bench contract's line):
+    the adjoint case, and the uneven batch replayed as a CUDA graph."""
+    import numpy as np
+    import torch
+    from paper_2608_06536_b300 import inputs, jk
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    eng = jk.Engine(dev)
+    st = torch.cuda.current_stream(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out = {"case": args.case, "engine": args.precision}
+    if args.case == "adjoint":
+        m, W, V = inputs.adjoint_case(with_factor=False)
+        L = inputs.factor_device(m.n, m.naux, m.tau, m.seed, device=dev)
+        X = [torch.from_numpy(x).to(dev) for x in m.X]
+        Y = [torch.from_numpy(y).to(dev) for y in m.Y]
+        Wd = torch.tensor(np.array(W), device=dev)
+        Vd = torch.tensor(np.array(V), device=dev)
+        for _ in range(args.warmup):
+            eng.adjoint(L, X, Y, m.sym, Wd, Vd, precision=args.precision)
+        torch.cuda.synchronize(dev)
+        e0.record(st)
+        for _ in range(args.steps):
+            eng.adjoint(L, X, Y, m.sym, Wd, Vd, precision=args.precision)
+        e1.record(st)
+        torch.cuda.synchronize(dev)
+        eng.sync_status()
+        ms = e0.elapsed_time(e1) / args.steps
+        out.update({"workload": "adjoint nbf=600 naux=3600, 8 non-symmetric densities k=60, W,V N(0,1); "
+                                "dX, dY and the symmetrized dL",
+                    "ms_per_step": ms, "value": adjoint_flops(m.n, m.naux, m.ks, m.sym) / (ms * 1e-3) / 1e12,
+                    "unit": "TFLOP/s (algorithmic)"})
+    else:
+        mols = inputs.uneven_batch(with_factor=False)
+        args_b = [(inputs.factor_device(mm.n, mm.naux, mm.tau, mm.seed, device=dev),
+                   [torch.from_numpy(x).to(dev) for x in mm.X], [torch.from_numpy(y).to(dev) for y in mm.Y],
+                   mm.sym) for mm in mols]
+        flops = sum(build_flops(mm.n, mm.naux, mm.ks, mm.sym) for mm in mols)
+        eng.build_batched(args_b, args.precision)
+        torch.cuda.synchronize(dev)
+        g = torch.cuda.CUDAGraph()
+        cs = torch.cuda.Stream(dev)
+        cs.wait_stream(st)
+        with torch.cuda.stream(cs):
+            with torch.cuda.graph(g, stream=cs):
+                eng.build_batched(args_b, args.precision, stream=cs)
+        st.wait_stream(cs)
+        for _ in range(args.warmup):
+            g.replay()
+        torch.cuda.synchronize(dev)
+        e0.record(st)
+        for _ in range(args.steps):
+            g.replay()
+        e1.record(st)
+        torch.cuda.synchronize(dev)
+        eng.sync_status()
+        ms = e0.elapsed_time(e1) / args.steps
+        out.update({"workload": "uneven batch: 64 molecules nbf U{100..600}, naux 6 nbf, 560 non-symmetric "
+                                "densities k = nbf/10 (208 GB of factors), one batched build replayed as a CUDA graph",
+                    "ms_per_step": ms, "value": flops / (ms * 1e-3) / 1e12, "unit": "TFLOP/s (algorithmic)"})
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -381,8 +454,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["split", "fp64"], default="split")
-    ap.add_argument("--case", choices=["multi_state", "profile"], default="multi_state",
-                    help="profile: nbf=400, naux=600 variant for ncu captures")
+    ap.add_argument("--case", choices=["multi_state", "profile", "adjoint", "batched"], default="multi_state",
+                    help="profile: nbf=400, naux=600 variant for ncu captures; adjoint, batched: extra reported cases")
     ap.add_argument("--no-tune", dest="tune", action="store_false",
                     help="skip the autotuner (default configuration)")
     ap.add_argument("--config", default="",
@@ -393,6 +466,8 @@ def main():
     rank, world, local = dist_init()
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.case in ("adjoint", "batched"):
+        run_extra_case(args, rank, local)
     else:
         run_ours(args, rank, world, local)
     if world > 1:
