@@ -34,6 +34,7 @@ static GOp gop(const double *p, long long sb, long long sr, long long sko,
 
 constexpr int GBM = 64, GBN = 64, GBK = 16;
 constexpr int kMaxRankSplit = 8;   // most aux-index groups one FP64 rank update is split into
+constexpr int kMaxAdjSplit = 16;   // the same for the adjoint's n x k products
 
 // C_b[m][n] = alpha * sum_kk A_b(m,kk) B_b(n,kk) + beta * C_b[m][n]
 // 64x64 tile per CTA, 256 threads, 4x4 outputs per thread; sums run in
@@ -434,41 +435,46 @@ __global__ void sum_parts_kernel(double *out, const double *part, int nb, long l
     out[e] = acc;
 }
 
-// Split of an n x n rank update over the chunk's aux indices so that its few
-// 64 x 64 output tiles still fill the GPU.
-static int rank_splits(const jk_ctx *h, int n, int np) {
-    const int tiles = ((n + GBN - 1) / GBN) * ((n + GBM - 1) / GBM);
+// C (+)= sum over q in [0, nq) and inner index t in [0, kin) of
+// A[m][q][t] B[n][q][t]  (element (m, q, t) of A at A + m*a_sr + q*a_sq + t*a_st,
+// likewise B), with C dense M x N.  A small output (few 64 x 64 tiles) would
+// leave most SMs idle for a long reduction, so the reduction is split over
+// groups of q: one batched launch of partial products (plus one for a
+// remainder group), then their sum into C in a fixed order.
+static jk_status dgemm_split_q(jk_ctx *h, int M, int N, int nq, int kin, const double *A, long long a_sr,
+                               long long a_sq, long long a_st, const double *B, long long b_sr, long long b_sq,
+                               long long b_st, double *C, bool accumulate, double *part, int max_split,
+                               cudaStream_t st) {
+    const long long MN = (long long)M * N;
+    const int tiles = ((N + GBN - 1) / GBN) * ((M + GBM - 1) / GBM);
     int ns = (h->num_sms + tiles - 1) / tiles;
-    if (ns > kMaxRankSplit) ns = kMaxRankSplit;
-    if (ns > np) ns = np;
-    return ns < 1 ? 1 : ns;
-}
-
-// K_s (+)= sum over the chunk's (p, i) of T[p][mu][offX+i] T[p][nu][offY+i]:
-// partial products over groups of p (one batched launch, plus one for a
-// remainder), then their sum into K_s in a fixed order.
-static jk_status rank_update_fp64(jk_ctx *h, const Problem &pb, const double *T, int np, int s, bool accumulate,
-                                  double *part, cudaStream_t st) {
-    const int n = pb.n, k = pb.k[s];
-    const long long n2 = (long long)n * n, sp = (long long)n * pb.ctot;
-    const int ns = rank_splits(h, n, np);
-    const int pbs = (np + ns - 1) / ns;
-    const int nfull = np / pbs, rem = np - nfull * pbs;
+    if (ns > max_split) ns = max_split;
+    if (ns > nq) ns = nq;
+    if (ns < 1) ns = 1;
+    const int qb = (nq + ns - 1) / ns;
+    const int nfull = nq / qb, rem = nq - nfull * qb;
     if (nfull > 0)
-        JK_TRY(dgemm(h, nfull, n, n, pbs * k, gop(T + pb.offX[s], pbs * sp, pb.ctot, sp, 1, k),
-                     gop(T + pb.offY[s], pbs * sp, pb.ctot, sp, 1, k), part, n, n2, 1.0, 0.0, st));
-    if (rem > 0) {
-        const long long b0 = (long long)nfull * pbs * sp;
-        JK_TRY(dgemm(h, 1, n, n, rem * k, gop(T + pb.offX[s] + b0, 0, pb.ctot, sp, 1, k),
-                     gop(T + pb.offY[s] + b0, 0, pb.ctot, sp, 1, k), part + nfull * n2, n, 0, 1.0, 0.0, st));
-    }
+        JK_TRY(dgemm(h, nfull, M, N, qb * kin, gop(A, qb * a_sq, a_sr, a_sq, a_st, kin),
+                     gop(B, qb * b_sq, b_sr, b_sq, b_st, kin), part, N, MN, 1.0, 0.0, st));
+    if (rem > 0)
+        JK_TRY(dgemm(h, 1, M, N, rem * kin, gop(A + (long long)nfull * qb * a_sq, 0, a_sr, a_sq, a_st, kin),
+                     gop(B + (long long)nfull * qb * b_sq, 0, b_sr, b_sq, b_st, kin), part + nfull * MN, N, 0,
+                     1.0, 0.0, st));
     {
         LaunchScope ls(h, KK_MISC, st);
-        sum_parts_kernel<<<(unsigned)((n2 + 255) / 256), 256, 0, st>>>(pb.K[s], part, nfull + (rem > 0), n2,
+        sum_parts_kernel<<<(unsigned)((MN + 255) / 256), 256, 0, st>>>(C, part, nfull + (rem > 0), MN,
                                                                       accumulate ? 1 : 0);
     }
     JK_LAUNCH_CHECK(h);
     return JK_OK;
+}
+
+// K_s (+)= sum over the chunk's (p, i) of T[p][mu][offX+i] T[p][nu][offY+i].
+static jk_status rank_update_fp64(jk_ctx *h, const Problem &pb, const double *T, int np, int s, bool accumulate,
+                                  double *part, cudaStream_t st) {
+    const long long sp = (long long)pb.n * pb.ctot;
+    return dgemm_split_q(h, pb.n, pb.n, np, pb.k[s], T + pb.offX[s], pb.ctot, sp, 1, T + pb.offY[s], pb.ctot, sp,
+                         1, pb.K[s], accumulate, part, kMaxRankSplit, st);
 }
 
 jk_status fp64_build(jk_ctx *h, const Problem &pb, cudaStream_t st) {
@@ -534,6 +540,7 @@ size_t fp64_adjoint_workspace(const Problem &pb, int pc, bool want_dl) {
     b += 2 * align_up(nd * n * n * 8);              // D, J(V)
     b += 2 * align_up((size_t)pc * n * pb.kmax * 8);  // U, Vp
     if (want_dl) b += align_up((size_t)pc * n * n * 8);  // G chunk
+    b += align_up((size_t)kMaxAdjSplit * n * pb.kmax * 8);   // split dX / dY partials
     return b;
 }
 
@@ -553,7 +560,8 @@ jk_status fp64_adjoint(jk_ctx *h, const Problem &pb, const double *W,
     double *U = ar.take<double>((size_t)pc * n * pb.kmax);
     double *Vp = ar.take<double>((size_t)pc * n * pb.kmax);
     double *G = dL ? ar.take<double>((size_t)pc * n2) : nullptr;
-    if (!Z || !T || !gamma || !cps || !D || !JV || !U || !Vp || (dL && !G))
+    double *part = ar.take<double>((size_t)kMaxAdjSplit * n * pb.kmax);
+    if (!Z || !T || !gamma || !cps || !D || !JV || !U || !Vp || (dL && !G) || !part)
         return set_error(h, JK_ERR_OOM, "workspace too small for the FP64 adjoint");
 
     // Offsets of each density's block in dX / dY.
@@ -607,10 +615,11 @@ jk_status fp64_adjoint(jk_ctx *h, const Problem &pb, const double *W,
             JK_TRY(dgemm(h, np, n, k, n, gop(Ws, 0, 1, 0, n, n),
                          gop(T + pb.offX[s], sp, 1, 0, pb.ctot, n), Vp, k, nk, 1.0, 0.0, st));
             // dX_s += sum_{p,lam} L^p[mu][lam] U^p[lam][i]; dY_s likewise with Vp
-            JK_TRY(dgemm(h, 1, n, k, np * n, gop(pb.L + (long long)P0 * n2, 0, n, n2, 1, n),
-                         gop(U, 0, 1, nk, k, n), dX + boff[s], k, 0, 1.0, 1.0, st));
-            JK_TRY(dgemm(h, 1, n, k, np * n, gop(pb.L + (long long)P0 * n2, 0, n, n2, 1, n),
-                         gop(Vp, 0, 1, nk, k, n), dY + boff[s], k, 0, 1.0, 1.0, st));
+            // (an n x k output: split over groups of p)
+            JK_TRY(dgemm_split_q(h, n, k, np, n, pb.L + (long long)P0 * n2, n, n2, 1, U, 1, nk, k, dX + boff[s],
+                                 true, part, kMaxAdjSplit, st));
+            JK_TRY(dgemm_split_q(h, n, k, np, n, pb.L + (long long)P0 * n2, n, n2, 1, Vp, 1, nk, k, dY + boff[s],
+                                 true, part, kMaxAdjSplit, st));
             if (dL) {
                 // G^p += U^p X_s^T + Y_s Vp^p^T
                 JK_TRY(dgemm(h, np, n, n, k, gop(U, nk, k, 0, 1, k), gop(Xs, 0, k, 0, 1, k),
