@@ -16,9 +16,10 @@
 
 Tolerance for the split path: 1e-10 absolute in output units for J, K and dL.
 The adjoint's dX, dY at the 600/3600 size are sums of n * naux = 2.2e6
-products and reach |dX| ~ 1.6e4, where the FP64 engine itself misses 1e-10
-absolute; there the split path is held to the Hartree-scaled form
-max(1e-10, 1e-13 * max|dX|), and both engines' errors are printed.
+products and reach |dX| ~ 5e4, far from Hartree-sized outputs; there the
+split path is held to the Hartree-scaled form max(1e-10, 1e-13 * max|dX|)
+(its 48-bit slices give ~1e-14 of max|dX|), and both engines' errors are
+printed.
 """
 import gc
 import json
