@@ -56,11 +56,11 @@ def build_flops(n, naux, ks, sym):
 # k=40; summary in profiles/ozgemm_tcgen05_profile_case.md) in the tuned
 # configuration (one aux chunk, grouped schedule: one panel launch and one
 # rank-update launch per build): the panel launch moved 2.268 GB and the
-# grouped rank-update launch 2.029 GB for 600 aux indices.  Both grow in
+# grouped rank-update launch 2.040 GB for 600 aux indices.  Both grow in
 # proportion to naux, which is how they are scaled to the full multi-state
 # launches.
 OZ_PANEL_BYTES_PER_P = 2.268e9 / 600
-OZ_RANK_BYTES_PER_P = 2.029e9 / 600
+OZ_RANK_BYTES_PER_P = 2.040e9 / 600
 
 
 def panel_rank_flops(n, naux, ks, sym):
