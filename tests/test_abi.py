@@ -99,3 +99,24 @@ def test_calls_on_null_handle(lib):
     assert lib.jk_adjoint(None, ct.byref(f), 1, d, None, None, None, None, None, 0, None) == jk.JK_ERR_ARG
     assert lib.jk_sync_status(None, None) == jk.JK_ERR_ARG
     assert lib.jk_last_error(None) == b""
+
+
+def test_host_build_query_is_staging_plus_one_chunk(lib):
+    """JK_OP_BUILD_HOST: two staging chunks of the factor and the device copies
+    of densities and outputs, plus one chunk's build; less than the resident
+    build for a factor much larger than its chunks, and growing with nbf."""
+    nb_host, nb_dev = ct.c_size_t(), ct.c_size_t()
+    f, d = _one(n=400, naux=2400, k=40)
+    fa = (jk.jk_factor * 1)(f)
+    for p in (jk.JK_FP64, jk.JK_SPLIT_BF16):
+        assert lib.jk_workspace_query(jk.JK_OP_BUILD_HOST, 1, fa, None, 1, d, p, ct.byref(nb_host)) == jk.JK_OK
+        assert lib.jk_workspace_query(jk.JK_OP_BUILD, 1, fa, None, 1, d, p, ct.byref(nb_dev)) == jk.JK_OK
+        # at least the two staging buffers of ~naux/12 aux indices each
+        assert nb_host.value >= 2 * (2400 // 12) * 400 * 400 * 8
+        if p == jk.JK_SPLIT_BF16:
+            assert nb_host.value < nb_dev.value + 2 * (2400 // 12 + 1) * 400 * 400 * 8
+    f2, d2 = _one(n=200, naux=2400, k=40)
+    fa2 = (jk.jk_factor * 1)(f2)
+    assert lib.jk_workspace_query(jk.JK_OP_BUILD_HOST, 1, fa2, None, 1, d2, jk.JK_FP64, ct.byref(nb_dev)) == jk.JK_OK
+    assert nb_dev.value < nb_host.value
+    assert lib.jk_build_host(None, ct.byref(f), 1, d, None, None, 0, None) == jk.JK_ERR_ARG
