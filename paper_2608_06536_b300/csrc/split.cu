@@ -371,6 +371,46 @@ __host__ __device__ constexpr int mma_a(int i) { return i == 0 ? 0 : i == 1 ? 1 
 __host__ __device__ constexpr int mma_b0(int i) { return i == 0 ? 4 : i == 1 ? 3 : i == 2 ? 3 : i == 8 ? 3 : 0; }
 __host__ __device__ constexpr int mma_nb(int i) { return i == 0 || i == 1 || i == 3 ? 2 : i == 2 || i == 4 || i == 8 ? 1 : 3; }
 __host__ __device__ constexpr int mma_d0(int i) { return mma_a(i) + mma_b0(i); }
+// Issue order per window residue r: the MMAs that touch an accumulator whose
+// window restarts at r go last (each group keeps the base order), so the MMA
+// thread has the most work queued before it must wait for that accumulator's
+// drain.  A table of constants, folded into the unrolled K-block loop.
+__host__ __device__ constexpr unsigned mma_mask(int i) { return ((1u << mma_nb(i)) - 1u) << mma_d0(i); }
+struct MmaOrder {
+    int v[WPERIOD][NMMA];
+};
+__host__ __device__ constexpr MmaOrder make_mma_order() {
+    MmaOrder t{};
+    for (int r = 0; r < WPERIOD; r++) {
+        const unsigned m = ws_mask(r);
+        int c = 0;
+        for (int pass = 0; pass < 2; pass++)
+            for (int j = 0; j < NMMA; j++)
+                if (((mma_mask(j) & m) != 0) == (pass == 1)) t.v[r][c++] = j;
+    }
+    return t;
+}
+// The same order written out (a switch the unrolled loop folds to constants);
+// checked against make_mma_order() at compile time.
+__host__ __device__ constexpr int mma_issue(int r, int i0) {
+    switch (r) {
+        case 2: { const int o[NMMA] = {0, 1, 2, 3, 4, 5, 8, 6, 7, 9}; return o[i0]; }
+        case 6: { const int o[NMMA] = {0, 1, 2, 3, 4, 9, 5, 6, 7, 8}; return o[i0]; }
+        case 8: { const int o[NMMA] = {0, 1, 2, 3, 4, 5, 6, 8, 7, 9}; return o[i0]; }
+        case 10: { const int o[NMMA] = {0, 1, 2, 3, 4, 5, 8, 6, 7, 9}; return o[i0]; }
+        case 14: { const int o[NMMA] = {0, 1, 2, 3, 4, 9, 5, 6, 7, 8}; return o[i0]; }
+        default: return i0;
+    }
+}
+__host__ __device__ constexpr bool mma_issue_matches() {
+    const MmaOrder t = make_mma_order();
+    for (int r = 0; r < WPERIOD; r++)
+        for (int i = 0; i < NMMA; i++)
+            if (mma_issue(r, i) != t.v[r][i]) return false;
+    return true;
+}
+static_assert(mma_issue_matches(), "MMA issue order table");
+
 // Drain order at a tile end: the first MMAs of the next tile need 4, 5, then 3, 2, 1, 0.
 __host__ __device__ constexpr int drain_acc(int j) { return j == 0 ? 4 : j == 1 ? 5 : 3 - (j - 2); }
 
@@ -565,7 +605,8 @@ ozgemm_kernel(const __grid_constant__ OzGroup g) {
                         const uint64_t ad0 = tc::sdesc_kmajor_sw32(tc::smem_u32(smem + stage * STAGE_BYTES));
                         const uint64_t bd0 = ad0 + static_cast<uint64_t>(A_BYTES / 16);
 #pragma unroll
-                        for (int i = 0; i < NMMA; i++) {
+                        for (int i0 = 0; i0 < NMMA; i0++) {
+                            const int i = mma_issue(r, i0);
                             const unsigned need = pend & (((1u << mma_nb(i)) - 1u) << mma_d0(i));
                             if (need) {
 #pragma unroll
