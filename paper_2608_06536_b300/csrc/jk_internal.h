@@ -75,6 +75,7 @@ struct jk_ctx {
     int cur_raster = 0;      // tile order in effect for the running call
     int cur_cluster = 0;     // 2-CTA clustered sliced GEMM in effect for the running call
     int max_clusters = 0;    // resident 2-CTA clusters of the sliced GEMM (0 = not yet queried)
+    bool gemm_smem_set = false;   // the sliced GEMM's shared-memory attribute is set on this device
     int host_chunk = 0;      // aux indices per streamed chunk of a host-resident factor (0 = automatic)
     cudaStream_t copy_stream = nullptr;   // host builds: uploads of the factor, created on first use
     cudaEvent_t ev_fork = nullptr, ev_up[2] = {nullptr, nullptr}, ev_used[2] = {nullptr, nullptr};

@@ -1019,14 +1019,14 @@ static jk_status oz_problem(jk_ctx *h, const Sliced &A, const Sliced &B, double 
 // Launch a list of problems: persistent grid, up to MAXG problems per launch.
 // Clustered (h->cur_cluster): 2-CTA clusters, as many as can be resident.
 static jk_status oz_launch(jk_ctx *h, const std::vector<oz::OzProb> &probs, cudaStream_t st) {
-    static bool smem_configured = false;
     int &max_clusters = h->max_clusters;
-    if (!smem_configured) {
+    if (!h->gemm_smem_set) {
+        // a per-device function attribute: set once per handle (a handle is bound to one device)
         JK_CUDA_TRY(h, cudaFuncSetAttribute(oz::ozgemm_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             oz::SMEM_BYTES));
         JK_CUDA_TRY(h, cudaFuncSetAttribute(oz::ozgemm_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             oz::SMEM_BYTES));
-        smem_configured = true;
+        h->gemm_smem_set = true;
     }
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
