@@ -24,6 +24,14 @@ jk_status jk_debug_sliced_gemm(jk_handle h, int32_t M, int32_t N, int32_t K,
                                void *stream);
 size_t jk_debug_sliced_gemm_workspace(int32_t M, int32_t N, int32_t K);
 
+/* Exercises the engine's bounded waits: one thread waits on an mbarrier
+ * phase that nothing completes, with the same helper and limit (4 s) the
+ * tcgen05 pipeline uses; when the limit runs out it raises JK_ERR_TIMEOUT in
+ * the handle's device status word and returns.  jk_sync_status(h, stream)
+ * then reports JK_ERR_TIMEOUT and clears it; the CUDA context stays usable.
+ * Nothing faults or hangs. */
+jk_status jk_debug_wait_timeout(jk_handle h, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1812,3 +1812,34 @@ extern "C" size_t jk_debug_sliced_gemm_workspace(int32_t M, int32_t N, int32_t K
     if (ns > 1) b += align_up(static_cast<size_t>(ns) * part_rows(M) * even_ld(N) * 8);
     return b + kArenaAlign;
 }
+
+namespace jk {
+namespace oz {
+// One thread waits on phase 0 of an mbarrier that nothing arrives on; the
+// bounded wait gives up after tc::kWaitTimeoutNs and the kernel reports it.
+__global__ void wait_timeout_kernel(int *err) {
+    __shared__ uint64_t bar;
+    __shared__ int abort_flag;
+    if (threadIdx.x == 0) {
+        tc::mbar_init(&bar, 1);
+        abort_flag = 0;
+        tc::fence_barrier_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && !tc::mbar_wait(&bar, 0u, &abort_flag))
+        atomicExch(err, static_cast<int>(JK_ERR_TIMEOUT));
+}
+}  // namespace oz
+}  // namespace jk
+
+extern "C" jk_status jk_debug_wait_timeout(jk_handle h, void *stream) {
+    using namespace jk;
+    if (!h) return JK_ERR_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    {
+        LaunchScope ls(h, KK_MISC, st);
+        oz::wait_timeout_kernel<<<1, 32, 0, st>>>(&h->flags->error);
+    }
+    JK_LAUNCH_CHECK(h);
+    return JK_OK;
+}
