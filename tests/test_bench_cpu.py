@@ -1,0 +1,64 @@
+"""Host-side pieces of bench.py and of the input recipe (no GPU needed): the
+algorithmic flop model of the metric, the peaks it divides by, and the
+device-side factor generator's properties (run on the CPU)."""
+import json
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import bench
+from paper_2608_06536_b300 import inputs
+
+
+def test_build_flops_model():
+    # per density: panels 2n^2k naux per half-transform (one for a symmetric
+    # density), rank update 2n^2k naux (half of it when symmetric), J 2n^2 naux,
+    # gamma 2nk naux
+    n, A = 400, 2400
+    ks, sym = [40] * 8, [True] + [False] * 7
+    expect = sum((2 + 1 if s else 4 + 2) * n * n * k * A + 2 * n * n * A + 2 * n * k * A for k, s in zip(ks, sym))
+    assert bench.build_flops(n, A, ks, sym) == pytest.approx(expect, rel=1e-15)
+    assert bench.build_flops(n, A, ks, sym) == pytest.approx(6.98e11, rel=2e-3)
+    assert bench.panel_rank_flops(n, A, ks, sym) == pytest.approx(45 * n * n * 40 * A, rel=1e-15)
+
+
+def test_adjoint_flops_model():
+    n, A, k = 600, 3600, 60
+    one = 12 * n * n * k * A + 4 * n * n * k * A + 4 * n * n * A
+    assert bench.adjoint_flops(n, A, [k] * 8, [False] * 8) == pytest.approx(8 * one, rel=1e-15)
+
+
+def test_peaks_fallback(tmp_path, monkeypatch):
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    d, src = bench.load_peaks()
+    assert src == "fallback" and d["bf16_tflops_sustained"] == 1400.0 and d["hbm_gbs"] == 6400.0
+    (tmp_path / "MEASURED_PEAKS.json").write_text(json.dumps({"bf16_tflops_sustained": 1371.7}))
+    d, src = bench.load_peaks()
+    assert src == "measured" and d["bf16_tflops_sustained"] == 1371.7
+
+
+def test_factor_device_recipe_on_cpu():
+    n, naux, tau = 9, 40, 7.0
+    L = inputs.factor_device(n, naux, tau, seed=3, device="cpu")
+    assert L.shape == (naux, n, n) and L.dtype == torch.float64
+    assert torch.equal(L, L.transpose(1, 2))                       # symmetric
+    assert torch.equal(L, inputs.factor_device(n, naux, tau, seed=3, device="cpu"))   # deterministic
+    assert not torch.equal(L, inputs.factor_device(n, naux, tau, seed=4, device="cpu"))
+    # undo the exp(-P/tau) scale: the upper triangles are then N(0,1) draws
+    unscaled = L * torch.exp(torch.arange(naux, dtype=torch.float64) / tau)[:, None, None]
+    iu = torch.triu_indices(n, n)
+    v = unscaled[:, iu[0], iu[1]].flatten().numpy()
+    assert abs(v.mean()) < 5 / math.sqrt(v.size) and abs(v.std() - 1.0) < 0.05
+
+
+def test_host_recipe_matches_its_statement():
+    L = inputs.factor(6, 3, 2.0, seed=1)
+    for P in range(3):
+        M = inputs.factor_slice(6, P, 2.0, seed=1)
+        np.testing.assert_array_equal(L[P], M)
+        assert np.array_equal(M, M.T)
+        rng = np.random.default_rng([1, 1, P])
+        iu = np.triu_indices(6)
+        np.testing.assert_allclose(M[iu], rng.standard_normal(iu[0].size) * math.exp(-P / 2.0), rtol=0, atol=0)
