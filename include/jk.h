@@ -22,6 +22,9 @@
  *    sub-allocated by bump, as the paper's engine does, Sec. IV).
  *  - All work is enqueued asynchronously on the caller's stream
  *    (a cudaStream_t passed as void*; NULL = legacy default stream).
+ *    Split builds run their FP64 J back-contraction, and jk_build_host its
+ *    uploads, on streams the handle owns; those fork from and join the
+ *    caller's stream inside the call, so every result is ordered on it.
  *  - Outputs are overwritten, never accumulated into.
  *  - Arguments are validated on the host before anything is launched; a
  *    failing check returns a status and stores a message retrievable with
@@ -129,7 +132,12 @@ jk_status jk_build_host(jk_handle h, const jk_factor *f, int32_t nd, const jk_de
  * call.  f[m] is molecule m's factor, nd_per_mol[m] its density count (host
  * array), d the densities of all molecules concatenated in molecule order,
  * J[i], K[i] (host arrays of device pointers, one per density in the same
- * order) point to [nbf_m][nbf_m] FP64 outputs; J or K may be NULL. */
+ * order) point to [nbf_m][nbf_m] FP64 outputs; J or K may be NULL.
+ * In split precision the molecules' panels go into shared persistent GEMM
+ * launches (up to 32 problems of different shapes each), as do their rank
+ * updates; the call allocates nothing and synchronizes nothing, so it can be
+ * recorded in a CUDA graph once the handle has run one eager call.
+ * Status as jk_build (JK_ERR_OOM against the JK_OP_BATCHED query). */
 jk_status jk_build_batched(jk_handle h, int32_t nmol, const jk_factor *f,
                            const int32_t *nd_per_mol, const jk_density *d,
                            double *const *J, double *const *K,
