@@ -120,3 +120,25 @@ def test_host_build_query_is_staging_plus_one_chunk(lib):
     assert lib.jk_workspace_query(jk.JK_OP_BUILD_HOST, 1, fa2, None, 1, d2, jk.JK_FP64, ct.byref(nb_dev)) == jk.JK_OK
     assert nb_dev.value < nb_host.value
     assert lib.jk_build_host(None, ct.byref(f), 1, d, None, None, 0, None) == jk.JK_ERR_ARG
+
+
+def test_headers_are_c99_and_link(lib, tmp_path):
+    """The ABI is plain C: a C99 program including both headers compiles with
+    -pedantic -Werror, links against libjk.so and makes a host-only call."""
+    import subprocess
+    src = tmp_path / "t.c"
+    src.write_text(
+        '#include <stdio.h>\n#include "jk.h"\n#include "jk_debug.h"\n'
+        "int main(void) {\n"
+        "    jk_factor f = {10, 7, (const double *)0x1000};\n"
+        "    jk_density d = {3, 0, (const double *)0x2000, (const double *)0x3000};\n"
+        "    size_t b = 0;\n"
+        "    jk_status s = jk_workspace_query(JK_OP_BUILD, 1, &f, NULL, 1, &d, JK_FP64, &b);\n"
+        '    printf("%s\\n", jk_status_string(s));\n'
+        "    return s == JK_OK && b > 0 ? 0 : 1;\n}\n")
+    libdir = os.path.dirname(jk.LIB_PATH)
+    exe = tmp_path / "t"
+    subprocess.run(["gcc", "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I", os.path.join(ROOT, "include"),
+                    str(src), "-L", libdir, "-ljk", f"-Wl,-rpath,{libdir}", "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert out.returncode == 0 and out.stdout.strip() == "ok"
