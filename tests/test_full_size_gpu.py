@@ -94,6 +94,20 @@ def test_multi_state_full(eng):
     assert eJ <= SPLIT_ABS and eK <= SPLIT_ABS
     assert fJ <= FP64_REL * np.abs(Jfn).max() and fK <= FP64_REL * np.abs(Kfn).max()
     assert abs_err(Jn, Jfn) < 2 * SPLIT_ABS and abs_err(Kn, Kfn) < 2 * SPLIT_ABS
+    # the configuration bench.py times on this workload (its autotuner's pick):
+    # all aux indices in one chunk, grouped launches, n-tile raster, one CTA per tile
+    for name, v in (("aux_chunk", 3834), ("schedule", 1), ("raster", 0), ("cluster", 0)):
+        eng.set_option(name, v)
+    Jt, Kt = eng.build(L, X, Y, m.sym, "split")
+    eng.sync_status()
+    for name in ("aux_chunk", "schedule", "raster", "cluster"):
+        eng.set_option(name, -1)
+    Jtn, Ktn = to_np(Jt), to_np(Kt)
+    tJ, tK = np.abs(Jtn[s, mu, nu] - Jo).max(), np.abs(Ktn[s, mu, nu] - Ko).max()
+    _report("multi_state_bench_config", split_J=tJ, split_K=tK, vs_default_J=abs_err(Jtn, Jn),
+            vs_default_K=abs_err(Ktn, Kn))
+    assert tJ <= SPLIT_ABS and tK <= SPLIT_ABS
+    assert abs_err(Jtn, Jfn) < 2 * SPLIT_ABS and abs_err(Ktn, Kfn) < 2 * SPLIT_ABS
 
 
 def test_large_single_full(eng):
