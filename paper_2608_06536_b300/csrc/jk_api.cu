@@ -504,6 +504,21 @@ static std::vector<int> chunk_candidates(int pc0, int naux_max) {
     return out;
 }
 
+// Problems of a host-only batched call (query, lookup): nd_per_mol must split
+// the nd densities of d exactly, and d is never read past its nd entries.
+static jk_status host_batched_problems(int32_t nmol, const jk_factor *f, const int32_t *nd_per_mol, int32_t nd,
+                                       const jk_density *d, std::vector<Problem> &pbs) {
+    if (nmol < 1 || !nd_per_mol) return JK_ERR_SHAPE;
+    pbs.resize(nmol);
+    int off = 0;
+    for (int m = 0; m < nmol; m++) {
+        if (nd_per_mol[m] < 1 || nd_per_mol[m] > nd - off) return JK_ERR_SHAPE;
+        JK_TRY(make_problem(nullptr, &f[m], nd_per_mol[m], d + off, false, pbs[m]));
+        off += nd_per_mol[m];
+    }
+    return off == nd ? JK_OK : JK_ERR_SHAPE;
+}
+
 // Workspace of a call under the configuration the handle would use (h may be
 // NULL: then the larger of the default and the tuned configuration).
 static jk_status query_impl(const jk_ctx *h, jk_op op, int32_t nmol, const jk_factor *f,
@@ -515,15 +530,7 @@ static jk_status query_impl(const jk_ctx *h, jk_op op, int32_t nmol, const jk_fa
     size_t need = 0;
     std::vector<Problem> pbs;
     if (op == JK_OP_BATCHED) {
-        if (nmol < 1 || !nd_per_mol) return JK_ERR_SHAPE;
-        pbs.resize(nmol);
-        int off = 0;
-        for (int m = 0; m < nmol; m++) {
-            jk_status s = make_problem(nullptr, &f[m], nd_per_mol[m], d + off, false, pbs[m]);
-            if (s != JK_OK) return s;
-            off += nd_per_mol[m];
-        }
-        if (off != nd) return JK_ERR_SHAPE;
+        JK_TRY(host_batched_problems(nmol, f, nd_per_mol, nd, d, pbs));
     } else if (op == JK_OP_BUILD || op == JK_OP_ADJOINT || op == JK_OP_BUILD_HOST) {
         pbs.resize(1);
         jk_status s = make_problem(nullptr, f, nd, d, false, pbs[0]);
@@ -716,14 +723,7 @@ jk_status jk_tune_lookup(jk_op op, int32_t nmol, const jk_factor *f, const int32
     if (!f || !d || !cfg) return JK_ERR_ARG;
     std::vector<Problem> pbs;
     if (op == JK_OP_BATCHED) {
-        if (nmol < 1 || !nd_per_mol) return JK_ERR_SHAPE;
-        pbs.resize(nmol);
-        int off = 0;
-        for (int m = 0; m < nmol; m++) {
-            JK_TRY(make_problem(nullptr, &f[m], nd_per_mol[m], d + off, false, pbs[m]));
-            off += nd_per_mol[m];
-        }
-        if (off != nd) return JK_ERR_SHAPE;
+        JK_TRY(host_batched_problems(nmol, f, nd_per_mol, nd, d, pbs));
     } else if (op == JK_OP_BUILD) {
         pbs.resize(1);
         JK_TRY(make_problem(nullptr, f, nd, d, false, pbs[0]));

@@ -85,6 +85,25 @@ def test_workspace_query_rejects_bad_args(lib):
     assert lib.jk_workspace_query(jk.JK_OP_BATCHED, 1, fa, ndm, 2, d, jk.JK_FP64, ct.byref(nb)) == jk.JK_ERR_SHAPE
 
 
+def test_batched_split_must_cover_nd_exactly(lib):
+    """nd_per_mol must split the nd densities exactly, with no zero or negative
+    count; a split that runs past nd is refused before d is read beyond it."""
+    f, _ = _one()
+    fa = (jk.jk_factor * 2)(f, f)
+    d = (jk.jk_density * 2)()
+    for s in range(2):
+        d[s].k, d[s].symmetric, d[s].X, d[s].Y = 3, 0, 0x2000, 0x3000
+    nb = ct.c_size_t()
+    cfg = jk.jk_tune_config()
+    for split, nd, want in [((1, 1), 2, jk.JK_OK), ((1, 2), 2, jk.JK_ERR_SHAPE), ((2, 1), 2, jk.JK_ERR_SHAPE),
+                            ((1, 1), 1, jk.JK_ERR_SHAPE), ((0, 2), 2, jk.JK_ERR_SHAPE), ((-1, 3), 2, jk.JK_ERR_SHAPE),
+                            ((1, 1), 3, jk.JK_ERR_SHAPE)]:
+        ndm = (ct.c_int32 * 2)(*split)
+        assert lib.jk_workspace_query(jk.JK_OP_BATCHED, 2, fa, ndm, nd, d, jk.JK_FP64, ct.byref(nb)) == want
+        got = lib.jk_tune_lookup(jk.JK_OP_BATCHED, 2, fa, ndm, nd, d, jk.JK_FP64, 148, ct.byref(cfg))
+        assert got == (jk.JK_ERR_UNSUPPORTED if want == jk.JK_OK else want)
+
+
 def test_create_rejects_bad_arena(lib):
     h = ct.c_void_p()
     assert lib.jk_create(None, None, 0) == jk.JK_ERR_ARG
