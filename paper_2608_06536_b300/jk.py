@@ -143,6 +143,48 @@ def _host_f64(t):
     return t.contiguous()
 
 
+def _shape(t):
+    return tuple(int(v) for v in t.shape)
+
+
+def _check_problem(L, X, Y=None, sym=None):
+    """Shapes of one molecule, checked before any device work: the C ABI takes
+    pointers and sizes only, so a mismatch here would become an out-of-bounds
+    access in the kernels.  L is [naux][nbf][nbf]; X_s (and Y_s of a
+    non-symmetric density) is [nbf][k_s].  Returns (nbf, naux, nd)."""
+    Ls = _shape(L)
+    if len(Ls) != 3 or Ls[1] != Ls[2] or min(Ls) < 1:
+        raise ValueError(f"L must be [naux][nbf][nbf] with naux, nbf >= 1, got {Ls}")
+    naux, n = Ls[0], Ls[1]
+    nd = len(X)
+    if nd < 1:
+        raise ValueError("at least one density is required")
+    if sym is not None and len(sym) != nd:
+        raise ValueError(f"sym has {len(sym)} entries for {nd} densities")
+    if Y is not None and len(Y) != nd:
+        raise ValueError(f"Y has {len(Y)} entries for {nd} densities")
+    for s in range(nd):
+        xs = _shape(X[s])
+        if len(xs) != 2 or xs[0] != n or xs[1] < 1:
+            raise ValueError(f"X[{s}] must be [{n}][k] with k >= 1, got {xs}")
+        symmetric = (sym is not None and sym[s]) or Y is None or Y[s] is None
+        if not symmetric and _shape(Y[s]) != xs:
+            raise ValueError(f"Y[{s}] must have the shape of X[{s}] {xs}, got {_shape(Y[s])}")
+    return n, naux, nd
+
+
+def _check_output(t, name, shape, device):
+    """A caller-supplied output: contiguous float64 of exactly `shape` on
+    `device`, 8-byte aligned (the library writes shape's elements through
+    the bare pointer)."""
+    if t is None:
+        return
+    if (t.dtype != torch.float64 or t.device != device or _shape(t) != tuple(shape)
+            or not t.is_contiguous() or t.data_ptr() % 8):
+        raise ValueError(f"{name} must be a contiguous float64 tensor of shape {tuple(shape)} on {device}, "
+                         f"got {t.dtype} {_shape(t)} on {t.device}")
+
+
 def _stream_ptr(stream):
     s = stream if stream is not None else torch.cuda.current_stream()
     return ct.c_void_p(s.cuda_stream)
@@ -230,6 +272,12 @@ class Engine:
     def sync_status(self, stream=None):
         self._check(self.lib.jk_sync_status(self._h, _stream_ptr(stream)), self._h)
 
+    def _record(self, stream):
+        """Work issued on a stream other than the current one keeps the arena
+        from being reused (after a later growth) until that work is done."""
+        if stream is not None and self._ws is not None and stream != torch.cuda.current_stream(self.device):
+            self._ws.record_stream(stream)
+
     # -- options ---------------------------------------------------------------
     def set_option(self, name: str, value: int):
         """Handle option (JK_OPT_*): "aux_chunk" (>= 0, 0 = automatic, -1 =
@@ -289,11 +337,15 @@ class Engine:
               J=None, K=None, stream=None):
         """J_s, K_s ([nd][n][n] float64) for D_s = X_s Y_s^T over factor L."""
         p = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        n, _, nd = _check_problem(L, X, Y, sym)
+        if want_j:
+            _check_output(J, "J", (nd, n, n), self.device)
+        if want_k:
+            _check_output(K, "K", (nd, n, n), self.device)
         L = _dev_f64(L, self.device)
         dens = Densities(X, Y, sym, self.device)
-        naux, n = int(L.shape[0]), int(L.shape[1])
+        naux = int(L.shape[0])
         f = jk_factor(n, naux, L.data_ptr())
-        nd = len(dens)
         self._ensure(self.query(JK_OP_BUILD, (jk_factor * 1)(f), dens.c, None, nd, p))
         if want_j and J is None:
             J = torch.empty((nd, n, n), dtype=torch.float64, device=self.device)
@@ -302,6 +354,7 @@ class Engine:
         st = self.lib.jk_build(self._h, ct.byref(f), nd, dens.c, _ptr(J if want_j else None),
                                _ptr(K if want_k else None), p, _stream_ptr(stream))
         self._check(st, self._h)
+        self._record(stream)
         return (J if want_j else None), (K if want_k else None)
 
     def build_host(self, L, X, Y=None, sym=None, precision="split", want_j=True, want_k=True,
@@ -311,14 +364,18 @@ class Engine:
         build; J, K ([nd][n][n], CPU) are written at the end of the stream's
         work (sync=True waits for it)."""
         p = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        n, _, nd = _check_problem(L, X, Y, sym)
+        if want_j:
+            _check_output(J, "J", (nd, n, n), torch.device("cpu"))
+        if want_k:
+            _check_output(K, "K", (nd, n, n), torch.device("cpu"))
         L = _host_f64(L)
         X = [_host_f64(x) for x in X]
-        nd = len(X)
         sym = list(sym) if sym is not None else [False] * nd
         Y = list(Y) if Y is not None else [None] * nd
         Y = [None if (sym[s] or Y[s] is None) else _host_f64(Y[s]) for s in range(nd)]
         symf = [sym[s] or Y[s] is None for s in range(nd)]
-        naux, n = int(L.shape[0]), int(L.shape[1])
+        naux = int(L.shape[0])
         f = jk_factor(n, naux, L.data_ptr())
         dens = (jk_density * nd)()
         for s in range(nd):
@@ -334,6 +391,7 @@ class Engine:
         st = self.lib.jk_build_host(self._h, ct.byref(f), nd, dens, _ptr(J if want_j else None),
                                     _ptr(K if want_k else None), p, _stream_ptr(stream))
         self._check(st, self._h)
+        self._record(stream)
         if sync:
             self.sync_status(stream)
         return (J if want_j else None), (K if want_k else None)
@@ -342,11 +400,10 @@ class Engine:
         """Time the candidate configurations of this build and cache the
         fastest for its shape bucket; returns (config dict, ms per build)."""
         p = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        n, naux, nd = _check_problem(L, X, Y, sym)
         L = _dev_f64(L, self.device)
         dens = Densities(X, Y, sym, self.device)
-        naux, n = int(L.shape[0]), int(L.shape[1])
         f = jk_factor(n, naux, L.data_ptr())
-        nd = len(dens)
         self._ensure(self._tune_bytes(JK_OP_BUILD, (jk_factor * 1)(f), dens.c, None, nd, p))
         J = torch.empty((nd, n, n), dtype=torch.float64, device=self.device)
         K = torch.empty((nd, n, n), dtype=torch.float64, device=self.device)
@@ -354,6 +411,7 @@ class Engine:
         st = self.lib.jk_autotune(self._h, ct.byref(f), nd, dens.c, _ptr(J), _ptr(K), p,
                                   _stream_ptr(stream), int(reps), ct.byref(cfg), ct.byref(ms))
         self._check(st, self._h)
+        self._record(stream)
         return cfg.as_dict(), ms.value
 
     def autotune_batched(self, mols, precision="split", reps: int = 3, stream=None):
@@ -368,6 +426,7 @@ class Engine:
         st = self.lib.jk_autotune_batched(self._h, len(mols), fac, ndm, dall, Jp, Kp, p, _stream_ptr(stream),
                                           int(reps), ct.byref(cfg), ct.byref(ms))
         self._check(st, self._h)
+        self._record(stream)
         return cfg.as_dict(), ms.value
 
     def _tune_bytes(self, op, factors, dens_c, nd_per_mol, nd, p) -> int:
@@ -392,6 +451,13 @@ class Engine:
         Ls, dens = [], []
         fac = (jk_factor * nmol)()
         nd_per = []
+        if nmol < 1:
+            raise ValueError("at least one molecule is required")
+        for m, (L, X, Y, sym) in enumerate(mols):
+            try:
+                _check_problem(L, X, Y, sym)
+            except ValueError as e:
+                raise ValueError(f"molecule {m}: {e}") from None
         for m, (L, X, Y, sym) in enumerate(mols):
             L = _dev_f64(L, self.device)
             d = Densities(X, Y, sym, self.device)
@@ -435,17 +501,20 @@ class Engine:
         st = self.lib.jk_build_batched(self._h, len(mols), fac, ndm, dall, Jp if want_j else None,
                                        Kp if want_k else None, p, _stream_ptr(stream))
         self._check(st, self._h)
+        self._record(stream)
         return outs
 
     def adjoint(self, L, X, Y=None, sym=None, W=None, V=None, want_dl=True,
                 precision="fp64", stream=None):
         """(dX list, dY list, dL or None) for E = sum_s <W_s,K_s> + <V_s,J_s>."""
         p = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        n, naux, nd = _check_problem(L, X, Y, sym)
+        for name, t in (("W", W), ("V", V)):
+            if t is not None and torch.as_tensor(t).numel() != nd * n * n:
+                raise ValueError(f"{name} must hold [{nd}][{n}][{n}] values")
         L = _dev_f64(L, self.device)
         dens = Densities(X, Y, sym, self.device)
-        naux, n = int(L.shape[0]), int(L.shape[1])
         f = jk_factor(n, naux, L.data_ptr())
-        nd = len(dens)
         W = None if W is None else _dev_f64(W, self.device).reshape(nd, n, n)
         V = None if V is None else _dev_f64(V, self.device).reshape(nd, n, n)
         self._ensure(self.query(JK_OP_ADJOINT, (jk_factor * 1)(f), dens.c, None, nd, p))
@@ -456,6 +525,7 @@ class Engine:
         st = self.lib.jk_adjoint(self._h, ct.byref(f), nd, dens.c, _ptr(W), _ptr(V), _ptr(dX),
                                  _ptr(dY), _ptr(dL), p, _stream_ptr(stream))
         self._check(st, self._h)
+        self._record(stream)
         outX, outY, off = [], [], 0
         for k in dens.k:
             outX.append(dX[off:off + n * k].view(n, k))

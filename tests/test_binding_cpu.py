@@ -1,0 +1,105 @@
+"""Host-side checks of the Python binding (no GPU needed): shapes and
+caller-supplied outputs are validated before any device work, since the C ABI
+takes bare pointers and sizes."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2608_06536_b300 import build as pkg_build
+from paper_2608_06536_b300 import jk
+
+
+@pytest.fixture(scope="module")
+def eng():
+    pkg_build.build()
+    return jk.Engine("cuda:0")      # no device work until a call passes its checks
+
+
+def _mol(n=6, naux=4, ks=(2, 3)):
+    rng = np.random.default_rng(0)
+    L = rng.standard_normal((naux, n, n))
+    X = [rng.standard_normal((n, k)) for k in ks]
+    Y = [rng.standard_normal((n, k)) for k in ks]
+    return L, X, Y
+
+
+def test_valid_shapes_pass():
+    L, X, Y = _mol()
+    assert jk._check_problem(L, X, Y, [False, True]) == (6, 4, 2)
+    assert jk._check_problem(L, X, None, None) == (6, 4, 2)
+    # a symmetric density's Y is not used, so its shape is not checked
+    assert jk._check_problem(L, X, [Y[0], np.zeros(3)], [False, True]) == (6, 4, 2)
+
+
+@pytest.mark.parametrize("case", ["L2d", "Lrect", "Lempty", "Xrows", "X1d", "Xk0", "Yshape", "nosym", "noY",
+                                  "none"])
+def test_bad_shapes_rejected_before_device_work(eng, case):
+    L, X, Y = _mol()
+    sym = [False, False]
+    if case == "L2d":
+        L = L[0]
+    elif case == "Lrect":
+        L = L[:, :, :5]
+    elif case == "Lempty":
+        L = L[:0]
+    elif case == "Xrows":
+        X[1] = X[1][:5]
+    elif case == "X1d":
+        X[0] = X[0][:, 0]
+    elif case == "Xk0":
+        X[0], Y[0] = X[0][:, :0], Y[0][:, :0]
+    elif case == "Yshape":
+        Y[1] = Y[1][:, :2]
+    elif case == "nosym":
+        sym = [False]
+    elif case == "noY":
+        Y = Y[:1]
+    elif case == "none":
+        X, Y, sym = [], [], []
+    for call in (lambda: eng.build(L, X, Y, sym, "split"),
+                 lambda: eng.build_host(L, X, Y, sym, "split"),
+                 lambda: eng.adjoint(L, X, Y, sym, precision="split"),
+                 lambda: eng.autotune(L, X, Y, sym, "split"),
+                 lambda: eng.build_batched([(L, X, Y, sym)], "split")):
+        with pytest.raises(ValueError):
+            call()
+
+
+def test_outputs_checked(eng):
+    L, X, Y = _mol()
+    sym = [False, False]
+    good = torch.empty((2, 6, 6), dtype=torch.float64)
+    jk._check_output(good, "J", (2, 6, 6), torch.device("cpu"))
+    jk._check_output(None, "J", (2, 6, 6), torch.device("cpu"))
+    bad = [torch.empty((2, 6, 6), dtype=torch.float32),          # dtype
+           torch.empty((1, 6, 6), dtype=torch.float64),          # too few densities
+           torch.empty((2, 6, 7), dtype=torch.float64)[:, :, :6]]  # not contiguous
+    for t in bad:
+        with pytest.raises(ValueError):
+            jk._check_output(t, "J", (2, 6, 6), torch.device("cpu"))
+        with pytest.raises(ValueError):
+            eng.build_host(L, X, Y, sym, "split", J=t)
+        with pytest.raises(ValueError):
+            eng.build_host(L, X, Y, sym, "split", K=t)
+    # a host tensor passed where the device build writes
+    with pytest.raises(ValueError):
+        eng.build(L, X, Y, sym, "split", J=good)
+
+
+def test_adjoint_seed_sizes_checked(eng):
+    L, X, Y = _mol()
+    for W in (np.zeros((2, 6, 5)), np.zeros((1, 6, 6)), np.zeros((3, 6, 6))):
+        with pytest.raises(ValueError):
+            eng.adjoint(L, X, Y, [False, False], W=W, precision="split")
+        with pytest.raises(ValueError):
+            eng.adjoint(L, X, Y, [False, False], V=W, precision="split")
+
+
+def test_batched_names_the_bad_molecule(eng):
+    good = _mol()
+    L, X, Y = _mol(n=7)
+    X[0] = X[0][:6]
+    with pytest.raises(ValueError, match="molecule 1"):
+        eng.build_batched([(*good, None), (L, X, Y, None)], "split")
+    with pytest.raises(ValueError):
+        eng.build_batched([], "split")
