@@ -182,8 +182,10 @@ jk_status jk_adjoint(jk_handle h, const jk_factor *f, int32_t nd,
  *  - All calls on a device share the one array and it keeps the last call's
  *    contents: calls whose work overlaps on the GPU (different streams, or
  *    different host threads) race on it and must be serialized by the caller.
- *  - Pointers are taken to be device memory (not checked); 16-byte alignment
- *    and shapes are checked as in jk_build (JK_ERR_ARG / JK_ERR_SHAPE). */
+ *  - Pointers are taken to be device memory (not checked).  Shapes are
+ *    checked as in jk_build (JK_ERR_SHAPE); every pointer, outputs included,
+ *    must be 16-byte aligned (JK_ERR_ARG).  All these checks, and the size
+ *    check above, come before any CUDA call. */
 #define JK_STATIC_SCRATCH_BYTES ((size_t)32 << 20)
 jk_status jk_build_noalloc(const jk_factor *f, int32_t nd, const jk_density *d,
                            double *J, double *K, void *stream);

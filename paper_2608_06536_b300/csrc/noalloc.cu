@@ -55,7 +55,7 @@ extern "C" jk_status jk_build_noalloc(const jk_factor *f, int32_t nd, const jk_d
     using namespace jk;
     if (!f || !d) return JK_ERR_ARG;
     if (!J && !K) return JK_OK;
-    if (f->nbf < 1 || f->naux < 1 || nd < 1 || nd > kMaxDens) return JK_ERR_SHAPE;
+    if (f->nbf < 1 || f->nbf > 65535 || f->naux < 1 || nd < 1 || nd > kMaxDens) return JK_ERR_SHAPE;
     if (!f->L || (reinterpret_cast<uintptr_t>(f->L) & 15u)) return JK_ERR_ARG;
     if ((J && (reinterpret_cast<uintptr_t>(J) & 15u)) || (K && (reinterpret_cast<uintptr_t>(K) & 15u)))
         return JK_ERR_ARG;

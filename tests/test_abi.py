@@ -161,3 +161,29 @@ def test_headers_are_c99_and_link(lib, tmp_path):
                     str(src), "-L", libdir, "-ljk", f"-Wl,-rpath,{libdir}", "-o", str(exe)], check=True)
     out = subprocess.run([str(exe)], capture_output=True, text=True)
     assert out.returncode == 0 and out.stdout.strip() == "ok"
+
+
+def test_noalloc_host_checks(lib):
+    """jk_build_noalloc refuses bad arguments and oversize problems before any
+    CUDA call, so these need no device (pointers are never dereferenced)."""
+    lib.jk_build_noalloc.argtypes = [ct.POINTER(jk.jk_factor), ct.c_int32, ct.POINTER(jk.jk_density),
+                                     ct.c_void_p, ct.c_void_p, ct.c_void_p]
+    lib.jk_build_noalloc.restype = ct.c_int
+    J, K = ct.c_void_p(0x10000), ct.c_void_p(0x20000)
+
+    def call(n=10, naux=7, k=3, nd=1, L=0x1000, X=0x2000, J=J, K=K):
+        f = jk.jk_factor(n, naux, L)
+        d = (jk.jk_density * max(nd, 1))()
+        for s in range(max(nd, 1)):
+            d[s].k, d[s].symmetric, d[s].X, d[s].Y = k, 0, X, 0x3000
+        return lib.jk_build_noalloc(ct.byref(f), nd, d, J, K, None)
+
+    assert call(J=None, K=None) == jk.JK_OK                  # nothing to form
+    assert lib.jk_build_noalloc(None, 1, None, J, K, None) == jk.JK_ERR_ARG
+    for kw in [dict(n=0), dict(n=65536), dict(naux=0), dict(nd=0), dict(nd=65), dict(k=0), dict(k=41)]:
+        assert call(**kw) == jk.JK_ERR_SHAPE, kw
+    for kw in [dict(L=0x1008), dict(X=0x2008), dict(J=ct.c_void_p(0x10008)), dict(K=ct.c_void_p(0x20008)),
+               dict(L=0)]:
+        assert call(**kw) == jk.JK_ERR_ARG, kw
+    # panel buffer of naux * nbf * 2k doubles well above the static scratch
+    assert call(n=160, naux=400, k=40) == jk.JK_ERR_OOM
