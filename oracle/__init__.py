@@ -11,7 +11,10 @@ four-index tensor, closed forms (rank-1 factor, identity factor, elementary
 symmetric factor, D = I), the identities of the J/K maps (J depends only on
 D + D^T, K(D^T) = K(D)^T, symmetry, linearity, bra-ket invariance,
 self-adjointness, positivity of <D, J(D)>) and central finite differences
-of E for the adjoint.
+of E for the adjoint.  The dense-density maps, the density gradient and the
+pairings (tests/test_oracle_dense.py) are pinned the same way: brute force,
+closed forms, exact differences of E in D, the chain rule to the factored
+adjoint, and the bra-ket symmetry of the pairing scalars.
 """
 from __future__ import annotations
 
@@ -41,8 +44,11 @@ def lib():
                                          ct.c_int, ip, ip, ip, dp, dp, ct.c_int, ip, ip, ip, dp]
         L.jko_energy.argtypes = [ct.c_int, ct.c_int, dp, ct.c_int, ip, dp, dp,
                                  dp, dp, ct.POINTER(ct.c_longdouble)]
+        L.jko_build_dense.argtypes = [ct.c_int, ct.c_int, dp, ct.c_int, dp, dp, dp]
+        L.jko_density_grad.argtypes = [ct.c_int, ct.c_int, dp, ct.c_int, dp, dp, dp]
+        L.jko_pairs.argtypes = [ct.c_int, ct.c_int, dp, ct.c_int, ip, dp, dp, ct.c_int, ip, dp, dp, dp, dp]
         for f in (L.jko_brute, L.jko_build, L.jko_sample, L.jko_adjoint, L.jko_adjoint_sample,
-                  L.jko_energy):
+                  L.jko_energy, L.jko_build_dense, L.jko_density_grad, L.jko_pairs):
             f.restype = ct.c_int
         _lib = L
     return _lib
@@ -163,3 +169,45 @@ def energy(L: np.ndarray, X: list, Y: list, W=None, V=None) -> float:
     _check(lib().jko_energy(n, naux, _d(L), nd, kp, _d(Xc), _d(Yc), _d(Wc), _d(Vc),
                             ct.byref(E)), "energy")
     return float(E.value)
+
+
+def build_dense(L: np.ndarray, D, want_j=True, want_k=True):
+    """O4: (J, K) as [nd][n][n] for dense, general densities D [nd][n][n]."""
+    L = np.ascontiguousarray(L, np.float64)
+    naux, n, _ = L.shape
+    Dc = np.ascontiguousarray(np.asarray(D, np.float64).reshape(-1, n, n))
+    nd = Dc.shape[0]
+    J = np.empty((nd, n, n)) if want_j else None
+    K = np.empty((nd, n, n)) if want_k else None
+    _check(lib().jko_build_dense(n, naux, _d(L), nd, _d(Dc), _d(J), _d(K)), "build_dense")
+    return J, K
+
+
+def density_grad(L: np.ndarray, W=None, V=None, nd=None):
+    """O4: G_s = dE/dD_s = K(W_s) + J(V_s), [nd][n][n], for
+    E = sum_s <W_s, K(D_s)> + <V_s, J(D_s)>; W or V may be None (zero)."""
+    L = np.ascontiguousarray(L, np.float64)
+    naux, n, _ = L.shape
+    Wc = None if W is None else np.ascontiguousarray(np.asarray(W, np.float64).reshape(-1, n, n))
+    Vc = None if V is None else np.ascontiguousarray(np.asarray(V, np.float64).reshape(-1, n, n))
+    if nd is None:
+        nd = (Wc if Wc is not None else Vc).shape[0]
+    G = np.empty((nd, n, n))
+    _check(lib().jko_density_grad(n, naux, _d(L), nd, _d(Wc), _d(Vc), _d(G)), "density_grad")
+    return G
+
+
+def pairs(L: np.ndarray, A: list, B: list, X: list, Y: list, want_j=True, want_k=True):
+    """O5: (Jp, Kp), each [nl][nr], Jp[a][b] = <WL_a, J(WR_b)> and
+    Kp[a][b] = <WL_a, K(WR_b)> for WL_a = A_a B_a^T, WR_b = X_b Y_b^T."""
+    L = np.ascontiguousarray(L, np.float64)
+    naux, n, _ = L.shape
+    nl, nr = len(A), len(X)
+    kla, klp = _i([a.shape[1] for a in A])
+    kra, krp = _i([x.shape[1] for x in X])
+    Ac, Bc, Xc, Yc = _cat(A), _cat(B), _cat(X), _cat(Y)
+    Jp = np.empty((nl, nr)) if want_j else None
+    Kp = np.empty((nl, nr)) if want_k else None
+    _check(lib().jko_pairs(n, naux, _d(L), nl, klp, _d(Ac), _d(Bc), nr, krp, _d(Xc), _d(Yc),
+                           _d(Jp), _d(Kp)), "pairs")
+    return Jp, Kp

@@ -547,3 +547,170 @@ int jko_energy(int n, int naux, const double *L, int nd, const int *k,
     free(J); free(K);
     return 0;
 }
+
+/* ------------------------------------------------------------------------
+ * O4: dense (general, non-symmetric) densities, the general primitive of
+ * Eq. 4 (Sec. II.C) with a dense argument instead of a factored one:
+ *   J(D)_{mu nu} = sum_P <L^P, D> L^P_{mu nu}
+ *   K(D)_{mu nu} = sum_P sum_{lam sig} L^P_{mu lam} D_{lam sig} L^P_{nu sig}
+ * (the CD form of the O1 definitions).  K is formed per P as T = L^P D
+ * followed by T (L^P)^T, so the transpose on the right factor is explicit
+ * and no symmetry of L^P is assumed.  DJ feeds J, DK feeds K; either side may
+ * be skipped (NULL input or NULL output).  With add != 0 the two results are
+ * summed into one output, J: the density gradient dE/dD_s = K(W_s) + J(V_s)
+ * of E = sum_s <W_s, K(D_s)> + <V_s, J(D_s)> (Eq. 1, Sec. II.A), each entry
+ * rounded to double once.
+ * ---------------------------------------------------------------------- */
+static int dense_maps(int n, int naux, const double *L, int nd, const double *DJ,
+                      const double *DK, double *J, double *K, int add)
+{
+    if (n < 1 || naux < 0 || nd < 0) return 1;
+    size_t n2 = (size_t)n * n;
+    ld *Jacc = (ld *)malloc(n2 * sizeof(ld));
+    ld *Kacc = (ld *)malloc(n2 * sizeof(ld));
+    ld *T = (ld *)malloc(n2 * sizeof(ld));
+    if (!Jacc || !Kacc || !T) {
+        free(Jacc); free(Kacc); free(T);
+        return 2;
+    }
+    const int doJ = DJ && (J || add), doK = DK && (add ? J != NULL : K != NULL);
+    for (int s = 0; s < nd; s++) {
+        const double *Ds_J = DJ ? DJ + (size_t)s * n2 : NULL;
+        const double *Ds_K = DK ? DK + (size_t)s * n2 : NULL;
+        memset(Jacc, 0, n2 * sizeof(ld));
+        memset(Kacc, 0, n2 * sizeof(ld));
+        for (int P = 0; P < naux; P++) {
+            const double *LP = L + (size_t)P * n2;
+            if (doJ) {
+                ld gamma = frob_dd(n, LP, Ds_J);
+                for (size_t e = 0; e < n2; e++) Jacc[e] += gamma * (ld)LP[e];
+            }
+            if (doK) {
+                #pragma omp parallel for schedule(static)
+                for (int mu = 0; mu < n; mu++)
+                    for (int sig = 0; sig < n; sig++) {
+                        ld t = 0.0L;
+                        for (int lam = 0; lam < n; lam++)
+                            t += (ld)LP[IDX2(mu, lam, n)] * (ld)Ds_K[IDX2(lam, sig, n)];
+                        T[IDX2(mu, sig, n)] = t;
+                    }
+                #pragma omp parallel for schedule(static)
+                for (int mu = 0; mu < n; mu++)
+                    for (int nu = 0; nu < n; nu++) {
+                        ld kk = 0.0L;
+                        for (int sig = 0; sig < n; sig++)
+                            kk += T[IDX2(mu, sig, n)] * (ld)LP[IDX2(nu, sig, n)];
+                        Kacc[IDX2(mu, nu, n)] += kk;
+                    }
+            }
+        }
+        for (size_t e = 0; e < n2; e++) {
+            if (add) {
+                J[(size_t)s * n2 + e] = (double)(Jacc[e] + Kacc[e]);
+            } else {
+                if (J) J[(size_t)s * n2 + e] = (double)Jacc[e];
+                if (K) K[(size_t)s * n2 + e] = (double)Kacc[e];
+            }
+        }
+    }
+    free(Jacc); free(Kacc); free(T);
+    return 0;
+}
+
+/* J_s = J(D_s), K_s = K(D_s) for dense D [nd][n][n]; J or K may be NULL. */
+int jko_build_dense(int n, int naux, const double *L, int nd, const double *D,
+                    double *J, double *K)
+{
+    return dense_maps(n, naux, L, nd, D, D, J, K, 0);
+}
+
+/* G_s = dE/dD_s = K(W_s) + J(V_s) [nd][n][n]; W or V may be NULL (zero). */
+int jko_density_grad(int n, int naux, const double *L, int nd, const double *W,
+                     const double *V, double *G)
+{
+    if (!G) return 1;
+    return dense_maps(n, naux, L, nd, V, W, G, NULL, 1);
+}
+
+/* ------------------------------------------------------------------------
+ * O5: scalar bra-ket pairings of many left and right weight densities, the
+ * contraction of Eq. 4 (Sec. II.C) with plain (non-derivative) CD integrals,
+ * i.e. the J and K terms Eq. 5 (Sec. II.D) combines:
+ *   Jp[a][b] = sum_{mu nu lam sig} WL_a^{mu nu} (mu nu|lam sig) WR_b^{lam sig}
+ *            = sum_P <L^P, WL_a> <L^P, WR_b>
+ *   Kp[a][b] = sum_{mu nu lam sig} WL_a^{mu nu} (mu lam|nu sig) WR_b^{lam sig}
+ *            = sum_P <WL_a, L^P WR_b (L^P)^T>
+ * with factored WL_a = A_a B_a^T ([n][kl_a] blocks concatenated in a order)
+ * and WR_b = X_b Y_b^T ([n][kr_b] blocks).  Per P: the two metric dots, then
+ * M_b = L^P WR_b (L^P)^T and its Frobenius product with every WL_a.  Jp, Kp
+ * are [nl][nr]; either may be NULL.
+ * ---------------------------------------------------------------------- */
+int jko_pairs(int n, int naux, const double *L, int nl, const int *kl,
+              const double *A, const double *B, int nr, const int *kr,
+              const double *X, const double *Y, double *Jp, double *Kp)
+{
+    if (n < 1 || naux < 0 || nl < 1 || nr < 1) return 1;
+    size_t n2 = (size_t)n * n;
+    ld *WL = (ld *)malloc((size_t)nl * n2 * sizeof(ld));
+    ld *WR = (ld *)malloc((size_t)nr * n2 * sizeof(ld));
+    ld *T = (ld *)malloc(n2 * sizeof(ld));
+    ld *M = (ld *)malloc(n2 * sizeof(ld));
+    ld *gl = (ld *)malloc((size_t)nl * sizeof(ld));
+    ld *gr = (ld *)malloc((size_t)nr * sizeof(ld));
+    ld *Jacc = (ld *)calloc((size_t)nl * nr, sizeof(ld));
+    ld *Kacc = (ld *)calloc((size_t)nl * nr, sizeof(ld));
+    int rc = 0;
+    if (!WL || !WR || !T || !M || !gl || !gr || !Jacc || !Kacc) { rc = 2; goto out; }
+    {
+        size_t off = 0;
+        for (int a = 0; a < nl; a++) {
+            if (kl[a] < 1) { rc = 1; goto out; }
+            dense_density(n, kl[a], A + off, B + off, WL + (size_t)a * n2);
+            off += (size_t)n * kl[a];
+        }
+        off = 0;
+        for (int b = 0; b < nr; b++) {
+            if (kr[b] < 1) { rc = 1; goto out; }
+            dense_density(n, kr[b], X + off, Y + off, WR + (size_t)b * n2);
+            off += (size_t)n * kr[b];
+        }
+    }
+    for (int P = 0; P < naux; P++) {
+        const double *LP = L + (size_t)P * n2;
+        for (int a = 0; a < nl; a++) gl[a] = frob_dl(n, LP, WL + (size_t)a * n2);
+        for (int b = 0; b < nr; b++) gr[b] = frob_dl(n, LP, WR + (size_t)b * n2);
+        for (int b = 0; b < nr; b++) {
+            const ld *Wb = WR + (size_t)b * n2;
+            #pragma omp parallel for schedule(static)
+            for (int mu = 0; mu < n; mu++)
+                for (int sig = 0; sig < n; sig++) {
+                    ld t = 0.0L;
+                    for (int lam = 0; lam < n; lam++)
+                        t += (ld)LP[IDX2(mu, lam, n)] * Wb[IDX2(lam, sig, n)];
+                    T[IDX2(mu, sig, n)] = t;
+                }
+            #pragma omp parallel for schedule(static)
+            for (int mu = 0; mu < n; mu++)
+                for (int nu = 0; nu < n; nu++) {
+                    ld m = 0.0L;
+                    for (int sig = 0; sig < n; sig++)
+                        m += T[IDX2(mu, sig, n)] * (ld)LP[IDX2(nu, sig, n)];
+                    M[IDX2(mu, nu, n)] = m;
+                }
+            for (int a = 0; a < nl; a++) {
+                const ld *Wa = WL + (size_t)a * n2;
+                ld s = 0.0L;
+                for (size_t e = 0; e < n2; e++) s += Wa[e] * M[e];
+                Kacc[(size_t)a * nr + b] += s;
+                Jacc[(size_t)a * nr + b] += gl[a] * gr[b];
+            }
+        }
+    }
+    for (size_t e = 0; e < (size_t)nl * nr; e++) {
+        if (Jp) Jp[e] = (double)Jacc[e];
+        if (Kp) Kp[e] = (double)Kacc[e];
+    }
+out:
+    free(WL); free(WR); free(T); free(M); free(gl); free(gr); free(Jacc); free(Kacc);
+    return rc;
+}
