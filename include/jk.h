@@ -86,7 +86,10 @@ typedef struct {
 } jk_density;
 
 /* Which entry point a workspace query is for. */
-typedef enum { JK_OP_BUILD = 0, JK_OP_ADJOINT = 1, JK_OP_BATCHED = 2, JK_OP_BUILD_HOST = 3 } jk_op;
+typedef enum {
+    JK_OP_BUILD = 0, JK_OP_ADJOINT = 1, JK_OP_BATCHED = 2, JK_OP_BUILD_HOST = 3,
+    JK_OP_BUILD_DENSE = 4, JK_OP_DENSITY_GRAD = 5
+} jk_op;
 
 /* Create a handle over a caller-owned device arena of `bytes` bytes
  * (256-byte aligned).  The arena must stay valid until jk_destroy. */
@@ -96,6 +99,8 @@ jk_status jk_destroy(jk_handle h);
 /* Bytes of arena a call with these shapes needs (host-only, no GPU work).
  * For JK_OP_BATCHED pass nmol factors and the concatenated densities, with
  * nd_per_mol giving the split; otherwise nmol = 1 and nd_per_mol may be NULL.
+ * For JK_OP_BUILD_DENSE and JK_OP_DENSITY_GRAD only f and nd are read (d may
+ * be NULL); the answer covers both maps.
  * Without a handle the answer covers both the default configuration and a
  * tuned one cached for these shapes (see jk_autotune); the _handle form
  * answers for the configuration that handle's options select. */
@@ -158,6 +163,34 @@ jk_status jk_adjoint(jk_handle h, const jk_factor *f, int32_t nd,
                      const jk_density *d, const double *W, const double *V,
                      double *dX, double *dY, double *dL,
                      jk_precision p, void *stream);
+
+/* ---- dense (general, non-symmetric) densities -----------------------------
+ * The general primitive of Eq. 4 (Sec. II.C) takes a weight density that is
+ * neither symmetric nor given in factored form.  For dense D:
+ *   J(D) = sum_P <L^P, D> L^P          K(D) = sum_P L^P D L^P
+ * J sees only the symmetric part of D; K(D^T) = K(D)^T.  K runs on the engine
+ * `p` selects (per aux chunk: the panels L^P D for all densities in one GEMM,
+ * then each K_s as the reduction of those panels against L^P itself); J runs
+ * on the FP64 streams in both precisions (the metric dot <L^P, D> read from
+ * D directly).  Arena: jk_workspace_query with JK_OP_BUILD_DENSE /
+ * JK_OP_DENSITY_GRAD (the aux chunk follows JK_OPT_AUX_CHUNK; tuned
+ * configurations do not apply).  Validation and status as jk_build.
+ *
+ * jk_build_dense: J_s = J(D_s), K_s = K(D_s).
+ *   D    : [nd][nbf][nbf] FP64 input (16-byte aligned).
+ *   J, K : [nd][nbf][nbf] FP64 outputs; either may be NULL (not formed). */
+jk_status jk_build_dense(jk_handle h, const jk_factor *f, int32_t nd, const double *D,
+                         double *J, double *K, jk_precision p, void *stream);
+
+/* jk_density_grad: the density gradient of E = sum_s <W_s, K(D_s)> + <V_s, J(D_s)>
+ * (Eq. 1, Sec. II.A), with D_s a free dense matrix:
+ *   G_s = dE/dD_s = K(W_s) + J(V_s)
+ * (K and J are self-adjoint under the Frobenius pairing).  jk_adjoint's
+ * dX_s = G_s Y_s and dY_s = G_s^T X_s are this gradient carried through
+ * D_s = X_s Y_s^T.  W, V: [nd][nbf][nbf] FP64 seeds, either may be NULL
+ * (zero; both NULL writes G = 0).  G: [nd][nbf][nbf] FP64 output. */
+jk_status jk_density_grad(jk_handle h, const jk_factor *f, int32_t nd, const double *W,
+                          const double *V, double *G, jk_precision p, void *stream);
 
 /* ---- building without a caller arena -------------------------------------
  * The paper has no counterpart of this entry point; it serves callers that

@@ -531,6 +531,76 @@ jk_status fp64_build(jk_ctx *h, const Problem &pb, cudaStream_t st) {
     return JK_OK;
 }
 
+// ---- dense densities -----------------------------------------------------
+// K_s = sum_P (L^P DK_s)(L^P)^T: per aux chunk one batched GEMM forms the
+// panels T[(p, mu)][s*n + nu] = (L^p DK_s)[mu][nu] for every density, then
+// each K_s is the reduction over (p, nu) of T against L^p itself (the second
+// factor needs no panel).  J_s = sum_P <L^P, DJ_s> L^P on the FP64 streams.
+
+// Aux indices per chunk: the panel chunk (pc x n x nd*n doubles) within
+// ~256 MB unless a chunk is set, and its rows within the GEMM grid's limit.
+static int fp64_dense_pchunk(const DenseProb &dp) {
+    const size_t per = (size_t)dp.n * dp.n * dp.nd * 8;
+    size_t pc = per ? ((size_t)256 << 20) / per : 1;
+    if (pc < 1) pc = 1;
+    if (dp.aux_chunk > 0) pc = dp.aux_chunk;
+    if (pc > (size_t)dp.naux) pc = dp.naux;
+    const size_t maxrows = (size_t)65535 * GBM;
+    if (pc * dp.n > maxrows) pc = maxrows / dp.n;
+    return (int)pc;
+}
+
+size_t fp64_dense_workspace(const DenseProb &dp) {
+    const size_t n2 = (size_t)dp.n * dp.n, nd = dp.nd;
+    size_t b = 0;
+    if (dp.DK) {
+        b += align_up((size_t)fp64_dense_pchunk(dp) * n2 * nd * 8);   // panels T
+        b += align_up((size_t)kMaxRankSplit * n2 * 8);               // rank-update partials
+    }
+    if (dp.DJ) {
+        b += align_up(nd * (size_t)dp.naux * 8);                     // gamma
+        if (dp.add_j) b += align_up(nd * n2 * 8);                    // J before it joins K
+    }
+    return b;
+}
+
+jk_status fp64_dense(jk_ctx *h, const DenseProb &dp, cudaStream_t st) {
+    const int n = dp.n, naux = dp.naux, nd = dp.nd;
+    const long long n2 = (long long)n * n, ctot = (long long)nd * n;
+    const int pc = fp64_dense_pchunk(dp);
+    Arena &ar = h->arena;
+    double *T = nullptr, *part = nullptr, *gamma = nullptr, *Jt = nullptr;
+    if (dp.DK) {
+        T = ar.take<double>((size_t)pc * n2 * nd);
+        part = ar.take<double>((size_t)kMaxRankSplit * n2);
+        if (!T || !part) return set_error(h, JK_ERR_OOM, "workspace too small for the dense FP64 build");
+    }
+    if (dp.DJ) {
+        gamma = ar.take<double>((size_t)nd * naux);
+        if (dp.add_j) Jt = ar.take<double>((size_t)nd * n2);
+        if (!gamma || (dp.add_j && !Jt)) return set_error(h, JK_ERR_OOM, "workspace too small for the dense J");
+    }
+    if (dp.DK) {
+        for (int P0 = 0; P0 < naux; P0 += pc) {
+            const int np = naux - P0 < pc ? naux - P0 : pc;
+            const double *Lc = dp.L + (long long)P0 * n2;
+            // T[(p, mu)][s*n + nu] = sum_lam L^{P0+p}[mu][lam] DK_s[lam][nu]  (batch s)
+            JK_TRY(dgemm(h, nd, np * n, n, n, gop(Lc, 0, n, 0, 1, n), gop(dp.DK, n2, 1, 0, n, n), T, ctot, n,
+                         1.0, 0.0, st));
+            // K_s (+)= sum_{p, nu} T[(p, mu)][s*n + nu] L^{P0+p}[sig][nu]
+            for (int s = 0; s < nd; s++)
+                JK_TRY(dgemm_split_q(h, n, n, np, n, T + (long long)s * n, ctot, (long long)n * ctot, 1, Lc, n,
+                                     n2, 1, dp.K + s * n2, P0 > 0, part, kMaxRankSplit, st));
+        }
+    }
+    if (dp.DJ) {
+        JK_TRY(fp64_frob_all(h, dp.L, n, naux, dp.DJ, nd, gamma, st));
+        JK_TRY(fp64_jstream_dense(h, dp.L, n, naux, gamma, nd, dp.add_j ? Jt : dp.J, st));
+        if (dp.add_j) JK_TRY(fp64_axpy(h, dp.K, Jt, nd * n2, st));
+    }
+    return JK_OK;
+}
+
 size_t fp64_adjoint_workspace(const Problem &pb, int pc, bool want_dl) {
     size_t n = pb.n, nd = pb.nd, A = pb.naux;
     size_t b = 0;

@@ -504,6 +504,56 @@ static std::vector<int> chunk_candidates(int pc0, int naux_max) {
     return out;
 }
 
+// ---- dense densities (jk_build_dense, jk_density_grad) ----------------------
+
+// Shape of a dense call; with check_ptrs, the factor is also checked (the
+// arrays are checked by the entry points).
+static jk_status make_dense(jk_ctx *h, const jk_factor *f, int32_t nd, bool check_ptrs, DenseProb &dp) {
+    if (!f) return set_error(h, JK_ERR_ARG, "factor is NULL");
+    if (f->nbf < 1 || f->naux < 1)
+        return set_error(h, JK_ERR_SHAPE, "nbf=%d naux=%d must be >= 1", f->nbf, f->naux);
+    if (f->nbf > 65535) return set_error(h, JK_ERR_SHAPE, "nbf=%d exceeds 65535", f->nbf);
+    if (nd < 1 || nd > kMaxDens) return set_error(h, JK_ERR_SHAPE, "nd=%d must be in [1, %d]", nd, kMaxDens);
+    dp.n = f->nbf;
+    dp.naux = f->naux;
+    dp.nd = nd;
+    dp.L = f->L;
+    if (check_ptrs) {
+        if (!f->L) return set_error(h, JK_ERR_ARG, "factor L is NULL");
+        if (!aligned16(f->L)) return set_error(h, JK_ERR_ARG, "factor L is not 16-byte aligned");
+        if (!device_readable(f->L)) return set_error(h, JK_ERR_ARG, "factor L is not device memory");
+    }
+    return JK_OK;
+}
+
+static size_t dense_bytes(const DenseProb &dp, jk_precision p) {
+    return p == JK_FP64 ? fp64_dense_workspace(dp) : split_dense_workspace(dp);
+}
+
+// Workspace of the largest form of a dense call (both maps; for the gradient,
+// J formed apart and added), for the query: the pointers only mark presence.
+static size_t dense_query_bytes(DenseProb dp, jk_op op, jk_precision p) {
+    static const double kShapeOnly = 0.0;
+    dp.DK = dp.DJ = &kShapeOnly;
+    dp.add_j = op == JK_OP_DENSITY_GRAD;
+    return dense_bytes(dp, p);
+}
+
+// Run-time configuration of a dense call: the handle's explicit options.
+static void dense_config(jk_ctx *h, DenseProb &dp) {
+    dp.aux_chunk = h->aux_chunk > 0 ? h->aux_chunk : 0;
+    h->cur_raster = h->raster >= 0 ? h->raster : 0;
+    h->cur_cluster = h->cluster >= 0 ? h->cluster : kDefaultCluster;
+}
+
+static jk_status run_dense(jk_ctx *h, const DenseProb &dp, jk_precision p, cudaStream_t st) {
+    const size_t need = flags_bytes() + dense_bytes(dp, p);
+    if (h->arena.bytes < need)
+        return set_error(h, JK_ERR_OOM, "arena has %zu bytes, this dense call needs %zu", h->arena.bytes, need);
+    h->arena.reset(flags_bytes());
+    return p == JK_FP64 ? fp64_dense(h, dp, st) : split_dense(h, dp, st);
+}
+
 // Problems of a host-only batched call (query, lookup): nd_per_mol must split
 // the nd densities of d exactly, and d is never read past its nd entries.
 static jk_status host_batched_problems(int32_t nmol, const jk_factor *f, const int32_t *nd_per_mol, int32_t nd,
@@ -524,8 +574,17 @@ static jk_status host_batched_problems(int32_t nmol, const jk_factor *f, const i
 static jk_status query_impl(const jk_ctx *h, jk_op op, int32_t nmol, const jk_factor *f,
                             const int32_t *nd_per_mol, int32_t nd, const jk_density *d, jk_precision p,
                             size_t *bytes) {
-    if (!bytes || !f || !d) return JK_ERR_ARG;
+    if (!bytes || !f) return JK_ERR_ARG;
     if (p != JK_FP64 && p != JK_SPLIT_BF16) return JK_ERR_ARG;
+    if (op == JK_OP_BUILD_DENSE || op == JK_OP_DENSITY_GRAD) {
+        DenseProb dp;
+        jk_status s = make_dense(nullptr, f, nd, false, dp);
+        if (s != JK_OK) return s;
+        dp.aux_chunk = h && h->aux_chunk > 0 ? h->aux_chunk : 0;
+        *bytes = dense_query_bytes(dp, op, p) + flags_bytes() + kArenaAlign;
+        return JK_OK;
+    }
+    if (!d) return JK_ERR_ARG;
     const int sms = h ? h->num_sms : current_sms();
     size_t need = 0;
     std::vector<Problem> pbs;
@@ -758,6 +817,55 @@ jk_status jk_adjoint(jk_handle h, const jk_factor *f, int32_t nd, const jk_densi
                          h->arena.bytes, need);
     return p == JK_FP64 ? fp64_adjoint(h, pb, W, V, dX, dY, dL, st)
                         : split_adjoint(h, pb, W, V, dX, dY, dL, st);
+}
+
+jk_status jk_build_dense(jk_handle h, const jk_factor *f, int32_t nd, const double *D, double *J, double *K,
+                         jk_precision p, void *stream) {
+    JK_TRY(begin_call(h));
+    if (p != JK_FP64 && p != JK_SPLIT_BF16)
+        return set_error(h, JK_ERR_ARG, "unknown precision %d", (int)p);
+    DenseProb dp;
+    JK_TRY(make_dense(h, f, nd, true, dp));
+    if (!D) return set_error(h, JK_ERR_ARG, "D is NULL");
+    JK_TRY(check_in(h, D, "D"));
+    JK_TRY(check_out(h, J, "J"));
+    JK_TRY(check_out(h, K, "K"));
+    if (!J && !K) return JK_OK;
+    dp.DJ = J ? D : nullptr;
+    dp.DK = K ? D : nullptr;
+    dp.J = J;
+    dp.K = K;
+    dense_config(h, dp);
+    return run_dense(h, dp, p, static_cast<cudaStream_t>(stream));
+}
+
+jk_status jk_density_grad(jk_handle h, const jk_factor *f, int32_t nd, const double *W, const double *V,
+                          double *G, jk_precision p, void *stream) {
+    JK_TRY(begin_call(h));
+    if (p != JK_FP64 && p != JK_SPLIT_BF16)
+        return set_error(h, JK_ERR_ARG, "unknown precision %d", (int)p);
+    DenseProb dp;
+    JK_TRY(make_dense(h, f, nd, true, dp));
+    if (!G) return set_error(h, JK_ERR_ARG, "G is NULL");
+    JK_TRY(check_out(h, G, "G"));
+    JK_TRY(check_in(h, W, "W"));
+    JK_TRY(check_in(h, V, "V"));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (!W && !V) {
+        // both seeds zero: so is the gradient
+        JK_CUDA_TRY(h, cudaMemsetAsync(G, 0, static_cast<size_t>(nd) * dp.n * dp.n * 8, st));
+        return JK_OK;
+    }
+    dp.DK = W;
+    dp.DJ = V;
+    if (W) {
+        dp.K = G;
+        dp.add_j = V != nullptr;
+    } else {
+        dp.J = G;
+    }
+    dense_config(h, dp);
+    return run_dense(h, dp, p, st);
 }
 
 jk_status jk_set_option(jk_handle h, jk_option opt, int64_t value) {

@@ -156,6 +156,26 @@ size_t split_batched_workspace(int nmol, const Problem *pbs);
 int split_auto_pchunk(const Problem &pb);   // aux chunk chosen from the workspace budget
 jk_status split_batched(jk_ctx *h, int nmol, const Problem *pbs, cudaStream_t st);
 
+// ---- dense (general, non-symmetric) densities ------------------------------
+// J(DJ_s) and K(DK_s) for dense [nd][n][n] arguments (Eq. 4 with a dense
+// argument): K_s = sum_P (L^P DK_s)(L^P)^T, J_s = sum_P <L^P, DJ_s> L^P.  With
+// add_j, J is formed in the workspace and added to K (the density gradient
+// K(W) + J(V)); K then must not be NULL.
+struct DenseProb {
+    int n = 0, naux = 0, nd = 0;
+    const double *L = nullptr;
+    const double *DK = nullptr;   // input of K, or NULL (no K)
+    const double *DJ = nullptr;   // input of J, or NULL (no J)
+    double *K = nullptr;          // [nd][n][n]
+    double *J = nullptr;          // [nd][n][n] (unused with add_j)
+    bool add_j = false;
+    int aux_chunk = 0;            // aux indices per chunk (0 = automatic)
+};
+size_t fp64_dense_workspace(const DenseProb &dp);
+jk_status fp64_dense(jk_ctx *h, const DenseProb &dp, cudaStream_t st);
+size_t split_dense_workspace(const DenseProb &dp);
+jk_status split_dense(jk_ctx *h, const DenseProb &dp, cudaStream_t st);
+
 // ---- batched builds (batched.cu) ------------------------------------------
 jk_status batched_build(jk_ctx *h, int nmol, const Problem *pbs, jk_precision p,
                         cudaStream_t st);

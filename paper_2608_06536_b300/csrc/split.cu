@@ -1344,6 +1344,124 @@ static jk_status gemm_into(jk_ctx *h, const Sliced &A, const Sliced &B, double *
     return fp64_axpy(h, out, tmp, static_cast<long long>(A.rows) * B.rows, st);
 }
 
+// ---------------------------------------------------------------------------
+// Dense densities on the split engine
+// ---------------------------------------------------------------------------
+// K_s = sum_P (L^P DK_s)(L^P)^T.  Per aux chunk: the panels
+// T[(p, mu)][s*n + nu] = (L^p DK_s)[mu][nu] in one sliced GEMM (A = the L
+// chunk, B = the rows (s, nu) of DK^T, sliced straight from DK), then per
+// density the reduction over (p, nu) of T against L itself, sliced once per
+// chunk with rows sig and reduction index (p, nu) (the layout the adjoint
+// uses for dX).  J on the FP64 streams of the aux stream, overlapped.
+
+// Aux indices per chunk: the per-index workspace (three sliced n x n blocks
+// and one FP64 panel row block) within ~12 GB, panel rows within the grid.
+static int dense_pchunk(const DenseProb &dp) {
+    const size_t n = dp.n;
+    const size_t per = n * n * (oz::S * 2) * 3 + n * even_ld(static_cast<long long>(dp.nd) * dp.n) * 8;
+    size_t pc = per ? (static_cast<size_t>(12) << 30) / per : 1;
+    if (pc < 1) pc = 1;
+    if (dp.aux_chunk > 0) pc = dp.aux_chunk;
+    if (pc > static_cast<size_t>(dp.naux)) pc = dp.naux;
+    const size_t maxrows = static_cast<size_t>(65535) * oz::BM;
+    if (pc * n > maxrows) pc = maxrows / n;
+    return static_cast<int>(pc);
+}
+
+static size_t dense_partials(const DenseProb &dp, int pc) {
+    const int ns = nsuper_of(pc * dp.n);
+    return ns > 1 ? static_cast<size_t>(ns) * part_rows(dp.n) * even_ld(dp.n) : 1;
+}
+
+size_t split_dense_workspace(const DenseProb &dp) {
+    const size_t n2 = static_cast<size_t>(dp.n) * dp.n, nd = dp.nd;
+    size_t b = 0;
+    if (dp.DJ) {
+        b += align_up(nd * dp.naux * 8);                                  // gamma
+        if (dp.add_j) b += align_up(nd * n2 * 8);                         // J before it joins K
+    }
+    if (dp.DK) {
+        const int pc = dense_pchunk(dp), n = dp.n, ctot = dp.nd * dp.n;
+        const long long ldT = even_ld(ctot);
+        b += sliced_bytes(pc * n, n, n);                                  // L chunk, panel operand
+        b += sliced_bytes(ctot, n, 1);                                    // rows (s, nu) of DK^T
+        b += align_up(static_cast<size_t>(pc) * n * ldT * 8);             // FP64 panels T
+        b += sliced_bytes(n, pc * n, 1);                                  // L chunk, rows sig
+        b += sliced_bytes(n, pc * n, 1);                                  // one density's panels, rows mu
+        b += align_up(dense_partials(dp, pc) * 8);                        // split-K partials
+        b += align_up(n2 * 8);                                            // a chunk's K before it is added
+        if (n > oz::SUPER)
+            b += align_up(static_cast<size_t>(nsuper_of(n)) * part_rows(static_cast<long long>(pc) * n) * ldT * 8);
+    }
+    return b;
+}
+
+jk_status split_dense(jk_ctx *h, const DenseProb &dp, cudaStream_t st) {
+    const int n = dp.n, naux = dp.naux, nd = dp.nd;
+    const long long n2 = static_cast<long long>(n) * n;
+    Arena &ar = h->arena;
+    double *gamma = nullptr, *Jt = nullptr;
+    if (dp.DJ) {
+        gamma = ar.take<double>(static_cast<size_t>(nd) * naux);
+        if (dp.add_j) Jt = ar.take<double>(static_cast<size_t>(nd) * n2);
+        if (!gamma || (dp.add_j && !Jt)) return set_error(h, JK_ERR_OOM, "workspace too small for the dense J");
+    }
+    const int pc = dp.DK ? dense_pchunk(dp) : 0, ctot = nd * n;
+    const long long ldT = even_ld(ctot);
+    Sliced Ls, Ds, LB, TS;
+    double *T = nullptr, *tmp = nullptr;
+    long long *Pbuf = nullptr, *Ppanel = nullptr;
+    if (dp.DK) {
+        bool ok = take_sliced(ar, pc * n, n, n, Ls) && take_sliced(ar, ctot, n, 1, Ds);
+        T = ar.take<double>(static_cast<size_t>(pc) * n * ldT);
+        ok = ok && T && take_sliced(ar, n, pc * n, 1, LB) && take_sliced(ar, n, pc * n, 1, TS);
+        Pbuf = ar.take<long long>(dense_partials(dp, pc));
+        tmp = ar.take<double>(static_cast<size_t>(n2));
+        if (n > oz::SUPER)
+            Ppanel = ar.take<long long>(static_cast<size_t>(nsuper_of(n)) * part_rows(static_cast<long long>(pc) * n) *
+                                        ldT);
+        if (!ok || !Pbuf || !tmp || (n > oz::SUPER && !Ppanel))
+            return set_error(h, JK_ERR_OOM, "workspace too small for the dense split build");
+    }
+    if (dp.DJ) {
+        JK_TRY(fork_jstream(h, st));
+        JK_TRY(fp64_frob_all(h, dp.L, n, naux, dp.DJ, nd, gamma, h->aux_stream));
+        JK_TRY(fp64_jstream_dense(h, dp.L, n, naux, gamma, nd, dp.add_j ? Jt : dp.J, h->aux_stream));
+    }
+    if (dp.DK) {
+        // rows (s, nu) of DK^T, reduction over lam: element DK_s[lam][nu]
+        oz::Src dsrc{dp.DK, n2, 0, n, n, n, 1};
+        JK_TRY(slice_operand(h, dsrc, ctot, n, 1, Ds, st));
+        for (int P0 = 0; P0 < naux; P0 += pc) {
+            const int np = naux - P0 < pc ? naux - P0 : pc;
+            oz::Src lsrc{dp.L + P0 * n2, n, 0, 1, n};
+            JK_TRY(slice_operand(h, lsrc, np * n, n, n, Ls, st));
+            // T[(p, mu)][s*n + nu] = sum_lam L^p[mu][lam] DK_s[lam][nu]
+            if (n > oz::SUPER) {
+                JK_TRY(ozgemm(h, Ls, Ds, nullptr, 0, Ppanel, st));
+                JK_TRY(reduce_partials(h, Ppanel, nsuper_of(n), Ls, Ds, T, ldT, false, st));
+            } else {
+                JK_TRY(ozgemm(h, Ls, Ds, T, ldT, nullptr, st));
+            }
+            // L with rows sig and reduction over (p, nu)
+            oz::Src lm{dp.L + P0 * n2, n, n2, 1, n};
+            JK_TRY(slice_operand(h, lm, n, np * n, 1, LB, st));
+            for (int s = 0; s < nd; s++) {
+                // rows mu, reduction over (p, nu): T[(p, mu)][s*n + nu]
+                oz::Src ts{T + static_cast<long long>(s) * n, ldT, static_cast<long long>(n) * ldT, 1, n};
+                JK_TRY(slice_operand(h, ts, n, np * n, 1, TS, st));
+                // K_s (+)= sum_{p, nu} T[(p, mu)][s*n + nu] L^p[sig][nu]
+                JK_TRY(gemm_into(h, TS, LB, dp.K + s * n2, n, P0 > 0, Pbuf, tmp, st));
+            }
+        }
+    }
+    if (dp.DJ) {
+        JK_TRY(join_jstream(h, st));
+        if (dp.add_j) JK_TRY(fp64_axpy(h, dp.K, Jt, static_cast<long long>(nd) * n2, st));
+    }
+    return JK_OK;
+}
+
 // Aux-index chunk of the split adjoint so that its workspace stays near 8 GB.
 static int split_adj_pchunk(const Problem &pb) {
     const size_t n = pb.n, ctot = pb.ctot, ks3 = 3 * static_cast<size_t>(pb.ksum);

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(HERE, "libjk.so")
 
 JK_OK, JK_ERR_ARG, JK_ERR_SHAPE, JK_ERR_OOM, JK_ERR_CUDA, JK_ERR_TIMEOUT, JK_ERR_UNSUPPORTED = range(7)
 JK_FP64, JK_SPLIT_BF16 = 0, 1
-JK_OP_BUILD, JK_OP_ADJOINT, JK_OP_BATCHED, JK_OP_BUILD_HOST = 0, 1, 2, 3
+JK_OP_BUILD, JK_OP_ADJOINT, JK_OP_BATCHED, JK_OP_BUILD_HOST, JK_OP_BUILD_DENSE, JK_OP_DENSITY_GRAD = range(6)
 
 PRECISIONS = {"fp64": JK_FP64, "split": JK_SPLIT_BF16, "split_bf16": JK_SPLIT_BF16}
 
@@ -91,6 +91,10 @@ def load_library(path: str = LIB_PATH):
         L.jk_tune_lookup.argtypes = [ct.c_int, ct.c_int32, ct.POINTER(jk_factor), ct.POINTER(ct.c_int32),
                                      ct.c_int32, ct.POINTER(jk_density), ct.c_int, ct.c_int32,
                                      ct.POINTER(jk_tune_config)]
+        L.jk_build_dense.argtypes = [vp, ct.POINTER(jk_factor), ct.c_int32, vp, vp, vp, ct.c_int, vp]
+        L.jk_density_grad.argtypes = [vp, ct.POINTER(jk_factor), ct.c_int32, vp, vp, vp, ct.c_int, vp]
+        L.jk_build_dense.restype = ct.c_int
+        L.jk_density_grad.restype = ct.c_int
         L.jk_tune_export.argtypes = [ct.c_char_p, sz, ct.POINTER(sz)]
         L.jk_tune_import.argtypes = [ct.c_char_p]
         for f in (L.jk_workspace_query_handle, L.jk_autotune, L.jk_autotune_batched, L.jk_tune_lookup,
@@ -170,6 +174,31 @@ def _check_problem(L, X, Y=None, sym=None):
         symmetric = (sym is not None and sym[s]) or Y is None or Y[s] is None
         if not symmetric and _shape(Y[s]) != xs:
             raise ValueError(f"Y[{s}] must have the shape of X[{s}] {xs}, got {_shape(Y[s])}")
+    return n, naux, nd
+
+
+def _check_dense(L, mats):
+    """Shapes of a dense call: L [naux][nbf][nbf] and each given matrix stack
+    [nd][nbf][nbf] (a single [nbf][nbf] matrix counts as nd = 1), all with the
+    same nd.  Returns (nbf, naux, nd)."""
+    Ls = _shape(L)
+    if len(Ls) != 3 or Ls[1] != Ls[2] or min(Ls) < 1:
+        raise ValueError(f"L must be [naux][nbf][nbf] with naux, nbf >= 1, got {Ls}")
+    naux, n = Ls[0], Ls[1]
+    nd = None
+    for name, m in mats:
+        if m is None:
+            continue
+        ms = _shape(m)
+        if len(ms) == 2:
+            ms = (1,) + ms
+        if len(ms) != 3 or ms[1:] != (n, n) or ms[0] < 1:
+            raise ValueError(f"{name} must be [nd][{n}][{n}], got {_shape(m)}")
+        if nd is not None and ms[0] != nd:
+            raise ValueError(f"{name} holds {ms[0]} matrices, another input {nd}")
+        nd = ms[0]
+    if nd is None:
+        raise ValueError("at least one input matrix is required")
     return n, naux, nd
 
 
@@ -395,6 +424,48 @@ class Engine:
         if sync:
             self.sync_status(stream)
         return (J if want_j else None), (K if want_k else None)
+
+    def build_dense(self, L, D, precision="fp64", want_j=True, want_k=True, J=None, K=None, stream=None):
+        """J(D_s), K(D_s) ([nd][n][n] float64) for dense, general densities
+        D ([nd][n][n] or [n][n])."""
+        p = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        n, naux, nd = _check_dense(L, [("D", D)])
+        if want_j:
+            _check_output(J, "J", (nd, n, n), self.device)
+        if want_k:
+            _check_output(K, "K", (nd, n, n), self.device)
+        L = _dev_f64(L, self.device)
+        D = _dev_f64(D, self.device).reshape(nd, n, n)
+        f = jk_factor(n, naux, L.data_ptr())
+        self._ensure(self.query(JK_OP_BUILD_DENSE, (jk_factor * 1)(f), None, None, nd, p))
+        if want_j and J is None:
+            J = torch.empty((nd, n, n), dtype=torch.float64, device=self.device)
+        if want_k and K is None:
+            K = torch.empty((nd, n, n), dtype=torch.float64, device=self.device)
+        st = self.lib.jk_build_dense(self._h, ct.byref(f), nd, _ptr(D), _ptr(J if want_j else None),
+                                     _ptr(K if want_k else None), p, _stream_ptr(stream))
+        self._check(st, self._h)
+        self._record(stream)
+        return (J if want_j else None), (K if want_k else None)
+
+    def density_grad(self, L, W=None, V=None, precision="fp64", G=None, stream=None):
+        """G_s = dE/dD_s = K(W_s) + J(V_s) ([nd][n][n] float64) for
+        E = sum_s <W_s, K(D_s)> + <V_s, J(D_s)>; W or V may be None (zero)."""
+        p = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        n, naux, nd = _check_dense(L, [("W", W), ("V", V)])
+        _check_output(G, "G", (nd, n, n), self.device)
+        L = _dev_f64(L, self.device)
+        W = None if W is None else _dev_f64(W, self.device).reshape(nd, n, n)
+        V = None if V is None else _dev_f64(V, self.device).reshape(nd, n, n)
+        f = jk_factor(n, naux, L.data_ptr())
+        self._ensure(self.query(JK_OP_DENSITY_GRAD, (jk_factor * 1)(f), None, None, nd, p))
+        if G is None:
+            G = torch.empty((nd, n, n), dtype=torch.float64, device=self.device)
+        st = self.lib.jk_density_grad(self._h, ct.byref(f), nd, _ptr(W), _ptr(V), _ptr(G), p,
+                                      _stream_ptr(stream))
+        self._check(st, self._h)
+        self._record(stream)
+        return G
 
     def autotune(self, L, X, Y=None, sym=None, precision="split", reps: int = 3, stream=None):
         """Time the candidate configurations of this build and cache the

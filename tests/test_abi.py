@@ -187,3 +187,35 @@ def test_noalloc_host_checks(lib):
         assert call(**kw) == jk.JK_ERR_ARG, kw
     # panel buffer of naux * nbf * 2k doubles well above the static scratch
     assert call(n=160, naux=400, k=40) == jk.JK_ERR_OOM
+
+
+def test_dense_query_host_only(lib):
+    """JK_OP_BUILD_DENSE / JK_OP_DENSITY_GRAD: only f and nd are read (d may be
+    NULL); the answer grows with nd and the gradient's covers J formed apart."""
+    nb = ct.c_size_t()
+
+    def q(op, n, naux, nd, p, f=None):
+        fa = (jk.jk_factor * 1)(jk.jk_factor(n, naux, 0x1000)) if f is None else f
+        st = lib.jk_workspace_query(op, 1, fa, None, nd, None, p, ct.byref(nb))
+        return st, nb.value
+
+    for p in (jk.JK_FP64, jk.JK_SPLIT_BF16):
+        st1, b1 = q(jk.JK_OP_BUILD_DENSE, 100, 500, 1, p)
+        st2, b2 = q(jk.JK_OP_BUILD_DENSE, 100, 500, 4, p)
+        st3, b3 = q(jk.JK_OP_DENSITY_GRAD, 100, 500, 4, p)
+        assert st1 == st2 == st3 == jk.JK_OK and 0 < b1 < b2 < b3
+        # the gradient needs exactly one more [nd][n][n] block than the build
+        assert b3 - b2 == 4 * 100 * 100 * 8
+        for n, naux, nd in [(0, 5, 1), (5, 0, 1), (5, 5, 0), (5, 5, 65), (65536, 1, 1)]:
+            assert q(jk.JK_OP_BUILD_DENSE, n, naux, nd, p)[0] == jk.JK_ERR_SHAPE
+    assert lib.jk_workspace_query(jk.JK_OP_BUILD_DENSE, 1, None, None, 1, None, jk.JK_FP64, ct.byref(nb)) == jk.JK_ERR_ARG
+    # the factored ops still need their densities
+    fa = (jk.jk_factor * 1)(jk.jk_factor(10, 7, 0x1000))
+    assert lib.jk_workspace_query(jk.JK_OP_BUILD, 1, fa, None, 1, None, jk.JK_FP64, ct.byref(nb)) == jk.JK_ERR_ARG
+
+
+def test_dense_calls_on_null_handle(lib):
+    f = jk.jk_factor(10, 7, 0x1000)
+    D = ct.c_void_p(0x2000)
+    assert lib.jk_build_dense(None, ct.byref(f), 1, D, D, D, 0, None) == jk.JK_ERR_ARG
+    assert lib.jk_density_grad(None, ct.byref(f), 1, D, D, D, 0, None) == jk.JK_ERR_ARG

@@ -103,3 +103,38 @@ def test_batched_names_the_bad_molecule(eng):
         eng.build_batched([(*good, None), (L, X, Y, None)], "split")
     with pytest.raises(ValueError):
         eng.build_batched([], "split")
+
+
+@pytest.mark.parametrize("case", ["L2d", "Lrect", "Dshape", "Dnd0", "WVmismatch", "none"])
+def test_dense_shapes_rejected_before_device_work(eng, case):
+    rng = np.random.default_rng(1)
+    n, naux = 6, 4
+    L = rng.standard_normal((naux, n, n))
+    D = rng.standard_normal((2, n, n))
+    W, V = D, D
+    if case == "L2d":
+        L = L[0]
+    elif case == "Lrect":
+        L = L[:, :, :5]
+    elif case == "Dshape":
+        D = D[:, :, :5]
+        W = V = D
+    elif case == "Dnd0":
+        D = D[:0]
+        W = V = D
+    elif case == "WVmismatch":
+        V = D[:1]
+    elif case == "none":
+        D = W = V = None
+    if case != "WVmismatch":
+        with pytest.raises(ValueError):
+            eng.build_dense(L, D, "split")
+    with pytest.raises(ValueError):
+        eng.density_grad(L, W, V, "split")
+
+
+def test_dense_shape_helper():
+    L = np.zeros((3, 5, 5))
+    assert jk._check_dense(L, [("D", np.zeros((5, 5)))]) == (5, 3, 1)
+    assert jk._check_dense(L, [("W", np.zeros((4, 5, 5))), ("V", None)]) == (5, 3, 4)
+    assert jk._check_dense(L, [("W", None), ("V", np.zeros((2, 5, 5)))]) == (5, 3, 2)
