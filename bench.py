@@ -381,9 +381,21 @@ def adjoint_flops(n, naux, ks, sym):
     return sum(12.0 * n * n * k * naux + 4.0 * n * n * k * naux + 4.0 * n * n * naux for k in ks)
 
 
+def dense_flops(n, naux, nd):
+    """Algorithmic flops of jk_build_dense (J and K) for nd dense densities:
+    K 2n^3 naux for the panels L^P D and 2n^3 naux for the rank update, J
+    2n^2 naux for the metric dot and 2n^2 naux for the back-contraction."""
+    return nd * (4.0 * n ** 3 * naux + 4.0 * n * n * naux)
+
+
+DENSE_WORKLOAD = ("dense densities: nbf=400 naux=2400 tau=400, 8 general non-symmetric D_s "
+                  "(N(0, 1/nbf^2) entries); jk_build_dense J and K, and jk_density_grad K(W) + J(V)")
+
+
 def run_extra_case(args, rank, local):
     """Reported beside the headline workload (not the bench contract's line):
-    the adjoint case, and the uneven batch replayed as a CUDA graph."""
+    the adjoint case, the uneven batch replayed as a CUDA graph, and the dense
+    densities."""
     import numpy as np
     import torch
     from paper_2608_06536_b300 import inputs, jk
@@ -415,6 +427,26 @@ def run_extra_case(args, rank, local):
                                 "dX, dY and the symmetrized dL",
                     "ms_per_step": ms, "value": adjoint_flops(m.n, m.naux, m.ks, m.sym) / (ms * 1e-3) / 1e12,
                     "unit": "TFLOP/s (algorithmic)"})
+    elif args.case == "dense":
+        n, naux, nd = 400, 2400, 8
+        L = inputs.factor_device(n, naux, 400.0, 0, device=dev)
+        D = torch.from_numpy(inputs.dense_densities(n, nd, seed=0)).to(dev)
+        W = torch.from_numpy(inputs.dense_densities(n, nd, seed=1)).to(dev)
+        res = {}
+        for name, call in (("build_dense", lambda: eng.build_dense(L, D, args.precision)),
+                           ("density_grad", lambda: eng.density_grad(L, W, D, args.precision))):
+            for _ in range(args.warmup):
+                call()
+            torch.cuda.synchronize(dev)
+            e0.record(st)
+            for _ in range(args.steps):
+                call()
+            e1.record(st)
+            torch.cuda.synchronize(dev)
+            eng.sync_status()
+            ms = e0.elapsed_time(e1) / args.steps
+            res[name] = {"ms_per_step": ms, "value": dense_flops(n, naux, nd) / (ms * 1e-3) / 1e12}
+        out.update({"workload": DENSE_WORKLOAD, "unit": "TFLOP/s (algorithmic)", **res})
     else:
         mols = inputs.uneven_batch(with_factor=False)
         args_b = [(inputs.factor_device(mm.n, mm.naux, mm.tau, mm.seed, device=dev),
@@ -454,8 +486,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["split", "fp64"], default="split")
-    ap.add_argument("--case", choices=["multi_state", "profile", "adjoint", "batched"], default="multi_state",
-                    help="profile: nbf=400, naux=600 variant for ncu captures; adjoint, batched: extra reported cases")
+    ap.add_argument("--case", choices=["multi_state", "profile", "adjoint", "batched", "dense"],
+                    default="multi_state",
+                    help="profile: nbf=400, naux=600 variant for ncu captures; adjoint, batched, dense: "
+                         "extra reported cases")
     ap.add_argument("--no-tune", dest="tune", action="store_false",
                     help="skip the autotuner (default configuration)")
     ap.add_argument("--config", default="",
@@ -466,7 +500,7 @@ def main():
     rank, world, local = dist_init()
     if args.impl == "reference":
         run_reference(args, rank, world)
-    elif args.case in ("adjoint", "batched"):
+    elif args.case in ("adjoint", "batched", "dense"):
         run_extra_case(args, rank, local)
     else:
         run_ours(args, rank, world, local)

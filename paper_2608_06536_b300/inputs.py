@@ -16,6 +16,9 @@ shapes stand in for them, with nbf spanning the paper's 236-472 AO range):
 * Symmetric ground density D = C_o C_o^T: C_o is the Q factor of the reduced QR
   of an nbf x k N(0,1) matrix (stream ``[seed, 2, s]``); X = Y = C_o.
 * Adjoint seeds W_s, V_s: nbf x nbf N(0,1), stream ``[seed, 3, s]``.
+* Dense (general, non-symmetric) density D_s: nbf x nbf with N(0, 1/nbf^2)
+  entries, the scale of X Y^T with N(0, 1/nbf) factors of width about nbf;
+  stream ``[seed, 4, s]``.
 * Uneven batch: molecule sizes nbf ~ U{100..600}, densities per molecule
   ~ U{1..16} from stream ``[seed, 0]``; molecule m then uses seed
   ``seed * 1000 + m`` for its own factor and densities.
@@ -88,6 +91,17 @@ def ground_density(n: int, k: int, s: int, seed: int = 0):
     Q, _ = np.linalg.qr(rng.standard_normal((n, k)), mode="reduced")
     Q = np.ascontiguousarray(Q)
     return Q, Q
+
+
+def dense_density(n: int, s: int, seed: int = 0) -> np.ndarray:
+    """D_s, [n][n] float64 with N(0, 1/n^2) entries (general, non-symmetric)."""
+    rng = np.random.default_rng([seed, 4, s])
+    return np.ascontiguousarray(rng.standard_normal((n, n)) / n)
+
+
+def dense_densities(n: int, nd: int, seed: int = 0) -> np.ndarray:
+    """[nd][n][n]: dense_density for s = 0 .. nd-1."""
+    return np.stack([dense_density(n, s, seed) for s in range(nd)])
 
 
 def adjoint_seeds(n: int, s: int, seed: int = 0):

@@ -62,3 +62,21 @@ def test_host_recipe_matches_its_statement():
         rng = np.random.default_rng([1, 1, P])
         iu = np.triu_indices(6)
         np.testing.assert_allclose(M[iu], rng.standard_normal(iu[0].size) * math.exp(-P / 2.0), rtol=0, atol=0)
+
+
+def test_dense_flops_model():
+    # per dense density: K = panels L^P D (2 n^3 per P) + reduction against
+    # L^P (2 n^3 per P); J = metric dot (2 n^2 per P) + back-contraction
+    # (2 n^2 per P)
+    n, A, nd = 400, 2400, 8
+    assert bench.dense_flops(n, A, nd) == pytest.approx(nd * A * (2 * n**3 + 2 * n**3 + 2 * n * n + 2 * n * n),
+                                                        rel=1e-15)
+
+
+def test_dense_density_recipe():
+    D = inputs.dense_density(50, 2, seed=3)
+    assert D.shape == (50, 50) and not np.array_equal(D, D.T)
+    rng = np.random.default_rng([3, 4, 2])
+    np.testing.assert_array_equal(D, rng.standard_normal((50, 50)) / 50)
+    S = inputs.dense_densities(50, 3, seed=3)
+    np.testing.assert_array_equal(S[2], D)

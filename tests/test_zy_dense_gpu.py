@@ -2,9 +2,8 @@
 J(D), K(D) (jk_build_dense) and the density gradient K(W) + J(V)
 (jk_density_grad), in both precisions, on ragged sizes, several aux chunks
 (so chunk results accumulate, through int64 split-K partials and through a
-plain FP64 sum) and the single-map forms.  Dense inputs are N(0, 1/nbf^2)
-per entry, the scale of a density X Y^T with N(0, 1/nbf) factors of width
-about nbf."""
+plain FP64 sum) and the single-map forms.  Dense inputs come from the seeded
+recipe (N(0, 1/nbf^2) entries)."""
 import numpy as np
 import pytest
 import torch
@@ -27,10 +26,9 @@ def eng():
 
 
 def _case(n, naux, nd, seed=0):
-    m = inputs.custom(n, naux, max(naux / 4, 1.0), [1], [False], seed=seed)
-    rng = np.random.default_rng(100 + seed)
-    mats = [rng.standard_normal((nd, n, n)) / n for _ in range(3)]
-    return m.L, mats
+    L = inputs.factor(n, naux, max(naux / 4, 1.0), seed)
+    mats = [inputs.dense_densities(n, nd, seed=10 * seed + j) for j in range(3)]
+    return L, mats
 
 
 def _ok(prec, got, ref):
