@@ -88,7 +88,7 @@ typedef struct {
 /* Which entry point a workspace query is for. */
 typedef enum {
     JK_OP_BUILD = 0, JK_OP_ADJOINT = 1, JK_OP_BATCHED = 2, JK_OP_BUILD_HOST = 3,
-    JK_OP_BUILD_DENSE = 4, JK_OP_DENSITY_GRAD = 5
+    JK_OP_BUILD_DENSE = 4, JK_OP_DENSITY_GRAD = 5, JK_OP_PAIR = 6
 } jk_op;
 
 /* Create a handle over a caller-owned device arena of `bytes` bytes
@@ -100,7 +100,9 @@ jk_status jk_destroy(jk_handle h);
  * For JK_OP_BATCHED pass nmol factors and the concatenated densities, with
  * nd_per_mol giving the split; otherwise nmol = 1 and nd_per_mol may be NULL.
  * For JK_OP_BUILD_DENSE and JK_OP_DENSITY_GRAD only f and nd are read (d may
- * be NULL); the answer covers both maps.
+ * be NULL); the answer covers both maps.  For JK_OP_PAIR pass nmol = 2,
+ * nd_per_mol = {nl, nr}, nd = nl + nr and d = the left densities followed by
+ * the right ones (one factor); the answer covers both pairings.
  * Without a handle the answer covers both the default configuration and a
  * tuned one cached for these shapes (see jk_autotune); the _handle form
  * answers for the configuration that handle's options select. */
@@ -191,6 +193,23 @@ jk_status jk_build_dense(jk_handle h, const jk_factor *f, int32_t nd, const doub
  * (zero; both NULL writes G = 0).  G: [nd][nbf][nbf] FP64 output. */
 jk_status jk_density_grad(jk_handle h, const jk_factor *f, int32_t nd, const double *W,
                           const double *V, double *G, jk_precision p, void *stream);
+
+/* ---- bra-ket pairings -------------------------------------------------------
+ * jk_pair: the scalar contractions of Eq. 4 (Sec. II.C) with the plain CD
+ * integrals between nl left and nr right weight densities (the J and K terms
+ * Eq. 5, Sec. II.D, combines):
+ *   Jp[a][b] = sum W_L^{mu nu} (mu nu|lam sig) W_R^{lam sig} = <W_L^a, J(W_R^b)>
+ *   Kp[a][b] = sum W_L^{mu nu} (mu lam|nu sig) W_R^{lam sig} = <W_L^a, K(W_R^b)>
+ * with factored W_L^a = X_a Y_a^T (left[a]) and W_R^b = X_b Y_b^T (right[b]),
+ * one factor.  Both scalars are invariant under W_L <-> W_R (bra-ket
+ * symmetry): jk_pair(right, left) gives the transposes.
+ *   Jp, Kp : [nl][nr] FP64 device outputs; either may be NULL (not formed).
+ * The right densities' J_b, K_b are built as by jk_build (engine `p`, tuned
+ * configuration of that build) into the workspace, then each pairing is
+ * <X_a Y_a^T, M_b> = sum (X_a . M_b Y_a) in FP64.  Arena: jk_workspace_query
+ * with JK_OP_PAIR.  Validation and status as jk_build (nl, nr in [1, 64]). */
+jk_status jk_pair(jk_handle h, const jk_factor *f, int32_t nl, const jk_density *left, int32_t nr,
+                  const jk_density *right, double *Jp, double *Kp, jk_precision p, void *stream);
 
 /* ---- building without a caller arena -------------------------------------
  * The paper has no counterpart of this entry point; it serves callers that

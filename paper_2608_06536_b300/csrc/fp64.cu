@@ -601,6 +601,54 @@ jk_status fp64_dense(jk_ctx *h, const DenseProb &dp, cudaStream_t st) {
     return JK_OK;
 }
 
+// ---- bra-ket pairings -----------------------------------------------------
+// out[a*nr + b] = <A_a B_a^T, M_b> = sum_{mu, i} A_a[mu][i] (M_b B_a)[mu][i]
+// for left densities packed as ZL = [A_0 | B_0 | A_1 | ...] (n x ctotL; a
+// symmetric density has one block, B = A) and dense M_b ([nr][n][n]): one
+// batched GEMM U_b = M_b ZL, then one CTA per (a, b) sums A_a . U_b over the
+// (mu, i) of density a in a fixed order.
+struct PairTab {
+    int offA[kMaxDens], offB[kMaxDens], k[kMaxDens];
+};
+
+__global__ void __launch_bounds__(256)
+pair_dot_kernel(const double *ZL, const double *U, int n, int ctotL, PairTab tab, double *out, int nr) {
+    __shared__ double red[8];
+    const int a = blockIdx.x, b = blockIdx.y;
+    const int k = tab.k[a], oa = tab.offA[a], ob = tab.offB[a];
+    const double *Ub = U + (long long)b * n * ctotL;
+    double acc = 0.0;
+    const long long nk = (long long)n * k;
+    for (long long e = threadIdx.x; e < nk; e += 256) {
+        const long long mu = e / k;
+        const int i = (int)(e - mu * k);
+        acc = fma(ZL[mu * ctotL + oa + i], Ub[mu * ctotL + ob + i], acc);
+    }
+    const double t = block_sum_256(acc, red);
+    if (threadIdx.x == 0) out[(long long)a * nr + b] = t;
+}
+
+jk_status fp64_pair_contract(jk_ctx *h, const Problem &left, const double *ZL, const double *M, int nr, double *U,
+                             double *out, cudaStream_t st) {
+    const int n = left.n, ctotL = left.ctot;
+    const long long n2 = (long long)n * n;
+    // U_b[mu][c] = sum_nu M_b[mu][nu] ZL[nu][c]   (batch b)
+    JK_TRY(dgemm(h, nr, n, ctotL, n, gop(M, n2, n, 0, 1, n), gop(ZL, 0, 1, 0, ctotL, n), U, ctotL,
+                 (long long)n * ctotL, 1.0, 0.0, st));
+    PairTab tab;
+    for (int a = 0; a < left.nd; a++) {
+        tab.offA[a] = left.offX[a];
+        tab.offB[a] = left.offY[a];
+        tab.k[a] = left.k[a];
+    }
+    {
+        LaunchScope ls(h, KK_MISC, st);
+        pair_dot_kernel<<<dim3(left.nd, nr), 256, 0, st>>>(ZL, U, n, ctotL, tab, out, nr);
+    }
+    JK_LAUNCH_CHECK(h);
+    return JK_OK;
+}
+
 size_t fp64_adjoint_workspace(const Problem &pb, int pc, bool want_dl) {
     size_t n = pb.n, nd = pb.nd, A = pb.naux;
     size_t b = 0;

@@ -504,6 +504,22 @@ static std::vector<int> chunk_candidates(int pc0, int naux_max) {
     return out;
 }
 
+// ---- bra-ket pairings (jk_pair) ---------------------------------------------
+// The right densities' J_b and K_b (an ordinary build into workspace buffers
+// that outlive it), the packed left factors, then the FP64 contraction
+// <A_a B_a^T, M_b> per pair.
+
+static size_t pair_persist_bytes(const Problem &pl, int nr, bool wantJ, bool wantK) {
+    const size_t nn = static_cast<size_t>(nr) * pl.n * pl.n * 8;
+    return (wantJ ? align_up(nn) : 0) + (wantK ? align_up(nn) : 0) +
+           align_up(static_cast<size_t>(pl.n) * pl.ctot * 8) +
+           align_up(static_cast<size_t>(nr) * pl.n * pl.ctot * 8) + kArenaAlign;
+}
+
+static size_t pair_bytes(const Problem &pl, const Problem &pr, jk_precision p, bool wantJ, bool wantK) {
+    return pair_persist_bytes(pl, pr.nd, wantJ, wantK) + build_bytes(pr, p);
+}
+
 // ---- dense densities (jk_build_dense, jk_density_grad) ----------------------
 
 // Shape of a dense call; with check_ptrs, the factor is also checked (the
@@ -556,14 +572,15 @@ static jk_status run_dense(jk_ctx *h, const DenseProb &dp, jk_precision p, cudaS
 
 // Problems of a host-only batched call (query, lookup): nd_per_mol must split
 // the nd densities of d exactly, and d is never read past its nd entries.
+// With one_factor every group uses f[0] (the two sides of a pairing).
 static jk_status host_batched_problems(int32_t nmol, const jk_factor *f, const int32_t *nd_per_mol, int32_t nd,
-                                       const jk_density *d, std::vector<Problem> &pbs) {
+                                       const jk_density *d, std::vector<Problem> &pbs, bool one_factor = false) {
     if (nmol < 1 || !nd_per_mol) return JK_ERR_SHAPE;
     pbs.resize(nmol);
     int off = 0;
     for (int m = 0; m < nmol; m++) {
         if (nd_per_mol[m] < 1 || nd_per_mol[m] > nd - off) return JK_ERR_SHAPE;
-        JK_TRY(make_problem(nullptr, &f[m], nd_per_mol[m], d + off, false, pbs[m]));
+        JK_TRY(make_problem(nullptr, &f[one_factor ? 0 : m], nd_per_mol[m], d + off, false, pbs[m]));
         off += nd_per_mol[m];
     }
     return off == nd ? JK_OK : JK_ERR_SHAPE;
@@ -586,6 +603,22 @@ static jk_status query_impl(const jk_ctx *h, jk_op op, int32_t nmol, const jk_fa
     }
     if (!d) return JK_ERR_ARG;
     const int sms = h ? h->num_sms : current_sms();
+    if (op == JK_OP_PAIR) {
+        // nmol = 2: nd_per_mol = {left count, right count}, d = left then right
+        if (nmol != 2 || !nd_per_mol) return JK_ERR_SHAPE;
+        std::vector<Problem> pp;
+        JK_TRY(host_batched_problems(2, f, nd_per_mol, nd, d, pp, true));
+        size_t need = 0;
+        const jk_tune_config cfgs[2] = {resolve_config(h, JK_OP_BUILD, p, sms, 1, &pp[1]),
+                                        jk_tune_config{0, 0, 0, kDefaultCluster}};
+        for (int v = 0; v < (h ? 1 : 2); v++) {
+            Problem q = pp[1];
+            apply_config(q, cfgs[v]);
+            need = std::max(need, pair_bytes(pp[0], q, p, true, true));
+        }
+        *bytes = need + flags_bytes() + kArenaAlign;
+        return JK_OK;
+    }
     size_t need = 0;
     std::vector<Problem> pbs;
     if (op == JK_OP_BATCHED) {
@@ -866,6 +899,54 @@ jk_status jk_density_grad(jk_handle h, const jk_factor *f, int32_t nd, const dou
     }
     dense_config(h, dp);
     return run_dense(h, dp, p, st);
+}
+
+jk_status jk_pair(jk_handle h, const jk_factor *f, int32_t nl, const jk_density *left, int32_t nr,
+                  const jk_density *right, double *Jp, double *Kp, jk_precision p, void *stream) {
+    JK_TRY(begin_call(h));
+    if (p != JK_FP64 && p != JK_SPLIT_BF16)
+        return set_error(h, JK_ERR_ARG, "unknown precision %d", (int)p);
+    Problem pl, pr;
+    JK_TRY(make_problem(h, f, nl, left, true, pl));
+    JK_TRY(make_problem(h, f, nr, right, true, pr));
+    JK_TRY(check_out(h, Jp, "Jp"));
+    JK_TRY(check_out(h, Kp, "Kp"));
+    if (!Jp && !Kp) return JK_OK;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const jk_tune_config c = resolve_config(h, JK_OP_BUILD, p, h->num_sms, 1, &pr);
+    apply_config(pr, c);
+    h->cur_raster = c.raster;
+    h->cur_cluster = c.cluster;
+    const size_t need = flags_bytes() + pair_bytes(pl, pr, p, Jp != nullptr, Kp != nullptr);
+    if (h->arena.bytes < need)
+        return set_error(h, JK_ERR_OOM, "arena has %zu bytes, this pairing needs %zu", h->arena.bytes, need);
+    Arena &ar = h->arena;
+    const int n = pl.n;
+    const size_t nn = static_cast<size_t>(nr) * n * n;
+    double *Jall = Jp ? ar.take<double>(nn) : nullptr;
+    double *Kall = Kp ? ar.take<double>(nn) : nullptr;
+    double *ZL = ar.take<double>(static_cast<size_t>(n) * pl.ctot);
+    double *U = ar.take<double>(static_cast<size_t>(nr) * n * pl.ctot);
+    if ((Jp && !Jall) || (Kp && !Kall) || !ZL || !U)
+        return set_error(h, JK_ERR_OOM, "arena too small for the pairing's buffers");
+    const long long n2 = static_cast<long long>(n) * n;
+    pr.wantJ = Jp != nullptr;
+    pr.wantK = Kp != nullptr;
+    for (int b = 0; b < nr; b++) {
+        pr.J[b] = Jall ? Jall + b * n2 : nullptr;
+        pr.K[b] = Kall ? Kall + b * n2 : nullptr;
+    }
+    // the right densities' J_b, K_b: an ordinary build above the buffers kept
+    struct FloorGuard {
+        Arena &a;
+        ~FloorGuard() { a.floor = 0; }
+    } guard{ar};
+    ar.floor = ar.off;
+    JK_TRY(run_build(h, pr, p, st));
+    JK_TRY(split_pack_z(h, pl, ZL, st));
+    if (Jp) JK_TRY(fp64_pair_contract(h, pl, ZL, Jall, nr, U, Jp, st));
+    if (Kp) JK_TRY(fp64_pair_contract(h, pl, ZL, Kall, nr, U, Kp, st));
+    return JK_OK;
 }
 
 jk_status jk_set_option(jk_handle h, jk_option opt, int64_t value) {

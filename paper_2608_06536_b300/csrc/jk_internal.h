@@ -176,6 +176,13 @@ jk_status fp64_dense(jk_ctx *h, const DenseProb &dp, cudaStream_t st);
 size_t split_dense_workspace(const DenseProb &dp);
 jk_status split_dense(jk_ctx *h, const DenseProb &dp, cudaStream_t st);
 
+// ---- bra-ket pairings ------------------------------------------------------
+// out[a*nr + b] = <A_a B_a^T, M_b> for the left densities of `left` packed in
+// ZL (split_pack_z layout) and dense M_b [nr][n][n]; U: [nr][n][left.ctot].
+jk_status fp64_pair_contract(jk_ctx *h, const Problem &left, const double *ZL, const double *M, int nr, double *U,
+                             double *out, cudaStream_t st);
+jk_status split_pack_z(jk_ctx *h, const Problem &pb, double *Z, cudaStream_t st);
+
 // ---- batched builds (batched.cu) ------------------------------------------
 jk_status batched_build(jk_ctx *h, int nmol, const Problem *pbs, jk_precision p,
                         cudaStream_t st);

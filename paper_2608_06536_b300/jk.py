@@ -18,7 +18,8 @@ LIB_PATH = os.path.join(HERE, "libjk.so")
 
 JK_OK, JK_ERR_ARG, JK_ERR_SHAPE, JK_ERR_OOM, JK_ERR_CUDA, JK_ERR_TIMEOUT, JK_ERR_UNSUPPORTED = range(7)
 JK_FP64, JK_SPLIT_BF16 = 0, 1
-JK_OP_BUILD, JK_OP_ADJOINT, JK_OP_BATCHED, JK_OP_BUILD_HOST, JK_OP_BUILD_DENSE, JK_OP_DENSITY_GRAD = range(6)
+(JK_OP_BUILD, JK_OP_ADJOINT, JK_OP_BATCHED, JK_OP_BUILD_HOST, JK_OP_BUILD_DENSE, JK_OP_DENSITY_GRAD,
+ JK_OP_PAIR) = range(7)
 
 PRECISIONS = {"fp64": JK_FP64, "split": JK_SPLIT_BF16, "split_bf16": JK_SPLIT_BF16}
 
@@ -93,6 +94,9 @@ def load_library(path: str = LIB_PATH):
                                      ct.POINTER(jk_tune_config)]
         L.jk_build_dense.argtypes = [vp, ct.POINTER(jk_factor), ct.c_int32, vp, vp, vp, ct.c_int, vp]
         L.jk_density_grad.argtypes = [vp, ct.POINTER(jk_factor), ct.c_int32, vp, vp, vp, ct.c_int, vp]
+        L.jk_pair.argtypes = [vp, ct.POINTER(jk_factor), ct.c_int32, ct.POINTER(jk_density), ct.c_int32,
+                              ct.POINTER(jk_density), vp, vp, ct.c_int, vp]
+        L.jk_pair.restype = ct.c_int
         L.jk_build_dense.restype = ct.c_int
         L.jk_density_grad.restype = ct.c_int
         L.jk_tune_export.argtypes = [ct.c_char_p, sz, ct.POINTER(sz)]
@@ -466,6 +470,30 @@ class Engine:
         self._check(st, self._h)
         self._record(stream)
         return G
+
+    def pairs(self, L, XL, YL=None, symL=None, XR=None, YR=None, symR=None, precision="fp64",
+              want_j=True, want_k=True, stream=None):
+        """(Jp, Kp), each [nl][nr] float64: Jp[a][b] = <W_L^a, J(W_R^b)> and
+        Kp[a][b] = <W_L^a, K(W_R^b)> for left densities W_L^a = XL_a YL_a^T and
+        right densities W_R^b = XR_b YR_b^T over one factor L."""
+        p = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        if XR is None:
+            raise ValueError("right densities XR are required")
+        n, naux, nl = _check_problem(L, XL, YL, symL)
+        _, _, nr = _check_problem(L, XR, YR, symR)
+        L = _dev_f64(L, self.device)
+        left = Densities(XL, YL, symL, self.device)
+        right = Densities(XR, YR, symR, self.device)
+        f = jk_factor(n, naux, L.data_ptr())
+        both = (jk_density * (nl + nr))(*left.c, *right.c)
+        self._ensure(self.query(JK_OP_PAIR, (jk_factor * 1)(f), both, [nl, nr], nl + nr, p))
+        Jp = torch.empty((nl, nr), dtype=torch.float64, device=self.device) if want_j else None
+        Kp = torch.empty((nl, nr), dtype=torch.float64, device=self.device) if want_k else None
+        st = self.lib.jk_pair(self._h, ct.byref(f), nl, left.c, nr, right.c, _ptr(Jp), _ptr(Kp), p,
+                              _stream_ptr(stream))
+        self._check(st, self._h)
+        self._record(stream)
+        return Jp, Kp
 
     def autotune(self, L, X, Y=None, sym=None, precision="split", reps: int = 3, stream=None):
         """Time the candidate configurations of this build and cache the

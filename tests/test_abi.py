@@ -219,3 +219,31 @@ def test_dense_calls_on_null_handle(lib):
     D = ct.c_void_p(0x2000)
     assert lib.jk_build_dense(None, ct.byref(f), 1, D, D, D, 0, None) == jk.JK_ERR_ARG
     assert lib.jk_density_grad(None, ct.byref(f), 1, D, D, D, 0, None) == jk.JK_ERR_ARG
+
+
+def test_pair_query_host_only(lib):
+    """JK_OP_PAIR: nmol = 2, nd_per_mol = {nl, nr}, d = left then right, one
+    factor; the answer grows with the right count (their J, K are built)."""
+    nb = ct.c_size_t()
+    fa = (jk.jk_factor * 1)(jk.jk_factor(100, 500, 0x1000))
+    d = (jk.jk_density * 8)()
+    for s in range(8):
+        d[s].k, d[s].symmetric, d[s].X, d[s].Y = 10, s % 2, 0x2000, 0x3000
+
+    def q(nmol, split, nd, p=jk.JK_FP64):
+        ndm = (ct.c_int32 * len(split))(*split)
+        return lib.jk_workspace_query(jk.JK_OP_PAIR, nmol, fa, ndm, nd, d, p, ct.byref(nb)), nb.value
+
+    st1, b1 = q(2, (4, 2), 6)
+    st2, b2 = q(2, (4, 4), 8)
+    assert st1 == st2 == jk.JK_OK and 0 < b1 < b2
+    assert q(2, (4, 4), 8, jk.JK_SPLIT_BF16)[0] == jk.JK_OK
+    for nmol, split, nd in [(1, (4, 4), 8), (3, (4, 2, 2), 8), (2, (4, 4), 7), (2, (0, 4), 4), (2, (6, 4), 8)]:
+        assert q(nmol, split, nd)[0] == jk.JK_ERR_SHAPE, (nmol, split, nd)
+
+
+def test_pair_call_on_null_handle(lib):
+    f = jk.jk_factor(10, 7, 0x1000)
+    d = (jk.jk_density * 1)()
+    d[0].k, d[0].symmetric, d[0].X, d[0].Y = 3, 0, 0x2000, 0x3000
+    assert lib.jk_pair(None, ct.byref(f), 1, d, 1, d, None, None, 0, None) == jk.JK_ERR_ARG

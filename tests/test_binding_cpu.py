@@ -138,3 +138,15 @@ def test_dense_shape_helper():
     assert jk._check_dense(L, [("D", np.zeros((5, 5)))]) == (5, 3, 1)
     assert jk._check_dense(L, [("W", np.zeros((4, 5, 5))), ("V", None)]) == (5, 3, 4)
     assert jk._check_dense(L, [("W", None), ("V", np.zeros((2, 5, 5)))]) == (5, 3, 2)
+
+
+def test_pairs_shapes_rejected_before_device_work(eng):
+    L, X, Y = _mol()
+    with pytest.raises(ValueError):
+        eng.pairs(L, X, Y, None, None)                       # no right densities
+    with pytest.raises(ValueError):
+        eng.pairs(L, X, Y, None, [X[0][:5]], [Y[0][:5]])      # right rows != nbf
+    with pytest.raises(ValueError):
+        eng.pairs(L, [X[0][:, :0]], None, None, X, Y)         # zero-width left density
+    with pytest.raises(ValueError):
+        eng.pairs(L[0], X, Y, None, X, Y)                     # factor not [naux][nbf][nbf]
