@@ -211,3 +211,36 @@ def pairs(L: np.ndarray, A: list, B: list, X: list, Y: list, want_j=True, want_k
     _check(lib().jko_pairs(n, naux, _d(L), nl, klp, _d(Ac), _d(Bc), nr, krp, _d(Xc), _d(Yc),
                            _d(Jp), _d(Kp)), "pairs")
     return Jp, Kp
+
+
+def laplace_factors(CX, epsX, sx, CY, epsY, sy, alpha, w=None):
+    """Energy-scaled coefficients of the Laplace (LT-AO) representation
+    (Eq. 3, Sec. II.B): for quadrature point k,
+    X_k[mu][p] = CX[mu][p] exp(sx alpha_k epsX[p] / 2) (times w_k when weights
+    are given) and Y_k[mu][p] = CY[mu][p] exp(sy alpha_k epsY[p] / 2), so that
+    D_k = X_k Y_k^T carries exp(alpha_k (sx epsX_p + sy epsY_p) / 2) per column
+    pair p.  Returns the lists (X_k), (Y_k)."""
+    CX, CY = np.asarray(CX, np.float64), np.asarray(CY, np.float64)
+    epsX, epsY = np.asarray(epsX, np.float64), np.asarray(epsY, np.float64)
+    X, Y = [], []
+    for k, a in enumerate(alpha):
+        xs = CX * np.exp(sx * a * epsX / 2.0)[None, :]
+        if w is not None:
+            xs = xs * w[k]
+        X.append(np.ascontiguousarray(xs))
+        Y.append(np.ascontiguousarray(CY * np.exp(sy * a * epsY / 2.0)[None, :]))
+    return X, Y
+
+
+def laplace(L: np.ndarray, CX, epsX, sx, CY, epsY, sy, alpha, w=None):
+    """O6: the n_L builds of the Laplace representation (Eq. 3, Sec. II.B):
+    J_k = J(X_k Y_k^T), K_k = K(X_k Y_k^T) on the energy-scaled coefficients
+    (laplace_factors), each through O2.  Without weights: [nq][n][n] arrays;
+    with weights w: the single sums sum_k w_k J_k, sum_k w_k K_k ([n][n], the
+    weight folded into X_k, the sum over k in long double)."""
+    X, Y = laplace_factors(CX, epsX, sx, CY, epsY, sy, alpha, w)
+    J, K = build(L, X, Y)
+    if w is None:
+        return J, K
+    return (np.sum(J.astype(np.longdouble), axis=0).astype(np.float64),
+            np.sum(K.astype(np.longdouble), axis=0).astype(np.float64))
