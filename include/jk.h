@@ -88,7 +88,7 @@ typedef struct {
 /* Which entry point a workspace query is for. */
 typedef enum {
     JK_OP_BUILD = 0, JK_OP_ADJOINT = 1, JK_OP_BATCHED = 2, JK_OP_BUILD_HOST = 3,
-    JK_OP_BUILD_DENSE = 4, JK_OP_DENSITY_GRAD = 5, JK_OP_PAIR = 6
+    JK_OP_BUILD_DENSE = 4, JK_OP_DENSITY_GRAD = 5, JK_OP_PAIR = 6, JK_OP_LAPLACE = 7
 } jk_op;
 
 /* Create a handle over a caller-owned device arena of `bytes` bytes
@@ -102,7 +102,9 @@ jk_status jk_destroy(jk_handle h);
  * For JK_OP_BUILD_DENSE and JK_OP_DENSITY_GRAD only f and nd are read (d may
  * be NULL); the answer covers both maps.  For JK_OP_PAIR pass nmol = 2,
  * nd_per_mol = {nl, nr}, nd = nl + nr and d = the left densities followed by
- * the right ones (one factor); the answer covers both pairings.
+ * the right ones (one factor); the answer covers both pairings.  For
+ * JK_OP_LAPLACE pass nd = nq and d[0] with k = m and symmetric = (CY == NULL)
+ * (only d[0]'s shape is read); the answer covers the weighted form.
  * Without a handle the answer covers both the default configuration and a
  * tuned one cached for these shapes (see jk_autotune); the _handle form
  * answers for the configuration that handle's options select. */
@@ -210,6 +212,29 @@ jk_status jk_density_grad(jk_handle h, const jk_factor *f, int32_t nd, const dou
  * with JK_OP_PAIR.  Validation and status as jk_build (nl, nr in [1, 64]). */
 jk_status jk_pair(jk_handle h, const jk_factor *f, int32_t nl, const jk_density *left, int32_t nr,
                   const jk_density *right, double *Jp, double *Kp, jk_precision p, void *stream);
+
+/* ---- Laplace (LT-AO) builds -------------------------------------------------
+ * jk_build_laplace: the nq builds of the Laplace representation (Eq. 3,
+ * Sec. II.B), each on energy-scaled coefficients
+ *   X_k[mu][p] = CX[mu][p] exp(sx alpha_k epsX[p] / 2)
+ *   Y_k[mu][p] = CY[mu][p] exp(sy alpha_k epsY[p] / 2)        D_k = X_k Y_k^T
+ * (sx = +1 for occupied, -1 for virtual orbital energies, so that each
+ * column pair carries the factorized exp(-alpha_k D) of the denominator).
+ *   alpha, w : host arrays of nq quadrature exponents and weights (w may be
+ *              NULL); nq in [1, 64], all finite.
+ *   CX, CY   : [nbf][m] FP64 device; epsX, epsY: [m] FP64 device.  CY and
+ *              epsY NULL: Y_k = X_k (CY = CX, epsY = epsX, sy = sx), a
+ *              symmetric density per point, built at half the K cost.
+ *   J, K     : without weights [nq][nbf][nbf] (J_k = J(D_k), K_k = K(D_k));
+ *              with weights [nbf][nbf]: sum_k w_k J_k and sum_k w_k K_k,
+ *              summed in FP64 in increasing k.  Either may be NULL.
+ * The scaling is one elementwise kernel; the nq points are the densities of
+ * one ordinary build (engine `p`, the tuned configuration of that build).
+ * Arena: jk_workspace_query with JK_OP_LAPLACE.  Status as jk_build; m must
+ * lie in [1, 4 nbf]. */
+jk_status jk_build_laplace(jk_handle h, const jk_factor *f, int32_t nq, const double *alpha, const double *w,
+                           int32_t m, const double *CX, const double *epsX, int32_t sx, const double *CY,
+                           const double *epsY, int32_t sy, double *J, double *K, jk_precision p, void *stream);
 
 /* ---- building without a caller arena -------------------------------------
  * The paper has no counterpart of this entry point; it serves callers that

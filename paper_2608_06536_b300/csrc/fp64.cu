@@ -649,6 +649,58 @@ jk_status fp64_pair_contract(jk_ctx *h, const Problem &left, const double *ZL, c
     return JK_OK;
 }
 
+// ---- Laplace (LT-AO) energy scaling ------------------------------------------
+// out[k][mu][p] = C[mu][p] exp(s alpha_k eps[p] / 2) for the nq quadrature
+// points (Eq. 3): the energy-scaled coefficients each point's build runs on.
+struct LapAlpha {
+    double a[kMaxDens];
+};
+
+__global__ void laplace_scale_kernel(const double *C, const double *eps, int n, int m, double s, LapAlpha al,
+                                     int nq, double *out) {
+    const long long nm = (long long)n * m;
+    const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (e >= nm * nq) return;
+    const int k = (int)(e / nm);
+    const long long r = e - (long long)k * nm;
+    const int p = (int)(r % m);
+    out[e] = C[r] * exp(s * al.a[k] * eps[p] * 0.5);
+}
+
+jk_status fp64_laplace_scale(jk_ctx *h, const double *C, const double *eps, int n, int m, int sign,
+                             const double *alpha, int nq, double *out, cudaStream_t st) {
+    LapAlpha al;
+    for (int k = 0; k < nq; k++) al.a[k] = alpha[k];
+    const long long tot = (long long)n * m * nq;
+    {
+        LaunchScope ls(h, KK_PACK, st);
+        laplace_scale_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(C, eps, n, m, (double)sign, al, nq, out);
+    }
+    JK_LAUNCH_CHECK(h);
+    return JK_OK;
+}
+
+// out[e] = sum_k w_k part[k][e], k in increasing order (weighted Laplace sums).
+__global__ void weighted_sum_kernel(double *out, const double *part, LapAlpha w, int nq, long long cnt) {
+    const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (e >= cnt) return;
+    double acc = 0.0;
+    for (int k = 0; k < nq; k++) acc = fma(w.a[k], part[(long long)k * cnt + e], acc);
+    out[e] = acc;
+}
+
+jk_status fp64_weighted_sum(jk_ctx *h, double *out, const double *part, const double *w, int nq, long long cnt,
+                            cudaStream_t st) {
+    LapAlpha wt;
+    for (int k = 0; k < nq; k++) wt.a[k] = w[k];
+    {
+        LaunchScope ls(h, KK_MISC, st);
+        weighted_sum_kernel<<<(unsigned)((cnt + 255) / 256), 256, 0, st>>>(out, part, wt, nq, cnt);
+    }
+    JK_LAUNCH_CHECK(h);
+    return JK_OK;
+}
+
 size_t fp64_adjoint_workspace(const Problem &pb, int pc, bool want_dl) {
     size_t n = pb.n, nd = pb.nd, A = pb.naux;
     size_t b = 0;

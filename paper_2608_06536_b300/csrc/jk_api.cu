@@ -520,6 +520,31 @@ static size_t pair_bytes(const Problem &pl, const Problem &pr, jk_precision p, b
     return pair_persist_bytes(pl, pr.nd, wantJ, wantK) + build_bytes(pr, p);
 }
 
+// ---- Laplace (LT-AO) builds (jk_build_laplace) -------------------------------
+// The energy-scaled coefficients of every quadrature point go into workspace
+// buffers kept across the build (the arena floor); the nq points are the nq
+// densities of one ordinary build.  With weights, each point's J and K land
+// in the workspace and a fixed-order weighted sum writes the outputs.
+
+// Densities of the build over the scaled coefficients XY (point k: X_k at
+// XY + k*n*m, Y_k at XY + (nq + k)*n*m unless symmetric); with XY NULL only
+// the shapes are filled in (for validation and queries).
+static void laplace_densities(int n, int nq, int m, bool sym, double *XY, jk_density *d) {
+    const size_t nm = static_cast<size_t>(n) * m;
+    for (int k = 0; k < nq; k++) {
+        d[k].k = m;
+        d[k].symmetric = sym ? 1 : 0;
+        d[k].X = XY ? XY + k * nm : nullptr;
+        d[k].Y = XY && !sym ? XY + (nq + k) * nm : nullptr;
+    }
+}
+
+static size_t laplace_persist_bytes(int n, int nq, int m, bool sym, bool weighted, bool wantJ, bool wantK) {
+    const size_t nm = static_cast<size_t>(n) * m, nn = static_cast<size_t>(nq) * n * n * 8;
+    return align_up(nm * nq * (sym ? 1 : 2) * 8) + (weighted && wantJ ? align_up(nn) : 0) +
+           (weighted && wantK ? align_up(nn) : 0) + kArenaAlign;
+}
+
 // ---- dense densities (jk_build_dense, jk_density_grad) ----------------------
 
 // Shape of a dense call; with check_ptrs, the factor is also checked (the
@@ -603,6 +628,21 @@ static jk_status query_impl(const jk_ctx *h, jk_op op, int32_t nmol, const jk_fa
     }
     if (!d) return JK_ERR_ARG;
     const int sms = h ? h->num_sms : current_sms();
+    if (op == JK_OP_LAPLACE) {
+        // nd = nq points of width d[0].k, symmetric as d[0]; the weighted form
+        if (nd < 1 || nd > kMaxDens) return JK_ERR_SHAPE;
+        std::vector<jk_density> dl(nd);
+        laplace_densities(f->nbf, nd, d[0].k, d[0].symmetric != 0, nullptr, dl.data());
+        Problem pb;
+        JK_TRY(make_problem(nullptr, f, nd, dl.data(), false, pb));
+        Problem q = pb;
+        apply_config(pb, resolve_config(h, JK_OP_BUILD, p, sms, 1, &pb));
+        apply_config(q, jk_tune_config{0, 0, 0, kDefaultCluster});
+        const size_t b = h ? build_bytes(pb, p) : std::max(build_bytes(pb, p), build_bytes(q, p));
+        *bytes = b + laplace_persist_bytes(pb.n, nd, d[0].k, d[0].symmetric != 0, true, true, true) +
+                 flags_bytes() + kArenaAlign;
+        return JK_OK;
+    }
     if (op == JK_OP_PAIR) {
         // nmol = 2: nd_per_mol = {left count, right count}, d = left then right
         if (nmol != 2 || !nd_per_mol) return JK_ERR_SHAPE;
@@ -946,6 +986,80 @@ jk_status jk_pair(jk_handle h, const jk_factor *f, int32_t nl, const jk_density 
     JK_TRY(split_pack_z(h, pl, ZL, st));
     if (Jp) JK_TRY(fp64_pair_contract(h, pl, ZL, Jall, nr, U, Jp, st));
     if (Kp) JK_TRY(fp64_pair_contract(h, pl, ZL, Kall, nr, U, Kp, st));
+    return JK_OK;
+}
+
+jk_status jk_build_laplace(jk_handle h, const jk_factor *f, int32_t nq, const double *alpha, const double *w,
+                           int32_t m, const double *CX, const double *epsX, int32_t sx, const double *CY,
+                           const double *epsY, int32_t sy, double *J, double *K, jk_precision p, void *stream) {
+    JK_TRY(begin_call(h));
+    if (p != JK_FP64 && p != JK_SPLIT_BF16)
+        return set_error(h, JK_ERR_ARG, "unknown precision %d", (int)p);
+    if (!f) return set_error(h, JK_ERR_ARG, "factor is NULL");
+    if (nq < 1 || nq > kMaxDens) return set_error(h, JK_ERR_SHAPE, "nq=%d must be in [1, %d]", nq, kMaxDens);
+    if (!alpha) return set_error(h, JK_ERR_ARG, "alpha is NULL");
+    if (sx != 1 && sx != -1) return set_error(h, JK_ERR_ARG, "sx=%d must be +1 or -1", sx);
+    const bool sym = CY == nullptr;
+    if (sym != (epsY == nullptr)) return set_error(h, JK_ERR_ARG, "CY and epsY must both be given or both NULL");
+    if (!sym && sy != 1 && sy != -1) return set_error(h, JK_ERR_ARG, "sy=%d must be +1 or -1", sy);
+    if (!CX || !epsX) return set_error(h, JK_ERR_ARG, "CX or epsX is NULL");
+    for (int k = 0; k < nq; k++)
+        if (!std::isfinite(alpha[k]) || (w && !std::isfinite(w[k])))
+            return set_error(h, JK_ERR_ARG, "alpha[%d] or w[%d] is not finite", k, k);
+    JK_TRY(check_in(h, CX, "CX"));
+    JK_TRY(check_in(h, epsX, "epsX"));
+    JK_TRY(check_in(h, CY, "CY"));
+    JK_TRY(check_in(h, epsY, "epsY"));
+    JK_TRY(check_out(h, J, "J"));
+    JK_TRY(check_out(h, K, "K"));
+    // shapes: the nq points are densities of width m over f (as jk_build checks them)
+    std::vector<jk_density> d(nq);
+    laplace_densities(f->nbf, nq, m, sym, nullptr, d.data());
+    Problem pb;
+    JK_TRY(make_problem(h, f, nq, d.data(), false, pb));
+    if (!f->L) return set_error(h, JK_ERR_ARG, "factor L is NULL");
+    if (!aligned16(f->L)) return set_error(h, JK_ERR_ARG, "factor L is not 16-byte aligned");
+    if (!device_readable(f->L)) return set_error(h, JK_ERR_ARG, "factor L is not device memory");
+    if (!J && !K) return JK_OK;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const jk_tune_config c = resolve_config(h, JK_OP_BUILD, p, h->num_sms, 1, &pb);
+    apply_config(pb, c);
+    h->cur_raster = c.raster;
+    h->cur_cluster = c.cluster;
+    const int n = pb.n;
+    const bool weighted = w != nullptr;
+    const size_t need = flags_bytes() + laplace_persist_bytes(n, nq, m, sym, weighted, J != nullptr, K != nullptr) +
+                        build_bytes(pb, p);
+    if (h->arena.bytes < need)
+        return set_error(h, JK_ERR_OOM, "arena has %zu bytes, this Laplace build needs %zu", h->arena.bytes, need);
+    Arena &ar = h->arena;
+    const size_t nm = static_cast<size_t>(n) * m;
+    const long long n2 = static_cast<long long>(n) * n;
+    double *XY = ar.take<double>(nm * nq * (sym ? 1 : 2));
+    double *Jall = weighted && J ? ar.take<double>(static_cast<size_t>(nq) * n2) : nullptr;
+    double *Kall = weighted && K ? ar.take<double>(static_cast<size_t>(nq) * n2) : nullptr;
+    if (!XY || (weighted && J && !Jall) || (weighted && K && !Kall))
+        return set_error(h, JK_ERR_OOM, "arena too small for the Laplace buffers");
+    // the scaled coefficients, then the build over them
+    JK_TRY(fp64_laplace_scale(h, CX, epsX, n, m, sx, alpha, nq, XY, st));
+    if (!sym) JK_TRY(fp64_laplace_scale(h, CY, epsY, n, m, sy, alpha, nq, XY + nq * nm, st));
+    laplace_densities(n, nq, m, sym, XY, d.data());
+    JK_TRY(make_problem(h, f, nq, d.data(), false, pb));
+    apply_config(pb, c);
+    pb.wantJ = J != nullptr;
+    pb.wantK = K != nullptr;
+    for (int k = 0; k < nq; k++) {
+        pb.J[k] = J ? (weighted ? Jall : J) + k * n2 : nullptr;
+        pb.K[k] = K ? (weighted ? Kall : K) + k * n2 : nullptr;
+    }
+    struct FloorGuard {
+        Arena &a;
+        ~FloorGuard() { a.floor = 0; }
+    } guard{ar};
+    ar.floor = ar.off;
+    JK_TRY(run_build(h, pb, p, st));
+    if (weighted && J) JK_TRY(fp64_weighted_sum(h, J, Jall, w, nq, n2, st));
+    if (weighted && K) JK_TRY(fp64_weighted_sum(h, K, Kall, w, nq, n2, st));
     return JK_OK;
 }
 

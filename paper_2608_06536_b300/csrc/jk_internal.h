@@ -183,6 +183,14 @@ jk_status fp64_pair_contract(jk_ctx *h, const Problem &left, const double *ZL, c
                              double *out, cudaStream_t st);
 jk_status split_pack_z(jk_ctx *h, const Problem &pb, double *Z, cudaStream_t st);
 
+// ---- Laplace (LT-AO) builds -------------------------------------------------
+// out[k][mu][p] = C[mu][p] exp(sign alpha[k] eps[p] / 2), k < nq <= kMaxDens
+// (alpha on the host); out[e] = sum_k w[k] part[k][e] (w on the host).
+jk_status fp64_laplace_scale(jk_ctx *h, const double *C, const double *eps, int n, int m, int sign,
+                             const double *alpha, int nq, double *out, cudaStream_t st);
+jk_status fp64_weighted_sum(jk_ctx *h, double *out, const double *part, const double *w, int nq, long long cnt,
+                            cudaStream_t st);
+
 // ---- batched builds (batched.cu) ------------------------------------------
 jk_status batched_build(jk_ctx *h, int nmol, const Problem *pbs, jk_precision p,
                         cudaStream_t st);

@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(HERE, "libjk.so")
 JK_OK, JK_ERR_ARG, JK_ERR_SHAPE, JK_ERR_OOM, JK_ERR_CUDA, JK_ERR_TIMEOUT, JK_ERR_UNSUPPORTED = range(7)
 JK_FP64, JK_SPLIT_BF16 = 0, 1
 (JK_OP_BUILD, JK_OP_ADJOINT, JK_OP_BATCHED, JK_OP_BUILD_HOST, JK_OP_BUILD_DENSE, JK_OP_DENSITY_GRAD,
- JK_OP_PAIR) = range(7)
+ JK_OP_PAIR, JK_OP_LAPLACE) = range(8)
 
 PRECISIONS = {"fp64": JK_FP64, "split": JK_SPLIT_BF16, "split_bf16": JK_SPLIT_BF16}
 
@@ -97,6 +97,10 @@ def load_library(path: str = LIB_PATH):
         L.jk_pair.argtypes = [vp, ct.POINTER(jk_factor), ct.c_int32, ct.POINTER(jk_density), ct.c_int32,
                               ct.POINTER(jk_density), vp, vp, ct.c_int, vp]
         L.jk_pair.restype = ct.c_int
+        dpp = ct.POINTER(ct.c_double)
+        L.jk_build_laplace.argtypes = [vp, ct.POINTER(jk_factor), ct.c_int32, dpp, dpp, ct.c_int32, vp, vp,
+                                       ct.c_int32, vp, vp, ct.c_int32, vp, vp, ct.c_int, vp]
+        L.jk_build_laplace.restype = ct.c_int
         L.jk_build_dense.restype = ct.c_int
         L.jk_density_grad.restype = ct.c_int
         L.jk_tune_export.argtypes = [ct.c_char_p, sz, ct.POINTER(sz)]
@@ -494,6 +498,50 @@ class Engine:
         self._check(st, self._h)
         self._record(stream)
         return Jp, Kp
+
+    def build_laplace(self, L, CX, epsX, sx, alpha, w=None, CY=None, epsY=None, sy=None, precision="fp64",
+                      want_j=True, want_k=True, stream=None):
+        """The nq Laplace builds on energy-scaled coefficients
+        X_k = CX diag(exp(sx alpha_k epsX / 2)), Y_k likewise from CY, epsY, sy
+        (CY None: Y_k = X_k).  Returns (J, K): [nq][n][n] per point, or the
+        weighted sums [n][n] when w is given."""
+        p = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        Ls = _shape(L)
+        if len(Ls) != 3 or Ls[1] != Ls[2] or min(Ls) < 1:
+            raise ValueError(f"L must be [naux][nbf][nbf] with naux, nbf >= 1, got {Ls}")
+        naux, n = Ls[0], Ls[1]
+        sym = CY is None
+        if sym != (epsY is None):
+            raise ValueError("CY and epsY must both be given or both omitted")
+        cs = _shape(CX)
+        if len(cs) != 2 or cs[0] != n or cs[1] < 1:
+            raise ValueError(f"CX must be [{n}][m], got {cs}")
+        m = cs[1]
+        if _shape(epsX) != (m,) or (not sym and (_shape(CY) != cs or _shape(epsY) != (m,))):
+            raise ValueError(f"epsX (and CY, epsY) must match CX's m = {m}")
+        alpha = [float(a) for a in alpha]
+        nq = len(alpha)
+        if w is not None and len(w) != nq:
+            raise ValueError(f"w has {len(w)} entries for {nq} quadrature points")
+        L = _dev_f64(L, self.device)
+        CX, epsX = _dev_f64(CX, self.device), _dev_f64(epsX, self.device)
+        if not sym:
+            CY, epsY = _dev_f64(CY, self.device), _dev_f64(epsY, self.device)
+        f = jk_factor(n, naux, L.data_ptr())
+        d = (jk_density * 1)()
+        d[0].k, d[0].symmetric = m, 1 if sym else 0
+        self._ensure(self.query(JK_OP_LAPLACE, (jk_factor * 1)(f), d, None, nq, p))
+        shape = (n, n) if w is not None else (nq, n, n)
+        J = torch.empty(shape, dtype=torch.float64, device=self.device) if want_j else None
+        K = torch.empty(shape, dtype=torch.float64, device=self.device) if want_k else None
+        a_arr = (ct.c_double * nq)(*alpha)
+        w_arr = (ct.c_double * nq)(*[float(x) for x in w]) if w is not None else None
+        st = self.lib.jk_build_laplace(self._h, ct.byref(f), nq, a_arr, w_arr, m, _ptr(CX), _ptr(epsX), int(sx),
+                                       _ptr(CY) if not sym else None, _ptr(epsY) if not sym else None,
+                                       int(sy) if sy is not None else 0, _ptr(J), _ptr(K), p, _stream_ptr(stream))
+        self._check(st, self._h)
+        self._record(stream)
+        return J, K
 
     def autotune(self, L, X, Y=None, sym=None, precision="split", reps: int = 3, stream=None):
         """Time the candidate configurations of this build and cache the

@@ -247,3 +247,24 @@ def test_pair_call_on_null_handle(lib):
     d = (jk.jk_density * 1)()
     d[0].k, d[0].symmetric, d[0].X, d[0].Y = 3, 0, 0x2000, 0x3000
     assert lib.jk_pair(None, ct.byref(f), 1, d, 1, d, None, None, 0, None) == jk.JK_ERR_ARG
+
+
+def test_laplace_query_and_checks(lib):
+    """JK_OP_LAPLACE: nd = nq points, d[0] gives m and symmetry; the
+    non-symmetric form needs more (two scaled coefficient sets)."""
+    nb = ct.c_size_t()
+    fa = (jk.jk_factor * 1)(jk.jk_factor(100, 500, 0x1000))
+    d = (jk.jk_density * 1)()
+    d[0].k, d[0].symmetric = 10, 1
+    assert lib.jk_workspace_query(jk.JK_OP_LAPLACE, 1, fa, None, 6, d, jk.JK_FP64, ct.byref(nb)) == jk.JK_OK
+    b_sym = nb.value
+    d[0].symmetric = 0
+    assert lib.jk_workspace_query(jk.JK_OP_LAPLACE, 1, fa, None, 6, d, jk.JK_FP64, ct.byref(nb)) == jk.JK_OK
+    assert nb.value > b_sym
+    for nq, k in [(0, 10), (65, 10), (6, 0), (6, 401)]:
+        d[0].k = k
+        assert lib.jk_workspace_query(jk.JK_OP_LAPLACE, 1, fa, None, nq, d, jk.JK_FP64, ct.byref(nb)) == jk.JK_ERR_SHAPE
+    f = jk.jk_factor(10, 7, 0x1000)
+    a = (ct.c_double * 2)(0.5, 1.0)
+    assert lib.jk_build_laplace(None, ct.byref(f), 2, a, None, 3, 0x2000, 0x3000, 1, None, None, 0,
+                                0x4000, 0x5000, 0, None) == jk.JK_ERR_ARG

@@ -150,3 +150,19 @@ def test_pairs_shapes_rejected_before_device_work(eng):
         eng.pairs(L, [X[0][:, :0]], None, None, X, Y)         # zero-width left density
     with pytest.raises(ValueError):
         eng.pairs(L[0], X, Y, None, X, Y)                     # factor not [naux][nbf][nbf]
+
+
+def test_laplace_shapes_rejected_before_device_work(eng):
+    rng = np.random.default_rng(2)
+    n, naux, m = 6, 4, 3
+    L = rng.standard_normal((naux, n, n))
+    C = rng.standard_normal((n, m))
+    e = np.array([-1.0, -0.5, -0.2])
+    bad = [dict(CX=C[:5]), dict(epsX=e[:2]), dict(CY=C), dict(CY=C[:, :2], epsY=e[:2]), dict(w=[1.0])]
+    for kw in bad:
+        args = dict(CX=C, epsX=e, sx=1, alpha=[0.5, 1.0])
+        args.update(kw)
+        with pytest.raises(ValueError):
+            eng.build_laplace(L, **args)
+    with pytest.raises(ValueError):
+        eng.build_laplace(L[0], C, e, 1, [0.5])
