@@ -388,6 +388,20 @@ def dense_flops(n, naux, nd):
     return nd * (4.0 * n ** 3 * naux + 4.0 * n * n * naux)
 
 
+def pair_flops(n, naux, kl, syml, kr, symr):
+    """Algorithmic flops of jk_pair with both pairings: the right densities'
+    build plus, per map and right density, U_b = M_b Z_L (2 n^2 ctot_L) and the
+    pair dots (2 n k_a per pair)."""
+    ctot_l = sum(k if s else 2 * k for k, s in zip(kl, syml))
+    contract = 2 * len(kr) * (2.0 * n * n * ctot_l + sum(2.0 * n * k for k in kl))
+    return build_flops(n, naux, kr, symr) + contract
+
+
+PAIR_WORKLOAD = ("bra-ket pairings: nbf=400 naux=2400 tau=400, 8 left x 8 right non-symmetric densities k=40; "
+                 "jk_pair Jp and Kp")
+LAPLACE_WORKLOAD = ("Laplace (LT-AO) builds: nbf=400 naux=2400 tau=400, 8 Gauss-Laguerre points, m=40 occupied "
+                    "against virtual coefficient columns; jk_build_laplace weighted J and K")
+
 DENSE_WORKLOAD = ("dense densities: nbf=400 naux=2400 tau=400, 8 general non-symmetric D_s "
                   "(N(0, 1/nbf^2) entries); jk_build_dense J and K, and jk_density_grad K(W) + J(V)")
 
@@ -447,6 +461,36 @@ def run_extra_case(args, rank, local):
             ms = e0.elapsed_time(e1) / args.steps
             res[name] = {"ms_per_step": ms, "value": dense_flops(n, naux, nd) / (ms * 1e-3) / 1e12}
         out.update({"workload": DENSE_WORKLOAD, "unit": "TFLOP/s (algorithmic)", **res})
+    elif args.case in ("pairs", "laplace"):
+        n, naux, k, nq = 400, 2400, 40, 8
+        L = inputs.factor_device(n, naux, 400.0, 0, device=dev)
+        left = inputs.custom_densities(n, [k] * 8, seed=1)
+        right = inputs.custom_densities(n, [k] * 8, seed=2)
+        XL, YL = ([torch.from_numpy(x).to(dev) for x in side] for side in left)
+        XR, YR = ([torch.from_numpy(x).to(dev) for x in side] for side in right)
+        if args.case == "pairs":
+            call = lambda: eng.pairs(L, XL, YL, None, XR, YR, None, args.precision)
+            flops, workload = pair_flops(n, naux, [k] * 8, [False] * 8, [k] * 8, [False] * 8), PAIR_WORKLOAD
+        else:
+            t, u = np.polynomial.laguerre.laggauss(nq)
+            alpha, w = t, u * np.exp(t)
+            rng = np.random.default_rng([0, 5])
+            ei = torch.from_numpy(-np.sort(rng.uniform(0.3, 1.5, k))).to(dev)
+            ea = torch.from_numpy(np.sort(rng.uniform(0.2, 2.0, k))).to(dev)
+            call = lambda: eng.build_laplace(L, XL[0], ei, +1, alpha, w, YL[0], ea, -1, args.precision)
+            flops, workload = build_flops(n, naux, [k] * nq, [False] * nq), LAPLACE_WORKLOAD
+        for _ in range(args.warmup):
+            call()
+        torch.cuda.synchronize(dev)
+        e0.record(st)
+        for _ in range(args.steps):
+            call()
+        e1.record(st)
+        torch.cuda.synchronize(dev)
+        eng.sync_status()
+        ms = e0.elapsed_time(e1) / args.steps
+        out.update({"workload": workload, "ms_per_step": ms, "value": flops / (ms * 1e-3) / 1e12,
+                    "unit": "TFLOP/s (algorithmic)"})
     else:
         mols = inputs.uneven_batch(with_factor=False)
         args_b = [(inputs.factor_device(mm.n, mm.naux, mm.tau, mm.seed, device=dev),
@@ -486,10 +530,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["split", "fp64"], default="split")
-    ap.add_argument("--case", choices=["multi_state", "profile", "adjoint", "batched", "dense"],
+    ap.add_argument("--case", choices=["multi_state", "profile", "adjoint", "batched", "dense", "pairs", "laplace"],
                     default="multi_state",
-                    help="profile: nbf=400, naux=600 variant for ncu captures; adjoint, batched, dense: "
-                         "extra reported cases")
+                    help="profile: nbf=400, naux=600 variant for ncu captures; adjoint, batched, dense, pairs, "
+                         "laplace: extra reported cases")
     ap.add_argument("--no-tune", dest="tune", action="store_false",
                     help="skip the autotuner (default configuration)")
     ap.add_argument("--config", default="",
@@ -500,7 +544,7 @@ def main():
     rank, world, local = dist_init()
     if args.impl == "reference":
         run_reference(args, rank, world)
-    elif args.case in ("adjoint", "batched", "dense"):
+    elif args.case in ("adjoint", "batched", "dense", "pairs", "laplace"):
         run_extra_case(args, rank, local)
     else:
         run_ours(args, rank, world, local)

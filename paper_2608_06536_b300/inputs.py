@@ -199,6 +199,13 @@ def uneven_batch(nmol: int = 64, seed: int = 0, with_factor: bool = True,
     return mols
 
 
+def custom_densities(n: int, ks, seed: int = 0):
+    """(X list, Y list) of non-symmetric transition densities of widths ks,
+    without a factor (the recipe of transition_density)."""
+    XY = [transition_density(n, k, s, seed) for s, k in enumerate(ks)]
+    return [x for x, _ in XY], [y for _, y in XY]
+
+
 def custom(n: int, naux: int, tau: float, ks, sym=None, seed: int = 0) -> Molecule:
     """Arbitrary shapes for tests (ragged sizes, tiny cases)."""
     sym = sym if sym is not None else [False] * len(ks)

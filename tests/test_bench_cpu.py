@@ -80,3 +80,22 @@ def test_dense_density_recipe():
     np.testing.assert_array_equal(D, rng.standard_normal((50, 50)) / 50)
     S = inputs.dense_densities(50, 3, seed=3)
     np.testing.assert_array_equal(S[2], D)
+
+
+def test_pair_flops_model():
+    # right build + per map and right density: U_b = M_b Z_L and the pair dots
+    n, A = 400, 2400
+    kl, kr = [40] * 8, [40] * 8
+    ctot_l = 8 * 80
+    expect = bench.build_flops(n, A, kr, [False] * 8) + 2 * 8 * (2 * n * n * ctot_l + 8 * 2 * n * 40)
+    assert bench.pair_flops(n, A, kl, [False] * 8, kr, [False] * 8) == pytest.approx(expect, rel=1e-15)
+    # a symmetric left density contributes one column block
+    assert bench.pair_flops(n, A, [40], [True], [40], [False]) < bench.pair_flops(n, A, [40], [False], [40], [False])
+
+
+def test_custom_densities_recipe():
+    X, Y = inputs.custom_densities(30, [3, 4], seed=2)
+    for s, k in enumerate([3, 4]):
+        x, y = inputs.transition_density(30, k, s, seed=2)
+        np.testing.assert_array_equal(X[s], x)
+        np.testing.assert_array_equal(Y[s], y)
