@@ -490,7 +490,8 @@ class Engine:
         right = Densities(XR, YR, symR, self.device)
         f = jk_factor(n, naux, L.data_ptr())
         both = (jk_density * (nl + nr))(*left.c, *right.c)
-        self._ensure(self.query(JK_OP_PAIR, (jk_factor * 1)(f), both, [nl, nr], nl + nr, p))
+        # the pair query takes two groups (left, right) over one factor
+        self._ensure(self.query(JK_OP_PAIR, (jk_factor * 2)(f, f), both, [nl, nr], nl + nr, p))
         Jp = torch.empty((nl, nr), dtype=torch.float64, device=self.device) if want_j else None
         Kp = torch.empty((nl, nr), dtype=torch.float64, device=self.device) if want_k else None
         st = self.lib.jk_pair(self._h, ct.byref(f), nl, left.c, nr, right.c, _ptr(Jp), _ptr(Kp), p,

@@ -166,3 +166,82 @@ def test_laplace_shapes_rejected_before_device_work(eng):
             eng.build_laplace(L, **args)
     with pytest.raises(ValueError):
         eng.build_laplace(L[0], C, e, 1, [0.5])
+
+
+class _RecordingLib:
+    """The real library for host-only calls (the workspace query); compute
+    entry points are recorded instead of called (no device here)."""
+    COMPUTE = ("jk_build", "jk_adjoint", "jk_build_batched", "jk_build_dense", "jk_density_grad", "jk_pair",
+               "jk_build_laplace", "jk_set_option")
+
+    def __init__(self, real):
+        self.real, self.calls, self.queries = real, [], []
+
+    def __getattr__(self, name):
+        if name == "jk_workspace_query_handle":
+            def query(h, op, nmol, f, ndm, nd, d, p, nb):
+                st = self.real.jk_workspace_query(op, nmol, f, ndm, nd, d, p, nb)
+                self.queries.append((op, nmol, nd, st, nb._obj.value))
+                return st
+            return query
+        if name in self.COMPUTE:
+            def record(*args):
+                self.calls.append((name, args))
+                return 0
+            return record
+        return getattr(self.real, name)
+
+
+@pytest.fixture()
+def rec():
+    """An Engine on host tensors whose compute calls are recorded: the
+    marshalling and the workspace query run for real."""
+    import ctypes as ct
+    import types
+    pkg_build.build()
+    e = object.__new__(jk.Engine)
+    e.lib = _RecordingLib(jk.load_library())
+    e.device = torch.device("cpu")
+    e._ws, e._h, e._opts = None, ct.c_void_p(1), {}
+    e.sized = []
+    e._ensure = lambda nbytes: e.sized.append(nbytes)
+    e.stream = types.SimpleNamespace(cuda_stream=0)
+    yield e
+    e._h = ct.c_void_p()      # the stand-in handle must never reach jk_destroy
+
+
+def test_binding_queries_succeed_for_every_entry_point(rec):
+    """Each binding method builds query arguments the library accepts and
+    passes the compute entry point what its header declares."""
+    rng = np.random.default_rng(3)
+    n, naux = 8, 5
+    L = rng.standard_normal((naux, n, n))
+    X = [rng.standard_normal((n, k)) for k in (2, 3)]
+    Y = [rng.standard_normal((n, k)) for k in (2, 3)]
+    D = rng.standard_normal((2, n, n))
+    st = rec.stream
+    rec.build(L, X, Y, [False, True], "split", stream=st)
+    rec.adjoint(L, X, Y, [False, False], D, D, precision="split", stream=st)
+    rec.build_batched([(L, X, Y, None), (L[:, :6, :6], [x[:6] for x in X], None, [True, True])], "split",
+                      stream=st)
+    rec.build_dense(L, D, "split", stream=st)
+    rec.density_grad(L, D, None, "split", stream=st)
+    Jp, Kp = rec.pairs(L, X, Y, None, X[:1], Y[:1], None, "split", stream=st)
+    assert Jp.shape == (2, 1) and Kp.shape == (2, 1)
+    J, K = rec.build_laplace(L, X[0], np.array([-1.0, -0.5]), +1, [0.3, 1.2], [0.5, 2.0], Y[0],
+                             np.array([0.4, 0.8]), -1, "split", stream=st)
+    assert J.shape == (n, n) and K.shape == (n, n)
+    J, K = rec.build_laplace(L, X[0], np.array([-1.0, -0.5]), +1, [0.3, 1.2, 2.0], stream=st)
+    assert J.shape == (3, n, n)
+    ops = [q[0] for q in rec.lib.queries]
+    assert ops == [jk.JK_OP_BUILD, jk.JK_OP_ADJOINT, jk.JK_OP_BATCHED, jk.JK_OP_BUILD_DENSE,
+                   jk.JK_OP_DENSITY_GRAD, jk.JK_OP_PAIR, jk.JK_OP_LAPLACE, jk.JK_OP_LAPLACE]
+    assert all(q[3] == jk.JK_OK and q[4] > 0 for q in rec.lib.queries), rec.lib.queries
+    assert rec.sized == [q[4] for q in rec.lib.queries]
+    names = [c[0] for c in rec.lib.calls]
+    assert names == ["jk_build", "jk_adjoint", "jk_build_batched", "jk_build_dense", "jk_density_grad", "jk_pair",
+                     "jk_build_laplace", "jk_build_laplace"]
+    pair_args = rec.lib.calls[5][1]
+    assert pair_args[2] == 2 and pair_args[4] == 1          # nl, nr
+    lap_args = rec.lib.calls[6][1]
+    assert lap_args[2] == 2 and lap_args[5] == 2 and lap_args[4] is not None   # nq, m, weights
