@@ -1,0 +1,118 @@
+"""The library's host code end to end without a GPU (CPU test).
+
+libjk.so is driven through every entry point in a child process whose CUDA
+runtime is the recording stand-in of tests/hostsim/cudart_shim.c: host
+memory stands in for device memory, kernels are recorded instead of run.
+For each case (both engines, chunked, grouped and clustered schedules,
+batched, host-resident, adjoint, dense densities, the density gradient,
+pairings, Laplace builds, the arena-free build, the autotuner) this checks:
+
+- the call succeeds in an arena of exactly the size the workspace query
+  reports (the query and the buffers the code takes agree);
+- every launch shape is within the device's limits (grid, block, dynamic
+  shared memory, cluster shape);
+- every tensor map obeys the TMA encoding rules (16-byte aligned base and
+  strides, box at most 256 per dimension, inner box a multiple of 16 bytes
+  and within the swizzle span) and addresses only memory the call owns
+  (the arena or one of its inputs or outputs).
+Values are not checked here: the kernels do not run.
+"""
+import json
+import os
+import subprocess
+import sys
+
+import pytest
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SIM = os.path.join(HERE, "hostsim")
+
+ESIZE = {5: 8, 9: 2}            # CU_TENSOR_MAP_DATA_TYPE_INT64, _BFLOAT16
+SWIZZLE_SPAN = {0: None, 1: 32, 2: 64, 3: 128}
+
+
+@pytest.fixture(scope="module")
+def records(tmp_path_factory):
+    from paper_2608_06536_b300 import build as pkg_build
+    pkg_build.build()
+    d = tmp_path_factory.mktemp("cudart")
+    (d / "ver.map").write_text("libcudart.so.13 { global: *; };\n")
+    subprocess.run(["gcc", "-O1", "-fPIC", "-shared", "-std=c11", "-I/usr/local/cuda/include",
+                    f"-Wl,--version-script={d / 'ver.map'}", "-Wl,-soname,libcudart.so.13",
+                    "-o", str(d / "libcudart.so.13"), os.path.join(SIM, "cudart_shim.c")], check=True)
+    env = dict(os.environ, LD_LIBRARY_PATH=str(d))
+    r = subprocess.run([sys.executable, os.path.join(SIM, "drive.py")], env=env, capture_output=True, text=True,
+                       timeout=600)
+    assert r.returncode == 0, r.stderr[-3000:]
+    out = {}
+    for line in r.stdout.splitlines():
+        rec = json.loads(line)
+        out[rec["case"]] = rec
+    return out
+
+
+def _names():
+    # the case list, read from the driver's source without importing it (the
+    # driver loads the library at import)
+    src = open(os.path.join(SIM, "drive.py")).read()
+    body = src.split("CASES = {", 1)[1].split("\n}\n", 1)[0]
+    return [line.split('"')[1] for line in body.splitlines() if line.strip().startswith('"')]
+
+
+NAMES = _names()
+
+
+def test_every_case_ran(records):
+    assert sorted(records) == sorted(NAMES)
+
+
+@pytest.mark.parametrize("name", NAMES)
+def test_case(records, name):
+    rec = records[name]
+    assert rec["status"] == 0, (rec["status"], rec["error"])
+    assert rec["launches"], "no kernel was launched"
+    for kname, grid, block, cluster, smem in rec["launches"]:
+        assert 1 <= grid[0] <= 2**31 - 1 and 1 <= grid[1] <= 65535 and 1 <= grid[2] <= 65535, (kname, grid)
+        assert 1 <= block[0] * block[1] * block[2] <= 1024, (kname, block)
+        assert smem <= 227 * 1024, (kname, smem)
+        assert cluster[0] * cluster[1] * cluster[2] <= 8 and grid[0] % cluster[0] == 0, (kname, grid, cluster)
+    owned = rec["owned"]
+    for t in rec["tmaps"]:
+        es = ESIZE[t["dtype"]]
+        assert t["base"] % 16 == 0, t
+        assert all(s % 16 == 0 and s < 2**40 for s in t["strides"][1:]), t
+        assert all(1 <= b <= 256 for b in t["box"]), t
+        inner = t["box"][0] * es
+        assert inner % 16 == 0, t
+        span = SWIZZLE_SPAN[t["swizzle"]]
+        assert span is None or inner <= span, t
+        lo = t["base"]
+        hi = lo + t["dims"][0] * es + sum((dim - 1) * s for dim, s in zip(t["dims"][1:], t["strides"][1:]))
+        inside = [o[2] for o in owned if o[0] <= lo and hi <= o[0] + o[1]]
+        assert inside, f"tensor map [{lo:#x}, {hi:#x}) is outside every buffer of the call: {t}"
+
+
+def _kernels(rec):
+    return [k[0] for k in rec["launches"]]
+
+
+@pytest.mark.parametrize("name,must", [
+    ("dense_split", ["ozgemm_kernel", "frob_stream_kernel", "jstream_sym_kernel"]),
+    ("dense_fp64", ["dgemm_nt_kernel", "frob_stream_kernel", "jstream_sym_kernel"]),
+    ("grad_split_WV", ["ozgemm_kernel", "frob_stream_kernel", "axpy_kernel"]),
+    ("pairs_split", ["ozgemm_kernel", "pair_dot_kernel"]),
+    ("laplace_split", ["laplace_scale_kernel", "ozgemm_kernel"]),
+    ("laplace_fp64_weighted", ["laplace_scale_kernel", "weighted_sum_kernel"]),
+    ("build_split_grouped_clustered", ["ozgemm_kernelILb1E"]),
+])
+def test_expected_kernels(records, name, must):
+    names = _kernels(records[name])
+    for m in must:
+        assert any(m in k for k in names), (m, sorted(set(names)))
+
+
+def test_dense_split_needs_no_identity_panel(records):
+    """K(D) reduces the panels against L itself: per aux chunk one panel GEMM
+    for all densities and one reduction GEMM per density."""
+    names = _kernels(records["dense_split"])
+    assert sum("ozgemm_kernel" in k for k in names) == 1 + 2
