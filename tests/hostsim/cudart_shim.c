@@ -52,13 +52,25 @@ static int g_nvars;
 static struct { dim3 grid, block; size_t smem; void *stream; } g_cfg;
 static int g_fail_launch;
 
+/* Called at every launch while the argument array is alive, so the test can
+ * decode each kernel's arguments from its signature. */
+typedef void (*launch_hook_t)(const char *name, const unsigned *grid, const unsigned *block, void **args);
+static launch_hook_t g_hook;
+void shim_set_hook(launch_hook_t h) { g_hook = h; }
+
 static int func_index(const void *host) {
     for (int i = 0; i < g_nfuncs; i++)
         if (g_funcs[i].host == host) return i;
     return -1;
 }
 
-static void record_launch(const void *host, dim3 grid, dim3 block, size_t smem, const unsigned *cluster) {
+static void record_launch(const void *host, dim3 grid, dim3 block, size_t smem, const unsigned *cluster,
+                          void **args) {
+    if (g_hook) {
+        const int f = func_index(host);
+        const unsigned g[3] = {grid.x, grid.y, grid.z}, b[3] = {block.x, block.y, block.z};
+        g_hook(f >= 0 ? g_funcs[f].name : "?", g, b, args);
+    }
     if (!g_launch) g_launch = (Launch *)calloc(MAX_LAUNCH, sizeof(Launch));
     if (g_nlaunch >= MAX_LAUNCH) { g_fail_launch = 1; return; }
     Launch *l = &g_launch[g_nlaunch++];
@@ -110,13 +122,12 @@ cudaError_t __cudaGetKernel(cudaKernel_t *k, const void *fun) { *k = (cudaKernel
 
 cudaError_t __cudaLaunchKernel(cudaKernel_t kernel, dim3 grid, dim3 block, void **args, size_t smem,
                                cudaStream_t stream) {
-    (void)args; (void)stream;
-    record_launch((const void *)kernel, grid, block, smem, NULL);
+    (void)stream;
+    record_launch((const void *)kernel, grid, block, smem, NULL, args);
     return cudaSuccess;
 }
 
 cudaError_t cudaLaunchKernelExC(const cudaLaunchConfig_t *config, const void *func, void **args) {
-    (void)args;
     unsigned cl[3] = {1, 1, 1};
     for (unsigned i = 0; i < config->numAttrs; i++)
         if (config->attrs[i].id == cudaLaunchAttributeClusterDimension) {
@@ -124,7 +135,7 @@ cudaError_t cudaLaunchKernelExC(const cudaLaunchConfig_t *config, const void *fu
             cl[1] = config->attrs[i].val.clusterDim.y;
             cl[2] = config->attrs[i].val.clusterDim.z;
         }
-    record_launch(func, config->gridDim, config->blockDim, config->dynamicSmemBytes, cl);
+    record_launch(func, config->gridDim, config->blockDim, config->dynamicSmemBytes, cl, args);
     return cudaSuccess;
 }
 
@@ -228,6 +239,13 @@ cudaError_t cudaGetDriverEntryPointByVersion(const char *symbol, void **fn, unsi
 }
 
 /* ---- read-back for the test driver ----------------------------------------- */
+int shim_var(int i, void **p, size_t *size) {
+    if (i >= g_nvars) return 0;
+    *p = g_vars[i].buf;
+    *size = g_vars[i].size;
+    return 1;
+}
+
 int shim_launch_count(void) { return g_nlaunch; }
 int shim_tmap_count(void) { return g_ntmap; }
 void shim_reset(void) { g_nlaunch = 0; g_ntmap = 0; g_fail_launch = 0; }

@@ -33,6 +33,334 @@ shim.shim_launch.restype = ct.c_char_p
 assert hasattr(shim, "shim_reset"), "the stand-in runtime is not the one loaded"
 
 OPT = {"aux_chunk": 0, "schedule": 1, "raster": 2, "use_tuned": 3, "cluster": 4, "host_chunk": 5}
+
+# ---- kernel arguments ----------------------------------------------------------
+# Each decoder reads one kernel's arguments (layouts as in the CUDA sources)
+# and returns the byte ranges [lo, hi) its pointer arguments can touch, from
+# the kernel's own index bounds; every range must lie in memory the call owns.
+VP, I32, I64, F64 = ct.c_void_p, ct.c_int32, ct.c_int64, ct.c_double
+SUPER, NSLICE, MAXD = 2048, 6, 64
+
+
+class Src(ct.Structure):
+    _fields_ = [("p", VP), ("sr", I64), ("sko", I64), ("ski", I64), ("kin", I32), ("rin", I32), ("sri", I64)]
+
+
+class GOp(ct.Structure):
+    _fields_ = [("p", VP), ("sb", I64), ("sr", I64), ("sko", I64), ("ski", I64), ("kin", I32)]
+
+
+class DensTab(ct.Structure):
+    _fields_ = [("Y", VP * MAXD), ("offX", I32 * MAXD), ("k", I32 * MAXD)]
+
+
+class OutTab(ct.Structure):
+    _fields_ = [("p", VP * 8)]
+
+
+class PairTab(ct.Structure):
+    _fields_ = [("offA", I32 * MAXD), ("offB", I32 * MAXD), ("k", I32 * MAXD)]
+
+
+class OzArgs(ct.Structure):
+    _fields_ = [("M", I32), ("N", I32), ("K", I32), ("nsuper", I32), ("eA", VP), ("a_rpe", I32), ("eB", VP),
+                ("b_rpe", I32), ("C", VP), ("ldc", I64), ("P", VP), ("pz", I64), ("ldp", I64),
+                ("use_tma_store", I32), ("err", VP)]
+
+
+class OzTail(ct.Structure):
+    _fields_ = [("tile0", I32), ("ntn", I32), ("ntm", I32), ("un", I32), ("um", I32), ("pair_n", I32)]
+
+
+OZ_PROB_BYTES = (4 * 128 + ct.sizeof(OzArgs) + ct.sizeof(OzTail) + 63) // 64 * 64
+OZ_BM, OZ_BN = 128, 80
+
+
+def _a(args, i, t):
+    return t.from_address(args[i])
+
+
+def _v(args, i, t):
+    return t.from_address(args[i]).value
+
+
+def _lin_max(n, inner, s_out, s_in):
+    """max over idx < n of (idx // inner) * s_out + (idx % inner) * s_in (strides >= 0)."""
+    if n <= 0:
+        return 0
+    q, r = divmod(n - 1, inner)
+    best = q * s_out + r * s_in
+    if q > 0:
+        best = max(best, (q - 1) * s_out + (inner - 1) * s_in)
+    return best
+
+
+def _src_range(src, rows, K, esize=8):
+    assert min(src.sr, src.sko, src.ski, src.sri) >= 0, "negative stride"
+    hi = _lin_max(rows, src.rin, src.sr, src.sri) + _lin_max(K, src.kin, src.sko, src.ski)
+    return (src.p, src.p + (hi + 1) * esize, "src")
+
+
+def _gop_range(g, batch, rows, K):
+    assert min(g.sb, g.sr, g.sko, g.ski) >= 0, "negative stride"
+    hi = (batch - 1) * g.sb + (rows - 1) * g.sr + _lin_max(K, g.kin, g.sko, g.ski)
+    return (g.p, g.p + (hi + 1) * 8, "gop")
+
+
+def dec_expo(grid, args):
+    src, rows, K, rpe, e = _a(args, 0, Src), _v(args, 1, I32), _v(args, 2, I32), _v(args, 3, I32), _v(args, 4, VP)
+    assert (grid[0] - 1) * rpe < rows <= grid[0] * rpe and grid[1] == (K + SUPER - 1) // SUPER, (grid, rows, K)
+    return [_src_range(src, rows, K), (e, e + 4 * grid[0] * grid[1], "e")]
+
+
+def dec_expo_flat(grid, args):
+    p, ln, e = _v(args, 0, VP), _v(args, 1, I64), _v(args, 2, VP)
+    assert ln % 2 == 0 and p % 16 == 0
+    return [(p, p + 8 * grid[0] * ln, "p"), (e, e + 4 * grid[0], "e")]
+
+
+def _slice(grid, args, esize_out, per):
+    src, rows, K, Kpad = _a(args, 0, Src), _v(args, 1, I32), _v(args, 2, I32), _v(args, 3, I32)
+    e, rpe, nsc, out, ss = _v(args, 4, VP), _v(args, 5, I32), _v(args, 6, I32), _v(args, 7, VP), _v(args, 8, I64)
+    assert grid[0] * 256 * per >= Kpad and Kpad % 16 == 0 and K <= Kpad
+    ne = ((rows - 1) // rpe) * nsc + (K - 1) // SUPER + 1
+    nout = (NSLICE - 1) * ss + (rows * Kpad) // per
+    return [_src_range(src, rows, K), (e, e + 4 * ne, "e"), (out, out + esize_out * nout, "slices")]
+
+
+def dec_slice(grid, args):
+    return _slice(grid, args, 2, 1)
+
+
+def dec_slice4(grid, args):
+    src = _a(args, 0, Src)
+    assert src.ski == 1 and src.kin % 4 == 0 and _v(args, 2, I32) % 4 == 0 and src.p % 16 == 0
+    return _slice(grid, args, 8, 4)
+
+
+def dec_dgemm(grid, args):
+    M, N, K = _v(args, 0, I32), _v(args, 1, I32), _v(args, 2, I32)
+    A, B, C, ldc, scb = _a(args, 3, GOp), _a(args, 4, GOp), _v(args, 5, VP), _v(args, 6, I64), _v(args, 7, I64)
+    nb = grid[2]
+    assert grid[0] * 64 >= N and grid[1] * 64 >= M
+    return [_gop_range(A, nb, M, K), _gop_range(B, nb, N, K),
+            (C, C + 8 * ((nb - 1) * scb + (M - 1) * ldc + N), "C")]
+
+
+def dec_pack_cols(grid, args):
+    src, n, k, Z, ctot, off = (_v(args, 0, VP), _v(args, 1, I32), _v(args, 2, I32), _v(args, 3, VP),
+                               _v(args, 4, I32), _v(args, 5, I32))
+    assert off + k <= ctot
+    return [(src, src + 8 * n * k, "src"), (Z, Z + 8 * ((n - 1) * ctot + off + k), "Z")]
+
+
+def dec_frob(grid, args):
+    L, n2, M, nd, g, ldg, P0 = (_v(args, 0, VP), _v(args, 1, I64), _v(args, 2, VP), _v(args, 3, I32),
+                                _v(args, 4, VP), _v(args, 5, I32), _v(args, 6, I32))
+    assert grid[1] == (nd + 3) // 4
+    return [(L, L + 8 * (P0 + grid[0]) * n2, "L"), (M, M + 8 * nd * n2, "Mats"),
+            (g, g + 8 * ((nd - 1) * ldg + P0 + grid[0]), "gamma")]
+
+
+def dec_gamma_panel(grid, args):
+    T, n, ctot, tab, g, ldg, P0 = (_v(args, 0, VP), _v(args, 1, I32), _v(args, 2, I64), _a(args, 3, DensTab),
+                                   _v(args, 4, VP), _v(args, 5, I32), _v(args, 6, I32))
+    np_, nd = grid[0], grid[1]
+    out = [(g, g + 8 * ((nd - 1) * ldg + P0 + np_), "gamma")]
+    for s in range(nd):
+        k, off = tab.k[s], tab.offX[s]
+        assert off + k <= ctot
+        out.append((T, T + 8 * ((np_ - 1) * n * ctot + (n - 1) * ctot + off + k), "T"))
+        out.append((tab.Y[s], tab.Y[s] + 8 * n * k, "Y"))
+    return out
+
+
+def dec_jstream_sym(grid, args, name):
+    ns = int(name.split("ILi")[1].split("E")[0])
+    L, n, naux, g, ldg, o = (_v(args, 0, VP), _v(args, 1, I32), _v(args, 2, I32), _v(args, 3, VP),
+                             _v(args, 4, I32), _a(args, 5, OutTab))
+    assert grid[0] * 64 >= n * (n + 1) // 2
+    out = [(L, L + 8 * naux * n * n, "L"), (g, g + 8 * ((ns - 1) * ldg + naux), "g")]
+    out += [(o.p[j], o.p[j] + 8 * n * n, "J") for j in range(ns)]
+    return out
+
+
+def dec_axpy(grid, args):
+    y, x, cnt = _v(args, 0, VP), _v(args, 1, VP), _v(args, 2, I64)
+    return [(y, y + 8 * cnt, "y"), (x, x + 8 * cnt, "x")]
+
+
+def dec_sum_parts(grid, args):
+    out, part, nb, cnt = _v(args, 0, VP), _v(args, 1, VP), _v(args, 2, I32), _v(args, 3, I64)
+    return [(out, out + 8 * cnt, "out"), (part, part + 8 * nb * cnt, "part")]
+
+
+def dec_reduce(grid, args):
+    P, pz, ldp, nz, M, N = (_v(args, 0, VP), _v(args, 1, I64), _v(args, 2, I64), _v(args, 3, I32),
+                            _v(args, 4, I32), _v(args, 5, I32))
+    eA, arpe, eB, brpe, out, ldo = (_v(args, 6, VP), _v(args, 7, I32), _v(args, 8, VP), _v(args, 9, I32),
+                                    _v(args, 10, VP), _v(args, 11, I64))
+    return [(P, P + 8 * ((nz - 1) * pz + (M - 1) * ldp + N), "P"),
+            (eA, eA + 4 * ((M - 1) // arpe + 1) * nz, "eA"), (eB, eB + 4 * ((N - 1) // brpe + 1) * nz, "eB"),
+            (out, out + 8 * ((M - 1) * ldo + N), "out")]
+
+
+def dec_pair_dot(grid, args):
+    ZL, U, n, ctot, tab, out, nr = (_v(args, 0, VP), _v(args, 1, VP), _v(args, 2, I32), _v(args, 3, I32),
+                                    _a(args, 4, PairTab), _v(args, 5, VP), _v(args, 6, I32))
+    nl = grid[0]
+    assert grid[1] == nr
+    res = [(out, out + 8 * nl * nr, "out")]
+    for a in range(nl):
+        k = tab.k[a]
+        assert tab.offA[a] + k <= ctot and tab.offB[a] + k <= ctot
+        res.append((ZL, ZL + 8 * ((n - 1) * ctot + tab.offA[a] + k), "ZL"))
+        res.append((U, U + 8 * ((nr - 1) * n * ctot + (n - 1) * ctot + tab.offB[a] + k), "U"))
+    return res
+
+
+def dec_laplace_scale(grid, args):
+    C, eps, n, m, nq, out = (_v(args, 0, VP), _v(args, 1, VP), _v(args, 2, I32), _v(args, 3, I32),
+                             _v(args, 6, I32), _v(args, 7, VP))
+    assert grid[0] * 256 >= n * m * nq and 1 <= nq <= MAXD
+    return [(C, C + 8 * n * m, "C"), (eps, eps + 8 * m, "eps"), (out, out + 8 * nq * n * m, "out")]
+
+
+def dec_weighted_sum(grid, args):
+    out, part, nq, cnt = _v(args, 0, VP), _v(args, 1, VP), _v(args, 3, I32), _v(args, 4, I64)
+    assert 1 <= nq <= MAXD
+    return [(out, out + 8 * cnt, "out"), (part, part + 8 * nq * cnt, "part")]
+
+
+def dec_gterms(grid, args):
+    G, n2, nd = _v(args, 0, VP), _v(args, 1, I64), _v(args, 3, I32)
+    D, V, c, g, ldg, P0 = (_v(args, 4, VP), _v(args, 5, VP), _v(args, 6, VP), _v(args, 7, VP), _v(args, 8, I32),
+                           _v(args, 9, I32))
+    np_ = grid[1]
+    res = [(G, G + 8 * np_ * n2, "G")]
+    top = 8 * ((nd - 1) * ldg + P0 + np_)
+    if D:
+        res += [(D, D + 8 * nd * n2, "D"), (c, c + top, "c")]
+    if V:
+        res += [(V, V + 8 * nd * n2, "V"), (g, g + top, "g")]
+    return res
+
+
+def dec_symmetrize(grid, args):
+    G, n, dL = _v(args, 0, VP), _v(args, 1, I32), _v(args, 2, VP)
+    return [(G, G + 8 * grid[1] * n * n, "G"), (dL, dL + 8 * grid[1] * n * n, "dL")]
+
+
+def dec_sym_dl(grid, args):
+    G, GV, n, dL = _v(args, 0, VP), _v(args, 1, VP), _v(args, 2, I32), _v(args, 3, VP)
+    nb = 8 * grid[1] * n * n
+    res = [(G, G + nb, "G"), (dL, dL + nb, "dL")]
+    if GV:
+        res.append((GV, GV + nb, "GV"))
+    return res
+
+
+def dec_fold(grid, args):
+    dX, dY, cnt = _v(args, 0, VP), _v(args, 1, VP), _v(args, 2, I64)
+    return [(dX, dX + 8 * cnt, "dX"), (dY, dY + 8 * cnt, "dY")]
+
+
+def dec_pack_ag(grid, args):
+    AG, ldag, off, U, Vp, X, cps, P0, n, k, np_ = (
+        _v(args, 0, VP), _v(args, 1, I64), _v(args, 2, I32), _v(args, 3, VP), _v(args, 4, VP), _v(args, 5, VP),
+        _v(args, 6, VP), _v(args, 7, I32), _v(args, 8, I32), _v(args, 9, I32), _v(args, 10, I32))
+    assert off + 3 * k <= ldag
+    res = [(AG, AG + 8 * ((np_ * n - 1) * ldag + off + 3 * k), "AG")]
+    for ptr_, what in ((U, "U"), (Vp, "Vp")):
+        if ptr_:
+            res.append((ptr_, ptr_ + 8 * n * np_ * k, what))
+    if cps:
+        res += [(cps, cps + 8 * (P0 + np_), "cps"), (X, X + 8 * n * k, "X")]
+    return res
+
+
+def dec_pack_bg(grid, args):
+    BG, ldbg, off, X, Y, n, k = (_v(args, 0, VP), _v(args, 1, I64), _v(args, 2, I32), _v(args, 3, VP),
+                                 _v(args, 4, VP), _v(args, 5, I32), _v(args, 6, I32))
+    assert off + 3 * k <= ldbg
+    return [(BG, BG + 8 * ((n - 1) * ldbg + off + 3 * k), "BG"), (X, X + 8 * n * k, "X"), (Y, Y + 8 * n * k, "Y")]
+
+
+def dec_ozgemm(grid, args):
+    base = args[0]
+    nprob = I32.from_address(base + 32 * OZ_PROB_BYTES).value
+    nunits = I32.from_address(base + 32 * OZ_PROB_BYTES + 4).value
+    assert 1 <= nprob <= 32, nprob
+    units, res = 0, []
+    for i in range(nprob):
+        pb = base + i * OZ_PROB_BYTES
+        a = OzArgs.from_address(pb + 512)
+        t = OzTail.from_address(pb + 512 + ct.sizeof(OzArgs))
+        assert t.tile0 == units, (t.tile0, units)
+        units += t.un * t.um * a.nsuper
+        assert a.M >= 1 and a.N >= 1 and a.K >= 1 and a.nsuper == (a.K + SUPER - 1) // SUPER
+        assert t.ntm == (a.M + OZ_BM - 1) // OZ_BM and t.ntn == (a.N + OZ_BN - 1) // OZ_BN
+        nsc = a.nsuper
+        res.append((a.eA, a.eA + 4 * ((a.M - 1) // a.a_rpe + 1) * nsc, "eA"))
+        res.append((a.eB, a.eB + 4 * ((a.N - 1) // a.b_rpe + 1) * nsc, "eB"))
+        if not a.use_tma_store:
+            res.append((a.C, a.C + 8 * ((a.M - 1) * a.ldc + a.N), "C"))
+    assert units == nunits, (units, nunits)
+    return res
+
+
+DECODERS = [
+    ("expo_flat_kernel", dec_expo_flat), ("expo_kernel", dec_expo), ("slice4_kernel", dec_slice4),
+    ("slice_kernel", dec_slice), ("dgemm_nt_kernel", dec_dgemm), ("pack_cols_kernel", dec_pack_cols),
+    ("frob_stream_kernel", dec_frob), ("gamma_panel_kernel", dec_gamma_panel), ("axpy_kernel", dec_axpy),
+    ("sum_parts_kernel", dec_sum_parts), ("reduce_partials_kernel", dec_reduce), ("pair_dot_kernel", dec_pair_dot),
+    ("laplace_scale_kernel", dec_laplace_scale), ("weighted_sum_kernel", dec_weighted_sum),
+    ("ozgemm_kernel", dec_ozgemm), ("jstream_sym_kernel", dec_jstream_sym), ("gterms_kernel", dec_gterms),
+    ("symmetrize_kernel", dec_symmetrize), ("sym_dl_kernel", dec_sym_dl), ("fold_sym_split_kernel", dec_fold),
+    ("fold_sym_kernel", dec_fold), ("pack_ag_kernel", dec_pack_ag), ("pack_bg_kernel", dec_pack_bg),
+]
+violations, decoded, undecoded = [], [0], set()
+
+
+def _inside(lo, hi):
+    if hi <= lo:
+        return True
+    for base, nbytes, _label, *_ in owned + statics():
+        if base <= lo and hi <= base + nbytes:
+            return True
+    return False
+
+
+def statics():
+    out, i = [], 0
+    p, sz = ct.c_void_p(), ct.c_size_t()
+    while shim.shim_var(i, ct.byref(p), ct.byref(sz)):
+        if p.value:
+            out.append((p.value, sz.value, "static"))
+        i += 1
+    return out
+
+
+@ct.CFUNCTYPE(None, ct.c_char_p, ct.POINTER(ct.c_uint), ct.POINTER(ct.c_uint), ct.POINTER(ct.c_void_p))
+def on_launch(name, grid, block, args):
+    name = name.decode()
+    g = (grid[0], grid[1], grid[2])
+    for key, fn in DECODERS:
+        if key in name:
+            try:
+                ranges = fn(g, args, name) if fn is dec_jstream_sym else fn(g, args)
+            except AssertionError as e:
+                violations.append(f"{key}: inconsistent arguments {e}")
+                return
+            decoded[0] += 1
+            for lo, hi, what in ranges:
+                if not _inside(lo, hi):
+                    violations.append(f"{key}: {what} [{lo:#x}, {hi:#x}) outside the call's memory")
+            return
+    undecoded.add(name)
+
+
+shim.shim_set_hook(on_launch)
 rng = np.random.default_rng(0)
 owned = []      # (base, nbytes, label) of every buffer a case hands to the library
 
@@ -105,11 +433,15 @@ def record(name, status, h):
                       "strides": list(strides)[:r], "box": list(box)[:r]})
     err = lib.jk_last_error(h).decode() if h else ""
     print(json.dumps({"case": name, "status": status, "error": err, "launches": launches, "tmaps": tmaps,
-                      "owned": [[o[0], o[1], o[2]] for o in owned]}), flush=True)
+                      "owned": [[o[0], o[1], o[2]] for o in owned + statics()], "violations": list(violations),
+                      "decoded": decoded[0], "undecoded": sorted(undecoded)}), flush=True)
 
 
 def run(name, fn):
     owned.clear()
+    violations.clear()
+    undecoded.clear()
+    decoded[0] = 0
     shim.shim_reset()
     status, h = fn()
     record(name, status, h)

@@ -14,7 +14,11 @@ pairings, Laplace builds, the arena-free build, the autotuner) this checks:
 - every tensor map obeys the TMA encoding rules (16-byte aligned base and
   strides, box at most 256 per dimension, inner box a multiple of 16 bytes
   and within the swizzle span) and addresses only memory the call owns
-  (the arena or one of its inputs or outputs).
+  (the arena or one of its inputs or outputs);
+- every kernel's arguments, decoded from its signature at launch time
+  (tests/hostsim/drive.py), are self-consistent with its grid, and every
+  byte range its pointer arguments can touch (from the kernel's own index
+  bounds) lies in memory the call owns.  Every launch must be decoded.
 Values are not checked here: the kernels do not run.
 """
 import json
@@ -76,6 +80,8 @@ def test_case(records, name):
         assert 1 <= block[0] * block[1] * block[2] <= 1024, (kname, block)
         assert smem <= 227 * 1024, (kname, smem)
         assert cluster[0] * cluster[1] * cluster[2] <= 8 and grid[0] % cluster[0] == 0, (kname, grid, cluster)
+    assert not rec["violations"], rec["violations"][:5]
+    assert not rec["undecoded"] and rec["decoded"] == len(rec["launches"]), rec["undecoded"]
     owned = rec["owned"]
     for t in rec["tmaps"]:
         es = ESIZE[t["dtype"]]
