@@ -36,7 +36,7 @@ SWIZZLE_SPAN = {0: None, 1: 32, 2: 64, 3: 128}
 
 
 @pytest.fixture(scope="module")
-def records(tmp_path_factory):
+def shim_dir(tmp_path_factory):
     from paper_2608_06536_b300 import build as pkg_build
     pkg_build.build()
     d = tmp_path_factory.mktemp("cudart")
@@ -44,9 +44,13 @@ def records(tmp_path_factory):
     subprocess.run(["gcc", "-O1", "-fPIC", "-shared", "-std=c11", "-I/usr/local/cuda/include",
                     f"-Wl,--version-script={d / 'ver.map'}", "-Wl,-soname,libcudart.so.13",
                     "-o", str(d / "libcudart.so.13"), os.path.join(SIM, "cudart_shim.c")], check=True)
-    env = dict(os.environ, LD_LIBRARY_PATH=str(d))
-    r = subprocess.run([sys.executable, os.path.join(SIM, "drive.py")], env=env, capture_output=True, text=True,
-                       timeout=600)
+    return d
+
+
+def _drive(shim_dir, names=()):
+    env = dict(os.environ, LD_LIBRARY_PATH=str(shim_dir))
+    r = subprocess.run([sys.executable, os.path.join(SIM, "drive.py"), *names], env=env, capture_output=True,
+                       text=True, timeout=600)
     assert r.returncode == 0, r.stderr[-3000:]
     out = {}
     for line in r.stdout.splitlines():
@@ -55,15 +59,29 @@ def records(tmp_path_factory):
     return out
 
 
-def _names():
-    # the case list, read from the driver's source without importing it (the
+@pytest.fixture(scope="module")
+def records(shim_dir):
+    return _drive(shim_dir)
+
+
+@pytest.fixture(scope="module")
+def full_records(shim_dir):
+    import psutil
+    if psutil.virtual_memory().available < 24 << 30:
+        pytest.skip("the full-size host simulation maps about 20 GB of (untouched) buffers")
+    return _drive(shim_dir, FULL_NAMES)
+
+
+def _names(table):
+    # the case lists, read from the driver's source without importing it (the
     # driver loads the library at import)
     src = open(os.path.join(SIM, "drive.py")).read()
-    body = src.split("CASES = {", 1)[1].split("\n}\n", 1)[0]
+    body = src.split(f"{table} = {{", 1)[1].split("\n}\n", 1)[0]
     return [line.split('"')[1] for line in body.splitlines() if line.strip().startswith('"')]
 
 
-NAMES = _names()
+NAMES = _names("CASES")
+FULL_NAMES = _names("FULL_CASES")
 
 
 def test_every_case_ran(records):
@@ -72,7 +90,22 @@ def test_every_case_ran(records):
 
 @pytest.mark.parametrize("name", NAMES)
 def test_case(records, name):
-    rec = records[name]
+    _check(records[name])
+
+
+@pytest.mark.parametrize("name", FULL_NAMES)
+def test_full_size_case(full_records, name):
+    """The measured workloads at their full sizes (bench.py's shapes)."""
+    _check(full_records[name])
+
+
+def test_full_size_tuned_build_launch_count(full_records):
+    """The tuned multi-state build issues the launches bench.py counts on the
+    B300 (61 per build: grouped persistent GEMMs, slicers, FP64 J streams)."""
+    assert len(full_records["full_multi_state_tuned"]["launches"]) == 61
+
+
+def _check(rec):
     assert rec["status"] == 0, (rec["status"], rec["error"])
     assert rec["launches"], "no kernel was launched"
     for kname, grid, block, cluster, smem in rec["launches"]:
