@@ -166,13 +166,16 @@ cudaError_t cudaPointerGetAttributes(struct cudaPointerAttributes *a, const void
     return cudaSuccess;
 }
 
+static int g_ncopies;   /* memsets and copies enqueued on a stream */
 cudaError_t cudaMemset(void *p, int v, size_t n) { memset(p, v, n); return cudaSuccess; }
-cudaError_t cudaMemsetAsync(void *p, int v, size_t n, cudaStream_t s) { (void)s; memset(p, v, n); return cudaSuccess; }
+cudaError_t cudaMemsetAsync(void *p, int v, size_t n, cudaStream_t s) {
+    (void)s; g_ncopies++; memset(p, v, n); return cudaSuccess;
+}
 cudaError_t cudaMemcpy(void *d, const void *s, size_t n, enum cudaMemcpyKind k) {
     (void)k; memmove(d, s, n); return cudaSuccess;
 }
 cudaError_t cudaMemcpyAsync(void *d, const void *s, size_t n, enum cudaMemcpyKind k, cudaStream_t st) {
-    (void)k; (void)st; memmove(d, s, n); return cudaSuccess;
+    (void)k; (void)st; g_ncopies++; memmove(d, s, n); return cudaSuccess;
 }
 
 cudaError_t cudaGetSymbolAddress(void **p, const void *symbol) {
@@ -248,7 +251,8 @@ int shim_var(int i, void **p, size_t *size) {
 
 int shim_launch_count(void) { return g_nlaunch; }
 int shim_tmap_count(void) { return g_ntmap; }
-void shim_reset(void) { g_nlaunch = 0; g_ntmap = 0; g_fail_launch = 0; }
+int shim_copy_count(void) { return g_ncopies; }
+void shim_reset(void) { g_nlaunch = 0; g_ntmap = 0; g_fail_launch = 0; g_ncopies = 0; }
 
 const char *shim_launch(int i, unsigned *grid, unsigned *block, unsigned *cluster, size_t *smem) {
     const Launch *l = &g_launch[i];

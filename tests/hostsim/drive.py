@@ -366,6 +366,7 @@ owned = []      # (base, nbytes, label) of every buffer a case hands to the libr
 
 
 BIG = [False]     # full-size cases: inputs left as untouched zero pages
+ARENA_SCALE = [1.0]   # the arena handed to each call, as a fraction of the queried size
 
 
 def buf(shape, label, fill=True):
@@ -395,7 +396,9 @@ def mol(n, naux, ks, sym, tag="m"):
     return jk_factor(n, naux, L.ctypes.data), d, L, X, Y
 
 
-def handle(nbytes, opts):
+def handle(nbytes, opts, scaled=True):
+    if scaled:
+        nbytes = max(int(nbytes * ARENA_SCALE[0]), 1 << 16)
     ws = buf((nbytes // 8 + 1,), "arena", fill=False)
     h = ct.c_void_p()
     st = lib.jk_create(ct.byref(h), ct.c_void_p(ws.ctypes.data), ct.c_size_t(nbytes))
@@ -436,6 +439,7 @@ def record(name, status, h):
                       "strides": list(strides)[:r], "box": list(box)[:r]})
     err = lib.jk_last_error(h).decode() if h else ""
     print(json.dumps({"case": name, "status": status, "error": err, "launches": launches, "tmaps": tmaps,
+                      "copies": shim.shim_copy_count(),
                       "owned": [[o[0], o[1], o[2]] for o in owned + statics()], "violations": list(violations),
                       "decoded": decoded[0], "undecoded": sorted(undecoded)}), flush=True)
 
@@ -457,7 +461,7 @@ def run(name, fn):
 def build_case(n, naux, ks, sym, p, opts):
     def fn():
         f, d, *_ = mol(n, naux, ks, sym)
-        h = handle(1 << 20, opts)
+        h = handle(1 << 20, opts, scaled=False)
         nb = query(0, f, d, len(ks), p, h=h)
         lib.jk_destroy(h)
         h = handle(nb, opts)
@@ -477,7 +481,7 @@ def batched_case(shapes, p, opts):
         fa = (jk_factor * len(fs))(*fs)
         da = (jk_density * len(ds))(*ds)
         ndm = [len(s[2]) for s in shapes]
-        h = handle(1 << 20, opts)
+        h = handle(1 << 20, opts, scaled=False)
         nb = query(2, fa, da, len(ds), p, nmol=len(fs), ndm=ndm, h=h)
         lib.jk_destroy(h)
         h = handle(nb, opts)
@@ -490,7 +494,7 @@ def batched_case(shapes, p, opts):
 def host_case(n, naux, ks, p, opts):
     def fn():
         f, d, *_ = mol(n, naux, ks, [False] * len(ks))
-        h = handle(1 << 20, opts)
+        h = handle(1 << 20, opts, scaled=False)
         nb = query(3, f, d, len(ks), p, h=h)
         lib.jk_destroy(h)
         h = handle(nb, opts)
@@ -506,7 +510,7 @@ def adjoint_case(n, naux, ks, sym, p, opts, want_dl=True):
         W, V = buf((nd, n, n), "W"), buf((nd, n, n), "V")
         dX, dY = buf((tot,), "dX", False), buf((tot,), "dY", False)
         dL = buf((naux, n, n), "dL", False) if want_dl else None
-        h = handle(1 << 20, opts)
+        h = handle(1 << 20, opts, scaled=False)
         nb = query(1, f, d, nd, p, h=h)
         lib.jk_destroy(h)
         h = handle(nb, opts)
@@ -520,7 +524,7 @@ def dense_case(n, naux, nd, p, opts, grad=None):
         f = jk_factor(n, naux, L.ctypes.data)
         A, B = buf((nd, n, n), "A"), buf((nd, n, n), "B")
         O1, O2 = buf((nd, n, n), "O1", False), buf((nd, n, n), "O2", False)
-        h = handle(1 << 20, opts)
+        h = handle(1 << 20, opts, scaled=False)
         nb = query(5 if grad else 4, f, None, nd, p, h=h)
         lib.jk_destroy(h)
         h = handle(nb, opts)
@@ -542,7 +546,7 @@ def pair_case(n, naux, kl, sl, kr, sr, p, opts):
             dr[s].k, dr[s].symmetric, dr[s].X = k, int(sr[s]), XR[s].ctypes.data
             dr[s].Y = None if sr[s] else YR[s].ctypes.data
         both = (jk_density * (len(kl) + len(kr)))(*dl, *dr)
-        h = handle(1 << 20, opts)
+        h = handle(1 << 20, opts, scaled=False)
         nb = query(6, (jk_factor * 2)(f, f), both, len(kl) + len(kr), p, nmol=2, ndm=[len(kl), len(kr)], h=h)
         lib.jk_destroy(h)
         h = handle(nb, opts)
@@ -559,7 +563,7 @@ def laplace_case(n, naux, m, nq, sym, weighted, p, opts):
         eX, eY = buf((m,), "epsX"), buf((m,), "epsY")
         d = (jk_density * 1)()
         d[0].k, d[0].symmetric = m, int(sym)
-        h = handle(1 << 20, opts)
+        h = handle(1 << 20, opts, scaled=False)
         nb = query(7, f, d, nq, p, h=h)
         lib.jk_destroy(h)
         h = handle(nb, opts)
@@ -652,7 +656,11 @@ FULL_CASES = {
 }
 
 if __name__ == "__main__":
-    names = sys.argv[1:] or list(CASES)
+    args = sys.argv[1:]
+    for a in [a for a in args if a.startswith("--arena-scale=")]:
+        ARENA_SCALE[0] = float(a.split("=", 1)[1])
+        args.remove(a)
+    names = args or list(CASES)
     for name in names:
         BIG[0] = name in FULL_CASES
         run(name, CASES.get(name) or FULL_CASES[name])

@@ -18,7 +18,8 @@ pairings, Laplace builds, the arena-free build, the autotuner) this checks:
 - every kernel's arguments, decoded from its signature at launch time
   (tests/hostsim/drive.py), are self-consistent with its grid, and every
   byte range its pointer arguments can touch (from the kernel's own index
-  bounds) lies in memory the call owns.  Every launch must be decoded.
+  bounds) lies in memory the call owns.  Every launch must be decoded;
+- with too small an arena a call fails before enqueueing any device work.
 Values are not checked here: the kernels do not run.
 """
 import json
@@ -155,3 +156,19 @@ def test_dense_split_needs_no_identity_panel(records):
     for all densities and one reduction GEMM per density."""
     names = _kernels(records["dense_split"])
     assert sum("ozgemm_kernel" in k for k in names) == 1 + 2
+
+
+# needs far less than the query, which covers both maps; no arena; skips what does not fit
+FITS_IN_HALF = {"grad_fp64_V", "noalloc", "autotune_split"}
+
+
+def test_too_small_arena_fails_before_any_device_work(shim_dir):
+    """With half the queried arena every call reports JK_ERR_OOM and has
+    enqueued nothing: no kernel, no memset, no copy."""
+    recs = _drive(shim_dir, ["--arena-scale=0.5"])
+    assert sorted(recs) == sorted(NAMES)
+    for name, rec in recs.items():
+        if name in FITS_IN_HALF:
+            continue
+        assert rec["status"] == 3 and "arena" in rec["error"], (name, rec["status"], rec["error"])
+        assert not rec["launches"] and rec["copies"] == 0, (name, len(rec["launches"]), rec["copies"])
