@@ -51,6 +51,9 @@ static int g_nvars;
 
 static struct { dim3 grid, block; size_t smem; void *stream; } g_cfg;
 static int g_fail_launch;
+static int g_ncopies;   /* memsets and copies enqueued on a stream */
+static int g_nsync;     /* calls that wait for the device (illegal while capturing a graph) */
+static int g_nsetup;    /* one-time set-up: streams, events, function attributes, symbol and entry lookups */
 
 /* Called at every launch while the argument array is alive, so the test can
  * decode each kernel's arguments from its signature. */
@@ -141,11 +144,13 @@ cudaError_t cudaLaunchKernelExC(const cudaLaunchConfig_t *config, const void *fu
 
 cudaError_t cudaFuncSetAttribute(const void *func, enum cudaFuncAttribute attr, int value) {
     (void)func; (void)attr; (void)value;
+    g_nsetup++;
     return cudaSuccess;
 }
 
 cudaError_t cudaOccupancyMaxActiveClusters(int *n, const void *func, const cudaLaunchConfig_t *cfg) {
     (void)func; (void)cfg;
+    g_nsetup++;
     *n = 74;
     return cudaSuccess;
 }
@@ -166,19 +171,19 @@ cudaError_t cudaPointerGetAttributes(struct cudaPointerAttributes *a, const void
     return cudaSuccess;
 }
 
-static int g_ncopies;   /* memsets and copies enqueued on a stream */
-cudaError_t cudaMemset(void *p, int v, size_t n) { memset(p, v, n); return cudaSuccess; }
+cudaError_t cudaMemset(void *p, int v, size_t n) { g_nsync++; memset(p, v, n); return cudaSuccess; }
 cudaError_t cudaMemsetAsync(void *p, int v, size_t n, cudaStream_t s) {
     (void)s; g_ncopies++; memset(p, v, n); return cudaSuccess;
 }
 cudaError_t cudaMemcpy(void *d, const void *s, size_t n, enum cudaMemcpyKind k) {
-    (void)k; memmove(d, s, n); return cudaSuccess;
+    (void)k; g_nsync++; memmove(d, s, n); return cudaSuccess;
 }
 cudaError_t cudaMemcpyAsync(void *d, const void *s, size_t n, enum cudaMemcpyKind k, cudaStream_t st) {
     (void)k; (void)st; g_ncopies++; memmove(d, s, n); return cudaSuccess;
 }
 
 cudaError_t cudaGetSymbolAddress(void **p, const void *symbol) {
+    g_nsetup++;
     for (int i = 0; i < g_nvars; i++)
         if (g_vars[i].host == symbol) {
             if (!g_vars[i].buf) g_vars[i].buf = aligned_alloc(256, (g_vars[i].size + 255) / 256 * 256);
@@ -192,14 +197,14 @@ static char g_handles[256];
 static int g_nhandles;
 static void *new_handle(void) { return &g_handles[(g_nhandles++) % 256]; }
 
-cudaError_t cudaStreamCreateWithFlags(cudaStream_t *s, unsigned f) { (void)f; *s = (cudaStream_t)new_handle(); return cudaSuccess; }
+cudaError_t cudaStreamCreateWithFlags(cudaStream_t *s, unsigned f) { (void)f; g_nsetup++; *s = (cudaStream_t)new_handle(); return cudaSuccess; }
 cudaError_t cudaStreamDestroy(cudaStream_t s) { (void)s; return cudaSuccess; }
-cudaError_t cudaStreamSynchronize(cudaStream_t s) { (void)s; return cudaSuccess; }
+cudaError_t cudaStreamSynchronize(cudaStream_t s) { (void)s; g_nsync++; return cudaSuccess; }
 cudaError_t cudaStreamWaitEvent(cudaStream_t s, cudaEvent_t e, unsigned f) { (void)s; (void)e; (void)f; return cudaSuccess; }
-cudaError_t cudaEventCreate(cudaEvent_t *e) { *e = (cudaEvent_t)new_handle(); return cudaSuccess; }
-cudaError_t cudaEventCreateWithFlags(cudaEvent_t *e, unsigned f) { (void)f; *e = (cudaEvent_t)new_handle(); return cudaSuccess; }
+cudaError_t cudaEventCreate(cudaEvent_t *e) { g_nsetup++; *e = (cudaEvent_t)new_handle(); return cudaSuccess; }
+cudaError_t cudaEventCreateWithFlags(cudaEvent_t *e, unsigned f) { (void)f; g_nsetup++; *e = (cudaEvent_t)new_handle(); return cudaSuccess; }
 cudaError_t cudaEventRecord(cudaEvent_t e, cudaStream_t s) { (void)e; (void)s; return cudaSuccess; }
-cudaError_t cudaEventSynchronize(cudaEvent_t e) { (void)e; return cudaSuccess; }
+cudaError_t cudaEventSynchronize(cudaEvent_t e) { (void)e; g_nsync++; return cudaSuccess; }
 cudaError_t cudaEventElapsedTime(float *ms, cudaEvent_t a, cudaEvent_t b) { (void)a; (void)b; *ms = 1.0f; return cudaSuccess; }
 cudaError_t cudaEventDestroy(cudaEvent_t e) { (void)e; return cudaSuccess; }
 
@@ -231,6 +236,7 @@ static CUresult encode_tiled(CUtensorMap *map, CUtensorMapDataType dtype, cuuint
 cudaError_t cudaGetDriverEntryPointByVersion(const char *symbol, void **fn, unsigned int ver, unsigned long long flags,
                                              enum cudaDriverEntryPointQueryResult *status) {
     (void)ver; (void)flags;
+    g_nsetup++;
     if (strcmp(symbol, "cuTensorMapEncodeTiled") == 0) {
         *fn = (void *)encode_tiled;
         if (status) *status = cudaDriverEntryPointSuccess;
@@ -252,7 +258,9 @@ int shim_var(int i, void **p, size_t *size) {
 int shim_launch_count(void) { return g_nlaunch; }
 int shim_tmap_count(void) { return g_ntmap; }
 int shim_copy_count(void) { return g_ncopies; }
-void shim_reset(void) { g_nlaunch = 0; g_ntmap = 0; g_fail_launch = 0; g_ncopies = 0; }
+int shim_sync_count(void) { return g_nsync; }
+int shim_setup_count(void) { return g_nsetup; }
+void shim_reset(void) { g_nlaunch = 0; g_ntmap = 0; g_fail_launch = 0; g_ncopies = 0; g_nsync = 0; g_nsetup = 0; }
 
 const char *shim_launch(int i, unsigned *grid, unsigned *block, unsigned *cluster, size_t *smem) {
     const Launch *l = &g_launch[i];

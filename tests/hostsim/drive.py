@@ -26,8 +26,35 @@ class jk_tune_config(ct.Structure):
     _fields_ = [("aux_chunk", ct.c_int32), ("schedule", ct.c_int32), ("raster", ct.c_int32), ("cluster", ct.c_int32)]
 
 
-lib = ct.CDLL(os.path.join(ROOT, "paper_2608_06536_b300", "libjk.so"))
-lib.jk_last_error.restype = ct.c_char_p
+_lib = ct.CDLL(os.path.join(ROOT, "paper_2608_06536_b300", "libjk.so"))
+_lib.jk_last_error.restype = ct.c_char_p
+ENTRIES = {"jk_build", "jk_build_batched", "jk_build_host", "jk_adjoint", "jk_build_dense", "jk_density_grad",
+           "jk_pair", "jk_build_laplace", "jk_build_noalloc", "jk_autotune"}
+TWICE = [False]       # call each entry point twice on its handle and record only the second call
+
+
+class _Lib:
+    """The library; with TWICE set, an entry point runs once untraced (the
+    eager call that does any one-time set-up) and then once traced."""
+
+    def __getattr__(self, name):
+        fn = getattr(_lib, name)
+        if name not in ENTRIES:
+            return fn
+
+        def call(*args):
+            if TWICE[0]:
+                st = fn(*args)
+                if st != 0:
+                    return st
+                shim.shim_reset()
+                violations.clear()
+                decoded[0] = 0
+            return fn(*args)
+        return call
+
+
+lib = _Lib()
 shim = ct.CDLL("libcudart.so.13")
 shim.shim_launch.restype = ct.c_char_p
 assert hasattr(shim, "shim_reset"), "the stand-in runtime is not the one loaded"
@@ -439,7 +466,8 @@ def record(name, status, h):
                       "strides": list(strides)[:r], "box": list(box)[:r]})
     err = lib.jk_last_error(h).decode() if h else ""
     print(json.dumps({"case": name, "status": status, "error": err, "launches": launches, "tmaps": tmaps,
-                      "copies": shim.shim_copy_count(),
+                      "copies": shim.shim_copy_count(), "syncs": shim.shim_sync_count(),
+                      "setups": shim.shim_setup_count(),
                       "owned": [[o[0], o[1], o[2]] for o in owned + statics()], "violations": list(violations),
                       "decoded": decoded[0], "undecoded": sorted(undecoded)}), flush=True)
 
@@ -660,6 +688,9 @@ if __name__ == "__main__":
     for a in [a for a in args if a.startswith("--arena-scale=")]:
         ARENA_SCALE[0] = float(a.split("=", 1)[1])
         args.remove(a)
+    if "--twice" in args:
+        TWICE[0] = True
+        args.remove("--twice")
     names = args or list(CASES)
     for name in names:
         BIG[0] = name in FULL_CASES

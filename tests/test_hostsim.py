@@ -19,7 +19,8 @@ pairings, Laplace builds, the arena-free build, the autotuner) this checks:
   (tests/hostsim/drive.py), are self-consistent with its grid, and every
   byte range its pointer arguments can touch (from the kernel's own index
   bounds) lies in memory the call owns.  Every launch must be decoded;
-- with too small an arena a call fails before enqueueing any device work.
+- with too small an arena a call fails before enqueueing any device work;
+- a repeated call does no set-up and no synchronization (graph capture).
 Values are not checked here: the kernels do not run.
 """
 import json
@@ -172,3 +173,31 @@ def test_too_small_arena_fails_before_any_device_work(shim_dir):
             continue
         assert rec["status"] == 3 and "arena" in rec["error"], (name, rec["status"], rec["error"])
         assert not rec["launches"] and rec["copies"] == 0, (name, len(rec["launches"]), rec["copies"])
+
+
+def test_repeat_calls_are_capturable(shim_dir):
+    """After one eager call on a handle, a second identical call creates no
+    stream or event, sets no function attribute, looks nothing up and waits
+    for nothing: the prerequisites for recording it in a CUDA graph.  (The
+    autotuner times candidates and synchronizes by design.)"""
+    recs = _drive(shim_dir, ["--twice"])
+    assert sorted(recs) == sorted(NAMES)
+    for name, rec in recs.items():
+        assert rec["status"] == 0, (name, rec["error"])
+        if name == "autotune_split":
+            continue
+        assert rec["syncs"] == 0 and rec["setups"] == 0, (name, rec["syncs"], rec["setups"])
+        assert not rec["violations"], (name, rec["violations"][:3])
+
+
+def test_library_imports_no_allocator():
+    """libjk.so never allocates device or pinned memory: the CUDA runtime's
+    allocation routines are not among its imports."""
+    from paper_2608_06536_b300 import jk
+    out = subprocess.run(["nm", "-D", "--undefined-only", jk.LIB_PATH], capture_output=True, text=True,
+                         check=True).stdout
+    imported = {line.split()[-1].split("@")[0] for line in out.splitlines() if line.strip()}
+    assert "cudaGetDevice" in imported
+    banned = {s for s in imported if s.startswith("cuda") and ("Malloc" in s or "Free" in s or "HostAlloc" in s
+                                                                or "HostRegister" in s)}
+    assert not banned, banned
