@@ -237,6 +237,7 @@ def run_ours(args, rank, world, local):
     Xd = [torch.from_numpy(x).to(dev) for x in m.X]
     Yd = [torch.from_numpy(y).to(dev) for y in m.Y]
     eng = jk.Engine(dev)
+    eng.set_option("slicer", args.slicer)
     prec = args.precision
     st = torch.cuda.current_stream(dev)
 
@@ -287,7 +288,7 @@ def run_ours(args, rank, world, local):
         if rank == 0:
             print(json.dumps({"case": args.case, "engine": prec, "ms_per_step": ms_max, "value": value,
                               "kernels_ms": {k: v[0] / args.steps for k, v in prof.items()},
-                              "launches_per_step": launches / args.steps, "tuned": tuned,
+                              "launches_per_step": launches / args.steps, "tuned": tuned, "slicer": args.slicer,
                               "issued_tensor_tflops": issued / args.steps / (ms_max * 1e-3) / 1e12}),
                   flush=True)
         return
@@ -362,7 +363,7 @@ def run_ours(args, rank, world, local):
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "engine": prec, "nbf": n, "naux": naux, "nd": len(ks),
                    "k": ks[0], "l2": "inputs larger than L2 (L = 3.07 GB FP64), no flush",
-                   "parallelism": f"replicas x{world}", "tuned": tuned},
+                   "parallelism": f"replicas x{world}", "tuned": tuned, "slicer": args.slicer},
         "e2e": e2e,
         "gpu_launches": int(launches),
         "launches_per_step": launches / args.steps,
@@ -538,6 +539,8 @@ def main():
                     help="skip the autotuner (default configuration)")
     ap.add_argument("--config", default="",
                     help="fixed run-time configuration aux_chunk,schedule,raster,cluster (skips the autotuner)")
+    ap.add_argument("--slicer", type=int, choices=[0, 1], default=0,
+                    help="digit extraction of the vector slicer: 0 integer (default), 1 FP32 additions")
     ap.add_argument("--quick", action="store_true",
                     help="device-resident timing only (no e2e, no CPU baseline)")
     args = ap.parse_args()

@@ -282,8 +282,13 @@ typedef enum {
                                0 = ignore them                                    */
     JK_OPT_CLUSTER = 4,     /* -1 = tuned/default, 0 = one CTA per tile, 1 = 2-CTA
                                clusters sharing an operand tile by TMA multicast  */
-    JK_OPT_HOST_CHUNK = 5   /* jk_build_host: aux indices per streamed chunk of
+    JK_OPT_HOST_CHUNK = 5,  /* jk_build_host: aux indices per streamed chunk of
                                the factor, 0 = automatic (about 12 chunks)         */
+    JK_OPT_SLICER = 6       /* digit extraction of the split engine's vector
+                               slicer: 0 (default) integer arithmetic, 1 FP32
+                               additions (fewer instructions per element; an
+                               equally exact split, digits differ only where a
+                               digit rounds a tie)                               */
 } jk_option;
 /* Options set explicitly on a handle override tuned configurations. */
 jk_status jk_set_option(jk_handle h, jk_option opt, int64_t value);

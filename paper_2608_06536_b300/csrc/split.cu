@@ -39,6 +39,7 @@
 #include <type_traits>
 #include <vector>
 
+#include "digits.cuh"
 #include "jk_internal.h"
 #include "tc.cuh"
 
@@ -244,6 +245,50 @@ __global__ void __launch_bounds__(256) slice4_kernel(Src src, int rows, int K, i
                 w.y = qbf16(q[2][j], sc) | (qbf16(q[3][j], sc) << 16);
                 out[j * sstride4 + o] = w;
                 sc *= 0.00390625f;
+            }
+        }
+    }
+}
+
+// Vector slicer with the digits formed by FP32 additions (digits.cuh): the
+// same layout and requirements as slice4_kernel; the slices are an equally
+// exact split of the same 48-bit values (digits may differ from the integer
+// path only where a digit rounds a tie, to even here).  The BF16 words are
+// the upper halves of the FP32 digits, paired with one byte permute.
+__global__ void __launch_bounds__(256) slice4f_kernel(Src src, int rows, int K, int Kpad, const int *e, int rpe,
+                                                      int nsc, uint2 *out, long long sstride4) {
+    const int kk = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
+    if (kk >= Kpad) return;
+    long long koff = 0;
+    if (kk < K) {
+        const int ko = kk / src.kin, ki = kk - ko * src.kin;
+        koff = static_cast<long long>(ko) * src.sko + ki;
+    }
+    for (int rb = blockIdx.y * 8; rb < rows; rb += gridDim.y * 8) {
+        const int rend = min(rows, rb + 8);
+        for (int r = rb; r < rend; r++) {
+            float v[4][S];
+            if (kk < K) {
+                const double2 *p2 = reinterpret_cast<const double2 *>(src_row(src, r) + koff);
+                const double2 a = p2[0], b = p2[1];
+                const int er = e[(r / rpe) * nsc + kk / SUPER];
+                digits::split48(to_fixed48(a.x, er), v[0]);
+                digits::split48(to_fixed48(a.y, er), v[1]);
+                digits::split48(to_fixed48(b.x, er), v[2]);
+                digits::split48(to_fixed48(b.y, er), v[3]);
+            } else {
+#pragma unroll
+                for (int i = 0; i < 4; i++)
+#pragma unroll
+                    for (int j = 0; j < S; j++) v[i][j] = 0.0f;
+            }
+            const long long o = (static_cast<long long>(r) * Kpad + kk) >> 2;
+#pragma unroll
+            for (int j = 0; j < S; j++) {
+                uint2 w;
+                w.x = __byte_perm(__float_as_uint(v[0][j]), __float_as_uint(v[1][j]), 0x7632);
+                w.y = __byte_perm(__float_as_uint(v[2][j]), __float_as_uint(v[3][j]), 0x7632);
+                out[j * sstride4 + o] = w;
             }
         }
     }
@@ -934,9 +979,14 @@ static jk_status slice_operand(jk_ctx *h, const oz::Src &src, int rows, int K, i
         LaunchScope ls(h, KK_SLICE, st);
         if (vec) {
             dim3 grid((out.Kpad / 4 + 255) / 256, rblocks < 65535 ? rblocks : 65535);
-            oz::slice4_kernel<<<grid, 256, 0, st>>>(src, rows, K, out.Kpad, out.e, rpe, nsc,
-                                                     reinterpret_cast<uint2 *>(out.s),
-                                                     static_cast<long long>(rows) * out.Kpad / 4);
+            if (h->slicer == 1)
+                oz::slice4f_kernel<<<grid, 256, 0, st>>>(src, rows, K, out.Kpad, out.e, rpe, nsc,
+                                                          reinterpret_cast<uint2 *>(out.s),
+                                                          static_cast<long long>(rows) * out.Kpad / 4);
+            else
+                oz::slice4_kernel<<<grid, 256, 0, st>>>(src, rows, K, out.Kpad, out.e, rpe, nsc,
+                                                         reinterpret_cast<uint2 *>(out.s),
+                                                         static_cast<long long>(rows) * out.Kpad / 4);
         } else {
             dim3 grid((out.Kpad + 255) / 256, rblocks < 65535 ? rblocks : 65535);
             oz::slice_kernel<<<grid, 256, 0, st>>>(src, rows, K, out.Kpad, out.e, rpe, nsc,

@@ -42,7 +42,10 @@ class jk_tune_config(ct.Structure):
                 "cluster": self.cluster}
 
 
-OPTIONS = {"aux_chunk": 0, "schedule": 1, "raster": 2, "use_tuned": 3, "cluster": 4, "host_chunk": 5}
+OPTIONS = {"aux_chunk": 0, "schedule": 1, "raster": 2, "use_tuned": 3, "cluster": 4, "host_chunk": 5, "slicer": 6}
+# each option's value on a fresh handle (-1: not set, tuned or default configuration)
+OPTION_DEFAULTS = {"aux_chunk": -1, "schedule": -1, "raster": -1, "use_tuned": 1, "cluster": -1, "host_chunk": 0,
+                   "slicer": 0}
 
 
 class JKError(RuntimeError):
@@ -318,8 +321,9 @@ class Engine:
     # -- options ---------------------------------------------------------------
     def set_option(self, name: str, value: int):
         """Handle option (JK_OPT_*): "aux_chunk" (>= 0, 0 = automatic, -1 =
-        tuned/default), "schedule" and "raster" (-1 = tuned/default, 0, 1),
-        "use_tuned" (0 or 1).  Kept across arena growth."""
+        tuned/default), "schedule", "raster" and "cluster" (-1 = tuned/default,
+        0, 1), "use_tuned" (0 or 1), "host_chunk" (>= 0, 0 = automatic),
+        "slicer" (0 integer digits, 1 FP32 digits).  Kept across arena growth."""
         code = OPTIONS[name]
         self._opts[code] = int(value)
         if self._h:
@@ -590,8 +594,9 @@ class Engine:
         finally:
             self._opts = saved
             if self._h:
-                for code in range(len(OPTIONS)):
-                    self.lib.jk_set_option(self._h, code, saved.get(code, 1 if code == 3 else 0 if code == 5 else -1))
+                for name, code in OPTIONS.items():
+                    self._check(self.lib.jk_set_option(self._h, code, saved.get(code, OPTION_DEFAULTS[name])),
+                                self._h)
         return int(need * 2)
 
     def _marshal_batched(self, mols):

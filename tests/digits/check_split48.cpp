@@ -1,0 +1,72 @@
+// TEST INFRASTRUCTURE: checks jk::digits::split48 (csrc/digits.cuh, compiled
+// here as host C++) against the properties the slicer relies on, for random
+// and edge-case fixed-point values F, |F| <= 2^48:
+//   sum_j v_j * 2^48 == F exactly; |q_0| <= 256, |q_j| <= 128 (j >= 1) with
+//   q_j = v_j * 2^(8(j+1)) an integer; every v_j an exact BF16 value (the low
+//   16 bits of its FP32 word are zero).
+// Prints "ok <count>" and exits 0, or the first violation and exits 1.
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <random>
+
+#include "../../paper_2608_06536_b300/csrc/digits.cuh"
+
+static int check(long long F) {
+    float v[6];
+    jk::digits::split48(F, v);
+    __int128 sum = 0;
+    for (int j = 0; j < 6; j++) {
+        uint32_t bits;
+        std::memcpy(&bits, &v[j], 4);
+        if (bits & 0xFFFFu) {
+            std::printf("F=%lld: slice %d (%a) is not an exact BF16 value\n", F, j, v[j]);
+            return 1;
+        }
+        const double q = std::ldexp(static_cast<double>(v[j]), 8 * (j + 1));
+        if (q != std::floor(q) || std::fabs(q) > (j == 0 ? 256.0 : 128.0)) {
+            std::printf("F=%lld: digit %d = %.17g out of range\n", F, j, q);
+            return 1;
+        }
+        sum += static_cast<__int128>(static_cast<long long>(q)) << (8 * (5 - j));
+    }
+    if (sum != static_cast<__int128>(F)) {
+        std::printf("F=%lld: digits sum to %lld\n", F, static_cast<long long>(sum));
+        return 1;
+    }
+    return 0;
+}
+
+int main() {
+    const long long T = 1ll << 48;
+    long long n = 0;
+    // edge cases: the ends of the range, carries out of the low half, ties
+    const long long edges[] = {0, 1, -1, 127, 128, 129, -128, -129, 255, 256, 0x8080, 0x808080, 0xFFFFFF,
+                               0x1000000, 0x1000080, 0x17FFFFF, T, -T, T - 1, -T + 1, T - 0x800000,
+                               (T >> 1) + 0x808080, 0x800000, -0x800000, 0x7F7F7F7F7F7Fll, -0x7F7F7F7F7F7Fll,
+                               0x808080808080ll, -0x808080808080ll};
+    for (long long F : edges) {
+        if (check(F)) return 1;
+        n++;
+    }
+    // every pattern of the top and bottom digit around the half-way points
+    for (long long hi = -256; hi <= 256; hi++)
+        for (long long lo : {0ll, 0x7Fll, 0x80ll, 0x81ll, 0x7FFFFFll, 0x800000ll, 0x808080ll, 0xFFFFFFll}) {
+            const long long F = hi * (1ll << 40) + lo;
+            if (F > T || F < -T) continue;
+            if (check(F)) return 1;
+            n++;
+        }
+    // random values, uniform and with many tie digits
+    std::mt19937_64 rng(12345);
+    for (int i = 0; i < 4000000; i++) {
+        long long F = static_cast<long long>(rng() % (2 * T + 1)) - T;
+        if (i & 1) F = (F & ~0xFFll) | 0x80;                     // a tie in the lowest digit
+        if ((i & 7) == 2) F = static_cast<long long>(rng() % 4096) - 2048;   // small magnitudes
+        if (check(F)) return 1;
+        n++;
+    }
+    std::printf("ok %lld\n", n);
+    return 0;
+}

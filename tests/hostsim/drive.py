@@ -59,7 +59,7 @@ shim = ct.CDLL("libcudart.so.13")
 shim.shim_launch.restype = ct.c_char_p
 assert hasattr(shim, "shim_reset"), "the stand-in runtime is not the one loaded"
 
-OPT = {"aux_chunk": 0, "schedule": 1, "raster": 2, "use_tuned": 3, "cluster": 4, "host_chunk": 5}
+OPT = {"aux_chunk": 0, "schedule": 1, "raster": 2, "use_tuned": 3, "cluster": 4, "host_chunk": 5, "slicer": 6}
 
 # ---- kernel arguments ----------------------------------------------------------
 # Each decoder reads one kernel's arguments (layouts as in the CUDA sources)
@@ -343,6 +343,7 @@ DECODERS = [
     ("sum_parts_kernel", dec_sum_parts), ("reduce_partials_kernel", dec_reduce), ("pair_dot_kernel", dec_pair_dot),
     ("laplace_scale_kernel", dec_laplace_scale), ("weighted_sum_kernel", dec_weighted_sum),
     ("ozgemm_kernel", dec_ozgemm), ("jstream_sym_kernel", dec_jstream_sym), ("gterms_kernel", dec_gterms),
+    ("slice4f_kernel", dec_slice4),
     ("symmetrize_kernel", dec_symmetrize), ("sym_dl_kernel", dec_sym_dl), ("fold_sym_split_kernel", dec_fold),
     ("fold_sym_kernel", dec_fold), ("pack_ag_kernel", dec_pack_ag), ("pack_bg_kernel", dec_pack_bg),
 ]
@@ -641,6 +642,7 @@ CASES = {
     "build_split_clustered_chunks": build_case(130, 70, [64, 3, 9], [False, False, True], SPLIT,
                                                {"schedule": 0, "cluster": 1, "aux_chunk": 30}),
     "build_split_nbf_above_superchunk": build_case(2100, 3, [2], [False], SPLIT, {}),
+    "build_split_fp32_digits": build_case(400, 60, [40, 40], [True, False], SPLIT, {"slicer": 1, "schedule": 1}),
     "batched_split": batched_case([(60, 150, [6, 6]), (111, 222, [11]), (33, 99, [3, 3, 3])], SPLIT, {}),
     "batched_fp64": batched_case([(60, 150, [6, 6]), (33, 99, [3])], FP64, {}),
     "host_split": host_case(64, 200, [8, 5], SPLIT, {"host_chunk": 37}),

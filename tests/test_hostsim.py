@@ -145,6 +145,7 @@ def _kernels(rec):
     ("laplace_split", ["laplace_scale_kernel", "ozgemm_kernel"]),
     ("laplace_fp64_weighted", ["laplace_scale_kernel", "weighted_sum_kernel"]),
     ("build_split_grouped_clustered", ["ozgemm_kernelILb1E"]),
+    ("build_split_fp32_digits", ["slice4f_kernel"]),
 ])
 def test_expected_kernels(records, name, must):
     names = _kernels(records[name])
