@@ -202,3 +202,15 @@ def test_library_imports_no_allocator():
     banned = {s for s in imported if s.startswith("cuda") and ("Malloc" in s or "Free" in s or "HostAlloc" in s
                                                                 or "HostRegister" in s)}
     assert not banned, banned
+
+
+def test_random_cases(shim_dir):
+    """Random entry points, shapes (tile and K-step edges, odd sizes) and
+    options, under every per-call check above."""
+    recs = _drive(shim_dir, ["--fuzz=200,7"])
+    assert len(recs) == 200
+    for name, rec in recs.items():
+        try:
+            _check(rec)
+        except AssertionError as e:
+            raise AssertionError(f"{name}: {e}") from None
