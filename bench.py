@@ -294,7 +294,9 @@ def run_ours(args, rank, world, local):
         return
 
     # ---- end to end through the public API, host buffers ---------------------
-    Lh = torch.from_numpy(m.L).pin_memory()
+    # --e2e-packed: the factor kept on the host as packed upper triangles (its
+    # layout as a symmetric matrix), half the bytes over the host link
+    Lh = (jk.pack_factor(m.L) if args.e2e_packed else torch.from_numpy(m.L)).pin_memory()
     Xh = [torch.from_numpy(x).pin_memory() for x in m.X]
     Yh = [torch.from_numpy(y).pin_memory() for y in m.Y]
     Jh = torch.empty((len(ks), n, n), dtype=torch.float64).pin_memory()
@@ -306,18 +308,19 @@ def run_ours(args, rank, world, local):
     # on its own copy stream, overlapped with the build of the previous chunk;
     # densities up and J, K down on the caller's stream.  One untimed call sizes
     # the arena.
-    eng.build_host(Lh, Xh, Yh, sym, prec, J=Jh, K=Kh, stream=st)
+    eng.build_host(Lh, Xh, Yh, sym, prec, J=Jh, K=Kh, stream=st, packed=args.e2e_packed)
     barrier(world)
     torch.cuda.synchronize(dev)
     e0.record(st)
     for _ in range(e2e_steps):
-        eng.build_host(Lh, Xh, Yh, sym, prec, J=Jh, K=Kh, stream=st, sync=False)
+        eng.build_host(Lh, Xh, Yh, sym, prec, J=Jh, K=Kh, stream=st, sync=False, packed=args.e2e_packed)
     e1.record(st)
     torch.cuda.synchronize(dev)
     eng.sync_status(st)
     ms_e2e = max_over_ranks(e0.elapsed_time(e1) / e2e_steps, world, dev)
     e2e = {"value": job_tflops(flops, ms_e2e, world), "unit": "TFLOP/s",
            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "ms_per_step": ms_e2e,
+           "packed_factor": bool(args.e2e_packed),
            "path": "jk_build_host: pinned host inputs and outputs, factor streamed in aux chunks "
                    "overlapped with the build"}
 
@@ -541,6 +544,9 @@ def main():
                     help="fixed run-time configuration aux_chunk,schedule,raster,cluster (skips the autotuner)")
     ap.add_argument("--slicer", type=int, choices=[0, 1], default=0,
                     help="digit extraction of the vector slicer: 0 integer (default), 1 FP32 additions")
+    ap.add_argument("--e2e-packed", dest="e2e_packed", action="store_true",
+                    help="end-to-end leg with the factor on the host as packed upper triangles "
+                         "(jk_build_host_packed: half the bytes over the host link)")
     ap.add_argument("--quick", action="store_true",
                     help="device-resident timing only (no e2e, no CPU baseline)")
     args = ap.parse_args()

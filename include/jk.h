@@ -88,7 +88,8 @@ typedef struct {
 /* Which entry point a workspace query is for. */
 typedef enum {
     JK_OP_BUILD = 0, JK_OP_ADJOINT = 1, JK_OP_BATCHED = 2, JK_OP_BUILD_HOST = 3,
-    JK_OP_BUILD_DENSE = 4, JK_OP_DENSITY_GRAD = 5, JK_OP_PAIR = 6, JK_OP_LAPLACE = 7
+    JK_OP_BUILD_DENSE = 4, JK_OP_DENSITY_GRAD = 5, JK_OP_PAIR = 6, JK_OP_LAPLACE = 7,
+    JK_OP_BUILD_HOST_PACKED = 8
 } jk_op;
 
 /* Create a handle over a caller-owned device arena of `bytes` bytes
@@ -136,6 +137,16 @@ jk_status jk_build(jk_handle h, const jk_factor *f, int32_t nd,
  * JK_OP_BUILD_HOST.  Status as jk_build; host pointers are not checked. */
 jk_status jk_build_host(jk_handle h, const jk_factor *f, int32_t nd, const jk_density *d,
                         double *J, double *K, jk_precision p, void *stream);
+
+/* jk_build_host_packed: jk_build_host with the factor given as the packed upper
+ * triangle of each (symmetric) L^P: f->L is a host array [naux][nbf(nbf+1)/2],
+ * L^P_{mu nu} (mu <= nu) at index mu*nbf - mu(mu-1)/2 + (nu - mu) of block P
+ * (row-major upper triangle, diagonal included).  Half the factor's bytes cross
+ * the host link; each uploaded chunk is expanded to full L^P on the device
+ * before its build, so results equal jk_build_host's on the same L bit for bit.
+ * Arena: jk_workspace_query with JK_OP_BUILD_HOST_PACKED.  Status as jk_build_host. */
+jk_status jk_build_host_packed(jk_handle h, const jk_factor *f, int32_t nd, const jk_density *d,
+                               double *J, double *K, jk_precision p, void *stream);
 
 /* jk_build_batched: many independent molecules (uneven nbf, naux, nd) in one
  * call.  f[m] is molecule m's factor, nd_per_mol[m] its density count (host

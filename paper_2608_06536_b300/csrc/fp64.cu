@@ -343,7 +343,30 @@ static jk_status pack_z(jk_ctx *h, const Problem &pb, double *Z, cudaStream_t st
     return JK_OK;
 }
 
-// y += x (FP64, elementwise)
+// F[p][mu][nu] = P[p][t(min(mu,nu), max(mu,nu))] for p < np: symmetric L^P
+// expanded from its packed upper triangle, t(a, b) = a*n - a(a-1)/2 + (b - a)
+// (row-major upper triangle, diagonal included).  One thread per full entry.
+__global__ void unpack_sym_kernel(const double *P, int n, long long np, double *F) {
+    const long long n2 = (long long)n * n;
+    const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (e >= np * n2) return;
+    const long long p = e / n2, r = e - p * n2;
+    const int mu = (int)(r / n), nu = (int)(r - (long long)mu * n);
+    const long long a = mu < nu ? mu : nu, b = mu < nu ? nu : mu;
+    F[e] = P[p * (n2 + n) / 2 + a * n - a * (a - 1) / 2 + (b - a)];
+}
+
+jk_status fp64_unpack_sym(jk_ctx *h, const double *packed, int n, long long np, double *full, cudaStream_t st) {
+    const long long tot = np * n * n;
+    {
+        LaunchScope ls(h, KK_PACK, st);
+        unpack_sym_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(packed, n, np, full);
+    }
+    JK_LAUNCH_CHECK(h);
+    return JK_OK;
+}
+
+// y += x (FP64, elementwise)// y += x (FP64, elementwise)
 __global__ void axpy_kernel(double *y, const double *x, long long cnt) {
     long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (e < cnt) y[e] += x[e];

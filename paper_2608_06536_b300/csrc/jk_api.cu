@@ -190,7 +190,11 @@ struct HostBufs {
     double *XY = nullptr;          // X_s (and Y_s) packed density by density
     double *J = nullptr, *K = nullptr, *Jc = nullptr, *Kc = nullptr;
     double *stage[2] = {nullptr, nullptr};
+    double *pstage[2] = {nullptr, nullptr};   // packed factor chunks as uploaded (packed builds)
 };
+
+// Doubles of one packed L^P (upper triangle, diagonal included).
+static long long tri_count(int n) { return static_cast<long long>(n) * (n + 1) / 2; }
 
 static size_t host_xy_count(const Problem &pb) {
     size_t c = 0;
@@ -198,10 +202,11 @@ static size_t host_xy_count(const Problem &pb) {
     return c;
 }
 
-static size_t host_persist_bytes(const Problem &pb, int chunk, bool wantJ, bool wantK) {
+static size_t host_persist_bytes(const Problem &pb, int chunk, bool wantJ, bool wantK, bool packed = false) {
     const size_t nn = static_cast<size_t>(pb.nd) * pb.n * pb.n * 8;
     return align_up(host_xy_count(pb) * 8) + (wantJ ? 2 * align_up(nn) : 0) + (wantK ? 2 * align_up(nn) : 0) +
-           2 * align_up(static_cast<size_t>(chunk) * pb.n * pb.n * 8) + 8 * kArenaAlign;
+           2 * align_up(static_cast<size_t>(chunk) * pb.n * pb.n * 8) +
+           (packed ? 2 * align_up(static_cast<size_t>(chunk) * tri_count(pb.n) * 8) : 0) + 8 * kArenaAlign;
 }
 
 // The per-chunk problem: device copies of the densities, a staging factor.
@@ -242,14 +247,14 @@ static jk_tune_config host_config(const jk_ctx *h, jk_precision p, const Problem
     return c;
 }
 
-static size_t host_build_bytes(const jk_ctx *h, const Problem &pb, jk_precision p) {
+static size_t host_build_bytes(const jk_ctx *h, const Problem &pb, jk_precision p, bool packed = false) {
     const int chunk = host_chunk_of(h, pb);
     Problem q = pb;
     q.naux = chunk;
     jk_tune_config c{0, 1, 0, kDefaultCluster};
     if (h) c = host_config(h, p, q);
     apply_config(q, c);
-    return host_persist_bytes(pb, chunk, true, true) + build_bytes(q, p);
+    return host_persist_bytes(pb, chunk, true, true, packed) + build_bytes(q, p);
 }
 
 static jk_status ensure_copy_stream(jk_ctx *h) {
@@ -263,8 +268,10 @@ static jk_status ensure_copy_stream(jk_ctx *h) {
     return JK_OK;
 }
 
+// With `packed`, pb.L holds each L^P as its packed upper triangle: half the
+// bytes are uploaded, and each chunk is expanded on the device before its build.
 static jk_status host_build(jk_ctx *h, const Problem &pb, const jk_density *d, double *J, double *K,
-                            jk_precision p, cudaStream_t st) {
+                            jk_precision p, cudaStream_t st, bool packed = false) {
     const int n = pb.n, naux = pb.naux, nd = pb.nd;
     const long long n2 = static_cast<long long>(n) * n;
     const size_t nn = static_cast<size_t>(nd) * n2;
@@ -286,6 +293,10 @@ static jk_status host_build(jk_ctx *h, const Problem &pb, const jk_density *d, d
     for (int i = 0; i < 2; i++) {
         b.stage[i] = ar.take<double>(static_cast<size_t>(chunk) * n2);
         ok = ok && b.stage[i];
+        if (packed) {
+            b.pstage[i] = ar.take<double>(static_cast<size_t>(chunk) * tri_count(n));
+            ok = ok && b.pstage[i];
+        }
     }
     if (!ok) return set_error(h, JK_ERR_OOM, "arena too small for the host build's staging buffers");
     Problem q = host_chunk_problem(pb, b, chunk, 0);
@@ -325,11 +336,13 @@ static jk_status host_build(jk_ctx *h, const Problem &pb, const jk_density *d, d
         const int buf = c & 1;
         // ... uploads chunk c once the build of chunk c - 2 has released its buffer ...
         if (c >= 2) JK_CUDA_TRY(h, cudaStreamWaitEvent(h->copy_stream, h->ev_used[buf], 0));
-        JK_CUDA_TRY(h, cudaMemcpyAsync(b.stage[buf], pb.L + P0 * n2, static_cast<size_t>(np) * n2 * 8,
-                                       cudaMemcpyHostToDevice, h->copy_stream));
+        const long long per = packed ? tri_count(n) : n2;
+        JK_CUDA_TRY(h, cudaMemcpyAsync(packed ? b.pstage[buf] : b.stage[buf], pb.L + P0 * per,
+                                       static_cast<size_t>(np) * per * 8, cudaMemcpyHostToDevice, h->copy_stream));
         JK_CUDA_TRY(h, cudaEventRecord(h->ev_up[buf], h->copy_stream));
         // ... and every chunk's build waits for its upload (which also joins the streams)
         JK_CUDA_TRY(h, cudaStreamWaitEvent(st, h->ev_up[buf], 0));
+        if (packed) JK_TRY(fp64_unpack_sym(h, b.pstage[buf], n, np, b.stage[buf], st));
         Problem qc = host_chunk_problem(pb, b, np, buf);
         apply_config(qc, cfg);
         JK_TRY(run_build(h, qc, p, st));
@@ -663,13 +676,13 @@ static jk_status query_impl(const jk_ctx *h, jk_op op, int32_t nmol, const jk_fa
     std::vector<Problem> pbs;
     if (op == JK_OP_BATCHED) {
         JK_TRY(host_batched_problems(nmol, f, nd_per_mol, nd, d, pbs));
-    } else if (op == JK_OP_BUILD || op == JK_OP_ADJOINT || op == JK_OP_BUILD_HOST) {
+    } else if (op == JK_OP_BUILD || op == JK_OP_ADJOINT || op == JK_OP_BUILD_HOST || op == JK_OP_BUILD_HOST_PACKED) {
         pbs.resize(1);
         jk_status s = make_problem(nullptr, f, nd, d, false, pbs[0]);
         if (s != JK_OK) return s;
         nmol = 1;
-        if (op == JK_OP_BUILD_HOST) {
-            *bytes = host_build_bytes(h, pbs[0], p) + flags_bytes() + kArenaAlign;
+        if (op == JK_OP_BUILD_HOST || op == JK_OP_BUILD_HOST_PACKED) {
+            *bytes = host_build_bytes(h, pbs[0], p, op == JK_OP_BUILD_HOST_PACKED) + flags_bytes() + kArenaAlign;
             return JK_OK;
         }
     } else {
@@ -724,8 +737,8 @@ jk_status jk_build(jk_handle h, const jk_factor *f, int32_t nd, const jk_density
     return run_build(h, pb, p, st);
 }
 
-jk_status jk_build_host(jk_handle h, const jk_factor *f, int32_t nd, const jk_density *d,
-                        double *J, double *K, jk_precision p, void *stream) {
+static jk_status build_host_impl(jk_handle h, const jk_factor *f, int32_t nd, const jk_density *d, double *J,
+                                 double *K, jk_precision p, void *stream, bool packed) {
     JK_TRY(begin_call(h));
     if (p != JK_FP64 && p != JK_SPLIT_BF16)
         return set_error(h, JK_ERR_ARG, "unknown precision %d", (int)p);
@@ -738,7 +751,17 @@ jk_status jk_build_host(jk_handle h, const jk_factor *f, int32_t nd, const jk_de
     if (!J && !K) return JK_OK;
     pb.wantJ = J != nullptr;
     pb.wantK = K != nullptr;
-    return host_build(h, pb, d, J, K, p, static_cast<cudaStream_t>(stream));
+    return host_build(h, pb, d, J, K, p, static_cast<cudaStream_t>(stream), packed);
+}
+
+jk_status jk_build_host(jk_handle h, const jk_factor *f, int32_t nd, const jk_density *d,
+                        double *J, double *K, jk_precision p, void *stream) {
+    return build_host_impl(h, f, nd, d, J, K, p, stream, false);
+}
+
+jk_status jk_build_host_packed(jk_handle h, const jk_factor *f, int32_t nd, const jk_density *d,
+                               double *J, double *K, jk_precision p, void *stream) {
+    return build_host_impl(h, f, nd, d, J, K, p, stream, true);
 }
 
 jk_status jk_build_batched(jk_handle h, int32_t nmol, const jk_factor *f,

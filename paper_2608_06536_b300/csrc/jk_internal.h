@@ -144,6 +144,9 @@ jk_status fp64_adjoint(jk_ctx *h, const Problem &pb, const double *W,
                        cudaStream_t st);
 
 jk_status fp64_axpy(jk_ctx *h, double *y, const double *x, long long cnt, cudaStream_t st);
+// full[p] = the symmetric n x n matrix whose packed upper triangle is
+// packed[p] ([np][n(n+1)/2], row-major, diagonal included).
+jk_status fp64_unpack_sym(jk_ctx *h, const double *packed, int n, long long np, double *full, cudaStream_t st);
 
 // ---- split-precision engine (split.cu) -----------------------------------
 size_t split_build_workspace(const Problem &pb);

@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(HERE, "libjk.so")
 JK_OK, JK_ERR_ARG, JK_ERR_SHAPE, JK_ERR_OOM, JK_ERR_CUDA, JK_ERR_TIMEOUT, JK_ERR_UNSUPPORTED = range(7)
 JK_FP64, JK_SPLIT_BF16 = 0, 1
 (JK_OP_BUILD, JK_OP_ADJOINT, JK_OP_BATCHED, JK_OP_BUILD_HOST, JK_OP_BUILD_DENSE, JK_OP_DENSITY_GRAD,
- JK_OP_PAIR, JK_OP_LAPLACE) = range(8)
+ JK_OP_PAIR, JK_OP_LAPLACE, JK_OP_BUILD_HOST_PACKED) = range(9)
 
 PRECISIONS = {"fp64": JK_FP64, "split": JK_SPLIT_BF16, "split_bf16": JK_SPLIT_BF16}
 
@@ -78,6 +78,8 @@ def load_library(path: str = LIB_PATH):
         L.jk_build_host.argtypes = [vp, ct.POINTER(jk_factor), ct.c_int32, ct.POINTER(jk_density),
                                     vp, vp, ct.c_int, vp]
         L.jk_build_host.restype = ct.c_int
+        L.jk_build_host_packed.argtypes = L.jk_build_host.argtypes
+        L.jk_build_host_packed.restype = ct.c_int
         L.jk_build_batched.argtypes = [vp, ct.c_int32, ct.POINTER(jk_factor),
                                        ct.POINTER(ct.c_int32), ct.POINTER(jk_density),
                                        ct.POINTER(vp), ct.POINTER(vp), ct.c_int, vp]
@@ -162,6 +164,13 @@ def _shape(t):
     return tuple(int(v) for v in t.shape)
 
 
+class _ShapeOnly:
+    """A stand-in carrying only a shape (for shape checks of packed factors)."""
+
+    def __init__(self, shape):
+        self.shape = tuple(shape)
+
+
 def _check_problem(L, X, Y=None, sym=None):
     """Shapes of one molecule, checked before any device work: the C ABI takes
     pointers and sizes only, so a mismatch here would become an out-of-bounds
@@ -223,6 +232,16 @@ def _check_output(t, name, shape, device):
             or not t.is_contiguous() or t.data_ptr() % 8):
         raise ValueError(f"{name} must be a contiguous float64 tensor of shape {tuple(shape)} on {device}, "
                          f"got {t.dtype} {_shape(t)} on {t.device}")
+
+
+def pack_factor(L):
+    """[naux][n(n+1)/2]: the packed upper triangle (row-major, diagonal
+    included) of each symmetric L^P of a [naux][n][n] CPU tensor or array, the
+    layout jk_build_host_packed uploads."""
+    L = torch.as_tensor(L, dtype=torch.float64)
+    n = int(L.shape[-1])
+    iu = torch.triu_indices(n, n)
+    return L[:, iu[0], iu[1]].contiguous()
 
 
 def _stream_ptr(stream):
@@ -399,13 +418,21 @@ class Engine:
         return (J if want_j else None), (K if want_k else None)
 
     def build_host(self, L, X, Y=None, sym=None, precision="split", want_j=True, want_k=True,
-                   J=None, K=None, stream=None, sync=True):
+                   J=None, K=None, stream=None, sync=True, packed=False):
         """J, K for host-resident inputs (CPU float64 tensors, ideally pinned):
         the factor streams to the device chunk by chunk, overlapped with the
         build; J, K ([nd][n][n], CPU) are written at the end of the stream's
-        work (sync=True waits for it)."""
+        work (sync=True waits for it).  With packed=True, L is given as
+        pack_factor(L) ([naux][n(n+1)/2]): half the bytes are uploaded."""
         p = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
-        n, _, nd = _check_problem(L, X, Y, sym)
+        if packed:
+            Ls = _shape(L)
+            n = _shape(X[0])[0] if len(X) else 0
+            if len(Ls) != 2 or Ls[1] != n * (n + 1) // 2 or Ls[0] < 1:
+                raise ValueError(f"packed L must be [naux][{n * (n + 1) // 2}] for nbf = {n}, got {Ls}")
+            n, _, nd = _check_problem(_ShapeOnly((Ls[0], n, n)), X, Y, sym)
+        else:
+            n, _, nd = _check_problem(L, X, Y, sym)
         if want_j:
             _check_output(J, "J", (nd, n, n), torch.device("cpu"))
         if want_k:
@@ -418,19 +445,21 @@ class Engine:
         symf = [sym[s] or Y[s] is None for s in range(nd)]
         naux = int(L.shape[0])
         f = jk_factor(n, naux, L.data_ptr())
+        op = JK_OP_BUILD_HOST_PACKED if packed else JK_OP_BUILD_HOST
+        call = self.lib.jk_build_host_packed if packed else self.lib.jk_build_host
         dens = (jk_density * nd)()
         for s in range(nd):
             dens[s].k = int(X[s].shape[1])
             dens[s].symmetric = 1 if symf[s] else 0
             dens[s].X = X[s].data_ptr()
             dens[s].Y = Y[s].data_ptr() if Y[s] is not None else None
-        self._ensure(self.query(JK_OP_BUILD_HOST, (jk_factor * 1)(f), dens, None, nd, p))
+        self._ensure(self.query(op, (jk_factor * 1)(f), dens, None, nd, p))
         if want_j and J is None:
             J = torch.empty((nd, n, n), dtype=torch.float64).pin_memory()
         if want_k and K is None:
             K = torch.empty((nd, n, n), dtype=torch.float64).pin_memory()
-        st = self.lib.jk_build_host(self._h, ct.byref(f), nd, dens, _ptr(J if want_j else None),
-                                    _ptr(K if want_k else None), p, _stream_ptr(stream))
+        st = call(self._h, ct.byref(f), nd, dens, _ptr(J if want_j else None), _ptr(K if want_k else None), p,
+                  _stream_ptr(stream))
         self._check(st, self._h)
         self._record(stream)
         if sync:

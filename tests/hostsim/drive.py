@@ -28,8 +28,8 @@ class jk_tune_config(ct.Structure):
 
 _lib = ct.CDLL(os.path.join(ROOT, "paper_2608_06536_b300", "libjk.so"))
 _lib.jk_last_error.restype = ct.c_char_p
-ENTRIES = {"jk_build", "jk_build_batched", "jk_build_host", "jk_adjoint", "jk_build_dense", "jk_density_grad",
-           "jk_pair", "jk_build_laplace", "jk_build_noalloc", "jk_autotune"}
+ENTRIES = {"jk_build", "jk_build_batched", "jk_build_host", "jk_build_host_packed", "jk_adjoint", "jk_build_dense",
+           "jk_density_grad", "jk_pair", "jk_build_laplace", "jk_build_noalloc", "jk_autotune"}
 TWICE = [False]       # call each entry point twice on its handle and record only the second call
 
 
@@ -313,6 +313,12 @@ def dec_pack_bg(grid, args):
     return [(BG, BG + 8 * ((n - 1) * ldbg + off + 3 * k), "BG"), (X, X + 8 * n * k, "X"), (Y, Y + 8 * n * k, "Y")]
 
 
+def dec_unpack_sym(grid, args):
+    P, n, np_, F = _v(args, 0, VP), _v(args, 1, I32), _v(args, 2, I64), _v(args, 3, VP)
+    assert grid[0] * 256 >= np_ * n * n
+    return [(P, P + 8 * np_ * (n * (n + 1) // 2), "packed"), (F, F + 8 * np_ * n * n, "full")]
+
+
 def dec_ozgemm(grid, args):
     base = args[0]
     nprob = I32.from_address(base + 32 * OZ_PROB_BYTES).value
@@ -343,7 +349,7 @@ DECODERS = [
     ("sum_parts_kernel", dec_sum_parts), ("reduce_partials_kernel", dec_reduce), ("pair_dot_kernel", dec_pair_dot),
     ("laplace_scale_kernel", dec_laplace_scale), ("weighted_sum_kernel", dec_weighted_sum),
     ("ozgemm_kernel", dec_ozgemm), ("jstream_sym_kernel", dec_jstream_sym), ("gterms_kernel", dec_gterms),
-    ("slice4f_kernel", dec_slice4),
+    ("slice4f_kernel", dec_slice4), ("unpack_sym_kernel", dec_unpack_sym),
     ("symmetrize_kernel", dec_symmetrize), ("sym_dl_kernel", dec_sym_dl), ("fold_sym_split_kernel", dec_fold),
     ("fold_sym_kernel", dec_fold), ("pack_ag_kernel", dec_pack_ag), ("pack_bg_kernel", dec_pack_bg),
 ]
@@ -524,15 +530,19 @@ def batched_case(shapes, p, opts):
     return fn
 
 
-def host_case(n, naux, ks, p, opts):
+def host_case(n, naux, ks, p, opts, packed=False):
     def fn():
         f, d, *_ = mol(n, naux, ks, [False] * len(ks))
+        if packed:
+            Lp = buf((naux, n * (n + 1) // 2), "Lpacked")
+            f = jk_factor(n, naux, Lp.ctypes.data)
         h = handle(1 << 20, opts, scaled=False)
-        nb = query(3, f, d, len(ks), p, h=h)
+        nb = query(8 if packed else 3, f, d, len(ks), p, h=h)
         lib.jk_destroy(h)
         h = handle(nb, opts)
         J, K = buf((len(ks), n, n), "J", False), buf((len(ks), n, n), "K", False)
-        return lib.jk_build_host(h, ct.byref(f), len(ks), d, ptr(J), ptr(K), p, None), h
+        call = lib.jk_build_host_packed if packed else lib.jk_build_host
+        return call(h, ct.byref(f), len(ks), d, ptr(J), ptr(K), p, None), h
     return fn
 
 
@@ -651,6 +661,8 @@ CASES = {
     "batched_fp64": batched_case([(60, 150, [6, 6]), (33, 99, [3])], FP64, {}),
     "host_split": host_case(64, 200, [8, 5], SPLIT, {"host_chunk": 37}),
     "host_fp64": host_case(64, 200, [8, 5], FP64, {}),
+    "host_packed_split": host_case(64, 200, [8, 5], SPLIT, {"host_chunk": 37}, packed=True),
+    "host_packed_fp64": host_case(33, 90, [4], FP64, {}, packed=True),
     "adjoint_fp64": adjoint_case(33, 41, [4, 5], [True, False], FP64, {}),
     "adjoint_split": adjoint_case(70, 150, [8, 16, 3], [False, False, True], SPLIT, {}),
     "adjoint_split_no_dl_chunks": adjoint_case(70, 150, [8, 3], [False, False], SPLIT, {"aux_chunk": 40}, False),

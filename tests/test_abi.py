@@ -268,3 +268,17 @@ def test_laplace_query_and_checks(lib):
     a = (ct.c_double * 2)(0.5, 1.0)
     assert lib.jk_build_laplace(None, ct.byref(f), 2, a, None, 3, 0x2000, 0x3000, 1, None, None, 0,
                                 0x4000, 0x5000, 0, None) == jk.JK_ERR_ARG
+
+
+def test_packed_host_query(lib):
+    """JK_OP_BUILD_HOST_PACKED adds the two packed staging chunks to the host
+    build's workspace."""
+    nb_full, nb_packed = ct.c_size_t(), ct.c_size_t()
+    f, d = _one(n=100, naux=600, k=10)
+    fa = (jk.jk_factor * 1)(f)
+    for p in (jk.JK_FP64, jk.JK_SPLIT_BF16):
+        assert lib.jk_workspace_query(jk.JK_OP_BUILD_HOST, 1, fa, None, 1, d, p, ct.byref(nb_full)) == jk.JK_OK
+        assert lib.jk_workspace_query(jk.JK_OP_BUILD_HOST_PACKED, 1, fa, None, 1, d, p, ct.byref(nb_packed)) == jk.JK_OK
+        chunk = (600 + 11) // 12
+        assert nb_packed.value - nb_full.value >= 2 * chunk * (100 * 101 // 2) * 8
+    assert lib.jk_build_host_packed(None, ct.byref(f), 1, d, None, None, 0, None) == jk.JK_ERR_ARG

@@ -172,7 +172,7 @@ class _RecordingLib:
     """The real library for host-only calls (the workspace query); compute
     entry points are recorded instead of called (no device here)."""
     COMPUTE = ("jk_build", "jk_adjoint", "jk_build_batched", "jk_build_dense", "jk_density_grad", "jk_pair",
-               "jk_build_laplace", "jk_set_option")
+               "jk_build_laplace", "jk_set_option", "jk_build_host", "jk_build_host_packed")
 
     def __init__(self, real):
         self.real, self.calls, self.queries = real, [], []
@@ -233,15 +233,35 @@ def test_binding_queries_succeed_for_every_entry_point(rec):
     assert J.shape == (n, n) and K.shape == (n, n)
     J, K = rec.build_laplace(L, X[0], np.array([-1.0, -0.5]), +1, [0.3, 1.2, 2.0], stream=st)
     assert J.shape == (3, n, n)
+    Jh, Kh = torch.empty((2, n, n), dtype=torch.float64), torch.empty((2, n, n), dtype=torch.float64)
+    rec.build_host(L, X, Y, None, "split", J=Jh, K=Kh, stream=st, sync=False)
+    rec.build_host(jk.pack_factor(L), X, Y, None, "split", J=Jh, K=Kh, stream=st, sync=False, packed=True)
+    with pytest.raises(ValueError):
+        rec.build_host(jk.pack_factor(L)[:, 1:], X, Y, None, "split", J=Jh, K=Kh, stream=st, packed=True)
     ops = [q[0] for q in rec.lib.queries]
     assert ops == [jk.JK_OP_BUILD, jk.JK_OP_ADJOINT, jk.JK_OP_BATCHED, jk.JK_OP_BUILD_DENSE,
-                   jk.JK_OP_DENSITY_GRAD, jk.JK_OP_PAIR, jk.JK_OP_LAPLACE, jk.JK_OP_LAPLACE]
+                   jk.JK_OP_DENSITY_GRAD, jk.JK_OP_PAIR, jk.JK_OP_LAPLACE, jk.JK_OP_LAPLACE,
+                   jk.JK_OP_BUILD_HOST, jk.JK_OP_BUILD_HOST_PACKED]
     assert all(q[3] == jk.JK_OK and q[4] > 0 for q in rec.lib.queries), rec.lib.queries
     assert rec.sized == [q[4] for q in rec.lib.queries]
     names = [c[0] for c in rec.lib.calls]
     assert names == ["jk_build", "jk_adjoint", "jk_build_batched", "jk_build_dense", "jk_density_grad", "jk_pair",
-                     "jk_build_laplace", "jk_build_laplace"]
+                     "jk_build_laplace", "jk_build_laplace", "jk_build_host", "jk_build_host_packed"]
     pair_args = rec.lib.calls[5][1]
     assert pair_args[2] == 2 and pair_args[4] == 1          # nl, nr
     lap_args = rec.lib.calls[6][1]
     assert lap_args[2] == 2 and lap_args[5] == 2 and lap_args[4] is not None   # nq, m, weights
+
+
+def test_pack_factor_layout():
+    rng = np.random.default_rng(4)
+    L = rng.standard_normal((3, 6, 6))
+    L = L + L.transpose(0, 2, 1)
+    P = jk.pack_factor(L).numpy()
+    assert P.shape == (3, 21)
+    for p in range(3):
+        t = 0
+        for mu in range(6):
+            for nu in range(mu, 6):
+                assert P[p, t] == L[p, mu, nu]
+                t += 1
