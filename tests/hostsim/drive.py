@@ -699,6 +699,8 @@ FULL_CASES = {
     "full_pairs": pair_case(400, 2400, [40] * 8, [False] * 8, [40] * 8, [False] * 8, SPLIT, {}),
     "full_laplace": laplace_case(400, 2400, 40, 8, False, True, SPLIT, {}),
     "full_adjoint": adjoint_case(600, 3600, [60] * 8, [False] * 8, SPLIT, {}),
+    "full_host": host_case(400, 2400, [40] * 8, SPLIT, {}),
+    "full_host_packed": host_case(400, 2400, [40] * 8, SPLIT, {}, packed=True),
 }
 
 # ---- random cases ----------------------------------------------------------------
