@@ -164,19 +164,16 @@ def _shape(t):
     return tuple(int(v) for v in t.shape)
 
 
-class _ShapeOnly:
-    """A stand-in carrying only a shape (for shape checks of packed factors)."""
-
-    def __init__(self, shape):
-        self.shape = tuple(shape)
-
-
 def _check_problem(L, X, Y=None, sym=None):
     """Shapes of one molecule, checked before any device work: the C ABI takes
     pointers and sizes only, so a mismatch here would become an out-of-bounds
     access in the kernels.  L is [naux][nbf][nbf]; X_s (and Y_s of a
     non-symmetric density) is [nbf][k_s].  Returns (nbf, naux, nd)."""
-    Ls = _shape(L)
+    return _check_shapes(_shape(L), X, Y, sym)
+
+
+def _check_shapes(Ls, X, Y=None, sym=None):
+    """_check_problem with the factor given by its shape."""
     if len(Ls) != 3 or Ls[1] != Ls[2] or min(Ls) < 1:
         raise ValueError(f"L must be [naux][nbf][nbf] with naux, nbf >= 1, got {Ls}")
     naux, n = Ls[0], Ls[1]
@@ -430,7 +427,7 @@ class Engine:
             n = _shape(X[0])[0] if len(X) else 0
             if len(Ls) != 2 or Ls[1] != n * (n + 1) // 2 or Ls[0] < 1:
                 raise ValueError(f"packed L must be [naux][{n * (n + 1) // 2}] for nbf = {n}, got {Ls}")
-            n, _, nd = _check_problem(_ShapeOnly((Ls[0], n, n)), X, Y, sym)
+            n, _, nd = _check_shapes((Ls[0], n, n), X, Y, sym)
         else:
             n, _, nd = _check_problem(L, X, Y, sym)
         if want_j:
