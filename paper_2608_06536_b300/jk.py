@@ -738,6 +738,30 @@ def jk_adjoint(L, X, Y=None, sym=None, W=None, V=None, precision="fp64", **kw):
         L, X, Y, sym, W, V, precision=precision, **kw)
 
 
+def _engine_for(L):
+    return default_engine(L.device if torch.is_tensor(L) and L.is_cuda else None)
+
+
+def jk_build_dense(L, D, precision="fp64", **kw):
+    """J(D_s), K(D_s) for dense densities D ([nd][n][n]) on the default engine."""
+    return _engine_for(L).build_dense(L, D, precision, **kw)
+
+
+def jk_density_grad(L, W=None, V=None, precision="fp64", **kw):
+    """dE/dD_s = K(W_s) + J(V_s) on the default engine."""
+    return _engine_for(L).density_grad(L, W, V, precision, **kw)
+
+
+def jk_pair(L, XL, YL=None, symL=None, XR=None, YR=None, symR=None, precision="fp64", **kw):
+    """Bra-ket pairings (Jp, Kp) on the default engine (see Engine.pairs)."""
+    return _engine_for(L).pairs(L, XL, YL, symL, XR, YR, symR, precision, **kw)
+
+
+def jk_build_laplace(L, CX, epsX, sx, alpha, w=None, CY=None, epsY=None, sy=None, precision="fp64", **kw):
+    """Laplace (LT-AO) builds on the default engine (see Engine.build_laplace)."""
+    return _engine_for(L).build_laplace(L, CX, epsX, sx, alpha, w, CY, epsY, sy, precision, **kw)
+
+
 def tune_export() -> str:
     """The process-wide autotuner cache as text (one entry per line)."""
     lib = load_library()

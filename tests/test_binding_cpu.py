@@ -265,3 +265,23 @@ def test_pack_factor_layout():
             for nu in range(mu, 6):
                 assert P[p, t] == L[p, mu, nu]
                 t += 1
+
+
+def test_module_level_functions_dispatch_to_the_engine(rec, monkeypatch):
+    """jk_build_dense, jk_density_grad, jk_pair and jk_build_laplace pass their
+    arguments to the default engine's methods."""
+    monkeypatch.setattr(jk, "default_engine", lambda device=None: rec)
+    rng = np.random.default_rng(5)
+    n, naux = 6, 4
+    L = rng.standard_normal((naux, n, n))
+    D = rng.standard_normal((2, n, n))
+    X = [rng.standard_normal((n, 2))]
+    st = rec.stream
+    J, K = jk.jk_build_dense(L, D, "split", stream=st)
+    assert J.shape == (2, n, n) and K.shape == (2, n, n)
+    assert jk.jk_density_grad(L, D, None, "split", stream=st).shape == (2, n, n)
+    Jp, Kp = jk.jk_pair(L, X, X, None, X, X, None, "split", stream=st)
+    assert Jp.shape == (1, 1)
+    J, K = jk.jk_build_laplace(L, X[0], np.array([-1.0, -0.5]), +1, [0.5], stream=st)
+    assert J.shape == (1, n, n)
+    assert [c[0] for c in rec.lib.calls] == ["jk_build_dense", "jk_density_grad", "jk_pair", "jk_build_laplace"]
