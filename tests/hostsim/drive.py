@@ -29,7 +29,8 @@ class jk_tune_config(ct.Structure):
 _lib = ct.CDLL(os.path.join(ROOT, "paper_2608_06536_b300", "libjk.so"))
 _lib.jk_last_error.restype = ct.c_char_p
 ENTRIES = {"jk_build", "jk_build_batched", "jk_build_host", "jk_build_host_packed", "jk_adjoint", "jk_build_dense",
-           "jk_density_grad", "jk_pair", "jk_build_laplace", "jk_build_noalloc", "jk_autotune"}
+           "jk_density_grad", "jk_pair", "jk_build_laplace", "jk_build_noalloc", "jk_autotune", "jk_autotune_batched",
+           "jk_debug_sliced_gemm"}
 TWICE = [False]       # call each entry point twice on its handle and record only the second call
 
 
@@ -497,15 +498,49 @@ def run(name, fn):
 
 # ---- the cases ----------------------------------------------------------------
 
-def build_case(n, naux, ks, sym, p, opts):
+def build_case(n, naux, ks, sym, p, opts, want="JK"):
     def fn():
         f, d, *_ = mol(n, naux, ks, sym)
         h = handle(1 << 20, opts, scaled=False)
         nb = query(0, f, d, len(ks), p, h=h)
         lib.jk_destroy(h)
         h = handle(nb, opts)
-        J, K = buf((len(ks), n, n), "J", False), buf((len(ks), n, n), "K", False)
+        J = buf((len(ks), n, n), "J", False) if "J" in want else None
+        K = buf((len(ks), n, n), "K", False) if "K" in want else None
         return lib.jk_build(h, ct.byref(f), len(ks), d, ptr(J), ptr(K), p, None), h
+    return fn
+
+
+def sliced_gemm_case(M, N, K, opts):
+    def fn():
+        A, B, C = buf((M, K), "A"), buf((N, K), "B"), buf((M, N), "C", False)
+        lib.jk_debug_sliced_gemm_workspace.restype = ct.c_size_t
+        nb = lib.jk_debug_sliced_gemm_workspace(M, N, K)
+        h = handle(nb, opts)
+        return lib.jk_debug_sliced_gemm(h, M, N, K, ptr(A), ptr(B), ptr(C), None), h
+    return fn
+
+
+def autotune_batched_case(shapes, p):
+    def fn():
+        fs, ds, outs = [], [], []
+        for m, (n, naux, ks) in enumerate(shapes):
+            f, d, *_ = mol(n, naux, ks, [False] * len(ks), tag=f"m{m}")
+            fs.append(f)
+            ds += list(d)
+            outs += [(buf((n, n), f"J{m}.{s}", False), buf((n, n), f"K{m}.{s}", False)) for s in range(len(ks))]
+        fa = (jk_factor * len(fs))(*fs)
+        da = (jk_density * len(ds))(*ds)
+        ndm = [len(s[2]) for s in shapes]
+        nb = query(2, fa, da, len(ds), p, nmol=len(fs), ndm=ndm)
+        h = handle(4 * nb, {})
+        Jp = (ct.c_void_p * len(outs))(*[o[0].ctypes.data for o in outs])
+        Kp = (ct.c_void_p * len(outs))(*[o[1].ctypes.data for o in outs])
+        cfg, ms = jk_tune_config(), ct.c_double()
+        st = lib.jk_autotune_batched(h, len(fs), fa, (ct.c_int32 * len(ndm))(*ndm), da, Jp, Kp, p, None, 1,
+                                     ct.byref(cfg), ct.byref(ms))
+        lib.jk_tune_clear()
+        return st, h
     return fn
 
 
@@ -657,6 +692,12 @@ CASES = {
                                                {"schedule": 0, "cluster": 1, "aux_chunk": 30}),
     "build_split_nbf_above_superchunk": build_case(2100, 3, [2], [False], SPLIT, {}),
     "build_split_fp32_digits": build_case(400, 60, [40, 40], [True, False], SPLIT, {"slicer": 1, "schedule": 1}),
+    "build_split_j_only": build_case(37, 53, [5, 13], [False, True], SPLIT, {}, want="J"),
+    "build_split_k_only_grouped": build_case(37, 53, [5, 13], [False, True], SPLIT, {"schedule": 1}, want="K"),
+    "build_fp64_j_only": build_case(37, 53, [5, 13], [False, True], FP64, {}, want="J"),
+    "sliced_gemm": sliced_gemm_case(129, 257, 2047, {}),
+    "sliced_gemm_split_k_clustered": sliced_gemm_case(140, 130, 5000, {"cluster": 1, "raster": 1}),
+    "autotune_batched_split": autotune_batched_case([(60, 150, [6, 6]), (111, 222, [11]), (33, 99, [3, 3])], SPLIT),
     "batched_split": batched_case([(60, 150, [6, 6]), (111, 222, [11]), (33, 99, [3, 3, 3])], SPLIT, {}),
     "batched_fp64": batched_case([(60, 150, [6, 6]), (33, 99, [3])], FP64, {}),
     "host_split": host_case(64, 200, [8, 5], SPLIT, {"host_chunk": 37}),

@@ -161,7 +161,7 @@ def test_dense_split_needs_no_identity_panel(records):
 
 
 # needs far less than the query, which covers both maps; no arena; skips what does not fit
-FITS_IN_HALF = {"grad_fp64_V", "noalloc", "autotune_split"}
+FITS_IN_HALF = {"grad_fp64_V", "noalloc", "autotune_split", "autotune_batched_split"}
 
 
 def test_too_small_arena_fails_before_any_device_work(shim_dir):
@@ -172,7 +172,8 @@ def test_too_small_arena_fails_before_any_device_work(shim_dir):
     for name, rec in recs.items():
         if name in FITS_IN_HALF:
             continue
-        assert rec["status"] == 3 and "arena" in rec["error"], (name, rec["status"], rec["error"])
+        assert rec["status"] == 3 and ("arena" in rec["error"] or "workspace" in rec["error"]), (
+            name, rec["status"], rec["error"])
         assert not rec["launches"] and rec["copies"] == 0, (name, len(rec["launches"]), rec["copies"])
 
 
@@ -185,7 +186,7 @@ def test_repeat_calls_are_capturable(shim_dir):
     assert sorted(recs) == sorted(NAMES)
     for name, rec in recs.items():
         assert rec["status"] == 0, (name, rec["error"])
-        if name == "autotune_split":
+        if name.startswith("autotune"):
             continue
         assert rec["syncs"] == 0 and rec["setups"] == 0, (name, rec["syncs"], rec["setups"])
         assert not rec["violations"], (name, rec["violations"][:3])
