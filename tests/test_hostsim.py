@@ -227,3 +227,18 @@ def test_grouped_schedule_collapses_gemm_launches(full_records):
     assert gemms("full_multi_state_tuned") == 2
     assert gemms("full_multi_state_default") == 2 * (1 + 8)
     assert sum("jstream_sym_kernel" in k[0] for k in full_records["full_multi_state_tuned"]["launches"]) == 1
+
+
+def test_tuned_build_matches_the_measured_launch_list(full_records):
+    """Kernel by kernel, the tuned multi-state build records the launches the
+    ncu launch list of the same configuration counted on the B300 (183
+    launches for 3 builds, profiles/multistate_split_launches.md)."""
+    from collections import Counter
+    per_build = {"ozgemm_kernel": 2, "slice4_kernel": 16, "expo_kernel": 16, "expo_flat_kernel": 1,
+                 "jstream_sym_kernel": 1, "gamma_panel_kernel": 1, "reduce_partials_kernel": 8,
+                 "pack_cols_kernel": 15, "slice_kernel": 1}
+    got = Counter()
+    for k in full_records["full_multi_state_tuned"]["launches"]:
+        got[next(key for key in per_build if key in k[0] and not (key == "slice_kernel" and "slice4" in k[0])
+                 and not (key == "expo_kernel" and "expo_flat" in k[0]))] += 1
+    assert dict(got) == per_build and sum(per_build.values()) * 3 == 183
