@@ -56,3 +56,29 @@ def jk(L, X, Y=None, sym=None, precision="fp64", engine=None):
     for s in range(nd):
         xy += [X[s], Y[s]]
     return _JKFunction.apply(engine, precision, sym, L, *xy)
+
+
+class _JKDenseFunction(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, engine, precision, L, D):
+        J, K = engine.build_dense(L, D, precision)
+        ctx.engine, ctx.precision = engine, precision
+        ctx.save_for_backward(L)
+        return J, K
+
+    @staticmethod
+    def backward(ctx, gJ, gK):
+        (L,) = ctx.saved_tensors
+        if ctx.needs_input_grad[2]:
+            raise NotImplementedError("jk_dense differentiates with respect to D only")
+        # dE/dD = K(dE/dK) + J(dE/dJ): K and J are self-adjoint (Eq. 1, Sec. II.A)
+        G = ctx.engine.density_grad(L, W=gK.contiguous(), V=gJ.contiguous(), precision=ctx.precision)
+        return None, None, None, G
+
+
+def jk_dense(L, D, precision="fp64", engine=None):
+    """Differentiable (J, K), each [nd][n][n], for dense general densities D
+    ([nd][n][n]); the gradient with respect to D is the density gradient
+    K(dE/dK) + J(dE/dJ) (jk_density_grad).  L is not differentiated."""
+    engine = engine if engine is not None else _jk.default_engine(L.device)
+    return _JKDenseFunction.apply(engine, precision, L, D)

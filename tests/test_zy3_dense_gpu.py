@@ -92,3 +92,26 @@ def test_density_grad_carries_to_factored_adjoint(eng):
     for s in range(2):
         assert rel_err(to_np(dX[s]), to_np(G[s] @ Y[s])) < 1e-12
         assert rel_err(to_np(dY[s]), to_np(G[s].T @ X[s])) < 1e-12
+
+
+def test_autograd_dense_gradient_is_the_density_gradient(eng):
+    """jk_dense's backward gives d/dD of sum <A, J(D)> + <B, K(D)>, which is
+    J(A) + K(B); checked against the oracle and against central differences of
+    the forward (exact up to rounding: E is linear in D)."""
+    from paper_2608_06536_b300.autograd import jk_dense
+    L, (D, A, B) = _case(37, 53, 2, seed=4)
+    Ld = torch.from_numpy(L).cuda()
+    Dd = torch.from_numpy(D).cuda().requires_grad_(True)
+    Ad, Bd = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    J, K = jk_dense(Ld, Dd, "fp64", engine=eng)
+    ((Ad * J).sum() + (Bd * K).sum()).backward()
+    Go = oracle.density_grad(L, B, A, nd=2)
+    assert rel_err(to_np(Dd.grad), Go) < FP64_REL
+    rng = np.random.default_rng(8)
+    dD = torch.from_numpy(rng.standard_normal(D.shape)).cuda()
+    h = 1e-3
+    with torch.no_grad():
+        Jp, Kp = eng.build_dense(Ld, Dd + h * dD, "fp64")
+        Jm, Km = eng.build_dense(Ld, Dd - h * dD, "fp64")
+        fd = float(((Ad * (Jp - Jm)).sum() + (Bd * (Kp - Km)).sum()) / (2 * h))
+    assert abs(fd - float((Dd.grad * dD).sum())) <= 1e-9 * abs(fd)
