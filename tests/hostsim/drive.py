@@ -769,7 +769,7 @@ def fuzz_cases(count, seed):
         kind = g.choice(["build", "adjoint", "dense", "grad", "pairs", "laplace", "batched", "host"])
         label = f"fuzz{i}_{kind}_n{n}_a{naux}_p{p}"
         if kind == "build":
-            out[label] = build_case(n, naux, ks, sym, p, opts)
+            out[label] = build_case(n, naux, ks, sym, p, opts, want=str(g.choice(["JK", "JK", "J", "K"])))
         elif kind == "adjoint":
             out[label] = adjoint_case(n, naux, ks[:4], sym[:4], p, opts, want_dl=bool(g.random() < 0.5))
         elif kind == "dense":
