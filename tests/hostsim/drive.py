@@ -343,6 +343,164 @@ def dec_ozgemm(grid, args):
     return res
 
 
+# ---- FP64 kernels executed on the simulated device memory (--exec) -------------
+# The arithmetic of each FP64-engine kernel, in numpy, run at launch time on the
+# host buffers that stand in for device memory, so that FP64 calls produce
+# values the oracle can check.  Split-engine kernels are not executed.
+EXEC = [False]
+
+
+def dv(ptr, count):
+    """The `count` doubles at address ptr, as a writable numpy view."""
+    return np.ctypeslib.as_array(ct.cast(ct.c_void_p(ptr), ct.POINTER(ct.c_double)), shape=(max(count, 1),))
+
+
+def _gop_gather(g, b, rows, K):
+    r = np.arange(rows)[:, None]
+    kk = np.arange(K)[None, :]
+    idx = b * g.sb + r * g.sr + (kk // g.kin) * g.sko + (kk % g.kin) * g.ski
+    return dv(g.p, int(idx.max()) + 1)[idx]
+
+
+def ex_dgemm(grid, args):
+    M, N, K = _v(args, 0, I32), _v(args, 1, I32), _v(args, 2, I32)
+    A, B, C, ldc, scb = _a(args, 3, GOp), _a(args, 4, GOp), _v(args, 5, VP), _v(args, 6, I64), _v(args, 7, I64)
+    alpha, beta = _v(args, 8, F64), _v(args, 9, F64)
+    for b in range(grid[2]):
+        prod = _gop_gather(A, b, M, K) @ _gop_gather(B, b, N, K).T
+        idx = b * scb + np.arange(M)[:, None] * ldc + np.arange(N)[None, :]
+        Cv = dv(C, int(idx.max()) + 1)
+        Cv[idx] = alpha * prod + (beta * Cv[idx] if beta != 0.0 else 0.0)
+
+
+def ex_pack_cols(grid, args):
+    src, n, k, Z, ctot, off = (_v(args, 0, VP), _v(args, 1, I32), _v(args, 2, I32), _v(args, 3, VP),
+                               _v(args, 4, I32), _v(args, 5, I32))
+    idx = np.arange(n)[:, None] * ctot + off + np.arange(k)[None, :]
+    dv(Z, int(idx.max()) + 1)[idx] = dv(src, n * k).reshape(n, k)
+
+
+def ex_frob(grid, args):
+    L, n2, M, nd, g, ldg, P0 = (_v(args, 0, VP), _v(args, 1, I64), _v(args, 2, VP), _v(args, 3, I32),
+                                _v(args, 4, VP), _v(args, 5, I32), _v(args, 6, I32))
+    Lm = dv(L, (P0 + grid[0]) * n2).reshape(-1, n2)[P0:P0 + grid[0]]
+    Mm = dv(M, nd * n2).reshape(nd, n2)
+    gv = dv(g, (nd - 1) * ldg + P0 + grid[0])
+    for s in range(nd):
+        gv[s * ldg + P0:s * ldg + P0 + grid[0]] = Lm @ Mm[s]
+
+
+def ex_gamma_panel(grid, args):
+    T, n, ctot, tab, g, ldg, P0 = (_v(args, 0, VP), _v(args, 1, I32), _v(args, 2, I64), _a(args, 3, DensTab),
+                                   _v(args, 4, VP), _v(args, 5, I32), _v(args, 6, I32))
+    np_, nd = grid[0], grid[1]
+    Tm = dv(T, np_ * n * ctot).reshape(np_, n, ctot)
+    gv = dv(g, (nd - 1) * ldg + P0 + np_)
+    for s in range(nd):
+        k, off = tab.k[s], tab.offX[s]
+        Ys = dv(tab.Y[s], n * k).reshape(n, k)
+        gv[s * ldg + P0:s * ldg + P0 + np_] = np.einsum("pik,ik->p", Tm[:, :, off:off + k], Ys)
+
+
+def ex_jstream_sym(grid, args, name):
+    ns = int(name.split("ILi")[1].split("E")[0])
+    L, n, naux, g, ldg, o = (_v(args, 0, VP), _v(args, 1, I32), _v(args, 2, I32), _v(args, 3, VP),
+                             _v(args, 4, I32), _a(args, 5, OutTab))
+    Lm = dv(L, naux * n * n).reshape(naux, n * n)
+    for j in range(ns):
+        out = dv(g + 8 * j * ldg, naux) @ Lm
+        out = out.reshape(n, n)
+        dv(o.p[j], n * n)[:] = np.triu(out).ravel() + np.triu(out, 1).T.ravel()   # upper triangle, mirrored
+
+
+def ex_axpy(grid, args):
+    y, x, cnt = _v(args, 0, VP), _v(args, 1, VP), _v(args, 2, I64)
+    dv(y, cnt)[:] += dv(x, cnt)
+
+
+def ex_sum_parts(grid, args):
+    out, part, nb, cnt, acc = _v(args, 0, VP), _v(args, 1, VP), _v(args, 2, I32), _v(args, 3, I64), _v(args, 4, I32)
+    tot = dv(part, nb * cnt).reshape(nb, cnt).sum(axis=0)
+    o = dv(out, cnt)
+    o[:] = (o if acc else 0.0) + tot
+
+
+def ex_pair_dot(grid, args):
+    ZL, U, n, ctot, tab, out, nr = (_v(args, 0, VP), _v(args, 1, VP), _v(args, 2, I32), _v(args, 3, I32),
+                                    _a(args, 4, PairTab), _v(args, 5, VP), _v(args, 6, I32))
+    Zm = dv(ZL, n * ctot).reshape(n, ctot)
+    Um = dv(U, nr * n * ctot).reshape(nr, n, ctot)
+    ov = dv(out, grid[0] * nr)
+    for a in range(grid[0]):
+        k, oa, ob = tab.k[a], tab.offA[a], tab.offB[a]
+        for b in range(nr):
+            ov[a * nr + b] = np.sum(Zm[:, oa:oa + k] * Um[b, :, ob:ob + k])
+
+
+def ex_laplace_scale(grid, args):
+    C, eps, n, m, sgn = _v(args, 0, VP), _v(args, 1, VP), _v(args, 2, I32), _v(args, 3, I32), _v(args, 4, F64)
+    al = (F64 * MAXD).from_address(args[5])
+    nq, out = _v(args, 6, I32), _v(args, 7, VP)
+    Cm, ev = dv(C, n * m).reshape(n, m), dv(eps, m)
+    o = dv(out, nq * n * m).reshape(nq, n, m)
+    for k in range(nq):
+        o[k] = Cm * np.exp(sgn * al[k] * ev * 0.5)[None, :]
+
+
+def ex_weighted_sum(grid, args):
+    out, part = _v(args, 0, VP), _v(args, 1, VP)
+    w = (F64 * MAXD).from_address(args[2])
+    nq, cnt = _v(args, 3, I32), _v(args, 4, I64)
+    dv(out, cnt)[:] = np.tensordot(np.array(w[:nq]), dv(part, nq * cnt).reshape(nq, cnt), 1)
+
+
+def ex_unpack_sym(grid, args):
+    P, n, np_, F = _v(args, 0, VP), _v(args, 1, I32), _v(args, 2, I64), _v(args, 3, VP)
+    t = n * (n + 1) // 2
+    iu = np.triu_indices(n)
+    Pm = dv(P, np_ * t).reshape(np_, t)
+    Fm = dv(F, np_ * n * n).reshape(np_, n, n)
+    for p in range(np_):
+        M = np.zeros((n, n))
+        M[iu] = Pm[p]
+        Fm[p] = M + np.triu(M, 1).T
+
+
+def ex_gterms(grid, args):
+    G, n2, nd = _v(args, 0, VP), _v(args, 1, I64), _v(args, 3, I32)
+    D, V, c, g, ldg, P0 = (_v(args, 4, VP), _v(args, 5, VP), _v(args, 6, VP), _v(args, 7, VP), _v(args, 8, I32),
+                           _v(args, 9, I32))
+    np_ = grid[1]
+    Gm = dv(G, np_ * n2).reshape(np_, n2)
+    for p in range(np_):
+        for s in range(nd):
+            if D:
+                Gm[p] += dv(c, s * ldg + P0 + p + 1)[s * ldg + P0 + p] * dv(D, nd * n2).reshape(nd, n2)[s]
+            if V:
+                Gm[p] += dv(g, s * ldg + P0 + p + 1)[s * ldg + P0 + p] * dv(V, nd * n2).reshape(nd, n2)[s]
+
+
+def ex_symmetrize(grid, args):
+    G, n, dL = _v(args, 0, VP), _v(args, 1, I32), _v(args, 2, VP)
+    np_ = grid[1]
+    Gm = dv(G, np_ * n * n).reshape(np_, n, n)
+    dv(dL, np_ * n * n).reshape(np_, n, n)[:] = 0.5 * (Gm + Gm.transpose(0, 2, 1))
+
+
+def ex_fold(grid, args):
+    dX, dY, cnt = _v(args, 0, VP), _v(args, 1, VP), _v(args, 2, I64)
+    dv(dX, cnt)[:] += dv(dY, cnt)
+    dv(dY, cnt)[:] = 0.0
+
+
+EXECUTORS = [
+    ("dgemm_nt_kernel", ex_dgemm), ("pack_cols_kernel", ex_pack_cols), ("frob_stream_kernel", ex_frob),
+    ("gamma_panel_kernel", ex_gamma_panel), ("jstream_sym_kernel", ex_jstream_sym), ("axpy_kernel", ex_axpy),
+    ("sum_parts_kernel", ex_sum_parts), ("pair_dot_kernel", ex_pair_dot), ("laplace_scale_kernel", ex_laplace_scale),
+    ("weighted_sum_kernel", ex_weighted_sum), ("unpack_sym_kernel", ex_unpack_sym), ("gterms_kernel", ex_gterms),
+    ("symmetrize_kernel", ex_symmetrize), ("fold_sym_kernel", ex_fold),
+]
+
 DECODERS = [
     ("expo_flat_kernel", dec_expo_flat), ("expo_kernel", dec_expo), ("slice4_kernel", dec_slice4),
     ("slice_kernel", dec_slice), ("dgemm_nt_kernel", dec_dgemm), ("pack_cols_kernel", dec_pack_cols),
@@ -388,9 +546,16 @@ def on_launch(name, grid, block, args):
                 violations.append(f"{key}: inconsistent arguments {e}")
                 return
             decoded[0] += 1
+            bad = False
             for lo, hi, what in ranges:
                 if not _inside(lo, hi):
+                    bad = True
                     violations.append(f"{key}: {what} [{lo:#x}, {hi:#x}) outside the call's memory")
+            if EXEC[0] and not bad:
+                for ekey, ex in EXECUTORS:
+                    if ekey in name and not (ekey == "fold_sym_kernel" and "fold_sym_split" in name):
+                        ex(g, args, name) if ex is ex_jstream_sym else ex(g, args)
+                        break
             return
     undecoded.add(name)
 
@@ -422,6 +587,8 @@ def ptr(a):
 
 def mol(n, naux, ks, sym, tag="m"):
     L = buf((naux, n, n), f"{tag}.L")
+    if not BIG[0]:
+        L[...] = L + L.transpose(0, 2, 1)      # L^P symmetric, as the engine assumes
     X = [buf((n, k), f"{tag}.X{s}") for s, k in enumerate(ks)]
     Y = [buf((n, k), f"{tag}.Y{s}") for s, k in enumerate(ks)]
     d = (jk_density * len(ks))()
@@ -455,6 +622,23 @@ def query(op, f, d, nd, p, nmol=1, ndm=None, h=None):
     return nb.value
 
 
+CHECKS = []   # (label, computed, oracle reference) of the current case, with --exec
+
+
+def oracle_mod():
+    sys.path.insert(0, ROOT)
+    import oracle
+    return oracle
+
+
+def check(label, got, ref):
+    CHECKS.append((label, np.array(got, dtype=np.float64), np.array(ref, dtype=np.float64)))
+
+
+def _ylist(X, Y, sym):
+    return [X[s] if sym[s] else Y[s] for s in range(len(X))]
+
+
 def record(name, status, h):
     launches = []
     g, b, c = (ct.c_uint * 3)(), (ct.c_uint * 3)(), (ct.c_uint * 3)()
@@ -477,6 +661,8 @@ def record(name, status, h):
                       "copies": shim.shim_copy_count(), "syncs": shim.shim_sync_count(),
                       "setups": shim.shim_setup_count(),
                       "owned": [[o[0], o[1], o[2]] for o in owned + statics()], "violations": list(violations),
+                      "checks": [[lab, float(np.abs(g - r).max() / max(np.abs(r).max(), 1e-300))]
+                                 for lab, g, r in CHECKS],
                       "decoded": decoded[0], "undecoded": sorted(undecoded)}), flush=True)
 
 
@@ -484,6 +670,7 @@ def run(name, fn):
     owned.clear()
     violations.clear()
     undecoded.clear()
+    CHECKS.clear()
     decoded[0] = 0
     shim.shim_reset()
     try:
@@ -500,14 +687,21 @@ def run(name, fn):
 
 def build_case(n, naux, ks, sym, p, opts, want="JK"):
     def fn():
-        f, d, *_ = mol(n, naux, ks, sym)
+        f, d, L, X, Y = mol(n, naux, ks, sym)
         h = handle(1 << 20, opts, scaled=False)
         nb = query(0, f, d, len(ks), p, h=h)
         lib.jk_destroy(h)
         h = handle(nb, opts)
         J = buf((len(ks), n, n), "J", False) if "J" in want else None
         K = buf((len(ks), n, n), "K", False) if "K" in want else None
-        return lib.jk_build(h, ct.byref(f), len(ks), d, ptr(J), ptr(K), p, None), h
+        st = lib.jk_build(h, ct.byref(f), len(ks), d, ptr(J), ptr(K), p, None)
+        if EXEC[0] and p == FP64 and st == 0:
+            Jo, Ko = oracle_mod().build(L, X, _ylist(X, Y, sym))
+            if J is not None:
+                check("J", J, Jo)
+            if K is not None:
+                check("K", K, Ko)
+        return st, h
     return fn
 
 
@@ -546,11 +740,12 @@ def autotune_batched_case(shapes, p):
 
 def batched_case(shapes, p, opts):
     def fn():
-        fs, ds, outs = [], [], []
+        fs, ds, outs, mols = [], [], [], []
         for m, (n, naux, ks) in enumerate(shapes):
-            f, d, *_ = mol(n, naux, ks, [False] * len(ks), tag=f"m{m}")
+            f, d, L, X, Y = mol(n, naux, ks, [False] * len(ks), tag=f"m{m}")
             fs.append(f)
             ds += list(d)
+            mols.append((L, X, Y))
             outs += [(buf((n, n), f"J{m}.{s}", False), buf((n, n), f"K{m}.{s}", False)) for s in range(len(ks))]
         fa = (jk_factor * len(fs))(*fs)
         da = (jk_density * len(ds))(*ds)
@@ -561,15 +756,27 @@ def batched_case(shapes, p, opts):
         h = handle(nb, opts)
         Jp = (ct.c_void_p * len(outs))(*[o[0].ctypes.data for o in outs])
         Kp = (ct.c_void_p * len(outs))(*[o[1].ctypes.data for o in outs])
-        return lib.jk_build_batched(h, len(fs), fa, (ct.c_int32 * len(ndm))(*ndm), da, Jp, Kp, p, None), h
+        st = lib.jk_build_batched(h, len(fs), fa, (ct.c_int32 * len(ndm))(*ndm), da, Jp, Kp, p, None)
+        if EXEC[0] and p == FP64 and st == 0:
+            i = 0
+            for m, (L, X, Y) in enumerate(mols):
+                Jo, Ko = oracle_mod().build(L, X, Y)
+                for s_ in range(len(X)):
+                    check(f"J{m}.{s_}", outs[i][0], Jo[s_])
+                    check(f"K{m}.{s_}", outs[i][1], Ko[s_])
+                    i += 1
+        return st, h
     return fn
 
 
 def host_case(n, naux, ks, p, opts, packed=False):
     def fn():
-        f, d, *_ = mol(n, naux, ks, [False] * len(ks))
+        f, d, L, X, Y = mol(n, naux, ks, [False] * len(ks))
         if packed:
-            Lp = buf((naux, n * (n + 1) // 2), "Lpacked")
+            Lp = buf((naux, n * (n + 1) // 2), "Lpacked", fill=False)
+            if not BIG[0]:
+                iu = np.triu_indices(n)
+                Lp[...] = L[:, iu[0], iu[1]]
             f = jk_factor(n, naux, Lp.ctypes.data)
         h = handle(1 << 20, opts, scaled=False)
         nb = query(8 if packed else 3, f, d, len(ks), p, h=h)
@@ -577,13 +784,18 @@ def host_case(n, naux, ks, p, opts, packed=False):
         h = handle(nb, opts)
         J, K = buf((len(ks), n, n), "J", False), buf((len(ks), n, n), "K", False)
         call = lib.jk_build_host_packed if packed else lib.jk_build_host
-        return call(h, ct.byref(f), len(ks), d, ptr(J), ptr(K), p, None), h
+        st = call(h, ct.byref(f), len(ks), d, ptr(J), ptr(K), p, None)
+        if EXEC[0] and p == FP64 and st == 0:
+            Jo, Ko = oracle_mod().build(L, X, Y)
+            check("J", J, Jo)
+            check("K", K, Ko)
+        return st, h
     return fn
 
 
 def adjoint_case(n, naux, ks, sym, p, opts, want_dl=True):
     def fn():
-        f, d, *_ = mol(n, naux, ks, sym)
+        f, d, L, X, Y = mol(n, naux, ks, sym)
         nd, tot = len(ks), n * sum(ks)
         W, V = buf((nd, n, n), "W"), buf((nd, n, n), "V")
         dX, dY = buf((tot,), "dX", False), buf((tot,), "dY", False)
@@ -592,13 +804,27 @@ def adjoint_case(n, naux, ks, sym, p, opts, want_dl=True):
         nb = query(1, f, d, nd, p, h=h)
         lib.jk_destroy(h)
         h = handle(nb, opts)
-        return lib.jk_adjoint(h, ct.byref(f), nd, d, ptr(W), ptr(V), ptr(dX), ptr(dY), ptr(dL), p, None), h
+        st = lib.jk_adjoint(h, ct.byref(f), nd, d, ptr(W), ptr(V), ptr(dX), ptr(dY), ptr(dL), p, None)
+        if EXEC[0] and p == FP64 and st == 0:
+            dXo, dYo, dLo = oracle_mod().adjoint(L, X, _ylist(X, Y, sym), list(W), list(V), want_dl=want_dl)
+            off = 0
+            for s_, k in enumerate(ks):
+                gx, gy = dX[off:off + n * k].reshape(n, k), dY[off:off + n * k].reshape(n, k)
+                check(f"dX{s_}", gx, dXo[s_] + dYo[s_] if sym[s_] else dXo[s_])
+                if not sym[s_]:
+                    check(f"dY{s_}", gy, dYo[s_])
+                off += n * k
+            if want_dl:
+                check("dL", dL, dLo)
+        return st, h
     return fn
 
 
 def dense_case(n, naux, nd, p, opts, grad=None):
     def fn():
         L = buf((naux, n, n), "L")
+        if not BIG[0]:
+            L[...] = L + L.transpose(0, 2, 1)
         f = jk_factor(n, naux, L.ctypes.data)
         A, B = buf((nd, n, n), "A"), buf((nd, n, n), "B")
         O1, O2 = buf((nd, n, n), "O1", False), buf((nd, n, n), "O2", False)
@@ -607,16 +833,24 @@ def dense_case(n, naux, nd, p, opts, grad=None):
         lib.jk_destroy(h)
         h = handle(nb, opts)
         if grad is None:
-            return lib.jk_build_dense(h, ct.byref(f), nd, ptr(A), ptr(O1), ptr(O2), p, None), h
+            st = lib.jk_build_dense(h, ct.byref(f), nd, ptr(A), ptr(O1), ptr(O2), p, None)
+            if EXEC[0] and p == FP64 and st == 0:
+                Jo, Ko = oracle_mod().build_dense(L, A)
+                check("J", O1, Jo)
+                check("K", O2, Ko)
+            return st, h
         W = A if "W" in grad else None
         V = B if "V" in grad else None
-        return lib.jk_density_grad(h, ct.byref(f), nd, ptr(W), ptr(V), ptr(O1), p, None), h
+        st = lib.jk_density_grad(h, ct.byref(f), nd, ptr(W), ptr(V), ptr(O1), p, None)
+        if EXEC[0] and p == FP64 and st == 0:
+            check("G", O1, oracle_mod().density_grad(L, W, V, nd=nd))
+        return st, h
     return fn
 
 
 def pair_case(n, naux, kl, sl, kr, sr, p, opts):
     def fn():
-        f, dl, L, *_ = mol(n, naux, kl, sl, tag="left")
+        f, dl, L, XL, YL = mol(n, naux, kl, sl, tag="left")
         XR = [buf((n, k), f"right.X{s}") for s, k in enumerate(kr)]
         YR = [buf((n, k), f"right.Y{s}") for s, k in enumerate(kr)]
         dr = (jk_density * len(kr))()
@@ -629,13 +863,20 @@ def pair_case(n, naux, kl, sl, kr, sr, p, opts):
         lib.jk_destroy(h)
         h = handle(nb, opts)
         Jp, Kp = buf((len(kl), len(kr)), "Jp", False), buf((len(kl), len(kr)), "Kp", False)
-        return lib.jk_pair(h, ct.byref(f), len(kl), dl, len(kr), dr, ptr(Jp), ptr(Kp), p, None), h
+        st = lib.jk_pair(h, ct.byref(f), len(kl), dl, len(kr), dr, ptr(Jp), ptr(Kp), p, None)
+        if EXEC[0] and p == FP64 and st == 0:
+            Jo, Ko = oracle_mod().pairs(L, XL, _ylist(XL, YL, sl), XR, _ylist(XR, YR, sr))
+            check("Jp", Jp, Jo)
+            check("Kp", Kp, Ko)
+        return st, h
     return fn
 
 
 def laplace_case(n, naux, m, nq, sym, weighted, p, opts):
     def fn():
         L = buf((naux, n, n), "L")
+        if not BIG[0]:
+            L[...] = L + L.transpose(0, 2, 1)
         f = jk_factor(n, naux, L.ctypes.data)
         CX, CY = buf((n, m), "CX"), buf((n, m), "CY")
         eX, eY = buf((m,), "epsX"), buf((m,), "epsY")
@@ -656,15 +897,25 @@ def laplace_case(n, naux, m, nq, sym, weighted, p, opts):
         st = lib.jk_build_laplace(h, ct.byref(f), nq, alpha, w, m, ptr(CX), ptr(eX), 1,
                                   None if sym else ptr(CY), None if sym else ptr(eY), 0 if sym else -1,
                                   ptr(J), ptr(K), p, None)
+        if EXEC[0] and p == FP64 and st == 0:
+            Jo, Ko = oracle_mod().laplace(L, CX, eX, 1, CX if sym else CY, eX if sym else eY, 1 if sym else -1,
+                                          np.array(alpha[:]), np.array(w[:]) if weighted else None)
+            check("J", J, Jo)
+            check("K", K, Ko)
         return st, h
     return fn
 
 
 def noalloc_case(n, naux, ks):
     def fn():
-        f, d, *_ = mol(n, naux, ks, [False] * len(ks))
+        f, d, L, X, Y = mol(n, naux, ks, [False] * len(ks))
         J, K = buf((len(ks), n, n), "J", False), buf((len(ks), n, n), "K", False)
-        return lib.jk_build_noalloc(ct.byref(f), len(ks), d, ptr(J), ptr(K), None), None
+        st = lib.jk_build_noalloc(ct.byref(f), len(ks), d, ptr(J), ptr(K), None)
+        if EXEC[0] and st == 0:
+            Jo, Ko = oracle_mod().build(L, X, Y)
+            check("J", J, Jo)
+            check("K", K, Ko)
+        return st, None
     return fn
 
 
@@ -810,6 +1061,9 @@ if __name__ == "__main__":
     if "--twice" in args:
         TWICE[0] = True
         args.remove("--twice")
+    if "--exec" in args:
+        EXEC[0] = True
+        args.remove("--exec")
     names = args or list(CASES)
     for name in names:
         BIG[0] = name in FULL_CASES
