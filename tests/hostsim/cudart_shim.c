@@ -218,6 +218,17 @@ static CUresult encode_tiled(CUtensorMap *map, CUtensorMapDataType dtype, cuuint
                              CUtensorMapL2promotion l2, CUtensorMapFloatOOBfill oob) {
     (void)estr; (void)il; (void)l2; (void)oob;
     memset(map, 0, sizeof *map);
+    /* The map is opaque to the library: record what it addresses in it, so a
+     * test executing the kernel can find its operand (magic, type, rank, base,
+     * extents, byte strides of dimensions 1 and 2). */
+    {
+        unsigned long long *w = (unsigned long long *)map;
+        w[0] = 0x6A6B73696D6D6170ull;
+        w[1] = ((unsigned long long)dtype << 32) | rank;
+        w[2] = (unsigned long long)(uintptr_t)base;
+        for (unsigned i = 0; i < rank && i < 3; i++) w[3 + i] = dims[i];
+        for (unsigned i = 1; i < rank && i < 3; i++) w[5 + i] = strides[i - 1];
+    }
     if (!g_tmap) g_tmap = (TMap *)calloc(MAX_TMAP, sizeof(TMap));
     if (g_ntmap >= MAX_TMAP || rank < 1 || rank > 5) return CUDA_ERROR_INVALID_VALUE;
     TMap *t = &g_tmap[g_ntmap++];

@@ -493,12 +493,181 @@ def ex_fold(grid, args):
     dv(dY, cnt)[:] = 0.0
 
 
+# ---- split engine, executed --------------------------------------------------
+# Exponents and digit slices as the slicers define them; the sliced GEMM as
+# the exact sum of the rebuilt 48-bit operands per 2048-element super-chunk
+# (int64 partials in units of 2^-48, or FP64 output); the partial reduction
+# in FP64.  This checks the orchestration of the split paths, not the
+# tensor-core arithmetic (which tests/test_split_gpu.py covers on the GPU).
+
+def uv(ptr, count, dtype):
+    ctype = {np.uint16: ct.c_uint16, np.int32: ct.c_int32, np.int64: ct.c_int64}[dtype]
+    return np.ctypeslib.as_array(ct.cast(ct.c_void_p(ptr), ct.POINTER(ctype)), shape=(max(count, 1),))
+
+
+def _src_gather(src, rows, K):
+    r = np.arange(rows)[:, None]
+    kk = np.arange(K)[None, :]
+    idx = (r // src.rin) * src.sr + (r % src.rin) * src.sri + (kk // src.kin) * src.sko + (kk % src.kin) * src.ski
+    return dv(src.p, int(idx.max()) + 1)[idx]
+
+
+def _expo_of(m):
+    """e with max|x| < 2^e from the maximum magnitude (-1000 for zero)."""
+    m = np.asarray(m, dtype=np.float64)
+    e = np.frexp(m)[1].astype(np.int64)
+    return np.where(m > 0, e, -1000)
+
+
+def ex_expo(grid, args):
+    src, rows, K, rpe, e = _a(args, 0, Src), _v(args, 1, I32), _v(args, 2, I32), _v(args, 3, I32), _v(args, 4, VP)
+    X = np.abs(_src_gather(src, rows, K))
+    nsc = grid[1]
+    ev = uv(e, grid[0] * nsc, np.int32)
+    for g in range(grid[0]):
+        for z in range(nsc):
+            blk = X[g * rpe:min(rows, g * rpe + rpe), z * SUPER:min(K, (z + 1) * SUPER)]
+            ev[g * nsc + z] = _expo_of(blk.max() if blk.size else 0.0)
+
+
+def ex_expo_flat(grid, args):
+    p, ln, e = _v(args, 0, VP), _v(args, 1, I64), _v(args, 2, VP)
+    X = np.abs(dv(p, grid[0] * ln).reshape(grid[0], ln))
+    uv(e, grid[0], np.int32)[:] = _expo_of(X.max(axis=1))
+
+
+def _digits_bf16(x, e):
+    """The six BF16 slice words of x at exponent e (integer balanced digits)."""
+    F = np.sign(x) * np.floor(np.abs(x) * np.exp2(48.0 - e) + 0.5)
+    F = F.astype(np.int64)
+    lo = F & 0xFFFFFF
+    hi = F >> 24
+    q = [None] * 6
+    for j in (5, 4, 3):
+        q[j] = ((lo + 128) & 255) - 128
+        lo = (lo - q[j]) >> 8
+    hi = hi + lo
+    for j in (2, 1):
+        q[j] = ((hi + 128) & 255) - 128
+        hi = (hi - q[j]) >> 8
+    q[0] = hi
+    return [((q[j].astype(np.float64) * 2.0 ** (-8 * (j + 1))).astype(np.float32).view(np.uint32) >> 16)
+            .astype(np.uint16) for j in range(6)]
+
+
+def ex_slice(grid, args):
+    src, rows, K, Kpad = _a(args, 0, Src), _v(args, 1, I32), _v(args, 2, I32), _v(args, 3, I32)
+    e, rpe, nsc, out = _v(args, 4, VP), _v(args, 5, I32), _v(args, 6, I32), _v(args, 7, VP)
+    X = _src_gather(src, rows, K)
+    ev = uv(e, ((rows - 1) // rpe + 1) * nsc, np.int32)
+    E = ev[(np.arange(rows)[:, None] // rpe) * nsc + np.arange(K)[None, :] // SUPER]
+    planes = _digits_bf16(X, E)
+    o = uv(out, NSLICE * rows * Kpad, np.uint16).reshape(NSLICE, rows, Kpad)
+    o[:] = 0
+    for j in range(NSLICE):
+        o[j, :, :K] = planes[j]
+
+
+def _tmap(ptr):
+    w = (ct.c_uint64 * 16).from_address(ptr)
+    assert w[0] == 0x6A6B73696D6D6170, "tensor map not encoded by the stand-in"
+    return {"dtype": w[1] >> 32, "rank": w[1] & 0xFFFFFFFF, "base": w[2], "dims": [w[3], w[4], w[5]],
+            "strides": [0, w[6], w[7]]}
+
+
+def _operand(tm, e, rpe, rows, K, nsuper):
+    """Rebuilt operand values in units of 2^(exponent): [rows][K] float64, and
+    the exponents [rows][nsuper]."""
+    Kpad, nrows = tm["dims"][0], tm["dims"][1]
+    planes = uv(tm["base"], NSLICE * nrows * Kpad, np.uint16).reshape(NSLICE, nrows, Kpad)[:, :rows, :K]
+    vals = np.zeros((rows, K))
+    for j in range(NSLICE):
+        vals += (planes[j].astype(np.uint32) << 16).view(np.float32).astype(np.float64)
+    ev = uv(e, ((rows - 1) // rpe + 1) * nsuper, np.int32).reshape(-1, nsuper)[np.arange(rows) // rpe]
+    return vals, ev
+
+
+def ex_ozgemm(grid, args):
+    base = args[0]
+    nprob = I32.from_address(base + 32 * OZ_PROB_BYTES).value
+    for i in range(nprob):
+        pb = base + i * OZ_PROB_BYTES
+        a = OzArgs.from_address(pb + 512)
+        tA, tB = _tmap(pb), _tmap(pb + 128)
+        A, eA = _operand(tA, a.eA, a.a_rpe, a.M, a.K, a.nsuper)
+        B, eB = _operand(tB, a.eB, a.b_rpe, a.N, a.K, a.nsuper)
+        for z in range(a.nsuper):
+            S = A[:, z * SUPER:(z + 1) * SUPER] @ B[:, z * SUPER:(z + 1) * SUPER].T
+            if a.nsuper == 1:
+                idx = np.arange(a.M)[:, None] * a.ldc + np.arange(a.N)[None, :]
+                dv(a.C, int(idx.max()) + 1)[idx] = np.ldexp(S, eA[:, z:z + 1] + eB[:, z][None, :])
+            else:
+                idx = z * a.pz + np.arange(a.M)[:, None] * a.ldp + np.arange(a.N)[None, :]
+                uv(a.P, int(idx.max()) + 1, np.int64)[idx] = np.rint(S * 2.0 ** 48).astype(np.int64)
+
+
+def ex_reduce(grid, args):
+    P, pz, ldp, nz, M, N = (_v(args, 0, VP), _v(args, 1, I64), _v(args, 2, I64), _v(args, 3, I32),
+                            _v(args, 4, I32), _v(args, 5, I32))
+    eA, arpe, eB, brpe, out, ldo, acc = (_v(args, 6, VP), _v(args, 7, I32), _v(args, 8, VP), _v(args, 9, I32),
+                                         _v(args, 10, VP), _v(args, 11, I64), _v(args, 12, I32))
+    ea = uv(eA, ((M - 1) // arpe + 1) * nz, np.int32).reshape(-1, nz)[np.arange(M) // arpe]
+    eb = uv(eB, ((N - 1) // brpe + 1) * nz, np.int32).reshape(-1, nz)[np.arange(N) // brpe]
+    tot = np.zeros((M, N))
+    for z in range(nz):
+        idx = z * pz + np.arange(M)[:, None] * ldp + np.arange(N)[None, :]
+        Pz = uv(P, int(idx.max()) + 1, np.int64)[idx].astype(np.float64)
+        tot += np.ldexp(Pz, ea[:, z:z + 1] + eb[:, z][None, :] - 48)
+    oidx = np.arange(M)[:, None] * ldo + np.arange(N)[None, :]
+    o = dv(out, int(oidx.max()) + 1)
+    o[oidx] = (o[oidx] if acc else 0.0) + tot
+
+
+def ex_pack_ag(grid, args):
+    AG, ldag, off, U, Vp, X, cps, P0, n, k, np_ = (
+        _v(args, 0, VP), _v(args, 1, I64), _v(args, 2, I32), _v(args, 3, VP), _v(args, 4, VP), _v(args, 5, VP),
+        _v(args, 6, VP), _v(args, 7, I32), _v(args, 8, I32), _v(args, 9, I32), _v(args, 10, I32))
+    pm = np.arange(np_ * n)
+    mu, p = pm % n, pm // n
+    rows = dv(AG, (np_ * n - 1) * ldag + off + 3 * k)
+    for i in range(k):
+        uo = mu * np_ * k + p * k + i
+        rows[pm * ldag + off + i] = dv(U, n * np_ * k)[uo] if U else 0.0
+        rows[pm * ldag + off + k + i] = dv(Vp, n * np_ * k)[uo] if Vp else 0.0
+        rows[pm * ldag + off + 2 * k + i] = (dv(cps, P0 + np_)[P0 + p] * dv(X, n * k)[mu * k + i]) if cps else 0.0
+
+
+def ex_pack_bg(grid, args):
+    BG, ldbg, off, X, Y, n, k = (_v(args, 0, VP), _v(args, 1, I64), _v(args, 2, I32), _v(args, 3, VP),
+                                 _v(args, 4, VP), _v(args, 5, I32), _v(args, 6, I32))
+    Xm, Ym = dv(X, n * k).reshape(n, k), dv(Y, n * k).reshape(n, k)
+    rows = dv(BG, (n - 1) * ldbg + off + 3 * k)
+    for nu in range(n):
+        b = nu * ldbg + off
+        rows[b:b + k], rows[b + k:b + 2 * k], rows[b + 2 * k:b + 3 * k] = Xm[nu], Ym[nu], Ym[nu]
+
+
+def ex_sym_dl(grid, args):
+    G, GV, n, dL = _v(args, 0, VP), _v(args, 1, VP), _v(args, 2, I32), _v(args, 3, VP)
+    np_ = grid[1]
+    Gm = dv(G, np_ * n * n).reshape(np_, n, n)
+    v = 0.5 * (Gm + Gm.transpose(0, 2, 1))
+    if GV:
+        Vm = dv(GV, np_ * n * n).reshape(np_, n, n)
+        v = v + 0.5 * (Vm + Vm.transpose(0, 2, 1))
+    dv(dL, np_ * n * n).reshape(np_, n, n)[:] = v
+
+
 EXECUTORS = [
     ("dgemm_nt_kernel", ex_dgemm), ("pack_cols_kernel", ex_pack_cols), ("frob_stream_kernel", ex_frob),
     ("gamma_panel_kernel", ex_gamma_panel), ("jstream_sym_kernel", ex_jstream_sym), ("axpy_kernel", ex_axpy),
     ("sum_parts_kernel", ex_sum_parts), ("pair_dot_kernel", ex_pair_dot), ("laplace_scale_kernel", ex_laplace_scale),
     ("weighted_sum_kernel", ex_weighted_sum), ("unpack_sym_kernel", ex_unpack_sym), ("gterms_kernel", ex_gterms),
-    ("symmetrize_kernel", ex_symmetrize), ("fold_sym_kernel", ex_fold),
+    ("symmetrize_kernel", ex_symmetrize), ("fold_sym_split_kernel", ex_fold), ("fold_sym_kernel", ex_fold),
+    ("expo_flat_kernel", ex_expo_flat), ("expo_kernel", ex_expo), ("slice4f_kernel", ex_slice),
+    ("slice4_kernel", ex_slice), ("slice_kernel", ex_slice), ("ozgemm_kernel", ex_ozgemm),
+    ("reduce_partials_kernel", ex_reduce), ("pack_ag_kernel", ex_pack_ag), ("pack_bg_kernel", ex_pack_bg),
+    ("sym_dl_kernel", ex_sym_dl),
 ]
 
 DECODERS = [
@@ -553,7 +722,7 @@ def on_launch(name, grid, block, args):
                     violations.append(f"{key}: {what} [{lo:#x}, {hi:#x}) outside the call's memory")
             if EXEC[0] and not bad:
                 for ekey, ex in EXECUTORS:
-                    if ekey in name and not (ekey == "fold_sym_kernel" and "fold_sym_split" in name):
+                    if ekey in name:
                         ex(g, args, name) if ex is ex_jstream_sym else ex(g, args)
                         break
             return
@@ -695,7 +864,7 @@ def build_case(n, naux, ks, sym, p, opts, want="JK"):
         J = buf((len(ks), n, n), "J", False) if "J" in want else None
         K = buf((len(ks), n, n), "K", False) if "K" in want else None
         st = lib.jk_build(h, ct.byref(f), len(ks), d, ptr(J), ptr(K), p, None)
-        if EXEC[0] and p == FP64 and st == 0:
+        if EXEC[0] and st == 0:
             Jo, Ko = oracle_mod().build(L, X, _ylist(X, Y, sym))
             if J is not None:
                 check("J", J, Jo)
@@ -711,7 +880,10 @@ def sliced_gemm_case(M, N, K, opts):
         lib.jk_debug_sliced_gemm_workspace.restype = ct.c_size_t
         nb = lib.jk_debug_sliced_gemm_workspace(M, N, K)
         h = handle(nb, opts)
-        return lib.jk_debug_sliced_gemm(h, M, N, K, ptr(A), ptr(B), ptr(C), None), h
+        st = lib.jk_debug_sliced_gemm(h, M, N, K, ptr(A), ptr(B), ptr(C), None)
+        if EXEC[0] and st == 0:
+            check("C", C, A.astype(np.longdouble) @ B.T.astype(np.longdouble))
+        return st, h
     return fn
 
 
@@ -757,7 +929,7 @@ def batched_case(shapes, p, opts):
         Jp = (ct.c_void_p * len(outs))(*[o[0].ctypes.data for o in outs])
         Kp = (ct.c_void_p * len(outs))(*[o[1].ctypes.data for o in outs])
         st = lib.jk_build_batched(h, len(fs), fa, (ct.c_int32 * len(ndm))(*ndm), da, Jp, Kp, p, None)
-        if EXEC[0] and p == FP64 and st == 0:
+        if EXEC[0] and st == 0:
             i = 0
             for m, (L, X, Y) in enumerate(mols):
                 Jo, Ko = oracle_mod().build(L, X, Y)
@@ -785,7 +957,7 @@ def host_case(n, naux, ks, p, opts, packed=False):
         J, K = buf((len(ks), n, n), "J", False), buf((len(ks), n, n), "K", False)
         call = lib.jk_build_host_packed if packed else lib.jk_build_host
         st = call(h, ct.byref(f), len(ks), d, ptr(J), ptr(K), p, None)
-        if EXEC[0] and p == FP64 and st == 0:
+        if EXEC[0] and st == 0:
             Jo, Ko = oracle_mod().build(L, X, Y)
             check("J", J, Jo)
             check("K", K, Ko)
@@ -805,7 +977,7 @@ def adjoint_case(n, naux, ks, sym, p, opts, want_dl=True):
         lib.jk_destroy(h)
         h = handle(nb, opts)
         st = lib.jk_adjoint(h, ct.byref(f), nd, d, ptr(W), ptr(V), ptr(dX), ptr(dY), ptr(dL), p, None)
-        if EXEC[0] and p == FP64 and st == 0:
+        if EXEC[0] and st == 0:
             dXo, dYo, dLo = oracle_mod().adjoint(L, X, _ylist(X, Y, sym), list(W), list(V), want_dl=want_dl)
             off = 0
             for s_, k in enumerate(ks):
@@ -834,7 +1006,7 @@ def dense_case(n, naux, nd, p, opts, grad=None):
         h = handle(nb, opts)
         if grad is None:
             st = lib.jk_build_dense(h, ct.byref(f), nd, ptr(A), ptr(O1), ptr(O2), p, None)
-            if EXEC[0] and p == FP64 and st == 0:
+            if EXEC[0] and st == 0:
                 Jo, Ko = oracle_mod().build_dense(L, A)
                 check("J", O1, Jo)
                 check("K", O2, Ko)
@@ -842,7 +1014,7 @@ def dense_case(n, naux, nd, p, opts, grad=None):
         W = A if "W" in grad else None
         V = B if "V" in grad else None
         st = lib.jk_density_grad(h, ct.byref(f), nd, ptr(W), ptr(V), ptr(O1), p, None)
-        if EXEC[0] and p == FP64 and st == 0:
+        if EXEC[0] and st == 0:
             check("G", O1, oracle_mod().density_grad(L, W, V, nd=nd))
         return st, h
     return fn
@@ -864,7 +1036,7 @@ def pair_case(n, naux, kl, sl, kr, sr, p, opts):
         h = handle(nb, opts)
         Jp, Kp = buf((len(kl), len(kr)), "Jp", False), buf((len(kl), len(kr)), "Kp", False)
         st = lib.jk_pair(h, ct.byref(f), len(kl), dl, len(kr), dr, ptr(Jp), ptr(Kp), p, None)
-        if EXEC[0] and p == FP64 and st == 0:
+        if EXEC[0] and st == 0:
             Jo, Ko = oracle_mod().pairs(L, XL, _ylist(XL, YL, sl), XR, _ylist(XR, YR, sr))
             check("Jp", Jp, Jo)
             check("Kp", Kp, Ko)
@@ -897,7 +1069,7 @@ def laplace_case(n, naux, m, nq, sym, weighted, p, opts):
         st = lib.jk_build_laplace(h, ct.byref(f), nq, alpha, w, m, ptr(CX), ptr(eX), 1,
                                   None if sym else ptr(CY), None if sym else ptr(eY), 0 if sym else -1,
                                   ptr(J), ptr(K), p, None)
-        if EXEC[0] and p == FP64 and st == 0:
+        if EXEC[0] and st == 0:
             Jo, Ko = oracle_mod().laplace(L, CX, eX, 1, CX if sym else CY, eX if sym else eY, 1 if sym else -1,
                                           np.array(alpha[:]), np.array(w[:]) if weighted else None)
             check("J", J, Jo)

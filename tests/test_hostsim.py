@@ -244,27 +244,29 @@ def test_tuned_build_matches_the_measured_launch_list(full_records):
     assert dict(got) == per_build and sum(per_build.values()) * 3 == 183
 
 
-FP64_CASES = [n for n in NAMES if "fp64" in n or n == "noalloc"]
+EXEC_CASES = [n for n in NAMES if not n.startswith("autotune")]
 
 
-def test_fp64_paths_compute_the_oracle(shim_dir):
-    """With the FP64 kernels' arithmetic executed in numpy at each launch (on
-    the memory standing in for the device's), every FP64 call, through the
-    library's own host code, reproduces the oracle."""
-    recs = _drive(shim_dir, ["--exec", *FP64_CASES])
-    assert sorted(recs) == sorted(FP64_CASES)
+def test_executed_calls_compute_the_oracle(shim_dir):
+    """With each kernel's arithmetic executed at launch (numpy, on the memory
+    standing in for the device's; the split GEMM as the exact product of its
+    rebuilt 48-bit operands), every call of both engines, through the
+    library's own host code, reproduces the oracle (the split paths to the
+    48-bit rounding of their operands)."""
+    recs = _drive(shim_dir, ["--exec", *EXEC_CASES])
+    assert sorted(recs) == sorted(EXEC_CASES)
     for name, rec in recs.items():
         assert rec["status"] == 0 and rec["checks"], (name, rec["error"])
         worst = max(c[1] for c in rec["checks"])
         assert worst < 1e-12, (name, rec["checks"])
 
 
-def test_random_fp64_cases_compute_the_oracle(shim_dir):
-    recs = _drive(shim_dir, ["--exec", "--fuzz=120,21"])
+def test_random_executed_cases_compute_the_oracle(shim_dir):
+    recs = _drive(shim_dir, ["--exec", "--fuzz=80,21"])
     checked = 0
     for name, rec in recs.items():
         assert rec["status"] == 0, (name, rec["error"])
         for label, err in rec["checks"]:
             assert err < 1e-12, (name, label, err)
             checked += 1
-    assert checked > 50
+    assert checked > 40
