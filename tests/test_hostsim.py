@@ -270,3 +270,17 @@ def test_random_executed_cases_compute_the_oracle(shim_dir):
             assert err < 1e-12, (name, label, err)
             checked += 1
     assert checked > 40
+
+
+REPEAT_EXEC = ["build_split", "build_fp64_chunks", "batched_split", "host_packed_split", "adjoint_split",
+               "dense_split_chunks", "grad_split_WV", "pairs_split", "laplace_split", "noalloc"]
+
+
+def test_repeat_calls_compute_the_oracle(shim_dir):
+    """A second call on the same handle (arena, streams and flags left by the
+    first) computes the oracle's values too."""
+    recs = _drive(shim_dir, ["--exec", "--twice", *REPEAT_EXEC])
+    for name in REPEAT_EXEC:
+        rec = recs[name]
+        assert rec["status"] == 0 and rec["checks"], (name, rec["error"])
+        assert max(c[1] for c in rec["checks"]) < 1e-12, (name, rec["checks"])
