@@ -111,12 +111,22 @@ struct Problem {
 
 jk_status set_error(jk_ctx *h, jk_status s, const char *fmt, ...);
 
+// The file name of a source path (messages name the file, not the directory
+// it was built in).
+inline const char *source_name(const char *path) {
+    const char *b = path;
+    for (const char *c = path; *c; ++c)
+        if (*c == '/' || *c == '\\') b = c + 1;
+    return b;
+}
+
 #define JK_CUDA_TRY(h, call)                                                   \
     do {                                                                       \
         cudaError_t e_ = (call);                                               \
         if (e_ != cudaSuccess)                                                 \
             return ::jk::set_error((h), JK_ERR_CUDA, "%s failed: %s (%s:%d)",  \
-                                   #call, cudaGetErrorString(e_), __FILE__,    \
+                                   #call, cudaGetErrorString(e_),              \
+                                   ::jk::source_name(__FILE__),                \
                                    __LINE__);                                  \
     } while (0)
 
@@ -125,7 +135,8 @@ jk_status set_error(jk_ctx *h, jk_status s, const char *fmt, ...);
         cudaError_t e_ = cudaGetLastError();                                   \
         if (e_ != cudaSuccess)                                                 \
             return ::jk::set_error((h), JK_ERR_CUDA, "launch failed: %s (%s:%d)", \
-                                   cudaGetErrorString(e_), __FILE__, __LINE__); \
+                                   cudaGetErrorString(e_),                      \
+                                   ::jk::source_name(__FILE__), __LINE__);      \
     } while (0)
 
 #define JK_TRY(expr)                                                           \

@@ -51,6 +51,8 @@ static int g_nvars;
 
 static struct { dim3 grid, block; size_t smem; void *stream; } g_cfg;
 static int g_fail_launch;
+static int g_fail_at = -1;   /* index (within the current case) of a launch made to fail, or -1 */
+static int g_launch_error;   /* a failed launch not yet reported by cudaGetLastError */
 static int g_ncopies;   /* memsets and copies enqueued on a stream */
 static int g_nsync;     /* calls that wait for the device (illegal while capturing a graph) */
 static int g_nsetup;    /* one-time set-up: streams, events, function attributes, symbol and entry lookups */
@@ -67,21 +69,29 @@ static int func_index(const void *host) {
     return -1;
 }
 
-static void record_launch(const void *host, dim3 grid, dim3 block, size_t smem, const unsigned *cluster,
-                          void **args) {
+/* Returns nonzero when this launch is the one made to fail (it is then not
+ * recorded and the kernel does not "run"). */
+static int record_launch(const void *host, dim3 grid, dim3 block, size_t smem, const unsigned *cluster,
+                         void **args) {
+    if (g_fail_at >= 0 && g_nlaunch == g_fail_at) {
+        g_fail_at = -1;
+        g_launch_error = 1;
+        return 1;
+    }
     if (g_hook) {
         const int f = func_index(host);
         const unsigned g[3] = {grid.x, grid.y, grid.z}, b[3] = {block.x, block.y, block.z};
         g_hook(f >= 0 ? g_funcs[f].name : "?", g, b, args);
     }
     if (!g_launch) g_launch = (Launch *)calloc(MAX_LAUNCH, sizeof(Launch));
-    if (g_nlaunch >= MAX_LAUNCH) { g_fail_launch = 1; return; }
+    if (g_nlaunch >= MAX_LAUNCH) { g_fail_launch = 1; return 0; }
     Launch *l = &g_launch[g_nlaunch++];
     l->func = func_index(host);
     l->grid[0] = grid.x; l->grid[1] = grid.y; l->grid[2] = grid.z;
     l->block[0] = block.x; l->block[1] = block.y; l->block[2] = block.z;
     l->smem = smem;
     for (int i = 0; i < 3; i++) l->cluster[i] = cluster ? cluster[i] : 1;
+    return 0;
 }
 
 /* ---- module registration and launch hooks -------------------------------- */
@@ -126,8 +136,8 @@ cudaError_t __cudaGetKernel(cudaKernel_t *k, const void *fun) { *k = (cudaKernel
 cudaError_t __cudaLaunchKernel(cudaKernel_t kernel, dim3 grid, dim3 block, void **args, size_t smem,
                                cudaStream_t stream) {
     (void)stream;
-    record_launch((const void *)kernel, grid, block, smem, NULL, args);
-    return cudaSuccess;
+    return record_launch((const void *)kernel, grid, block, smem, NULL, args) ? cudaErrorLaunchOutOfResources
+                                                                               : cudaSuccess;
 }
 
 cudaError_t cudaLaunchKernelExC(const cudaLaunchConfig_t *config, const void *func, void **args) {
@@ -138,7 +148,10 @@ cudaError_t cudaLaunchKernelExC(const cudaLaunchConfig_t *config, const void *fu
             cl[1] = config->attrs[i].val.clusterDim.y;
             cl[2] = config->attrs[i].val.clusterDim.z;
         }
-    record_launch(func, config->gridDim, config->blockDim, config->dynamicSmemBytes, cl, args);
+    if (record_launch(func, config->gridDim, config->blockDim, config->dynamicSmemBytes, cl, args)) {
+        g_launch_error = 0;   /* reported by the return value, as the runtime does */
+        return cudaErrorLaunchOutOfResources;
+    }
     return cudaSuccess;
 }
 
@@ -208,7 +221,13 @@ cudaError_t cudaEventSynchronize(cudaEvent_t e) { (void)e; g_nsync++; return cud
 cudaError_t cudaEventElapsedTime(float *ms, cudaEvent_t a, cudaEvent_t b) { (void)a; (void)b; *ms = 1.0f; return cudaSuccess; }
 cudaError_t cudaEventDestroy(cudaEvent_t e) { (void)e; return cudaSuccess; }
 
-cudaError_t cudaGetLastError(void) { return g_fail_launch ? cudaErrorLaunchFailure : cudaSuccess; }
+cudaError_t cudaGetLastError(void) {
+    if (g_launch_error) {
+        g_launch_error = 0;
+        return cudaErrorLaunchOutOfResources;
+    }
+    return g_fail_launch ? cudaErrorLaunchFailure : cudaSuccess;
+}
 const char *cudaGetErrorString(cudaError_t e) { return e == cudaSuccess ? "no error" : "host simulation error"; }
 
 /* ---- tensor maps ------------------------------------------------------------ */
@@ -266,6 +285,7 @@ int shim_var(int i, void **p, size_t *size) {
     return 1;
 }
 
+void shim_fail_launch_at(int i) { g_fail_at = i; g_launch_error = 0; }
 int shim_launch_count(void) { return g_nlaunch; }
 int shim_tmap_count(void) { return g_ntmap; }
 int shim_copy_count(void) { return g_ncopies; }

@@ -32,6 +32,8 @@ ENTRIES = {"jk_build", "jk_build_batched", "jk_build_host", "jk_build_host_packe
            "jk_density_grad", "jk_pair", "jk_build_laplace", "jk_build_noalloc", "jk_autotune", "jk_autotune_batched",
            "jk_debug_sliced_gemm"}
 TWICE = [False]       # call each entry point twice on its handle and record only the second call
+FAIL_AT = [-1]        # make this launch of the first call fail, then call again (--fail-launch=N)
+FIRST = {}            # status and message of that failed first call
 
 
 class _Lib:
@@ -44,6 +46,15 @@ class _Lib:
             return fn
 
         def call(*args):
+            if FAIL_AT[0] >= 0:
+                shim.shim_fail_launch_at(FAIL_AT[0])
+                st = fn(*args)
+                shim.shim_fail_launch_at(-1)
+                h = args[0] if name != "jk_build_noalloc" else None
+                FIRST.update(status=st, error=_lib.jk_last_error(h).decode() if h else "")
+                shim.shim_reset()
+                violations.clear()
+                decoded[0] = 0
             if TWICE[0]:
                 st = fn(*args)
                 if st != 0:
@@ -827,7 +838,7 @@ def record(name, status, h):
                       "strides": list(strides)[:r], "box": list(box)[:r]})
     err = lib.jk_last_error(h).decode() if h else ""
     print(json.dumps({"case": name, "status": status, "error": err, "launches": launches, "tmaps": tmaps,
-                      "copies": shim.shim_copy_count(), "syncs": shim.shim_sync_count(),
+                      "copies": shim.shim_copy_count(), "syncs": shim.shim_sync_count(), "first": dict(FIRST),
                       "setups": shim.shim_setup_count(),
                       "owned": [[o[0], o[1], o[2]] for o in owned + statics()], "violations": list(violations),
                       "checks": [[lab, float(np.abs(g - r).max() / max(np.abs(r).max(), 1e-300))]
@@ -840,6 +851,7 @@ def run(name, fn):
     violations.clear()
     undecoded.clear()
     CHECKS.clear()
+    FIRST.clear()
     decoded[0] = 0
     shim.shim_reset()
     try:
@@ -1236,6 +1248,9 @@ if __name__ == "__main__":
     if "--exec" in args:
         EXEC[0] = True
         args.remove("--exec")
+    for a in [a for a in args if a.startswith("--fail-launch=")]:
+        FAIL_AT[0] = int(a.split("=", 1)[1])
+        args.remove(a)
     names = args or list(CASES)
     for name in names:
         BIG[0] = name in FULL_CASES

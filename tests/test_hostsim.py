@@ -284,3 +284,24 @@ def test_repeat_calls_compute_the_oracle(shim_dir):
         rec = recs[name]
         assert rec["status"] == 0 and rec["checks"], (name, rec["error"])
         assert max(c[1] for c in rec["checks"]) < 1e-12, (name, rec["checks"])
+
+
+FAULT_CASES = ["build_split", "build_split_grouped_clustered", "build_fp64_chunks", "batched_split",
+               "host_packed_split", "adjoint_split", "dense_split_chunks", "grad_split_WV", "pairs_split",
+               "laplace_split_weighted_sym", "noalloc"]
+
+
+@pytest.mark.parametrize("at", [0, 1, 4])
+def test_failed_launch_is_reported_and_the_handle_recovers(shim_dir, at):
+    """A launch the runtime refuses (injected on the host) makes the call
+    return JK_ERR_CUDA with a message naming the failure; an immediate retry
+    on the same handle computes the oracle's values."""
+    recs = _drive(shim_dir, ["--exec", f"--fail-launch={at}", *FAULT_CASES])
+    for name in FAULT_CASES:
+        rec = recs[name]
+        first = rec["first"]
+        assert first["status"] == 4, (name, first)
+        if name != "noalloc":          # the arena-free build has no handle to hold a message
+            assert "failed" in first["error"] and "/" not in first["error"], (name, first)
+        assert rec["status"] == 0 and rec["checks"], (name, rec["error"])
+        assert max(c[1] for c in rec["checks"]) < 1e-12, (name, rec["checks"])
