@@ -76,7 +76,8 @@ typedef struct {
     const double *L;
 } jk_factor;
 
-/* One factored density D = X Y^T.  X, Y are [nbf][k] FP64 on the device.
+/* One factored density D = X Y^T.  X, Y are [nbf][k] FP64 on the device,
+ * 1 <= k <= 4 nbf and nbf*k <= 2^31 - 1.
  * symmetric != 0 means D = X X^T: Y is ignored (may be NULL). */
 typedef struct {
     int32_t k;
@@ -118,7 +119,8 @@ jk_status jk_workspace_query_handle(jk_handle h, jk_op op, int32_t nmol, const j
 
 /* jk_build: J_s and K_s for nd densities over one factor (Eq. 4, Sec. II.C).
  *   J, K : [nd][nbf][nbf] FP64 outputs; either may be NULL (not formed).
- * Status: JK_ERR_SHAPE if nbf < 1, naux < 1, nd < 1 or any k < 1;
+ * Status: JK_ERR_SHAPE if nbf is outside [1, 65535], naux < 1, nd is outside
+ *         [1, 64], or a density has k outside [1, 4 nbf] or nbf*k > 2^31 - 1;
  *         JK_ERR_OOM if the arena is smaller than jk_workspace_query says. */
 jk_status jk_build(jk_handle h, const jk_factor *f, int32_t nd,
                    const jk_density *d, double *J, double *K,

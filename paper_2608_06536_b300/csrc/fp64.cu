@@ -366,7 +366,7 @@ jk_status fp64_unpack_sym(jk_ctx *h, const double *packed, int n, long long np, 
     return JK_OK;
 }
 
-// y += x (FP64, elementwise)// y += x (FP64, elementwise)
+// y += x (FP64, elementwise)
 __global__ void axpy_kernel(double *y, const double *x, long long cnt) {
     long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (e < cnt) y[e] += x[e];

@@ -52,6 +52,9 @@ static jk_status make_problem(jk_ctx *h, const jk_factor *f, int nd,
     for (int s = 0; s < nd; s++) {
         if (d[s].k < 1 || d[s].k > f->nbf * 4)
             return set_error(h, JK_ERR_SHAPE, "density %d: k=%d out of range [1, 4*nbf]", s, d[s].k);
+        if (static_cast<long long>(f->nbf) * d[s].k > INT32_MAX)
+            return set_error(h, JK_ERR_SHAPE, "density %d: nbf*k=%lld exceeds 2^31-1", s,
+                             static_cast<long long>(f->nbf) * d[s].k);
         pb.k[s] = d[s].k;
         pb.sym[s] = d[s].symmetric ? 1 : 0;
         pb.X[s] = d[s].X;

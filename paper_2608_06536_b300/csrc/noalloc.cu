@@ -68,7 +68,8 @@ extern "C" jk_status jk_build_noalloc(const jk_factor *f, int32_t nd, const jk_d
     pb.L = f->L;
     int c = 0, kmax = 0, ksum = 0;
     for (int s = 0; s < nd; s++) {
-        if (d[s].k < 1 || d[s].k > f->nbf * 4) return JK_ERR_SHAPE;
+        if (d[s].k < 1 || d[s].k > f->nbf * 4 || static_cast<long long>(f->nbf) * d[s].k > INT32_MAX)
+            return JK_ERR_SHAPE;
         if (!d[s].X || (!d[s].symmetric && !d[s].Y)) return JK_ERR_ARG;
         if ((reinterpret_cast<uintptr_t>(d[s].X) & 15u) ||
             (!d[s].symmetric && (reinterpret_cast<uintptr_t>(d[s].Y) & 15u)))

@@ -65,12 +65,23 @@ def test_workspace_query_host_only(lib):
     assert lib.jk_workspace_query(jk.JK_OP_ADJOINT, 1, fa2, None, 1, d2, jk.JK_FP64, ct.byref(nb)) == jk.JK_OK
 
 
-@pytest.mark.parametrize("n,naux,k", [(0, 5, 1), (5, 0, 1), (5, 5, 0), (5, 5, 100)])
+@pytest.mark.parametrize("n,naux,k", [(0, 5, 1), (5, 0, 1), (5, 5, 0), (5, 5, 100), (65536, 1, 1),
+                                      (46341, 1, 46341), (50000, 1, 60000)])
 def test_workspace_query_rejects_bad_shapes(lib, n, naux, k):
     f, d = _one(n, naux, k)
     nb = ct.c_size_t()
     fa = (jk.jk_factor * 1)(f)
     assert lib.jk_workspace_query(jk.JK_OP_BUILD, 1, fa, None, 1, d, jk.JK_FP64, ct.byref(nb)) == jk.JK_ERR_SHAPE
+
+
+def test_density_width_limit(lib):
+    """nbf*k up to 2^31 - 1 is accepted, one more element is not (kernels index X_s with 32 bits)."""
+    nb = ct.c_size_t()
+    for n, k, want in [(46340, 46341, jk.JK_OK), (46341, 46341, jk.JK_ERR_SHAPE), (65535, 32768, jk.JK_OK),
+                       (65535, 32769, jk.JK_ERR_SHAPE)]:
+        f, d = _one(n, 1, k)
+        fa = (jk.jk_factor * 1)(f)
+        assert lib.jk_workspace_query(jk.JK_OP_BUILD, 1, fa, None, 1, d, jk.JK_FP64, ct.byref(nb)) == want, (n, k)
 
 
 def test_workspace_query_rejects_bad_args(lib):
@@ -180,7 +191,8 @@ def test_noalloc_host_checks(lib):
 
     assert call(J=None, K=None) == jk.JK_OK                  # nothing to form
     assert lib.jk_build_noalloc(None, 1, None, J, K, None) == jk.JK_ERR_ARG
-    for kw in [dict(n=0), dict(n=65536), dict(naux=0), dict(nd=0), dict(nd=65), dict(k=0), dict(k=41)]:
+    for kw in [dict(n=0), dict(n=65536), dict(naux=0), dict(nd=0), dict(nd=65), dict(k=0), dict(k=41),
+               dict(n=65535, k=32769)]:
         assert call(**kw) == jk.JK_ERR_SHAPE, kw
     for kw in [dict(L=0x1008), dict(X=0x2008), dict(J=ct.c_void_p(0x10008)), dict(K=ct.c_void_p(0x20008)),
                dict(L=0)]:
