@@ -19,10 +19,12 @@
 
 #include <stdint.h>
 
+#if !defined(JK_HD)
 #if defined(__CUDACC__)
 #define JK_HD __host__ __device__ __forceinline__
 #else
 #define JK_HD static inline
+#endif
 #endif
 
 namespace jk {

@@ -40,6 +40,7 @@
 #include <vector>
 
 #include "digits.cuh"
+#include "fixed.cuh"
 #include "jk_internal.h"
 #include "tc.cuh"
 
@@ -75,55 +76,10 @@ constexpr int SMEM_BYTES = NSTAGE * STAGE_BYTES + OUT_BYTES + 1024 /*align slack
 // Integer helpers
 // ---------------------------------------------------------------------------
 
-// Exponent e with max|x| < 2^e (from the biased exponent field of max|x|).
-// An all-zero group gets a very small exponent so it never sets the scale
-// when partial sums are aligned.
-__device__ __forceinline__ int exponent_of_max(unsigned long long maxbits) {
-    int ex = static_cast<int>((maxbits >> 52) & 0x7FF);
-    return ex == 0 ? -1000 : ex - 1022;
-}
-
-// F = round(x * 2^(48 - e)) as a signed integer, |F| <= 2^48 when |x| <= 2^e.
-// Zero and subnormal inputs give 0.
-__device__ __forceinline__ long long to_fixed48(double x, int e) {
-    const unsigned long long bits = static_cast<unsigned long long>(__double_as_longlong(x));
-    const int ex = static_cast<int>((bits >> 52) & 0x7FF);
-    if (ex == 0) return 0;
-    const unsigned long long m = (bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-    const int r = 1027 + e - ex;   // right shift of the 53-bit significand, >= 4
-    long long F;
-    if (r <= 0) F = static_cast<long long>(m << (-r));
-    else if (r >= 64) F = 0;
-    else F = static_cast<long long>((m + (1ull << (r - 1))) >> r);
-    return (bits >> 63) ? -F : F;
-}
-
-// v * 2^e2 rounded to nearest-even double, computed with integer operations.
-// Requires the result to be a normal double (true for all values built here).
-__device__ __forceinline__ double i64_to_f64_scaled(long long v, int e2) {
-    if (v == 0) return 0.0;
-    const unsigned long long sign = v < 0 ? 0x8000000000000000ull : 0ull;
-    unsigned long long a = v < 0 ? static_cast<unsigned long long>(-v) : static_cast<unsigned long long>(v);
-    int lz = __clzll(static_cast<long long>(a));
-    a <<= lz;                                   // leading one at bit 63
-    unsigned long long mant = a >> 11;          // 53 bits including the leading one
-    const unsigned long long rem = a & 0x7FFull;
-    if (rem > 0x400ull || (rem == 0x400ull && (mant & 1ull))) mant++;
-    int exp2 = 63 - lz + e2;
-    if (mant >> 53) { mant >>= 1; exp2++; }
-    const unsigned long long bits =
-        sign | (static_cast<unsigned long long>(exp2 + 1023) << 52) | (mant & 0xFFFFFFFFFFFFFull);
-    return __longlong_as_double(static_cast<long long>(bits));
-}
-
-__device__ __forceinline__ double i128_to_f64_scaled(__int128 v, int e2) {
-    // Split into a high part (exactly representable shift) and a low part.
-    const long long hi = static_cast<long long>(v >> 62);
-    const long long lo = static_cast<long long>(v - (static_cast<__int128>(hi) << 62));
-    // hi * 2^62 + lo, both converted exactly-rounded, summed in FP64 (one rounding step
-    // is negligible: |lo| < 2^62 and hi carries the leading bits).
-    return i64_to_f64_scaled(hi, e2 + 62) + i64_to_f64_scaled(lo, e2);
-}
+using fixed::exponent_of_max;
+using fixed::i128_to_f64_scaled;
+using fixed::i64_to_f64_scaled;
+using fixed::to_fixed48;
 
 // ---------------------------------------------------------------------------
 // Slicers
@@ -854,8 +810,9 @@ ozgemm_kernel(const __grid_constant__ OzGroup g) {
 }
 
 // out[r][c] (+)= sum_z P[z][r][c] 2^(eA[r/arpe][z] + eB[c/brpe][z] - 48).  The
-// partials are aligned to the largest scale by 128-bit shifts (52 guard bits)
-// and summed exactly; one rounding to FP64 at the end.
+// partials are aligned to the largest scale by 128-bit shifts (52 guard bits:
+// a partial on a smaller scale loses only bits below 2^-52 of the largest
+// scale's unit) and summed exactly; one rounding to FP64 at the end.
 __global__ void __launch_bounds__(256)
 reduce_partials_kernel(const long long *P, long long pz, long long ldp, int nz, int M, int N, const int *eA,
                        int arpe, const int *eB, int brpe, double *out, long long ldo, int accumulate) {
