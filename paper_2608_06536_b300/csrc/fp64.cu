@@ -13,6 +13,7 @@
 #include <cstdarg>
 
 #include "jk_internal.h"
+#include "packed.cuh"
 
 namespace jk {
 
@@ -242,17 +243,10 @@ jstream_kernel(const double *L, long long n2, int naux, const double *g,
 template <int NS>
 __global__ void __launch_bounds__(64)
 jstream_sym_kernel(const double *L, int n, int naux, const double *g, int ldg, OutTab Out) {
-    const long long ntri = (long long)n * (n + 1) / 2;
     const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (t >= ntri) return;
-    // row mu of the upper triangle starts at mu*n - mu*(mu-1)/2
-    const double nn = 2.0 * n + 1.0;
-    int mu = (int)((nn - sqrt(nn * nn - 8.0 * (double)t)) * 0.5);
-    if (mu < 0) mu = 0;
-    if (mu > n - 1) mu = n - 1;
-    while (mu > 0 && (long long)mu * n - (long long)mu * (mu - 1) / 2 > t) mu--;
-    while (mu < n - 1 && (long long)(mu + 1) * n - (long long)(mu + 1) * mu / 2 <= t) mu++;
-    const int nu = mu + (int)(t - ((long long)mu * n - (long long)mu * (mu - 1) / 2));
+    if (t >= packed::tri_count(n)) return;
+    int mu, nu;
+    packed::tri_row_col(n, t, &mu, &nu);
     const long long n2 = (long long)n * n;
     const long long e = (long long)mu * n + nu;
     double a[NS];
@@ -344,8 +338,8 @@ static jk_status pack_z(jk_ctx *h, const Problem &pb, double *Z, cudaStream_t st
 }
 
 // F[p][mu][nu] = P[p][t(min(mu,nu), max(mu,nu))] for p < np: symmetric L^P
-// expanded from its packed upper triangle, t(a, b) = a*n - a(a-1)/2 + (b - a)
-// (row-major upper triangle, diagonal included).  One thread per full entry.
+// expanded from its packed upper triangle (packed.cuh: row-major, diagonal
+// included).  One thread per full entry.
 __global__ void unpack_sym_kernel(const double *P, int n, long long np, double *F) {
     const long long n2 = (long long)n * n;
     const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -353,7 +347,7 @@ __global__ void unpack_sym_kernel(const double *P, int n, long long np, double *
     const long long p = e / n2, r = e - p * n2;
     const int mu = (int)(r / n), nu = (int)(r - (long long)mu * n);
     const long long a = mu < nu ? mu : nu, b = mu < nu ? nu : mu;
-    F[e] = P[p * (n2 + n) / 2 + a * n - a * (a - 1) / 2 + (b - a)];
+    F[e] = P[p * packed::tri_count(n) + packed::tri_index(n, a, b)];
 }
 
 jk_status fp64_unpack_sym(jk_ctx *h, const double *packed, int n, long long np, double *full, cudaStream_t st) {

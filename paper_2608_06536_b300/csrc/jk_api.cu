@@ -6,6 +6,7 @@
 #include <new>
 
 #include "jk_internal.h"
+#include "packed.cuh"
 
 namespace jk {
 
@@ -197,7 +198,7 @@ struct HostBufs {
 };
 
 // Doubles of one packed L^P (upper triangle, diagonal included).
-static long long tri_count(int n) { return static_cast<long long>(n) * (n + 1) / 2; }
+using packed::tri_count;
 
 static size_t host_xy_count(const Problem &pb) {
     size_t c = 0;
