@@ -1,7 +1,10 @@
-// Six-digit splitting of a 48-bit fixed-point value into BF16 slices with
-// FP32 additions (the slicer's alternative to integer digit extraction).
+// Six-digit splits of a 48-bit fixed-point value F (|F| <= 2^48) into BF16
+// slices, the slicer's two ways of forming them:
+//   digits6 + qbf16   32-bit integer digit extraction, then one exact FP32
+//                     conversion per digit (the default slicer);
+//   split48           FP32 additions only (JK_OPT_SLICER = 1), below.
 //
-// F (|F| <= 2^48) is cut into two exact halves, lo = F mod 2^24 and
+// split48: F is cut into two exact halves, lo = F mod 2^24 and
 // hi = F div 2^24, each converted to FP32 exactly and pre-scaled by a power
 // of two.  Each digit then costs three FP32 additions: adding and removing
 // 1.5 * 2^(k+23) rounds a value to a multiple of 2^k (round to nearest even,
@@ -14,10 +17,14 @@
 //
 // Host-compilable (for the CPU test of these properties): the additions use
 // __fadd_rn on the device, which the compiler may not contract or
-// reassociate, and plain IEEE additions on the host.
+// reassociate, and plain IEEE additions on the host; bit casts use the CUDA
+// intrinsics on the device and memcpy on the host.
 #pragma once
 
 #include <stdint.h>
+#if !defined(__CUDA_ARCH__)
+#include <string.h>
+#endif
 
 #if !defined(JK_HD)
 #if defined(__CUDACC__)
@@ -37,6 +44,49 @@ JK_HD float add_rn(float a, float b) {
     volatile float s = a + b;   // no excess precision, no reassociation
     return s;
 #endif
+}
+
+// Six balanced base-256 digits of F (|F| <= 2^48) in 32-bit integer
+// arithmetic: F = sum_j q_j 2^(8(5-j)), q_1..q_5 in [-128, 127] and
+// |q_0| <= 256 (the integer slicer's split of the same value).
+JK_HD void digits6(long long F, int q[6]) {
+    int lo = static_cast<int>(F & 0xFFFFFFll);        // [0, 2^24)
+    int hi = static_cast<int>(F >> 24);               // arithmetic shift
+    q[5] = ((lo + 128) & 255) - 128; lo = (lo - q[5]) >> 8;
+    q[4] = ((lo + 128) & 255) - 128; lo = (lo - q[4]) >> 8;
+    q[3] = ((lo + 128) & 255) - 128; lo = (lo - q[3]) >> 8;
+    hi += lo;
+    q[2] = ((hi + 128) & 255) - 128; hi = (hi - q[2]) >> 8;
+    q[1] = ((hi + 128) & 255) - 128; hi = (hi - q[1]) >> 8;
+    q[0] = hi;
+}
+
+JK_HD float f32_of_bits(uint32_t b) {
+#if defined(__CUDA_ARCH__)
+    return __uint_as_float(b);
+#else
+    float f;
+    memcpy(&f, &b, sizeof f);
+    return f;
+#endif
+}
+
+JK_HD uint32_t bits_of_f32(float f) {
+#if defined(__CUDA_ARCH__)
+    return __float_as_uint(f);
+#else
+    uint32_t b;
+    memcpy(&b, &f, sizeof b);
+    return b;
+#endif
+}
+
+// BF16 bits of q * scale for |q| <= 256 and a power-of-two scale: the integer
+// is formed exactly by the 1.5*2^23 bias trick and has at most 8 significant
+// bits, so after the exact scaling the low half of the FP32 word is zero.
+JK_HD uint32_t qbf16(int q, float scale) {
+    const float f = (f32_of_bits(static_cast<uint32_t>(0x4B400000 + q)) - 12582912.0f) * scale;
+    return bits_of_f32(f) >> 16;
 }
 
 // x rounded to a multiple of 2^k, M = 1.5 * 2^(k+23); exact for |x| <= 2^(k+22).

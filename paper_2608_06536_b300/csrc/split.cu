@@ -140,27 +140,8 @@ __global__ void __launch_bounds__(256) expo_kernel(Src src, int rows, int K, int
     }
 }
 
-// Six balanced base-256 digits of F (|F| <= 2^48): F = sum_j q_j 2^(8(6-j)),
-// q_2..q_6 in [-128, 127], |q_1| <= 256.  32-bit integer arithmetic only.
-__device__ __forceinline__ void digits6(long long F, int q[S]) {
-    int lo = static_cast<int>(F & 0xFFFFFFll);        // [0, 2^24)
-    int hi = static_cast<int>(F >> 24);               // arithmetic shift
-    q[5] = ((lo + 128) & 255) - 128; lo = (lo - q[5]) >> 8;
-    q[4] = ((lo + 128) & 255) - 128; lo = (lo - q[4]) >> 8;
-    q[3] = ((lo + 128) & 255) - 128; lo = (lo - q[3]) >> 8;
-    hi += lo;
-    q[2] = ((hi + 128) & 255) - 128; hi = (hi - q[2]) >> 8;
-    q[1] = ((hi + 128) & 255) - 128; hi = (hi - q[1]) >> 8;
-    q[0] = hi;
-}
-
-// BF16 bits of q * 2^(-8(j+1)) for |q| <= 256: exact through FP32 (the integer
-// is formed with the 1.5*2^23 add, scaled by a power of two, and has at most
-// 8 significant bits, so the low half of the FP32 word is zero).
-__device__ __forceinline__ uint32_t qbf16(int q, float scale) {
-    const float f = (__int_as_float(0x4B400000 + q) - 12582912.0f) * scale;
-    return __float_as_uint(f) >> 16;
-}
+using digits::digits6;
+using digits::qbf16;
 
 // Vector slicer: 4 consecutive reduction elements per thread.  Requires
 // src.ski == 1, src.kin % 4 == 0, K % 4 == 0 and 16-byte aligned pairs

@@ -1,9 +1,11 @@
-// TEST INFRASTRUCTURE: checks jk::digits::split48 (csrc/digits.cuh, compiled
+// TEST INFRASTRUCTURE: checks both digit splits of csrc/digits.cuh (compiled
 // here as host C++) against the properties the slicer relies on, for random
 // and edge-case fixed-point values F, |F| <= 2^48:
-//   sum_j v_j * 2^48 == F exactly; |q_0| <= 256, |q_j| <= 128 (j >= 1) with
-//   q_j = v_j * 2^(8(j+1)) an integer; every v_j an exact BF16 value (the low
-//   16 bits of its FP32 word are zero).
+//   split48: sum_j v_j * 2^48 == F exactly; |q_0| <= 256, |q_j| <= 128
+//   (j >= 1) with q_j = v_j * 2^(8(j+1)) an integer; every v_j an exact BF16
+//   value (the low 16 bits of its FP32 word are zero).
+//   digits6 + qbf16: the same bounds and exact sum for the integer digits,
+//   and qbf16(q_j, 2^-8(j+1)) is the BF16 encoding of q_j * 2^-8(j+1).
 // Prints "ok <count>" and exits 0, or the first violation and exits 1.
 #include <cmath>
 #include <cstdint>
@@ -33,6 +35,30 @@ static int check(long long F) {
     }
     if (sum != static_cast<__int128>(F)) {
         std::printf("F=%lld: digits sum to %lld\n", F, static_cast<long long>(sum));
+        return 1;
+    }
+    // the integer path
+    int q[6];
+    jk::digits::digits6(F, q);
+    __int128 isum = 0;
+    float sc = 0.00390625f;
+    for (int j = 0; j < 6; j++) {
+        if (q[j] > (j == 0 ? 256 : 127) || q[j] < (j == 0 ? -256 : -128)) {
+            std::printf("F=%lld: integer digit %d = %d out of range\n", F, j, q[j]);
+            return 1;
+        }
+        const uint32_t w = jk::digits::qbf16(q[j], sc) << 16;
+        float back;
+        std::memcpy(&back, &w, 4);
+        if (static_cast<double>(back) != std::ldexp(static_cast<double>(q[j]), -8 * (j + 1))) {
+            std::printf("F=%lld: qbf16(%d) of slice %d is %a\n", F, q[j], j, back);
+            return 1;
+        }
+        isum += static_cast<__int128>(q[j]) << (8 * (5 - j));
+        sc *= 0.00390625f;
+    }
+    if (isum != static_cast<__int128>(F)) {
+        std::printf("F=%lld: integer digits sum to %lld\n", F, static_cast<long long>(isum));
         return 1;
     }
     return 0;

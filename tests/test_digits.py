@@ -1,8 +1,10 @@
-"""The FP32 digit split of the slicer (csrc/digits.cuh), compiled as host C++
-and checked on the CPU over random and edge-case 48-bit values: the six BF16
+"""Both digit splits of the slicer (csrc/digits.cuh: the integer digits6 with
+its BF16 encoding qbf16, and the FP32-addition split48), compiled as host C++
+and checked on the CPU over random and edge-case 48-bit values: the six
 digits sum exactly to the value, stay within the bounds the GEMM's exact
 accumulation windows assume (|q_0| <= 256, |q_j| <= 128), and are exact BF16
-values.  The same source compiles into the device kernel (slice4f_kernel)."""
+values.  The same source compiles into the device kernels (slice_kernel,
+slice4_kernel, slice4f_kernel)."""
 import os
 import subprocess
 
