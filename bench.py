@@ -237,6 +237,7 @@ def run_ours(args, rank, world, local):
     Yd = [torch.from_numpy(y).to(dev) for y in m.Y]
     eng = jk.Engine(dev)
     eng.set_option("slicer", args.slicer)
+    eng.set_option("syrk", args.syrk)
     prec = args.precision
     st = torch.cuda.current_stream(dev)
 
@@ -288,6 +289,7 @@ def run_ours(args, rank, world, local):
             print(json.dumps({"case": args.case, "engine": prec, "ms_per_step": ms_max, "value": value,
                               "kernels_ms": {k: v[0] / args.steps for k, v in prof.items()},
                               "launches_per_step": launches / args.steps, "tuned": tuned, "slicer": args.slicer,
+                              "syrk": args.syrk,
                               "issued_tensor_tflops": issued / args.steps / (ms_max * 1e-3) / 1e12}),
                   flush=True)
         return
@@ -365,7 +367,8 @@ def run_ours(args, rank, world, local):
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "engine": prec, "nbf": n, "naux": naux, "nd": len(ks),
                    "k": ks[0], "l2": "inputs larger than L2 (L = 3.07 GB FP64), no flush",
-                   "parallelism": f"replicas x{world}", "tuned": tuned, "slicer": args.slicer},
+                   "parallelism": f"replicas x{world}", "tuned": tuned, "slicer": args.slicer,
+                   "syrk": args.syrk},
         "e2e": e2e,
         "gpu_launches": int(launches),
         "launches_per_step": launches / args.steps,
@@ -543,6 +546,9 @@ def main():
                     help="fixed run-time configuration aux_chunk,schedule,raster,cluster (skips the autotuner)")
     ap.add_argument("--slicer", type=int, choices=[0, 1], default=0,
                     help="digit extraction of the vector slicer: 0 integer (default), 1 FP32 additions")
+    ap.add_argument("--syrk", type=int, choices=[0, 1], default=0,
+                    help="symmetric densities (split engine): 0 full rank update (default), "
+                         "1 blocked symmetric rank update, the rest mirrored")
     ap.add_argument("--e2e-packed", dest="e2e_packed", action="store_true",
                     help="end-to-end leg with the factor on the host as packed upper triangles "
                          "(jk_build_host_packed: half the bytes over the host link)")

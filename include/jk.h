@@ -297,11 +297,17 @@ typedef enum {
                                clusters sharing an operand tile by TMA multicast  */
     JK_OPT_HOST_CHUNK = 5,  /* jk_build_host: aux indices per streamed chunk of
                                the factor, 0 = automatic (about 12 chunks)         */
-    JK_OPT_SLICER = 6       /* digit extraction of the split engine's vector
+    JK_OPT_SLICER = 6,      /* digit extraction of the split engine's vector
                                slicer: 0 (default) integer arithmetic, 1 FP32
                                additions (fewer instructions per element; an
                                equally exact split, digits differ only where a
                                digit rounds a tie)                               */
+    JK_OPT_SYRK = 7         /* split engine, symmetric densities: 0 (default)
+                               full rank update, 1 only the row blocks of
+                               128 rows from their diagonal on (K of the
+                               symmetric build, the U = V case of Sec. II.C,
+                               is symmetric), the rest mirrored; results
+                               within rounding of those of 0                  */
 } jk_option;
 /* Options set explicitly on a handle override tuned configurations. */
 jk_status jk_set_option(jk_handle h, jk_option opt, int64_t value);

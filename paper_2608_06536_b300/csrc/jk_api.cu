@@ -1113,6 +1113,11 @@ jk_status jk_set_option(jk_handle h, jk_option opt, int64_t value) {
         h->slicer = static_cast<int>(value);
         return JK_OK;
     }
+    if (opt == JK_OPT_SYRK) {
+        if (value != 0 && value != 1) return set_error(h, JK_ERR_ARG, "JK_OPT_SYRK takes 0 or 1");
+        h->syrk = static_cast<int>(value);
+        return JK_OK;
+    }
     if (opt == JK_OPT_USE_TUNED) {
         if (value != 0 && value != 1) return set_error(h, JK_ERR_ARG, "JK_OPT_USE_TUNED takes 0 or 1");
         h->use_tuned = static_cast<int>(value);

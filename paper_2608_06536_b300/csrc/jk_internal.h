@@ -77,7 +77,8 @@ struct jk_ctx {
     int max_clusters = 0;    // resident 2-CTA clusters of the sliced GEMM (0 = not yet queried)
     bool gemm_smem_set = false;   // the sliced GEMM's shared-memory attribute is set on this device
     int host_chunk = 0;      // aux indices per streamed chunk of a host-resident factor (0 = automatic)
-    int slicer = 0;          // digit extraction of the vector slicer: 0 integer, 1 FP32 additions
+    int slicer = 0;
+    int syrk = 0;            // split engine: symmetric rank updates by row blocks, rest mirrored          // digit extraction of the vector slicer: 0 integer, 1 FP32 additions
     cudaStream_t copy_stream = nullptr;   // host builds: uploads of the factor, created on first use
     cudaEvent_t ev_fork = nullptr, ev_up[2] = {nullptr, nullptr}, ev_used[2] = {nullptr, nullptr};
     cudaStream_t aux_stream = nullptr;    // FP64 J streams overlapped with the rank updates

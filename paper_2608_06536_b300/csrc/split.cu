@@ -816,6 +816,16 @@ reduce_partials_kernel(const long long *P, long long pz, long long ldp, int nz, 
     *o = accumulate ? (*o + v) : v;
 }
 
+// K[r][c] = K[c][r] for the entries a blocked symmetric rank update leaves
+// unformed: c < bm * (r / bm), left of row r's diagonal block (those (c, r)
+// all lie in the formed blocks, so no entry is both read and written).
+__global__ void __launch_bounds__(256) mirror_blocks_kernel(double *K, int n, int bm) {
+    const long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
+    if (e >= static_cast<long long>(n) * n) return;
+    const int r = static_cast<int>(e / n), c = static_cast<int>(e - static_cast<long long>(r) * n);
+    if (c < bm * (r / bm)) K[e] = K[static_cast<long long>(c) * n + r];
+}
+
 }  // namespace oz
 
 // ---------------------------------------------------------------------------
@@ -849,13 +859,15 @@ EncodeTiledFn encode_fn() {
 }
 
 // Tensor map over slices [S][rows][Kpad] (bf16), box = {16, box_rows, S}, 32-byte swizzle.
+// Consecutive planes lie plane_rows * Kpad elements apart (plane_rows >= rows:
+// a map over a block of rows of a larger sliced operand).
 jk_status make_slice_map(jk_ctx *h, CUtensorMap *map, const __nv_bfloat16 *base, int rows, int Kpad,
-                         int box_rows, int box_planes = oz::S) {
+                         int box_rows, long long plane_rows, int box_planes = oz::S) {
     EncodeTiledFn fn = encode_fn();
     if (!fn) return set_error(h, JK_ERR_CUDA, "cuTensorMapEncodeTiled is unavailable");
     cuuint64_t dims[3] = {static_cast<cuuint64_t>(Kpad), static_cast<cuuint64_t>(rows),
                           static_cast<cuuint64_t>(oz::S)};
-    cuuint64_t strides[2] = {static_cast<cuuint64_t>(Kpad) * 2, static_cast<cuuint64_t>(rows) * Kpad * 2};
+    cuuint64_t strides[2] = {static_cast<cuuint64_t>(Kpad) * 2, static_cast<cuuint64_t>(plane_rows) * Kpad * 2};
     cuuint32_t box[3] = {oz::KB, static_cast<cuuint32_t>(box_rows), static_cast<cuuint32_t>(box_planes)};
     cuuint32_t estr[3] = {1, 1, 1};
     CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<__nv_bfloat16 *>(base), dims, strides,
@@ -891,11 +903,26 @@ inline long long part_rows(long long M) { return (M + oz::BM - 1) / oz::BM * oz:
 }  // namespace
 
 // A sliced operand: S bf16 slices [S][rows][Kpad] plus per-group exponents.
+// A row view (row_view) addresses rows [r0, r1) of a larger operand: its
+// planes keep the parent's spacing of prows rows.
 struct Sliced {
     __nv_bfloat16 *s = nullptr;
     int *e = nullptr;
     int rows = 0, K = 0, Kpad = 0, rpe = 1;
+    int prows = 0;      // rows between consecutive planes (0: rows)
+    long long plane_rows() const { return prows > 0 ? prows : rows; }
 };
+
+// Rows [r0, r1) of a sliced operand (r0 a multiple of its exponent group).
+static Sliced row_view(const Sliced &S, int r0, int r1) {
+    Sliced v = S;
+    const long long nsc = (S.K + oz::SUPER - 1) / oz::SUPER;
+    v.s = S.s + static_cast<long long>(r0) * S.Kpad;
+    v.e = S.e + static_cast<long long>(r0 / S.rpe) * nsc;
+    v.rows = r1 - r0;
+    v.prows = static_cast<int>(S.plane_rows());
+    return v;
+}
 
 static jk_status slice_operand(jk_ctx *h, const oz::Src &src, int rows, int K, int rpe, Sliced &out,
                                cudaStream_t st) {
@@ -963,8 +990,8 @@ static jk_status oz_problem(jk_ctx *h, const Sliced &A, const Sliced &B, double 
                             oz::OzProb &pr) {
     if (A.K != B.K) return set_error(h, JK_ERR_ARG, "internal: sliced K mismatch");
     std::memset(&pr, 0, sizeof pr);
-    JK_TRY(make_slice_map(h, &pr.tmA, A.s, A.rows, A.Kpad, oz::BM));
-    JK_TRY(make_slice_map(h, &pr.tmB, B.s, B.rows, B.Kpad, oz::BN));
+    JK_TRY(make_slice_map(h, &pr.tmA, A.s, A.rows, A.Kpad, oz::BM, A.plane_rows()));
+    JK_TRY(make_slice_map(h, &pr.tmB, B.s, B.rows, B.Kpad, oz::BN, B.plane_rows()));
     oz::OzArgs &a = pr.a;
     a.M = A.rows; a.N = B.rows; a.K = A.K; a.nsuper = nsuper_of(A.K);
     a.eA = A.e; a.a_rpe = A.rpe; a.eB = B.e; a.b_rpe = B.rpe;
@@ -996,8 +1023,8 @@ static jk_status oz_problem(jk_ctx *h, const Sliced &A, const Sliced &B, double 
         pr.pair_n = rows_n <= rows_m ? 1 : 0;
         if (pr.pair_n) pr.un = static_cast<int>((ntn + 1) / 2);
         else pr.um = static_cast<int>((ntm + 1) / 2);
-        if (pr.pair_n) JK_TRY(make_slice_map(h, &pr.tmS, A.s, A.rows, A.Kpad, oz::BM, oz::S / 2));
-        else JK_TRY(make_slice_map(h, &pr.tmS, B.s, B.rows, B.Kpad, oz::BN, oz::S / 2));
+        if (pr.pair_n) JK_TRY(make_slice_map(h, &pr.tmS, A.s, A.rows, A.Kpad, oz::BM, A.plane_rows(), oz::S / 2));
+        else JK_TRY(make_slice_map(h, &pr.tmS, B.s, B.rows, B.Kpad, oz::BN, B.plane_rows(), oz::S / 2));
     }
     // Issued MMA work: every tile (virtual pair members included) runs all 21
     // slice pairs over its K-blocks.
@@ -1086,6 +1113,71 @@ static jk_status reduce_partials(jk_ctx *h, const long long *P, int nz, const Sl
         oz::reduce_partials_kernel<<<static_cast<unsigned>((tot + 255) / 256), 256, 0, st>>>(
             P, part_rows(A.rows) * ldp, ldp, nz, A.rows, B.rows, A.e, A.rpe, B.e, B.rpe, out, ldo,
             accumulate ? 1 : 0);
+    }
+    JK_LAUNCH_CHECK(h);
+    return JK_OK;
+}
+
+// ---- symmetric rank updates (JK_OPT_SYRK) -----------------------------------
+// K_s = T_X T_X^T of a symmetric density is symmetric.  Row block i (rows
+// [r0, r1) = [BM i, BM (i+1)) of T_X) is multiplied by rows [r0, n) only: one
+// GEMM problem per block on row views of the same sliced operand, forming
+// every entry on or above the diagonal (and the lower half of the diagonal
+// blocks); mirror_blocks_kernel fills the rest from its transpose once all
+// aux chunks are summed.  For n = 400 that is 12 output tiles instead of 20.
+struct SymPart {
+    Sliced A, B;
+    long long out_off;   // offset of the block in the n x n output
+    long long p_off;     // offset of its int64 partials (nsuper > 1)
+};
+
+static std::vector<SymPart> sym_parts(const Sliced &TX, int n, int nsuper) {
+    std::vector<SymPart> v;
+    long long p = 0;
+    for (int r0 = 0; r0 < n; r0 += oz::BM) {
+        const int r1 = std::min(n, r0 + oz::BM);
+        SymPart sp{row_view(TX, r0, r1), row_view(TX, r0, n), static_cast<long long>(r0) * n + r0, p};
+        if (nsuper > 1) p += static_cast<long long>(nsuper) * part_rows(r1 - r0) * even_ld(n - r0);
+        v.push_back(sp);
+    }
+    return v;
+}
+
+// Partial words of one blocked symmetric rank update (at most those of the full one).
+static long long sym_partial_words(int n, int nsuper) {
+    long long w = 0;
+    for (int r0 = 0; r0 < n; r0 += oz::BM)
+        w += static_cast<long long>(nsuper) * part_rows(std::min(n, r0 + oz::BM) - r0) * even_ld(n - r0);
+    return w;
+}
+
+// Append the problems of the blocked symmetric rank update of TX (nsuper ==
+// 1: FP64 into C, row stride n; otherwise int64 partials from P).
+static jk_status sym_rank_problems(jk_ctx *h, const Sliced &TX, int n, double *C, long long *P,
+                                   std::vector<oz::OzProb> &probs) {
+    const int ns = nsuper_of(TX.K);
+    for (const SymPart &sp : sym_parts(TX, n, ns)) {
+        probs.emplace_back();
+        if (ns == 1) JK_TRY(oz_problem(h, sp.A, sp.B, C + sp.out_off, n, nullptr, probs.back()));
+        else JK_TRY(oz_problem(h, sp.A, sp.B, nullptr, 0, P + sp.p_off, probs.back()));
+    }
+    return JK_OK;
+}
+
+// The split-K reductions of those problems into K (+= when accumulate).
+static jk_status sym_rank_reduce(jk_ctx *h, const Sliced &TX, int n, const long long *P, double *K, bool accumulate,
+                                 cudaStream_t st) {
+    const int ns = nsuper_of(TX.K);
+    for (const SymPart &sp : sym_parts(TX, n, ns))
+        JK_TRY(reduce_partials(h, P + sp.p_off, ns, sp.A, sp.B, K + sp.out_off, n, accumulate, st));
+    return JK_OK;
+}
+
+static jk_status mirror_blocks(jk_ctx *h, double *K, int n, cudaStream_t st) {
+    const long long n2 = static_cast<long long>(n) * n;
+    {
+        LaunchScope ls(h, KK_MISC, st);
+        oz::mirror_blocks_kernel<<<static_cast<unsigned>((n2 + 255) / 256), 256, 0, st>>>(K, n, oz::BM);
     }
     JK_LAUNCH_CHECK(h);
     return JK_OK;
@@ -1237,6 +1329,20 @@ jk_status split_build(jk_ctx *h, const Problem &pb, cudaStream_t st) {
             }
             double *Kout = pb.K[s];
             const int ns = nsuper_of(Kr);
+            if (pb.sym[s] && h->syrk) {
+                // blocked symmetric rank update (mirrored after the last chunk)
+                std::vector<oz::OzProb> probs;
+                double *dst = P0 == 0 ? Kout : Kacc + s * n2;
+                JK_TRY(sym_rank_problems(h, TX[s], n, dst, Pcur, probs));
+                JK_TRY(oz_launch(h, probs, st));
+                if (ns > 1) {
+                    JK_TRY(sym_rank_reduce(h, TX[s], n, Pcur, Kout, P0 > 0, st));
+                    Pcur += sym_partial_words(n, ns);
+                } else if (P0 > 0) {
+                    JK_TRY(fp64_axpy(h, Kout, dst, n2, st));
+                }
+                continue;
+            }
             if (ns == 1) {
                 if (P0 == 0) {
                     JK_TRY(ozgemm(h, TX[s], *B, Kout, n, nullptr, st));
@@ -1253,6 +1359,9 @@ jk_status split_build(jk_ctx *h, const Problem &pb, cudaStream_t st) {
             }
         }
     }
+    if (pb.wantK && h->syrk)
+        for (int s = 0; s < nd; s++)
+            if (pb.sym[s]) JK_TRY(mirror_blocks(h, pb.K[s], n, st));
     if (pb.wantJ) JK_TRY(join_jstream(h, st));
     return JK_OK;
 }
@@ -1709,6 +1818,18 @@ jk_status split_batched(jk_ctx *h, int nmol, const Problem *pbs, cudaStream_t st
             for (int s = 0; s < pb.nd; s++) {
                 const Sliced &B = pb.sym[s] ? it.TX[s] : it.TY[s];
                 const int ns = nsuper_of(it.np * pb.k[s]);
+                if (pb.sym[s] && h->syrk) {
+                    // blocked symmetric rank update (mirrored after the last wave)
+                    double *dst = it.P0 == 0 ? pb.K[s] : it.tmp + s * n2;
+                    JK_TRY(sym_rank_problems(h, it.TX[s], pb.n, dst, Pcur, probs));
+                    if (ns > 1) {
+                        reds.push_back({&it, s, Pcur, nullptr});
+                        Pcur += sym_partial_words(pb.n, ns);
+                    } else if (it.P0 > 0) {
+                        reds.push_back({&it, s, nullptr, dst});
+                    }
+                    continue;
+                }
                 probs.emplace_back();
                 if (ns == 1) {
                     double *out = it.P0 == 0 ? pb.K[s] : it.tmp + s * n2;
@@ -1727,7 +1848,9 @@ jk_status split_batched(jk_ctx *h, int nmol, const Problem *pbs, cudaStream_t st
             const Problem &pb = pbs[r.it->mol];
             const long long n2 = static_cast<long long>(pb.n) * pb.n;
             const Sliced &B = pb.sym[r.s] ? r.it->TX[r.s] : r.it->TY[r.s];
-            if (r.P) {
+            if (r.P && pb.sym[r.s] && h->syrk) {
+                JK_TRY(sym_rank_reduce(h, r.it->TX[r.s], pb.n, r.P, pb.K[r.s], r.it->P0 > 0, st));
+            } else if (r.P) {
                 JK_TRY(reduce_partials(h, r.P, nsuper_of(r.it->np * pb.k[r.s]), r.it->TX[r.s], B, pb.K[r.s], pb.n,
                                        r.it->P0 > 0, st));
             } else {
@@ -1736,6 +1859,11 @@ jk_status split_batched(jk_ctx *h, int nmol, const Problem *pbs, cudaStream_t st
         }
         w0 = w1;
     }
+    if (h->syrk)
+        for (int m = 0; m < nmol; m++)
+            if (pbs[m].wantK)
+                for (int s = 0; s < pbs[m].nd; s++)
+                    if (pbs[m].sym[s]) JK_TRY(mirror_blocks(h, pbs[m].K[s], pbs[m].n, st));
     if (forked) JK_TRY(join_jstream(h, st));
     return JK_OK;
 }

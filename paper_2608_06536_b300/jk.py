@@ -42,10 +42,11 @@ class jk_tune_config(ct.Structure):
                 "cluster": self.cluster}
 
 
-OPTIONS = {"aux_chunk": 0, "schedule": 1, "raster": 2, "use_tuned": 3, "cluster": 4, "host_chunk": 5, "slicer": 6}
+OPTIONS = {"aux_chunk": 0, "schedule": 1, "raster": 2, "use_tuned": 3, "cluster": 4, "host_chunk": 5, "slicer": 6,
+           "syrk": 7}
 # each option's value on a fresh handle (-1: not set, tuned or default configuration)
 OPTION_DEFAULTS = {"aux_chunk": -1, "schedule": -1, "raster": -1, "use_tuned": 1, "cluster": -1, "host_chunk": 0,
-                   "slicer": 0}
+                   "slicer": 0, "syrk": 0}
 
 
 class JKError(RuntimeError):
@@ -339,7 +340,9 @@ class Engine:
         """Handle option (JK_OPT_*): "aux_chunk" (>= 0, 0 = automatic, -1 =
         tuned/default), "schedule", "raster" and "cluster" (-1 = tuned/default,
         0, 1), "use_tuned" (0 or 1), "host_chunk" (>= 0, 0 = automatic),
-        "slicer" (0 integer digits, 1 FP32 digits).  Kept across arena growth."""
+        "slicer" (0 integer digits, 1 FP32 digits), "syrk" (split engine,
+        symmetric densities: 0 full rank update, 1 blocked symmetric rank
+        update with the rest mirrored).  Kept across arena growth."""
         code = OPTIONS[name]
         self._opts[code] = int(value)
         if self._h:

@@ -71,7 +71,8 @@ shim = ct.CDLL("libcudart.so.13")
 shim.shim_launch.restype = ct.c_char_p
 assert hasattr(shim, "shim_reset"), "the stand-in runtime is not the one loaded"
 
-OPT = {"aux_chunk": 0, "schedule": 1, "raster": 2, "use_tuned": 3, "cluster": 4, "host_chunk": 5, "slicer": 6}
+OPT = {"aux_chunk": 0, "schedule": 1, "raster": 2, "use_tuned": 3, "cluster": 4, "host_chunk": 5, "slicer": 6,
+       "syrk": 7}
 
 # ---- kernel arguments ----------------------------------------------------------
 # Each decoder reads one kernel's arguments (layouts as in the CUDA sources)
@@ -227,6 +228,12 @@ def dec_jstream_sym(grid, args, name):
 def dec_axpy(grid, args):
     y, x, cnt = _v(args, 0, VP), _v(args, 1, VP), _v(args, 2, I64)
     return [(y, y + 8 * cnt, "y"), (x, x + 8 * cnt, "x")]
+
+
+def dec_mirror_blocks(grid, args):
+    K, n, bm = _v(args, 0, VP), _v(args, 1, I32), _v(args, 2, I32)
+    assert bm >= 1 and grid[0] * 256 >= n * n, (grid, n)
+    return [(K, K + 8 * n * n, "K")]
 
 
 def dec_sum_parts(grid, args):
@@ -429,6 +436,14 @@ def ex_axpy(grid, args):
     dv(y, cnt)[:] += dv(x, cnt)
 
 
+def ex_mirror_blocks(grid, args):
+    K, n, bm = _v(args, 0, VP), _v(args, 1, I32), _v(args, 2, I32)
+    M = dv(K, n * n).reshape(n, n)
+    r, c = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    mask = c < bm * (r // bm)
+    M[mask] = M.T.copy()[mask]
+
+
 def ex_sum_parts(grid, args):
     out, part, nb, cnt, acc = _v(args, 0, VP), _v(args, 1, VP), _v(args, 2, I32), _v(args, 3, I64), _v(args, 4, I32)
     tot = dv(part, nb * cnt).reshape(nb, cnt).sum(axis=0)
@@ -590,10 +605,13 @@ def _operand(tm, e, rpe, rows, K, nsuper):
     """Rebuilt operand values in units of 2^(exponent): [rows][K] float64, and
     the exponents [rows][nsuper]."""
     Kpad, nrows = tm["dims"][0], tm["dims"][1]
-    planes = uv(tm["base"], NSLICE * nrows * Kpad, np.uint16).reshape(NSLICE, nrows, Kpad)[:, :rows, :K]
+    assert tm["strides"][1] == 2 * Kpad, tm
+    pstride = tm["strides"][2] // 2              # elements between planes (a row view keeps its parent's)
+    flat = uv(tm["base"], (NSLICE - 1) * pstride + nrows * Kpad, np.uint16)
     vals = np.zeros((rows, K))
     for j in range(NSLICE):
-        vals += (planes[j].astype(np.uint32) << 16).view(np.float32).astype(np.float64)
+        plane = flat[j * pstride:j * pstride + nrows * Kpad].reshape(nrows, Kpad)[:rows, :K]
+        vals += (plane.astype(np.uint32) << 16).view(np.float32).astype(np.float64)
     ev = uv(e, ((rows - 1) // rpe + 1) * nsuper, np.int32).reshape(-1, nsuper)[np.arange(rows) // rpe]
     return vals, ev
 
@@ -678,7 +696,7 @@ EXECUTORS = [
     ("expo_flat_kernel", ex_expo_flat), ("expo_kernel", ex_expo), ("slice4f_kernel", ex_slice),
     ("slice4_kernel", ex_slice), ("slice_kernel", ex_slice), ("ozgemm_kernel", ex_ozgemm),
     ("reduce_partials_kernel", ex_reduce), ("pack_ag_kernel", ex_pack_ag), ("pack_bg_kernel", ex_pack_bg),
-    ("sym_dl_kernel", ex_sym_dl),
+    ("sym_dl_kernel", ex_sym_dl), ("mirror_blocks_kernel", ex_mirror_blocks),
 ]
 
 DECODERS = [
@@ -691,6 +709,7 @@ DECODERS = [
     ("slice4f_kernel", dec_slice4), ("unpack_sym_kernel", dec_unpack_sym),
     ("symmetrize_kernel", dec_symmetrize), ("sym_dl_kernel", dec_sym_dl), ("fold_sym_split_kernel", dec_fold),
     ("fold_sym_kernel", dec_fold), ("pack_ag_kernel", dec_pack_ag), ("pack_bg_kernel", dec_pack_bg),
+    ("mirror_blocks_kernel", dec_mirror_blocks),
 ]
 violations, decoded, undecoded = [], [0], set()
 
@@ -922,14 +941,15 @@ def autotune_batched_case(shapes, p):
     return fn
 
 
-def batched_case(shapes, p, opts):
+def batched_case(shapes, p, opts, sym=False):
     def fn():
         fs, ds, outs, mols = [], [], [], []
         for m, (n, naux, ks) in enumerate(shapes):
-            f, d, L, X, Y = mol(n, naux, ks, [False] * len(ks), tag=f"m{m}")
+            sy = [sym and s % 2 == 0 for s in range(len(ks))]     # every other density symmetric
+            f, d, L, X, Y = mol(n, naux, ks, sy, tag=f"m{m}")
             fs.append(f)
             ds += list(d)
-            mols.append((L, X, Y))
+            mols.append((L, X, _ylist(X, Y, sy)))
             outs += [(buf((n, n), f"J{m}.{s}", False), buf((n, n), f"K{m}.{s}", False)) for s in range(len(ks))]
         fa = (jk_factor * len(fs))(*fs)
         da = (jk_density * len(ds))(*ds)
@@ -1128,6 +1148,16 @@ CASES = {
     "build_split_nbf_above_superchunk": build_case(2100, 3, [2], [False], SPLIT, {}),
     "build_split_fp32_digits": build_case(400, 60, [40, 40], [True, False], SPLIT, {"slicer": 1, "schedule": 1}),
     "build_split_j_only": build_case(37, 53, [5, 13], [False, True], SPLIT, {}, want="J"),
+    "build_split_syrk": build_case(300, 70, [20, 9, 33], [True, False, True], SPLIT,
+                                   {"syrk": 1, "schedule": 0, "aux_chunk": 30}),
+    "build_split_syrk_partials": build_case(300, 120, [40, 7], [True, True], SPLIT,
+                                            {"syrk": 1, "schedule": 0, "aux_chunk": 70}),
+    "build_split_syrk_grouped": build_case(257, 90, [64, 5, 11], [True, True, False], SPLIT,
+                                           {"syrk": 1, "schedule": 1, "aux_chunk": 40}),
+    "build_split_syrk_small_clustered": build_case(100, 30, [7, 4], [True, False], SPLIT,
+                                                   {"syrk": 1, "schedule": 1, "cluster": 1}),
+    "batched_split_syrk": batched_case([(60, 150, [6, 6]), (140, 222, [11]), (33, 99, [3, 3, 3])], SPLIT,
+                                       {"syrk": 1}, sym=True),
     "build_split_k_only_grouped": build_case(37, 53, [5, 13], [False, True], SPLIT, {"schedule": 1}, want="K"),
     "build_fp64_j_only": build_case(37, 53, [5, 13], [False, True], FP64, {}, want="J"),
     "sliced_gemm": sliced_gemm_case(129, 257, 2047, {}),
@@ -1168,6 +1198,8 @@ FULL_CASES = {
     "full_multi_state_tuned": build_case(400, 2400, [40] * 8, [True] + [False] * 7, SPLIT,
                                          {"aux_chunk": 3834, "schedule": 1, "raster": 0, "cluster": 0}),
     "full_multi_state_default": build_case(400, 2400, [40] * 8, [True] + [False] * 7, SPLIT, {}),
+    "full_multi_state_syrk": build_case(400, 2400, [40] * 8, [True] + [False] * 7, SPLIT,
+                                        {"aux_chunk": 3834, "schedule": 1, "raster": 0, "cluster": 0, "syrk": 1}),
     "full_multi_state_clustered": build_case(400, 2400, [40] * 8, [True] + [False] * 7, SPLIT,
                                              {"schedule": 1, "cluster": 1}),
     "full_dense": dense_case(400, 2400, 8, SPLIT, {}),
@@ -1198,7 +1230,7 @@ def fuzz_cases(count, seed):
         opts = {}
         if g.random() < 0.5:
             opts["aux_chunk"] = int(g.integers(1, naux + 3))
-        for name in ("schedule", "raster", "cluster", "slicer"):
+        for name in ("schedule", "raster", "cluster", "slicer", "syrk"):
             if g.random() < 0.5:
                 opts[name] = int(g.integers(0, 2))
         kind = g.choice(["build", "adjoint", "dense", "grad", "pairs", "laplace", "batched", "host"])
