@@ -69,7 +69,8 @@ typedef enum {
 
 typedef struct jk_ctx *jk_handle;
 
-/* One Cholesky factor: L is [naux][nbf][nbf] FP64 on the device. */
+/* One Cholesky factor: L is [naux][nbf][nbf] FP64 on the device (packed
+ * upper triangles [naux][nbf(nbf+1)/2] under JK_OPT_PACKED_FACTOR). */
 typedef struct {
     int32_t nbf;
     int32_t naux;
@@ -302,12 +303,26 @@ typedef enum {
                                additions (fewer instructions per element; an
                                equally exact split, digits differ only where a
                                digit rounds a tie)                               */
-    JK_OPT_SYRK = 7         /* split engine, symmetric densities: 0 (default)
+    JK_OPT_SYRK = 7,        /* split engine, symmetric densities: 0 (default)
                                full rank update, 1 only the row blocks of
                                128 rows from their diagonal on (K of the
                                symmetric build, the U = V case of Sec. II.C,
                                is symmetric), the rest mirrored; results
                                within rounding of those of 0                  */
+    JK_OPT_PACKED_FACTOR = 8 /* 0 (default) dense factor; 1 every factor passed
+                               to jk_build, jk_build_batched, jk_pair,
+                               jk_build_laplace and jk_autotune* on this handle
+                               holds packed upper triangles, L = [naux]
+                               [nbf(nbf+1)/2] row-major, diagonal included
+                               (position a*nbf - a(a-1)/2 + b - a for a <= b):
+                               half the device memory.  Each aux chunk is
+                               expanded into the workspace before its
+                               products; the FP64 J back-contraction reads the
+                               packed form.  Results equal the dense factor's
+                               bit for bit.  Size the arena with
+                               jk_workspace_query_handle (the handle-free query
+                               assumes a dense factor).  The other entry
+                               points return JK_ERR_UNSUPPORTED while it is 1 */
 } jk_option;
 /* Options set explicitly on a handle override tuned configurations. */
 jk_status jk_set_option(jk_handle h, jk_option opt, int64_t value);

@@ -240,7 +240,9 @@ jstream_kernel(const double *L, long long n2, int naux, const double *g,
 // Symmetric form: L^P = L^P^T, so J = sum_P g_P L^P is symmetric and only the
 // n(n+1)/2 upper-triangle entries are formed (one per thread, consecutive
 // threads on consecutive columns of a row), then mirrored: half the FP64 work.
-template <int NS>
+// PK: L is stored as packed upper triangles ([naux][n(n+1)/2]), read at the
+// thread's own position t (contiguous across the threads of a warp).
+template <int NS, bool PK>
 __global__ void __launch_bounds__(64)
 jstream_sym_kernel(const double *L, int n, int naux, const double *g, int ldg, OutTab Out) {
     const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -252,9 +254,10 @@ jstream_sym_kernel(const double *L, int n, int naux, const double *g, int ldg, O
     double a[NS];
 #pragma unroll
     for (int j = 0; j < NS; j++) a[j] = 0.0;
-    const double *Lp = L + e;
+    const double *Lp = PK ? L + t : L + e;
+    const long long pstride = PK ? packed::tri_count(n) : n2;
     for (int P = 0; P < naux; P++) {
-        const double l = __ldg(Lp + (long long)P * n2);
+        const double l = __ldg(Lp + (long long)P * pstride);
 #pragma unroll
         for (int j = 0; j < NS; j++) a[j] = fma(__ldg(g + (long long)j * ldg + P), l, a[j]);
     }
@@ -265,10 +268,11 @@ jstream_sym_kernel(const double *L, int n, int naux, const double *g, int ldg, O
     }
 }
 
-// Out[s] = sum_P g[s][P] L^P for s < nd (Out[s] are [n][n] device arrays).
+// Out[s] = sum_P g[s][P] L^P for s < nd (Out[s] are [n][n] device arrays);
+// pk: L holds packed upper triangles.
 static jk_status jstream(jk_ctx *h, const double *L, int n, int naux,
                          const double *g, int ldg, int nd, double *const *Out,
-                         cudaStream_t st) {
+                         cudaStream_t st, bool pk = false) {
     const long long ntri = (long long)n * (n + 1) / 2;
     const int blocks = (int)((ntri + 63) / 64);
     for (int s0 = 0; s0 < nd; s0 += 8) {
@@ -278,7 +282,11 @@ static jk_status jstream(jk_ctx *h, const double *L, int n, int naux,
         for (int j = 0; j < 8; j++) o.p[j] = j < ns ? Out[s0 + j] : nullptr;
         LaunchScope ls(h, KK_JSTREAM, st);
         switch (ns) {
-#define JS(N) case N: jstream_sym_kernel<N><<<blocks, 64, 0, st>>>(L, n, naux, gs, ldg, o); break;
+#define JS(N)                                                                              \
+    case N:                                                                                \
+        if (pk) jstream_sym_kernel<N, true><<<blocks, 64, 0, st>>>(L, n, naux, gs, ldg, o);  \
+        else jstream_sym_kernel<N, false><<<blocks, 64, 0, st>>>(L, n, naux, gs, ldg, o);    \
+        break;
             JS(1) JS(2) JS(3) JS(4) JS(5) JS(6) JS(7) JS(8)
 #undef JS
         }
@@ -418,12 +426,13 @@ jk_status fp64_jstream_dense(jk_ctx *h, const double *L, int n, int naux, const 
 }
 
 jk_status fp64_jstream(jk_ctx *h, const Problem &pb, const double *gamma, cudaStream_t st) {
-    return jstream(h, pb.L, pb.n, pb.naux, gamma, pb.naux, pb.nd, pb.J, st);
+    return jstream(h, pb.L, pb.n, pb.naux, gamma, pb.naux, pb.nd, pb.J, st, pb.packed);
 }
 
 int fp64_default_pchunk(const Problem &pb) {
-    // Panel chunk of at most ~256 MB of FP64 (T^P for pc aux indices).
-    size_t per = (size_t)pb.n * (size_t)pb.ctot * 8;
+    // Panel chunk of at most ~256 MB of FP64 (T^P for pc aux indices, and the
+    // expanded factor chunk of a packed factor).
+    size_t per = (size_t)pb.n * (size_t)pb.ctot * 8 + (pb.packed ? (size_t)pb.n * pb.n * 8 : 0);
     size_t pc = (size_t)256 << 20;
     pc = per ? pc / per : 1;
     if (pc < 1) pc = 1;
@@ -440,6 +449,7 @@ size_t fp64_build_workspace(const Problem &pb, int pc) {
     b += align_up(nd * (size_t)pb.naux * 8);        // gamma
     b += align_up(nd * n * n * 8);                  // dense D (J-only path)
     b += align_up((size_t)kMaxRankSplit * n * n * 8);   // split rank-update partials
+    if (pb.packed) b += align_up((size_t)pc * n * n * 8);   // expanded factor chunk
     return b;
 }
 
@@ -505,8 +515,21 @@ jk_status fp64_build(jk_ctx *h, const Problem &pb, cudaStream_t st) {
     double *gamma = ar.take<double>((size_t)nd * naux);
     double *D = ar.take<double>((size_t)nd * n2);
     double *part = ar.take<double>((size_t)kMaxRankSplit * n2);
-    if (!Z || !T || !gamma || !D || !part)
+    double *Lx = pb.packed ? ar.take<double>((size_t)pc * n2) : nullptr;
+    if (!Z || !T || !gamma || !D || !part || (pb.packed && !Lx))
         return set_error(h, JK_ERR_OOM, "workspace too small for the FP64 build");
+    const long long ntri = packed::tri_count(n);
+    // L^{P0..P0+np-1} as dense [np][n][n]: the factor itself, or its packed
+    // triangles expanded into Lx.
+    auto chunk_of = [&](int P0, int np, const double **out) -> jk_status {
+        if (!pb.packed) {
+            *out = pb.L + (long long)P0 * n2;
+            return JK_OK;
+        }
+        JK_TRY(fp64_unpack_sym(h, pb.L + (long long)P0 * ntri, n, np, Lx, st));
+        *out = Lx;
+        return JK_OK;
+    };
 
     if (K) {
         JK_TRY(pack_z(h, pb, Z, st));
@@ -518,9 +541,11 @@ jk_status fp64_build(jk_ctx *h, const Problem &pb, cudaStream_t st) {
         }
         for (int P0 = 0; P0 < naux; P0 += pc) {
             const int np = naux - P0 < pc ? naux - P0 : pc;
+            const double *Lc;
+            JK_TRY(chunk_of(P0, np, &Lc));
             // T[(p,mu)][c] = sum_lam L^{P0+p}[mu][lam] Z[lam][c]
             JK_TRY(dgemm(h, 1, np * n, pb.ctot, n,
-                         gop(pb.L + (long long)P0 * n2, 0, n, 0, 1, n),
+                         gop(Lc, 0, n, 0, 1, n),
                          gop(Z, 0, 1, 0, pb.ctot, n),
                          T, pb.ctot, 0, 1.0, 0.0, st));
             if (J) {
@@ -539,12 +564,24 @@ jk_status fp64_build(jk_ctx *h, const Problem &pb, cudaStream_t st) {
                          gop(Ys, 0, pb.k[s], 0, 1, pb.k[s]), D + (long long)s * n2, n, 0,
                          1.0, 0.0, st));
         }
-        { LaunchScope ls_f(h, KK_FROB, st);
-        frob_stream_kernel<<<dim3(naux, (nd + 3) / 4), 256, 0, st>>>(pb.L, n2, D, nd, gamma, naux, 0);
+        if (!pb.packed) {
+            LaunchScope ls_f(h, KK_FROB, st);
+            frob_stream_kernel<<<dim3(naux, (nd + 3) / 4), 256, 0, st>>>(pb.L, n2, D, nd, gamma, naux, 0);
         }
         JK_LAUNCH_CHECK(h);
+        // packed factor: the same metric dots chunk by chunk on the expanded copy
+        for (int P0 = 0; pb.packed && P0 < naux; P0 += pc) {
+            const int np = naux - P0 < pc ? naux - P0 : pc;
+            const double *Lc;
+            JK_TRY(chunk_of(P0, np, &Lc));
+            {
+                LaunchScope ls_f(h, KK_FROB, st);
+                frob_stream_kernel<<<dim3(np, (nd + 3) / 4), 256, 0, st>>>(Lc, n2, D, nd, gamma + P0, naux, 0);
+            }
+            JK_LAUNCH_CHECK(h);
+        }
     }
-    if (J) JK_TRY(jstream(h, pb.L, n, naux, gamma, naux, nd, pb.J, st));
+    if (J) JK_TRY(jstream(h, pb.L, n, naux, gamma, naux, nd, pb.J, st, pb.packed));
     return JK_OK;
 }
 

@@ -49,6 +49,7 @@ static jk_status make_problem(jk_ctx *h, const jk_factor *f, int nd,
     pb.naux = f->naux;
     pb.nd = nd;
     pb.L = f->L;
+    pb.packed = h && h->packed_factor;
     int c = 0, ks = 0, km = 0;
     for (int s = 0; s < nd; s++) {
         if (d[s].k < 1 || d[s].k > f->nbf * 4)
@@ -91,6 +92,14 @@ static jk_status make_problem(jk_ctx *h, const jk_factor *f, int nd,
 }
 
 static size_t flags_bytes() { return align_up(sizeof(DeviceFlags)); }
+
+// Entry points that read the factor only through ordinary builds take a
+// packed factor (JK_OPT_PACKED_FACTOR); the others refuse the option.
+static jk_status refuse_packed(jk_ctx *h, const char *what) {
+    if (h && h->packed_factor)
+        return set_error(h, JK_ERR_UNSUPPORTED, "%s does not take a packed factor (JK_OPT_PACKED_FACTOR)", what);
+    return JK_OK;
+}
 
 // Without a tuned entry: one CTA per tile (clusters are a tuning candidate).
 constexpr int kDefaultCluster = 0;
@@ -635,6 +644,10 @@ static jk_status query_impl(const jk_ctx *h, jk_op op, int32_t nmol, const jk_fa
                             size_t *bytes) {
     if (!bytes || !f) return JK_ERR_ARG;
     if (p != JK_FP64 && p != JK_SPLIT_BF16) return JK_ERR_ARG;
+    // a packed factor (handle option) is taken by the ordinary builds only
+    const bool pk = h && h->packed_factor;
+    if (pk && op != JK_OP_BUILD && op != JK_OP_BATCHED && op != JK_OP_PAIR && op != JK_OP_LAPLACE)
+        return JK_ERR_UNSUPPORTED;
     if (op == JK_OP_BUILD_DENSE || op == JK_OP_DENSITY_GRAD) {
         DenseProb dp;
         jk_status s = make_dense(nullptr, f, nd, false, dp);
@@ -652,6 +665,7 @@ static jk_status query_impl(const jk_ctx *h, jk_op op, int32_t nmol, const jk_fa
         laplace_densities(f->nbf, nd, d[0].k, d[0].symmetric != 0, nullptr, dl.data());
         Problem pb;
         JK_TRY(make_problem(nullptr, f, nd, dl.data(), false, pb));
+        pb.packed = pk;
         Problem q = pb;
         apply_config(pb, resolve_config(h, JK_OP_BUILD, p, sms, 1, &pb));
         apply_config(q, jk_tune_config{0, 0, 0, kDefaultCluster});
@@ -665,6 +679,7 @@ static jk_status query_impl(const jk_ctx *h, jk_op op, int32_t nmol, const jk_fa
         if (nmol != 2 || !nd_per_mol) return JK_ERR_SHAPE;
         std::vector<Problem> pp;
         JK_TRY(host_batched_problems(2, f, nd_per_mol, nd, d, pp, true));
+        for (auto &q : pp) q.packed = pk;
         size_t need = 0;
         const jk_tune_config cfgs[2] = {resolve_config(h, JK_OP_BUILD, p, sms, 1, &pp[1]),
                                         jk_tune_config{0, 0, 0, kDefaultCluster}};
@@ -680,10 +695,12 @@ static jk_status query_impl(const jk_ctx *h, jk_op op, int32_t nmol, const jk_fa
     std::vector<Problem> pbs;
     if (op == JK_OP_BATCHED) {
         JK_TRY(host_batched_problems(nmol, f, nd_per_mol, nd, d, pbs));
+        for (auto &q : pbs) q.packed = pk;
     } else if (op == JK_OP_BUILD || op == JK_OP_ADJOINT || op == JK_OP_BUILD_HOST || op == JK_OP_BUILD_HOST_PACKED) {
         pbs.resize(1);
         jk_status s = make_problem(nullptr, f, nd, d, false, pbs[0]);
         if (s != JK_OK) return s;
+        pbs[0].packed = pk;
         nmol = 1;
         if (op == JK_OP_BUILD_HOST || op == JK_OP_BUILD_HOST_PACKED) {
             *bytes = host_build_bytes(h, pbs[0], p, op == JK_OP_BUILD_HOST_PACKED) + flags_bytes() + kArenaAlign;
@@ -747,6 +764,7 @@ static jk_status build_host_impl(jk_handle h, const jk_factor *f, int32_t nd, co
     if (p != JK_FP64 && p != JK_SPLIT_BF16)
         return set_error(h, JK_ERR_ARG, "unknown precision %d", (int)p);
     Problem pb;
+    JK_TRY(refuse_packed(h, packed ? "jk_build_host_packed" : "jk_build_host"));
     JK_TRY(make_problem(h, f, nd, d, false, pb));
     if (!f->L) return set_error(h, JK_ERR_ARG, "factor L is NULL");
     for (int s = 0; s < nd; s++)
@@ -900,6 +918,7 @@ jk_status jk_adjoint(jk_handle h, const jk_factor *f, int32_t nd, const jk_densi
     if (p != JK_FP64 && p != JK_SPLIT_BF16)
         return set_error(h, JK_ERR_ARG, "unknown precision %d", (int)p);
     Problem pb;
+    JK_TRY(refuse_packed(h, "jk_adjoint"));
     JK_TRY(make_problem(h, f, nd, d, true, pb));
     if (h->aux_chunk >= 0) pb.aux_chunk = h->aux_chunk;
     h->cur_raster = h->raster >= 0 ? h->raster : 0;
@@ -925,6 +944,7 @@ jk_status jk_build_dense(jk_handle h, const jk_factor *f, int32_t nd, const doub
     if (p != JK_FP64 && p != JK_SPLIT_BF16)
         return set_error(h, JK_ERR_ARG, "unknown precision %d", (int)p);
     DenseProb dp;
+    JK_TRY(refuse_packed(h, "jk_build_dense"));
     JK_TRY(make_dense(h, f, nd, true, dp));
     if (!D) return set_error(h, JK_ERR_ARG, "D is NULL");
     JK_TRY(check_in(h, D, "D"));
@@ -945,6 +965,7 @@ jk_status jk_density_grad(jk_handle h, const jk_factor *f, int32_t nd, const dou
     if (p != JK_FP64 && p != JK_SPLIT_BF16)
         return set_error(h, JK_ERR_ARG, "unknown precision %d", (int)p);
     DenseProb dp;
+    JK_TRY(refuse_packed(h, "jk_density_grad"));
     JK_TRY(make_dense(h, f, nd, true, dp));
     if (!G) return set_error(h, JK_ERR_ARG, "G is NULL");
     JK_TRY(check_out(h, G, "G"));
@@ -1116,6 +1137,11 @@ jk_status jk_set_option(jk_handle h, jk_option opt, int64_t value) {
     if (opt == JK_OPT_SYRK) {
         if (value != 0 && value != 1) return set_error(h, JK_ERR_ARG, "JK_OPT_SYRK takes 0 or 1");
         h->syrk = static_cast<int>(value);
+        return JK_OK;
+    }
+    if (opt == JK_OPT_PACKED_FACTOR) {
+        if (value != 0 && value != 1) return set_error(h, JK_ERR_ARG, "JK_OPT_PACKED_FACTOR takes 0 or 1");
+        h->packed_factor = static_cast<int>(value);
         return JK_OK;
     }
     if (opt == JK_OPT_USE_TUNED) {

@@ -78,7 +78,8 @@ struct jk_ctx {
     bool gemm_smem_set = false;   // the sliced GEMM's shared-memory attribute is set on this device
     int host_chunk = 0;      // aux indices per streamed chunk of a host-resident factor (0 = automatic)
     int slicer = 0;
-    int syrk = 0;            // split engine: symmetric rank updates by row blocks, rest mirrored          // digit extraction of the vector slicer: 0 integer, 1 FP32 additions
+    int syrk = 0;            // split engine: symmetric rank updates by row blocks, rest mirrored
+    int packed_factor = 0;   // factors passed to builds hold packed upper triangles          // digit extraction of the vector slicer: 0 integer, 1 FP32 additions
     cudaStream_t copy_stream = nullptr;   // host builds: uploads of the factor, created on first use
     cudaEvent_t ev_fork = nullptr, ev_up[2] = {nullptr, nullptr}, ev_used[2] = {nullptr, nullptr};
     cudaStream_t aux_stream = nullptr;    // FP64 J streams overlapped with the rank updates
@@ -108,6 +109,8 @@ struct Problem {
     bool wantJ = false, wantK = false;
     int aux_chunk = 0;   // at most this many aux indices per chunk (0 = automatic)
     int schedule = 0;    // split precision: 0 per-density launches, 1 grouped launches
+    bool packed = false; // L holds packed upper triangles [naux][n(n+1)/2]; each aux
+                         // chunk is expanded into a dense workspace copy before use
 };
 
 jk_status set_error(jk_ctx *h, jk_status s, const char *fmt, ...);

@@ -42,6 +42,7 @@
 
 #include "digits.cuh"
 #include "fixed.cuh"
+#include "packed.cuh"
 #include "jk_internal.h"
 #include "tc.cuh"
 
@@ -1191,6 +1192,7 @@ static jk_status mirror_blocks(jk_ctx *h, double *K, int n, cudaStream_t st) {
 static int split_pchunk(const Problem &pb) {
     const size_t n = pb.n;
     size_t per = n * n * (oz::S * 2) + n * pb.ctot * 8 + n * pb.ctot * (oz::S * 2);
+    if (pb.packed) per += n * n * 8;               // the expanded factor chunk
     size_t budget = static_cast<size_t>(12) << 30;
     size_t pc = per ? budget / per : 1;
     if (pc < 1) pc = 1;
@@ -1235,11 +1237,13 @@ size_t split_build_workspace(const Problem &pb) {
     b += align_up(static_cast<size_t>(pb.nd) * n * n * 8);           // K accumulators (if K not wanted)
     if (pb.n > oz::SUPER)
         b += align_up(static_cast<size_t>(nsuper_of(pb.n)) * part_rows(static_cast<long long>(pc) * n) * even_ld(pb.ctot) * 8);
+    if (pb.packed) b += align_up(static_cast<size_t>(pc) * n * n * 8);   // expanded factor chunk
     return b;
 }
 
 
 jk_status split_pack_z(jk_ctx *h, const Problem &pb, double *Z, cudaStream_t st);
+jk_status fp64_unpack_sym(jk_ctx *h, const double *packed, int n, long long np, double *full, cudaStream_t st);
 jk_status fp64_gamma_panel(jk_ctx *h, const Problem &pb, const double *T, long long ldT, int np, double *gamma,
                            int P0, cudaStream_t st);
 jk_status fp64_jstream(jk_ctx *h, const Problem &pb, const double *gamma, cudaStream_t st);
@@ -1286,7 +1290,8 @@ jk_status split_build(jk_ctx *h, const Problem &pb, cudaStream_t st) {
     long long *Ppanel = nullptr;
     if (n > oz::SUPER)
         Ppanel = ar.take<long long>(static_cast<size_t>(nsuper_of(n)) * part_rows(static_cast<long long>(pc) * n) * ldT);
-    if (!ok || !T || !gamma || !Pbuf || !Kacc || (n > oz::SUPER && !Ppanel))
+    double *Lx = pb.packed ? ar.take<double>(static_cast<size_t>(pc) * n2) : nullptr;
+    if (!ok || !T || !gamma || !Pbuf || !Kacc || (n > oz::SUPER && !Ppanel) || (pb.packed && !Lx))
         return set_error(h, JK_ERR_OOM, "workspace too small for the split build");
 
     // Z = [X_0 | Y_0 | ...] and its transpose sliced per column (rows of Z^T).
@@ -1296,8 +1301,11 @@ jk_status split_build(jk_ctx *h, const Problem &pb, cudaStream_t st) {
 
     for (int P0 = 0; P0 < naux; P0 += pc) {
         const int np = naux - P0 < pc ? naux - P0 : pc;
+        // a packed factor chunk is expanded first
+        if (pb.packed) JK_TRY(fp64_unpack_sym(h, pb.L + P0 * packed::tri_count(n), n, np, Lx, st));
+        const double *Lchunk = pb.packed ? Lx : pb.L + P0 * n2;
         // L^P rows (P, mu), reduction over lam, one exponent per P.
-        oz::Src lsrc{pb.L + P0 * n2, n, 0, 1, n};
+        oz::Src lsrc{Lchunk, n, 0, 1, n};
         Sliced Lc = Ls;
         JK_TRY(slice_operand(h, lsrc, np * n, n, n, Lc, st));
         // T[(p, mu)][c] = sum_lam L^p[mu][lam] Z[lam][c]
@@ -1664,6 +1672,7 @@ struct ItemBufs {
     Sliced Ls, TX[kMaxDens], TY[kMaxDens];
     double *T = nullptr, *tmp = nullptr;
     long long *P = nullptr;
+    double *Lx = nullptr;     // packed factor: the chunk expanded to [np][n][n]
 };
 
 size_t item_bytes(const Problem &pb, int pc) {
@@ -1675,6 +1684,7 @@ size_t item_bytes(const Problem &pb, int pc) {
     }
     b += align_up(partial_count(pb, pc) * 8 + 8);
     b += align_up(static_cast<size_t>(pb.nd) * n * n * 8);   // per-density tmp for chunk accumulation
+    if (pb.packed) b += align_up(static_cast<size_t>(pc) * n * n * 8);   // expanded factor chunk
     return b + 16 * kArenaAlign;
 }
 
@@ -1694,7 +1704,8 @@ bool take_item(Arena &ar, const Problem &pb, int pc, ItemBufs &it) {
     }
     it.P = ar.take<long long>(partial_count(pb, pc) + 1);
     it.tmp = ar.take<double>(static_cast<size_t>(pb.nd) * n * n);
-    return ok && it.P && it.tmp;
+    if (pb.packed) it.Lx = ar.take<double>(static_cast<size_t>(pc) * n * n);
+    return ok && it.P && it.tmp && (!pb.packed || it.Lx);
 }
 
 }  // namespace
@@ -1764,7 +1775,10 @@ jk_status split_batched(jk_ctx *h, int nmol, const Problem *pbs, cudaStream_t st
         for (auto &it : items) {
             const Problem &pb = pbs[it.mol];
             const long long n2 = static_cast<long long>(pb.n) * pb.n;
-            oz::Src lsrc{pb.L + it.P0 * n2, pb.n, 0, 1, pb.n};
+            if (pb.packed)
+                JK_TRY(fp64_unpack_sym(h, pb.L + it.P0 * packed::tri_count(pb.n), pb.n, it.np, it.Lx, st));
+            const double *Lc = pb.packed ? it.Lx : pb.L + it.P0 * n2;
+            oz::Src lsrc{Lc, pb.n, 0, 1, pb.n};
             JK_TRY(slice_operand(h, lsrc, it.np * pb.n, pb.n, pb.n, it.Ls, st));
         }
         // 2. all panels of the wave: grouped persistent launches

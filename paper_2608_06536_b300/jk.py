@@ -43,10 +43,10 @@ class jk_tune_config(ct.Structure):
 
 
 OPTIONS = {"aux_chunk": 0, "schedule": 1, "raster": 2, "use_tuned": 3, "cluster": 4, "host_chunk": 5, "slicer": 6,
-           "syrk": 7}
+           "syrk": 7, "packed_factor": 8}
 # each option's value on a fresh handle (-1: not set, tuned or default configuration)
 OPTION_DEFAULTS = {"aux_chunk": -1, "schedule": -1, "raster": -1, "use_tuned": 1, "cluster": -1, "host_chunk": 0,
-                   "slicer": 0, "syrk": 0}
+                   "slicer": 0, "syrk": 0, "packed_factor": 0}
 
 
 class JKError(RuntimeError):
@@ -165,11 +165,18 @@ def _shape(t):
     return tuple(int(v) for v in t.shape)
 
 
-def _check_problem(L, X, Y=None, sym=None):
+def _check_problem(L, X, Y=None, sym=None, packed=False):
     """Shapes of one molecule, checked before any device work: the C ABI takes
     pointers and sizes only, so a mismatch here would become an out-of-bounds
-    access in the kernels.  L is [naux][nbf][nbf]; X_s (and Y_s of a
-    non-symmetric density) is [nbf][k_s].  Returns (nbf, naux, nd)."""
+    access in the kernels.  L is [naux][nbf][nbf] (packed: [naux][nbf(nbf+1)/2],
+    nbf taken from X); X_s (and Y_s of a non-symmetric density) is [nbf][k_s].
+    Returns (nbf, naux, nd)."""
+    if packed:
+        Ls = _shape(L)
+        n = _shape(X[0])[0] if len(X) and len(_shape(X[0])) == 2 else 0
+        if len(Ls) != 2 or n < 1 or Ls[1] != n * (n + 1) // 2 or Ls[0] < 1:
+            raise ValueError(f"packed L must be [naux][{n * (n + 1) // 2}] for nbf = {n}, got {Ls}")
+        return _check_shapes((Ls[0], n, n), X, Y, sym)
     return _check_shapes(_shape(L), X, Y, sym)
 
 
@@ -329,6 +336,10 @@ class Engine:
     def sync_status(self, stream=None):
         self._check(self.lib.jk_sync_status(self._h, _stream_ptr(stream)), self._h)
 
+    @property
+    def _packed(self) -> bool:
+        return self._opts.get(OPTIONS["packed_factor"], 0) == 1
+
     def _record(self, stream):
         """Work issued on a stream other than the current one keeps the arena
         from being reused (after a later growth) until that work is done."""
@@ -342,7 +353,10 @@ class Engine:
         0, 1), "use_tuned" (0 or 1), "host_chunk" (>= 0, 0 = automatic),
         "slicer" (0 integer digits, 1 FP32 digits), "syrk" (split engine,
         symmetric densities: 0 full rank update, 1 blocked symmetric rank
-        update with the rest mirrored).  Kept across arena growth."""
+        update with the rest mirrored), "packed_factor" (1: the factor given
+        to build, build_batched, pairs, build_laplace and autotune* is
+        pack_factor(L), [naux][n(n+1)/2] on the device; half the memory).
+        Kept across arena growth."""
         code = OPTIONS[name]
         self._opts[code] = int(value)
         if self._h:
@@ -397,7 +411,7 @@ class Engine:
               J=None, K=None, stream=None):
         """J_s, K_s ([nd][n][n] float64) for D_s = X_s Y_s^T over factor L."""
         p = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
-        n, _, nd = _check_problem(L, X, Y, sym)
+        n, _, nd = _check_problem(L, X, Y, sym, self._packed)
         if want_j:
             _check_output(J, "J", (nd, n, n), self.device)
         if want_k:
@@ -425,14 +439,7 @@ class Engine:
         work (sync=True waits for it).  With packed=True, L is given as
         pack_factor(L) ([naux][n(n+1)/2]): half the bytes are uploaded."""
         p = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
-        if packed:
-            Ls = _shape(L)
-            n = _shape(X[0])[0] if len(X) else 0
-            if len(Ls) != 2 or Ls[1] != n * (n + 1) // 2 or Ls[0] < 1:
-                raise ValueError(f"packed L must be [naux][{n * (n + 1) // 2}] for nbf = {n}, got {Ls}")
-            n, _, nd = _check_shapes((Ls[0], n, n), X, Y, sym)
-        else:
-            n, _, nd = _check_problem(L, X, Y, sym)
+        n, _, nd = _check_problem(L, X, Y, sym, packed)
         if want_j:
             _check_output(J, "J", (nd, n, n), torch.device("cpu"))
         if want_k:
@@ -516,8 +523,8 @@ class Engine:
         p = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         if XR is None:
             raise ValueError("right densities XR are required")
-        n, naux, nl = _check_problem(L, XL, YL, symL)
-        _, _, nr = _check_problem(L, XR, YR, symR)
+        n, naux, nl = _check_problem(L, XL, YL, symL, self._packed)
+        _, _, nr = _check_problem(L, XR, YR, symR, self._packed)
         L = _dev_f64(L, self.device)
         left = Densities(XL, YL, symL, self.device)
         right = Densities(XR, YR, symR, self.device)
@@ -541,6 +548,11 @@ class Engine:
         weighted sums [n][n] when w is given."""
         p = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         Ls = _shape(L)
+        if self._packed:
+            n = _shape(CX)[0] if len(_shape(CX)) == 2 else 0
+            if len(Ls) != 2 or n < 1 or Ls[1] != n * (n + 1) // 2 or Ls[0] < 1:
+                raise ValueError(f"packed L must be [naux][{n * (n + 1) // 2}] for nbf = {n}, got {Ls}")
+            Ls = (Ls[0], n, n)
         if len(Ls) != 3 or Ls[1] != Ls[2] or min(Ls) < 1:
             raise ValueError(f"L must be [naux][nbf][nbf] with naux, nbf >= 1, got {Ls}")
         naux, n = Ls[0], Ls[1]
@@ -581,7 +593,7 @@ class Engine:
         """Time the candidate configurations of this build and cache the
         fastest for its shape bucket; returns (config dict, ms per build)."""
         p = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
-        n, naux, nd = _check_problem(L, X, Y, sym)
+        n, naux, nd = _check_problem(L, X, Y, sym, self._packed)
         L = _dev_f64(L, self.device)
         dens = Densities(X, Y, sym, self.device)
         f = jk_factor(n, naux, L.data_ptr())
@@ -635,16 +647,17 @@ class Engine:
         nd_per = []
         if nmol < 1:
             raise ValueError("at least one molecule is required")
+        shapes = []
         for m, (L, X, Y, sym) in enumerate(mols):
             try:
-                _check_problem(L, X, Y, sym)
+                shapes.append(_check_problem(L, X, Y, sym, self._packed))
             except ValueError as e:
                 raise ValueError(f"molecule {m}: {e}") from None
         for m, (L, X, Y, sym) in enumerate(mols):
             L = _dev_f64(L, self.device)
             d = Densities(X, Y, sym, self.device)
             Ls.append(L); dens.append(d)
-            fac[m] = jk_factor(int(L.shape[1]), int(L.shape[0]), L.data_ptr())
+            fac[m] = jk_factor(shapes[m][0], shapes[m][1], L.data_ptr())
             nd_per.append(len(d))
         ndt = sum(nd_per)
         dall = (jk_density * ndt)()

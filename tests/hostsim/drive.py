@@ -72,7 +72,7 @@ shim.shim_launch.restype = ct.c_char_p
 assert hasattr(shim, "shim_reset"), "the stand-in runtime is not the one loaded"
 
 OPT = {"aux_chunk": 0, "schedule": 1, "raster": 2, "use_tuned": 3, "cluster": 4, "host_chunk": 5, "slicer": 6,
-       "syrk": 7}
+       "syrk": 7, "packed_factor": 8}
 
 # ---- kernel arguments ----------------------------------------------------------
 # Each decoder reads one kernel's arguments (layouts as in the CUDA sources)
@@ -220,7 +220,8 @@ def dec_jstream_sym(grid, args, name):
     L, n, naux, g, ldg, o = (_v(args, 0, VP), _v(args, 1, I32), _v(args, 2, I32), _v(args, 3, VP),
                              _v(args, 4, I32), _a(args, 5, OutTab))
     assert grid[0] * 64 >= n * (n + 1) // 2
-    out = [(L, L + 8 * naux * n * n, "L"), (g, g + 8 * ((ns - 1) * ldg + naux), "g")]
+    per = n * (n + 1) // 2 if "Lb1E" in name else n * n          # packed factor: upper triangles
+    out = [(L, L + 8 * naux * per, "L"), (g, g + 8 * ((ns - 1) * ldg + naux), "g")]
     out += [(o.p[j], o.p[j] + 8 * n * n, "J") for j in range(ns)]
     return out
 
@@ -424,7 +425,15 @@ def ex_jstream_sym(grid, args, name):
     ns = int(name.split("ILi")[1].split("E")[0])
     L, n, naux, g, ldg, o = (_v(args, 0, VP), _v(args, 1, I32), _v(args, 2, I32), _v(args, 3, VP),
                              _v(args, 4, I32), _a(args, 5, OutTab))
-    Lm = dv(L, naux * n * n).reshape(naux, n * n)
+    if "Lb1E" in name:                                            # packed upper triangles
+        iu = np.triu_indices(n)
+        P = dv(L, naux * len(iu[0])).reshape(naux, -1)
+        full = np.zeros((naux, n, n))
+        full[:, iu[0], iu[1]] = P
+        full[:, iu[1], iu[0]] = P
+        Lm = full.reshape(naux, n * n)
+    else:
+        Lm = dv(L, naux * n * n).reshape(naux, n * n)
     for j in range(ns):
         out = dv(g + 8 * j * ldg, naux) @ Lm
         out = out.reshape(n, n)
@@ -765,6 +774,7 @@ owned = []      # (base, nbytes, label) of every buffer a case hands to the libr
 
 
 BIG = [False]     # full-size cases: inputs left as untouched zero pages
+PACKED_MODE = [False]   # factors handed over as packed upper triangles (JK_OPT_PACKED_FACTOR)
 ARENA_SCALE = [1.0]   # the arena handed to each call, as a fraction of the queried size
 
 
@@ -784,6 +794,30 @@ def ptr(a):
     return None if a is None else ct.c_void_p(a.ctypes.data)
 
 
+def factor_of(L, n, naux, tag):
+    """The jk_factor of L: L itself, or (PACKED_MODE) a packed copy of its upper
+    triangles, the only factor memory the library then sees."""
+    if not PACKED_MODE[0]:
+        return jk_factor(n, naux, L.ctypes.data)
+    iu = np.triu_indices(n)
+    LP = buf((naux, n * (n + 1) // 2), f"{tag}.Lpacked", fill=False)
+    if not BIG[0]:
+        LP[...] = L[:, iu[0], iu[1]]
+    owned[:] = [o for o in owned if o[0] != L.ctypes.data]     # the dense copy is the test's alone
+    return jk_factor(n, naux, LP.ctypes.data)
+
+
+def packed(case):
+    """The same case with every factor passed as packed upper triangles."""
+    def fn():
+        PACKED_MODE[0] = True
+        try:
+            return case()
+        finally:
+            PACKED_MODE[0] = False
+    return fn
+
+
 def mol(n, naux, ks, sym, tag="m"):
     L = buf((naux, n, n), f"{tag}.L")
     if not BIG[0]:
@@ -794,7 +828,7 @@ def mol(n, naux, ks, sym, tag="m"):
     for s, k in enumerate(ks):
         d[s].k, d[s].symmetric, d[s].X = k, int(sym[s]), X[s].ctypes.data
         d[s].Y = None if sym[s] else Y[s].ctypes.data
-    return jk_factor(n, naux, L.ctypes.data), d, L, X, Y
+    return factor_of(L, n, naux, tag), d, L, X, Y
 
 
 def handle(nbytes, opts, scaled=True):
@@ -1081,7 +1115,7 @@ def laplace_case(n, naux, m, nq, sym, weighted, p, opts):
         L = buf((naux, n, n), "L")
         if not BIG[0]:
             L[...] = L + L.transpose(0, 2, 1)
-        f = jk_factor(n, naux, L.ctypes.data)
+        f = factor_of(L, n, naux, "m")
         CX, CY = buf((n, m), "CX"), buf((n, m), "CY")
         eX, eY = buf((m,), "epsX"), buf((m,), "epsY")
         d = (jk_density * 1)()
@@ -1107,6 +1141,34 @@ def laplace_case(n, naux, m, nq, sym, weighted, p, opts):
             check("J", J, Jo)
             check("K", K, Ko)
         return st, h
+    return fn
+
+
+def packed_refused_case():
+    """With JK_OPT_PACKED_FACTOR set, the entry points that read the factor
+    outside ordinary builds refuse the call before any device work."""
+    def fn():
+        n, naux, ks = 20, 30, [3, 4]
+        f, d, L, X, Y = mol(n, naux, ks, [False, False])
+        nd, tot = len(ks), n * sum(ks)
+        h = handle(1 << 24, {"packed_factor": 1}, scaled=False)
+        W, V = buf((nd, n, n), "W"), buf((nd, n, n), "V")
+        dX, dY = buf((tot,), "dX", False), buf((tot,), "dY", False)
+        O = buf((nd, n, n), "O", False)
+        got = {
+            "adjoint": lib.jk_adjoint(h, ct.byref(f), nd, d, ptr(W), ptr(V), ptr(dX), ptr(dY), None, SPLIT, None),
+            "dense": lib.jk_build_dense(h, ct.byref(f), nd, ptr(W), ptr(O), None, SPLIT, None),
+            "grad": lib.jk_density_grad(h, ct.byref(f), nd, ptr(W), ptr(V), ptr(O), SPLIT, None),
+            "host": lib.jk_build_host(h, ct.byref(f), nd, d, ptr(O), None, SPLIT, None),
+            "host_packed": lib.jk_build_host_packed(h, ct.byref(f), nd, d, ptr(O), None, SPLIT, None),
+        }
+        nb = ct.c_size_t()
+        for op in (1, 3, 4, 5, 8):
+            got[f"query{op}"] = lib.jk_workspace_query_handle(h, op, 1, (jk_factor * 1)(f), None, nd, d, SPLIT,
+                                                               ct.byref(nb))
+        bad = {k: v for k, v in got.items() if v != 6}
+        assert not bad, bad
+        return 0, h
     return fn
 
 
@@ -1189,6 +1251,22 @@ CASES = {
     "laplace_split_weighted_sym": laplace_case(130, 70, 9, 3, True, True, SPLIT, {}),
     "laplace_fp64_weighted": laplace_case(37, 53, 5, 4, False, True, FP64, {}),
     "noalloc": noalloc_case(37, 53, [5, 1, 13]),
+    "build_split_packed": packed(build_case(130, 70, [9, 3, 20], [False, True, False], SPLIT,
+                                            {"packed_factor": 1, "aux_chunk": 30})),
+    "build_split_packed_grouped_syrk": packed(build_case(
+        257, 90, [64, 5], [True, False], SPLIT, {"packed_factor": 1, "schedule": 1, "aux_chunk": 40, "syrk": 1})),
+    "build_split_packed_j_only": packed(build_case(37, 53, [5, 13], [False, True], SPLIT,
+                                                   {"packed_factor": 1, "aux_chunk": 17}, want="J")),
+    "build_fp64_packed": packed(build_case(37, 53, [5, 1, 13], [False, True, False], FP64,
+                                           {"packed_factor": 1, "aux_chunk": 17})),
+    "build_fp64_packed_j_only": packed(build_case(37, 53, [5, 13], [False, True], FP64,
+                                                  {"packed_factor": 1, "aux_chunk": 17}, want="J")),
+    "batched_split_packed": packed(batched_case([(60, 150, [6, 6]), (140, 222, [11]), (33, 99, [3, 3, 3])], SPLIT,
+                                                {"packed_factor": 1}, sym=True)),
+    "batched_fp64_packed": packed(batched_case([(60, 150, [6, 6]), (33, 99, [3])], FP64, {"packed_factor": 1})),
+    "pairs_split_packed": packed(pair_case(40, 60, [3, 5], [False, True], [4, 6, 2], [False, False, True], SPLIT,
+                                           {"packed_factor": 1})),
+    "laplace_split_packed": packed(laplace_case(37, 53, 5, 4, False, True, SPLIT, {"packed_factor": 1})),
     "autotune_split": autotune_case(37, 53, [5, 13], SPLIT),
 }
 
@@ -1209,6 +1287,13 @@ FULL_CASES = {
     "full_adjoint": adjoint_case(600, 3600, [60] * 8, [False] * 8, SPLIT, {}),
     "full_host": host_case(400, 2400, [40] * 8, SPLIT, {}),
     "full_host_packed": host_case(400, 2400, [40] * 8, SPLIT, {}, packed=True),
+    "full_multi_state_packed": packed(build_case(400, 2400, [40] * 8, [True] + [False] * 7, SPLIT,
+                                                 {"packed_factor": 1, "schedule": 1})),
+}
+
+# Calls that must be refused before any device work (run by name only).
+REFUSE_CASES = {
+    "packed_refused": packed_refused_case(),
 }
 
 # ---- random cases ----------------------------------------------------------------
@@ -1286,4 +1371,4 @@ if __name__ == "__main__":
     names = args or list(CASES)
     for name in names:
         BIG[0] = name in FULL_CASES
-        run(name, CASES.get(name) or FULL_CASES[name])
+        run(name, CASES.get(name) or FULL_CASES.get(name) or REFUSE_CASES[name])

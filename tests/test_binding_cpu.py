@@ -285,3 +285,39 @@ def test_module_level_functions_dispatch_to_the_engine(rec, monkeypatch):
     J, K = jk.jk_build_laplace(L, X[0], np.array([-1.0, -0.5]), +1, [0.5], stream=st)
     assert J.shape == (1, n, n)
     assert [c[0] for c in rec.lib.calls] == ["jk_build_dense", "jk_density_grad", "jk_pair", "jk_build_laplace"]
+
+
+def test_packed_factor_through_the_binding(rec):
+    """With the packed_factor option the binding takes pack_factor(L)
+    ([naux][n(n+1)/2]) for the ordinary builds, derives nbf from the
+    densities (or CX), passes the library the factor's true nbf and naux, and
+    rejects a dense or mis-sized factor before any device work."""
+    rng = np.random.default_rng(6)
+    n, naux = 8, 5
+    L = rng.standard_normal((naux, n, n))
+    L = L + L.transpose(0, 2, 1)
+    P = jk.pack_factor(L)
+    X = [rng.standard_normal((n, k)) for k in (2, 3)]
+    Y = [rng.standard_normal((n, k)) for k in (2, 3)]
+    st = rec.stream
+    rec.set_option("packed_factor", 1)
+    rec.build(P, X, Y, [False, True], "split", stream=st)
+    rec.build_batched([(P, X, Y, None), (jk.pack_factor(L[:, :6, :6]), [x[:6] for x in X], None, [True, True])],
+                      "split", stream=st)
+    rec.pairs(P, X, Y, None, X[:1], Y[:1], None, "split", stream=st)
+    J, K = rec.build_laplace(P, X[0], np.array([-1.0, -0.5]), +1, [0.3, 1.2], stream=st)
+    assert J.shape == (2, n, n)
+    for bad in (L, P[:, 1:], P[0]):
+        with pytest.raises(ValueError):
+            rec.build(bad, X, Y, None, "split")
+        with pytest.raises(ValueError):
+            rec.build_laplace(bad, X[0], np.array([-1.0, -0.5]), +1, [0.3])
+    calls = [c for c in rec.lib.calls if c[0] != "jk_set_option"]
+    assert [c[0] for c in calls] == ["jk_build", "jk_build_batched", "jk_pair", "jk_build_laplace"]
+    f = calls[0][1][1]._obj
+    assert (f.nbf, f.naux) == (n, naux)
+    fac = calls[1][1][2]
+    assert [(fac[m].nbf, fac[m].naux) for m in range(2)] == [(n, naux), (6, naux)]
+    assert calls[3][1][1]._obj.nbf == n
+    opt = [c for c in rec.lib.calls if c[0] == "jk_set_option"]
+    assert opt and opt[0][1][1:] == (jk.OPTIONS["packed_factor"], 1)

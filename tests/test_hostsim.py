@@ -95,6 +95,15 @@ def test_case(records, name):
     _check(records[name])
 
 
+def test_packed_factor_refused_before_device_work(shim_dir):
+    """With JK_OPT_PACKED_FACTOR set, the adjoint, the dense-density calls, the
+    host builds and their workspace queries return JK_ERR_UNSUPPORTED before
+    any kernel, memset or copy."""
+    rec = _drive(shim_dir, ["packed_refused"])["packed_refused"]
+    assert rec["status"] == 0 and not rec["violations"], (rec["error"], rec["violations"])
+    assert not rec["launches"] and rec["copies"] == 0
+
+
 @pytest.mark.parametrize("name", FULL_NAMES)
 def test_full_size_case(full_records, name):
     """The measured workloads at their full sizes (bench.py's shapes)."""

@@ -1,0 +1,98 @@
+"""A packed device factor (JK_OPT_PACKED_FACTOR = 1) on the GPU: the factor
+lives on the device as packed upper triangles ([naux][n(n+1)/2], half the
+memory); each aux chunk is expanded in the workspace before its products and
+the FP64 J back-contraction reads the packed form.  With the same aux chunk the
+results must equal the dense factor's bit for bit (the expansion is exact and
+everything downstream is unchanged), and match the oracle."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2608_06536_b300 import inputs, jk
+from tests._util import FP64_REL, SPLIT_ABS, abs_err, rel_err, to_np
+
+pytestmark = pytest.mark.gpu
+
+
+def _both(m, precision, opts, want_k=True):
+    L = torch.from_numpy(m.L).cuda()
+    P = jk.pack_factor(m.L).cuda()
+    X = [torch.from_numpy(x).cuda() for x in m.X]
+    Y = [torch.from_numpy(y).cuda() for y in m.Y]
+    out = []
+    for packed, fac in ((0, L), (1, P)):
+        eng = jk.Engine("cuda:0")
+        for k, v in opts.items():
+            eng.set_option(k, v)
+        eng.set_option("packed_factor", packed)
+        J, K = eng.build(fac, X, Y, m.sym, precision, want_k=want_k)
+        eng.sync_status()
+        out.append((to_np(J), None if K is None else to_np(K)))
+        eng.close()
+    return out
+
+
+@pytest.mark.parametrize("precision,n,naux,ks,sym,opts", [
+    ("split", 130, 70, [9, 3, 20], [False, True, False], {"aux_chunk": 30, "schedule": 0}),
+    ("split", 257, 90, [64, 5], [True, False], {"aux_chunk": 40, "schedule": 1, "syrk": 1}),
+    ("split", 400, 600, [40] * 4, [True, False, False, False], {"aux_chunk": 600, "schedule": 1}),
+    ("fp64", 37, 53, [5, 1, 13], [False, True, False], {"aux_chunk": 17}),
+])
+def test_packed_factor_equals_dense(precision, n, naux, ks, sym, opts):
+    m = inputs.custom(n, naux, max(naux / 4, 1.0), ks, sym)
+    (Jd, Kd), (Jp, Kp) = _both(m, precision, opts)
+    np.testing.assert_array_equal(Jp, Jd)
+    np.testing.assert_array_equal(Kp, Kd)
+    Jo, Ko = oracle.build(m.L, m.X, m.Y)
+    if precision == "split":
+        assert abs_err(Jp, Jo) < SPLIT_ABS and abs_err(Kp, Ko) < SPLIT_ABS
+    else:
+        assert rel_err(Jp, Jo) < FP64_REL and rel_err(Kp, Ko) < FP64_REL
+
+
+@pytest.mark.parametrize("precision", ["fp64", "split"])
+def test_packed_factor_j_only(precision):
+    m = inputs.custom(37, 53, 13.0, [5, 13], [False, True])
+    (Jd, _), (Jp, _) = _both(m, precision, {"aux_chunk": 17}, want_k=False)
+    np.testing.assert_array_equal(Jp, Jd)
+    Jo, _ = oracle.build(m.L, m.X, m.Y)
+    assert abs_err(Jp, Jo) < SPLIT_ABS
+
+
+def test_packed_factor_batched():
+    shapes = [(60, 150, [6, 6]), (140, 222, [11]), (33, 99, [3, 3, 3])]
+    mols = [inputs.custom(n, naux, max(naux / 4, 1.0), ks, [s % 2 == 0 for s in range(len(ks))], seed=i)
+            for i, (n, naux, ks) in enumerate(shapes)]
+    outs = []
+    for packed in (0, 1):
+        eng = jk.Engine("cuda:0")
+        eng.set_option("aux_chunk", 50)
+        eng.set_option("packed_factor", packed)
+        args = []
+        for m in mols:
+            fac = jk.pack_factor(m.L) if packed else torch.from_numpy(m.L)
+            args.append((fac.cuda(), [torch.from_numpy(x).cuda() for x in m.X],
+                         [torch.from_numpy(y).cuda() for y in m.Y], m.sym))
+        res = eng.build_batched(args, "split")
+        eng.sync_status()
+        outs.append([(to_np(J), to_np(K)) for J, K in res])
+        eng.close()
+    for (Jd, Kd), (Jp, Kp), m in zip(outs[0], outs[1], mols):
+        np.testing.assert_array_equal(Jp, Jd)
+        np.testing.assert_array_equal(Kp, Kd)
+        Jo, Ko = oracle.build(m.L, m.X, m.Y)
+        assert abs_err(Jp, Jo) < SPLIT_ABS and abs_err(Kp, Ko) < SPLIT_ABS
+
+
+def test_other_entry_points_refuse_a_packed_factor():
+    m = inputs.custom(20, 30, 8.0, [3], [False])
+    eng = jk.Engine("cuda:0")
+    eng.set_option("packed_factor", 1)
+    L = torch.from_numpy(m.L).cuda()
+    X = [torch.from_numpy(x).cuda() for x in m.X]
+    W = torch.zeros((1, 20, 20), dtype=torch.float64, device="cuda")
+    with pytest.raises(jk.JKError) as e:
+        eng.build_dense(L, W, "split")
+    assert e.value.status == jk.JK_ERR_UNSUPPORTED
+    eng.close()
