@@ -232,12 +232,14 @@ def run_ours(args, rank, world, local):
         m = inputs.multi_state()
     n, naux, ks, sym = m.n, m.naux, m.ks, m.sym
     flops = build_flops(n, naux, ks, sym)
-    Ld = torch.from_numpy(m.L).to(dev)
+    # --packed-factor: the factor resident as packed upper triangles (half the memory)
+    Ld = (jk.pack_factor(m.L) if args.packed_factor else torch.from_numpy(m.L)).to(dev)
     Xd = [torch.from_numpy(x).to(dev) for x in m.X]
     Yd = [torch.from_numpy(y).to(dev) for y in m.Y]
     eng = jk.Engine(dev)
     eng.set_option("slicer", args.slicer)
     eng.set_option("syrk", args.syrk)
+    eng.set_option("packed_factor", 1 if args.packed_factor else 0)
     prec = args.precision
     st = torch.cuda.current_stream(dev)
 
@@ -289,7 +291,7 @@ def run_ours(args, rank, world, local):
             print(json.dumps({"case": args.case, "engine": prec, "ms_per_step": ms_max, "value": value,
                               "kernels_ms": {k: v[0] / args.steps for k, v in prof.items()},
                               "launches_per_step": launches / args.steps, "tuned": tuned, "slicer": args.slicer,
-                              "syrk": args.syrk,
+                              "syrk": args.syrk, "packed_factor": bool(args.packed_factor),
                               "issued_tensor_tflops": issued / args.steps / (ms_max * 1e-3) / 1e12}),
                   flush=True)
         return
@@ -305,6 +307,7 @@ def run_ours(args, rank, world, local):
     h2d = Lh.numel() * 8 + sum(x.numel() * 8 for x in Xh) + sum(y.numel() * 8 for y, s in zip(Yh, sym) if not s)
     d2h = (Jh.numel() + Kh.numel()) * 8
     e2e_steps = max(1, min(args.steps, 3))
+    eng.set_option("packed_factor", 0)      # the host builds take the factor from host memory
     # jk_build_host: the library streams the factor to the device in aux chunks
     # on its own copy stream, overlapped with the build of the previous chunk;
     # densities up and J, K down on the caller's stream.  One untimed call sizes
@@ -368,7 +371,7 @@ def run_ours(args, rank, world, local):
         "config": {"workload": WORKLOAD, "engine": prec, "nbf": n, "naux": naux, "nd": len(ks),
                    "k": ks[0], "l2": "inputs larger than L2 (L = 3.07 GB FP64), no flush",
                    "parallelism": f"replicas x{world}", "tuned": tuned, "slicer": args.slicer,
-                   "syrk": args.syrk},
+                   "syrk": args.syrk, "packed_factor": bool(args.packed_factor)},
         "e2e": e2e,
         "gpu_launches": int(launches),
         "launches_per_step": launches / args.steps,
@@ -549,6 +552,9 @@ def main():
     ap.add_argument("--syrk", type=int, choices=[0, 1], default=0,
                     help="symmetric densities (split engine): 0 full rank update (default), "
                          "1 blocked symmetric rank update, the rest mirrored")
+    ap.add_argument("--packed-factor", dest="packed_factor", action="store_true",
+                    help="device factor stored as packed upper triangles (half the memory; chunks expanded "
+                         "in the workspace)")
     ap.add_argument("--e2e-packed", dest="e2e_packed", action="store_true",
                     help="end-to-end leg with the factor on the host as packed upper triangles "
                          "(jk_build_host_packed: half the bytes over the host link)")
