@@ -1319,7 +1319,10 @@ def fuzz_cases(count, seed):
             if g.random() < 0.5:
                 opts[name] = int(g.integers(0, 2))
         kind = g.choice(["build", "adjoint", "dense", "grad", "pairs", "laplace", "batched", "host"])
-        label = f"fuzz{i}_{kind}_n{n}_a{naux}_p{p}"
+        pk = kind in ("build", "pairs", "laplace", "batched") and g.random() < 0.3   # packed device factor
+        if pk:
+            opts["packed_factor"] = 1
+        label = f"fuzz{i}_{kind}_n{n}_a{naux}_p{p}" + ("_packed" if pk else "")
         if kind == "build":
             out[label] = build_case(n, naux, ks, sym, p, opts, want=str(g.choice(["JK", "JK", "J", "K"])))
         elif kind == "adjoint":
@@ -1346,6 +1349,8 @@ def fuzz_cases(count, seed):
             if g.random() < 0.5:
                 opts["host_chunk"] = int(g.integers(1, naux + 3))
             out[label] = host_case(n, naux, ks[:4], p, opts)
+        if pk:
+            out[label] = packed(out[label])
     return out
 
 
