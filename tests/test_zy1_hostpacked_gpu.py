@@ -6,7 +6,7 @@ import torch
 
 import oracle
 from paper_2608_06536_b300 import inputs
-from tests._util import FP64_REL, SPLIT_ABS, abs_err, rel_err, to_np
+from tests._util import FP64_REL, SPLIT_ABS, abs_err, rel_err
 
 pytestmark = pytest.mark.gpu
 
