@@ -241,11 +241,13 @@ def _check_output(t, name, shape, device):
 
 def pack_factor(L):
     """[naux][n(n+1)/2]: the packed upper triangle (row-major, diagonal
-    included) of each symmetric L^P of a [naux][n][n] CPU tensor or array, the
-    layout jk_build_host_packed uploads."""
+    included) of each symmetric L^P of a [naux][n][n] tensor or array, on the
+    input's device: the layout jk_build_host_packed uploads and the packed
+    device factor (option packed_factor) holds.  A one-time input conversion,
+    not a step of the build."""
     L = torch.as_tensor(L, dtype=torch.float64)
     n = int(L.shape[-1])
-    iu = torch.triu_indices(n, n)
+    iu = torch.triu_indices(n, n, device=L.device)
     return L[:, iu[0], iu[1]].contiguous()
 
 
