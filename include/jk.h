@@ -303,7 +303,7 @@ typedef enum {
                                additions (fewer instructions per element; an
                                equally exact split, digits differ only where a
                                digit rounds a tie)                               */
-    JK_OPT_SYRK = 7,        /* split engine, symmetric densities: 0 (default)
+    JK_OPT_SYRK = 7,        /* symmetric densities (both engines): 0 (default)
                                full rank update, 1 only the row blocks of
                                128 rows from their diagonal on (K of the
                                symmetric build, the U = V case of Sec. II.C,

@@ -462,16 +462,31 @@ __global__ void sum_parts_kernel(double *out, const double *part, int nb, long l
     out[e] = acc;
 }
 
+// out[r*ldo + c] (+)= sum_b part[b][r*N + c] for r < M, c < N, b in increasing
+// order: the same sum into a block of a larger matrix.
+__global__ void sum_parts_ld_kernel(double *out, long long ldo, const double *part, int nb, int M, int N,
+                                    int accumulate) {
+    const long long MN = (long long)M * N;
+    const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (e >= MN) return;
+    const long long r = e / N, c = e - r * N;
+    double *o = out + r * ldo + c;
+    double acc = accumulate ? *o : 0.0;
+    for (int b = 0; b < nb; b++) acc += part[(long long)b * MN + e];
+    *o = acc;
+}
+
 // C (+)= sum over q in [0, nq) and inner index t in [0, kin) of
 // A[m][q][t] B[n][q][t]  (element (m, q, t) of A at A + m*a_sr + q*a_sq + t*a_st,
-// likewise B), with C dense M x N.  A small output (few 64 x 64 tiles) would
-// leave most SMs idle for a long reduction, so the reduction is split over
-// groups of q: one batched launch of partial products (plus one for a
-// remainder group), then their sum into C in a fixed order.
+// likewise B), with C M x N of row stride ldc (0: dense, ldc = N).  A small
+// output (few 64 x 64 tiles) would leave most SMs idle for a long reduction,
+// so the reduction is split over groups of q: one batched launch of partial
+// products (plus one for a remainder group), then their sum into C in a fixed
+// order.
 static jk_status dgemm_split_q(jk_ctx *h, int M, int N, int nq, int kin, const double *A, long long a_sr,
                                long long a_sq, long long a_st, const double *B, long long b_sr, long long b_sq,
                                long long b_st, double *C, bool accumulate, double *part, int max_split,
-                               cudaStream_t st) {
+                               cudaStream_t st, long long ldc = 0) {
     const long long MN = (long long)M * N;
     const int tiles = ((N + GBN - 1) / GBN) * ((M + GBM - 1) / GBM);
     int ns = (h->num_sms + tiles - 1) / tiles;
@@ -489,19 +504,35 @@ static jk_status dgemm_split_q(jk_ctx *h, int M, int N, int nq, int kin, const d
                      1.0, 0.0, st));
     {
         LaunchScope ls(h, KK_MISC, st);
-        sum_parts_kernel<<<(unsigned)((MN + 255) / 256), 256, 0, st>>>(C, part, nfull + (rem > 0), MN,
-                                                                      accumulate ? 1 : 0);
+        if (ldc == 0 || ldc == N)
+            sum_parts_kernel<<<(unsigned)((MN + 255) / 256), 256, 0, st>>>(C, part, nfull + (rem > 0), MN,
+                                                                          accumulate ? 1 : 0);
+        else
+            sum_parts_ld_kernel<<<(unsigned)((MN + 255) / 256), 256, 0, st>>>(C, ldc, part, nfull + (rem > 0), M, N,
+                                                                             accumulate ? 1 : 0);
     }
     JK_LAUNCH_CHECK(h);
     return JK_OK;
 }
 
 // K_s (+)= sum over the chunk's (p, i) of T[p][mu][offX+i] T[p][nu][offY+i].
+// A symmetric density under JK_OPT_SYRK forms only row blocks of kSymBlock
+// rows from their diagonal on (the rest is mirrored after the last chunk).
 static jk_status rank_update_fp64(jk_ctx *h, const Problem &pb, const double *T, int np, int s, bool accumulate,
                                   double *part, cudaStream_t st) {
     const long long sp = (long long)pb.n * pb.ctot;
-    return dgemm_split_q(h, pb.n, pb.n, np, pb.k[s], T + pb.offX[s], pb.ctot, sp, 1, T + pb.offY[s], pb.ctot, sp,
-                         1, pb.K[s], accumulate, part, kMaxRankSplit, st);
+    const int n = pb.n;
+    if (!(pb.sym[s] && h->syrk))
+        return dgemm_split_q(h, n, n, np, pb.k[s], T + pb.offX[s], pb.ctot, sp, 1, T + pb.offY[s], pb.ctot, sp, 1,
+                             pb.K[s], accumulate, part, kMaxRankSplit, st);
+    for (int r0 = 0; r0 < n; r0 += kSymBlock) {
+        const int m = n - r0 < kSymBlock ? n - r0 : kSymBlock;
+        const long long ro = (long long)r0 * pb.ctot;
+        JK_TRY(dgemm_split_q(h, m, n - r0, np, pb.k[s], T + pb.offX[s] + ro, pb.ctot, sp, 1, T + pb.offY[s] + ro,
+                             pb.ctot, sp, 1, pb.K[s] + (long long)r0 * n + r0, accumulate, part, kMaxRankSplit, st,
+                             n));
+    }
+    return JK_OK;
 }
 
 jk_status fp64_build(jk_ctx *h, const Problem &pb, cudaStream_t st) {
@@ -581,6 +612,9 @@ jk_status fp64_build(jk_ctx *h, const Problem &pb, cudaStream_t st) {
             JK_LAUNCH_CHECK(h);
         }
     }
+    if (K && h->syrk)
+        for (int s = 0; s < nd; s++)
+            if (pb.sym[s]) JK_TRY(mirror_sym_blocks(h, pb.K[s], n, st));
     if (J) JK_TRY(jstream(h, pb.L, n, naux, gamma, naux, nd, pb.J, st, pb.packed));
     return JK_OK;
 }

@@ -115,6 +115,13 @@ struct Problem {
 
 jk_status set_error(jk_ctx *h, jk_status s, const char *fmt, ...);
 
+// Rows per block of the blocked symmetric rank update (JK_OPT_SYRK): row block
+// [r0, r0 + kSymBlock) of K_s is formed from column r0 on.
+constexpr int kSymBlock = 128;
+// K[r][c] = K[c][r] for every c < kSymBlock * (r / kSymBlock): the entries a
+// blocked symmetric rank update leaves unformed.
+jk_status mirror_sym_blocks(jk_ctx *h, double *K, int n, cudaStream_t st);
+
 // The file name of a source path (messages name the file, not the directory
 // it was built in).
 inline const char *source_name(const char *path) {

@@ -1174,15 +1174,19 @@ static jk_status sym_rank_reduce(jk_ctx *h, const Sliced &TX, int n, const long 
     return JK_OK;
 }
 
-static jk_status mirror_blocks(jk_ctx *h, double *K, int n, cudaStream_t st) {
+static_assert(kSymBlock == oz::BM, "symmetric row blocks are single GEMM row tiles");
+
+jk_status mirror_sym_blocks(jk_ctx *h, double *K, int n, cudaStream_t st) {
     const long long n2 = static_cast<long long>(n) * n;
     {
         LaunchScope ls(h, KK_MISC, st);
-        oz::mirror_blocks_kernel<<<static_cast<unsigned>((n2 + 255) / 256), 256, 0, st>>>(K, n, oz::BM);
+        oz::mirror_blocks_kernel<<<static_cast<unsigned>((n2 + 255) / 256), 256, 0, st>>>(K, n, kSymBlock);
     }
     JK_LAUNCH_CHECK(h);
     return JK_OK;
 }
+
+static jk_status mirror_blocks(jk_ctx *h, double *K, int n, cudaStream_t st) { return mirror_sym_blocks(h, K, n, st); }
 
 // ---------------------------------------------------------------------------
 // The split build

@@ -353,8 +353,8 @@ class Engine:
         """Handle option (JK_OPT_*): "aux_chunk" (>= 0, 0 = automatic, -1 =
         tuned/default), "schedule", "raster" and "cluster" (-1 = tuned/default,
         0, 1), "use_tuned" (0 or 1), "host_chunk" (>= 0, 0 = automatic),
-        "slicer" (0 integer digits, 1 FP32 digits), "syrk" (split engine,
-        symmetric densities: 0 full rank update, 1 blocked symmetric rank
+        "slicer" (0 integer digits, 1 FP32 digits), "syrk" (symmetric
+        densities, both engines: 0 full rank update, 1 blocked symmetric rank
         update with the rest mirrored), "packed_factor" (1: the factor given
         to build, build_batched, pairs, build_laplace and autotune* is
         pack_factor(L), [naux][n(n+1)/2] on the device; half the memory).

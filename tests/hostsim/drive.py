@@ -231,6 +231,13 @@ def dec_axpy(grid, args):
     return [(y, y + 8 * cnt, "y"), (x, x + 8 * cnt, "x")]
 
 
+def dec_sum_parts_ld(grid, args):
+    out, ldo, part, nb, M, N = (_v(args, 0, VP), _v(args, 1, I64), _v(args, 2, VP), _v(args, 3, I32),
+                                _v(args, 4, I32), _v(args, 5, I32))
+    assert grid[0] * 256 >= M * N and ldo >= N, (grid, M, N, ldo)
+    return [(out, out + 8 * ((M - 1) * ldo + N), "out"), (part, part + 8 * nb * M * N, "part")]
+
+
 def dec_mirror_blocks(grid, args):
     K, n, bm = _v(args, 0, VP), _v(args, 1, I32), _v(args, 2, I32)
     assert bm >= 1 and grid[0] * 256 >= n * n, (grid, n)
@@ -443,6 +450,15 @@ def ex_jstream_sym(grid, args, name):
 def ex_axpy(grid, args):
     y, x, cnt = _v(args, 0, VP), _v(args, 1, VP), _v(args, 2, I64)
     dv(y, cnt)[:] += dv(x, cnt)
+
+
+def ex_sum_parts_ld(grid, args):
+    out, ldo, part, nb, M, N, acc = (_v(args, 0, VP), _v(args, 1, I64), _v(args, 2, VP), _v(args, 3, I32),
+                                     _v(args, 4, I32), _v(args, 5, I32), _v(args, 6, I32))
+    tot = dv(part, nb * M * N).reshape(nb, M, N).sum(axis=0)
+    idx = np.arange(M)[:, None] * ldo + np.arange(N)[None, :]
+    o = dv(out, (M - 1) * ldo + N)
+    o[idx] = (o[idx] if acc else 0.0) + tot
 
 
 def ex_mirror_blocks(grid, args):
@@ -705,7 +721,7 @@ EXECUTORS = [
     ("expo_flat_kernel", ex_expo_flat), ("expo_kernel", ex_expo), ("slice4f_kernel", ex_slice),
     ("slice4_kernel", ex_slice), ("slice_kernel", ex_slice), ("ozgemm_kernel", ex_ozgemm),
     ("reduce_partials_kernel", ex_reduce), ("pack_ag_kernel", ex_pack_ag), ("pack_bg_kernel", ex_pack_bg),
-    ("sym_dl_kernel", ex_sym_dl), ("mirror_blocks_kernel", ex_mirror_blocks),
+    ("sym_dl_kernel", ex_sym_dl), ("mirror_blocks_kernel", ex_mirror_blocks), ("sum_parts_ld_kernel", ex_sum_parts_ld),
 ]
 
 DECODERS = [
@@ -718,7 +734,7 @@ DECODERS = [
     ("slice4f_kernel", dec_slice4), ("unpack_sym_kernel", dec_unpack_sym),
     ("symmetrize_kernel", dec_symmetrize), ("sym_dl_kernel", dec_sym_dl), ("fold_sym_split_kernel", dec_fold),
     ("fold_sym_kernel", dec_fold), ("pack_ag_kernel", dec_pack_ag), ("pack_bg_kernel", dec_pack_bg),
-    ("mirror_blocks_kernel", dec_mirror_blocks),
+    ("mirror_blocks_kernel", dec_mirror_blocks), ("sum_parts_ld_kernel", dec_sum_parts_ld),
 ]
 violations, decoded, undecoded = [], [0], set()
 
@@ -1216,6 +1232,9 @@ CASES = {
                                             {"syrk": 1, "schedule": 0, "aux_chunk": 70}),
     "build_split_syrk_grouped": build_case(257, 90, [64, 5, 11], [True, True, False], SPLIT,
                                            {"syrk": 1, "schedule": 1, "aux_chunk": 40}),
+    "build_fp64_syrk": build_case(300, 70, [20, 9, 33], [True, False, True], FP64, {"syrk": 1, "aux_chunk": 30}),
+    "build_fp64_syrk_packed": packed(build_case(257, 40, [12, 5], [True, True], FP64,
+                                                {"syrk": 1, "packed_factor": 1})),
     "build_split_syrk_small_clustered": build_case(100, 30, [7, 4], [True, False], SPLIT,
                                                    {"syrk": 1, "schedule": 1, "cluster": 1}),
     "batched_split_syrk": batched_case([(60, 150, [6, 6]), (140, 222, [11]), (33, 99, [3, 3, 3])], SPLIT,

@@ -35,6 +35,7 @@ def _dev(m):
 
 
 @pytest.mark.parametrize("n,naux,ks,sym,opts", [
+    (300, 70, [20, 9, 33], [True, False, True], {"aux_chunk": 30, "precision": "fp64"}),  # FP64 engine
     (300, 70, [20, 9, 33], [True, False, True], {"schedule": 0, "aux_chunk": 30}),      # chunk sums
     (300, 120, [40, 7], [True, True], {"schedule": 0, "aux_chunk": 70}),                # split-K partials
     (257, 90, [64, 5, 11], [True, True, False], {"schedule": 1, "aux_chunk": 40}),      # grouped, ragged
@@ -43,15 +44,17 @@ def _dev(m):
 ])
 def test_blocked_symmetric_rank_update(n, naux, ks, sym, opts):
     from paper_2608_06536_b300 import jk
+    opts = dict(opts)
+    prec = opts.pop("precision", "split")
     m = inputs.custom(n, naux, max(naux / 4, 1.0), ks, sym)
     Jo, Ko = oracle.build(m.L, m.X, m.Y)
     L, X, Y = _dev(m)
     eng = jk.Engine("cuda:0")
     for k, v in opts.items():
         eng.set_option(k, v)
-    J0, K0 = eng.build(L, X, Y, m.sym, "split")
+    J0, K0 = eng.build(L, X, Y, m.sym, prec)
     eng.set_option("syrk", 1)
-    J1, K1 = eng.build(L, X, Y, m.sym, "split")
+    J1, K1 = eng.build(L, X, Y, m.sym, prec)
     eng.sync_status()
     J0, K0, J1, K1 = to_np(J0), to_np(K0), to_np(J1), to_np(K1)
     eng.close()
