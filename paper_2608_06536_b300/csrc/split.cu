@@ -1186,8 +1186,6 @@ jk_status mirror_sym_blocks(jk_ctx *h, double *K, int n, cudaStream_t st) {
     return JK_OK;
 }
 
-static jk_status mirror_blocks(jk_ctx *h, double *K, int n, cudaStream_t st) { return mirror_sym_blocks(h, K, n, st); }
-
 // ---------------------------------------------------------------------------
 // The split build
 // ---------------------------------------------------------------------------
@@ -1373,7 +1371,7 @@ jk_status split_build(jk_ctx *h, const Problem &pb, cudaStream_t st) {
     }
     if (pb.wantK && h->syrk)
         for (int s = 0; s < nd; s++)
-            if (pb.sym[s]) JK_TRY(mirror_blocks(h, pb.K[s], n, st));
+            if (pb.sym[s]) JK_TRY(mirror_sym_blocks(h, pb.K[s], n, st));
     if (pb.wantJ) JK_TRY(join_jstream(h, st));
     return JK_OK;
 }
@@ -1881,7 +1879,7 @@ jk_status split_batched(jk_ctx *h, int nmol, const Problem *pbs, cudaStream_t st
         for (int m = 0; m < nmol; m++)
             if (pbs[m].wantK)
                 for (int s = 0; s < pbs[m].nd; s++)
-                    if (pbs[m].sym[s]) JK_TRY(mirror_blocks(h, pbs[m].K[s], pbs[m].n, st));
+                    if (pbs[m].sym[s]) JK_TRY(mirror_sym_blocks(h, pbs[m].K[s], pbs[m].n, st));
     if (forked) JK_TRY(join_jstream(h, st));
     return JK_OK;
 }
