@@ -294,3 +294,21 @@ def test_packed_host_query(lib):
         chunk = (600 + 11) // 12
         assert nb_packed.value - nb_full.value >= 2 * chunk * (100 * 101 // 2) * 8
     assert lib.jk_build_host_packed(None, ct.byref(f), 1, d, None, None, 0, None) == jk.JK_ERR_ARG
+
+
+def test_binding_constants_match_the_header():
+    """The binding's option, operation, status and precision codes (and the host
+    simulation's option table) are the values include/jk.h declares."""
+    hdr = open(os.path.join(ROOT, "include", "jk.h")).read()
+    enum = {m.group(1): int(m.group(2)) for m in re.finditer(r"\b(JK_[A-Z0-9_]+)\s*=\s*(\d+)", hdr)}
+    for name, code in jk.OPTIONS.items():
+        assert enum["JK_OPT_" + name.upper()] == code, name
+    assert {k for k in enum if k.startswith("JK_OPT_")} == {"JK_OPT_" + k.upper() for k in jk.OPTIONS}
+    for name in ("JK_OK", "JK_ERR_ARG", "JK_ERR_SHAPE", "JK_ERR_OOM", "JK_ERR_CUDA", "JK_ERR_TIMEOUT",
+                 "JK_ERR_UNSUPPORTED", "JK_FP64", "JK_SPLIT_BF16", "JK_OP_BUILD", "JK_OP_ADJOINT", "JK_OP_BATCHED",
+                 "JK_OP_BUILD_HOST", "JK_OP_BUILD_DENSE", "JK_OP_DENSITY_GRAD", "JK_OP_PAIR", "JK_OP_LAPLACE",
+                 "JK_OP_BUILD_HOST_PACKED"):
+        assert getattr(jk, name) == enum[name], name
+    sim = open(os.path.join(ROOT, "tests", "hostsim", "drive.py")).read()
+    table = sim.split("OPT = {", 1)[1].split("}", 1)[0]
+    assert {k: int(v) for k, v in re.findall(r'"(\w+)": (\d+)', table)} == jk.OPTIONS

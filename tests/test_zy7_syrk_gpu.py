@@ -1,4 +1,4 @@
-"""The blocked symmetric rank update of the split engine (JK_OPT_SYRK = 1) on
+"""The blocked symmetric rank update (JK_OPT_SYRK = 1, both engines) on
 the GPU: for symmetric densities only the row blocks from the diagonal on are
 formed (row views of the sliced T_X) and the rest is mirrored.  The mirrored
 entries must equal their transposes exactly, and K must match the full rank update (option 0) within the split
