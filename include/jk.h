@@ -327,6 +327,17 @@ typedef enum {
 /* Options set explicitly on a handle override tuned configurations. */
 jk_status jk_set_option(jk_handle h, jk_option opt, int64_t value);
 
+/* jk_pack_factor: the packed form of a symmetric factor, for
+ * JK_OPT_PACKED_FACTOR (L^P = L^P^T, Sec. II.C's CD vectors; only the upper
+ * triangle is read).  P[p][a*nbf - a(a-1)/2 + b - a] = L[p][a][b], a <= b.
+ *   L : [naux][nbf][nbf] FP64 device input (16-byte aligned).
+ *   P : [naux][nbf(nbf+1)/2] FP64 device output, caller-owned, not
+ *       overlapping L (16-byte aligned for use as a factor).
+ * One kernel on `stream`, no workspace.  Status: JK_ERR_SHAPE if nbf is
+ * outside [1, 65535] or naux < 1; JK_ERR_ARG for a NULL, misaligned,
+ * non-device or overlapping pointer (nothing is launched). */
+jk_status jk_pack_factor(jk_handle h, int32_t nbf, int32_t naux, const double *L, double *P, void *stream);
+
 /* ---------------------------------------------------------------------------
  * Autotuner.  A configuration is the set of run-time choices a build makes
  * (aux-index chunk, launch schedule, GEMM tile order, CTA clustering).  jk_autotune times the

@@ -368,6 +368,29 @@ jk_status fp64_unpack_sym(jk_ctx *h, const double *packed, int n, long long np, 
     return JK_OK;
 }
 
+// P[p][t] = F[p][a][b] for the packed position t of (a, b), a <= b: the upper
+// triangles of np symmetric n x n matrices (packed.cuh layout).  One thread per
+// packed entry; consecutive threads read consecutive columns of a row.
+__global__ void pack_sym_kernel(const double *F, int n, long long np, double *P) {
+    const long long ntri = packed::tri_count(n);
+    const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (e >= np * ntri) return;
+    const long long p = e / ntri, t = e - p * ntri;
+    int a, b;
+    packed::tri_row_col(n, t, &a, &b);
+    P[e] = F[p * (long long)n * n + (long long)a * n + b];
+}
+
+jk_status fp64_pack_sym(jk_ctx *h, const double *full, int n, long long np, double *packed_out, cudaStream_t st) {
+    const long long tot = np * packed::tri_count(n);
+    {
+        LaunchScope ls(h, KK_PACK, st);
+        pack_sym_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(full, n, np, packed_out);
+    }
+    JK_LAUNCH_CHECK(h);
+    return JK_OK;
+}
+
 // y += x (FP64, elementwise)
 __global__ void axpy_kernel(double *y, const double *x, long long cnt) {
     long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;

@@ -1111,6 +1111,20 @@ jk_status jk_build_laplace(jk_handle h, const jk_factor *f, int32_t nq, const do
     return JK_OK;
 }
 
+jk_status jk_pack_factor(jk_handle h, int32_t nbf, int32_t naux, const double *L, double *P, void *stream) {
+    JK_TRY(begin_call(h));
+    if (nbf < 1 || nbf > 65535 || naux < 1)
+        return set_error(h, JK_ERR_SHAPE, "nbf=%d naux=%d: nbf must be in [1, 65535], naux >= 1", nbf, naux);
+    if (!L || !P) return set_error(h, JK_ERR_ARG, "L or P is NULL");
+    JK_TRY(check_in(h, L, "L"));
+    JK_TRY(check_out(h, P, "P"));
+    const long long tri = tri_count(nbf);
+    const char *lo = reinterpret_cast<const char *>(L), *po = reinterpret_cast<const char *>(P);
+    const long long lb = static_cast<long long>(naux) * nbf * nbf * 8, pb = static_cast<long long>(naux) * tri * 8;
+    if (po < lo + lb && lo < po + pb) return set_error(h, JK_ERR_ARG, "L and P overlap");
+    return fp64_pack_sym(h, L, nbf, naux, P, static_cast<cudaStream_t>(stream));
+}
+
 jk_status jk_set_option(jk_handle h, jk_option opt, int64_t value) {
     if (!h) return JK_ERR_ARG;
     if (opt == JK_OPT_AUX_CHUNK) {

@@ -169,6 +169,8 @@ jk_status fp64_axpy(jk_ctx *h, double *y, const double *x, long long cnt, cudaSt
 // full[p] = the symmetric n x n matrix whose packed upper triangle is
 // packed[p] ([np][n(n+1)/2], row-major, diagonal included).
 jk_status fp64_unpack_sym(jk_ctx *h, const double *packed, int n, long long np, double *full, cudaStream_t st);
+// packed[p][t(a,b)] = full[p][a][b], a <= b (the inverse of fp64_unpack_sym)
+jk_status fp64_pack_sym(jk_ctx *h, const double *full, int n, long long np, double *packed_out, cudaStream_t st);
 
 // ---- split-precision engine (split.cu) -----------------------------------
 size_t split_build_workspace(const Problem &pb);

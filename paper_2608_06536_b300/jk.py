@@ -107,6 +107,8 @@ def load_library(path: str = LIB_PATH):
         L.jk_build_laplace.argtypes = [vp, ct.POINTER(jk_factor), ct.c_int32, dpp, dpp, ct.c_int32, vp, vp,
                                        ct.c_int32, vp, vp, ct.c_int32, vp, vp, ct.c_int, vp]
         L.jk_build_laplace.restype = ct.c_int
+        L.jk_pack_factor.argtypes = [vp, ct.c_int32, ct.c_int32, vp, vp, vp]
+        L.jk_pack_factor.restype = ct.c_int
         L.jk_build_dense.restype = ct.c_int
         L.jk_density_grad.restype = ct.c_int
         L.jk_tune_export.argtypes = [ct.c_char_p, sz, ct.POINTER(sz)]
@@ -243,11 +245,14 @@ def pack_factor(L):
     """[naux][n(n+1)/2]: the packed upper triangle (row-major, diagonal
     included) of each symmetric L^P of a [naux][n][n] tensor or array, on the
     input's device: the layout jk_build_host_packed uploads and the packed
-    device factor (option packed_factor) holds.  A one-time input conversion,
-    not a step of the build."""
+    device factor (option packed_factor) holds.  A device tensor is packed by
+    the library (jk_pack_factor); a host one (the host link's input) by an
+    index gather on the host."""
     L = torch.as_tensor(L, dtype=torch.float64)
+    if L.is_cuda:
+        return default_engine(L.device).pack_factor(L)
     n = int(L.shape[-1])
-    iu = torch.triu_indices(n, n, device=L.device)
+    iu = torch.triu_indices(n, n)
     return L[:, iu[0], iu[1]].contiguous()
 
 
@@ -590,6 +595,23 @@ class Engine:
         self._check(st, self._h)
         self._record(stream)
         return J, K
+
+    def pack_factor(self, L, P=None, stream=None):
+        """jk_pack_factor: [naux][n(n+1)/2] packed upper triangles of a device
+        factor [naux][n][n] (into P if given)."""
+        Ls = _shape(L)
+        if len(Ls) != 3 or Ls[1] != Ls[2] or min(Ls) < 1:
+            raise ValueError(f"L must be [naux][nbf][nbf] with naux, nbf >= 1, got {Ls}")
+        naux, n = Ls[0], Ls[1]
+        L = _dev_f64(L, self.device)
+        _check_output(P, "P", (naux, n * (n + 1) // 2), self.device)
+        if P is None:
+            P = torch.empty((naux, n * (n + 1) // 2), dtype=torch.float64, device=self.device)
+        if not self._h:
+            self._ensure(1 << 20)
+        self._check(self.lib.jk_pack_factor(self._h, n, naux, _ptr(L), _ptr(P), _stream_ptr(stream)), self._h)
+        self._record(stream)
+        return P
 
     def autotune(self, L, X, Y=None, sym=None, precision="split", reps: int = 3, stream=None):
         """Time the candidate configurations of this build and cache the

@@ -238,6 +238,13 @@ def dec_sum_parts_ld(grid, args):
     return [(out, out + 8 * ((M - 1) * ldo + N), "out"), (part, part + 8 * nb * M * N, "part")]
 
 
+def dec_pack_sym(grid, args):
+    F, n, np_, P = _v(args, 0, VP), _v(args, 1, I32), _v(args, 2, I64), _v(args, 3, VP)
+    tri = n * (n + 1) // 2
+    assert grid[0] * 256 >= np_ * tri
+    return [(F, F + 8 * np_ * n * n, "full"), (P, P + 8 * np_ * tri, "packed")]
+
+
 def dec_mirror_blocks(grid, args):
     K, n, bm = _v(args, 0, VP), _v(args, 1, I32), _v(args, 2, I32)
     assert bm >= 1 and grid[0] * 256 >= n * n, (grid, n)
@@ -459,6 +466,12 @@ def ex_sum_parts_ld(grid, args):
     idx = np.arange(M)[:, None] * ldo + np.arange(N)[None, :]
     o = dv(out, (M - 1) * ldo + N)
     o[idx] = (o[idx] if acc else 0.0) + tot
+
+
+def ex_pack_sym(grid, args):
+    F, n, np_, P = _v(args, 0, VP), _v(args, 1, I32), _v(args, 2, I64), _v(args, 3, VP)
+    iu = np.triu_indices(n)
+    dv(P, np_ * len(iu[0])).reshape(np_, -1)[:] = dv(F, np_ * n * n).reshape(np_, n, n)[:, iu[0], iu[1]]
 
 
 def ex_mirror_blocks(grid, args):
@@ -722,6 +735,7 @@ EXECUTORS = [
     ("slice4_kernel", ex_slice), ("slice_kernel", ex_slice), ("ozgemm_kernel", ex_ozgemm),
     ("reduce_partials_kernel", ex_reduce), ("pack_ag_kernel", ex_pack_ag), ("pack_bg_kernel", ex_pack_bg),
     ("sym_dl_kernel", ex_sym_dl), ("mirror_blocks_kernel", ex_mirror_blocks), ("sum_parts_ld_kernel", ex_sum_parts_ld),
+    ("pack_sym_kernel", ex_pack_sym),
 ]
 
 DECODERS = [
@@ -735,6 +749,7 @@ DECODERS = [
     ("symmetrize_kernel", dec_symmetrize), ("sym_dl_kernel", dec_sym_dl), ("fold_sym_split_kernel", dec_fold),
     ("fold_sym_kernel", dec_fold), ("pack_ag_kernel", dec_pack_ag), ("pack_bg_kernel", dec_pack_bg),
     ("mirror_blocks_kernel", dec_mirror_blocks), ("sum_parts_ld_kernel", dec_sum_parts_ld),
+    ("pack_sym_kernel", dec_pack_sym),
 ]
 violations, decoded, undecoded = [], [0], set()
 
@@ -1160,6 +1175,40 @@ def laplace_case(n, naux, m, nq, sym, weighted, p, opts):
     return fn
 
 
+def pack_factor_case(n, naux):
+    """jk_pack_factor, then a build on the packed factor it wrote."""
+    def fn():
+        f, d, L, X, Y = mol(n, naux, [5, 3], [False, True])
+        h = handle(1 << 20, {}, scaled=False)
+        P = buf((naux, n * (n + 1) // 2), "P", False)
+        lib.jk_pack_factor.argtypes = [ct.c_void_p, ct.c_int32, ct.c_int32, ct.c_void_p, ct.c_void_p, ct.c_void_p]
+        st = lib.jk_pack_factor(h, n, naux, ptr(L), ptr(P), None)
+        if st != 0:
+            return st, h
+        bad = [lib.jk_pack_factor(h, 0, naux, ptr(L), ptr(P), None), lib.jk_pack_factor(h, n, 0, ptr(L), ptr(P), None),
+               lib.jk_pack_factor(h, n, naux, None, ptr(P), None),
+               lib.jk_pack_factor(h, n, naux, ptr(L), ct.c_void_p(L.ctypes.data + 8), None)]
+        assert bad == [2, 2, 1, 1], bad
+        if EXEC[0]:
+            iu = np.triu_indices(n)
+            check("P", P, L[:, iu[0], iu[1]])
+        lib.jk_destroy(h)
+        opts = {"packed_factor": 1}
+        h = handle(1 << 20, opts, scaled=False)
+        fp = jk_factor(n, naux, P.ctypes.data)
+        nb = query(0, fp, d, 2, SPLIT, h=h)
+        lib.jk_destroy(h)
+        h = handle(nb, opts)
+        J, K = buf((2, n, n), "J", False), buf((2, n, n), "K", False)
+        st = lib.jk_build(h, ct.byref(fp), 2, d, ptr(J), ptr(K), SPLIT, None)
+        if EXEC[0] and st == 0:
+            Jo, Ko = oracle_mod().build(L, X, _ylist(X, Y, [False, True]))
+            check("J", J, Jo)
+            check("K", K, Ko)
+        return st, h
+    return fn
+
+
 def packed_refused_case():
     """With JK_OPT_PACKED_FACTOR set, the entry points that read the factor
     outside ordinary builds refuse the call before any device work."""
@@ -1286,6 +1335,7 @@ CASES = {
     "pairs_split_packed": packed(pair_case(40, 60, [3, 5], [False, True], [4, 6, 2], [False, False, True], SPLIT,
                                            {"packed_factor": 1})),
     "laplace_split_packed": packed(laplace_case(37, 53, 5, 4, False, True, SPLIT, {"packed_factor": 1})),
+    "pack_factor_then_build": pack_factor_case(70, 45),
     "autotune_split": autotune_case(37, 53, [5, 13], SPLIT),
 }
 

@@ -96,3 +96,21 @@ def test_other_entry_points_refuse_a_packed_factor():
         eng.build_dense(L, W, "split")
     assert e.value.status == jk.JK_ERR_UNSUPPORTED
     eng.close()
+
+
+def test_pack_factor_on_the_device():
+    """jk_pack_factor writes exactly the host packing, and builds run on it."""
+    m = inputs.custom(70, 45, 12.0, [5, 3], [False, True])
+    L = torch.from_numpy(m.L).cuda()
+    eng = jk.Engine("cuda:0")
+    P = eng.pack_factor(L)
+    eng.sync_status()
+    np.testing.assert_array_equal(to_np(P), jk.pack_factor(m.L).numpy())
+    np.testing.assert_array_equal(to_np(jk.pack_factor(L)), to_np(P))      # module-level, device input
+    eng.set_option("packed_factor", 1)
+    J, K = eng.build(P, [torch.from_numpy(x).cuda() for x in m.X], [torch.from_numpy(y).cuda() for y in m.Y],
+                     m.sym, "split")
+    eng.sync_status()
+    Jo, Ko = oracle.build(m.L, m.X, m.Y)
+    assert abs_err(to_np(J), Jo) < SPLIT_ABS and abs_err(to_np(K), Ko) < SPLIT_ABS
+    eng.close()
