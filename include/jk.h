@@ -319,7 +319,10 @@ typedef enum {
                                expanded into the workspace before its
                                products; the FP64 J back-contraction reads the
                                packed form.  Results equal the dense factor's
-                               bit for bit.  Size the arena with
+                               bit for bit at the same aux chunk (the automatic
+                               chunk can be smaller, as the expanded copy counts
+                               against its budget: then they differ by
+                               summation order only).  Size the arena with
                                jk_workspace_query_handle (the handle-free query
                                assumes a dense factor).  The other entry
                                points return JK_ERR_UNSUPPORTED while it is 1 */
