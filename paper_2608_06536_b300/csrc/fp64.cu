@@ -171,6 +171,38 @@ frob_stream_kernel(const double *L, long long n2, const double *Mats, int nd,
     }
 }
 
+// The same metric dots from packed upper triangles ([naux][n(n+1)/2]):
+// <L^P, M> = sum_{a <= b} L^P_t(a,b) (M_ab + M_ba), the diagonal once.  Each
+// thread walks its packed positions t, t + 256, ... keeping (a, b)
+// incrementally (no square root per element).
+__global__ void __launch_bounds__(256)
+frob_packed_kernel(const double *L, int n, const double *Mats, int nd, double *gamma, int ldg, int P0) {
+    __shared__ double red[8];
+    const int p = blockIdx.x;
+    const int s0 = blockIdx.y * 4;
+    const int ns = min(4, nd - s0);
+    const long long ntri = packed::tri_count(n), n2 = (long long)n * n;
+    const double *LP = L + (long long)(P0 + p) * ntri;
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    int a = 0, b = 0;
+    if (threadIdx.x < ntri) packed::tri_row_col(n, threadIdx.x, &a, &b);
+    for (long long t = threadIdx.x; t < ntri; t += 256) {
+        const double l = LP[t];
+        const long long ab = (long long)a * n + b, ba = (long long)b * n + a;
+#pragma unroll
+        for (int j = 0; j < 4; j++)
+            if (j < ns) {
+                const double *M = Mats + (long long)(s0 + j) * n2;
+                acc[j] = fma(l, a == b ? M[ab] : M[ab] + M[ba], acc[j]);
+            }
+        packed::tri_advance(n, 256, &a, &b);   // the next position of this thread
+    }
+    for (int j = 0; j < ns; j++) {
+        double t = block_sum_256(acc[j], red);
+        if (threadIdx.x == 0) gamma[(long long)(s0 + j) * ldg + P0 + p] = t;
+    }
+}
+
 // gamma[s*ldg + P0 + p] = sum_{sig,i} T^p[sig][offX_s + i] * Y_s[sig][i]
 // (= <L^P, X_s Y_s^T>, from the panel already formed for K).
 struct DensTab {
@@ -430,22 +462,28 @@ jk_status fp64_gamma_panel(jk_ctx *h, const Problem &pb, const double *T, long l
     return JK_OK;
 }
 
-// out[s*naux + P] = <L^P, M_s> for dense n x n matrices M_s (s < nd).
+// out[s*naux + P] = <L^P, M_s> for dense n x n matrices M_s (s < nd); pk: L
+// holds packed upper triangles.
 jk_status fp64_frob_all(jk_ctx *h, const double *L, int n, int naux, const double *Mats, int nd, double *out,
-                        cudaStream_t st) {
+                        cudaStream_t st, bool pk) {
     const long long n2 = (long long)n * n;
-    LaunchScope ls(h, KK_FROB, st);
-    frob_stream_kernel<<<dim3(naux, (nd + 3) / 4), 256, 0, st>>>(L, n2, Mats, nd, out, naux, 0);
+    {
+        LaunchScope ls(h, KK_FROB, st);
+        if (pk)
+            frob_packed_kernel<<<dim3(naux, (nd + 3) / 4), 256, 0, st>>>(L, n, Mats, nd, out, naux, 0);
+        else
+            frob_stream_kernel<<<dim3(naux, (nd + 3) / 4), 256, 0, st>>>(L, n2, Mats, nd, out, naux, 0);
+    }
     JK_LAUNCH_CHECK(h);
     return JK_OK;
 }
 
-// out[s] = sum_P g[s*naux + P] L^P (dense [nd][n][n] output).
+// out[s] = sum_P g[s*naux + P] L^P (dense [nd][n][n] output); pk as above.
 jk_status fp64_jstream_dense(jk_ctx *h, const double *L, int n, int naux, const double *g, int nd, double *out,
-                             cudaStream_t st) {
+                             cudaStream_t st, bool pk) {
     double *ptrs[kMaxDens];
     for (int s = 0; s < nd; s++) ptrs[s] = out + (long long)s * n * n;
-    return jstream(h, L, n, naux, g, naux, nd, ptrs, st);
+    return jstream(h, L, n, naux, g, naux, nd, ptrs, st, pk);
 }
 
 jk_status fp64_jstream(jk_ctx *h, const Problem &pb, const double *gamma, cudaStream_t st) {
@@ -651,7 +689,7 @@ jk_status fp64_build(jk_ctx *h, const Problem &pb, cudaStream_t st) {
 // Aux indices per chunk: the panel chunk (pc x n x nd*n doubles) within
 // ~256 MB unless a chunk is set, and its rows within the GEMM grid's limit.
 static int fp64_dense_pchunk(const DenseProb &dp) {
-    const size_t per = (size_t)dp.n * dp.n * dp.nd * 8;
+    const size_t per = (size_t)dp.n * dp.n * dp.nd * 8 + (dp.packed ? (size_t)dp.n * dp.n * 8 : 0);
     size_t pc = per ? ((size_t)256 << 20) / per : 1;
     if (pc < 1) pc = 1;
     if (dp.aux_chunk > 0) pc = dp.aux_chunk;
@@ -667,6 +705,7 @@ size_t fp64_dense_workspace(const DenseProb &dp) {
     if (dp.DK) {
         b += align_up((size_t)fp64_dense_pchunk(dp) * n2 * nd * 8);   // panels T
         b += align_up((size_t)kMaxRankSplit * n2 * 8);               // rank-update partials
+        if (dp.packed) b += align_up((size_t)fp64_dense_pchunk(dp) * n2 * 8);   // expanded factor chunk
     }
     if (dp.DJ) {
         b += align_up(nd * (size_t)dp.naux * 8);                     // gamma
@@ -680,11 +719,13 @@ jk_status fp64_dense(jk_ctx *h, const DenseProb &dp, cudaStream_t st) {
     const long long n2 = (long long)n * n, ctot = (long long)nd * n;
     const int pc = fp64_dense_pchunk(dp);
     Arena &ar = h->arena;
-    double *T = nullptr, *part = nullptr, *gamma = nullptr, *Jt = nullptr;
+    double *T = nullptr, *part = nullptr, *gamma = nullptr, *Jt = nullptr, *Lx = nullptr;
     if (dp.DK) {
         T = ar.take<double>((size_t)pc * n2 * nd);
         part = ar.take<double>((size_t)kMaxRankSplit * n2);
-        if (!T || !part) return set_error(h, JK_ERR_OOM, "workspace too small for the dense FP64 build");
+        if (dp.packed) Lx = ar.take<double>((size_t)pc * n2);
+        if (!T || !part || (dp.packed && !Lx))
+            return set_error(h, JK_ERR_OOM, "workspace too small for the dense FP64 build");
     }
     if (dp.DJ) {
         gamma = ar.take<double>((size_t)nd * naux);
@@ -694,7 +735,9 @@ jk_status fp64_dense(jk_ctx *h, const DenseProb &dp, cudaStream_t st) {
     if (dp.DK) {
         for (int P0 = 0; P0 < naux; P0 += pc) {
             const int np = naux - P0 < pc ? naux - P0 : pc;
-            const double *Lc = dp.L + (long long)P0 * n2;
+            // a packed factor chunk is expanded first
+            if (dp.packed) JK_TRY(fp64_unpack_sym(h, dp.L + (long long)P0 * packed::tri_count(n), n, np, Lx, st));
+            const double *Lc = dp.packed ? Lx : dp.L + (long long)P0 * n2;
             // T[(p, mu)][s*n + nu] = sum_lam L^{P0+p}[mu][lam] DK_s[lam][nu]  (batch s)
             JK_TRY(dgemm(h, nd, np * n, n, n, gop(Lc, 0, n, 0, 1, n), gop(dp.DK, n2, 1, 0, n, n), T, ctot, n,
                          1.0, 0.0, st));
@@ -705,8 +748,8 @@ jk_status fp64_dense(jk_ctx *h, const DenseProb &dp, cudaStream_t st) {
         }
     }
     if (dp.DJ) {
-        JK_TRY(fp64_frob_all(h, dp.L, n, naux, dp.DJ, nd, gamma, st));
-        JK_TRY(fp64_jstream_dense(h, dp.L, n, naux, gamma, nd, dp.add_j ? Jt : dp.J, st));
+        JK_TRY(fp64_frob_all(h, dp.L, n, naux, dp.DJ, nd, gamma, st, dp.packed));
+        JK_TRY(fp64_jstream_dense(h, dp.L, n, naux, gamma, nd, dp.add_j ? Jt : dp.J, st, dp.packed));
         if (dp.add_j) JK_TRY(fp64_axpy(h, dp.K, Jt, nd * n2, st));
     }
     return JK_OK;

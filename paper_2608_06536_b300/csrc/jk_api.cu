@@ -93,8 +93,8 @@ static jk_status make_problem(jk_ctx *h, const jk_factor *f, int nd,
 
 static size_t flags_bytes() { return align_up(sizeof(DeviceFlags)); }
 
-// Entry points that read the factor only through ordinary builds take a
-// packed factor (JK_OPT_PACKED_FACTOR); the others refuse the option.
+// The builds (ordinary and dense) take a packed factor (JK_OPT_PACKED_FACTOR);
+// the adjoint and the host builds refuse the option.
 static jk_status refuse_packed(jk_ctx *h, const char *what) {
     if (h && h->packed_factor)
         return set_error(h, JK_ERR_UNSUPPORTED, "%s does not take a packed factor (JK_OPT_PACKED_FACTOR)", what);
@@ -585,6 +585,7 @@ static jk_status make_dense(jk_ctx *h, const jk_factor *f, int32_t nd, bool chec
     dp.naux = f->naux;
     dp.nd = nd;
     dp.L = f->L;
+    dp.packed = h && h->packed_factor;
     if (check_ptrs) {
         if (!f->L) return set_error(h, JK_ERR_ARG, "factor L is NULL");
         if (!aligned16(f->L)) return set_error(h, JK_ERR_ARG, "factor L is not 16-byte aligned");
@@ -646,12 +647,13 @@ static jk_status query_impl(const jk_ctx *h, jk_op op, int32_t nmol, const jk_fa
     if (p != JK_FP64 && p != JK_SPLIT_BF16) return JK_ERR_ARG;
     // a packed factor (handle option) is taken by the ordinary builds only
     const bool pk = h && h->packed_factor;
-    if (pk && op != JK_OP_BUILD && op != JK_OP_BATCHED && op != JK_OP_PAIR && op != JK_OP_LAPLACE)
+    if (pk && (op == JK_OP_ADJOINT || op == JK_OP_BUILD_HOST || op == JK_OP_BUILD_HOST_PACKED))
         return JK_ERR_UNSUPPORTED;
     if (op == JK_OP_BUILD_DENSE || op == JK_OP_DENSITY_GRAD) {
         DenseProb dp;
         jk_status s = make_dense(nullptr, f, nd, false, dp);
         if (s != JK_OK) return s;
+        dp.packed = pk;
         dp.aux_chunk = h && h->aux_chunk > 0 ? h->aux_chunk : 0;
         *bytes = dense_query_bytes(dp, op, p) + flags_bytes() + kArenaAlign;
         return JK_OK;
@@ -944,7 +946,6 @@ jk_status jk_build_dense(jk_handle h, const jk_factor *f, int32_t nd, const doub
     if (p != JK_FP64 && p != JK_SPLIT_BF16)
         return set_error(h, JK_ERR_ARG, "unknown precision %d", (int)p);
     DenseProb dp;
-    JK_TRY(refuse_packed(h, "jk_build_dense"));
     JK_TRY(make_dense(h, f, nd, true, dp));
     if (!D) return set_error(h, JK_ERR_ARG, "D is NULL");
     JK_TRY(check_in(h, D, "D"));
@@ -965,7 +966,6 @@ jk_status jk_density_grad(jk_handle h, const jk_factor *f, int32_t nd, const dou
     if (p != JK_FP64 && p != JK_SPLIT_BF16)
         return set_error(h, JK_ERR_ARG, "unknown precision %d", (int)p);
     DenseProb dp;
-    JK_TRY(refuse_packed(h, "jk_density_grad"));
     JK_TRY(make_dense(h, f, nd, true, dp));
     if (!G) return set_error(h, JK_ERR_ARG, "G is NULL");
     JK_TRY(check_out(h, G, "G"));

@@ -198,6 +198,7 @@ struct DenseProb {
     double *J = nullptr;          // [nd][n][n] (unused with add_j)
     bool add_j = false;
     int aux_chunk = 0;            // aux indices per chunk (0 = automatic)
+    bool packed = false;          // L holds packed upper triangles (chunks expanded before use)
 };
 size_t fp64_dense_workspace(const DenseProb &dp);
 jk_status fp64_dense(jk_ctx *h, const DenseProb &dp, cudaStream_t st);

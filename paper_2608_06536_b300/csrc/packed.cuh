@@ -40,5 +40,17 @@ JK_HD void tri_row_col(int n, long long t, int *a, int *b) {
     *b = mu + static_cast<int>(t - tri_index(n, mu, mu));
 }
 
+// (a, b) of position t + step, given (a, b) of position t (both positions
+// below tri_count(n)): whole rows are skipped without a square root.
+JK_HD void tri_advance(int n, int step, int *a, int *b) {
+    int r = *a, c = *b + step;
+    while (c >= n && r < n - 1) {
+        c -= n - r - 1;      // row r + 1 starts at column r + 1
+        r++;
+    }
+    *a = r;
+    *b = c;
+}
+
 }  // namespace packed
 }  // namespace jk

@@ -1436,9 +1436,9 @@ __global__ void fold_sym_split_kernel(double *dX, double *dY, long long cnt) {
 }  // namespace
 
 jk_status fp64_frob_all(jk_ctx *h, const double *L, int n, int naux, const double *Mats, int nd, double *out,
-                        cudaStream_t st);
+                        cudaStream_t st, bool pk);
 jk_status fp64_jstream_dense(jk_ctx *h, const double *L, int n, int naux, const double *g, int nd, double *out,
-                             cudaStream_t st);
+                             cudaStream_t st, bool pk);
 jk_status fp64_gemm_nt(jk_ctx *h, int M, int N, int K, const double *A, long long a_sr, long long a_sk,
                        const double *B, long long b_sr, long long b_sk, double *C, long long ldc, double beta,
                        cudaStream_t st);
@@ -1472,7 +1472,8 @@ static jk_status gemm_into(jk_ctx *h, const Sliced &A, const Sliced &B, double *
 // and one FP64 panel row block) within ~12 GB, panel rows within the grid.
 static int dense_pchunk(const DenseProb &dp) {
     const size_t n = dp.n;
-    const size_t per = n * n * (oz::S * 2) * 3 + n * even_ld(static_cast<long long>(dp.nd) * dp.n) * 8;
+    const size_t per = n * n * (oz::S * 2) * 3 + n * even_ld(static_cast<long long>(dp.nd) * dp.n) * 8 +
+                       (dp.packed ? n * n * 8 : 0);     // the expanded chunk of a packed factor
     size_t pc = per ? (static_cast<size_t>(12) << 30) / per : 1;
     if (pc < 1) pc = 1;
     if (dp.aux_chunk > 0) pc = dp.aux_chunk;
@@ -1506,6 +1507,7 @@ size_t split_dense_workspace(const DenseProb &dp) {
         b += align_up(n2 * 8);                                            // a chunk's K before it is added
         if (n > oz::SUPER)
             b += align_up(static_cast<size_t>(nsuper_of(n)) * part_rows(static_cast<long long>(pc) * n) * ldT * 8);
+        if (dp.packed) b += align_up(static_cast<size_t>(pc) * n2 * 8);  // expanded factor chunk
     }
     return b;
 }
@@ -1523,7 +1525,7 @@ jk_status split_dense(jk_ctx *h, const DenseProb &dp, cudaStream_t st) {
     const int pc = dp.DK ? dense_pchunk(dp) : 0, ctot = nd * n;
     const long long ldT = even_ld(ctot);
     Sliced Ls, Ds, LB, TS;
-    double *T = nullptr, *tmp = nullptr;
+    double *T = nullptr, *tmp = nullptr, *Lx = nullptr;
     long long *Pbuf = nullptr, *Ppanel = nullptr;
     if (dp.DK) {
         bool ok = take_sliced(ar, pc * n, n, n, Ls) && take_sliced(ar, ctot, n, 1, Ds);
@@ -1534,13 +1536,14 @@ jk_status split_dense(jk_ctx *h, const DenseProb &dp, cudaStream_t st) {
         if (n > oz::SUPER)
             Ppanel = ar.take<long long>(static_cast<size_t>(nsuper_of(n)) * part_rows(static_cast<long long>(pc) * n) *
                                         ldT);
-        if (!ok || !Pbuf || !tmp || (n > oz::SUPER && !Ppanel))
+        if (dp.packed) Lx = ar.take<double>(static_cast<size_t>(pc) * n2);
+        if (!ok || !Pbuf || !tmp || (n > oz::SUPER && !Ppanel) || (dp.packed && !Lx))
             return set_error(h, JK_ERR_OOM, "workspace too small for the dense split build");
     }
     if (dp.DJ) {
         JK_TRY(fork_jstream(h, st));
-        JK_TRY(fp64_frob_all(h, dp.L, n, naux, dp.DJ, nd, gamma, h->aux_stream));
-        JK_TRY(fp64_jstream_dense(h, dp.L, n, naux, gamma, nd, dp.add_j ? Jt : dp.J, h->aux_stream));
+        JK_TRY(fp64_frob_all(h, dp.L, n, naux, dp.DJ, nd, gamma, h->aux_stream, dp.packed));
+        JK_TRY(fp64_jstream_dense(h, dp.L, n, naux, gamma, nd, dp.add_j ? Jt : dp.J, h->aux_stream, dp.packed));
     }
     if (dp.DK) {
         // rows (s, nu) of DK^T, reduction over lam: element DK_s[lam][nu]
@@ -1548,7 +1551,10 @@ jk_status split_dense(jk_ctx *h, const DenseProb &dp, cudaStream_t st) {
         JK_TRY(slice_operand(h, dsrc, ctot, n, 1, Ds, st));
         for (int P0 = 0; P0 < naux; P0 += pc) {
             const int np = naux - P0 < pc ? naux - P0 : pc;
-            oz::Src lsrc{dp.L + P0 * n2, n, 0, 1, n};
+            // a packed factor chunk is expanded first
+            if (dp.packed) JK_TRY(fp64_unpack_sym(h, dp.L + P0 * packed::tri_count(n), n, np, Lx, st));
+            const double *Lchunk = dp.packed ? Lx : dp.L + P0 * n2;
+            oz::Src lsrc{Lchunk, n, 0, 1, n};
             JK_TRY(slice_operand(h, lsrc, np * n, n, n, Ls, st));
             // T[(p, mu)][s*n + nu] = sum_lam L^p[mu][lam] DK_s[lam][nu]
             if (n > oz::SUPER) {
@@ -1558,7 +1564,7 @@ jk_status split_dense(jk_ctx *h, const DenseProb &dp, cudaStream_t st) {
                 JK_TRY(ozgemm(h, Ls, Ds, T, ldT, nullptr, st));
             }
             // L with rows sig and reduction over (p, nu)
-            oz::Src lm{dp.L + P0 * n2, n, n2, 1, n};
+            oz::Src lm{Lchunk, n, n2, 1, n};
             JK_TRY(slice_operand(h, lm, n, np * n, 1, LB, st));
             for (int s = 0; s < nd; s++) {
                 // rows mu, reduction over (p, nu): T[(p, mu)][s*n + nu]
@@ -1907,8 +1913,8 @@ jk_status split_adjoint(jk_ctx *h, const Problem &pb, const double *W, const dou
     JK_TRY(slice_operand(h, zsrc, pb.ctot, n, 1, b.Zs, st));
     if (wantV) {
         // c_{P,s} = <V_s, L^P> and J(V_s) = sum_P c_{P,s} L^P in FP64
-        JK_TRY(fp64_frob_all(h, pb.L, n, naux, V, nd, b.cps, st));
-        JK_TRY(fp64_jstream_dense(h, pb.L, n, naux, b.cps, nd, b.JV, st));
+        JK_TRY(fp64_frob_all(h, pb.L, n, naux, V, nd, b.cps, st, false));
+        JK_TRY(fp64_jstream_dense(h, pb.L, n, naux, b.cps, nd, b.JV, st, false));
     }
     if (wantW) {
         for (int s = 0; s < nd; s++) {

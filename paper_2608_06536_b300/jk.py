@@ -204,11 +204,18 @@ def _check_shapes(Ls, X, Y=None, sym=None):
     return n, naux, nd
 
 
-def _check_dense(L, mats):
-    """Shapes of a dense call: L [naux][nbf][nbf] and each given matrix stack
-    [nd][nbf][nbf] (a single [nbf][nbf] matrix counts as nd = 1), all with the
-    same nd.  Returns (nbf, naux, nd)."""
+def _check_dense(L, mats, packed=False):
+    """Shapes of a dense call: L [naux][nbf][nbf] (packed: [naux][nbf(nbf+1)/2],
+    nbf taken from the matrices) and each given matrix stack [nd][nbf][nbf] (a
+    single [nbf][nbf] matrix counts as nd = 1), all with the same nd.  Returns
+    (nbf, naux, nd)."""
     Ls = _shape(L)
+    if packed:
+        first = next((_shape(m) for _, m in mats if m is not None), ())
+        n = first[-1] if len(first) >= 2 else 0
+        if len(Ls) != 2 or n < 1 or Ls[1] != n * (n + 1) // 2 or Ls[0] < 1:
+            raise ValueError(f"packed L must be [naux][{n * (n + 1) // 2}] for nbf = {n}, got {Ls}")
+        Ls = (Ls[0], n, n)
     if len(Ls) != 3 or Ls[1] != Ls[2] or min(Ls) < 1:
         raise ValueError(f"L must be [naux][nbf][nbf] with naux, nbf >= 1, got {Ls}")
     naux, n = Ls[0], Ls[1]
@@ -361,8 +368,9 @@ class Engine:
         "slicer" (0 integer digits, 1 FP32 digits), "syrk" (symmetric
         densities, both engines: 0 full rank update, 1 blocked symmetric rank
         update with the rest mirrored), "packed_factor" (1: the factor given
-        to build, build_batched, pairs, build_laplace and autotune* is
-        pack_factor(L), [naux][n(n+1)/2] on the device; half the memory).
+        to build, build_batched, build_dense, density_grad, pairs,
+        build_laplace and autotune* is pack_factor(L), [naux][n(n+1)/2] on
+        the device; half the memory).
         Kept across arena growth."""
         code = OPTIONS[name]
         self._opts[code] = int(value)
@@ -484,7 +492,7 @@ class Engine:
         """J(D_s), K(D_s) ([nd][n][n] float64) for dense, general densities
         D ([nd][n][n] or [n][n])."""
         p = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
-        n, naux, nd = _check_dense(L, [("D", D)])
+        n, naux, nd = _check_dense(L, [("D", D)], self._packed)
         if want_j:
             _check_output(J, "J", (nd, n, n), self.device)
         if want_k:
@@ -507,7 +515,7 @@ class Engine:
         """G_s = dE/dD_s = K(W_s) + J(V_s) ([nd][n][n] float64) for
         E = sum_s <W_s, K(D_s)> + <V_s, J(D_s)>; W or V may be None (zero)."""
         p = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
-        n, naux, nd = _check_dense(L, [("W", W), ("V", V)])
+        n, naux, nd = _check_dense(L, [("W", W), ("V", V)], self._packed)
         _check_output(G, "G", (nd, n, n), self.device)
         L = _dev_f64(L, self.device)
         W = None if W is None else _dev_f64(W, self.device).reshape(nd, n, n)

@@ -13,6 +13,7 @@
 
 using jk::packed::tri_count;
 using jk::packed::tri_index;
+using jk::packed::tri_advance;
 using jk::packed::tri_row_col;
 
 static long long checked = 0;
@@ -68,6 +69,27 @@ int main(int argc, char **argv) {
         if (tri_index(n, n - 1, n - 1) != tc - 1 || !inverse_ok(n, tc - 1)) return 1;
         for (int i = 0; i < 200000; i++)
             if (!inverse_ok(n, static_cast<long long>(rng() % static_cast<unsigned long long>(tc)))) return 1;
+    }
+    // stepping: from each position, tri_advance by `step` lands on the
+    // position's (row, column) that tri_row_col gives
+    for (int n : {1, 2, 3, 7, 31, 64, 255, 256, 257, 400, 1000}) {
+        const long long tc = tri_count(n);
+        for (int step : {1, 3, 64, 256, 1000}) {
+            for (long long t0 = 0; t0 < step && t0 < tc; t0++) {
+                int a, b;
+                tri_row_col(n, t0, &a, &b);
+                for (long long t = t0 + step; t < tc; t += step) {
+                    tri_advance(n, step, &a, &b);
+                    int ra, rb;
+                    tri_row_col(n, t, &ra, &rb);
+                    ++checked;
+                    if (a != ra || b != rb) {
+                        printf("advance n=%d step=%d t=%lld -> (%d, %d), want (%d, %d)\n", n, step, t, a, b, ra, rb);
+                        return 1;
+                    }
+                }
+            }
+        }
     }
     printf("ok %lld\n", checked);
     return 0;

@@ -202,6 +202,14 @@ def dec_frob(grid, args):
             (g, g + 8 * ((nd - 1) * ldg + P0 + grid[0]), "gamma")]
 
 
+def dec_frob_packed(grid, args):
+    L, n, M, nd, g, ldg, P0 = (_v(args, 0, VP), _v(args, 1, I32), _v(args, 2, VP), _v(args, 3, I32),
+                               _v(args, 4, VP), _v(args, 5, I32), _v(args, 6, I32))
+    assert grid[1] == (nd + 3) // 4
+    return [(L, L + 8 * (P0 + grid[0]) * (n * (n + 1) // 2), "L"), (M, M + 8 * nd * n * n, "Mats"),
+            (g, g + 8 * ((nd - 1) * ldg + P0 + grid[0]), "gamma")]
+
+
 def dec_gamma_panel(grid, args):
     T, n, ctot, tab, g, ldg, P0 = (_v(args, 0, VP), _v(args, 1, I32), _v(args, 2, I64), _a(args, 3, DensTab),
                                    _v(args, 4, VP), _v(args, 5, I32), _v(args, 6, I32))
@@ -421,6 +429,21 @@ def ex_frob(grid, args):
     gv = dv(g, (nd - 1) * ldg + P0 + grid[0])
     for s in range(nd):
         gv[s * ldg + P0:s * ldg + P0 + grid[0]] = Lm @ Mm[s]
+
+
+def ex_frob_packed(grid, args):
+    L, n, M, nd, g, ldg, P0 = (_v(args, 0, VP), _v(args, 1, I32), _v(args, 2, VP), _v(args, 3, I32),
+                               _v(args, 4, VP), _v(args, 5, I32), _v(args, 6, I32))
+    iu = np.triu_indices(n)
+    tri = len(iu[0])
+    P = dv(L, (P0 + grid[0]) * tri).reshape(-1, tri)[P0:P0 + grid[0]]
+    full = np.zeros((grid[0], n, n))
+    full[:, iu[0], iu[1]] = P
+    full[:, iu[1], iu[0]] = P
+    Mm = dv(M, nd * n * n).reshape(nd, n * n)
+    gv = dv(g, (nd - 1) * ldg + P0 + grid[0])
+    for s in range(nd):
+        gv[s * ldg + P0:s * ldg + P0 + grid[0]] = full.reshape(grid[0], -1) @ Mm[s]
 
 
 def ex_gamma_panel(grid, args):
@@ -735,7 +758,7 @@ EXECUTORS = [
     ("slice4_kernel", ex_slice), ("slice_kernel", ex_slice), ("ozgemm_kernel", ex_ozgemm),
     ("reduce_partials_kernel", ex_reduce), ("pack_ag_kernel", ex_pack_ag), ("pack_bg_kernel", ex_pack_bg),
     ("sym_dl_kernel", ex_sym_dl), ("mirror_blocks_kernel", ex_mirror_blocks), ("sum_parts_ld_kernel", ex_sum_parts_ld),
-    ("pack_sym_kernel", ex_pack_sym),
+    ("pack_sym_kernel", ex_pack_sym), ("frob_packed_kernel", ex_frob_packed),
 ]
 
 DECODERS = [
@@ -749,7 +772,7 @@ DECODERS = [
     ("symmetrize_kernel", dec_symmetrize), ("sym_dl_kernel", dec_sym_dl), ("fold_sym_split_kernel", dec_fold),
     ("fold_sym_kernel", dec_fold), ("pack_ag_kernel", dec_pack_ag), ("pack_bg_kernel", dec_pack_bg),
     ("mirror_blocks_kernel", dec_mirror_blocks), ("sum_parts_ld_kernel", dec_sum_parts_ld),
-    ("pack_sym_kernel", dec_pack_sym),
+    ("pack_sym_kernel", dec_pack_sym), ("frob_packed_kernel", dec_frob_packed),
 ]
 violations, decoded, undecoded = [], [0], set()
 
@@ -1094,7 +1117,7 @@ def dense_case(n, naux, nd, p, opts, grad=None):
         L = buf((naux, n, n), "L")
         if not BIG[0]:
             L[...] = L + L.transpose(0, 2, 1)
-        f = jk_factor(n, naux, L.ctypes.data)
+        f = factor_of(L, n, naux, "m")
         A, B = buf((nd, n, n), "A"), buf((nd, n, n), "B")
         O1, O2 = buf((nd, n, n), "O1", False), buf((nd, n, n), "O2", False)
         h = handle(1 << 20, opts, scaled=False)
@@ -1210,8 +1233,8 @@ def pack_factor_case(n, naux):
 
 
 def packed_refused_case():
-    """With JK_OPT_PACKED_FACTOR set, the entry points that read the factor
-    outside ordinary builds refuse the call before any device work."""
+    """With JK_OPT_PACKED_FACTOR set, the adjoint and the host builds refuse
+    the call before any device work."""
     def fn():
         n, naux, ks = 20, 30, [3, 4]
         f, d, L, X, Y = mol(n, naux, ks, [False, False])
@@ -1222,13 +1245,11 @@ def packed_refused_case():
         O = buf((nd, n, n), "O", False)
         got = {
             "adjoint": lib.jk_adjoint(h, ct.byref(f), nd, d, ptr(W), ptr(V), ptr(dX), ptr(dY), None, SPLIT, None),
-            "dense": lib.jk_build_dense(h, ct.byref(f), nd, ptr(W), ptr(O), None, SPLIT, None),
-            "grad": lib.jk_density_grad(h, ct.byref(f), nd, ptr(W), ptr(V), ptr(O), SPLIT, None),
             "host": lib.jk_build_host(h, ct.byref(f), nd, d, ptr(O), None, SPLIT, None),
             "host_packed": lib.jk_build_host_packed(h, ct.byref(f), nd, d, ptr(O), None, SPLIT, None),
         }
         nb = ct.c_size_t()
-        for op in (1, 3, 4, 5, 8):
+        for op in (1, 3, 8):
             got[f"query{op}"] = lib.jk_workspace_query_handle(h, op, 1, (jk_factor * 1)(f), None, nd, d, SPLIT,
                                                                ct.byref(nb))
         bad = {k: v for k, v in got.items() if v != 6}
@@ -1336,6 +1357,10 @@ CASES = {
                                            {"packed_factor": 1})),
     "laplace_split_packed": packed(laplace_case(37, 53, 5, 4, False, True, SPLIT, {"packed_factor": 1})),
     "pack_factor_then_build": pack_factor_case(70, 45),
+    "dense_split_packed": packed(dense_case(130, 70, 2, SPLIT, {"packed_factor": 1, "aux_chunk": 30})),
+    "dense_fp64_packed": packed(dense_case(37, 53, 3, FP64, {"packed_factor": 1, "aux_chunk": 17})),
+    "grad_split_WV_packed": packed(dense_case(37, 53, 3, SPLIT, {"packed_factor": 1}, grad="WV")),
+    "grad_fp64_V_packed": packed(dense_case(40, 33, 2, FP64, {"packed_factor": 1}, grad="V")),
     "autotune_split": autotune_case(37, 53, [5, 13], SPLIT),
 }
 
@@ -1388,7 +1413,7 @@ def fuzz_cases(count, seed):
             if g.random() < 0.5:
                 opts[name] = int(g.integers(0, 2))
         kind = g.choice(["build", "adjoint", "dense", "grad", "pairs", "laplace", "batched", "host"])
-        pk = kind in ("build", "pairs", "laplace", "batched") and g.random() < 0.3   # packed device factor
+        pk = kind in ("build", "pairs", "laplace", "batched", "dense", "grad") and g.random() < 0.3   # packed factor
         if pk:
             opts["packed_factor"] = 1
         label = f"fuzz{i}_{kind}_n{n}_a{naux}_p{p}" + ("_packed" if pk else "")

@@ -171,7 +171,7 @@ def test_dense_split_needs_no_identity_panel(records):
 
 # needs far less than the query, which covers both maps; no arena; skips what does not fit;
 # packs its factor (no arena) before the build that runs out
-FITS_IN_HALF = {"grad_fp64_V", "noalloc", "autotune_split", "autotune_batched_split", "pack_factor_then_build"}
+FITS_IN_HALF = {"grad_fp64_V", "grad_fp64_V_packed", "noalloc", "autotune_split", "autotune_batched_split", "pack_factor_then_build"}
 
 
 def test_too_small_arena_fails_before_any_device_work(shim_dir):
