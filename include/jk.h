@@ -310,9 +310,9 @@ typedef enum {
                                is symmetric), the rest mirrored; results
                                within rounding of those of 0                  */
     JK_OPT_PACKED_FACTOR = 8 /* 0 (default) dense factor; 1 every factor passed
-                               to jk_build, jk_build_batched, jk_build_dense,
-                               jk_density_grad, jk_pair, jk_build_laplace and
-                               jk_autotune* on this handle
+                               to jk_build, jk_build_batched, jk_adjoint,
+                               jk_build_dense, jk_density_grad, jk_pair,
+                               jk_build_laplace and jk_autotune* on this handle
                                holds packed upper triangles, L = [naux]
                                [nbf(nbf+1)/2] row-major, diagonal included
                                (position a*nbf - a(a-1)/2 + b - a for a <= b):
@@ -326,9 +326,10 @@ typedef enum {
                                against its budget: then they differ by
                                summation order only).  Size the arena with
                                jk_workspace_query_handle (the handle-free query
-                               assumes a dense factor).  jk_adjoint and the
-                               host builds return JK_ERR_UNSUPPORTED while it
-                               is 1                                            */
+                               assumes a dense factor).  The host builds (their
+                               factor is in host memory) return
+                               JK_ERR_UNSUPPORTED while it is 1; dL of the
+                               adjoint stays dense [naux][nbf][nbf]            */
 } jk_option;
 /* Options set explicitly on a handle override tuned configurations. */
 jk_status jk_set_option(jk_handle h, jk_option opt, int64_t value);

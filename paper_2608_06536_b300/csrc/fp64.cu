@@ -865,6 +865,7 @@ size_t fp64_adjoint_workspace(const Problem &pb, int pc, bool want_dl) {
     b += 2 * align_up((size_t)pc * n * pb.kmax * 8);  // U, Vp
     if (want_dl) b += align_up((size_t)pc * n * n * 8);  // G chunk
     b += align_up((size_t)kMaxAdjSplit * n * pb.kmax * 8);   // split dX / dY partials
+    if (pb.packed) b += align_up((size_t)pc * n * n * 8);     // expanded factor chunk
     return b;
 }
 
@@ -885,7 +886,8 @@ jk_status fp64_adjoint(jk_ctx *h, const Problem &pb, const double *W,
     double *Vp = ar.take<double>((size_t)pc * n * pb.kmax);
     double *G = dL ? ar.take<double>((size_t)pc * n2) : nullptr;
     double *part = ar.take<double>((size_t)kMaxAdjSplit * n * pb.kmax);
-    if (!Z || !T || !gamma || !cps || !D || !JV || !U || !Vp || (dL && !G) || !part)
+    double *Lx = pb.packed ? ar.take<double>((size_t)pc * n2) : nullptr;
+    if (!Z || !T || !gamma || !cps || !D || !JV || !U || !Vp || (dL && !G) || !part || (pb.packed && !Lx))
         return set_error(h, JK_ERR_OOM, "workspace too small for the FP64 adjoint");
 
     // Offsets of each density's block in dX / dY.
@@ -904,14 +906,20 @@ jk_status fp64_adjoint(jk_ctx *h, const Problem &pb, const double *W,
     }
     if (V) {
         // c_{P,s} = <V_s, L^P>, J(V_s) = sum_P c_{P,s} L^P
-        { LaunchScope ls_f(h, KK_FROB, st);
-        frob_stream_kernel<<<dim3(naux, (nd + 3) / 4), 256, 0, st>>>(pb.L, n2, V, nd, cps, naux, 0);
+        if (pb.packed) {
+            JK_TRY(fp64_frob_all(h, pb.L, n, naux, V, nd, cps, st, true));
+        } else {
+            { LaunchScope ls_f(h, KK_FROB, st);
+            frob_stream_kernel<<<dim3(naux, (nd + 3) / 4), 256, 0, st>>>(pb.L, n2, V, nd, cps, naux, 0);
+            }
+            JK_LAUNCH_CHECK(h);
         }
-        JK_LAUNCH_CHECK(h);
         double *jv[kMaxDens];
         for (int s = 0; s < nd; s++) jv[s] = JV + (long long)s * n2;
-        JK_TRY(jstream(h, pb.L, n, naux, cps, naux, nd, jv, st));
-        if (dL) {
+        JK_TRY(jstream(h, pb.L, n, naux, cps, naux, nd, jv, st, pb.packed));
+        if (dL && pb.packed) {
+            JK_TRY(fp64_frob_all(h, pb.L, n, naux, D, nd, gamma, st, true));
+        } else if (dL) {
             { LaunchScope ls_f(h, KK_FROB, st);
             frob_stream_kernel<<<dim3(naux, (nd + 3) / 4), 256, 0, st>>>(pb.L, n2, D, nd, gamma, naux, 0);
             }
@@ -922,9 +930,12 @@ jk_status fp64_adjoint(jk_ctx *h, const Problem &pb, const double *W,
     for (int P0 = 0; need_chunks && P0 < naux; P0 += pc) {
         const int np = naux - P0 < pc ? naux - P0 : pc;
         const long long sp = (long long)n * pb.ctot;
+        // a packed factor chunk is expanded first
+        if (pb.packed) JK_TRY(fp64_unpack_sym(h, pb.L + (long long)P0 * packed::tri_count(n), n, np, Lx, st));
+        const double *Lc = pb.packed ? Lx : pb.L + (long long)P0 * n2;
         if (W)
             JK_TRY(dgemm(h, 1, np * n, pb.ctot, n,
-                         gop(pb.L + (long long)P0 * n2, 0, n, 0, 1, n),
+                         gop(Lc, 0, n, 0, 1, n),
                          gop(Z, 0, 1, 0, pb.ctot, n), T, pb.ctot, 0, 1.0, 0.0, st));
         if (dL) JK_CUDA_TRY(h, cudaMemsetAsync(G, 0, (size_t)np * n2 * sizeof(double), st));
         for (int s = 0; W && s < nd; s++) {
@@ -940,9 +951,9 @@ jk_status fp64_adjoint(jk_ctx *h, const Problem &pb, const double *W,
                          gop(T + pb.offX[s], sp, 1, 0, pb.ctot, n), Vp, k, nk, 1.0, 0.0, st));
             // dX_s += sum_{p,lam} L^p[mu][lam] U^p[lam][i]; dY_s likewise with Vp
             // (an n x k output: split over groups of p)
-            JK_TRY(dgemm_split_q(h, n, k, np, n, pb.L + (long long)P0 * n2, n, n2, 1, U, 1, nk, k, dX + boff[s],
+            JK_TRY(dgemm_split_q(h, n, k, np, n, Lc, n, n2, 1, U, 1, nk, k, dX + boff[s],
                                  true, part, kMaxAdjSplit, st));
-            JK_TRY(dgemm_split_q(h, n, k, np, n, pb.L + (long long)P0 * n2, n, n2, 1, Vp, 1, nk, k, dY + boff[s],
+            JK_TRY(dgemm_split_q(h, n, k, np, n, Lc, n, n2, 1, Vp, 1, nk, k, dY + boff[s],
                                  true, part, kMaxAdjSplit, st));
             if (dL) {
                 // G^p += U^p X_s^T + Y_s Vp^p^T

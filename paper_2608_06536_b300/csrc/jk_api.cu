@@ -93,8 +93,8 @@ static jk_status make_problem(jk_ctx *h, const jk_factor *f, int nd,
 
 static size_t flags_bytes() { return align_up(sizeof(DeviceFlags)); }
 
-// The builds (ordinary and dense) take a packed factor (JK_OPT_PACKED_FACTOR);
-// the adjoint and the host builds refuse the option.
+// Every device-factor call takes a packed factor (JK_OPT_PACKED_FACTOR); the
+// host builds, whose factor lives in host memory, refuse the option.
 static jk_status refuse_packed(jk_ctx *h, const char *what) {
     if (h && h->packed_factor)
         return set_error(h, JK_ERR_UNSUPPORTED, "%s does not take a packed factor (JK_OPT_PACKED_FACTOR)", what);
@@ -647,7 +647,7 @@ static jk_status query_impl(const jk_ctx *h, jk_op op, int32_t nmol, const jk_fa
     if (p != JK_FP64 && p != JK_SPLIT_BF16) return JK_ERR_ARG;
     // a packed factor (handle option) is taken by the ordinary builds only
     const bool pk = h && h->packed_factor;
-    if (pk && (op == JK_OP_ADJOINT || op == JK_OP_BUILD_HOST || op == JK_OP_BUILD_HOST_PACKED))
+    if (pk && (op == JK_OP_BUILD_HOST || op == JK_OP_BUILD_HOST_PACKED))
         return JK_ERR_UNSUPPORTED;
     if (op == JK_OP_BUILD_DENSE || op == JK_OP_DENSITY_GRAD) {
         DenseProb dp;
@@ -920,7 +920,6 @@ jk_status jk_adjoint(jk_handle h, const jk_factor *f, int32_t nd, const jk_densi
     if (p != JK_FP64 && p != JK_SPLIT_BF16)
         return set_error(h, JK_ERR_ARG, "unknown precision %d", (int)p);
     Problem pb;
-    JK_TRY(refuse_packed(h, "jk_adjoint"));
     JK_TRY(make_problem(h, f, nd, d, true, pb));
     if (h->aux_chunk >= 0) pb.aux_chunk = h->aux_chunk;
     h->cur_raster = h->raster >= 0 ? h->raster : 0;

@@ -1590,7 +1590,8 @@ static int split_adj_pchunk(const Problem &pb) {
                  + 2 * pb.kmax * n * 12          // T_X, T_Y as B operands
                  + 2 * n * pb.kmax * 8 + pb.kmax * n * 12 * 2   // U, Vp and their slices
                  + n * ks3 * (8 + 12)            // AG and its slices
-                 + n * n * 8 * 2;                // G, GV
+                 + n * n * 8 * 2                 // G, GV
+                 + (pb.packed ? n * n * 8 : 0);  // the expanded chunk of a packed factor
     size_t budget = static_cast<size_t>(8) << 30;
     size_t pc = per ? budget / per : 1;
     if (pc < 1) pc = 1;
@@ -1603,6 +1604,7 @@ static int split_adj_pchunk(const Problem &pb) {
 
 struct AdjBufs {
     double *Z, *T, *gam, *cps, *JV, *U, *Vp, *AG, *BG, *G, *GV, *tmp;
+    double *Lx = nullptr;     // packed factor: the chunk expanded to [np][n][n]
     long long *P;
     Sliced Zs, Ls, Lm, Ws[kMaxDens], WTs[kMaxDens], TXb, TYb, Ub, Vpb, AGs, BGs, Gam, Vs;
 };
@@ -1640,6 +1642,7 @@ static bool adj_take(Arena &ar, const Problem &pb, int pc, bool W, bool V, bool 
     tk(b.GV, dl && V ? static_cast<size_t>(pc) * n2 : 1);
     tk(b.tmp, static_cast<size_t>(n) * std::max(kmax, 1));
     tk(b.P, adj_partials(pb, pc));
+    if (pb.packed) tk(b.Lx, static_cast<size_t>(pc) * n2);
     ok = ok && take_sliced(ar, pb.ctot, n, 1, b.Zs) && take_sliced(ar, pc * n, n, n, b.Ls) &&
          take_sliced(ar, n, pc * n, 1, b.Lm);
     for (int s = 0; ok && W && s < nd; s++)
@@ -1913,8 +1916,8 @@ jk_status split_adjoint(jk_ctx *h, const Problem &pb, const double *W, const dou
     JK_TRY(slice_operand(h, zsrc, pb.ctot, n, 1, b.Zs, st));
     if (wantV) {
         // c_{P,s} = <V_s, L^P> and J(V_s) = sum_P c_{P,s} L^P in FP64
-        JK_TRY(fp64_frob_all(h, pb.L, n, naux, V, nd, b.cps, st, false));
-        JK_TRY(fp64_jstream_dense(h, pb.L, n, naux, b.cps, nd, b.JV, st, false));
+        JK_TRY(fp64_frob_all(h, pb.L, n, naux, V, nd, b.cps, st, pb.packed));
+        JK_TRY(fp64_jstream_dense(h, pb.L, n, naux, b.cps, nd, b.JV, st, pb.packed));
     }
     if (wantW) {
         for (int s = 0; s < nd; s++) {
@@ -1948,8 +1951,11 @@ jk_status split_adjoint(jk_ctx *h, const Problem &pb, const double *W, const dou
 
     for (int P0 = 0; P0 < naux; P0 += pc) {
         const int np = naux - P0 < pc ? naux - P0 : pc;
+        // a packed factor chunk is expanded first
+        if (pb.packed) JK_TRY(fp64_unpack_sym(h, pb.L + P0 * packed::tri_count(n), n, np, b.Lx, st));
+        const double *Lchunk = pb.packed ? b.Lx : pb.L + P0 * n2;
         // Panels T^p = L^p Z (the half-transforms), as in the build
-        oz::Src lsrc{pb.L + P0 * n2, n, 0, 1, n};
+        oz::Src lsrc{Lchunk, n, 0, 1, n};
         JK_TRY(slice_operand(h, lsrc, np * n, n, n, b.Ls, st));
         if (n > oz::SUPER) {
             JK_TRY(ozgemm(h, b.Ls, b.Zs, nullptr, 0, b.P, st));
@@ -1960,7 +1966,7 @@ jk_status split_adjoint(jk_ctx *h, const Problem &pb, const double *W, const dou
         if (wantV && wantL) JK_TRY(fp64_gamma_panel(h, pb, b.T, ldT, np, b.gam, P0, st));
         if (wantW) {
             // L with rows mu and reduction over (p, lam), for dX and dY
-            oz::Src lm{pb.L + P0 * n2, n, n2, 1, n};
+            oz::Src lm{Lchunk, n, n2, 1, n};
             JK_TRY(slice_operand(h, lm, n, np * n, 1, b.Lm, st));
         }
         for (int s = 0; s < nd; s++) {

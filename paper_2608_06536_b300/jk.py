@@ -368,9 +368,9 @@ class Engine:
         "slicer" (0 integer digits, 1 FP32 digits), "syrk" (symmetric
         densities, both engines: 0 full rank update, 1 blocked symmetric rank
         update with the rest mirrored), "packed_factor" (1: the factor given
-        to build, build_batched, build_dense, density_grad, pairs,
-        build_laplace and autotune* is pack_factor(L), [naux][n(n+1)/2] on
-        the device; half the memory).
+        to every device call (build, build_batched, adjoint, build_dense,
+        density_grad, pairs, build_laplace, autotune*) is pack_factor(L),
+        [naux][n(n+1)/2] on the device; half the memory).
         Kept across arena growth."""
         code = OPTIONS[name]
         self._opts[code] = int(value)
@@ -735,7 +735,7 @@ class Engine:
                 precision="fp64", stream=None):
         """(dX list, dY list, dL or None) for E = sum_s <W_s,K_s> + <V_s,J_s>."""
         p = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
-        n, naux, nd = _check_problem(L, X, Y, sym)
+        n, naux, nd = _check_problem(L, X, Y, sym, self._packed)
         for name, t in (("W", W), ("V", V)):
             if t is not None and torch.as_tensor(t).numel() != nd * n * n:
                 raise ValueError(f"{name} must hold [{nd}][{n}][{n}] values")

@@ -1233,23 +1233,20 @@ def pack_factor_case(n, naux):
 
 
 def packed_refused_case():
-    """With JK_OPT_PACKED_FACTOR set, the adjoint and the host builds refuse
-    the call before any device work."""
+    """With JK_OPT_PACKED_FACTOR set, the host builds (their factor is in host
+    memory) refuse the call before any device work."""
     def fn():
         n, naux, ks = 20, 30, [3, 4]
         f, d, L, X, Y = mol(n, naux, ks, [False, False])
-        nd, tot = len(ks), n * sum(ks)
+        nd = len(ks)
         h = handle(1 << 24, {"packed_factor": 1}, scaled=False)
-        W, V = buf((nd, n, n), "W"), buf((nd, n, n), "V")
-        dX, dY = buf((tot,), "dX", False), buf((tot,), "dY", False)
         O = buf((nd, n, n), "O", False)
         got = {
-            "adjoint": lib.jk_adjoint(h, ct.byref(f), nd, d, ptr(W), ptr(V), ptr(dX), ptr(dY), None, SPLIT, None),
             "host": lib.jk_build_host(h, ct.byref(f), nd, d, ptr(O), None, SPLIT, None),
             "host_packed": lib.jk_build_host_packed(h, ct.byref(f), nd, d, ptr(O), None, SPLIT, None),
         }
         nb = ct.c_size_t()
-        for op in (1, 3, 8):
+        for op in (3, 8):
             got[f"query{op}"] = lib.jk_workspace_query_handle(h, op, 1, (jk_factor * 1)(f), None, nd, d, SPLIT,
                                                                ct.byref(nb))
         bad = {k: v for k, v in got.items() if v != 6}
@@ -1361,6 +1358,10 @@ CASES = {
     "dense_fp64_packed": packed(dense_case(37, 53, 3, FP64, {"packed_factor": 1, "aux_chunk": 17})),
     "grad_split_WV_packed": packed(dense_case(37, 53, 3, SPLIT, {"packed_factor": 1}, grad="WV")),
     "grad_fp64_V_packed": packed(dense_case(40, 33, 2, FP64, {"packed_factor": 1}, grad="V")),
+    "adjoint_split_packed": packed(adjoint_case(70, 150, [8, 16, 3], [False, False, True], SPLIT,
+                                                {"packed_factor": 1, "aux_chunk": 40})),
+    "adjoint_fp64_packed": packed(adjoint_case(33, 41, [4, 5], [True, False], FP64,
+                                               {"packed_factor": 1, "aux_chunk": 10})),
     "autotune_split": autotune_case(37, 53, [5, 13], SPLIT),
 }
 
@@ -1413,7 +1414,7 @@ def fuzz_cases(count, seed):
             if g.random() < 0.5:
                 opts[name] = int(g.integers(0, 2))
         kind = g.choice(["build", "adjoint", "dense", "grad", "pairs", "laplace", "batched", "host"])
-        pk = kind in ("build", "pairs", "laplace", "batched", "dense", "grad") and g.random() < 0.3   # packed factor
+        pk = kind != "host" and g.random() < 0.3   # packed device factor
         if pk:
             opts["packed_factor"] = 1
         label = f"fuzz{i}_{kind}_n{n}_a{naux}_p{p}" + ("_packed" if pk else "")

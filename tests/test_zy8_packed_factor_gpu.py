@@ -143,3 +143,34 @@ def test_packed_factor_dense_and_gradient(precision):
     Jo, Ko = oracle.build_dense(m.L, inputs.dense_densities(n, 2, seed=3))
     Go = oracle.density_grad(m.L, inputs.dense_densities(n, 2, seed=4), inputs.dense_densities(n, 2, seed=3), nd=2)
     assert abs_err(Jp, Jo) < SPLIT_ABS and abs_err(Kp, Ko) < SPLIT_ABS and abs_err(Gp, Go) < SPLIT_ABS
+
+
+@pytest.mark.parametrize("precision", ["split", "fp64"])
+def test_packed_factor_adjoint(precision):
+    """jk_adjoint on a packed factor: the chunks are expanded for the products
+    and the J terms' metric dots are summed over the triangles, so dX, dY and
+    dL agree with the dense factor's to rounding and match the oracle."""
+    m = inputs.custom(70, 45, 12.0, [5, 3], [False, True])
+    rng = np.random.default_rng(9)
+    W = [rng.standard_normal((70, 70)) for _ in range(2)]
+    V = [rng.standard_normal((70, 70)) for _ in range(2)]
+    dXo, dYo, dLo = oracle.adjoint(m.L, m.X, m.Y, W, V)
+    Wd, Vd = torch.tensor(np.array(W)).cuda(), torch.tensor(np.array(V)).cuda()
+    X = [torch.from_numpy(x).cuda() for x in m.X]
+    Y = [torch.from_numpy(y).cuda() for y in m.Y]
+    res = []
+    for packed in (0, 1):
+        eng = jk.Engine("cuda:0")
+        eng.set_option("aux_chunk", 20)
+        eng.set_option("packed_factor", packed)
+        fac = jk.pack_factor(m.L).cuda() if packed else torch.from_numpy(m.L).cuda()
+        dX, dY, dL = eng.adjoint(fac, X, Y, m.sym, Wd, Vd, precision=precision)
+        eng.sync_status()
+        res.append(([to_np(t) for t in dX], [to_np(t) for t in dY], to_np(dL)))
+        eng.close()
+    (dXd, dYd, dLd), (dXp, dYp, dLp) = res
+    tol = 1e-9 if precision == "split" else 1e-11          # dX reaches ~1e3 here
+    for s in range(2):
+        assert abs_err(dXp[s], dXd[s]) < tol and abs_err(dXp[s], dXo[s]) < tol
+    assert abs_err(dYp[0], dYd[0]) < tol and abs_err(dYp[0], dYo[0]) < tol
+    assert abs_err(dLp, dLd) < SPLIT_ABS and abs_err(dLp, dLo) < SPLIT_ABS
