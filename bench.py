@@ -248,7 +248,7 @@ def run_ours(args, rank, world, local):
     tuned = None
     if args.config:
         # a fixed configuration (for profiling runs): no tuning
-        for name, v in zip(("aux_chunk", "schedule", "raster", "cluster"), args.config.split(",")):
+        for name, v in zip(("aux_chunk", "schedule", "raster"), args.config.split(",")):
             eng.set_option(name, int(v))
         tuned = {"fixed": args.config}
     elif args.tune:
@@ -553,7 +553,7 @@ def main():
     ap.add_argument("--no-tune", dest="tune", action="store_false",
                     help="skip the autotuner (default configuration)")
     ap.add_argument("--config", default="",
-                    help="fixed run-time configuration aux_chunk,schedule,raster,cluster (skips the autotuner)")
+                    help="fixed run-time configuration aux_chunk,schedule,raster (skips the autotuner)")
     ap.add_argument("--slicer", type=int, choices=[0, 1], default=0,
                     help="digit extraction of the vector slicer: 0 integer (default), 1 FP32 additions")
     ap.add_argument("--syrk", type=int, choices=[0, 1], default=0,

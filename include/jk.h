@@ -294,8 +294,7 @@ typedef enum {
                                1 = m-tile fastest (tile order of the sliced GEMM) */
     JK_OPT_USE_TUNED = 3,   /* 1 (default) = apply autotuned configurations,
                                0 = ignore them                                    */
-    JK_OPT_CLUSTER = 4,     /* -1 = tuned/default, 0 = one CTA per tile, 1 = 2-CTA
-                               clusters sharing an operand tile by TMA multicast  */
+    /* 4 is unused */
     JK_OPT_HOST_CHUNK = 5,  /* jk_build_host: aux indices per streamed chunk of
                                the factor, 0 = automatic (about 12 chunks)         */
     JK_OPT_SLICER = 6,      /* digit extraction of the split engine's vector
@@ -347,7 +346,7 @@ jk_status jk_pack_factor(jk_handle h, int32_t nbf, int32_t naux, const double *L
 
 /* ---------------------------------------------------------------------------
  * Autotuner.  A configuration is the set of run-time choices a build makes
- * (aux-index chunk, launch schedule, GEMM tile order, CTA clustering).  jk_autotune times the
+ * (aux-index chunk, launch schedule, GEMM tile order).  jk_autotune times the
  * candidate configurations of one problem with CUDA events on `stream` (it
  * synchronizes the stream, so it must not be called during stream capture),
  * keeps the fastest in a process-wide cache keyed by a shape bucket (op,
@@ -363,7 +362,6 @@ typedef struct {
     int32_t aux_chunk;   /* aux indices per chunk, 0 = automatic */
     int32_t schedule;    /* 0 per-density launches, 1 grouped persistent launches */
     int32_t raster;      /* 0 n-tile fastest, 1 m-tile fastest */
-    int32_t cluster;     /* 0 one CTA per tile, 1 2-CTA clusters with operand multicast */
 } jk_tune_config;
 
 jk_status jk_autotune(jk_handle h, const jk_factor *f, int32_t nd, const jk_density *d,

@@ -101,14 +101,11 @@ static jk_status refuse_packed(jk_ctx *h, const char *what) {
     return JK_OK;
 }
 
-// Without a tuned entry: one CTA per tile (clusters are a tuning candidate).
-constexpr int kDefaultCluster = 0;
-
 // Effective run-time configuration of a call: the tuned entry of its shape
 // bucket (when allowed), overridden by options set explicitly on the handle.
 static jk_tune_config resolve_config(const jk_ctx *h, jk_op op, jk_precision p, int sms, int nmol,
                                      const Problem *pbs) {
-    jk_tune_config c{0, 0, 0, kDefaultCluster};
+    jk_tune_config c{0, 0, 0};
     if (!h || h->use_tuned) {
         jk_tune_config t;
         if (tune_lookup(tune_key(op, p, sms, nmol, pbs), t)) c = t;
@@ -117,7 +114,6 @@ static jk_tune_config resolve_config(const jk_ctx *h, jk_op op, jk_precision p, 
         if (h->aux_chunk >= 0) c.aux_chunk = h->aux_chunk;
         if (h->schedule >= 0) c.schedule = h->schedule;
         if (h->raster >= 0) c.raster = h->raster;
-        if (h->cluster >= 0) c.cluster = h->cluster;
     }
     return c;
 }
@@ -250,13 +246,12 @@ static Problem host_chunk_problem(const Problem &pb, const HostBufs &b, int np, 
 // Configuration of the chunk builds: tuned for the chunk shape, else the
 // grouped schedule (one launch per phase for all densities of the chunk).
 static jk_tune_config host_config(const jk_ctx *h, jk_precision p, const Problem &q) {
-    jk_tune_config c{0, 1, 0, kDefaultCluster};
+    jk_tune_config c{0, 1, 0};
     jk_tune_config t;
     if (h->use_tuned && tune_lookup(tune_key(JK_OP_BUILD, p, h->num_sms, 1, &q), t)) c = t;
     if (h->aux_chunk >= 0) c.aux_chunk = h->aux_chunk;
     if (h->schedule >= 0) c.schedule = h->schedule;
     if (h->raster >= 0) c.raster = h->raster;
-    if (h->cluster >= 0) c.cluster = h->cluster;
     return c;
 }
 
@@ -264,7 +259,7 @@ static size_t host_build_bytes(const jk_ctx *h, const Problem &pb, jk_precision 
     const int chunk = host_chunk_of(h, pb);
     Problem q = pb;
     q.naux = chunk;
-    jk_tune_config c{0, 1, 0, kDefaultCluster};
+    jk_tune_config c{0, 1, 0};
     if (h) c = host_config(h, p, q);
     apply_config(q, c);
     return host_persist_bytes(pb, chunk, true, true, packed) + build_bytes(q, p);
@@ -320,7 +315,6 @@ static jk_status host_build(jk_ctx *h, const Problem &pb, const jk_density *d, d
                          ar.off + build_bytes(q, p));
     JK_TRY(ensure_copy_stream(h));
     h->cur_raster = cfg.raster;
-    h->cur_cluster = cfg.cluster;
 
     // densities up, accumulators cleared (on the caller's stream)
     size_t off = 0;
@@ -611,7 +605,6 @@ static size_t dense_query_bytes(DenseProb dp, jk_op op, jk_precision p) {
 static void dense_config(jk_ctx *h, DenseProb &dp) {
     dp.aux_chunk = h->aux_chunk > 0 ? h->aux_chunk : 0;
     h->cur_raster = h->raster >= 0 ? h->raster : 0;
-    h->cur_cluster = h->cluster >= 0 ? h->cluster : kDefaultCluster;
 }
 
 static jk_status run_dense(jk_ctx *h, const DenseProb &dp, jk_precision p, cudaStream_t st) {
@@ -670,7 +663,7 @@ static jk_status query_impl(const jk_ctx *h, jk_op op, int32_t nmol, const jk_fa
         pb.packed = pk;
         Problem q = pb;
         apply_config(pb, resolve_config(h, JK_OP_BUILD, p, sms, 1, &pb));
-        apply_config(q, jk_tune_config{0, 0, 0, kDefaultCluster});
+        apply_config(q, jk_tune_config{0, 0, 0});
         const size_t b = h ? build_bytes(pb, p) : std::max(build_bytes(pb, p), build_bytes(q, p));
         *bytes = b + laplace_persist_bytes(pb.n, nd, d[0].k, d[0].symmetric != 0, true, true, true) +
                  flags_bytes() + kArenaAlign;
@@ -684,7 +677,7 @@ static jk_status query_impl(const jk_ctx *h, jk_op op, int32_t nmol, const jk_fa
         for (auto &q : pp) q.packed = pk;
         size_t need = 0;
         const jk_tune_config cfgs[2] = {resolve_config(h, JK_OP_BUILD, p, sms, 1, &pp[1]),
-                                        jk_tune_config{0, 0, 0, kDefaultCluster}};
+                                        jk_tune_config{0, 0, 0}};
         for (int v = 0; v < (h ? 1 : 2); v++) {
             Problem q = pp[1];
             apply_config(q, cfgs[v]);
@@ -712,7 +705,7 @@ static jk_status query_impl(const jk_ctx *h, jk_op op, int32_t nmol, const jk_fa
         return JK_ERR_ARG;
     }
     const jk_tune_config cfgs[2] = {resolve_config(h, op, p, sms, nmol, pbs.data()),
-                                    jk_tune_config{0, 0, 0, kDefaultCluster}};
+                                    jk_tune_config{0, 0, 0}};
     for (int v = 0; v < (h ? 1 : 2); v++) {
         for (auto &pb : pbs) apply_config(pb, cfgs[v]);
         size_t b = op == JK_OP_BATCHED ? batched_bytes(nmol, pbs.data(), p)
@@ -753,7 +746,6 @@ jk_status jk_build(jk_handle h, const jk_factor *f, int32_t nd, const jk_density
     const jk_tune_config c = resolve_config(h, JK_OP_BUILD, p, h->num_sms, 1, &pb);
     apply_config(pb, c);
     h->cur_raster = c.raster;
-    h->cur_cluster = c.cluster;
     if (h->arena.bytes < flags_bytes() + build_bytes(pb, p))
         return set_error(h, JK_ERR_OOM, "arena has %zu bytes, this build needs %zu",
                          h->arena.bytes, flags_bytes() + build_bytes(pb, p));
@@ -802,7 +794,6 @@ jk_status jk_build_batched(jk_handle h, int32_t nmol, const jk_factor *f,
     const jk_tune_config c = resolve_config(h, JK_OP_BATCHED, p, h->num_sms, nmol, pbs.data());
     for (auto &pb : pbs) apply_config(pb, c);
     h->cur_raster = c.raster;
-    h->cur_cluster = c.cluster;
     if (h->arena.bytes < flags_bytes() + batched_bytes(nmol, pbs.data(), p))
         return set_error(h, JK_ERR_OOM, "arena has %zu bytes, this batched build needs %zu", h->arena.bytes,
                          flags_bytes() + batched_bytes(nmol, pbs.data(), p));
@@ -827,8 +818,7 @@ jk_status jk_autotune(jk_handle h, const jk_factor *f, int32_t nd, const jk_dens
     for (int ch : chunk_candidates(pc0, pb.naux))
         for (int sc = 0; sc < (p == JK_FP64 ? 1 : 2); sc++)
             for (int ra = 0; ra < (p == JK_FP64 ? 1 : 2); ra++)
-                for (int cl = 0; cl < (p == JK_FP64 ? 1 : 2); cl++)
-                    cands.push_back(jk_tune_config{ch, sc, ra, p == JK_FP64 ? kDefaultCluster : cl});
+                cands.push_back(jk_tune_config{ch, sc, ra});
     auto fits = [&](const jk_tune_config &c) {
         Problem q = pb;
         apply_config(q, c);
@@ -838,10 +828,9 @@ jk_status jk_autotune(jk_handle h, const jk_factor *f, int32_t nd, const jk_dens
         Problem q = pb;
         apply_config(q, c);
         h->cur_raster = c.raster;
-        h->cur_cluster = c.cluster;
         return run_build(h, q, p, st);
     };
-    jk_tune_config bc{0, 0, 0, kDefaultCluster};
+    jk_tune_config bc{0, 0, 0};
     double bms = 0.0;
     JK_TRY(time_candidates(h, cands, reps, st, fits, run, bc, bms));
     tune_store(tune_key(JK_OP_BUILD, p, h->num_sms, 1, &pb), bc, bms);
@@ -873,8 +862,7 @@ jk_status jk_autotune_batched(jk_handle h, int32_t nmol, const jk_factor *f,
     std::vector<jk_tune_config> cands;
     for (int ch : chunk_candidates(pc0, naux_max))
         for (int ra = 0; ra < (p == JK_FP64 ? 1 : 2); ra++)
-            for (int cl = 0; cl < (p == JK_FP64 ? 1 : 2); cl++)
-                cands.push_back(jk_tune_config{ch, 1, ra, p == JK_FP64 ? kDefaultCluster : cl});
+            cands.push_back(jk_tune_config{ch, 1, ra});
     auto fits = [&](const jk_tune_config &c) {
         std::vector<Problem> q = pbs;
         for (auto &pb : q) apply_config(pb, c);
@@ -884,10 +872,9 @@ jk_status jk_autotune_batched(jk_handle h, int32_t nmol, const jk_factor *f,
         std::vector<Problem> q = pbs;
         for (auto &pb : q) apply_config(pb, c);
         h->cur_raster = c.raster;
-        h->cur_cluster = c.cluster;
         return batched_build(h, nmol, q.data(), p, st);
     };
-    jk_tune_config bc{0, 1, 0, kDefaultCluster};
+    jk_tune_config bc{0, 1, 0};
     double bms = 0.0;
     JK_TRY(time_candidates(h, cands, reps, st, fits, run, bc, bms));
     tune_store(tune_key(JK_OP_BATCHED, p, h->num_sms, nmol, pbs.data()), bc, bms);
@@ -923,7 +910,6 @@ jk_status jk_adjoint(jk_handle h, const jk_factor *f, int32_t nd, const jk_densi
     JK_TRY(make_problem(h, f, nd, d, true, pb));
     if (h->aux_chunk >= 0) pb.aux_chunk = h->aux_chunk;
     h->cur_raster = h->raster >= 0 ? h->raster : 0;
-    h->cur_cluster = h->cluster >= 0 ? h->cluster : kDefaultCluster;
     if (!dX || !dY) return set_error(h, JK_ERR_ARG, "dX and dY are required");
     JK_TRY(check_out(h, dX, "dX"));
     JK_TRY(check_out(h, dY, "dY"));
@@ -1003,7 +989,6 @@ jk_status jk_pair(jk_handle h, const jk_factor *f, int32_t nl, const jk_density 
     const jk_tune_config c = resolve_config(h, JK_OP_BUILD, p, h->num_sms, 1, &pr);
     apply_config(pr, c);
     h->cur_raster = c.raster;
-    h->cur_cluster = c.cluster;
     const size_t need = flags_bytes() + pair_bytes(pl, pr, p, Jp != nullptr, Kp != nullptr);
     if (h->arena.bytes < need)
         return set_error(h, JK_ERR_OOM, "arena has %zu bytes, this pairing needs %zu", h->arena.bytes, need);
@@ -1072,7 +1057,6 @@ jk_status jk_build_laplace(jk_handle h, const jk_factor *f, int32_t nq, const do
     const jk_tune_config c = resolve_config(h, JK_OP_BUILD, p, h->num_sms, 1, &pb);
     apply_config(pb, c);
     h->cur_raster = c.raster;
-    h->cur_cluster = c.cluster;
     const int n = pb.n;
     const bool weighted = w != nullptr;
     const size_t need = flags_bytes() + laplace_persist_bytes(n, nq, m, sym, weighted, J != nullptr, K != nullptr) +
@@ -1131,10 +1115,9 @@ jk_status jk_set_option(jk_handle h, jk_option opt, int64_t value) {
         h->aux_chunk = static_cast<int>(value);
         return JK_OK;
     }
-    if (opt == JK_OPT_SCHEDULE || opt == JK_OPT_RASTER || opt == JK_OPT_CLUSTER) {
+    if (opt == JK_OPT_SCHEDULE || opt == JK_OPT_RASTER) {
         if (value < -1 || value > 1) return set_error(h, JK_ERR_ARG, "option %d takes -1, 0 or 1", (int)opt);
-        (opt == JK_OPT_SCHEDULE ? h->schedule : opt == JK_OPT_RASTER ? h->raster : h->cluster) =
-            static_cast<int>(value);
+        (opt == JK_OPT_SCHEDULE ? h->schedule : h->raster) = static_cast<int>(value);
         return JK_OK;
     }
     if (opt == JK_OPT_HOST_CHUNK) {

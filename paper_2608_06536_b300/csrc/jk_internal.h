@@ -70,16 +70,13 @@ struct jk_ctx {
     int aux_chunk = -1;      // explicit options (JK_OPT_*); -1 = not set
     int schedule = -1;
     int raster = -1;
-    int cluster = -1;
     int use_tuned = 1;
     int cur_raster = 0;      // tile order in effect for the running call
-    int cur_cluster = 0;     // 2-CTA clustered sliced GEMM in effect for the running call
-    int max_clusters = 0;    // resident 2-CTA clusters of the sliced GEMM (0 = not yet queried)
     bool gemm_smem_set = false;   // the sliced GEMM's shared-memory attribute is set on this device
     int host_chunk = 0;      // aux indices per streamed chunk of a host-resident factor (0 = automatic)
-    int slicer = 0;
+    int slicer = 0;          // digit extraction of the vector slicer: 0 integer, 1 FP32 additions
     int syrk = 0;            // split engine: symmetric rank updates by row blocks, rest mirrored
-    int packed_factor = 0;   // factors passed to builds hold packed upper triangles          // digit extraction of the vector slicer: 0 integer, 1 FP32 additions
+    int packed_factor = 0;   // factors passed to builds hold packed upper triangles
     cudaStream_t copy_stream = nullptr;   // host builds: uploads of the factor, created on first use
     cudaEvent_t ev_fork = nullptr, ev_up[2] = {nullptr, nullptr}, ev_used[2] = {nullptr, nullptr};
     cudaStream_t aux_stream = nullptr;    // FP64 J streams overlapped with the rank updates

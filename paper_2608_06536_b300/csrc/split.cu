@@ -404,18 +404,15 @@ __host__ __device__ constexpr int drain_acc(int j) { return j == 0 ? 4 : j == 1 
 // descriptor tables (and stays capturable in a CUDA graph).
 struct OzProb {
     CUtensorMap tmA, tmB, tmC;
-    CUtensorMap tmS;    // clustered launches: three slice planes of the shared operand
     OzArgs a;
     int tile0;          // first launch-wide work unit of this problem
     int ntn, ntm;       // output tiles along N and M
-    int un, um;         // work units along N and M (tiles, or tile pairs along pair_n ? N : M)
-    int pair_n;         // clustered: the two CTAs take adjacent n-tiles (share A) or m-tiles (share B)
 };
 constexpr int MAXG = 32;
 struct OzGroup {
     OzProb p[MAXG];
     int nprob;
-    int nunits;         // work units of the launch (tiles, or tile pairs for 2-CTA clusters)
+    int nunits;         // output tiles of the launch (split-K super-chunks counted apart)
     int raster;         // 0: n-tile fastest, 1: m-tile fastest
 };
 
@@ -425,36 +422,23 @@ __device__ __forceinline__ int prob_of(const OzGroup &g, int t) {
     return i;
 }
 
-// Work unit u of a problem: raster 0 runs the n-units of one A row block side
-// by side (they share the A tile in L2), raster 1 the m-units of one B column
-// block; the split-K super-chunk z varies slowest.  In a 2-CTA cluster a unit
-// is a pair of tiles, adjacent along N (pair_n: both need the same A tile) or
-// along M (both need the same B tile); CTA rank r takes tile 2i + r.  A pair
-// member past the last tile (odd tile count) is virtual: it loads its half of
-// the shared operand for its partner and stores nothing.
+// Work unit u of a problem: raster 0 runs the n-tiles of one A row block side
+// by side (they share the A tile in L2), raster 1 the m-tiles of one B column
+// block; the split-K super-chunk z varies slowest.
 struct TileCoord {
     int n, m, z, kbeg, nkb;
-    bool virt;
 };
 
-__device__ __forceinline__ TileCoord tile_of(const OzProb &pr, int u, int raster, bool cl, int crank) {
+__device__ __forceinline__ TileCoord tile_of(const OzProb &pr, int u, int raster) {
     TileCoord c;
-    int cn, cm;
     if (raster == 0) {
-        cn = u % pr.un;
-        cm = (u / pr.un) % pr.um;
+        c.n = u % pr.ntn;
+        c.m = (u / pr.ntn) % pr.ntm;
     } else {
-        cm = u % pr.um;
-        cn = (u / pr.um) % pr.un;
+        c.m = u % pr.ntm;
+        c.n = (u / pr.ntm) % pr.ntn;
     }
-    c.n = cn;
-    c.m = cm;
-    if (cl) {
-        if (pr.pair_n) c.n = 2 * cn + crank;
-        else c.m = 2 * cm + crank;
-    }
-    c.virt = c.n >= pr.ntn || c.m >= pr.ntm;
-    c.z = u / (pr.un * pr.um);
+    c.z = u / (pr.ntn * pr.ntm);
     const int K = pr.a.K;
     c.kbeg = c.z * SUPER;
     const int kend = min(K, c.kbeg + SUPER);
@@ -466,16 +450,6 @@ __device__ __forceinline__ TileCoord tile_of(const OzProb &pr, int u, int raster
 // with TMA, warp 1 issues the 21 slice-pair MMAs per stage, warps 2..9 drain
 // the six TMEM accumulators after every window into int64 registers and write
 // the finished tile while the next tile's MMAs run.
-//
-// CL = true: 2-CTA clusters.  The two CTAs compute tiles that share one
-// operand tile; each loads three of its six slice planes once and multicasts
-// them into both CTAs, which halves that operand's TMA traffic (the kernel is
-// bound by the TMA's row rate on 32-byte rows).  A stage is refilled only
-// after both CTAs' MMAs have read it: each MMA issuer's commit arrives on the
-// stage's empty barrier in both CTAs.
-constexpr int A_HALF = A_BYTES / 2, B_HALF = B_BYTES / 2;
-
-template <bool CL>
 __global__ void __launch_bounds__(THREADS, 1)
 ozgemm_kernel(const __grid_constant__ OzGroup g) {
     extern __shared__ uint8_t smem_raw[];
@@ -490,12 +464,11 @@ ozgemm_kernel(const __grid_constant__ OzGroup g) {
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nunits = g.nunits;
-    const int crank = CL ? static_cast<int>(tc::cluster_ctarank()) : 0;
-    const int u0 = CL ? static_cast<int>(tc::cluster_id_x()) : static_cast<int>(blockIdx.x);
-    const int ustep = CL ? static_cast<int>(tc::cluster_count_x()) : static_cast<int>(gridDim.x);
+    const int u0 = static_cast<int>(blockIdx.x);
+    const int ustep = static_cast<int>(gridDim.x);
 
     if (threadIdx.x == 0) {
-        for (int i = 0; i < NSTAGE; i++) { tc::mbar_init(&full[i], 1); tc::mbar_init(&empty[i], CL ? 2 : 1); }
+        for (int i = 0; i < NSTAGE; i++) { tc::mbar_init(&full[i], 1); tc::mbar_init(&empty[i], 1); }
         for (int i = 0; i < NACC; i++) { tc::mbar_init(&accfull[i], 1); tc::mbar_init(&accempty[i], 8); }
         *abort_flag = 0;
         tc::fence_barrier_init();
@@ -506,8 +479,6 @@ ozgemm_kernel(const __grid_constant__ OzGroup g) {
     }
     tc::fence_before_sync();
     __syncthreads();
-    // the peer's barriers must be initialized before anything is multicast into it
-    if (CL) tc::cluster_sync();
     tc::fence_after_sync();
     const uint32_t tmem = *tmem_slot;
 
@@ -524,42 +495,18 @@ ozgemm_kernel(const __grid_constant__ OzGroup g) {
                 if (pi != last) {
                     tc::prefetch_tmap(&pr.tmA);
                     tc::prefetch_tmap(&pr.tmB);
-                    if (CL) tc::prefetch_tmap(&pr.tmS);
                     last = pi;
                 }
-                const TileCoord tc_ = tile_of(pr, u - pr.tile0, g.raster, CL, crank);
-                // bytes landing in this CTA per stage: both operands, less the
-                // unshared one when this CTA's tile is virtual
-                const uint32_t own = pr.pair_n ? B_BYTES : A_BYTES;
-                const uint32_t bytes = STAGE_BYTES - (tc_.virt ? own : 0u);
+                const TileCoord tc_ = tile_of(pr, u - pr.tile0, g.raster);
                 for (int kb = 0; kb < tc_.nkb; kb++) {
                     if (!tc::mbar_wait(&empty[stage], phase ^ 1u, abort_flag)) { ok = false; break; }
                     const int kc = tc_.kbeg + kb * KB;
                     uint8_t *sa = smem + stage * STAGE_BYTES;
-                    if (!CL) {
-                        tc::mbar_expect_tx(&full[stage], STAGE_BYTES);
-                        tc::tma_load_3d(sa, &pr.tmA, &full[stage], kc, tc_.m * BM, 0);
-                        tc::tma_load_3d(sa + A_BYTES, &pr.tmB, &full[stage], kc, tc_.n * BN, 0);
-                    } else {
-                        tc::mbar_expect_tx(&full[stage], bytes);
-                        if (pr.pair_n) {
-                            tc::tma_load_3d_mc(sa + crank * A_HALF, &pr.tmS, &full[stage], kc, tc_.m * BM,
-                                               3 * crank, 0x3);
-                            if (!tc_.virt) tc::tma_load_3d(sa + A_BYTES, &pr.tmB, &full[stage], kc, tc_.n * BN, 0);
-                        } else {
-                            tc::tma_load_3d_mc(sa + A_BYTES + crank * B_HALF, &pr.tmS, &full[stage], kc,
-                                               tc_.n * BN, 3 * crank, 0x3);
-                            if (!tc_.virt) tc::tma_load_3d(sa, &pr.tmA, &full[stage], kc, tc_.m * BM, 0);
-                        }
-                    }
+                    tc::mbar_expect_tx(&full[stage], STAGE_BYTES);
+                    tc::tma_load_3d(sa, &pr.tmA, &full[stage], kc, tc_.m * BM, 0);
+                    tc::tma_load_3d(sa + A_BYTES, &pr.tmB, &full[stage], kc, tc_.n * BN, 0);
                     if (++stage == NSTAGE) { stage = 0; phase ^= 1u; }
                 }
-            }
-            // Tail: wait until the last fill of every stage has been consumed by
-            // both CTAs, so no arrival from the peer is still on its way here.
-            for (int i = 0; i < NSTAGE && ok; i++) {
-                if (!tc::mbar_wait(&empty[stage], phase ^ 1u, abort_flag)) break;
-                if (++stage == NSTAGE) { stage = 0; phase ^= 1u; }
             }
         }
     } else if (warp == 1) {
@@ -571,7 +518,7 @@ ozgemm_kernel(const __grid_constant__ OzGroup g) {
             bool ok = true;
             for (int u = u0; u < nunits && ok; u += ustep) {
                 const OzProb &pr = g.p[prob_of(g, u)];
-                const TileCoord tc_ = tile_of(pr, u - pr.tile0, g.raster, CL, crank);
+                const TileCoord tc_ = tile_of(pr, u - pr.tile0, g.raster);
                 for (int kb0 = 0; kb0 < tc_.nkb && ok; kb0 += WPERIOD) {
                     // Unrolled over one window period: the window bookkeeping below is
                     // compile-time except for the tile's first and last K-block.  The
@@ -613,8 +560,7 @@ ozgemm_kernel(const __grid_constant__ OzGroup g) {
                                          tc::idesc_bf16_f32(BM, BN * mma_nb(i)), 1u);
                         }
                         if (!ok) break;
-                        if (CL) tc::mma_commit_mc(&empty[stage], 0x3);
-                        else tc::mma_commit(&empty[stage]);
+                        tc::mma_commit(&empty[stage]);
                         const unsigned ends = we_mask(r) | (kb == tc_.nkb - 1 ? 0x3Fu : 0u);
 #pragma unroll
                         for (int d = 0; d < NACC; d++)
@@ -649,7 +595,7 @@ ozgemm_kernel(const __grid_constant__ OzGroup g) {
             const int pi = prob_of(g, u);
             const OzArgs a = g.p[pi].a;
             const CUtensorMap *tmC = &g.p[pi].tmC;
-            const TileCoord tc_ = tile_of(g.p[pi], u - g.p[pi].tile0, g.raster, CL, crank);
+            const TileCoord tc_ = tile_of(g.p[pi], u - g.p[pi].tile0, g.raster);
             long long acc64[BN / 2];
 #pragma unroll
             for (int i = 0; i < BN / 2; i++) acc64[i] = 0;
@@ -712,7 +658,6 @@ ozgemm_kernel(const __grid_constant__ OzGroup g) {
                 }
             }
             if (!ok) break;
-            if (tc_.virt) continue;   // a virtual pair member: accumulators drained, nothing stored
             if (a.use_tma_store) {
                 // This warp's 32 x 48 block: lane = row, three swizzled 32 x 16 sub-blocks.
                 uint8_t *wbuf = outbuf + ew * OUT_WARP_BYTES;
@@ -775,14 +720,11 @@ ozgemm_kernel(const __grid_constant__ OzGroup g) {
     }
     tc::fence_before_sync();
     __syncthreads();
-    if (CL) {
-        // Neither CTA leaves while the other may still address its shared memory.
-        tc::cluster_sync();
-        if (*abort_flag) {
-            // an abandoned pipeline may still have copies in flight: let them land
-            const unsigned long long t0 = tc::globaltimer();
-            while (tc::globaltimer() - t0 < 2000000ull) {
-            }
+    if (*abort_flag) {
+        // an abandoned pipeline may still have copies in flight: let them land
+        // before the shared memory is released
+        const unsigned long long t0 = tc::globaltimer();
+        while (tc::globaltimer() - t0 < 2000000ull) {
         }
     }
     if (warp == 1) {
@@ -1013,23 +955,8 @@ static jk_status oz_problem(jk_ctx *h, const Sliced &A, const Sliced &B, double 
     if (ntn * ntm * a.nsuper > 0x3fffffffLL) return set_error(h, JK_ERR_SHAPE, "too many tiles");
     pr.ntn = static_cast<int>(ntn);
     pr.ntm = static_cast<int>(ntm);
-    pr.un = pr.ntn;
-    pr.um = pr.ntm;
-    pr.pair_n = 1;
-    if (h->cur_cluster) {
-        // Pair the tiles along the dimension that moves fewer TMA rows per K-step
-        // (shared operand halved), counting the padding of an odd tile count.
-        const double rows_n = (oz::S * oz::BM / 2 + oz::S * oz::BN) * (2.0 * ((ntn + 1) / 2) / ntn);
-        const double rows_m = (oz::S * oz::BM + oz::S * oz::BN / 2) * (2.0 * ((ntm + 1) / 2) / ntm);
-        pr.pair_n = rows_n <= rows_m ? 1 : 0;
-        if (pr.pair_n) pr.un = static_cast<int>((ntn + 1) / 2);
-        else pr.um = static_cast<int>((ntm + 1) / 2);
-        if (pr.pair_n) JK_TRY(make_slice_map(h, &pr.tmS, A.s, A.rows, A.Kpad, oz::BM, A.plane_rows(), oz::S / 2));
-        else JK_TRY(make_slice_map(h, &pr.tmS, B.s, B.rows, B.Kpad, oz::BN, B.plane_rows(), oz::S / 2));
-    }
-    // Issued MMA work: every tile (virtual pair members included) runs all 21
-    // slice pairs over its K-blocks.
-    const double tiles = h->cur_cluster ? 2.0 * pr.un * pr.um : static_cast<double>(ntn) * ntm;
+    // Issued MMA work: every tile runs all 21 slice pairs over its K-blocks.
+    const double tiles = static_cast<double>(ntn) * ntm;
     double kblocks = 0.0;
     for (int zz = 0; zz < a.nsuper; zz++) {
         const int kb = (a.K - zz * oz::SUPER < oz::SUPER ? a.K - zz * oz::SUPER : oz::SUPER);
@@ -1040,34 +967,12 @@ static jk_status oz_problem(jk_ctx *h, const Sliced &A, const Sliced &B, double 
 }
 
 // Launch a list of problems: persistent grid, up to MAXG problems per launch.
-// Clustered (h->cur_cluster): 2-CTA clusters, as many as can be resident.
 static jk_status oz_launch(jk_ctx *h, const std::vector<oz::OzProb> &probs, cudaStream_t st) {
-    int &max_clusters = h->max_clusters;
     if (!h->gemm_smem_set) {
         // a per-device function attribute: set once per handle (a handle is bound to one device)
-        JK_CUDA_TRY(h, cudaFuncSetAttribute(oz::ozgemm_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            oz::SMEM_BYTES));
-        JK_CUDA_TRY(h, cudaFuncSetAttribute(oz::ozgemm_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        JK_CUDA_TRY(h, cudaFuncSetAttribute(oz::ozgemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             oz::SMEM_BYTES));
         h->gemm_smem_set = true;
-    }
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = 2;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cudaLaunchConfig_t cfg = {};
-    cfg.blockDim = dim3(oz::THREADS);
-    cfg.dynamicSmemBytes = oz::SMEM_BYTES;
-    cfg.stream = st;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    if (h->cur_cluster && max_clusters == 0) {
-        cfg.gridDim = dim3(2 * h->num_sms);
-        int n = 0;
-        JK_CUDA_TRY(h, cudaOccupancyMaxActiveClusters(&n, oz::ozgemm_kernel<true>, &cfg));
-        if (n < 1) return set_error(h, JK_ERR_UNSUPPORTED, "no 2-CTA cluster of the sliced GEMM fits an SM pair");
-        max_clusters = n;
     }
     static thread_local oz::OzGroup grp;   // ~20 KB of launch parameters, built on the host
     for (size_t i0 = 0; i0 < probs.size(); i0 += oz::MAXG) {
@@ -1076,21 +981,16 @@ static jk_status oz_launch(jk_ctx *h, const std::vector<oz::OzProb> &probs, cuda
         for (int i = 0; i < np; i++) {
             grp.p[i] = probs[i0 + i];
             grp.p[i].tile0 = static_cast<int>(units);
-            units += static_cast<long long>(grp.p[i].un) * grp.p[i].um * grp.p[i].a.nsuper;
+            units += static_cast<long long>(grp.p[i].ntn) * grp.p[i].ntm * grp.p[i].a.nsuper;
         }
         if (units > 0x7fffffffLL) return set_error(h, JK_ERR_SHAPE, "too many tiles in one launch");
         grp.nprob = np;
         grp.nunits = static_cast<int>(units);
         grp.raster = h->cur_raster;
-        if (h->cur_cluster) {
-            const long long ncl = units < max_clusters ? units : max_clusters;
-            cfg.gridDim = dim3(static_cast<unsigned>(2 * ncl));
+        const int grid = static_cast<int>(units < h->num_sms ? units : h->num_sms);
+        {
             LaunchScope ls(h, KK_OZGEMM, st);
-            JK_CUDA_TRY(h, cudaLaunchKernelEx(&cfg, oz::ozgemm_kernel<true>, grp));
-        } else {
-            const int grid = static_cast<int>(units < h->num_sms ? units : h->num_sms);
-            LaunchScope ls(h, KK_OZGEMM, st);
-            oz::ozgemm_kernel<false><<<grid, oz::THREADS, oz::SMEM_BYTES, st>>>(grp);
+            oz::ozgemm_kernel<<<grid, oz::THREADS, oz::SMEM_BYTES, st>>>(grp);
         }
         JK_LAUNCH_CHECK(h);
     }
@@ -2054,9 +1954,8 @@ extern "C" jk_status jk_debug_sliced_gemm(jk_handle h, int32_t M, int32_t N, int
     if (!A || !B || !C) return set_error(h, JK_ERR_ARG, "NULL operand");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     h->arena.reset(align_up(sizeof(DeviceFlags)));
-    // tile order and clustering: the handle's explicit options, else the defaults
+    // tile order: the handle's explicit option, else the default
     h->cur_raster = h->raster >= 0 ? h->raster : 0;
-    h->cur_cluster = h->cluster >= 0 ? h->cluster : 0;
     Sliced As, Bs;
     if (!take_sliced(h->arena, M, K, 1, As) || !take_sliced(h->arena, N, K, 1, Bs))
         return set_error(h, JK_ERR_OOM, "workspace too small");

@@ -34,18 +34,16 @@ class jk_density(ct.Structure):
 
 
 class jk_tune_config(ct.Structure):
-    _fields_ = [("aux_chunk", ct.c_int32), ("schedule", ct.c_int32), ("raster", ct.c_int32),
-                ("cluster", ct.c_int32)]
+    _fields_ = [("aux_chunk", ct.c_int32), ("schedule", ct.c_int32), ("raster", ct.c_int32)]
 
     def as_dict(self) -> dict:
-        return {"aux_chunk": self.aux_chunk, "schedule": self.schedule, "raster": self.raster,
-                "cluster": self.cluster}
+        return {"aux_chunk": self.aux_chunk, "schedule": self.schedule, "raster": self.raster}
 
 
-OPTIONS = {"aux_chunk": 0, "schedule": 1, "raster": 2, "use_tuned": 3, "cluster": 4, "host_chunk": 5, "slicer": 6,
+OPTIONS = {"aux_chunk": 0, "schedule": 1, "raster": 2, "use_tuned": 3, "host_chunk": 5, "slicer": 6,
            "syrk": 7, "packed_factor": 8}
 # each option's value on a fresh handle (-1: not set, tuned or default configuration)
-OPTION_DEFAULTS = {"aux_chunk": -1, "schedule": -1, "raster": -1, "use_tuned": 1, "cluster": -1, "host_chunk": 0,
+OPTION_DEFAULTS = {"aux_chunk": -1, "schedule": -1, "raster": -1, "use_tuned": 1, "host_chunk": 0,
                    "slicer": 0, "syrk": 0, "packed_factor": 0}
 
 
@@ -363,7 +361,7 @@ class Engine:
     # -- options ---------------------------------------------------------------
     def set_option(self, name: str, value: int):
         """Handle option (JK_OPT_*): "aux_chunk" (>= 0, 0 = automatic, -1 =
-        tuned/default), "schedule", "raster" and "cluster" (-1 = tuned/default,
+        tuned/default), "schedule" and "raster" (-1 = tuned/default,
         0, 1), "use_tuned" (0 or 1), "host_chunk" (>= 0, 0 = automatic),
         "slicer" (0 integer digits, 1 FP32 digits), "syrk" (symmetric
         densities, both engines: 0 full rank update, 1 blocked symmetric rank

@@ -23,7 +23,7 @@ class jk_density(ct.Structure):
 
 
 class jk_tune_config(ct.Structure):
-    _fields_ = [("aux_chunk", ct.c_int32), ("schedule", ct.c_int32), ("raster", ct.c_int32), ("cluster", ct.c_int32)]
+    _fields_ = [("aux_chunk", ct.c_int32), ("schedule", ct.c_int32), ("raster", ct.c_int32)]
 
 
 _lib = ct.CDLL(os.path.join(ROOT, "paper_2608_06536_b300", "libjk.so"))
@@ -71,7 +71,7 @@ shim = ct.CDLL("libcudart.so.13")
 shim.shim_launch.restype = ct.c_char_p
 assert hasattr(shim, "shim_reset"), "the stand-in runtime is not the one loaded"
 
-OPT = {"aux_chunk": 0, "schedule": 1, "raster": 2, "use_tuned": 3, "cluster": 4, "host_chunk": 5, "slicer": 6,
+OPT = {"aux_chunk": 0, "schedule": 1, "raster": 2, "use_tuned": 3, "host_chunk": 5, "slicer": 6,
        "syrk": 7, "packed_factor": 8}
 
 # ---- kernel arguments ----------------------------------------------------------
@@ -109,10 +109,13 @@ class OzArgs(ct.Structure):
 
 
 class OzTail(ct.Structure):
-    _fields_ = [("tile0", I32), ("ntn", I32), ("ntm", I32), ("un", I32), ("um", I32), ("pair_n", I32)]
+    _fields_ = [("tile0", I32), ("ntn", I32), ("ntm", I32)]
 
 
-OZ_PROB_BYTES = (4 * 128 + ct.sizeof(OzArgs) + ct.sizeof(OzTail) + 63) // 64 * 64
+# one problem of a grouped launch: three 128-byte tensor maps (A, B, C), its
+# arguments, its tile counts; 64-byte aligned (the maps' alignment)
+OZ_ARGS_OFF = 3 * 128
+OZ_PROB_BYTES = (OZ_ARGS_OFF + ct.sizeof(OzArgs) + ct.sizeof(OzTail) + 63) // 64 * 64
 OZ_BM, OZ_BN = 128, 80
 
 
@@ -369,10 +372,10 @@ def dec_ozgemm(grid, args):
     units, res = 0, []
     for i in range(nprob):
         pb = base + i * OZ_PROB_BYTES
-        a = OzArgs.from_address(pb + 512)
-        t = OzTail.from_address(pb + 512 + ct.sizeof(OzArgs))
+        a = OzArgs.from_address(pb + OZ_ARGS_OFF)
+        t = OzTail.from_address(pb + OZ_ARGS_OFF + ct.sizeof(OzArgs))
         assert t.tile0 == units, (t.tile0, units)
-        units += t.un * t.um * a.nsuper
+        units += t.ntn * t.ntm * a.nsuper
         assert a.M >= 1 and a.N >= 1 and a.K >= 1 and a.nsuper == (a.K + SUPER - 1) // SUPER
         assert t.ntm == (a.M + OZ_BM - 1) // OZ_BM and t.ntn == (a.N + OZ_BN - 1) // OZ_BN
         nsc = a.nsuper
@@ -682,7 +685,7 @@ def ex_ozgemm(grid, args):
     nprob = I32.from_address(base + 32 * OZ_PROB_BYTES).value
     for i in range(nprob):
         pb = base + i * OZ_PROB_BYTES
-        a = OzArgs.from_address(pb + 512)
+        a = OzArgs.from_address(pb + OZ_ARGS_OFF)
         tA, tB = _tmap(pb), _tmap(pb + 128)
         A, eA = _operand(tA, a.eA, a.a_rpe, a.M, a.K, a.nsuper)
         B, eB = _operand(tB, a.eB, a.b_rpe, a.N, a.K, a.nsuper)
@@ -1286,10 +1289,10 @@ CASES = {
     "build_fp64": build_case(37, 53, [5, 1, 13], [False, True, False], FP64, {}),
     "build_fp64_chunks": build_case(37, 53, [5, 1, 13], [False, True, False], FP64, {"aux_chunk": 17}),
     "build_split": build_case(37, 53, [5, 1, 13], [False, True, False], SPLIT, {}),
-    "build_split_grouped_clustered": build_case(130, 70, [64, 3, 9], [False, False, True], SPLIT,
-                                                {"schedule": 1, "cluster": 1, "raster": 1, "aux_chunk": 17}),
-    "build_split_clustered_chunks": build_case(130, 70, [64, 3, 9], [False, False, True], SPLIT,
-                                               {"schedule": 0, "cluster": 1, "aux_chunk": 30}),
+    "build_split_grouped_raster1": build_case(130, 70, [64, 3, 9], [False, False, True], SPLIT,
+                                              {"schedule": 1, "raster": 1, "aux_chunk": 17}),
+    "build_split_raster1_chunks": build_case(130, 70, [64, 3, 9], [False, False, True], SPLIT,
+                                             {"schedule": 0, "raster": 1, "aux_chunk": 30}),
     "build_split_nbf_above_superchunk": build_case(2100, 3, [2], [False], SPLIT, {}),
     "build_split_fp32_digits": build_case(400, 60, [40, 40], [True, False], SPLIT, {"slicer": 1, "schedule": 1}),
     "build_split_j_only": build_case(37, 53, [5, 13], [False, True], SPLIT, {}, want="J"),
@@ -1302,14 +1305,14 @@ CASES = {
     "build_fp64_syrk": build_case(300, 70, [20, 9, 33], [True, False, True], FP64, {"syrk": 1, "aux_chunk": 30}),
     "build_fp64_syrk_packed": packed(build_case(257, 40, [12, 5], [True, True], FP64,
                                                 {"syrk": 1, "packed_factor": 1})),
-    "build_split_syrk_small_clustered": build_case(100, 30, [7, 4], [True, False], SPLIT,
-                                                   {"syrk": 1, "schedule": 1, "cluster": 1}),
+    "build_split_syrk_small_raster1": build_case(100, 30, [7, 4], [True, False], SPLIT,
+                                                 {"syrk": 1, "schedule": 1, "raster": 1}),
     "batched_split_syrk": batched_case([(60, 150, [6, 6]), (140, 222, [11]), (33, 99, [3, 3, 3])], SPLIT,
                                        {"syrk": 1}, sym=True),
     "build_split_k_only_grouped": build_case(37, 53, [5, 13], [False, True], SPLIT, {"schedule": 1}, want="K"),
     "build_fp64_j_only": build_case(37, 53, [5, 13], [False, True], FP64, {}, want="J"),
     "sliced_gemm": sliced_gemm_case(129, 257, 2047, {}),
-    "sliced_gemm_split_k_clustered": sliced_gemm_case(140, 130, 5000, {"cluster": 1, "raster": 1}),
+    "sliced_gemm_split_k_raster1": sliced_gemm_case(140, 130, 5000, {"raster": 1}),
     "autotune_batched_split": autotune_batched_case([(60, 150, [6, 6]), (111, 222, [11]), (33, 99, [3, 3])], SPLIT),
     "batched_split": batched_case([(60, 150, [6, 6]), (111, 222, [11]), (33, 99, [3, 3, 3])], SPLIT, {}),
     "batched_fp64": batched_case([(60, 150, [6, 6]), (33, 99, [3])], FP64, {}),
@@ -1324,7 +1327,7 @@ CASES = {
     "dense_fp64_chunks": dense_case(37, 53, 3, FP64, {"aux_chunk": 17}),
     "dense_split": dense_case(130, 70, 2, SPLIT, {}),
     "dense_split_chunks": dense_case(130, 70, 2, SPLIT, {"aux_chunk": 30}),
-    "dense_split_clustered": dense_case(37, 53, 3, SPLIT, {"aux_chunk": 17, "cluster": 1}),
+    "dense_split_raster1": dense_case(37, 53, 3, SPLIT, {"aux_chunk": 17, "raster": 1}),
     "dense_split_nbf_above_superchunk": dense_case(2100, 2, 1, SPLIT, {}),
     "grad_split_WV": dense_case(37, 53, 3, SPLIT, {"aux_chunk": 17}, grad="WV"),
     "grad_split_W": dense_case(37, 53, 3, SPLIT, {}, grad="W"),
@@ -1369,12 +1372,12 @@ CASES = {
 # the factors are never touched and cost no memory beyond their page tables.
 FULL_CASES = {
     "full_multi_state_tuned": build_case(400, 2400, [40] * 8, [True] + [False] * 7, SPLIT,
-                                         {"aux_chunk": 3834, "schedule": 1, "raster": 0, "cluster": 0}),
+                                         {"aux_chunk": 3834, "schedule": 1, "raster": 0}),
     "full_multi_state_default": build_case(400, 2400, [40] * 8, [True] + [False] * 7, SPLIT, {}),
     "full_multi_state_syrk": build_case(400, 2400, [40] * 8, [True] + [False] * 7, SPLIT,
-                                        {"aux_chunk": 3834, "schedule": 1, "raster": 0, "cluster": 0, "syrk": 1}),
-    "full_multi_state_clustered": build_case(400, 2400, [40] * 8, [True] + [False] * 7, SPLIT,
-                                             {"schedule": 1, "cluster": 1}),
+                                        {"aux_chunk": 3834, "schedule": 1, "raster": 0, "syrk": 1}),
+    "full_multi_state_raster1": build_case(400, 2400, [40] * 8, [True] + [False] * 7, SPLIT,
+                                           {"schedule": 1, "raster": 1}),
     "full_dense": dense_case(400, 2400, 8, SPLIT, {}),
     "full_density_grad": dense_case(400, 2400, 8, SPLIT, {}, grad="WV"),
     "full_pairs": pair_case(400, 2400, [40] * 8, [False] * 8, [40] * 8, [False] * 8, SPLIT, {}),
@@ -1410,7 +1413,7 @@ def fuzz_cases(count, seed):
         opts = {}
         if g.random() < 0.5:
             opts["aux_chunk"] = int(g.integers(1, naux + 3))
-        for name in ("schedule", "raster", "cluster", "slicer", "syrk"):
+        for name in ("schedule", "raster", "slicer", "syrk"):
             if g.random() < 0.5:
                 opts[name] = int(g.integers(0, 2))
         kind = g.choice(["build", "adjoint", "dense", "grad", "pairs", "laplace", "batched", "host"])

@@ -95,12 +95,12 @@ def test_multi_state_full(eng):
     assert fJ <= FP64_REL * np.abs(Jfn).max() and fK <= FP64_REL * np.abs(Kfn).max()
     assert abs_err(Jn, Jfn) < 2 * SPLIT_ABS and abs_err(Kn, Kfn) < 2 * SPLIT_ABS
     # the configuration bench.py times on this workload (its autotuner's pick):
-    # all aux indices in one chunk, grouped launches, n-tile raster, one CTA per tile
-    for name, v in (("aux_chunk", 3834), ("schedule", 1), ("raster", 0), ("cluster", 0)):
+    # all aux indices in one chunk, grouped launches, n-tile raster
+    for name, v in (("aux_chunk", 3834), ("schedule", 1), ("raster", 0)):
         eng.set_option(name, v)
     Jt, Kt = eng.build(L, X, Y, m.sym, "split")
     eng.sync_status()
-    for name in ("aux_chunk", "schedule", "raster", "cluster"):
+    for name in ("aux_chunk", "schedule", "raster"):
         eng.set_option(name, -1)
     Jtn, Ktn = to_np(Jt), to_np(Kt)
     tJ, tK = np.abs(Jtn[s, mu, nu] - Jo).max(), np.abs(Ktn[s, mu, nu] - Ko).max()

@@ -3,7 +3,7 @@
 libjk.so is driven through every entry point in a child process whose CUDA
 runtime is the recording stand-in of tests/hostsim/cudart_shim.c: host
 memory stands in for device memory, kernels are recorded instead of run.
-For each case (both engines, chunked, grouped and clustered schedules,
+For each case (both engines, chunked and grouped schedules, both tile orders,
 batched, host-resident, adjoint, dense densities, the density gradient,
 pairings, Laplace builds, the arena-free build, the autotuner) this checks:
 
@@ -153,7 +153,6 @@ def _kernels(rec):
     ("pairs_split", ["ozgemm_kernel", "pair_dot_kernel"]),
     ("laplace_split", ["laplace_scale_kernel", "ozgemm_kernel"]),
     ("laplace_fp64_weighted", ["laplace_scale_kernel", "weighted_sum_kernel"]),
-    ("build_split_grouped_clustered", ["ozgemm_kernelILb1E"]),
     ("build_split_fp32_digits", ["slice4f_kernel"]),
 ])
 def test_expected_kernels(records, name, must):
@@ -296,7 +295,7 @@ def test_repeat_calls_compute_the_oracle(shim_dir):
         assert max(c[1] for c in rec["checks"]) < 1e-12, (name, rec["checks"])
 
 
-FAULT_CASES = ["build_split", "build_split_grouped_clustered", "build_fp64_chunks", "batched_split",
+FAULT_CASES = ["build_split", "build_split_grouped_raster1", "build_fp64_chunks", "batched_split",
                "host_packed_split", "adjoint_split", "dense_split_chunks", "grad_split_WV", "pairs_split",
                "laplace_split_weighted_sym", "noalloc"]
 

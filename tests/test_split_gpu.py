@@ -26,13 +26,13 @@ def dbg():
     return lib
 
 
-def sliced_gemm(lib, A, B, cluster=-1, raster=-1):
+def sliced_gemm(lib, A, B, raster=-1):
     M, K = A.shape
     N = B.shape[0]
     ws = torch.empty(lib.jk_debug_sliced_gemm_workspace(M, N, K), dtype=torch.uint8, device="cuda")
     h = ct.c_void_p()
     assert lib.jk_create(ct.byref(h), ct.c_void_p(ws.data_ptr()), ws.numel()) == 0
-    assert lib.jk_set_option(h, 4, cluster) == 0 and lib.jk_set_option(h, 2, raster) == 0
+    assert lib.jk_set_option(h, 2, raster) == 0
     Ad = torch.from_numpy(np.ascontiguousarray(A)).cuda()
     Bd = torch.from_numpy(np.ascontiguousarray(B)).cuda()
     C = torch.full((M, N), float("nan"), dtype=torch.float64, device="cuda")
@@ -47,16 +47,16 @@ def exact_product(A, B):
     return (A.astype(np.longdouble) @ B.T.astype(np.longdouble))
 
 
-@pytest.mark.parametrize("cluster", [0, 1])
+@pytest.mark.parametrize("raster", [0, 1])
 @pytest.mark.parametrize("M,N,K", [(1, 1, 1), (128, 128, 128), (300, 200, 500), (129, 257, 2047), (700, 90, 64),
                                    (130, 500, 100)])
-def test_sliced_gemm_random(dbg, M, N, K, cluster):
-    """Odd and even tile counts along M and N: 2-CTA clusters pair tiles along
-    either dimension and pad an odd count with a virtual tile."""
+def test_sliced_gemm_random(dbg, M, N, K, raster):
+    """Odd and even tile counts along M and N, ragged tails in every
+    dimension, both tile orders."""
     rng = np.random.default_rng(M + N + K)
     A = rng.standard_normal((M, K))
     B = rng.standard_normal((N, K))
-    C = sliced_gemm(dbg, A, B, cluster=cluster)
+    C = sliced_gemm(dbg, A, B, raster=raster)
     ref = exact_product(A, B)
     assert np.all(np.isfinite(C))
     # error budget: 2^-48 of each row's scale per operand, summed over K
@@ -64,15 +64,15 @@ def test_sliced_gemm_random(dbg, M, N, K, cluster):
     assert float(np.max(np.abs(C - ref) / scale)) < 2.0 ** -44
 
 
-@pytest.mark.parametrize("cluster,raster", [(0, 0), (1, 0), (1, 1)])
-def test_sliced_gemm_split_k(dbg, cluster, raster):
-    """K > 2048: int64 partials summed in 128-bit integers (partials of a
-    virtual tile must not land in the next super-chunk's rows)."""
+@pytest.mark.parametrize("raster", [0, 1])
+def test_sliced_gemm_split_k(dbg, raster):
+    """K > 2048: int64 partials summed in 128-bit integers (the padding rows
+    of a ragged row tile must not land in the next super-chunk's rows)."""
     rng = np.random.default_rng(11)
     M, N, K = 140, 130, 5000
     A = rng.standard_normal((M, K)) * np.exp(-np.arange(K) / 2000.0)
     B = rng.standard_normal((N, K))
-    C = sliced_gemm(dbg, A, B, cluster=cluster, raster=raster)
+    C = sliced_gemm(dbg, A, B, raster=raster)
     ref = exact_product(A, B)
     scale = np.abs(A).max(1)[:, None] * np.abs(B).max(1)[None, :] * np.sqrt(K)
     assert float(np.max(np.abs(C - ref) / scale)) < 2.0 ** -44
@@ -89,8 +89,8 @@ def test_sliced_gemm_integers_exact(dbg):
     A[:, :64] = 1000.0
     B[:, :64] = 1000.0
     A[:, 64:128] = 1.0
-    for cluster in (0, 1):
-        C = sliced_gemm(dbg, A, B, cluster=cluster)
+    for raster in (0, 1):
+        C = sliced_gemm(dbg, A, B, raster=raster)
         np.testing.assert_array_equal(C, (A.astype(np.int64) @ B.T.astype(np.int64)).astype(np.float64))
     C = sliced_gemm(dbg, A, B)
     ref = (A.astype(np.int64) @ B.T.astype(np.int64)).astype(np.float64)

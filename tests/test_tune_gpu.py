@@ -26,17 +26,15 @@ def _gpu(m):
             [torch.from_numpy(y).cuda() for y in m.Y])
 
 
-@pytest.mark.parametrize("chunk,schedule,raster,cluster", [
-    (0, 0, 1, 1), (0, 1, 0, 1), (0, 1, 1, 0), (37, 1, 1, 1), (37, 0, 1, 0), (300, 1, 0, 0), (0, 0, 0, 0),
-    (300, 0, 0, 1)])
-def test_every_split_configuration_matches_oracle(eng, chunk, schedule, raster, cluster):
+@pytest.mark.parametrize("chunk,schedule,raster", [
+    (0, 0, 1), (0, 1, 0), (0, 1, 1), (37, 1, 1), (37, 0, 1), (300, 1, 0), (0, 0, 0), (300, 0, 0)])
+def test_every_split_configuration_matches_oracle(eng, chunk, schedule, raster):
     m = inputs.custom(150, 300, 60.0, [12, 9, 20], [False, True, False], seed=3)
     Jo, Ko = oracle.build(m.L, m.X, m.Y)
     L, X, Y = _gpu(m)
     eng.set_option("aux_chunk", chunk)
     eng.set_option("schedule", schedule)
     eng.set_option("raster", raster)
-    eng.set_option("cluster", cluster)
     J, K = eng.build(L, X, Y, m.sym, "split")
     eng.sync_status()
     assert abs_err(to_np(J), Jo) < SPLIT_ABS and abs_err(to_np(K), Ko) < SPLIT_ABS
@@ -52,7 +50,7 @@ def test_autotune_split_caches_and_is_used(eng):
     text = jk.tune_export()
     assert len(text.splitlines()) == 1
     fields = text.split()
-    assert [int(v) for v in fields[10:14]] == [cfg["aux_chunk"], cfg["schedule"], cfg["raster"], cfg["cluster"]]
+    assert [int(v) for v in fields[10:13]] == [cfg["aux_chunk"], cfg["schedule"], cfg["raster"]]
     # the tuned configuration is applied to the next build: same launch count
     # as forcing it explicitly, and the oracle's result
     eng.profile(True)
@@ -76,7 +74,7 @@ def test_autotune_fp64(eng):
     Jo, Ko = oracle.build(m.L, m.X, m.Y)
     L, X, Y = _gpu(m)
     cfg, ms = eng.autotune(L, X, Y, m.sym, "fp64", reps=1)
-    assert ms > 0 and cfg["schedule"] == 0 and cfg["raster"] == 0 and cfg["cluster"] == 0
+    assert ms > 0 and cfg["schedule"] == 0 and cfg["raster"] == 0
     J, K = eng.build(L, X, Y, m.sym, "fp64")
     assert rel_err(to_np(J), Jo) < FP64_REL and rel_err(to_np(K), Ko) < FP64_REL
 

@@ -39,7 +39,7 @@ def _dev(m):
     (300, 70, [20, 9, 33], [True, False, True], {"schedule": 0, "aux_chunk": 30}),      # chunk sums
     (300, 120, [40, 7], [True, True], {"schedule": 0, "aux_chunk": 70}),                # split-K partials
     (257, 90, [64, 5, 11], [True, True, False], {"schedule": 1, "aux_chunk": 40}),      # grouped, ragged
-    (100, 30, [7, 4], [True, False], {"schedule": 1, "cluster": 1}),                    # one block, clusters
+    (100, 30, [7, 4], [True, False], {"schedule": 1, "raster": 1}),                     # one block, m-tile raster
     (400, 240, [40, 40], [True, False], {"schedule": 1}),                               # the multi-state shape
 ])
 def test_blocked_symmetric_rank_update(n, naux, ks, sym, opts):
