@@ -1,24 +1,41 @@
 #!/usr/bin/env python
 """Throughput of the Cholesky J/K engine on one B300 (or N replicas).
 
-One step = one full J/K build (panels, J metric dot, J back-contraction,
-K rank update, final FP64 reduction) for the multi-state workload:
-nbf = 400, naux = 2400, eight densities of width 40 (one symmetric ground
-density, seven non-symmetric transition densities), seeded synthetic inputs.
+One step = one full split-precision J/K build (panels L^P X, L^P Y on the
+tensor cores, J metric dot, FP64 J back-contraction, K rank update, FP64
+final reduction) for the large single molecule: nbf = 1000, naux = 5000,
+sixteen non-symmetric transition densities of width 100, the 40 GB FP64
+factor drawn on the device (seeded synthetic inputs).
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision split|fp64]
-                  [--impl ours|reference]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--case large_single|multi_state|...] [--headline-only]
 
-Prints ONE JSON line on rank 0.  `value` is algorithmic TFLOP/s (FP64-
-equivalent work, slice products of the split path are cost, not counted) with
-all inputs resident in HBM; `e2e` is the same metric through the public API
-with pinned host inputs copied in and J/K copied out inside the timed region.
+Prints ONE JSON line on rank 0.  `value` is algorithmic TFLOP/s (the
+FP64-equivalent work of the build; the split path's slice products are cost,
+not counted) with every input resident in HBM.  In the same line:
+  e2e            the same metric through jk_build_host(_packed) with pinned
+                 host inputs uploaded and J, K read back inside the timed region;
+  fp64_gpu       the plain FP64 engine on the same inputs: time, TFLOP/s, the
+                 split engine's speed-up over it;
+  error          max |split - FP64 engine| per output, and both engines
+                 against the CPU oracle on sampled entries;
+  roofline       the dominant kernel (the tcgen05 sliced GEMM): algorithmic
+                 TFLOP/s against the measured BF16 peak, beside the issued
+                 BF16 MMA rate;
+  j_stream       the FP64 J back-contraction: HBM GB/s and FP64 TFLOP/s
+                 against the measured HBM peak and the FP64 FMA rate this run
+                 measures with the library's probe kernel;
+  cpu_baseline   the oracle on a bounded, named sample of the same workload;
+  configs        the other workloads (one molecule small, multi-state,
+                 adjoint, uneven batch replayed as a CUDA graph), unless
+                 --headline-only.
 Under torchrun every rank runs its own replica (the path has no exchange
 step); value = all ranks' work / the slowest rank's time.
 """
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import statistics
@@ -31,12 +48,32 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "Cholesky J/K TFLOP/s (% tensor peak), split-prec vs FP64 GPU at ≤1e-10 error"
-WORKLOAD = "multi-state nbf=400 naux=2400 tau=400, 8 densities k=40 (1 symmetric ground + 7 non-symmetric transition), FP64 in/out"
+WORKLOADS = {
+    "large_single": "large single molecule: nbf=1000 naux=5000 tau=1000 (L = 40 GB FP64, drawn on the device), "
+                    "16 non-symmetric transition densities k=100, split precision vs the FP64 engine",
+    "multi_state": "multi-state nbf=400 naux=2400 tau=400, 8 densities k=40 (1 symmetric ground + 7 "
+                   "non-symmetric transition), FP64 in/out",
+    "small": "one molecule small: nbf=48 naux=300 tau=60, one non-symmetric density k=6",
+    "profile": "the large single molecule's structure with naux=400 (L = 3.2 GB FP64, larger than L2), for ncu",
+}
+SPLIT_GATE = 1e-10       # absolute, output units (split engine)
+FP64_GATE = 1e-12        # relative to max |output| (FP64 engine)
 
-# FP64 issue-rate peak of B300 for the plain engine's roofline: a dependent-
-# free FP64 FMA stream measured 1.20 TFLOP/s on this machine's B300 (148 SMs at
-# 2032 MHz, i.e. 2 FP64 FMA per clock per SM; nominal 1.25 TFLOP/s).
-FP64_PEAK_TFLOPS = 1.20
+# ncu figures of the sliced GEMM (one capture of the profile case), valid only
+# for the kernel sources they were taken on: keyed by kernel_source_hash().
+# Each entry: per-launch DRAM bytes of a full-size launch (dram__bytes_read.sum
+# + dram__bytes_write.sum of the capture, scaled by aux indices),
+# sm__pipe_tensor_cycles_active (% of peak, elapsed) and the capture's command.
+NCU_GEMM = {}
+KERNEL_SOURCES = ("split.cu", "tc.cuh", "fixed.cuh", "digits.cuh")
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2608_06536_b300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
 
 
 def build_flops(n, naux, ks, sym):
@@ -50,20 +87,40 @@ def build_flops(n, naux, ks, sym):
     return f
 
 
-# DRAM bytes of the sliced GEMM measured by ncu (dram__bytes_read.sum +
-# dram__bytes_write.sum) on the profile case (nbf=400, naux=600, 8 densities
-# k=40; summary in profiles/ozgemm_tcgen05_profile_case.md) in the tuned
-# configuration (one aux chunk, grouped schedule: one panel launch and one
-# rank-update launch per build): the panel launch moved 2.268 GB and the
-# grouped rank-update launch 2.040 GB for 600 aux indices.  Both grow in
-# proportion to naux, which is how they are scaled to the full multi-state
-# launches.
-OZ_PANEL_BYTES_PER_P = 2.268e9 / 600
-OZ_RANK_BYTES_PER_P = 2.040e9 / 600
-
-
 def panel_rank_flops(n, naux, ks, sym):
+    """The part of build_flops the sliced GEMM carries (panels and rank updates)."""
     return sum((3.0 if s else 6.0) * n * n * k * naux for k, s in zip(ks, sym))
+
+
+def jstream_bytes_flops(n, naux, nd):
+    """Algorithmic HBM bytes and FP64 flops of the J back-contraction: the
+    upper triangle of every L^P read once for all densities, J written once;
+    one FMA per upper-triangle entry, aux index and density."""
+    tri = n * (n + 1) // 2
+    return 8.0 * tri * naux + 8.0 * nd * n * n, 2.0 * tri * naux * nd
+
+
+def adjoint_flops(n, naux, ks, sym):
+    """Algorithmic flops of the adjoint: 12 n^2 k naux (dX, dY with the panels
+    recomputed) + 4 n^2 k naux (dL outer products) + 4 n^2 naux (J terms) per
+    density."""
+    return sum(12.0 * n * n * k * naux + 4.0 * n * n * k * naux + 4.0 * n * n * naux for k in ks)
+
+
+def dense_flops(n, naux, nd):
+    """Algorithmic flops of jk_build_dense (J and K) for nd dense densities:
+    K 2n^3 naux for the panels L^P D and 2n^3 naux for the rank update, J
+    2n^2 naux for the metric dot and 2n^2 naux for the back-contraction."""
+    return nd * (4.0 * n ** 3 * naux + 4.0 * n * n * naux)
+
+
+def pair_flops(n, naux, kl, syml, kr, symr):
+    """Algorithmic flops of jk_pair with both pairings: the right densities'
+    build plus, per map and right density, U_b = M_b Z_L (2 n^2 ctot_L) and the
+    pair dots (2 n k_a per pair)."""
+    ctot_l = sum(k if s else 2 * k for k, s in zip(kl, syml))
+    contract = 2 * len(kr) * (2.0 * n * n * ctot_l + sum(2.0 * n * k for k in kl))
+    return build_flops(n, naux, kr, symr) + contract
 
 
 def load_peaks():
@@ -116,6 +173,7 @@ class ClockSampler:
         os.unlink(self.path)
         if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+
         def num(x):
             try:
                 return float(x)
@@ -169,98 +227,224 @@ def job_tflops(flops_per_rank, ms_max, world):
     return world * flops_per_rank / (ms_max * 1e-3) / 1e12
 
 
-_CPU_SAMPLE = {}
+# ---------------------------------------------------------------------------
+# The oracle on bounded samples (CPU baseline and reference arm)
+# ---------------------------------------------------------------------------
+# (densities, aux indices) of the oracle's sample per workload: about 10-30 s
+# of CPU work on the machine's host cores.
+CPU_SAMPLE = {"large_single": (2, 160), "profile": (2, 160), "multi_state": (3, 2400), "small": (1, 300)}
 
 
-def cpu_baseline_sample(L=None):
-    """The oracle as it stands on a bounded sample of the workload: three of
-    the seven non-symmetric densities (k=40) over all 2400 aux indices."""
+def cpu_sample_molecule(case):
+    from paper_2608_06536_b300 import inputs
+    if case in ("large_single", "profile"):
+        return inputs.large_single()
+    if case == "small":
+        return inputs.one_molecule_small(with_factor=False)
+    return inputs.multi_state(with_factor=False)
+
+
+def cpu_baseline_sample(case, L=None, _cache={}):
+    """The oracle as it stands on a bounded sample of the workload: the first
+    `nds` non-symmetric densities over the first `na` aux indices (exact
+    subsets of the same inputs, never extrapolated).  L: the workload's host
+    factor, if the caller has it (else the needed slices are drawn)."""
+    import numpy as np
     import oracle
     from paper_2608_06536_b300 import inputs
-    n, tau, na, nds = 400, 400.0, 2400, 3
-    if "L" not in _CPU_SAMPLE:
-        _CPU_SAMPLE["L"] = L if L is not None else inputs.factor(n, na, tau, 0)
-        _CPU_SAMPLE["XY"] = [inputs.transition_density(n, 40, s, 0) for s in range(1, 1 + nds)]
-    L = _CPU_SAMPLE["L"]
-    X = [xy[0] for xy in _CPU_SAMPLE["XY"]]
-    Y = [xy[1] for xy in _CPU_SAMPLE["XY"]]
-    oracle.build(L[:2], X[:1], Y[:1])   # load + warm
+    m = cpu_sample_molecule(case)
+    nds, na = CPU_SAMPLE.get(case, (2, 160))
+    na = min(na, m.naux)
+    sel = [s for s in range(m.nd) if not m.sym[s]][:nds]
+    key = (case, na)
+    if key not in _cache:
+        _cache[key] = np.ascontiguousarray(L[:na]) if L is not None else inputs.factor(m.n, na, m.tau, m.seed)
+    Ls = _cache[key]
+    X = [m.X[s] for s in sel]
+    Y = [m.Y[s] for s in sel]
+    oracle.build(Ls[:2], X[:1], Y[:1])   # load + warm
     t0 = time.perf_counter()
-    oracle.build(L, X, Y)
+    oracle.build(Ls, X, Y)
     dt = time.perf_counter() - t0
-    flops = build_flops(n, na, [40] * nds, [False] * nds)
+    flops = build_flops(m.n, na, [m.ks[s] for s in sel], [False] * len(sel))
     cores = len(os.sched_getaffinity(0))
     omp = os.environ.get("OMP_NUM_THREADS")
     return {"value": flops / dt / 1e12, "unit": "TFLOP/s", "cores": int(omp) if omp else cores,
             "kind": "oracle",
-            "sample": f"{nds} of the 7 non-symmetric densities (k=40) x all {na} aux indices, nbf=400; "
-                      f"{flops:.3g} algorithmic flop in {dt:.2f} s",
+            "sample": f"{len(sel)} of the {m.nd} densities (k={m.ks[sel[0]]}) x the first {na} of {m.naux} aux "
+                      f"indices, nbf={m.n}; {flops:.3g} algorithmic flop in {dt:.2f} s",
             "seconds": dt}
 
 
 def run_reference(args, rank, world):
     if rank != 0:
         return
+    case = args.case if args.case in CPU_SAMPLE else "large_single"
     steps = []
     for _ in range(args.warmup):
-        cpu_baseline_sample()
+        cpu_baseline_sample(case)
     for _ in range(args.steps):
-        steps.append(cpu_baseline_sample())
+        steps.append(cpu_baseline_sample(case))
     v = statistics.median(s["value"] for s in steps)
     sec = statistics.median(s["seconds"] for s in steps)
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "TFLOP/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64 (long double accumulation)", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "sample": steps[0]["sample"]},
+            "config": {"workload": WORKLOADS[case], "sample": steps[0]["sample"]},
             "cpu_baseline": {k: steps[0][k] for k in ("unit", "cores", "kind", "sample")} | {"value": v},
             "e2e": {"value": v, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------------------
+# Measurement helpers
+# ---------------------------------------------------------------------------
+_T0 = time.perf_counter()
+
+
+def phase(name):
+    """Wall-clock progress on stderr (the JSON line stays alone on stdout)."""
+    print(f"[bench {time.perf_counter() - _T0:7.1f} s] {name}", file=sys.stderr, flush=True)
+
+
+def timed(fn, steps, warmup, stream):
+    """ms per call of fn() on `stream`: warmup untimed calls, then `steps`
+    calls bracketed by CUDA events, synchronized on both sides."""
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def fp64_peak(eng, stream):
+    """FP64 TFLOP/s of the library's FMA-stream probe (best of three launches)."""
+    import torch
+    eng.fp64_fma_probe(stream=stream)
+    torch.cuda.synchronize()
+    best = 0.0
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fl = eng.fp64_fma_probe(blocks_per_sm=8, iters=1 << 16, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        best = max(best, fl / (e0.elapsed_time(e1) * 1e-3) / 1e12)
+    return best
+
+
+def sample_entries(rng, nd, n, count):
+    s = rng.integers(0, nd, count)
+    mu = rng.integers(0, n, count)
+    nu = rng.integers(0, n, count)
+    s[:2] = [0, nd - 1]
+    mu[:2] = [0, n - 1]
+    nu[:2] = [n - 1, 0]
+    return s, mu, nu
+
+
+def gemm_roofline(prof, flops_alg_per_step, issued, steps, peaks, peak_src):
+    ms, cnt = prof.get("ozgemm_tcgen05", (0.0, 0))
+    if not cnt:
+        return None
+    pk = peaks.get("bf16_tflops_sustained")
+    achieved = flops_alg_per_step * steps / (ms * 1e-3) / 1e12
+    issued_tf = issued / (ms * 1e-3) / 1e12 if issued else None
+    h = kernel_source_hash()
+    ncu = NCU_GEMM.get(h)
+    return {"kernel": "ozgemm_kernel (tcgen05 sliced GEMM: panels and rank updates)", "bound": "tensor",
+            "achieved": achieved, "peak": pk, "unit": "TFLOP/s", "frac": achieved / pk,
+            "achieved_counts": "algorithmic (FP64-equivalent) flops of the panels and rank updates, 6 n^2 k naux "
+                               "per non-symmetric density; slice products are cost, not counted",
+            "peak_source": f"bf16_tflops_sustained of the {peak_src} peaks (MEASURED_PEAKS.json)",
+            "issued_tflops": issued_tf, "issued_frac": (issued_tf / pk) if issued_tf else None,
+            "issued_counts": "dense BF16 MMA flops issued (21 slice pairs over the padded tiles)",
+            "traffic": ncu["traffic"] if ncu else None,
+            "tensor_pipe_active": ncu["tensor_pipe_active"] if ncu else None,
+            "ncu_capture": ncu["capture"] if ncu else "none for the current kernel sources",
+            "kernel_sources": h, "avg_launch_ms": ms / cnt, "launches": cnt}
+
+
+def jstream_roofline(prof, n, naux, nd, steps, peaks, fp64_tflops):
+    ms, cnt = prof.get("jstream_fp64", (0.0, 0))
+    if not cnt:
+        return None
+    by, fl = jstream_bytes_flops(n, naux, nd)
+    per = ms / steps
+    gbs = by / (per * 1e-3) / 1e9
+    tf = fl / (per * 1e-3) / 1e12
+    hbm = peaks.get("hbm_gbs")
+    return {"kernel": "jstream_sym_kernel (FP64 J back-contraction, second stream)", "ms_per_step": per,
+            "launches": cnt, "algorithmic_bytes": by, "achieved_gbs": gbs, "hbm_peak_gbs": hbm,
+            "hbm_frac": gbs / hbm, "fp64_tflops": tf, "fp64_peak_tflops": fp64_tflops,
+            "fp64_frac": tf / fp64_tflops if fp64_tflops else None,
+            "fp64_peak_source": "the library's FP64 FMA-stream probe (jk_debug_fp64_fma), measured in this run",
+            "bound": "fp64" if (fp64_tflops and tf / fp64_tflops > gbs / hbm) else "hbm"}
+
+
+# ---------------------------------------------------------------------------
+# Headline: one molecule, split engine, beside the FP64 engine
+# ---------------------------------------------------------------------------
+def headline_molecule(case, dev):
+    """(molecule, device factor, host factor or None)."""
+    import torch
+    from paper_2608_06536_b300 import inputs
+    if case == "large_single":
+        m = inputs.large_single()
+        return m, inputs.factor_device(m.n, m.naux, m.tau, m.seed, device=dev), None
+    if case == "profile":
+        m = inputs.molecule(1000, 400, 1000.0, [(100, False)] * 16, 0, with_factor=False)
+        return m, inputs.factor_device(m.n, m.naux, m.tau, m.seed, device=dev), None
+    m = inputs.one_molecule_small() if case == "small" else inputs.multi_state()
+    return m, torch.from_numpy(m.L).to(dev), m.L
+
+
 def run_ours(args, rank, world, local):
     import numpy as np
     import torch
-    from paper_2608_06536_b300 import inputs, jk
+    from paper_2608_06536_b300 import jk
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    if args.case == "profile":
-        # same structure, a quarter of the aux indices (L = 768 MB > L2): for ncu captures
-        m = inputs.molecule(400, 600, 400.0, [(40, True)] + [(40, False)] * 7, 0)
-    else:
-        m = inputs.multi_state()
+    st = torch.cuda.current_stream(dev)
+    case = args.case
+    m, Ld, Lhost = headline_molecule(case, dev)
+    phase(f"inputs of {case} ready")
     n, naux, ks, sym = m.n, m.naux, m.ks, m.sym
     flops = build_flops(n, naux, ks, sym)
-    # --packed-factor: the factor resident as packed upper triangles (half the memory)
-    Ld = (jk.pack_factor(m.L) if args.packed_factor else torch.from_numpy(m.L)).to(dev)
+    Lfac = jk.pack_factor(Ld) if args.packed_factor else Ld     # packed: half the device memory
     Xd = [torch.from_numpy(x).to(dev) for x in m.X]
     Yd = [torch.from_numpy(y).to(dev) for y in m.Y]
     eng = jk.Engine(dev)
     eng.set_option("slicer", args.slicer)
     eng.set_option("syrk", args.syrk)
     eng.set_option("packed_factor", 1 if args.packed_factor else 0)
-    prec = args.precision
-    st = torch.cuda.current_stream(dev)
 
-    # autotune (untimed): the fastest run-time configuration for this shape is
-    # cached and every build below uses it
+    # run-time configuration: fixed (--config), or the autotuner's pick for
+    # this shape (untimed; the cached pick is used by every build below)
     tuned = None
     if args.config:
-        # a fixed configuration (for profiling runs): no tuning
         for name, v in zip(("aux_chunk", "schedule", "raster"), args.config.split(",")):
             eng.set_option(name, int(v))
         tuned = {"fixed": args.config}
     elif args.tune:
-        cfg, tms = eng.autotune(Ld, Xd, Yd, sym, prec, reps=1 if prec == "fp64" else 2)
+        cfg, tms = eng.autotune(Lfac, Xd, Yd, sym, "split", reps=1)
         tuned = dict(cfg, ms=tms)
-    # warm-up (also sizes the arena)
-    for _ in range(args.warmup):
-        J, K = eng.build(Ld, Xd, Yd, sym, prec)
+    phase(f"configuration {tuned}")
+    J, K = eng.build(Lfac, Xd, Yd, sym, "split")
     eng.sync_status()
-    torch.cuda.synchronize(dev)
 
-    # ---- device-resident timed region --------------------------------------
+    # ---- device-resident timed region (split engine) -----------------------
+    for _ in range(args.warmup):
+        eng.build(Lfac, Xd, Yd, sym, "split", J=J, K=K)
+    torch.cuda.synchronize(dev)
     clocks = ClockSampler(local)
     clocks.start()
     eng.profile(True)
@@ -268,209 +452,311 @@ def run_ours(args, rank, world, local):
     l0 = eng.launch_count()
     tf0 = eng.issued_tensor_flops()
     barrier(world)
-    torch.cuda.synchronize(dev)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(st)
-    for _ in range(args.steps):
-        J, K = eng.build(Ld, Xd, Yd, sym, prec, J=J, K=K)
-    e1.record(st)
-    torch.cuda.synchronize(dev)
+    ms = timed(lambda: eng.build(Lfac, Xd, Yd, sym, "split", J=J, K=K), args.steps, 0, st)
     barrier(world)
-    ms = e0.elapsed_time(e1) / args.steps
+    prof = eng.profile_read()
     launches = eng.launch_count() - l0
     issued = eng.issued_tensor_flops() - tf0
-    prof = eng.profile_read()
     eng.profile(False)
     clk = clocks.stop()
     eng.sync_status()
     ms_max = max_over_ranks(ms, world, dev)
     value = job_tflops(flops, ms_max, world)
+    kernels_ms = {k: v[0] / args.steps for k, v in prof.items()}
+    phase(f"split engine: {ms:.2f} ms per build")
 
     if args.quick:
         if rank == 0:
-            print(json.dumps({"case": args.case, "engine": prec, "ms_per_step": ms_max, "value": value,
-                              "kernels_ms": {k: v[0] / args.steps for k, v in prof.items()},
+            print(json.dumps({"case": case, "ms_per_step": ms_max, "value": value, "kernels_ms": kernels_ms,
                               "launches_per_step": launches / args.steps, "tuned": tuned, "slicer": args.slicer,
                               "syrk": args.syrk, "packed_factor": bool(args.packed_factor),
-                              "issued_tensor_tflops": issued / args.steps / (ms_max * 1e-3) / 1e12}),
-                  flush=True)
+                              "issued_tensor_tflops": issued / args.steps / (ms_max * 1e-3) / 1e12,
+                              "clocks": clk}), flush=True)
         return
 
-    # ---- end to end through the public API, host buffers ---------------------
-    # --e2e-packed: the factor kept on the host as packed upper triangles (its
-    # layout as a symmetric matrix), half the bytes over the host link
-    Lh = (jk.pack_factor(m.L) if args.e2e_packed else torch.from_numpy(m.L)).pin_memory()
-    Xh = [torch.from_numpy(x).pin_memory() for x in m.X]
-    Yh = [torch.from_numpy(y).pin_memory() for y in m.Y]
-    Jh = torch.empty((len(ks), n, n), dtype=torch.float64).pin_memory()
-    Kh = torch.empty((len(ks), n, n), dtype=torch.float64).pin_memory()
-    h2d = Lh.numel() * 8 + sum(x.numel() * 8 for x in Xh) + sum(y.numel() * 8 for y, s in zip(Yh, sym) if not s)
-    d2h = (Jh.numel() + Kh.numel()) * 8
-    e2e_steps = max(1, min(args.steps, 3))
-    eng.set_option("packed_factor", 0)      # the host builds take the factor from host memory
-    # jk_build_host: the library streams the factor to the device in aux chunks
-    # on its own copy stream, overlapped with the build of the previous chunk;
-    # densities up and J, K down on the caller's stream.  One untimed call sizes
-    # the arena.
-    eng.build_host(Lh, Xh, Yh, sym, prec, J=Jh, K=Kh, stream=st, packed=args.e2e_packed)
-    barrier(world)
-    torch.cuda.synchronize(dev)
-    e0.record(st)
-    for _ in range(e2e_steps):
-        eng.build_host(Lh, Xh, Yh, sym, prec, J=Jh, K=Kh, stream=st, sync=False, packed=args.e2e_packed)
-    e1.record(st)
-    torch.cuda.synchronize(dev)
-    eng.sync_status(st)
-    ms_e2e = max_over_ranks(e0.elapsed_time(e1) / e2e_steps, world, dev)
-    e2e = {"value": job_tflops(flops, ms_e2e, world), "unit": "TFLOP/s",
-           "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "ms_per_step": ms_e2e,
-           "packed_factor": bool(args.e2e_packed),
-           "path": "jk_build_host: pinned host inputs and outputs, factor streamed in aux chunks "
-                   "overlapped with the build"}
+    # ---- the FP64 engine on the same inputs --------------------------------
+    fp64 = None
+    Jf = Kf = None
+    if not args.no_fp64:
+        nwarm = max(1, naux // 10)
+        eng.build(Lfac[:nwarm], Xd, Yd, sym, "fp64")        # warm-up on the first tenth of the aux indices
+        torch.cuda.synchronize(dev)
+        Jf, Kf = torch.empty_like(J), torch.empty_like(K)
+        ms64 = timed(lambda: eng.build(Lfac, Xd, Yd, sym, "fp64", J=Jf, K=Kf), 1, 0, st)
+        eng.sync_status()
+        phase(f"FP64 engine: {ms64:.1f} ms per build")
+        fp64 = {"ms_per_step": ms64, "value": flops / (ms64 * 1e-3) / 1e12, "unit": "TFLOP/s",
+                "speedup_split_over_fp64": ms64 / ms_max, "steps": 1,
+                "how": "the plain FP64 engine (FP64 SIMT GEMMs, FP64 J kernels) on the same inputs: one timed "
+                       "build after a warm-up build on the first tenth of the aux indices"}
 
-    # ---- roofline of the dominant kernel ------------------------------------
+    # ---- errors: split vs FP64 engine (all entries), both vs the oracle ----
     peaks, peak_src = load_peaks()
-    top = max(prof.items(), key=lambda kv: kv[1][0]) if prof else ("none", (0.0, 0))
-    top_name, (top_ms, top_cnt) = top
-    roofline = None
-    if top_name == "dgemm_fp64" and top_cnt:
-        alg = panel_rank_flops(n, naux, ks, sym) * args.steps
-        achieved = alg / (top_ms * 1e-3) / 1e12
-        roofline = {"kernel": top_name, "bound": "alu", "achieved": achieved,
-                    "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-                    "peak_source": "FP64 FMA stream probe, 1.20 TFLOP/s (148 SM x 2 FMA/clk x 2032 MHz)",
-                    "traffic": None, "avg_launch_ms": top_ms / top_cnt,
-                    "share_of_step": top_ms / (ms * args.steps)}
-    elif top_name == "ozgemm_tcgen05" and top_cnt:
-        pk = peaks.get("bf16_tflops_sustained")
-        traffic = None
-        if args.case == "multi_state":
-            per_step = (OZ_PANEL_BYTES_PER_P + OZ_RANK_BYTES_PER_P) * naux
-            traffic = per_step * args.steps / top_cnt
-        achieved = issued / (top_ms * 1e-3) / 1e12 if issued else None
-        alg = panel_rank_flops(n, naux, ks, sym) * args.steps
-        roofline = {"kernel": top_name, "bound": "tensor", "achieved": achieved, "peak": pk,
-                    "unit": "TFLOP/s", "frac": (achieved / pk) if achieved else None,
-                    "peak_source": f"bf16_tflops_sustained of {peak_src} (MEASURED_PEAKS)",
-                    "achieved_counts": "dense BF16 MMA flops issued (21 slice pairs over padded tiles)",
-                    "algorithmic_fp64_equiv_tflops": alg / (top_ms * 1e-3) / 1e12,
-                    "traffic": traffic,
-                    "traffic_note": "DRAM bytes per launch, ncu capture of the profile case scaled by naux",
-                    "avg_launch_ms": top_ms / top_cnt,
-                    "share_of_step": top_ms / (ms * args.steps)}
+    error = None
+    if rank == 0 and not args.no_oracle and fp64 is not None:
+        import oracle
+        Lh = torch.from_numpy(Lhost) if Lhost is not None else torch.empty(Ld.shape, dtype=Ld.dtype).copy_(Ld)
+        s, mu, nu = sample_entries(np.random.default_rng(2), len(ks), n, args.samples)
+        t0 = time.perf_counter()
+        Jo, Ko = oracle.sample(Lh.numpy(), m.X, m.Y, s, mu, nu)
+        t_or = time.perf_counter() - t0
+        del Lh
+        phase(f"oracle samples: {t_or:.1f} s")
+        Jn, Kn, Jfn, Kfn = (t.cpu().numpy() for t in (J, K, Jf, Kf))
+        err = {
+            "split_vs_fp64_J": float(np.abs(Jn - Jfn).max()), "split_vs_fp64_K": float(np.abs(Kn - Kfn).max()),
+            "split_vs_oracle_J": float(np.abs(Jn[s, mu, nu] - Jo).max()),
+            "split_vs_oracle_K": float(np.abs(Kn[s, mu, nu] - Ko).max()),
+            "fp64_vs_oracle_J": float(np.abs(Jfn[s, mu, nu] - Jo).max()),
+            "fp64_vs_oracle_K": float(np.abs(Kfn[s, mu, nu] - Ko).max()),
+            "max_abs_J": float(np.abs(Jfn).max()), "max_abs_K": float(np.abs(Kfn).max())}
+        gate_j = max(SPLIT_GATE, err["fp64_vs_oracle_J"])
+        gate_k = max(SPLIT_GATE, err["fp64_vs_oracle_K"])
+        error = dict(err, samples=int(args.samples), oracle_seconds=t_or,
+                     split_gate_abs=SPLIT_GATE, fp64_gate_rel=FP64_GATE,
+                     split_within_gate=bool(err["split_vs_oracle_J"] <= gate_j and
+                                            err["split_vs_oracle_K"] <= gate_k),
+                     fp64_within_gate=bool(err["fp64_vs_oracle_J"] <= FP64_GATE * err["max_abs_J"] and
+                                           err["fp64_vs_oracle_K"] <= FP64_GATE * err["max_abs_K"]),
+                     how="max |error| over all entries (split vs the FP64 engine) and over sampled entries "
+                         "(both engines vs the CPU oracle, long-double accumulation)")
+
+    # ---- end to end through the public API, host buffers -------------------
+    # the oracle's CPU baseline below takes the first aux indices of the factor
+    Lcpu = np.ascontiguousarray(Lhost[:CPU_SAMPLE[case][1]]) if Lhost is not None else \
+        Ld[:CPU_SAMPLE[case][1]].cpu().numpy()
+    e2e = None
+    if not args.no_e2e:
+        packed_link = args.e2e_link == "packed"
+        src = jk.pack_factor(Ld) if packed_link else Ld          # packed on the device: half the upload
+        Lup = torch.empty(src.shape, dtype=src.dtype, pin_memory=True)
+        Lup.copy_(src)
+        del src
+        Xh = [torch.from_numpy(x).pin_memory() for x in m.X]
+        Yh = [torch.from_numpy(y).pin_memory() for y in m.Y]
+        Jh = torch.empty((len(ks), n, n), dtype=torch.float64).pin_memory()
+        Kh = torch.empty((len(ks), n, n), dtype=torch.float64).pin_memory()
+        h2d = Lup.numel() * 8 + sum(x.numel() * 8 for x in Xh) + sum(y.numel() * 8 for y, s in zip(Yh, sym) if not s)
+        d2h = (Jh.numel() + Kh.numel()) * 8
+        e2e_steps = max(1, min(args.steps, 3))
+        eng.set_option("packed_factor", 0)      # the host builds take the factor from host memory
+        eng.build_host(Lup, Xh, Yh, sym, "split", J=Jh, K=Kh, stream=st, packed=packed_link)
+        barrier(world)
+        ms_e2e = timed(lambda: eng.build_host(Lup, Xh, Yh, sym, "split", J=Jh, K=Kh, stream=st, sync=False,
+                                              packed=packed_link), e2e_steps, 0, st)
+        eng.sync_status(st)
+        ms_e2e = max_over_ranks(ms_e2e, world, dev)
+        phase(f"end to end: {ms_e2e:.1f} ms per build")
+        e2e = {"value": job_tflops(flops, ms_e2e, world), "unit": "TFLOP/s",
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "ms_per_step": ms_e2e,
+               "steps": e2e_steps, "packed_factor": packed_link,
+               "path": ("jk_build_host_packed" if packed_link else "jk_build_host") +
+                       ": pinned host inputs and outputs, the factor streamed in aux chunks on the library's copy "
+                       "stream, overlapped with the chunk builds; J, K read back"}
+        del Lup
+
+    # ---- rooflines ----------------------------------------------------------
+    fp64_tf = fp64_peak(eng, st)
+    roofline = gemm_roofline(prof, panel_rank_flops(n, naux, ks, sym), issued, args.steps, peaks, peak_src)
+    jstream = jstream_roofline(prof, n, naux, len(ks), args.steps, peaks, fp64_tf)
+    if fp64 is not None:
+        fp64["fp64_pipe_peak_tflops"] = fp64_tf
+        fp64["fp64_pipe_frac"] = fp64["value"] / fp64_tf
+
+    del Ld, Lfac, Xd, Yd, J, K, Jf, Kf
+    eng.close()
+    torch.cuda.empty_cache()
+
+    configs = None
+    if not args.headline_only and case == "large_single":
+        configs = other_configs(dev, st)
 
     if rank != 0:
         return
-    cpu = cpu_baseline_sample(m.L)
+    cpu = cpu_baseline_sample(case, Lcpu)
+    phase("cpu baseline measured")
     line = {
         "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if prec == "fp64" else "bf16-slices/fp32-tmem/int64 -> f64",
-        "data": "synthetic",
-        "config": {"workload": WORKLOAD, "engine": prec, "nbf": n, "naux": naux, "nd": len(ks),
-                   "k": ks[0], "l2": "inputs larger than L2 (L = 3.07 GB FP64), no flush",
+        "dtype": "bf16-slices/fp32-tmem/int64 -> f64",
+        "data": "synthetic (seeded; the paper's molecules stand in)",
+        "config": {"workload": WORKLOADS[case], "engine": "split", "nbf": n, "naux": naux, "nd": len(ks),
+                   "k": ks[0], "l2": "inputs larger than L2 (factor %.1f GB FP64), no flush" % (8e-9 * n * n * naux),
                    "parallelism": f"replicas x{world}", "tuned": tuned, "slicer": args.slicer,
                    "syrk": args.syrk, "packed_factor": bool(args.packed_factor)},
         "e2e": e2e,
         "gpu_launches": int(launches),
         "launches_per_step": launches / args.steps,
-        "kernels_ms": {k: v[0] / args.steps for k, v in prof.items()},
+        "kernels_ms": kernels_ms,
+        "fp64_gpu": fp64,
+        "error": error,
         "roofline": roofline,
+        "j_stream": jstream,
         "cpu_baseline": {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")},
         "clocks": clk,
+        "configs": configs,
     }
     print(json.dumps(line), flush=True)
 
 
-def adjoint_flops(n, naux, ks, sym):
-    """Algorithmic flops of the adjoint: 12 n^2 k naux (dX, dY with the panels
-    recomputed) + 4 n^2 k naux (dL outer products) + 4 n^2 naux (J terms) per
-    density."""
-    return sum(12.0 * n * n * k * naux + 4.0 * n * n * k * naux + 4.0 * n * n * naux for k in ks)
+# ---------------------------------------------------------------------------
+# The other workloads, reported beside the headline (same JSON line)
+# ---------------------------------------------------------------------------
+def measure_small(dev, st, reps=200):
+    """One molecule small: latency-bound; microseconds per build, both engines."""
+    import torch
+    from paper_2608_06536_b300 import inputs, jk
+    m = inputs.one_molecule_small()
+    L = torch.from_numpy(m.L).to(dev)
+    X = [torch.from_numpy(x).to(dev) for x in m.X]
+    Y = [torch.from_numpy(y).to(dev) for y in m.Y]
+    eng = jk.Engine(dev)
+    out = {"workload": WORKLOADS["small"]}
+    for prec in ("split", "fp64"):
+        J, K = eng.build(L, X, Y, m.sym, prec)
+        l0 = eng.launch_count()
+        ms = timed(lambda: eng.build(L, X, Y, m.sym, prec, J=J, K=K), reps, 10, st)
+        nl = (eng.launch_count() - l0) / (reps + 10)
+        eng.sync_status()
+        out[prec] = {"us_per_build": ms * 1e3, "launches_per_build": nl,
+                     "value": build_flops(m.n, m.naux, m.ks, m.sym) / (ms * 1e-3) / 1e12}
+    eng.close()
+    return out
 
 
-def dense_flops(n, naux, nd):
-    """Algorithmic flops of jk_build_dense (J and K) for nd dense densities:
-    K 2n^3 naux for the panels L^P D and 2n^3 naux for the rank update, J
-    2n^2 naux for the metric dot and 2n^2 naux for the back-contraction."""
-    return nd * (4.0 * n ** 3 * naux + 4.0 * n * n * naux)
+def measure_multi_state(dev, st, steps=5, warmup=2):
+    """Multi-state workload, both engines (FP64: one timed build)."""
+    import torch
+    from paper_2608_06536_b300 import inputs, jk
+    m = inputs.multi_state()
+    L = torch.from_numpy(m.L).to(dev)
+    X = [torch.from_numpy(x).to(dev) for x in m.X]
+    Y = [torch.from_numpy(y).to(dev) for y in m.Y]
+    eng = jk.Engine(dev)
+    fl = build_flops(m.n, m.naux, m.ks, m.sym)
+    out = {"workload": WORKLOADS["multi_state"]}
+    for prec, (s_, w_) in (("split", (steps, warmup)), ("fp64", (1, 1))):
+        J, K = eng.build(L, X, Y, m.sym, prec)
+        ms = timed(lambda: eng.build(L, X, Y, m.sym, prec, J=J, K=K), s_, w_, st)
+        eng.sync_status()
+        out[prec] = {"ms_per_step": ms, "value": fl / (ms * 1e-3) / 1e12, "steps": s_}
+    out["speedup_split_over_fp64"] = out["fp64"]["ms_per_step"] / out["split"]["ms_per_step"]
+    eng.close()
+    return out
 
 
-def pair_flops(n, naux, kl, syml, kr, symr):
-    """Algorithmic flops of jk_pair with both pairings: the right densities'
-    build plus, per map and right density, U_b = M_b Z_L (2 n^2 ctot_L) and the
-    pair dots (2 n k_a per pair)."""
-    ctot_l = sum(k if s else 2 * k for k, s in zip(kl, syml))
-    contract = 2 * len(kr) * (2.0 * n * n * ctot_l + sum(2.0 * n * k for k in kl))
-    return build_flops(n, naux, kr, symr) + contract
+def measure_adjoint(dev, st, steps=2, warmup=1):
+    """Adjoint case: dX, dY and the symmetrized dL, split and FP64 engines."""
+    import numpy as np
+    import torch
+    from paper_2608_06536_b300 import inputs, jk
+    m, W, V = inputs.adjoint_case(with_factor=False)
+    L = inputs.factor_device(m.n, m.naux, m.tau, m.seed, device=dev)
+    X = [torch.from_numpy(x).to(dev) for x in m.X]
+    Y = [torch.from_numpy(y).to(dev) for y in m.Y]
+    Wd = torch.tensor(np.array(W), device=dev)
+    Vd = torch.tensor(np.array(V), device=dev)
+    eng = jk.Engine(dev)
+    fl = adjoint_flops(m.n, m.naux, m.ks, m.sym)
+    out = {"workload": "adjoint: nbf=600 naux=3600, 8 non-symmetric densities k=60, W, V N(0,1); dX, dY and the "
+                       "symmetrized dL", "algorithmic_flop": fl}
+    for prec, (s_, w_) in (("split", (steps, warmup)), ("fp64", (1, 1))):
+        ms = timed(lambda: eng.adjoint(L, X, Y, m.sym, Wd, Vd, precision=prec), s_, w_, st)
+        eng.sync_status()
+        out[prec] = {"ms_per_step": ms, "value": fl / (ms * 1e-3) / 1e12, "steps": s_}
+    out["speedup_split_over_fp64"] = out["fp64"]["ms_per_step"] / out["split"]["ms_per_step"]
+    eng.close()
+    del L
+    torch.cuda.empty_cache()
+    return out
 
 
+def measure_batched(dev, st, steps=2, warmup=1):
+    """Uneven batch: one batched split build of 64 molecules, captured in a
+    CUDA graph and replayed; launches counted at capture."""
+    import torch
+    from paper_2608_06536_b300 import inputs, jk
+    mols = inputs.uneven_batch(with_factor=False)
+    eng = jk.Engine(dev)
+    args_b = [(inputs.factor_device(mm.n, mm.naux, mm.tau, mm.seed, device=dev),
+               [torch.from_numpy(x).to(dev) for x in mm.X], [torch.from_numpy(y).to(dev) for y in mm.Y], mm.sym)
+              for mm in mols]
+    flops = sum(build_flops(mm.n, mm.naux, mm.ks, mm.sym) for mm in mols)
+    eng.build_batched(args_b, "split")
+    torch.cuda.synchronize(dev)
+    g = torch.cuda.CUDAGraph()
+    cs = torch.cuda.Stream(dev)
+    cs.wait_stream(st)
+    l0 = eng.launch_count()
+    with torch.cuda.stream(cs):
+        with torch.cuda.graph(g, stream=cs):
+            eng.build_batched(args_b, "split", stream=cs)
+    captured = eng.launch_count() - l0
+    st.wait_stream(cs)
+    ms = timed(g.replay, steps, warmup, st)
+    eng.sync_status()
+    out = {"workload": "uneven batch: 64 molecules nbf U{100..600}, naux 6 nbf, 560 non-symmetric densities "
+                       "k = nbf/10 (208 GB of factors), one batched split build replayed as a CUDA graph",
+           "ms_per_step": ms, "value": flops / (ms * 1e-3) / 1e12, "unit": "TFLOP/s (algorithmic)",
+           "launches_per_build": captured, "steps": steps}
+    eng.close()
+    del args_b, g
+    torch.cuda.empty_cache()
+    return out
+
+
+def other_configs(dev, st):
+    out = {}
+    for name, fn in (("one_molecule_small", measure_small), ("multi_state", measure_multi_state),
+                     ("adjoint", measure_adjoint), ("uneven_batch", measure_batched)):
+        t0 = time.perf_counter()
+        try:
+            out[name] = fn(dev, st)
+            phase(f"{name} measured")
+        except Exception as e:          # reported, never silently dropped
+            out[name] = {"error": f"{type(e).__name__}: {e}"}
+        out[name]["wall_s"] = time.perf_counter() - t0
+    return out
+
+
+# ---------------------------------------------------------------------------
+# Single extra cases (bench.py --case ...), one JSON line each
+# ---------------------------------------------------------------------------
 PAIR_WORKLOAD = ("bra-ket pairings: nbf=400 naux=2400 tau=400, 8 left x 8 right non-symmetric densities k=40; "
                  "jk_pair Jp and Kp")
 LAPLACE_WORKLOAD = ("Laplace (LT-AO) builds: nbf=400 naux=2400 tau=400, 8 Gauss-Laguerre points, m=40 occupied "
                     "against virtual coefficient columns; jk_build_laplace weighted J and K")
-
 DENSE_WORKLOAD = ("dense densities: nbf=400 naux=2400 tau=400, 8 general non-symmetric D_s "
                   "(N(0, 1/nbf^2) entries); jk_build_dense J and K, and jk_density_grad K(W) + J(V)")
 
 
 def run_extra_case(args, rank, local):
-    """Reported beside the headline workload (not the bench contract's line):
-    the adjoint case, the uneven batch replayed as a CUDA graph, and the dense
-    densities."""
     import numpy as np
     import torch
     from paper_2608_06536_b300 import inputs, jk
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    eng = jk.Engine(dev)
     st = torch.cuda.current_stream(dev)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    out = {"case": args.case, "engine": args.precision}
     if args.case == "adjoint":
-        m, W, V = inputs.adjoint_case(with_factor=False)
-        L = inputs.factor_device(m.n, m.naux, m.tau, m.seed, device=dev)
-        X = [torch.from_numpy(x).to(dev) for x in m.X]
-        Y = [torch.from_numpy(y).to(dev) for y in m.Y]
-        Wd = torch.tensor(np.array(W), device=dev)
-        Vd = torch.tensor(np.array(V), device=dev)
-        for _ in range(args.warmup):
-            eng.adjoint(L, X, Y, m.sym, Wd, Vd, precision=args.precision)
-        torch.cuda.synchronize(dev)
-        e0.record(st)
-        for _ in range(args.steps):
-            eng.adjoint(L, X, Y, m.sym, Wd, Vd, precision=args.precision)
-        e1.record(st)
-        torch.cuda.synchronize(dev)
-        eng.sync_status()
-        ms = e0.elapsed_time(e1) / args.steps
-        out.update({"workload": "adjoint nbf=600 naux=3600, 8 non-symmetric densities k=60, W,V N(0,1); "
-                                "dX, dY and the symmetrized dL",
-                    "ms_per_step": ms, "value": adjoint_flops(m.n, m.naux, m.ks, m.sym) / (ms * 1e-3) / 1e12,
-                    "unit": "TFLOP/s (algorithmic)"})
+        out = measure_adjoint(dev, st, args.steps, args.warmup)
+    elif args.case == "batched":
+        out = measure_batched(dev, st, args.steps, args.warmup)
     elif args.case == "dense":
+        eng = jk.Engine(dev)
         n, naux, nd = 400, 2400, 8
         L = inputs.factor_device(n, naux, 400.0, 0, device=dev)
         D = torch.from_numpy(inputs.dense_densities(n, nd, seed=0)).to(dev)
         W = torch.from_numpy(inputs.dense_densities(n, nd, seed=1)).to(dev)
-        res = {}
+        out = {"workload": DENSE_WORKLOAD, "unit": "TFLOP/s (algorithmic)"}
         for name, call in (("build_dense", lambda: eng.build_dense(L, D, args.precision)),
                            ("density_grad", lambda: eng.density_grad(L, W, D, args.precision))):
-            for _ in range(args.warmup):
-                call()
-            torch.cuda.synchronize(dev)
-            e0.record(st)
-            for _ in range(args.steps):
-                call()
-            e1.record(st)
-            torch.cuda.synchronize(dev)
+            ms = timed(call, args.steps, args.warmup, st)
             eng.sync_status()
-            ms = e0.elapsed_time(e1) / args.steps
-            res[name] = {"ms_per_step": ms, "value": dense_flops(n, naux, nd) / (ms * 1e-3) / 1e12}
-        out.update({"workload": DENSE_WORKLOAD, "unit": "TFLOP/s (algorithmic)", **res})
-    elif args.case in ("pairs", "laplace"):
+            out[name] = {"ms_per_step": ms, "value": dense_flops(n, naux, nd) / (ms * 1e-3) / 1e12}
+    else:
+        eng = jk.Engine(dev)
         n, naux, k, nq = 400, 2400, 40, 8
         L = inputs.factor_device(n, naux, 400.0, 0, device=dev)
         left = inputs.custom_densities(n, [k] * 8, seed=1)
@@ -488,53 +774,11 @@ def run_extra_case(args, rank, local):
             ea = torch.from_numpy(np.sort(rng.uniform(0.2, 2.0, k))).to(dev)
             call = lambda: eng.build_laplace(L, XL[0], ei, +1, alpha, w, YL[0], ea, -1, args.precision)
             flops, workload = build_flops(n, naux, [k] * nq, [False] * nq), LAPLACE_WORKLOAD
-        for _ in range(args.warmup):
-            call()
-        torch.cuda.synchronize(dev)
-        e0.record(st)
-        for _ in range(args.steps):
-            call()
-        e1.record(st)
-        torch.cuda.synchronize(dev)
+        ms = timed(call, args.steps, args.warmup, st)
         eng.sync_status()
-        ms = e0.elapsed_time(e1) / args.steps
-        out.update({"workload": workload, "ms_per_step": ms, "value": flops / (ms * 1e-3) / 1e12,
-                    "unit": "TFLOP/s (algorithmic)"})
-    else:
-        mols = inputs.uneven_batch(with_factor=False)
-
-        def factor(mm):
-            Lf = inputs.factor_device(mm.n, mm.naux, mm.tau, mm.seed, device=dev)
-            return jk.pack_factor(Lf) if args.packed_factor else Lf      # packed: 104 GB instead of 208 GB
-
-        eng.set_option("packed_factor", 1 if args.packed_factor else 0)
-        eng.set_option("syrk", args.syrk)
-        args_b = [(factor(mm), [torch.from_numpy(x).to(dev) for x in mm.X], [torch.from_numpy(y).to(dev) for y in mm.Y],
-                   mm.sym) for mm in mols]
-        flops = sum(build_flops(mm.n, mm.naux, mm.ks, mm.sym) for mm in mols)
-        eng.build_batched(args_b, args.precision)
-        torch.cuda.synchronize(dev)
-        g = torch.cuda.CUDAGraph()
-        cs = torch.cuda.Stream(dev)
-        cs.wait_stream(st)
-        with torch.cuda.stream(cs):
-            with torch.cuda.graph(g, stream=cs):
-                eng.build_batched(args_b, args.precision, stream=cs)
-        st.wait_stream(cs)
-        for _ in range(args.warmup):
-            g.replay()
-        torch.cuda.synchronize(dev)
-        e0.record(st)
-        for _ in range(args.steps):
-            g.replay()
-        e1.record(st)
-        torch.cuda.synchronize(dev)
-        eng.sync_status()
-        ms = e0.elapsed_time(e1) / args.steps
-        out.update({"workload": "uneven batch: 64 molecules nbf U{100..600}, naux 6 nbf, 560 non-symmetric "
-                                "densities k = nbf/10 (208 GB of factors), one batched build replayed as a CUDA graph",
-                    "ms_per_step": ms, "value": flops / (ms * 1e-3) / 1e12, "unit": "TFLOP/s (algorithmic)",
-                    "packed_factor": bool(args.packed_factor)})
+        out = {"workload": workload, "ms_per_step": ms, "value": flops / (ms * 1e-3) / 1e12,
+               "unit": "TFLOP/s (algorithmic)"}
+    out = {"case": args.case, "engine": args.precision, **out}
     if rank == 0:
         print(json.dumps(out), flush=True)
 
@@ -545,28 +789,33 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", choices=["split", "fp64"], default="split")
-    ap.add_argument("--case", choices=["multi_state", "profile", "adjoint", "batched", "dense", "pairs", "laplace"],
-                    default="multi_state",
-                    help="profile: nbf=400, naux=600 variant for ncu captures; adjoint, batched, dense, pairs, "
-                         "laplace: extra reported cases")
+    ap.add_argument("--precision", choices=["split", "fp64"], default="split",
+                    help="engine of the single extra cases (the headline times both)")
+    ap.add_argument("--case", default="large_single",
+                    choices=["large_single", "multi_state", "small", "profile", "adjoint", "batched", "dense",
+                             "pairs", "laplace"],
+                    help="large_single: the headline workload; multi_state, small: the other build workloads in "
+                         "the headline's form; profile: the large single molecule with naux=400 for ncu captures; "
+                         "adjoint, batched, dense, pairs, laplace: single extra cases")
     ap.add_argument("--no-tune", dest="tune", action="store_false",
                     help="skip the autotuner (default configuration)")
     ap.add_argument("--config", default="",
                     help="fixed run-time configuration aux_chunk,schedule,raster (skips the autotuner)")
     ap.add_argument("--slicer", type=int, choices=[0, 1], default=0,
-                    help="digit extraction of the vector slicer: 0 integer (default), 1 FP32 additions")
+                    help="digit extraction of the vector slicer: 0 integer, 1 FP32 additions")
     ap.add_argument("--syrk", type=int, choices=[0, 1], default=0,
-                    help="symmetric densities (split engine): 0 full rank update (default), "
-                         "1 blocked symmetric rank update, the rest mirrored")
+                    help="symmetric densities: 0 full rank update, 1 blocked symmetric rank update")
     ap.add_argument("--packed-factor", dest="packed_factor", action="store_true",
-                    help="device factor stored as packed upper triangles (half the memory; chunks expanded "
-                         "in the workspace)")
-    ap.add_argument("--e2e-packed", dest="e2e_packed", action="store_true",
-                    help="end-to-end leg with the factor on the host as packed upper triangles "
-                         "(jk_build_host_packed: half the bytes over the host link)")
-    ap.add_argument("--quick", action="store_true",
-                    help="device-resident timing only (no e2e, no CPU baseline)")
+                    help="device factor stored as packed upper triangles (half the memory)")
+    ap.add_argument("--e2e-link", dest="e2e_link", choices=["packed", "full"], default="packed",
+                    help="end-to-end leg: packed (jk_build_host_packed, the factor's upper triangles: half the "
+                         "bytes over the host link; default) or full (jk_build_host)")
+    ap.add_argument("--quick", action="store_true", help="device-resident timing only")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 engine (and the error comparison)")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg")
+    ap.add_argument("--no-oracle", action="store_true", help="skip the oracle's sampled entries")
+    ap.add_argument("--samples", type=int, default=24, help="oracle-sampled entries of the error check")
+    ap.add_argument("--headline-only", action="store_true", help="skip the other workloads")
     args = ap.parse_args()
     rank, world, local = dist_init()
     if args.impl == "reference":

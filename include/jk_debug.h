@@ -32,6 +32,17 @@ size_t jk_debug_sliced_gemm_workspace(int32_t M, int32_t N, int32_t K);
  * Nothing faults or hangs. */
 jk_status jk_debug_wait_timeout(jk_handle h, void *stream);
 
+/* Measures the device's FP64 FMA throughput, the ceiling of the plain FP64
+ * engine and of the FP64 J kernels: one launch of blocks_per_sm x SMs blocks
+ * of 256 threads, each thread running eight independent FMA chains for
+ * `iters` steps (no memory traffic inside the loop).  *flops receives the
+ * FP64 flops the launch performs (2 per FMA); time the launch on `stream`
+ * with CUDA events.  sink: one device double the kernel may write (keeps the
+ * chains live).  JK_ERR_ARG for a NULL handle, sink or flops pointer, or
+ * blocks_per_sm or iters outside [1, 64] / [1, 2^24]. */
+jk_status jk_debug_fp64_fma(jk_handle h, int32_t blocks_per_sm, int32_t iters, double *sink, double *flops,
+                            void *stream);
+
 #ifdef __cplusplus
 }
 #endif

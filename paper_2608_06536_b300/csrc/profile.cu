@@ -44,6 +44,24 @@ static void drain(jk_ctx *h) {
     p.used = 0;
 }
 
+// Eight independent FMA chains per thread: the FP64 pipe's issue rate with
+// no memory traffic.  The result is stored only if it equals a value the
+// chains cannot reach, which keeps them live without a store per thread.
+__global__ void __launch_bounds__(256) fma_stream_kernel(int iters, double *sink) {
+    double a[8];
+#pragma unroll
+    for (int j = 0; j < 8; j++) a[j] = 1.0 + 1e-3 * (threadIdx.x + j);
+    const double b = 0.999999, c = 1e-7;
+    for (int i = 0; i < iters; i++) {
+#pragma unroll
+        for (int j = 0; j < 8; j++) a[j] = fma(a[j], b, c);
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int j = 0; j < 8; j++) s += a[j];
+    if (s == -1.0) *sink = s;
+}
+
 }  // namespace jk
 
 using namespace jk;
@@ -80,6 +98,22 @@ jk_status jk_profile_read(jk_handle h, int32_t kind, double *ms, int64_t *launch
     drain(h);
     if (ms) *ms = h->prof.ms[kind];
     if (launches) *launches = h->prof.cnt[kind];
+    return JK_OK;
+}
+
+jk_status jk_debug_fp64_fma(jk_handle h, int32_t blocks_per_sm, int32_t iters, double *sink, double *flops,
+                            void *stream) {
+    if (!h || !sink || !flops) return JK_ERR_ARG;
+    if (blocks_per_sm < 1 || blocks_per_sm > 64 || iters < 1 || iters > (1 << 24))
+        return set_error(h, JK_ERR_ARG, "blocks_per_sm must be in [1, 64] and iters in [1, 2^24]");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int grid = blocks_per_sm * h->num_sms;
+    {
+        LaunchScope ls(h, KK_MISC, st);
+        fma_stream_kernel<<<grid, 256, 0, st>>>(iters, sink);
+    }
+    JK_LAUNCH_CHECK(h);
+    *flops = 2.0 * 8.0 * static_cast<double>(iters) * grid * 256.0;
     return JK_OK;
 }
 

@@ -134,6 +134,8 @@ def load_library(path: str = LIB_PATH):
         L.jk_issued_tensor_flops.restype = ct.c_double
         for f in (L.jk_profile_enable, L.jk_profile_reset, L.jk_profile_read):
             f.restype = ct.c_int
+        L.jk_debug_fp64_fma.argtypes = [vp, ct.c_int32, ct.c_int32, vp, ct.POINTER(ct.c_double), vp]
+        L.jk_debug_fp64_fma.restype = ct.c_int
         for f in (L.jk_create, L.jk_destroy, L.jk_workspace_query, L.jk_build,
                   L.jk_build_batched, L.jk_adjoint, L.jk_sync_status):
             f.restype = ct.c_int
@@ -408,6 +410,19 @@ class Engine:
         return out
 
     # -- queries -------------------------------------------------------------
+    def fp64_fma_probe(self, blocks_per_sm: int = 8, iters: int = 1 << 16, stream=None) -> float:
+        """Launch the library's FP64 FMA-rate kernel on `stream` (the current
+        stream by default) and return the FP64 flops it performs; time it with
+        CUDA events on that stream."""
+        self._ensure(1 << 20)
+        if getattr(self, "_sink", None) is None:
+            self._sink = torch.zeros(1, dtype=torch.float64, device=self.device)
+        flops = ct.c_double()
+        st = self.lib.jk_debug_fp64_fma(self._h, int(blocks_per_sm), int(iters), ct.c_void_p(self._sink.data_ptr()),
+                                        ct.byref(flops), _stream_ptr(stream))
+        self._check(st, self._h)
+        return flops.value
+
     def query(self, op, factors, dens_c, nd_per_mol, nd, precision) -> int:
         """Arena bytes for a call under this handle's options and tuned configs."""
         if not self._h:

@@ -3,6 +3,7 @@ algorithmic flop model of the metric, the peaks it divides by, and the
 device-side factor generator's properties (run on the CPU)."""
 import json
 import math
+import os
 
 import numpy as np
 import pytest
@@ -99,3 +100,39 @@ def test_custom_densities_recipe():
         x, y = inputs.transition_density(30, k, s, seed=2)
         np.testing.assert_array_equal(X[s], x)
         np.testing.assert_array_equal(Y[s], y)
+
+
+def test_jstream_model():
+    # the upper triangle of each L^P read once, J written once; one FMA per
+    # upper-triangle entry, aux index and density
+    n, A, nd = 1000, 5000, 16
+    by, fl = bench.jstream_bytes_flops(n, A, nd)
+    tri = n * (n + 1) // 2
+    assert by == 8 * tri * A + 8 * nd * n * n and fl == 2 * tri * A * nd
+
+
+def test_kernel_source_hash_tracks_the_sources(tmp_path, monkeypatch):
+    """ncu figures are reported only for the kernel sources they were taken
+    on: the hash changes with any byte of those sources."""
+    import shutil
+    src = tmp_path / "paper_2608_06536_b300" / "csrc"
+    src.mkdir(parents=True)
+    for name in bench.KERNEL_SOURCES:
+        shutil.copy(os.path.join(bench.ROOT, "paper_2608_06536_b300", "csrc", name), src / name)
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    h0 = bench.kernel_source_hash()
+    with open(src / "tc.cuh", "a") as f:
+        f.write("\n")
+    assert bench.kernel_source_hash() != h0
+
+
+def test_headline_sample_entries_cover_the_corners():
+    s, mu, nu = bench.sample_entries(np.random.default_rng(0), 16, 1000, 24)
+    assert (s[0], mu[0], nu[0]) == (0, 0, 999) and (s[1], mu[1], nu[1]) == (15, 999, 0)
+    assert s.max() < 16 and mu.max() < 1000 and nu.max() < 1000
+
+
+def test_cpu_sample_is_a_named_exact_subset():
+    for case, (nds, na) in bench.CPU_SAMPLE.items():
+        m = bench.cpu_sample_molecule(case)
+        assert 1 <= nds <= m.nd and 1 <= na <= m.naux
