@@ -325,15 +325,15 @@ def timed(fn, steps, warmup, stream):
 
 
 def fp64_peak(eng, stream):
-    """FP64 TFLOP/s of the library's FMA-stream probe (best of three launches)."""
+    """FP64 TFLOP/s of the library's FMA-stream probe (best of five launches)."""
     import torch
     eng.fp64_fma_probe(stream=stream)
     torch.cuda.synchronize()
     best = 0.0
-    for _ in range(3):
+    for _ in range(5):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        fl = eng.fp64_fma_probe(blocks_per_sm=8, iters=1 << 16, stream=stream)
+        fl = eng.fp64_fma_probe(blocks_per_sm=4, iters=1 << 15, stream=stream)
         e1.record(stream)
         torch.cuda.synchronize()
         best = max(best, fl / (e0.elapsed_time(e1) * 1e-3) / 1e12)
@@ -635,7 +635,8 @@ def measure_multi_state(dev, st, steps=5, warmup=2):
     Y = [torch.from_numpy(y).to(dev) for y in m.Y]
     eng = jk.Engine(dev)
     fl = build_flops(m.n, m.naux, m.ks, m.sym)
-    out = {"workload": WORKLOADS["multi_state"]}
+    cfg, _ = eng.autotune(L, X, Y, m.sym, "split", reps=1)
+    out = {"workload": WORKLOADS["multi_state"], "tuned": cfg}
     for prec, (s_, w_) in (("split", (steps, warmup)), ("fp64", (1, 1))):
         J, K = eng.build(L, X, Y, m.sym, prec)
         ms = timed(lambda: eng.build(L, X, Y, m.sym, prec, J=J, K=K), s_, w_, st)

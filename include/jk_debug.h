@@ -34,7 +34,7 @@ jk_status jk_debug_wait_timeout(jk_handle h, void *stream);
 
 /* Measures the device's FP64 FMA throughput, the ceiling of the plain FP64
  * engine and of the FP64 J kernels: one launch of blocks_per_sm x SMs blocks
- * of 256 threads, each thread running eight independent FMA chains for
+ * of 256 threads, each thread running sixteen independent FMA chains for
  * `iters` steps (no memory traffic inside the loop).  *flops receives the
  * FP64 flops the launch performs (2 per FMA); time the launch on `stream`
  * with CUDA events.  sink: one device double the kernel may write (keeps the
