@@ -431,7 +431,7 @@ def run_ours(args, rank, world, local):
     # this shape (untimed; the cached pick is used by every build below)
     tuned = None
     if args.config:
-        for name, v in zip(("aux_chunk", "schedule", "raster"), args.config.split(",")):
+        for name, v in zip(("aux_chunk", "schedule", "raster", "tile"), args.config.split(",")):
             eng.set_option(name, int(v))
         tuned = {"fixed": args.config}
     elif args.tune:
@@ -647,8 +647,9 @@ def measure_multi_state(dev, st, steps=5, warmup=2):
     return out
 
 
-def measure_adjoint(dev, st, steps=2, warmup=1):
-    """Adjoint case: dX, dY and the symmetrized dL, split and FP64 engines."""
+def measure_adjoint(dev, st, steps=2, warmup=1, slices=7):
+    """Adjoint case: dX, dY and the symmetrized dL, split (7 slices per
+    operand unless `slices` says 6) and FP64 engines."""
     import numpy as np
     import torch
     from paper_2608_06536_b300 import inputs, jk
@@ -659,9 +660,10 @@ def measure_adjoint(dev, st, steps=2, warmup=1):
     Wd = torch.tensor(np.array(W), device=dev)
     Vd = torch.tensor(np.array(V), device=dev)
     eng = jk.Engine(dev)
+    eng.set_option("adjoint_slices", slices)
     fl = adjoint_flops(m.n, m.naux, m.ks, m.sym)
     out = {"workload": "adjoint: nbf=600 naux=3600, 8 non-symmetric densities k=60, W, V N(0,1); dX, dY and the "
-                       "symmetrized dL", "algorithmic_flop": fl}
+                       "symmetrized dL", "algorithmic_flop": fl, "split_slices": slices}
     for prec, (s_, w_) in (("split", (steps, warmup)), ("fp64", (1, 1))):
         ms = timed(lambda: eng.adjoint(L, X, Y, m.sym, Wd, Vd, precision=prec), s_, w_, st)
         eng.sync_status()
@@ -741,7 +743,7 @@ def run_extra_case(args, rank, local):
     dev = torch.device("cuda", local)
     st = torch.cuda.current_stream(dev)
     if args.case == "adjoint":
-        out = measure_adjoint(dev, st, args.steps, args.warmup)
+        out = measure_adjoint(dev, st, args.steps, args.warmup, args.adjoint_slices)
     elif args.case == "batched":
         out = measure_batched(dev, st, args.steps, args.warmup)
     elif args.case == "dense":
@@ -801,7 +803,7 @@ def main():
     ap.add_argument("--no-tune", dest="tune", action="store_false",
                     help="skip the autotuner (default configuration)")
     ap.add_argument("--config", default="",
-                    help="fixed run-time configuration aux_chunk,schedule,raster (skips the autotuner)")
+                    help="fixed run-time configuration aux_chunk,schedule,raster[,tile] (skips the autotuner)")
     ap.add_argument("--slicer", type=int, choices=[0, 1], default=0,
                     help="digit extraction of the vector slicer: 0 integer, 1 FP32 additions")
     ap.add_argument("--syrk", type=int, choices=[0, 1], default=0,
@@ -817,6 +819,8 @@ def main():
     ap.add_argument("--no-oracle", action="store_true", help="skip the oracle's sampled entries")
     ap.add_argument("--samples", type=int, default=24, help="oracle-sampled entries of the error check")
     ap.add_argument("--headline-only", action="store_true", help="skip the other workloads")
+    ap.add_argument("--adjoint-slices", dest="adjoint_slices", type=int, choices=[6, 7], default=7,
+                    help="--case adjoint: BF16 slices per operand of the split adjoint")
     args = ap.parse_args()
     rank, world, local = dist_init()
     if args.impl == "reference":

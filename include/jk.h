@@ -308,7 +308,7 @@ typedef enum {
                                symmetric build, the U = V case of Sec. II.C,
                                is symmetric), the rest mirrored; results
                                within rounding of those of 0                  */
-    JK_OPT_PACKED_FACTOR = 8 /* 0 (default) dense factor; 1 every factor passed
+    JK_OPT_PACKED_FACTOR = 8, /* 0 (default) dense factor; 1 every factor passed
                                to jk_build, jk_build_batched, jk_adjoint,
                                jk_build_dense, jk_density_grad, jk_pair,
                                jk_build_laplace and jk_autotune* on this handle
@@ -329,6 +329,20 @@ typedef enum {
                                factor is in host memory) return
                                JK_ERR_UNSUPPORTED while it is 1; dL of the
                                adjoint stays dense [naux][nbf][nbf]            */
+    JK_OPT_TILE = 9,      /* split engine, six-slice products: -1 = tuned/
+                               default, 0 = output tiles of 128 x 80, 1 = 128 x
+                               64 (more, narrower tiles; a tuning candidate).
+                               Results are identical: the tile only changes
+                               which outputs a CTA forms, not how            */
+    JK_OPT_ADJOINT_SLICES = 10 /* split jk_adjoint: BF16 slices per operand of
+                               every product, 7 (default: 56-bit operands, 28
+                               slice pairs, 128 x 64 tiles) or 6 (48-bit, 21
+                               pairs, about a quarter fewer tensor-core flops).
+                               The adjoint's dX, dY are sums over aux indices
+                               and basis functions of three chained products,
+                               where 48-bit operands leave errors of ~1e-14
+                               relative to max |dX|; 56 bits bring them below
+                               the FP64 engine's own                          */
 } jk_option;
 /* Options set explicitly on a handle override tuned configurations. */
 jk_status jk_set_option(jk_handle h, jk_option opt, int64_t value);
@@ -346,7 +360,7 @@ jk_status jk_pack_factor(jk_handle h, int32_t nbf, int32_t naux, const double *L
 
 /* ---------------------------------------------------------------------------
  * Autotuner.  A configuration is the set of run-time choices a build makes
- * (aux-index chunk, launch schedule, GEMM tile order).  jk_autotune times the
+ * (aux-index chunk, launch schedule, GEMM tile order and tile width).  jk_autotune times the
  * candidate configurations of one problem with CUDA events on `stream` (it
  * synchronizes the stream, so it must not be called during stream capture),
  * keeps the fastest in a process-wide cache keyed by a shape bucket (op,
@@ -362,6 +376,7 @@ typedef struct {
     int32_t aux_chunk;   /* aux indices per chunk, 0 = automatic */
     int32_t schedule;    /* 0 per-density launches, 1 grouped persistent launches */
     int32_t raster;      /* 0 n-tile fastest, 1 m-tile fastest */
+    int32_t tile;        /* sliced GEMM output tiles: 0 128 x 80, 1 128 x 64 */
 } jk_tune_config;
 
 jk_status jk_autotune(jk_handle h, const jk_factor *f, int32_t nd, const jk_density *d,

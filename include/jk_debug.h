@@ -24,6 +24,15 @@ jk_status jk_debug_sliced_gemm(jk_handle h, int32_t M, int32_t N, int32_t K,
                                void *stream);
 size_t jk_debug_sliced_gemm_workspace(int32_t M, int32_t N, int32_t K);
 
+/* The same product with `slices` BF16 slices per operand: 6 (48-bit
+ * fixed-point operands, 21 slice pairs) or 7 (56-bit operands, 28 slice
+ * pairs, exact windows on one more diagonal, 128 x 64 tiles: the
+ * configuration of the split adjoint).  JK_ERR_ARG for another count.  The
+ * arena must hold jk_debug_sliced_gemm_workspace_slices(M, N, K, slices). */
+jk_status jk_debug_sliced_gemm_slices(jk_handle h, int32_t M, int32_t N, int32_t K, const double *A,
+                                      const double *B, double *C, int32_t slices, void *stream);
+size_t jk_debug_sliced_gemm_workspace_slices(int32_t M, int32_t N, int32_t K, int32_t slices);
+
 /* Exercises the engine's bounded waits: one thread waits on an mbarrier
  * phase that nothing completes, with the same helper and limit (4 s) the
  * tcgen05 pipeline uses; when the limit runs out it raises JK_ERR_TIMEOUT in

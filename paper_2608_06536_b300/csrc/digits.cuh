@@ -1,8 +1,12 @@
-// Six-digit splits of a 48-bit fixed-point value F (|F| <= 2^48) into BF16
-// slices, the slicer's two ways of forming them:
-//   digits6 + qbf16   32-bit integer digit extraction, then one exact FP32
-//                     conversion per digit (the default slicer);
-//   split48           FP32 additions only (JK_OPT_SLICER = 1), below.
+// Digit splits of a fixed-point value F into BF16 slices, the slicer's ways of
+// forming them:
+//   digits6 + qbf16   six digits of a 48-bit F (|F| <= 2^48) in 32-bit integer
+//                     arithmetic, then one exact FP32 conversion per digit
+//                     (the default slicer);
+//   digits_n<7>       seven digits of a 56-bit F in 64-bit arithmetic (the
+//                     seven-slice operands of the split adjoint);
+//   split48           six digits of a 48-bit F by FP32 additions only
+//                     (JK_OPT_SLICER = 1), below.
 //
 // split48: F is cut into two exact halves, lo = F mod 2^24 and
 // hi = F div 2^24, each converted to FP32 exactly and pre-scaled by a power
@@ -59,6 +63,19 @@ JK_HD void digits6(long long F, int q[6]) {
     q[2] = ((hi + 128) & 255) - 128; hi = (hi - q[2]) >> 8;
     q[1] = ((hi + 128) & 255) - 128; hi = (hi - q[1]) >> 8;
     q[0] = hi;
+}
+
+// S balanced base-256 digits of F (|F| <= 2^(8S)) in 64-bit integer
+// arithmetic: F = sum_j q_j 2^(8(S-1-j)), q_1..q_{S-1} in [-128, 127] and
+// |q_0| <= 256 (the seven-slice operands' split; digits6 is the same split for
+// S = 6 in 32-bit arithmetic).
+template <int S>
+JK_HD void digits_n(long long F, int q[S]) {
+    for (int j = S - 1; j >= 1; j--) {   // a constant trip count: unrolled by the compiler
+        q[j] = static_cast<int>(((F + 128) & 255) - 128);
+        F = (F - q[j]) >> 8;
+    }
+    q[0] = static_cast<int>(F);
 }
 
 JK_HD float f32_of_bits(uint32_t b) {

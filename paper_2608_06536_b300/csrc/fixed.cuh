@@ -1,7 +1,8 @@
 // Fixed-point conversions of the split-precision GEMM, in integer arithmetic
 // only (B300's FP64 pipe runs at 1/60 of the FP32 rate):
 //   exponent_of_max     the scale 2^e of a group of values (max|x| < 2^e);
-//   to_fixed48          x under that scale as a 48-bit signed integer;
+//   to_fixed(48)        x under that scale as a 48-bit (or nbits-bit) signed
+//                       integer;
 //   i64/i128_to_f64_scaled
 //                       an integer accumulator times 2^e2, rounded once to
 //                       the nearest FP64 value (ties to even).
@@ -64,20 +65,24 @@ JK_HD int exponent_of_max(uint64_t maxbits) {
     return ex == 0 ? -1000 : ex - 1022;
 }
 
-// F = x * 2^(48 - e) rounded to the nearest integer (ties away from zero), so
-// |F| <= 2^48 when |x| < 2^e.  Zero and subnormal inputs give 0.
-JK_HD long long to_fixed48(double x, int e) {
+// F = x * 2^(nbits - e) rounded to the nearest integer (ties away from zero),
+// so |F| <= 2^nbits when |x| < 2^e (nbits <= 60).  Zero and subnormal inputs
+// give 0.
+JK_HD long long to_fixed(double x, int e, int nbits) {
     const uint64_t bits = f64_bits(x);
     const int ex = static_cast<int>((bits >> 52) & 0x7FF);
     if (ex == 0) return 0;
     const uint64_t m = (bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-    const int r = 1027 + e - ex;   // right shift of the 53-bit significand; >= 5 when |x| < 2^e
+    const int r = 1075 - nbits + e - ex;   // right shift of the 53-bit significand; >= 53 - nbits when |x| < 2^e
     long long F;
     if (r <= 0) F = static_cast<long long>(m << (-r));
     else if (r >= 64) F = 0;
     else F = static_cast<long long>((m + (1ull << (r - 1))) >> r);
     return (bits >> 63) ? -F : F;
 }
+
+// The 48-bit form used by the six-slice operands.
+JK_HD long long to_fixed48(double x, int e) { return to_fixed(x, e, 48); }
 
 // The FP64 value nearest (ties to even) to (top + s) * 2^(x2 - 63), where top
 // has its leading one at bit 63 and 0 <= s < 1 is nonzero exactly when

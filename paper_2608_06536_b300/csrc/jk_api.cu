@@ -114,6 +114,7 @@ static jk_tune_config resolve_config(const jk_ctx *h, jk_op op, jk_precision p, 
         if (h->aux_chunk >= 0) c.aux_chunk = h->aux_chunk;
         if (h->schedule >= 0) c.schedule = h->schedule;
         if (h->raster >= 0) c.raster = h->raster;
+        if (h->tile >= 0) c.tile = h->tile;
     }
     return c;
 }
@@ -252,6 +253,7 @@ static jk_tune_config host_config(const jk_ctx *h, jk_precision p, const Problem
     if (h->aux_chunk >= 0) c.aux_chunk = h->aux_chunk;
     if (h->schedule >= 0) c.schedule = h->schedule;
     if (h->raster >= 0) c.raster = h->raster;
+    if (h->tile >= 0) c.tile = h->tile;
     return c;
 }
 
@@ -315,6 +317,7 @@ static jk_status host_build(jk_ctx *h, const Problem &pb, const jk_density *d, d
                          ar.off + build_bytes(q, p));
     JK_TRY(ensure_copy_stream(h));
     h->cur_raster = cfg.raster;
+    h->cur_tile = cfg.tile;
 
     // densities up, accumulators cleared (on the caller's stream)
     size_t off = 0;
@@ -605,6 +608,7 @@ static size_t dense_query_bytes(DenseProb dp, jk_op op, jk_precision p) {
 static void dense_config(jk_ctx *h, DenseProb &dp) {
     dp.aux_chunk = h->aux_chunk > 0 ? h->aux_chunk : 0;
     h->cur_raster = h->raster >= 0 ? h->raster : 0;
+    h->cur_tile = h->tile >= 0 ? h->tile : 0;
 }
 
 static jk_status run_dense(jk_ctx *h, const DenseProb &dp, jk_precision p, cudaStream_t st) {
@@ -696,6 +700,7 @@ static jk_status query_impl(const jk_ctx *h, jk_op op, int32_t nmol, const jk_fa
         jk_status s = make_problem(nullptr, f, nd, d, false, pbs[0]);
         if (s != JK_OK) return s;
         pbs[0].packed = pk;
+        pbs[0].slices = h ? h->adj_slices : 7;   // the split adjoint's operands (the default without a handle)
         nmol = 1;
         if (op == JK_OP_BUILD_HOST || op == JK_OP_BUILD_HOST_PACKED) {
             *bytes = host_build_bytes(h, pbs[0], p, op == JK_OP_BUILD_HOST_PACKED) + flags_bytes() + kArenaAlign;
@@ -746,6 +751,7 @@ jk_status jk_build(jk_handle h, const jk_factor *f, int32_t nd, const jk_density
     const jk_tune_config c = resolve_config(h, JK_OP_BUILD, p, h->num_sms, 1, &pb);
     apply_config(pb, c);
     h->cur_raster = c.raster;
+    h->cur_tile = c.tile;
     if (h->arena.bytes < flags_bytes() + build_bytes(pb, p))
         return set_error(h, JK_ERR_OOM, "arena has %zu bytes, this build needs %zu",
                          h->arena.bytes, flags_bytes() + build_bytes(pb, p));
@@ -794,6 +800,7 @@ jk_status jk_build_batched(jk_handle h, int32_t nmol, const jk_factor *f,
     const jk_tune_config c = resolve_config(h, JK_OP_BATCHED, p, h->num_sms, nmol, pbs.data());
     for (auto &pb : pbs) apply_config(pb, c);
     h->cur_raster = c.raster;
+    h->cur_tile = c.tile;
     if (h->arena.bytes < flags_bytes() + batched_bytes(nmol, pbs.data(), p))
         return set_error(h, JK_ERR_OOM, "arena has %zu bytes, this batched build needs %zu", h->arena.bytes,
                          flags_bytes() + batched_bytes(nmol, pbs.data(), p));
@@ -818,7 +825,8 @@ jk_status jk_autotune(jk_handle h, const jk_factor *f, int32_t nd, const jk_dens
     for (int ch : chunk_candidates(pc0, pb.naux))
         for (int sc = 0; sc < (p == JK_FP64 ? 1 : 2); sc++)
             for (int ra = 0; ra < (p == JK_FP64 ? 1 : 2); ra++)
-                cands.push_back(jk_tune_config{ch, sc, ra});
+                for (int ti = 0; ti < (p == JK_FP64 ? 1 : 2); ti++)
+                    cands.push_back(jk_tune_config{ch, sc, ra, ti});
     auto fits = [&](const jk_tune_config &c) {
         Problem q = pb;
         apply_config(q, c);
@@ -828,6 +836,7 @@ jk_status jk_autotune(jk_handle h, const jk_factor *f, int32_t nd, const jk_dens
         Problem q = pb;
         apply_config(q, c);
         h->cur_raster = c.raster;
+        h->cur_tile = c.tile;
         return run_build(h, q, p, st);
     };
     jk_tune_config bc{0, 0, 0};
@@ -862,7 +871,8 @@ jk_status jk_autotune_batched(jk_handle h, int32_t nmol, const jk_factor *f,
     std::vector<jk_tune_config> cands;
     for (int ch : chunk_candidates(pc0, naux_max))
         for (int ra = 0; ra < (p == JK_FP64 ? 1 : 2); ra++)
-            cands.push_back(jk_tune_config{ch, 1, ra});
+            for (int ti = 0; ti < (p == JK_FP64 ? 1 : 2); ti++)
+                cands.push_back(jk_tune_config{ch, 1, ra, ti});
     auto fits = [&](const jk_tune_config &c) {
         std::vector<Problem> q = pbs;
         for (auto &pb : q) apply_config(pb, c);
@@ -872,6 +882,7 @@ jk_status jk_autotune_batched(jk_handle h, int32_t nmol, const jk_factor *f,
         std::vector<Problem> q = pbs;
         for (auto &pb : q) apply_config(pb, c);
         h->cur_raster = c.raster;
+        h->cur_tile = c.tile;
         return batched_build(h, nmol, q.data(), p, st);
     };
     jk_tune_config bc{0, 1, 0};
@@ -909,7 +920,9 @@ jk_status jk_adjoint(jk_handle h, const jk_factor *f, int32_t nd, const jk_densi
     Problem pb;
     JK_TRY(make_problem(h, f, nd, d, true, pb));
     if (h->aux_chunk >= 0) pb.aux_chunk = h->aux_chunk;
+    pb.slices = h->adj_slices;
     h->cur_raster = h->raster >= 0 ? h->raster : 0;
+    h->cur_tile = h->tile >= 0 ? h->tile : 0;
     if (!dX || !dY) return set_error(h, JK_ERR_ARG, "dX and dY are required");
     JK_TRY(check_out(h, dX, "dX"));
     JK_TRY(check_out(h, dY, "dY"));
@@ -989,6 +1002,7 @@ jk_status jk_pair(jk_handle h, const jk_factor *f, int32_t nl, const jk_density 
     const jk_tune_config c = resolve_config(h, JK_OP_BUILD, p, h->num_sms, 1, &pr);
     apply_config(pr, c);
     h->cur_raster = c.raster;
+    h->cur_tile = c.tile;
     const size_t need = flags_bytes() + pair_bytes(pl, pr, p, Jp != nullptr, Kp != nullptr);
     if (h->arena.bytes < need)
         return set_error(h, JK_ERR_OOM, "arena has %zu bytes, this pairing needs %zu", h->arena.bytes, need);
@@ -1057,6 +1071,7 @@ jk_status jk_build_laplace(jk_handle h, const jk_factor *f, int32_t nq, const do
     const jk_tune_config c = resolve_config(h, JK_OP_BUILD, p, h->num_sms, 1, &pb);
     apply_config(pb, c);
     h->cur_raster = c.raster;
+    h->cur_tile = c.tile;
     const int n = pb.n;
     const bool weighted = w != nullptr;
     const size_t need = flags_bytes() + laplace_persist_bytes(n, nq, m, sym, weighted, J != nullptr, K != nullptr) +
@@ -1138,6 +1153,16 @@ jk_status jk_set_option(jk_handle h, jk_option opt, int64_t value) {
     if (opt == JK_OPT_PACKED_FACTOR) {
         if (value != 0 && value != 1) return set_error(h, JK_ERR_ARG, "JK_OPT_PACKED_FACTOR takes 0 or 1");
         h->packed_factor = static_cast<int>(value);
+        return JK_OK;
+    }
+    if (opt == JK_OPT_TILE) {
+        if (value < -1 || value > 1) return set_error(h, JK_ERR_ARG, "JK_OPT_TILE takes -1, 0 or 1");
+        h->tile = static_cast<int>(value);
+        return JK_OK;
+    }
+    if (opt == JK_OPT_ADJOINT_SLICES) {
+        if (value != 6 && value != 7) return set_error(h, JK_ERR_ARG, "JK_OPT_ADJOINT_SLICES takes 6 or 7");
+        h->adj_slices = static_cast<int>(value);
         return JK_OK;
     }
     if (opt == JK_OPT_USE_TUNED) {

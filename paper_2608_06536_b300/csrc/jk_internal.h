@@ -71,8 +71,11 @@ struct jk_ctx {
     int schedule = -1;
     int raster = -1;
     int use_tuned = 1;
+    int tile = -1;           // explicit tile width option (JK_OPT_TILE)
+    int adj_slices = 7;      // slices per operand of the split adjoint (JK_OPT_ADJOINT_SLICES)
     int cur_raster = 0;      // tile order in effect for the running call
-    bool gemm_smem_set = false;   // the sliced GEMM's shared-memory attribute is set on this device
+    int cur_tile = 0;        // tile width in effect for the running call: 0 80 columns, 1 64
+    int gemm_smem_set = 0;   // bit c: the shared-memory attribute of slice configuration c is set
     int host_chunk = 0;      // aux indices per streamed chunk of a host-resident factor (0 = automatic)
     int slicer = 0;          // digit extraction of the vector slicer: 0 integer, 1 FP32 additions
     int syrk = 0;            // split engine: symmetric rank updates by row blocks, rest mirrored
@@ -108,6 +111,7 @@ struct Problem {
     int schedule = 0;    // split precision: 0 per-density launches, 1 grouped launches
     bool packed = false; // L holds packed upper triangles [naux][n(n+1)/2]; each aux
                          // chunk is expanded into a dense workspace copy before use
+    int slices = 6;      // split adjoint: slices per operand (6: 48-bit, 7: 56-bit)
 };
 
 jk_status set_error(jk_ctx *h, jk_status s, const char *fmt, ...);

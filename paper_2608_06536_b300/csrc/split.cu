@@ -49,30 +49,59 @@
 namespace jk {
 namespace oz {
 
-constexpr int S = 6;            // slices per operand
-constexpr int BM = 128;         // rows of A per tile (TMEM lanes)
-constexpr int BN = 80;          // rows of B per tile (TMEM columns per accumulator)
-constexpr int KB = 16;          // reduction elements per pipeline stage (one MMA K-step)
-constexpr int CHUNK = 128;      // exact accumulation window
-constexpr int KBPC = CHUNK / KB;
-constexpr int SUPER = 2048;     // reduction elements per int64 partial
+constexpr int BM = 128;             // rows of A per tile (TMEM lanes)
+constexpr int KB = 16;              // reduction elements per pipeline stage (one MMA K-step)
+constexpr int KBPC = 8;             // K-blocks of a 128-element exact window
+constexpr int WPERIOD = 2 * KBPC;   // the window pattern repeats every 16 K-blocks
+constexpr int SUPER = 2048;         // reduction elements per int64 partial
 constexpr int NSTAGE = 3;
-constexpr int NACC = 6;
-constexpr int NPAIRS = 21;
-constexpr int FRAC = 48;        // fraction bits of the int64 accumulator
-constexpr int THREADS = 320;    // producer warp, MMA warp, 8 epilogue warps
+constexpr int THREADS = 320;        // producer warp, MMA warp, 8 epilogue warps
+constexpr int MAXMMA = 12;          // most merged MMAs per K-block of any configuration
 
-constexpr int A_BYTES = S * BM * 32;
-constexpr int B_BYTES = S * BN * 32;
-constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
-// Output staging: each epilogue warp owns 32 rows x 40 columns of 64-bit words,
-// kept as five 32x8 blocks in the 64-byte swizzled layout of a TMA store.
-constexpr int OUT_COLS = BN / 2;
-constexpr int OUT_BLK = 8;                         // 64-bit words per 64-byte row
-constexpr int OUT_WARP_BYTES = 32 * OUT_COLS * 8;  // 10 KB
-constexpr int OUT_BYTES = 8 * OUT_WARP_BYTES;
-constexpr int SMEM_BYTES = NSTAGE * STAGE_BYTES + OUT_BYTES + 1024 /*align slack*/ + 256 /*barriers*/;
-
+// A slice configuration.  Every operand element is an S-digit fixed-point
+// value (8S bits under its row's scale), cut into S BF16 slices of balanced
+// 8-bit digits; the slice pairs (a, b) with a + b < S are multiplied, and the
+// pairs on one diagonal d = a + b share a scale and one TMEM accumulator of BN
+// columns (S accumulators, laid out by d).  Diagonals d < NEXACT accumulate in
+// exact windows (128 or 256 reduction elements: every partial sum an integer
+// below 2^24 in its unit) and are drained into an int64 fixed point with FRAC
+// fraction bits; the two lowest diagonals, whose error is below the
+// representation's, accumulate over the whole tile.
+//   Cfg<6, 80>  48-bit operands, 21 pairs, 128 x 80 tiles (the default);
+//   Cfg<6, 64>  the same with 128 x 64 tiles (a tuning candidate);
+//   Cfg<7, 64>  56-bit operands, 28 pairs, 128 x 64 tiles (the split adjoint:
+//               its chained products need the extra bits).
+template <int S_, int BN_>
+struct Cfg {
+    static constexpr int S = S_;
+    static constexpr int BN = BN_;
+    static constexpr int NACC = S;
+    static constexpr int NEXACT = S - 2;
+    static constexpr int NPAIRS = S * (S + 1) / 2;
+    static constexpr int BITS = 8 * S;
+    // int64 accumulator: |sum| < K * 2^FRAC for K <= SUPER elements stays in range
+    static constexpr int FRAC = S == 6 ? 48 : 51;
+    static constexpr int A_BYTES = S * BM * 32;
+    static constexpr int B_BYTES = S * BN * 32;
+    static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+    // Output staging: each epilogue warp owns 32 rows x OUT_COLS columns of
+    // 64-bit words, kept as 32 x 8 blocks in the 64-byte swizzled layout of a
+    // TMA store.
+    static constexpr int OUT_COLS = BN / 2;
+    static constexpr int OUT_BLK = 8;
+    static constexpr int OUT_WARP_BYTES = 32 * OUT_COLS * 8;
+    static constexpr int OUT_BYTES = 8 * OUT_WARP_BYTES;
+    static constexpr int SMEM_BYTES = NSTAGE * STAGE_BYTES + OUT_BYTES + 1024 /*align slack*/ + 256 /*barriers*/;
+    static_assert(S * BN <= 512, "the accumulators fit tensor memory");
+    static_assert(BN % 16 == 0 && OUT_COLS % OUT_BLK == 0, "tile width");
+    static_assert(NEXACT >= 1 && NEXACT <= 5, "window schedule");
+    static_assert(FRAC >= 16 + 8 * (NEXACT - 1) && FRAC + 11 <= 62, "exact drains and the int64 range");
+    static_assert(SMEM_BYTES <= 227 * 1024, "shared memory");
+};
+using Cfg6 = Cfg<6, 80>;
+using Cfg6n = Cfg<6, 64>;
+using Cfg7 = Cfg<7, 64>;
+constexpr int OUT_BLK = 8;
 
 // ---------------------------------------------------------------------------
 // Integer helpers
@@ -81,7 +110,7 @@ constexpr int SMEM_BYTES = NSTAGE * STAGE_BYTES + OUT_BYTES + 1024 /*align slack
 using fixed::exponent_of_max;
 using fixed::i128_to_f64_scaled;
 using fixed::i64_to_f64_scaled;
-using fixed::to_fixed48;
+using fixed::to_fixed;
 
 // ---------------------------------------------------------------------------
 // Slicers
@@ -145,9 +174,19 @@ __global__ void __launch_bounds__(256) expo_kernel(Src src, int rows, int K, int
 using digits::digits6;
 using digits::qbf16;
 
+// The S digits of an element under its scale: the 32-bit split for six
+// slices, the 64-bit one for seven.
+template <int S>
+__device__ __forceinline__ void element_digits(double x, int e, int q[S]) {
+    const long long F = to_fixed(x, e, 8 * S);
+    if constexpr (S == 6) digits6(F, q);
+    else digits::digits_n<S>(F, q);
+}
+
 // Vector slicer: 4 consecutive reduction elements per thread.  Requires
 // src.ski == 1, src.kin % 4 == 0, K % 4 == 0 and 16-byte aligned pairs
 // (checked on the host).
+template <int S>
 __global__ void __launch_bounds__(256) slice4_kernel(Src src, int rows, int K, int Kpad, const int *e, int rpe,
                                                      int nsc, uint2 *out, long long sstride4) {
     const int kk = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
@@ -165,10 +204,10 @@ __global__ void __launch_bounds__(256) slice4_kernel(Src src, int rows, int K, i
                 const double2 *p2 = reinterpret_cast<const double2 *>(src_row(src, r) + koff);
                 const double2 a = p2[0], b = p2[1];
                 const int er = e[(r / rpe) * nsc + kk / SUPER];
-                digits6(to_fixed48(a.x, er), q[0]);
-                digits6(to_fixed48(a.y, er), q[1]);
-                digits6(to_fixed48(b.x, er), q[2]);
-                digits6(to_fixed48(b.y, er), q[3]);
+                element_digits<S>(a.x, er, q[0]);
+                element_digits<S>(a.y, er, q[1]);
+                element_digits<S>(b.x, er, q[2]);
+                element_digits<S>(b.y, er, q[3]);
             } else {
 #pragma unroll
                 for (int i = 0; i < 4; i++)
@@ -189,13 +228,14 @@ __global__ void __launch_bounds__(256) slice4_kernel(Src src, int rows, int K, i
     }
 }
 
-// Vector slicer with the digits formed by FP32 additions (digits.cuh): the
-// same layout and requirements as slice4_kernel; the slices are an equally
-// exact split of the same 48-bit values (digits may differ from the integer
-// path only where a digit rounds a tie, to even here).  The BF16 words are
-// the upper halves of the FP32 digits, paired with one byte permute.
+// Vector slicer with the digits formed by FP32 additions (digits.cuh, six
+// slices): the same layout and requirements as slice4_kernel; the slices are
+// an equally exact split of the same 48-bit values (digits may differ from the
+// integer path only where a digit rounds a tie, to even here).  The BF16 words
+// are the upper halves of the FP32 digits, paired with one byte permute.
 __global__ void __launch_bounds__(256) slice4f_kernel(Src src, int rows, int K, int Kpad, const int *e, int rpe,
                                                       int nsc, uint2 *out, long long sstride4) {
+    constexpr int S = 6;
     const int kk = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
     if (kk >= Kpad) return;
     long long koff = 0;
@@ -211,10 +251,10 @@ __global__ void __launch_bounds__(256) slice4f_kernel(Src src, int rows, int K, 
                 const double2 *p2 = reinterpret_cast<const double2 *>(src_row(src, r) + koff);
                 const double2 a = p2[0], b = p2[1];
                 const int er = e[(r / rpe) * nsc + kk / SUPER];
-                digits::split48(to_fixed48(a.x, er), v[0]);
-                digits::split48(to_fixed48(a.y, er), v[1]);
-                digits::split48(to_fixed48(b.x, er), v[2]);
-                digits::split48(to_fixed48(b.y, er), v[3]);
+                digits::split48(to_fixed(a.x, er, 48), v[0]);
+                digits::split48(to_fixed(a.y, er, 48), v[1]);
+                digits::split48(to_fixed(b.x, er, 48), v[2]);
+                digits::split48(to_fixed(b.y, er, 48), v[3]);
             } else {
 #pragma unroll
                 for (int i = 0; i < 4; i++)
@@ -262,7 +302,8 @@ __global__ void __launch_bounds__(256) expo_flat_kernel(const double *p, long lo
 
 constexpr int SLICE_ROWS = 8;   // rows per block of the slicer
 
-// out[j][r][kk] = q_j(r, kk) * 2^(-8(j+1)) for j = 0..5 (bf16), zero for kk >= K.
+// out[j][r][kk] = q_j(r, kk) * 2^(-8(j+1)) for j = 0..S-1 (bf16), zero for kk >= K.
+template <int S>
 __global__ void __launch_bounds__(256) slice_kernel(Src src, int rows, int K, int Kpad, const int *e,
                                                     int rpe, int nsc, unsigned short *out, long long sstride) {
     const int kk = blockIdx.x * blockDim.x + threadIdx.x;
@@ -275,8 +316,10 @@ __global__ void __launch_bounds__(256) slice_kernel(Src src, int rows, int K, in
     for (int rb = blockIdx.y * SLICE_ROWS; rb < rows; rb += gridDim.y * SLICE_ROWS) {
         const int rend = min(rows, rb + SLICE_ROWS);
         for (int r = rb; r < rend; r++) {
-            int q[S] = {0, 0, 0, 0, 0, 0};
-            if (kk < K) digits6(to_fixed48(src_row(src, r)[koff], e[(r / rpe) * nsc + kk / SUPER]), q);
+            int q[S];
+#pragma unroll
+            for (int j = 0; j < S; j++) q[j] = 0;
+            if (kk < K) element_digits<S>(src_row(src, r)[koff], e[(r / rpe) * nsc + kk / SUPER], q);
             const long long o = static_cast<long long>(r) * Kpad + kk;
             float sc = 0.00390625f;
 #pragma unroll
@@ -306,97 +349,140 @@ struct OzArgs {
     int *err;             // device error word (JK_ERR_TIMEOUT on a stalled pipeline)
 };
 
-// Accumulator windows.  Exactness bounds (|q_1| <= 256, |q_j| <= 128): one
-// reduction element adds at most 2^16 units to diagonals 0 and 1, and at most
-// 2^16 + 2^15 units to diagonals 2 and 3, so windows of 256 (d = 0, 1) and 128
-// (d = 2, 3) elements keep every partial sum below 2^24.  Window boundaries are
-// offset per accumulator so drains are spread over the K-blocks; accumulators
-// 4 and 5 (inexact) span the tile.
-__host__ __device__ constexpr int wper(int d) { return d < 2 ? 2 * KBPC : KBPC; }
-__host__ __device__ constexpr int woff(int d) { return d == 0 ? 0 : d == 1 ? KBPC : d == 2 ? 2 : 6; }
-
-__device__ __forceinline__ bool win_start(int d, int kb) {
-    if (kb == 0) return true;
-    if (d >= 4) return false;
-    return kb >= woff(d) && ((kb - woff(d)) % wper(d)) == 0;
-}
-
-__device__ __forceinline__ bool win_end(int d, int kb, int nkb) {
-    return kb == nkb - 1 || win_start(d, kb + 1);
-}
-
-// The same window pattern by residue r = kb mod 2*KBPC (compile-time inside the
-// unrolled K-block loop); tile starts and ends are added at run time.
-constexpr int WPERIOD = 2 * KBPC;
-__host__ __device__ constexpr bool ws_r(int d, int r) {
-    return d == 0 ? r == 0 : d == 1 ? r == KBPC : d == 2 ? (r % KBPC) == 2 : d == 3 ? (r % KBPC) == 6 : false;
-}
+// Accumulator windows.  Exactness bounds (|q_0| <= 256, |q_j| <= 128): one
+// reduction element adds at most 2^16 units to diagonals 0 and 1, at most
+// 2^16 + 2^14 to diagonal 2, 3 * 2^15 to diagonal 3 and 7 * 2^14 to diagonal
+// 4, so windows of 256 (d = 0, 1) and 128 (d = 2, 3, 4) elements keep every
+// partial sum below 2^24.  Window starts are spread over the even K-blocks of
+// the 16-block period (d0: 0; d1: 8; d2: 2, 10; d3: 6, 14; d4: 4, 12) so that
+// drains do not coincide and no two consecutive K-blocks both start one.
+__host__ __device__ constexpr int wper(int d) { return d < 2 ? WPERIOD : KBPC; }
+__host__ __device__ constexpr int woff(int d) { return d == 0 ? 0 : d == 1 ? KBPC : d == 2 ? 2 : d == 3 ? 6 : 4; }
+__host__ __device__ constexpr bool ws_r(int d, int r) { return (r - woff(d) + WPERIOD) % wper(d) == 0; }
+template <class C>
 __host__ __device__ constexpr unsigned ws_mask(int r) {
-    return (ws_r(0, r) ? 1u : 0u) | (ws_r(1, r) ? 2u : 0u) | (ws_r(2, r) ? 4u : 0u) | (ws_r(3, r) ? 8u : 0u);
+    unsigned m = 0;
+    for (int d = 0; d < C::NEXACT; d++)
+        if (ws_r(d, r)) m |= 1u << d;
+    return m;
 }
-__host__ __device__ constexpr unsigned we_mask(int r) { return ws_mask((r + 1) % WPERIOD); }
-// The same masks as 16 nibbles of one constant, for run-time r.
-__host__ __device__ constexpr unsigned long long ws_table() {
-    unsigned long long t = 0;
-    for (int r = 0; r < WPERIOD; r++) t |= static_cast<unsigned long long>(ws_mask(r)) << (4 * r);
-    return t;
+template <class C>
+__host__ __device__ constexpr unsigned we_mask(int r) { return ws_mask<C>((r + 1) % WPERIOD); }
+// The window ends of K-block residue r, at run time.
+template <class C>
+__device__ __forceinline__ unsigned we_mask_rt(int r) {
+    const int r1 = (r + 1) & (WPERIOD - 1);
+    unsigned m = 0;
+#pragma unroll
+    for (int d = 0; d < C::NEXACT; d++)
+        if (((r1 - woff(d)) & (wper(d) - 1)) == 0) m |= 1u << d;
+    return m;
 }
-static_assert(WPERIOD == 16, "one nibble per residue");
-__device__ __forceinline__ unsigned ws_mask_rt(int r) { return static_cast<unsigned>(ws_table() >> (4 * r)) & 0xFu; }
-__device__ __forceinline__ unsigned we_mask_rt(int r) { return ws_mask_rt((r + 1) & (WPERIOD - 1)); }
 
-// The 21 slice pairs as 10 merged MMAs: A slice a times B slices b0..b0+nb-1
-// into accumulators d0..d0+nb-1 (d = a + b).  Ordered so that MMAs touching
-// only the tile-long accumulators 4, 5 go first and the MMA touching
-// accumulator 0 goes last: the accumulator whose window just restarted is
-// needed as late as possible.
-constexpr int NMMA = 10;
-__host__ __device__ constexpr int mma_a(int i) { return i == 0 ? 0 : i == 1 ? 1 : i == 2 ? 2 : i == 3 ? 4 : i == 4 ? 5 : i == 5 ? 3 : i == 6 ? 2 : i == 7 ? 1 : 0; }
-__host__ __device__ constexpr int mma_b0(int i) { return i == 0 ? 4 : i == 1 ? 3 : i == 2 ? 3 : i == 8 ? 3 : 0; }
-__host__ __device__ constexpr int mma_nb(int i) { return i == 0 || i == 1 || i == 3 ? 2 : i == 2 || i == 4 || i == 8 ? 1 : 3; }
-__host__ __device__ constexpr int mma_d0(int i) { return mma_a(i) + mma_b0(i); }
-// Issue order per window residue r: the MMAs that touch an accumulator whose
-// window restarts at r go last (each group keeps the base order), so the MMA
-// thread has the most work queued before it must wait for that accumulator's
-// drain.  A table of constants, folded into the unrolled K-block loop.
-__host__ __device__ constexpr unsigned mma_mask(int i) { return ((1u << mma_nb(i)) - 1u) << mma_d0(i); }
-struct MmaOrder {
-    int v[WPERIOD][NMMA];
+// The merged MMAs of one K-block: A slice a times B slices b0..b0+nb-1 into
+// accumulators a+b0 .. a+b0+nb-1 (adjacent TMEM column blocks, since B's
+// slice planes are adjacent in shared memory): one tcgen05.mma with
+// N = nb * BN <= 256.
+struct MmaList {
+    int n;
+    int a[MAXMMA], b0[MAXMMA], nb[MAXMMA];
 };
-__host__ __device__ constexpr MmaOrder make_mma_order() {
+template <class C>
+__host__ __device__ constexpr MmaList make_mma_list() {
+    MmaList L{};
+    if (C::S == 6 && C::BN == 80) {
+        // 21 pairs as 10 MMAs: those touching only the tile-long accumulators
+        // 4, 5 first, the one touching accumulator 0 last (the accumulator
+        // whose window just restarted is needed as late as possible)
+        const int a[10] = {0, 1, 2, 4, 5, 3, 2, 1, 0, 0};
+        const int b0[10] = {4, 3, 3, 0, 0, 0, 0, 0, 3, 0};
+        const int nb[10] = {2, 2, 1, 2, 1, 3, 3, 3, 1, 3};
+        L.n = 10;
+        for (int i = 0; i < 10; i++) {
+            L.a[i] = a[i];
+            L.b0[i] = b0[i];
+            L.nb[i] = nb[i];
+        }
+        return L;
+    }
+    // otherwise: each A slice's B slices in runs of at most 256 / BN, ordered
+    // with the runs touching only the tile-long accumulators first, then by
+    // decreasing lowest diagonal
+    const int W = 256 / C::BN;
+    int a[MAXMMA] = {}, b0[MAXMMA] = {}, nb[MAXMMA] = {}, key[MAXMMA] = {};
+    int c = 0;
+    for (int aa = 0; aa < C::S; aa++)
+        for (int lo = 0; lo < C::S - aa; lo += W) {
+            a[c] = aa;
+            b0[c] = lo;
+            nb[c] = C::S - aa - lo < W ? C::S - aa - lo : W;
+            key[c] = (aa + lo >= C::NEXACT ? 1000 : 0) + 10 * (aa + lo) - aa;   // larger first
+            c++;
+        }
+    bool used[MAXMMA] = {};
+    for (int i = 0; i < c; i++) {
+        int best = -1;
+        for (int j = 0; j < c; j++)
+            if (!used[j] && (best < 0 || key[j] > key[best])) best = j;
+        used[best] = true;
+        L.a[i] = a[best];
+        L.b0[i] = b0[best];
+        L.nb[i] = nb[best];
+    }
+    L.n = c;
+    return L;
+}
+
+// Issue order per window residue r: the MMAs that touch an accumulator whose
+// window restarts at r go last (each group keeps the list's order), so the
+// MMA thread has the most work queued before it must wait for that
+// accumulator's drain.
+struct MmaOrder {
+    int v[WPERIOD][MAXMMA];
+};
+template <class C>
+__host__ __device__ constexpr MmaOrder make_mma_order(const MmaList &L) {
     MmaOrder t{};
     for (int r = 0; r < WPERIOD; r++) {
-        const unsigned m = ws_mask(r);
+        const unsigned m = ws_mask<C>(r);
         int c = 0;
         for (int pass = 0; pass < 2; pass++)
-            for (int j = 0; j < NMMA; j++)
-                if (((mma_mask(j) & m) != 0) == (pass == 1)) t.v[r][c++] = j;
+            for (int j = 0; j < L.n; j++) {
+                const unsigned mj = ((1u << L.nb[j]) - 1u) << (L.a[j] + L.b0[j]);
+                if (((mj & m) != 0) == (pass == 1)) t.v[r][c++] = j;
+            }
     }
     return t;
 }
-// The same order written out (a switch the unrolled loop folds to constants);
-// checked against make_mma_order() at compile time.
-__host__ __device__ constexpr int mma_issue(int r, int i0) {
-    switch (r) {
-        case 2: { const int o[NMMA] = {0, 1, 2, 3, 4, 5, 8, 6, 7, 9}; return o[i0]; }
-        case 6: { const int o[NMMA] = {0, 1, 2, 3, 4, 9, 5, 6, 7, 8}; return o[i0]; }
-        case 8: { const int o[NMMA] = {0, 1, 2, 3, 4, 5, 6, 8, 7, 9}; return o[i0]; }
-        case 10: { const int o[NMMA] = {0, 1, 2, 3, 4, 5, 8, 6, 7, 9}; return o[i0]; }
-        case 14: { const int o[NMMA] = {0, 1, 2, 3, 4, 9, 5, 6, 7, 8}; return o[i0]; }
-        default: return i0;
+
+template <class C>
+struct Tabs {
+    static constexpr MmaList list = make_mma_list<C>();
+    static constexpr MmaOrder order = make_mma_order<C>(list);
+};
+
+template <class C>
+__host__ __device__ constexpr bool mma_list_covers_pairs() {
+    constexpr MmaList L = Tabs<C>::list;
+    int seen[8][8] = {};
+    for (int i = 0; i < L.n; i++) {
+        if (L.nb[i] < 1 || L.nb[i] * C::BN > 256) return false;
+        for (int b = L.b0[i]; b < L.b0[i] + L.nb[i]; b++) seen[L.a[i]][b]++;
     }
-}
-__host__ __device__ constexpr bool mma_issue_matches() {
-    const MmaOrder t = make_mma_order();
-    for (int r = 0; r < WPERIOD; r++)
-        for (int i = 0; i < NMMA; i++)
-            if (mma_issue(r, i) != t.v[r][i]) return false;
+    for (int a = 0; a < C::S; a++)
+        for (int b = 0; b < C::S; b++)
+            if (seen[a][b] != (a + b < C::S ? 1 : 0)) return false;
     return true;
 }
-static_assert(mma_issue_matches(), "MMA issue order table");
+static_assert(mma_list_covers_pairs<Cfg6>() && mma_list_covers_pairs<Cfg6n>() && mma_list_covers_pairs<Cfg7>(),
+              "every slice pair with a + b < S exactly once");
 
-// Drain order at a tile end: the first MMAs of the next tile need 4, 5, then 3, 2, 1, 0.
-__host__ __device__ constexpr int drain_acc(int j) { return j == 0 ? 4 : j == 1 ? 5 : 3 - (j - 2); }
+// Drain order at a tile end: the first MMAs of the next tile need the
+// tile-long accumulators, then the exact ones from the lowest diagonal up.
+template <class C>
+__host__ __device__ constexpr int drain_acc(int j) {
+    return j < C::S - C::NEXACT ? C::NEXACT + j : C::NEXACT - 1 - (j - (C::S - C::NEXACT));
+}
 
 // One GEMM of a launch.  A launch carries up to MAXG of them (uneven shapes
 // from many molecules and densities) in its parameter space, so a whole
@@ -407,7 +493,13 @@ struct OzProb {
     OzArgs a;
     int tile0;          // first launch-wide work unit of this problem
     int ntn, ntm;       // output tiles along N and M
+    int cfg;            // slice configuration (host side: all problems of a launch share it)
 };
+// Configuration ids of OzProb::cfg.
+constexpr int CFG6 = 0, CFG6N = 1, CFG7 = 2;
+__host__ __device__ constexpr int cfg_slices(int c) { return c == CFG7 ? 7 : 6; }
+__host__ __device__ constexpr int cfg_bn(int c) { return c == CFG6 ? 80 : 64; }
+__host__ __device__ constexpr int cfg_frac(int c) { return c == CFG7 ? Cfg7::FRAC : Cfg6::FRAC; }
 constexpr int MAXG = 32;
 struct OzGroup {
     OzProb p[MAXG];
@@ -446,16 +538,104 @@ __device__ __forceinline__ TileCoord tile_of(const OzProb &pr, int u, int raster
     return c;
 }
 
+// The MMAs of one K-block of window residue R, in the residue's issue order
+// (compile-time tables): before the first MMA into an accumulator whose window
+// starts here (bit set in pend), wait until the epilogue has drained and
+// zeroed it.  Returns false if a wait gave up.
+template <class C, int R, int I>
+__device__ __forceinline__ bool issue_mmas(uint32_t tmem, uint64_t ad0, uint64_t bd0, unsigned &pend,
+                                           int (&wcnt)[C::NACC], uint64_t *accempty, volatile int *abort_flag) {
+    if constexpr (I == Tabs<C>::list.n) {
+        return true;
+    } else {
+        constexpr int i = Tabs<C>::order.v[R][I];
+        constexpr int a = Tabs<C>::list.a[i];
+        constexpr int b0 = Tabs<C>::list.b0[i];
+        constexpr int nb = Tabs<C>::list.nb[i];
+        constexpr int d0 = a + b0;
+        constexpr unsigned mask = ((1u << nb) - 1u) << d0;
+        const unsigned need = pend & mask;
+        if (need) {
+#pragma unroll
+            for (int d = 0; d < C::NACC; d++) {
+                if (!(need & (1u << d))) continue;
+                if (!tc::mbar_wait(&accempty[d], static_cast<uint32_t>(wcnt[d]) & 1u, abort_flag)) return false;
+                wcnt[d]++;
+            }
+            pend &= ~need;
+            tc::fence_after_sync();
+        }
+        // descriptor start addresses are in 16-byte units
+        tc::mma_bf16(tmem + d0 * C::BN, ad0 + static_cast<uint64_t>(a * (BM * 32 / 16)),
+                     bd0 + static_cast<uint64_t>(b0 * (C::BN * 32 / 16)), tc::idesc_bf16_f32(BM, C::BN * nb), 1u);
+        return issue_mmas<C, R, I + 1>(tmem, ad0, bd0, pend, wcnt, accempty, abort_flag);
+    }
+}
+
+// K-blocks kb0 + R .. kb0 + 15 of a tile (one window period, unrolled so that
+// the window bookkeeping is compile-time except for the tile's first and last
+// K-block).  Returns false if a wait gave up.
+template <class C, int R>
+__device__ __forceinline__ bool issue_period(uint8_t *smem, uint32_t tmem, int kb0, int nkb, int &stage,
+                                             uint32_t &phase, int (&wcnt)[C::NACC], uint64_t *full, uint64_t *empty,
+                                             uint64_t *accfull, uint64_t *accempty, volatile int *abort_flag) {
+    if constexpr (R == WPERIOD) {
+        return true;
+    } else {
+        const int kb = kb0 + R;
+        if (kb >= nkb) return true;
+        if (!tc::mbar_wait(&full[stage], phase, abort_flag)) return false;
+        tc::fence_after_sync();
+        constexpr unsigned kAll = (1u << C::NACC) - 1u;
+        constexpr unsigned kStarts = ws_mask<C>(R);
+        constexpr unsigned kEnds = we_mask<C>(R);
+        // the tile's first K-block opens every accumulator
+        unsigned pend = kStarts | ((R == 0 && kb0 == 0) ? kAll : 0u);
+        const uint64_t ad0 = tc::sdesc_kmajor_sw32(tc::smem_u32(smem + stage * C::STAGE_BYTES));
+        const uint64_t bd0 = ad0 + static_cast<uint64_t>(C::A_BYTES / 16);
+        if (!issue_mmas<C, R, 0>(tmem, ad0, bd0, pend, wcnt, accempty, abort_flag)) return false;
+        tc::mma_commit(&empty[stage]);
+        const unsigned ends = kEnds | (kb == nkb - 1 ? kAll : 0u);
+#pragma unroll
+        for (int d = 0; d < C::NACC; d++)
+            if (ends & (1u << d)) tc::mma_commit(&accfull[d]);
+        if (++stage == NSTAGE) {
+            stage = 0;
+            phase ^= 1u;
+        }
+        return issue_period<C, R + 1>(smem, tmem, kb0, nkb, stage, phase, wcnt, full, empty, accfull, accempty,
+                                      abort_flag);
+    }
+}
+
+// Load 32 lanes x N consecutive columns (N a multiple of 8) from TMEM.
+template <int N>
+__device__ __forceinline__ void tmem_ld_cols(uint32_t taddr, float *v) {
+#pragma unroll
+    for (int c = 0; c + 16 <= N; c += 16) tc::tmem_ld16(taddr + c, v + c);
+    if constexpr (N % 16 != 0) tc::tmem_ld8(taddr + (N / 16) * 16, v + (N / 16) * 16);
+}
+template <int N>
+__device__ __forceinline__ void tmem_zero_cols(uint32_t taddr) {
+#pragma unroll
+    for (int c = 0; c + 16 <= N; c += 16) tc::tmem_zero16(taddr + c);
+    if constexpr (N % 16 != 0) tc::tmem_zero8(taddr + (N / 16) * 16);
+}
+
 // Persistent, warp-specialized sliced GEMM.  Warp 0 streams operand stages
-// with TMA, warp 1 issues the 21 slice-pair MMAs per stage, warps 2..9 drain
-// the six TMEM accumulators after every window into int64 registers and write
-// the finished tile while the next tile's MMAs run.
+// with TMA, warp 1 issues the slice-pair MMAs per stage, warps 2..9 drain the
+// TMEM accumulators after every window into int64 registers and write the
+// finished tile while the next tile's MMAs run.
+template <class C>
 __global__ void __launch_bounds__(THREADS, 1)
 ozgemm_kernel(const __grid_constant__ OzGroup g) {
+    constexpr int NACC = C::NACC;
+    constexpr int BN = C::BN;
+    constexpr int OUT_COLS = C::OUT_COLS;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    uint8_t *outbuf = smem + NSTAGE * STAGE_BYTES;
-    uint64_t *full = reinterpret_cast<uint64_t *>(outbuf + OUT_BYTES);
+    uint8_t *outbuf = smem + NSTAGE * C::STAGE_BYTES;
+    uint64_t *full = reinterpret_cast<uint64_t *>(outbuf + C::OUT_BYTES);
     uint64_t *empty = full + NSTAGE;
     uint64_t *accfull = empty + NSTAGE;
     uint64_t *accempty = accfull + NACC;
@@ -501,10 +681,10 @@ ozgemm_kernel(const __grid_constant__ OzGroup g) {
                 for (int kb = 0; kb < tc_.nkb; kb++) {
                     if (!tc::mbar_wait(&empty[stage], phase ^ 1u, abort_flag)) { ok = false; break; }
                     const int kc = tc_.kbeg + kb * KB;
-                    uint8_t *sa = smem + stage * STAGE_BYTES;
-                    tc::mbar_expect_tx(&full[stage], STAGE_BYTES);
+                    uint8_t *sa = smem + stage * C::STAGE_BYTES;
+                    tc::mbar_expect_tx(&full[stage], C::STAGE_BYTES);
                     tc::tma_load_3d(sa, &pr.tmA, &full[stage], kc, tc_.m * BM, 0);
-                    tc::tma_load_3d(sa + A_BYTES, &pr.tmB, &full[stage], kc, tc_.n * BN, 0);
+                    tc::tma_load_3d(sa + C::A_BYTES, &pr.tmB, &full[stage], kc, tc_.n * BN, 0);
                     if (++stage == NSTAGE) { stage = 0; phase ^= 1u; }
                 }
             }
@@ -514,60 +694,16 @@ ozgemm_kernel(const __grid_constant__ OzGroup g) {
         if (lane == 0) {
             int stage = 0;
             uint32_t phase = 0;
-            int wcnt[NACC] = {0, 0, 0, 0, 0, 0};   // windows started per accumulator
+            int wcnt[NACC];   // windows started per accumulator
+#pragma unroll
+            for (int d = 0; d < NACC; d++) wcnt[d] = 0;
             bool ok = true;
             for (int u = u0; u < nunits && ok; u += ustep) {
                 const OzProb &pr = g.p[prob_of(g, u)];
                 const TileCoord tc_ = tile_of(pr, u - pr.tile0, g.raster);
-                for (int kb0 = 0; kb0 < tc_.nkb && ok; kb0 += WPERIOD) {
-                    // Unrolled over one window period: the window bookkeeping below is
-                    // compile-time except for the tile's first and last K-block.  The
-                    // waits' polling loops are out of line, which keeps this single
-                    // thread's code small enough for the instruction cache.
-#pragma unroll
-                    for (int r = 0; r < WPERIOD; r++) {
-                        const int kb = kb0 + r;
-                        if (kb >= tc_.nkb) break;
-                        if (!tc::mbar_wait(&full[stage], phase, abort_flag)) { ok = false; break; }
-                        tc::fence_after_sync();
-                        // window starts are compile-time per r; the tile start (r = 0 of the
-                        // first period) opens all six
-                        unsigned pend = ws_mask(r) | ((r == 0 && kb0 == 0) ? 0x3Fu : 0u);
-                        const uint64_t ad0 = tc::sdesc_kmajor_sw32(tc::smem_u32(smem + stage * STAGE_BYTES));
-                        const uint64_t bd0 = ad0 + static_cast<uint64_t>(A_BYTES / 16);
-#pragma unroll
-                        for (int i0 = 0; i0 < NMMA; i0++) {
-                            const int i = mma_issue(r, i0);
-                            const unsigned need = pend & (((1u << mma_nb(i)) - 1u) << mma_d0(i));
-                            if (need) {
-#pragma unroll
-                                for (int d = 0; d < NACC; d++) {
-                                    if (!(need & (1u << d))) continue;
-                                    // the epilogue has drained and zeroed accumulator d
-                                    if (!tc::mbar_wait(&accempty[d], static_cast<uint32_t>(wcnt[d]) & 1u, abort_flag)) {
-                                        ok = false;
-                                        break;
-                                    }
-                                    wcnt[d]++;
-                                }
-                                if (!ok) break;
-                                pend &= ~need;
-                                tc::fence_after_sync();
-                            }
-                            // descriptor start address is in 16-byte units
-                            tc::mma_bf16(tmem + mma_d0(i) * BN, ad0 + static_cast<uint64_t>(mma_a(i) * (BM * 32 / 16)),
-                                         bd0 + static_cast<uint64_t>(mma_b0(i) * (BN * 32 / 16)),
-                                         tc::idesc_bf16_f32(BM, BN * mma_nb(i)), 1u);
-                        }
-                        if (!ok) break;
-                        tc::mma_commit(&empty[stage]);
-                        const unsigned ends = we_mask(r) | (kb == tc_.nkb - 1 ? 0x3Fu : 0u);
-#pragma unroll
-                        for (int d = 0; d < NACC; d++)
-                            if (ends & (1u << d)) tc::mma_commit(&accfull[d]);
-                        if (++stage == NSTAGE) { stage = 0; phase ^= 1u; }
-                    }
-                }
+                for (int kb0 = 0; kb0 < tc_.nkb && ok; kb0 += WPERIOD)
+                    ok = issue_period<C, 0>(smem, tmem, kb0, tc_.nkb, stage, phase, wcnt, full, empty, accfull,
+                                            accempty, abort_flag);
             }
         }
     } else {
@@ -575,12 +711,10 @@ ozgemm_kernel(const __grid_constant__ OzGroup g) {
         const int ew = warp - 2;
         const int q = warp & 3;          // lane quarter this warp may access
         const int half = ew >> 2;        // which half of the tile's columns
-        const uint32_t tlane = tmem + (static_cast<uint32_t>(q * 32) << 16) + half * (BN / 2);
+        const uint32_t tlane = tmem + (static_cast<uint32_t>(q * 32) << 16) + half * OUT_COLS;
         // Accumulators start at zero: clear this warp's share, then open them.
 #pragma unroll
-        for (int d = 0; d < NACC; d++)
-#pragma unroll
-            for (int c = 0; c < BN / 2; c += 8) tc::tmem_zero8(tlane + d * BN + c);
+        for (int d = 0; d < NACC; d++) tmem_zero_cols<OUT_COLS>(tlane + d * BN);
         tc::tmem_wait_st();
         tc::fence_before_sync();
         __syncwarp();
@@ -596,28 +730,28 @@ ozgemm_kernel(const __grid_constant__ OzGroup g) {
             const OzArgs a = g.p[pi].a;
             const CUtensorMap *tmC = &g.p[pi].tmC;
             const TileCoord tc_ = tile_of(g.p[pi], u - g.p[pi].tile0, g.raster);
-            long long acc64[BN / 2];
+            long long acc64[OUT_COLS];
 #pragma unroll
-            for (int i = 0; i < BN / 2; i++) acc64[i] = 0;
+            for (int i = 0; i < OUT_COLS; i++) acc64[i] = 0;
             // Exponents of this warp's output rows and columns, fetched now so that
             // their latency hides under the tile's MMAs: lane l holds the column
-            // exponents of columns l and 32 + l of its 40 (shared by shuffles).
+            // exponents of columns l and 32 + l of its OUT_COLS (shared by shuffles).
             const int c0 = tc_.n * BN + half * OUT_COLS;
             const int row = tc_.m * BM + q * 32 + lane;
             int ea = 0, eb_lo = 0, eb_hi = 0;
             if (a.nsuper == 1) {
-                if (row < a.M) ea = a.eA[row / a.a_rpe] - FRAC;
+                if (row < a.M) ea = a.eA[row / a.a_rpe] - C::FRAC;
                 if (c0 + lane < a.N) eb_lo = a.eB[(c0 + lane) / a.b_rpe];
                 if (lane < OUT_COLS - 32 && c0 + 32 + lane < a.N) eb_hi = a.eB[(c0 + 32 + lane) / a.b_rpe];
             }
             for (int kb = 0; kb < tc_.nkb && ok; kb++) {
-                const unsigned ends = we_mask_rt(kb & (WPERIOD - 1)) | (kb == tc_.nkb - 1 ? 0x3Fu : 0u);
+                const unsigned ends = we_mask_rt<C>(kb & (WPERIOD - 1)) | (kb == tc_.nkb - 1 ? (1u << NACC) - 1u : 0u);
                 if (!ends) continue;
-                // one copy of the drain-and-convert code for all six accumulators
+                // one copy of the drain-and-convert code for all accumulators
                 // (per-accumulator unrolled copies cost instruction-cache misses)
 #pragma unroll 1
                 for (int j = 0; j < NACC; j++) {
-                    const int d = drain_acc(j);
+                    const int d = drain_acc<C>(j);
                     if (!(ends & (1u << d))) continue;
                     if (!tc::mbar_wait(&accfull[d], (epar >> d) & 1u, abort_flag)) {
                         ok = false;
@@ -626,31 +760,29 @@ ozgemm_kernel(const __grid_constant__ OzGroup g) {
                     epar ^= 1u << d;
                     __syncwarp();
                     tc::fence_after_sync();
-                    float v[BN / 2];
-                    static_assert(BN / 2 == 40, "drain shapes: 16 + 16 + 8 columns");
-                    tc::tmem_ld16(tlane + d * BN, v);
-                    tc::tmem_ld16(tlane + d * BN + 16, v + 16);
-                    tc::tmem_ld8(tlane + d * BN + 32, v + 32);
+                    float v[OUT_COLS];
+                    tmem_ld_cols<OUT_COLS>(tlane + d * BN, v);
                     tc::tmem_wait_ld();
-                    tc::tmem_zero16(tlane + d * BN);
-                    tc::tmem_zero16(tlane + d * BN + 16);
-                    tc::tmem_zero8(tlane + d * BN + 32);
+                    tmem_zero_cols<OUT_COLS>(tlane + d * BN);
                     tc::tmem_wait_st();
                     tc::fence_before_sync();
                     __syncwarp();
                     if (lane == 0) tc::mbar_arrive(&accempty[d]);
-                    // Accumulator d <= 3 holds integers in units of 2^-(8d+16) below 2^24;
-                    // accumulators 4, 5 (spanning the tile) stay below 2^-20.  Scale to
-                    // the unit and convert with one FFMA against 1.5*2^23 (exact below
-                    // 2^22; the rare larger value falls back to F2I), then add into the
-                    // 2^-48 fixed point of acc64 (shifted by 32 - 8d for the exact
-                    // diagonals).  No 64-bit float conversions: those run on the scarce
-                    // FP64 pipe.
-                    const float unit = d < 4 ? __int_as_float((127 + 16 + 8 * d) << 23) : 0x1p48f;
-                    const float vmax = d < 4 ? __int_as_float((127 + 22 - 16 - 8 * d) << 23) : 0x1p-26f;
-                    const int sh = d < 4 ? 32 - 8 * d : 0;
+                    // An exact accumulator d holds integers in units of 2^-(8d+16)
+                    // below 2^24; a tile-long one stays far below one unit of the
+                    // output's 2^-FRAC.  Scale to the unit and convert with one
+                    // FFMA against 1.5*2^23 (exact below 2^22; the rare larger
+                    // value falls back to F2I), then add into the 2^-FRAC fixed
+                    // point of acc64 (shifted by FRAC - 16 - 8d for the exact
+                    // diagonals).  No 64-bit float conversions: those run on the
+                    // scarce FP64 pipe.
+                    const bool exact = d < C::NEXACT;
+                    const float unit = exact ? __int_as_float((127 + 16 + 8 * d) << 23) : __int_as_float((127 + C::FRAC) << 23);
+                    const float vmax = exact ? __int_as_float((127 + 22 - 16 - 8 * d) << 23)
+                                             : __int_as_float((127 + 22 - C::FRAC) << 23);
+                    const int sh = exact ? C::FRAC - 16 - 8 * d : 0;
 #pragma unroll
-                    for (int i = 0; i < BN / 2; i++) {
+                    for (int i = 0; i < OUT_COLS; i++) {
                         int xi = __float_as_int(__fmaf_rn(v[i], unit, 12582912.0f)) - 0x4B400000;
                         if (fabsf(v[i]) > vmax) xi = __float2int_rn(v[i] * unit);
                         acc64[i] += static_cast<long long>(static_cast<unsigned long long>(static_cast<long long>(xi)) << sh);
@@ -659,8 +791,8 @@ ozgemm_kernel(const __grid_constant__ OzGroup g) {
             }
             if (!ok) break;
             if (a.use_tma_store) {
-                // This warp's 32 x 48 block: lane = row, three swizzled 32 x 16 sub-blocks.
-                uint8_t *wbuf = outbuf + ew * OUT_WARP_BYTES;
+                // This warp's 32 x OUT_COLS block: lane = row, swizzled 32 x 8 sub-blocks.
+                uint8_t *wbuf = outbuf + ew * C::OUT_WARP_BYTES;
                 if (lane == 0) tc::bulk_wait_read();   // previous tile's store has read the buffer
                 __syncwarp();
 #pragma unroll
@@ -699,17 +831,17 @@ ozgemm_kernel(const __grid_constant__ OzGroup g) {
                 }
             } else if (row < a.M) {
                 if (a.nsuper == 1) {
-                    const int ea = a.eA[row / a.a_rpe] - FRAC;
+                    const int ear = a.eA[row / a.a_rpe] - C::FRAC;
                     double *crow = a.C + static_cast<long long>(row) * a.ldc;
 #pragma unroll
-                    for (int i = 0; i < BN / 2; i++) {
+                    for (int i = 0; i < OUT_COLS; i++) {
                         const int col = c0 + i;
-                        if (col < a.N) crow[col] = i64_to_f64_scaled(acc64[i], ea + a.eB[col / a.b_rpe]);
+                        if (col < a.N) crow[col] = i64_to_f64_scaled(acc64[i], ear + a.eB[col / a.b_rpe]);
                     }
                 } else {
                     long long *prow = a.P + tc_.z * a.pz + static_cast<long long>(row) * a.ldp;
 #pragma unroll
-                    for (int i = 0; i < BN / 2; i++) {
+                    for (int i = 0; i < OUT_COLS; i++) {
                         const int col = c0 + i;
                         if (col < a.N) prow[col] = acc64[i];
                     }
@@ -734,13 +866,13 @@ ozgemm_kernel(const __grid_constant__ OzGroup g) {
     if (threadIdx.x == 0 && *abort_flag) atomicExch(g.p[0].a.err, static_cast<int>(JK_ERR_TIMEOUT));
 }
 
-// out[r][c] (+)= sum_z P[z][r][c] 2^(eA[r/arpe][z] + eB[c/brpe][z] - 48).  The
-// partials are aligned to the largest scale by 128-bit shifts (52 guard bits:
-// a partial on a smaller scale loses only bits below 2^-52 of the largest
-// scale's unit) and summed exactly; one rounding to FP64 at the end.
+// out[r][c] (+)= sum_z P[z][r][c] 2^(eA[r/arpe][z] + eB[c/brpe][z] - frac).
+// The partials are aligned to the largest scale by 128-bit shifts (52 guard
+// bits: a partial on a smaller scale loses only bits below 2^-52 of the
+// largest scale's unit) and summed exactly; one rounding to FP64 at the end.
 __global__ void __launch_bounds__(256)
 reduce_partials_kernel(const long long *P, long long pz, long long ldp, int nz, int M, int N, const int *eA,
-                       int arpe, const int *eB, int brpe, double *out, long long ldo, int accumulate) {
+                       int arpe, const int *eB, int brpe, double *out, long long ldo, int accumulate, int frac) {
     const long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
     if (e >= static_cast<long long>(M) * N) return;
     const int r = static_cast<int>(e / N), c = static_cast<int>(e % N);
@@ -754,7 +886,7 @@ reduce_partials_kernel(const long long *P, long long pz, long long ldp, int nz, 
         const int d = emax - (ea[zz] + eb[zz]);
         if (d < 100) s += (static_cast<__int128>(P[zz * pz + off]) << 52) >> d;
     }
-    const double v = i128_to_f64_scaled(s, emax - FRAC - 52);
+    const double v = i128_to_f64_scaled(s, emax - frac - 52);
     double *o = out + static_cast<long long>(r) * ldo + c;
     *o = accumulate ? (*o + v) : v;
 }
@@ -801,15 +933,17 @@ EncodeTiledFn encode_fn() {
     return f;
 }
 
-// Tensor map over slices [S][rows][Kpad] (bf16), box = {16, box_rows, S}, 32-byte swizzle.
-// Consecutive planes lie plane_rows * Kpad elements apart (plane_rows >= rows:
-// a map over a block of rows of a larger sliced operand).
+// Tensor map over slices [planes][rows][Kpad] (bf16), box = {16, box_rows,
+// planes}, 32-byte swizzle.  Consecutive planes lie plane_rows * Kpad elements
+// apart (plane_rows >= rows: a map over a block of rows of a larger sliced
+// operand).
 jk_status make_slice_map(jk_ctx *h, CUtensorMap *map, const __nv_bfloat16 *base, int rows, int Kpad,
-                         int box_rows, long long plane_rows, int box_planes = oz::S) {
+                         int box_rows, long long plane_rows, int planes) {
     EncodeTiledFn fn = encode_fn();
     if (!fn) return set_error(h, JK_ERR_CUDA, "cuTensorMapEncodeTiled is unavailable");
+    const int box_planes = planes;
     cuuint64_t dims[3] = {static_cast<cuuint64_t>(Kpad), static_cast<cuuint64_t>(rows),
-                          static_cast<cuuint64_t>(oz::S)};
+                          static_cast<cuuint64_t>(planes)};
     cuuint64_t strides[2] = {static_cast<cuuint64_t>(Kpad) * 2, static_cast<cuuint64_t>(plane_rows) * Kpad * 2};
     cuuint32_t box[3] = {oz::KB, static_cast<cuuint32_t>(box_rows), static_cast<cuuint32_t>(box_planes)};
     cuuint32_t estr[3] = {1, 1, 1};
@@ -828,7 +962,7 @@ jk_status make_out_map(jk_ctx *h, CUtensorMap *map, void *base, long long rows, 
     if (!fn) return set_error(h, JK_ERR_CUDA, "cuTensorMapEncodeTiled is unavailable");
     cuuint64_t dims[2] = {static_cast<cuuint64_t>(cols), static_cast<cuuint64_t>(rows)};
     cuuint64_t strides[1] = {static_cast<cuuint64_t>(ld) * 8};
-    cuuint32_t box[2] = {oz::OUT_BLK, 32};
+    cuuint32_t box[2] = {static_cast<cuuint32_t>(oz::OUT_BLK), 32};
     cuuint32_t estr[2] = {1, 1};
     CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_INT64, 2, base, dims, strides, box, estr,
                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_NONE,
@@ -851,6 +985,7 @@ inline long long part_rows(long long M) { return (M + oz::BM - 1) / oz::BM * oz:
 struct Sliced {
     __nv_bfloat16 *s = nullptr;
     int *e = nullptr;
+    int S = 6;          // slices (6: 48-bit operand, 7: 56-bit)
     int rows = 0, K = 0, Kpad = 0, rpe = 1;
     int prows = 0;      // rows between consecutive planes (0: rows)
     long long plane_rows() const { return prows > 0 ? prows : rows; }
@@ -894,33 +1029,38 @@ static jk_status slice_operand(jk_ctx *h, const oz::Src &src, int rows, int K, i
         LaunchScope ls(h, KK_SLICE, st);
         if (vec) {
             dim3 grid((out.Kpad / 4 + 255) / 256, rblocks < 65535 ? rblocks : 65535);
-            if (h->slicer == 1)
-                oz::slice4f_kernel<<<grid, 256, 0, st>>>(src, rows, K, out.Kpad, out.e, rpe, nsc,
-                                                          reinterpret_cast<uint2 *>(out.s),
-                                                          static_cast<long long>(rows) * out.Kpad / 4);
+            uint2 *o4 = reinterpret_cast<uint2 *>(out.s);
+            const long long ss4 = static_cast<long long>(rows) * out.Kpad / 4;
+            if (out.S == 7)
+                oz::slice4_kernel<7><<<grid, 256, 0, st>>>(src, rows, K, out.Kpad, out.e, rpe, nsc, o4, ss4);
+            else if (h->slicer == 1)
+                oz::slice4f_kernel<<<grid, 256, 0, st>>>(src, rows, K, out.Kpad, out.e, rpe, nsc, o4, ss4);
             else
-                oz::slice4_kernel<<<grid, 256, 0, st>>>(src, rows, K, out.Kpad, out.e, rpe, nsc,
-                                                         reinterpret_cast<uint2 *>(out.s),
-                                                         static_cast<long long>(rows) * out.Kpad / 4);
+                oz::slice4_kernel<6><<<grid, 256, 0, st>>>(src, rows, K, out.Kpad, out.e, rpe, nsc, o4, ss4);
         } else {
             dim3 grid((out.Kpad + 255) / 256, rblocks < 65535 ? rblocks : 65535);
-            oz::slice_kernel<<<grid, 256, 0, st>>>(src, rows, K, out.Kpad, out.e, rpe, nsc,
-                                                    reinterpret_cast<unsigned short *>(out.s),
-                                                    static_cast<long long>(rows) * out.Kpad);
+            unsigned short *o1 = reinterpret_cast<unsigned short *>(out.s);
+            const long long ss1 = static_cast<long long>(rows) * out.Kpad;
+            if (out.S == 7)
+                oz::slice_kernel<7><<<grid, 256, 0, st>>>(src, rows, K, out.Kpad, out.e, rpe, nsc, o1, ss1);
+            else
+                oz::slice_kernel<6><<<grid, 256, 0, st>>>(src, rows, K, out.Kpad, out.e, rpe, nsc, o1, ss1);
         }
     }
     JK_LAUNCH_CHECK(h);
     return JK_OK;
 }
 
-static size_t sliced_bytes(int rows, int K, int rpe) {
+static size_t sliced_bytes(int rows, int K, int rpe, int S = 6) {
     const size_t nsc = (K + oz::SUPER - 1) / oz::SUPER;
-    return align_up(static_cast<size_t>(oz::S) * rows * kpad_of(K) * 2) +
+    return align_up(static_cast<size_t>(S) * rows * kpad_of(K) * 2) +
            align_up(static_cast<size_t>((rows + rpe - 1) / rpe) * nsc * 4);
 }
 
-static bool take_sliced(Arena &ar, int rows, int K, int rpe, Sliced &out) {
-    out.s = ar.take<__nv_bfloat16>(static_cast<size_t>(oz::S) * rows * kpad_of(K));
+// Workspace of an S-slice operand (S = 6 unless the call asks for 7).
+static bool take_sliced(Arena &ar, int rows, int K, int rpe, Sliced &out, int S = 6) {
+    out.S = S;
+    out.s = ar.take<__nv_bfloat16>(static_cast<size_t>(S) * rows * kpad_of(K));
     out.e = ar.take<int>(static_cast<size_t>((rows + rpe - 1) / rpe) * ((K + oz::SUPER - 1) / oz::SUPER));
     return out.s && out.e;
 }
@@ -932,9 +1072,14 @@ static int nsuper_of(int K) { return (K + oz::SUPER - 1) / oz::SUPER; }
 static jk_status oz_problem(jk_ctx *h, const Sliced &A, const Sliced &B, double *C, long long ldc, long long *P,
                             oz::OzProb &pr) {
     if (A.K != B.K) return set_error(h, JK_ERR_ARG, "internal: sliced K mismatch");
+    if (A.S != B.S) return set_error(h, JK_ERR_ARG, "internal: operands with different slice counts");
     std::memset(&pr, 0, sizeof pr);
-    JK_TRY(make_slice_map(h, &pr.tmA, A.s, A.rows, A.Kpad, oz::BM, A.plane_rows()));
-    JK_TRY(make_slice_map(h, &pr.tmB, B.s, B.rows, B.Kpad, oz::BN, B.plane_rows()));
+    // seven-slice operands take 64-column tiles (seven accumulators of 80
+    // columns would not fit tensor memory); six-slice ones the handle's tile width
+    pr.cfg = A.S == 7 ? oz::CFG7 : (h->cur_tile == 1 ? oz::CFG6N : oz::CFG6);
+    const int BN = oz::cfg_bn(pr.cfg);
+    JK_TRY(make_slice_map(h, &pr.tmA, A.s, A.rows, A.Kpad, oz::BM, A.plane_rows(), A.S));
+    JK_TRY(make_slice_map(h, &pr.tmB, B.s, B.rows, B.Kpad, BN, B.plane_rows(), B.S));
     oz::OzArgs &a = pr.a;
     a.M = A.rows; a.N = B.rows; a.K = A.K; a.nsuper = nsuper_of(A.K);
     a.eA = A.e; a.a_rpe = A.rpe; a.eB = B.e; a.b_rpe = B.rpe;
@@ -951,32 +1096,46 @@ static jk_status oz_problem(jk_ctx *h, const Sliced &A, const Sliced &B, double 
         JK_TRY(make_out_map(h, &pr.tmC, C, a.M, a.N, ldc));
         a.use_tma_store = 1;
     }
-    const long long ntn = (a.N + oz::BN - 1) / oz::BN, ntm = (a.M + oz::BM - 1) / oz::BM;
+    const long long ntn = (a.N + BN - 1) / BN, ntm = (a.M + oz::BM - 1) / oz::BM;
     if (ntn * ntm * a.nsuper > 0x3fffffffLL) return set_error(h, JK_ERR_SHAPE, "too many tiles");
     pr.ntn = static_cast<int>(ntn);
     pr.ntm = static_cast<int>(ntm);
-    // Issued MMA work: every tile runs all 21 slice pairs over its K-blocks.
+    // Issued MMA work: every tile runs all S(S+1)/2 slice pairs over its K-blocks.
     const double tiles = static_cast<double>(ntn) * ntm;
     double kblocks = 0.0;
     for (int zz = 0; zz < a.nsuper; zz++) {
         const int kb = (a.K - zz * oz::SUPER < oz::SUPER ? a.K - zz * oz::SUPER : oz::SUPER);
         kblocks += (kb + oz::KB - 1) / oz::KB;
     }
-    h->prof.tensor_flops += 2.0 * oz::BM * oz::BN * oz::KB * oz::NPAIRS * kblocks * tiles;
+    const int S = A.S;
+    h->prof.tensor_flops += 2.0 * oz::BM * BN * oz::KB * (S * (S + 1) / 2) * kblocks * tiles;
     return JK_OK;
 }
 
-// Launch a list of problems: persistent grid, up to MAXG problems per launch.
-static jk_status oz_launch(jk_ctx *h, const std::vector<oz::OzProb> &probs, cudaStream_t st) {
-    if (!h->gemm_smem_set) {
+template <class C>
+static jk_status oz_launch_cfg(jk_ctx *h, const oz::OzGroup &grp, int grid, int cfg, cudaStream_t st) {
+    if (!(h->gemm_smem_set & (1 << cfg))) {
         // a per-device function attribute: set once per handle (a handle is bound to one device)
-        JK_CUDA_TRY(h, cudaFuncSetAttribute(oz::ozgemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            oz::SMEM_BYTES));
-        h->gemm_smem_set = true;
+        JK_CUDA_TRY(h, cudaFuncSetAttribute(oz::ozgemm_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            C::SMEM_BYTES));
+        h->gemm_smem_set |= 1 << cfg;
     }
+    {
+        LaunchScope ls(h, KK_OZGEMM, st);
+        oz::ozgemm_kernel<C><<<grid, oz::THREADS, C::SMEM_BYTES, st>>>(grp);
+    }
+    JK_LAUNCH_CHECK(h);
+    return JK_OK;
+}
+
+// Launch a list of problems: persistent grid, up to MAXG problems of one
+// slice configuration per launch (a change of configuration starts a new one).
+static jk_status oz_launch(jk_ctx *h, const std::vector<oz::OzProb> &probs, cudaStream_t st) {
     static thread_local oz::OzGroup grp;   // ~20 KB of launch parameters, built on the host
-    for (size_t i0 = 0; i0 < probs.size(); i0 += oz::MAXG) {
-        const int np = static_cast<int>(std::min<size_t>(oz::MAXG, probs.size() - i0));
+    for (size_t i0 = 0; i0 < probs.size();) {
+        const int cfg = probs[i0].cfg;
+        int np = 0;
+        while (np < oz::MAXG && i0 + np < probs.size() && probs[i0 + np].cfg == cfg) np++;
         long long units = 0;
         for (int i = 0; i < np; i++) {
             grp.p[i] = probs[i0 + i];
@@ -988,11 +1147,10 @@ static jk_status oz_launch(jk_ctx *h, const std::vector<oz::OzProb> &probs, cuda
         grp.nunits = static_cast<int>(units);
         grp.raster = h->cur_raster;
         const int grid = static_cast<int>(units < h->num_sms ? units : h->num_sms);
-        {
-            LaunchScope ls(h, KK_OZGEMM, st);
-            oz::ozgemm_kernel<<<grid, oz::THREADS, oz::SMEM_BYTES, st>>>(grp);
-        }
-        JK_LAUNCH_CHECK(h);
+        if (cfg == oz::CFG7) JK_TRY(oz_launch_cfg<oz::Cfg7>(h, grp, grid, cfg, st));
+        else if (cfg == oz::CFG6N) JK_TRY(oz_launch_cfg<oz::Cfg6n>(h, grp, grid, cfg, st));
+        else JK_TRY(oz_launch_cfg<oz::Cfg6>(h, grp, grid, cfg, st));
+        i0 += np;
     }
     return JK_OK;
 }
@@ -1013,7 +1171,7 @@ static jk_status reduce_partials(jk_ctx *h, const long long *P, int nz, const Sl
         LaunchScope ls(h, KK_OZREDUCE, st);
         oz::reduce_partials_kernel<<<static_cast<unsigned>((tot + 255) / 256), 256, 0, st>>>(
             P, part_rows(A.rows) * ldp, ldp, nz, A.rows, B.rows, A.e, A.rpe, B.e, B.rpe, out, ldo,
-            accumulate ? 1 : 0);
+            accumulate ? 1 : 0, A.S == 7 ? oz::Cfg7::FRAC : oz::Cfg6::FRAC);
     }
     JK_LAUNCH_CHECK(h);
     return JK_OK;
@@ -1093,7 +1251,7 @@ jk_status mirror_sym_blocks(jk_ctx *h, double *K, int n, cudaStream_t st) {
 // P-chunk so that the per-chunk workspace stays below ~12 GB.
 static int split_pchunk(const Problem &pb) {
     const size_t n = pb.n;
-    size_t per = n * n * (oz::S * 2) + n * pb.ctot * 8 + n * pb.ctot * (oz::S * 2);
+    size_t per = n * n * (6 * 2) + n * pb.ctot * 8 + n * pb.ctot * (6 * 2);
     if (pb.packed) per += n * n * 8;               // the expanded factor chunk
     size_t budget = static_cast<size_t>(12) << 30;
     size_t pc = per ? budget / per : 1;
@@ -1372,7 +1530,7 @@ static jk_status gemm_into(jk_ctx *h, const Sliced &A, const Sliced &B, double *
 // and one FP64 panel row block) within ~12 GB, panel rows within the grid.
 static int dense_pchunk(const DenseProb &dp) {
     const size_t n = dp.n;
-    const size_t per = n * n * (oz::S * 2) * 3 + n * even_ld(static_cast<long long>(dp.nd) * dp.n) * 8 +
+    const size_t per = n * n * (6 * 2) * 3 + n * even_ld(static_cast<long long>(dp.nd) * dp.n) * 8 +
                        (dp.packed ? n * n * 8 : 0);     // the expanded chunk of a packed factor
     size_t pc = per ? (static_cast<size_t>(12) << 30) / per : 1;
     if (pc < 1) pc = 1;
@@ -1485,11 +1643,12 @@ jk_status split_dense(jk_ctx *h, const DenseProb &dp, cudaStream_t st) {
 // Aux-index chunk of the split adjoint so that its workspace stays near 8 GB.
 static int split_adj_pchunk(const Problem &pb) {
     const size_t n = pb.n, ctot = pb.ctot, ks3 = 3 * static_cast<size_t>(pb.ksum);
-    size_t per = n * n * 12 * 2                  // L slices: panel layout and row-mu layout
+    const size_t sb = 2 * static_cast<size_t>(pb.slices);   // bytes of one sliced element
+    size_t per = n * n * sb * 2                  // L slices: panel layout and row-mu layout
                  + n * even_ld(ctot) * 8         // T
-                 + 2 * pb.kmax * n * 12          // T_X, T_Y as B operands
-                 + 2 * n * pb.kmax * 8 + pb.kmax * n * 12 * 2   // U, Vp and their slices
-                 + n * ks3 * (8 + 12)            // AG and its slices
+                 + 2 * pb.kmax * n * sb          // T_X, T_Y as B operands
+                 + 2 * n * pb.kmax * 8 + pb.kmax * n * sb * 2   // U, Vp and their slices
+                 + n * ks3 * (8 + sb)            // AG and its slices
                  + n * n * 8 * 2                 // G, GV
                  + (pb.packed ? n * n * 8 : 0);  // the expanded chunk of a packed factor
     size_t budget = static_cast<size_t>(8) << 30;
@@ -1522,6 +1681,7 @@ static size_t adj_partials(const Problem &pb, int pc) {
 
 static bool adj_take(Arena &ar, const Problem &pb, int pc, bool W, bool V, bool dl, AdjBufs &b) {
     const int n = pb.n, nd = pb.nd, kmax = pb.kmax, ks3 = 3 * pb.ksum;
+    const int S = pb.slices;   // every product of the adjoint on S-slice operands
     const long long n2 = static_cast<long long>(n) * n;
     bool ok = true;
     auto tk = [&](auto *&ptr, size_t cnt) {
@@ -1543,14 +1703,15 @@ static bool adj_take(Arena &ar, const Problem &pb, int pc, bool W, bool V, bool 
     tk(b.tmp, static_cast<size_t>(n) * std::max(kmax, 1));
     tk(b.P, adj_partials(pb, pc));
     if (pb.packed) tk(b.Lx, static_cast<size_t>(pc) * n2);
-    ok = ok && take_sliced(ar, pb.ctot, n, 1, b.Zs) && take_sliced(ar, pc * n, n, n, b.Ls) &&
-         take_sliced(ar, n, pc * n, 1, b.Lm);
+    ok = ok && take_sliced(ar, pb.ctot, n, 1, b.Zs, S) && take_sliced(ar, pc * n, n, n, b.Ls, S) &&
+         take_sliced(ar, n, pc * n, 1, b.Lm, S);
     for (int s = 0; ok && W && s < nd; s++)
-        ok = take_sliced(ar, n, n, 1, b.Ws[s]) && take_sliced(ar, n, n, 1, b.WTs[s]);
-    ok = ok && take_sliced(ar, pc * kmax, n, 1, b.TXb) && take_sliced(ar, pc * kmax, n, 1, b.TYb) &&
-         take_sliced(ar, kmax, pc * n, 1, b.Ub) && take_sliced(ar, kmax, pc * n, 1, b.Vpb);
-    if (ok && dl) ok = take_sliced(ar, pc * n, ks3, 1, b.AGs) && take_sliced(ar, n, ks3, 1, b.BGs);
-    if (ok && dl && V) ok = take_sliced(ar, pc, nd, 1, b.Gam) && take_sliced(ar, static_cast<int>(n2), nd, 1, b.Vs);
+        ok = take_sliced(ar, n, n, 1, b.Ws[s], S) && take_sliced(ar, n, n, 1, b.WTs[s], S);
+    ok = ok && take_sliced(ar, pc * kmax, n, 1, b.TXb, S) && take_sliced(ar, pc * kmax, n, 1, b.TYb, S) &&
+         take_sliced(ar, kmax, pc * n, 1, b.Ub, S) && take_sliced(ar, kmax, pc * n, 1, b.Vpb, S);
+    if (ok && dl) ok = take_sliced(ar, pc * n, ks3, 1, b.AGs, S) && take_sliced(ar, n, ks3, 1, b.BGs, S);
+    if (ok && dl && V)
+        ok = take_sliced(ar, pc, nd, 1, b.Gam, S) && take_sliced(ar, static_cast<int>(n2), nd, 1, b.Vs, S);
     return ok;
 }
 
@@ -1946,18 +2107,20 @@ jk_status split_adjoint(jk_ctx *h, const Problem &pb, const double *W, const dou
 // ---------------------------------------------------------------------------
 // Test hook: the sliced tensor-core GEMM on its own (see include/jk_debug.h).
 // ---------------------------------------------------------------------------
-extern "C" jk_status jk_debug_sliced_gemm(jk_handle h, int32_t M, int32_t N, int32_t K, const double *A,
-                                          const double *B, double *C, void *stream) {
-    using namespace jk;
+namespace jk {
+// C = A B^T through the split path with S-slice operands (the test hooks below).
+static jk_status debug_sliced_gemm(jk_handle h, int M, int N, int K, const double *A, const double *B, double *C,
+                                   int S, cudaStream_t st) {
     if (!h) return JK_ERR_ARG;
     if (M < 1 || N < 1 || K < 1) return set_error(h, JK_ERR_SHAPE, "M, N, K must be >= 1");
     if (!A || !B || !C) return set_error(h, JK_ERR_ARG, "NULL operand");
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (S != 6 && S != 7) return set_error(h, JK_ERR_ARG, "slices must be 6 or 7");
     h->arena.reset(align_up(sizeof(DeviceFlags)));
-    // tile order: the handle's explicit option, else the default
+    // tile order and width: the handle's explicit options, else the defaults
     h->cur_raster = h->raster >= 0 ? h->raster : 0;
+    h->cur_tile = h->tile >= 0 ? h->tile : 0;
     Sliced As, Bs;
-    if (!take_sliced(h->arena, M, K, 1, As) || !take_sliced(h->arena, N, K, 1, Bs))
+    if (!take_sliced(h->arena, M, K, 1, As, S) || !take_sliced(h->arena, N, K, 1, Bs, S))
         return set_error(h, JK_ERR_OOM, "workspace too small");
     const int ns = nsuper_of(K);
     long long *P = nullptr;
@@ -1973,12 +2136,30 @@ extern "C" jk_status jk_debug_sliced_gemm(jk_handle h, int32_t M, int32_t N, int
     return reduce_partials(h, P, ns, As, Bs, C, N, false, st);
 }
 
-extern "C" size_t jk_debug_sliced_gemm_workspace(int32_t M, int32_t N, int32_t K) {
-    using namespace jk;
-    size_t b = align_up(sizeof(DeviceFlags)) + sliced_bytes(M, K, 1) + sliced_bytes(N, K, 1);
+static size_t debug_sliced_gemm_workspace(int M, int N, int K, int S) {
+    size_t b = align_up(sizeof(DeviceFlags)) + sliced_bytes(M, K, 1, S) + sliced_bytes(N, K, 1, S);
     const int ns = nsuper_of(K);
     if (ns > 1) b += align_up(static_cast<size_t>(ns) * part_rows(M) * even_ld(N) * 8);
     return b + kArenaAlign;
+}
+}  // namespace jk
+
+extern "C" jk_status jk_debug_sliced_gemm(jk_handle h, int32_t M, int32_t N, int32_t K, const double *A,
+                                          const double *B, double *C, void *stream) {
+    return jk::debug_sliced_gemm(h, M, N, K, A, B, C, 6, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" size_t jk_debug_sliced_gemm_workspace(int32_t M, int32_t N, int32_t K) {
+    return jk::debug_sliced_gemm_workspace(M, N, K, 6);
+}
+
+extern "C" jk_status jk_debug_sliced_gemm_slices(jk_handle h, int32_t M, int32_t N, int32_t K, const double *A,
+                                                 const double *B, double *C, int32_t slices, void *stream) {
+    return jk::debug_sliced_gemm(h, M, N, K, A, B, C, slices, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" size_t jk_debug_sliced_gemm_workspace_slices(int32_t M, int32_t N, int32_t K, int32_t slices) {
+    return jk::debug_sliced_gemm_workspace(M, N, K, slices == 7 ? 7 : 6);
 }
 
 namespace jk {

@@ -28,7 +28,8 @@ std::map<TuneKey, Entry> g_cache;
 int ceil_div(long long x, int q) { return static_cast<int>((x + q - 1) / q); }
 
 bool valid_cfg(const jk_tune_config &c) {
-    return c.aux_chunk >= 0 && (c.schedule == 0 || c.schedule == 1) && (c.raster == 0 || c.raster == 1);
+    return c.aux_chunk >= 0 && (c.schedule == 0 || c.schedule == 1) && (c.raster == 0 || c.raster == 1) &&
+           (c.tile == 0 || c.tile == 1);
 }
 
 }  // namespace
@@ -88,9 +89,9 @@ jk_status jk_tune_export(char *buf, size_t cap, size_t *len) {
         for (const auto &kv : g_cache) {
             const TuneKey &k = kv.first;
             const Entry &e = kv.second;
-            std::snprintf(line, sizeof line, "jk-tune 3 %d %d %d %d %d %d %d %d %d %d %d %.6f\n", k.op,
+            std::snprintf(line, sizeof line, "jk-tune 4 %d %d %d %d %d %d %d %d %d %d %d %d %.6f\n", k.op,
                           k.prec, k.sms, k.nmol, k.nb, k.nauxb, k.nd, k.ksumb, e.cfg.aux_chunk, e.cfg.schedule,
-                          e.cfg.raster, e.ms);
+                          e.cfg.raster, e.cfg.tile, e.ms);
             out += line;
         }
     }
@@ -117,10 +118,10 @@ jk_status jk_tune_import(const char *text) {
         jk_tune_config c{};
         int ver = 0, used = 0;
         double ms = 0.0;
-        const int got = std::sscanf(line.c_str(),  " jk-tune %d %d %d %d %d %d %d %d %d %d %d %d %lf %n", &ver,
+        const int got = std::sscanf(line.c_str(),  " jk-tune %d %d %d %d %d %d %d %d %d %d %d %d %d %lf %n", &ver,
                                     &k.op, &k.prec, &k.sms, &k.nmol, &k.nb, &k.nauxb, &k.nd, &k.ksumb,
-                                    &c.aux_chunk, &c.schedule, &c.raster, &ms, &used);
-        if (got != 13 || ver != 3 || static_cast<size_t>(used) != line.size() || !valid_cfg(c) ||
+                                    &c.aux_chunk, &c.schedule, &c.raster, &c.tile, &ms, &used);
+        if (got != 14 || ver != 4 || static_cast<size_t>(used) != line.size() || !valid_cfg(c) ||
             !std::isfinite(ms))
             return JK_ERR_ARG;
         tune_store(k, c, ms);

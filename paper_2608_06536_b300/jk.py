@@ -34,17 +34,17 @@ class jk_density(ct.Structure):
 
 
 class jk_tune_config(ct.Structure):
-    _fields_ = [("aux_chunk", ct.c_int32), ("schedule", ct.c_int32), ("raster", ct.c_int32)]
+    _fields_ = [("aux_chunk", ct.c_int32), ("schedule", ct.c_int32), ("raster", ct.c_int32), ("tile", ct.c_int32)]
 
     def as_dict(self) -> dict:
-        return {"aux_chunk": self.aux_chunk, "schedule": self.schedule, "raster": self.raster}
+        return {"aux_chunk": self.aux_chunk, "schedule": self.schedule, "raster": self.raster, "tile": self.tile}
 
 
 OPTIONS = {"aux_chunk": 0, "schedule": 1, "raster": 2, "use_tuned": 3, "host_chunk": 5, "slicer": 6,
-           "syrk": 7, "packed_factor": 8}
+           "syrk": 7, "packed_factor": 8, "tile": 9, "adjoint_slices": 10}
 # each option's value on a fresh handle (-1: not set, tuned or default configuration)
 OPTION_DEFAULTS = {"aux_chunk": -1, "schedule": -1, "raster": -1, "use_tuned": 1, "host_chunk": 0,
-                   "slicer": 0, "syrk": 0, "packed_factor": 0}
+                   "slicer": 0, "syrk": 0, "packed_factor": 0, "tile": -1, "adjoint_slices": 7}
 
 
 class JKError(RuntimeError):
@@ -363,14 +363,16 @@ class Engine:
     # -- options ---------------------------------------------------------------
     def set_option(self, name: str, value: int):
         """Handle option (JK_OPT_*): "aux_chunk" (>= 0, 0 = automatic, -1 =
-        tuned/default), "schedule" and "raster" (-1 = tuned/default,
+        tuned/default), "schedule", "raster" and "tile" (-1 = tuned/default,
         0, 1), "use_tuned" (0 or 1), "host_chunk" (>= 0, 0 = automatic),
         "slicer" (0 integer digits, 1 FP32 digits), "syrk" (symmetric
         densities, both engines: 0 full rank update, 1 blocked symmetric rank
         update with the rest mirrored), "packed_factor" (1: the factor given
         to every device call (build, build_batched, adjoint, build_dense,
         density_grad, pairs, build_laplace, autotune*) is pack_factor(L),
-        [naux][n(n+1)/2] on the device; half the memory).
+        [naux][n(n+1)/2] on the device; half the memory), "tile" (0: sliced
+        GEMM tiles of 128 x 80 outputs, 1: 128 x 64), "adjoint_slices" (6 or
+        7, default 7: BF16 slices per operand of the split adjoint's products).
         Kept across arena growth."""
         code = OPTIONS[name]
         self._opts[code] = int(value)

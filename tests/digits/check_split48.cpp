@@ -6,6 +6,7 @@
 //   value (the low 16 bits of its FP32 word are zero).
 //   digits6 + qbf16: the same bounds and exact sum for the integer digits,
 //   and qbf16(q_j, 2^-8(j+1)) is the BF16 encoding of q_j * 2^-8(j+1).
+//   digits_n<7>: the same for seven digits of 56-bit values.
 // Prints "ok <count>" and exits 0, or the first violation and exits 1.
 #include <cmath>
 #include <cstdint>
@@ -64,6 +65,35 @@ static int check(long long F) {
     return 0;
 }
 
+// The seven-digit split of a 56-bit value: exact sum, digit bounds, and
+// exact BF16 encodings down to the last slice's scale 2^-56.
+static int check7(long long F) {
+    int q[7];
+    jk::digits::digits_n<7>(F, q);
+    __int128 sum = 0;
+    float sc = 0.00390625f;
+    for (int j = 0; j < 7; j++) {
+        if (q[j] > (j == 0 ? 256 : 127) || q[j] < (j == 0 ? -256 : -128)) {
+            std::printf("F=%lld: seven-slice digit %d = %d out of range\n", F, j, q[j]);
+            return 1;
+        }
+        const uint32_t w = jk::digits::qbf16(q[j], sc) << 16;
+        float back;
+        std::memcpy(&back, &w, 4);
+        if (static_cast<double>(back) != std::ldexp(static_cast<double>(q[j]), -8 * (j + 1))) {
+            std::printf("F=%lld: qbf16(%d) of seven-slice digit %d is %a\n", F, q[j], j, back);
+            return 1;
+        }
+        sum += static_cast<__int128>(q[j]) << (8 * (6 - j));
+        sc *= 0.00390625f;
+    }
+    if (sum != static_cast<__int128>(F)) {
+        std::printf("F=%lld: seven digits sum to %lld\n", F, static_cast<long long>(sum));
+        return 1;
+    }
+    return 0;
+}
+
 int main() {
     const long long T = 1ll << 48;
     long long n = 0;
@@ -91,6 +121,20 @@ int main() {
         if (i & 1) F = (F & ~0xFFll) | 0x80;                     // a tie in the lowest digit
         if ((i & 7) == 2) F = static_cast<long long>(rng() % 4096) - 2048;   // small magnitudes
         if (check(F)) return 1;
+        n++;
+    }
+    // the seven-digit split over 56-bit values
+    const long long T7 = 1ll << 56;
+    for (long long F : {0ll, 1ll, -1ll, 128ll, -128ll, 0x80ll, T7, -T7, T7 - 1, -T7 + 1, 0x80808080808080ll,
+                        -0x80808080808080ll, 0x7F7F7F7F7F7F7Fll, (T7 >> 1) + 0x808080ll}) {
+        if (check7(F)) return 1;
+        n++;
+    }
+    for (int i = 0; i < 2000000; i++) {
+        long long F = static_cast<long long>(rng() % (2 * static_cast<unsigned long long>(T7) + 1)) - T7;
+        if (i & 1) F = (F & ~0xFFll) | 0x80;
+        if ((i & 7) == 2) F = static_cast<long long>(rng() % 4096) - 2048;
+        if (check7(F)) return 1;
         n++;
     }
     std::printf("ok %lld\n", n);

@@ -23,7 +23,7 @@ class jk_density(ct.Structure):
 
 
 class jk_tune_config(ct.Structure):
-    _fields_ = [("aux_chunk", ct.c_int32), ("schedule", ct.c_int32), ("raster", ct.c_int32)]
+    _fields_ = [("aux_chunk", ct.c_int32), ("schedule", ct.c_int32), ("raster", ct.c_int32), ("tile", ct.c_int32)]
 
 
 _lib = ct.CDLL(os.path.join(ROOT, "paper_2608_06536_b300", "libjk.so"))
@@ -72,14 +72,19 @@ shim.shim_launch.restype = ct.c_char_p
 assert hasattr(shim, "shim_reset"), "the stand-in runtime is not the one loaded"
 
 OPT = {"aux_chunk": 0, "schedule": 1, "raster": 2, "use_tuned": 3, "host_chunk": 5, "slicer": 6,
-       "syrk": 7, "packed_factor": 8}
+       "syrk": 7, "packed_factor": 8, "tile": 9, "adjoint_slices": 10}
 
 # ---- kernel arguments ----------------------------------------------------------
 # Each decoder reads one kernel's arguments (layouts as in the CUDA sources)
 # and returns the byte ranges [lo, hi) its pointer arguments can touch, from
 # the kernel's own index bounds; every range must lie in memory the call owns.
 VP, I32, I64, F64 = ct.c_void_p, ct.c_int32, ct.c_int64, ct.c_double
-SUPER, NSLICE, MAXD = 2048, 6, 64
+SUPER, MAXD = 2048, 64
+
+
+def _slices_of(name):
+    """Slices per operand of a slicer launch, from its template argument."""
+    return 7 if "ILi7E" in name else 6
 
 
 class Src(ct.Structure):
@@ -109,14 +114,16 @@ class OzArgs(ct.Structure):
 
 
 class OzTail(ct.Structure):
-    _fields_ = [("tile0", I32), ("ntn", I32), ("ntm", I32)]
+    _fields_ = [("tile0", I32), ("ntn", I32), ("ntm", I32), ("cfg", I32)]
 
 
 # one problem of a grouped launch: three 128-byte tensor maps (A, B, C), its
 # arguments, its tile counts; 64-byte aligned (the maps' alignment)
 OZ_ARGS_OFF = 3 * 128
 OZ_PROB_BYTES = (OZ_ARGS_OFF + ct.sizeof(OzArgs) + ct.sizeof(OzTail) + 63) // 64 * 64
-OZ_BM, OZ_BN = 128, 80
+OZ_BM = 128
+# slice configurations of the sliced GEMM: id -> (slices, tile width, fraction bits)
+OZ_CFG = {0: (6, 80, 48), 1: (6, 64, 48), 2: (7, 64, 51)}
 
 
 def _a(args, i, t):
@@ -162,23 +169,23 @@ def dec_expo_flat(grid, args):
     return [(p, p + 8 * grid[0] * ln, "p"), (e, e + 4 * grid[0], "e")]
 
 
-def _slice(grid, args, esize_out, per):
+def _slice(grid, args, esize_out, per, nslice):
     src, rows, K, Kpad = _a(args, 0, Src), _v(args, 1, I32), _v(args, 2, I32), _v(args, 3, I32)
     e, rpe, nsc, out, ss = _v(args, 4, VP), _v(args, 5, I32), _v(args, 6, I32), _v(args, 7, VP), _v(args, 8, I64)
     assert grid[0] * 256 * per >= Kpad and Kpad % 16 == 0 and K <= Kpad
     ne = ((rows - 1) // rpe) * nsc + (K - 1) // SUPER + 1
-    nout = (NSLICE - 1) * ss + (rows * Kpad) // per
+    nout = (nslice - 1) * ss + (rows * Kpad) // per
     return [_src_range(src, rows, K), (e, e + 4 * ne, "e"), (out, out + esize_out * nout, "slices")]
 
 
-def dec_slice(grid, args):
-    return _slice(grid, args, 2, 1)
+def dec_slice(grid, args, name):
+    return _slice(grid, args, 2, 1, _slices_of(name))
 
 
-def dec_slice4(grid, args):
+def dec_slice4(grid, args, name):
     src = _a(args, 0, Src)
     assert src.ski == 1 and src.kin % 4 == 0 and _v(args, 2, I32) % 4 == 0 and src.p % 16 == 0
-    return _slice(grid, args, 8, 4)
+    return _slice(grid, args, 8, 4, _slices_of(name))
 
 
 def dec_dgemm(grid, args):
@@ -377,7 +384,9 @@ def dec_ozgemm(grid, args):
         assert t.tile0 == units, (t.tile0, units)
         units += t.ntn * t.ntm * a.nsuper
         assert a.M >= 1 and a.N >= 1 and a.K >= 1 and a.nsuper == (a.K + SUPER - 1) // SUPER
-        assert t.ntm == (a.M + OZ_BM - 1) // OZ_BM and t.ntn == (a.N + OZ_BN - 1) // OZ_BN
+        assert t.cfg in OZ_CFG, t.cfg
+        bn = OZ_CFG[t.cfg][1]
+        assert t.ntm == (a.M + OZ_BM - 1) // OZ_BM and t.ntn == (a.N + bn - 1) // bn
         nsc = a.nsuper
         res.append((a.eA, a.eA + 4 * ((a.M - 1) // a.a_rpe + 1) * nsc, "eA"))
         res.append((a.eB, a.eB + 4 * ((a.N - 1) // a.b_rpe + 1) * nsc, "eB"))
@@ -626,35 +635,35 @@ def ex_expo_flat(grid, args):
     uv(e, grid[0], np.int32)[:] = _expo_of(X.max(axis=1))
 
 
-def _digits_bf16(x, e):
-    """The six BF16 slice words of x at exponent e (integer balanced digits)."""
-    F = np.sign(x) * np.floor(np.abs(x) * np.exp2(48.0 - e) + 0.5)
-    F = F.astype(np.int64)
-    lo = F & 0xFFFFFF
-    hi = F >> 24
-    q = [None] * 6
-    for j in (5, 4, 3):
-        q[j] = ((lo + 128) & 255) - 128
-        lo = (lo - q[j]) >> 8
-    hi = hi + lo
-    for j in (2, 1):
-        q[j] = ((hi + 128) & 255) - 128
-        hi = (hi - q[j]) >> 8
-    q[0] = hi
+def _digits_bf16(x, e, nslice=6):
+    """The nslice BF16 slice words of x at exponent e (integer balanced
+    digits of the 8 * nslice-bit fixed-point value)."""
+    bits = 8 * nslice
+    xs = np.abs(x) * np.exp2(bits - e.astype(np.float64))
+    # the fixed-point value, rounded half away from zero; beyond 2^53 the
+    # product is an exact integer already (a double's significand)
+    F = np.where(xs < 2.0 ** 52, np.floor(xs + 0.5), xs)
+    F = (np.sign(x) * F).astype(np.int64)
+    q = [None] * nslice
+    for j in range(nslice - 1, 0, -1):
+        q[j] = ((F + 128) & 255) - 128
+        F = (F - q[j]) >> 8
+    q[0] = F
     return [((q[j].astype(np.float64) * 2.0 ** (-8 * (j + 1))).astype(np.float32).view(np.uint32) >> 16)
-            .astype(np.uint16) for j in range(6)]
+            .astype(np.uint16) for j in range(nslice)]
 
 
-def ex_slice(grid, args):
+def ex_slice(grid, args, name):
     src, rows, K, Kpad = _a(args, 0, Src), _v(args, 1, I32), _v(args, 2, I32), _v(args, 3, I32)
     e, rpe, nsc, out = _v(args, 4, VP), _v(args, 5, I32), _v(args, 6, I32), _v(args, 7, VP)
+    nslice = _slices_of(name)
     X = _src_gather(src, rows, K)
     ev = uv(e, ((rows - 1) // rpe + 1) * nsc, np.int32)
     E = ev[(np.arange(rows)[:, None] // rpe) * nsc + np.arange(K)[None, :] // SUPER]
-    planes = _digits_bf16(X, E)
-    o = uv(out, NSLICE * rows * Kpad, np.uint16).reshape(NSLICE, rows, Kpad)
+    planes = _digits_bf16(X, E, nslice)
+    o = uv(out, nslice * rows * Kpad, np.uint16).reshape(nslice, rows, Kpad)
     o[:] = 0
-    for j in range(NSLICE):
+    for j in range(nslice):
         o[j, :, :K] = planes[j]
 
 
@@ -670,10 +679,11 @@ def _operand(tm, e, rpe, rows, K, nsuper):
     the exponents [rows][nsuper]."""
     Kpad, nrows = tm["dims"][0], tm["dims"][1]
     assert tm["strides"][1] == 2 * Kpad, tm
+    nslice = tm["dims"][2]                       # one plane per slice
     pstride = tm["strides"][2] // 2              # elements between planes (a row view keeps its parent's)
-    flat = uv(tm["base"], (NSLICE - 1) * pstride + nrows * Kpad, np.uint16)
+    flat = uv(tm["base"], (nslice - 1) * pstride + nrows * Kpad, np.uint16)
     vals = np.zeros((rows, K))
-    for j in range(NSLICE):
+    for j in range(nslice):
         plane = flat[j * pstride:j * pstride + nrows * Kpad].reshape(nrows, Kpad)[:rows, :K]
         vals += (plane.astype(np.uint32) << 16).view(np.float32).astype(np.float64)
     ev = uv(e, ((rows - 1) // rpe + 1) * nsuper, np.int32).reshape(-1, nsuper)[np.arange(rows) // rpe]
@@ -686,7 +696,10 @@ def ex_ozgemm(grid, args):
     for i in range(nprob):
         pb = base + i * OZ_PROB_BYTES
         a = OzArgs.from_address(pb + OZ_ARGS_OFF)
+        t = OzTail.from_address(pb + OZ_ARGS_OFF + ct.sizeof(OzArgs))
+        frac = OZ_CFG[t.cfg][2]
         tA, tB = _tmap(pb), _tmap(pb + 128)
+        assert tA["dims"][2] == tB["dims"][2] == OZ_CFG[t.cfg][0]
         A, eA = _operand(tA, a.eA, a.a_rpe, a.M, a.K, a.nsuper)
         B, eB = _operand(tB, a.eB, a.b_rpe, a.N, a.K, a.nsuper)
         for z in range(a.nsuper):
@@ -696,21 +709,22 @@ def ex_ozgemm(grid, args):
                 dv(a.C, int(idx.max()) + 1)[idx] = np.ldexp(S, eA[:, z:z + 1] + eB[:, z][None, :])
             else:
                 idx = z * a.pz + np.arange(a.M)[:, None] * a.ldp + np.arange(a.N)[None, :]
-                uv(a.P, int(idx.max()) + 1, np.int64)[idx] = np.rint(S * 2.0 ** 48).astype(np.int64)
+                uv(a.P, int(idx.max()) + 1, np.int64)[idx] = np.rint(S * 2.0 ** frac).astype(np.int64)
 
 
 def ex_reduce(grid, args):
     P, pz, ldp, nz, M, N = (_v(args, 0, VP), _v(args, 1, I64), _v(args, 2, I64), _v(args, 3, I32),
                             _v(args, 4, I32), _v(args, 5, I32))
-    eA, arpe, eB, brpe, out, ldo, acc = (_v(args, 6, VP), _v(args, 7, I32), _v(args, 8, VP), _v(args, 9, I32),
-                                         _v(args, 10, VP), _v(args, 11, I64), _v(args, 12, I32))
+    eA, arpe, eB, brpe, out, ldo, acc, frac = (_v(args, 6, VP), _v(args, 7, I32), _v(args, 8, VP), _v(args, 9, I32),
+                                               _v(args, 10, VP), _v(args, 11, I64), _v(args, 12, I32),
+                                               _v(args, 13, I32))
     ea = uv(eA, ((M - 1) // arpe + 1) * nz, np.int32).reshape(-1, nz)[np.arange(M) // arpe]
     eb = uv(eB, ((N - 1) // brpe + 1) * nz, np.int32).reshape(-1, nz)[np.arange(N) // brpe]
     tot = np.zeros((M, N))
     for z in range(nz):
         idx = z * pz + np.arange(M)[:, None] * ldp + np.arange(N)[None, :]
         Pz = uv(P, int(idx.max()) + 1, np.int64)[idx].astype(np.float64)
-        tot += np.ldexp(Pz, ea[:, z:z + 1] + eb[:, z][None, :] - 48)
+        tot += np.ldexp(Pz, ea[:, z:z + 1] + eb[:, z][None, :] - frac)
     oidx = np.arange(M)[:, None] * ldo + np.arange(N)[None, :]
     o = dv(out, int(oidx.max()) + 1)
     o[oidx] = (o[oidx] if acc else 0.0) + tot
@@ -806,7 +820,7 @@ def on_launch(name, grid, block, args):
     for key, fn in DECODERS:
         if key in name:
             try:
-                ranges = fn(g, args, name) if fn is dec_jstream_sym else fn(g, args)
+                ranges = fn(g, args, name) if fn in (dec_jstream_sym, dec_slice, dec_slice4) else fn(g, args)
             except AssertionError as e:
                 violations.append(f"{key}: inconsistent arguments {e}")
                 return
@@ -819,7 +833,7 @@ def on_launch(name, grid, block, args):
             if EXEC[0] and not bad:
                 for ekey, ex in EXECUTORS:
                     if ekey in name:
-                        ex(g, args, name) if ex is ex_jstream_sym else ex(g, args)
+                        ex(g, args, name) if ex in (ex_jstream_sym, ex_slice) else ex(g, args)
                         break
             return
     undecoded.add(name)

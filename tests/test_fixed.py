@@ -138,6 +138,45 @@ def test_to_fixed48_rounds_to_nearest_and_stays_within_48_bits(exe):
         assert abs(F) <= 1 << 48
 
 
+def _fixed_ref(x, e, nbits):
+    if x == 0 or abs(x) < 2.0 ** -1022:
+        return 0
+    y = abs(Fraction(x) * Fraction(2) ** (nbits - e))
+    q = int(y + Fraction(1, 2))
+    return -q if x < 0 else q
+
+
+def test_to_fixed_56_bits(exe):
+    """The 56-bit form of the seven-slice operands: more bits than a double
+    carries, so values near the scale are shifted left (exactly) and small
+    ones rounded; |F| <= 2^56."""
+    rng = random.Random(17)
+    cases = []
+    for _ in range(20000):
+        e = rng.randint(-300, 300)
+        x = math.ldexp(rng.uniform(-1.0, 1.0), e) * (1 - 2 ** -53)
+        if rng.random() < 0.3:
+            x = math.ldexp(x, -rng.randint(0, 90))
+        cases.append((x, e))
+    for e in (0, 9):
+        for b in range(0, 57):
+            m = (rng.getrandbits(b) << 1) | 1
+            for x in (math.ldexp(m, e - 57), -math.ldexp(m, e - 57)):
+                if abs(x) < 2.0 ** e:
+                    cases.append((x, e))
+        cases += [(0.0, e), (5e-324, e), (math.ldexp(1.0, e) * (1 - 2 ** -53), e)]
+    got = _run(exe, [f"fxn 56 {_bits(x):016x} {e}" for x, e in cases])
+    for (x, e), g in zip(cases, got):
+        F = int(g, 16)
+        F = F - (1 << 64) if F >> 63 else F
+        assert F == _fixed_ref(x, e, 56), (x, e, F)
+        assert abs(F) <= 1 << 56
+    # the 48-bit form is the same function at nbits = 48
+    got48 = _run(exe, [f"fxn 48 {_bits(x):016x} {e}" for x, e in cases[:2000]])
+    got_fx = _run(exe, [f"fx {_bits(x):016x} {e}" for x, e in cases[:2000]])
+    assert got48 == got_fx
+
+
 def test_exponent_of_max_bounds_the_group(exe):
     rng = random.Random(14)
     xs = [math.ldexp(rng.uniform(0.5, 1.0), rng.randint(-1020, 1020)) for _ in range(20000)]

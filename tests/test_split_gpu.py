@@ -23,20 +23,28 @@ def dbg():
     lib.jk_debug_sliced_gemm_workspace.argtypes = [ct.c_int32, ct.c_int32, ct.c_int32]
     lib.jk_debug_sliced_gemm_workspace.restype = ct.c_size_t
     lib.jk_set_option.argtypes = [ct.c_void_p, ct.c_int, ct.c_int64]
+    lib.jk_debug_sliced_gemm_slices.argtypes = [ct.c_void_p, ct.c_int32, ct.c_int32, ct.c_int32, ct.c_void_p,
+                                                ct.c_void_p, ct.c_void_p, ct.c_int32, ct.c_void_p]
+    lib.jk_debug_sliced_gemm_slices.restype = ct.c_int
+    lib.jk_debug_sliced_gemm_workspace_slices.argtypes = [ct.c_int32, ct.c_int32, ct.c_int32, ct.c_int32]
+    lib.jk_debug_sliced_gemm_workspace_slices.restype = ct.c_size_t
     return lib
 
 
-def sliced_gemm(lib, A, B, raster=-1):
+def sliced_gemm(lib, A, B, raster=-1, slices=6, tile=-1):
     M, K = A.shape
     N = B.shape[0]
-    ws = torch.empty(lib.jk_debug_sliced_gemm_workspace(M, N, K), dtype=torch.uint8, device="cuda")
+    ws = torch.empty(lib.jk_debug_sliced_gemm_workspace_slices(M, N, K, slices), dtype=torch.uint8, device="cuda")
     h = ct.c_void_p()
     assert lib.jk_create(ct.byref(h), ct.c_void_p(ws.data_ptr()), ws.numel()) == 0
-    assert lib.jk_set_option(h, 2, raster) == 0
+    assert lib.jk_set_option(h, 2, raster) == 0 and lib.jk_set_option(h, 9, tile) == 0
     Ad = torch.from_numpy(np.ascontiguousarray(A)).cuda()
     Bd = torch.from_numpy(np.ascontiguousarray(B)).cuda()
     C = torch.full((M, N), float("nan"), dtype=torch.float64, device="cuda")
-    st = lib.jk_debug_sliced_gemm(h, M, N, K, Ad.data_ptr(), Bd.data_ptr(), C.data_ptr(), None)
+    if slices == 6 and tile == -1:
+        st = lib.jk_debug_sliced_gemm(h, M, N, K, Ad.data_ptr(), Bd.data_ptr(), C.data_ptr(), None)
+    else:
+        st = lib.jk_debug_sliced_gemm_slices(h, M, N, K, Ad.data_ptr(), Bd.data_ptr(), C.data_ptr(), slices, None)
     assert st == 0, lib.jk_last_error(h)
     assert lib.jk_sync_status(h, None) == 0, lib.jk_last_error(h)
     lib.jk_destroy(h)
@@ -95,6 +103,49 @@ def test_sliced_gemm_integers_exact(dbg):
     C = sliced_gemm(dbg, A, B)
     ref = (A.astype(np.int64) @ B.T.astype(np.int64)).astype(np.float64)
     np.testing.assert_array_equal(C, ref)
+
+
+# Seven slices (56-bit operands, 28 slice pairs, exact windows on diagonals
+# 0-4) and six slices on 64-column tiles: the configurations of the split
+# adjoint and of the tile-width tuning candidate.
+@pytest.mark.parametrize("slices,tile,bound", [(7, -1, 2.0 ** -50), (6, 1, 2.0 ** -44)])
+@pytest.mark.parametrize("M,N,K", [(1, 1, 1), (129, 257, 2047), (300, 65, 500), (140, 130, 5000)])
+def test_sliced_gemm_configurations(dbg, M, N, K, slices, tile, bound):
+    rng = np.random.default_rng(M * 7 + N + K)
+    A = rng.standard_normal((M, K)) * np.exp(-np.arange(K) / 3000.0)
+    B = rng.standard_normal((N, K))
+    C = sliced_gemm(dbg, A, B, slices=slices, tile=tile)
+    ref = exact_product(A, B)
+    assert np.all(np.isfinite(C))
+    scale = np.abs(A).max(1)[:, None] * np.abs(B).max(1)[None, :] * np.sqrt(K)
+    assert float(np.max(np.abs(C - ref) / scale)) < bound
+
+
+@pytest.mark.parametrize("slices,tile", [(7, -1), (6, 1)])
+def test_sliced_gemm_configurations_integers_exact(dbg, slices, tile):
+    """Integer operands are exact in both configurations (every exact window,
+    diagonal 4 of the seven-slice split included, stays exact in FP32)."""
+    rng = np.random.default_rng(13)
+    M, N, K = 256, 130, 1024
+    A = rng.integers(-1000, 1001, (M, K)).astype(np.float64)
+    B = rng.integers(-1000, 1001, (N, K)).astype(np.float64)
+    A[:, :64] = 1000.0
+    B[:, :64] = 1000.0
+    for raster in (0, 1):
+        C = sliced_gemm(dbg, A, B, raster=raster, slices=slices, tile=tile)
+        np.testing.assert_array_equal(C, (A.astype(np.int64) @ B.T.astype(np.int64)).astype(np.float64))
+
+
+def test_seven_slices_are_more_accurate(dbg):
+    """On the same random product the 56-bit operands leave at least 16x less
+    error than the 48-bit ones (the reason the split adjoint uses them)."""
+    rng = np.random.default_rng(21)
+    A = rng.standard_normal((200, 3000))
+    B = rng.standard_normal((150, 3000))
+    ref = exact_product(A, B)
+    e6 = float(np.max(np.abs(sliced_gemm(dbg, A, B, slices=6) - ref)))
+    e7 = float(np.max(np.abs(sliced_gemm(dbg, A, B, slices=7) - ref)))
+    assert e7 * 16 < e6, (e6, e7)
 
 
 @pytest.fixture(scope="module")

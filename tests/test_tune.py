@@ -29,8 +29,9 @@ def _problem(n, naux, ks):
 
 def _line(op, prec, sms, nmol, n, naux, nd, ksum, cfg, ms=1.5):
     # bucket: nbf in steps of 32, naux in steps of 256, width in steps of 16
-    return (f"jk-tune 3 {op} {prec} {sms} {nmol} {math.ceil(n / 32)} {math.ceil(naux / 256)} {nd} "
-            f"{math.ceil(ksum / 16)} {cfg[0]} {cfg[1]} {cfg[2]} {ms:.6f}\n")
+    tile = cfg[3] if len(cfg) > 3 else 0
+    return (f"jk-tune 4 {op} {prec} {sms} {nmol} {math.ceil(n / 32)} {math.ceil(naux / 256)} {nd} "
+            f"{math.ceil(ksum / 16)} {cfg[0]} {cfg[1]} {cfg[2]} {tile} {ms:.6f}\n")
 
 
 def _lookup(lib, n, naux, ks, prec=jk.JK_SPLIT_BF16, sms=148):
@@ -49,7 +50,7 @@ def test_empty_cache(lib):
 def test_import_lookup_and_bucket(lib):
     jk.tune_import(_line(0, 1, 148, 1, 400, 2400, 8, 320, (600, 1, 0)))
     st, cfg = _lookup(lib, 400, 2400, [40] * 8)
-    assert st == jk.JK_OK and cfg == {"aux_chunk": 600, "schedule": 1, "raster": 0}
+    assert st == jk.JK_OK and cfg == {"aux_chunk": 600, "schedule": 1, "raster": 0, "tile": 0}
     # same bucket: nbf 385..416, naux 2305..2560, same count, width 305..320
     assert _lookup(lib, 390, 2500, [39] * 8)[0] == jk.JK_OK
     # other buckets, other SM count, other precision
@@ -69,8 +70,8 @@ def test_export_round_trip_and_later_entries_win(lib):
     jk.tune_clear()
     jk.tune_import(text)
     assert jk.tune_export() == text
-    jk.tune_import(_line(0, 1, 148, 1, 400, 2400, 8, 320, (300, 0, 1)))
-    assert _lookup(lib, 400, 2400, [40] * 8)[1] == {"aux_chunk": 300, "schedule": 0, "raster": 1}
+    jk.tune_import(_line(0, 1, 148, 1, 400, 2400, 8, 320, (300, 0, 1, 1)))
+    assert _lookup(lib, 400, 2400, [40] * 8)[1] == {"aux_chunk": 300, "schedule": 0, "raster": 1, "tile": 1}
     # export into a short buffer: truncated, NUL-terminated, full length reported
     n = ct.c_size_t()
     buf = ct.create_string_buffer(10)
@@ -79,13 +80,14 @@ def test_export_round_trip_and_later_entries_win(lib):
 
 
 @pytest.mark.parametrize("bad", [
-    "jk-tune 2 0 1 148 1 13 10 8 20 600 1 0 0 1.0",       # an older version (four configuration fields)
-    "jk-tune 3 0 1 148 1 13 10 8 20 600 2 0 1.0",         # schedule out of range
-    "jk-tune 3 0 1 148 1 13 10 8 20 600 0 2 1.0",         # raster out of range
-    "jk-tune 3 0 1 148 1 13 10 8 20 -5 0 0 1.0",          # negative chunk
-    "jk-tune 3 0 1 148 1 13 10 8 20 600 0 0",             # missing field
-    "jk-tune 3 0 1 148 1 13 10 8 20 600 0 0 1.0 extra",   # trailing text
-    "tune 3 0 1 148 1 13 10 8 20 600 0 0 1.0",            # wrong tag
+    "jk-tune 3 0 1 148 1 13 10 8 20 600 1 0 1.0",         # an older version (no tile width)
+    "jk-tune 4 0 1 148 1 13 10 8 20 600 2 0 0 1.0",       # schedule out of range
+    "jk-tune 4 0 1 148 1 13 10 8 20 600 0 2 0 1.0",       # raster out of range
+    "jk-tune 4 0 1 148 1 13 10 8 20 600 0 0 2 1.0",       # tile out of range
+    "jk-tune 4 0 1 148 1 13 10 8 20 -5 0 0 0 1.0",        # negative chunk
+    "jk-tune 4 0 1 148 1 13 10 8 20 600 0 0 0",           # missing field
+    "jk-tune 4 0 1 148 1 13 10 8 20 600 0 0 0 1.0 extra", # trailing text
+    "tune 4 0 1 148 1 13 10 8 20 600 0 0 0 1.0",          # wrong tag
 ])
 def test_malformed_lines_rejected(lib, bad):
     good = _line(0, 1, 148, 1, 400, 2400, 8, 320, (600, 1, 0))

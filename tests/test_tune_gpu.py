@@ -50,7 +50,7 @@ def test_autotune_split_caches_and_is_used(eng):
     text = jk.tune_export()
     assert len(text.splitlines()) == 1
     fields = text.split()
-    assert [int(v) for v in fields[10:13]] == [cfg["aux_chunk"], cfg["schedule"], cfg["raster"]]
+    assert [int(v) for v in fields[10:14]] == [cfg["aux_chunk"], cfg["schedule"], cfg["raster"], cfg["tile"]]
     # the tuned configuration is applied to the next build: same launch count
     # as forcing it explicitly, and the oracle's result
     eng.profile(True)
