@@ -332,6 +332,176 @@ __global__ void __launch_bounds__(256) slice_kernel(Src src, int rows, int K, in
 }
 
 // ---------------------------------------------------------------------------
+// Grouped slicing: many operands in one launch
+// ---------------------------------------------------------------------------
+// A batched build slices the factor chunk and both panel operands of every
+// density of every molecule in a wave; one exponent launch and one slicer
+// launch take them all, their jobs carried in the parameter space (no device
+// table to upload, so the launch stays capturable in a CUDA graph).  Each job
+// is one operand as slice_operand would slice it; block b of a launch belongs
+// to the job whose block range [b0, b0 + blocks) holds it.
+struct SliceJob {
+    Src src;
+    int *e;                // exponents: written by the exponent launch, read by the slicer
+    void *out;             // S planes, rows x Kpad each
+    long long sstride;     // plane stride in units of the output words (uint2 when vec, else ushort)
+    int rows, K, Kpad, rpe, nsc;
+    int vec;               // 4-element vector path (alignment checked on the host)
+    int flat;              // exponent groups are contiguous runs of rpe * K doubles
+    int eb0, sb0;          // first block of this job in the exponent and the slicer launch
+    int nbx, nby;          // slicer blocks along K (x) and rows (y)
+};
+constexpr int MAXJOB = 200;
+struct SliceGroup {
+    SliceJob j[MAXJOB];
+    int njob;
+};
+
+__device__ __forceinline__ int job_of_block(const SliceGroup &g, int b, bool expo) {
+    int lo = 0, hi = g.njob - 1;
+    while (lo < hi) {   // the last job whose first block is <= b
+        const int mid = (lo + hi + 1) >> 1;
+        if ((expo ? g.j[mid].eb0 : g.j[mid].sb0) <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// The exponents of every job: expo_kernel's (or expo_flat_kernel's) work for
+// the job's row group g and super-chunk z.
+__global__ void __launch_bounds__(256) expo_group_kernel(const __grid_constant__ SliceGroup g) {
+    __shared__ unsigned long long red[8];
+    const int ji = job_of_block(g, blockIdx.x, true);
+    const SliceJob &jb = g.j[ji];
+    const int lb = blockIdx.x - jb.eb0;
+    unsigned long long mx = 0;
+    int slot;
+    if (jb.flat) {
+        const long long len = static_cast<long long>(jb.rpe) * jb.K;
+        const double2 *q = reinterpret_cast<const double2 *>(jb.src.p + lb * len);
+        for (long long t = threadIdx.x; t < len / 2; t += 256) {
+            const double2 v = q[t];
+            const unsigned long long a = static_cast<unsigned long long>(__double_as_longlong(v.x)) & 0x7FFFFFFFFFFFFFFFull;
+            const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(v.y)) & 0x7FFFFFFFFFFFFFFFull;
+            mx = a > mx ? a : mx;
+            mx = b > mx ? b : mx;
+        }
+        slot = lb;
+    } else {
+        const Src src = jb.src;
+        const int gi = lb / jb.nsc, z = lb - gi * jb.nsc;
+        const int r0 = gi * jb.rpe, r1 = min(jb.rows, r0 + jb.rpe);
+        const int k0 = z * SUPER, k1 = min(jb.K, k0 + SUPER);
+        const int step_o = 256 / src.kin, step_i = 256 % src.kin;
+        for (int r = r0; r < r1; r++) {
+            const double *row = src_row(src, r);
+            int ko = (k0 + threadIdx.x) / src.kin, ki = k0 + threadIdx.x - ko * src.kin;
+            for (int kk = k0 + threadIdx.x; kk < k1; kk += 256) {
+                const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(
+                                                 row[static_cast<long long>(ko) * src.sko +
+                                                     static_cast<long long>(ki) * src.ski])) &
+                                             0x7FFFFFFFFFFFFFFFull;
+                mx = b > mx ? b : mx;
+                ko += step_o;
+                ki += step_i;
+                if (ki >= src.kin) { ki -= src.kin; ko++; }
+            }
+        }
+        slot = gi * jb.nsc + z;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long y = __shfl_down_sync(0xffffffffu, mx, o);
+        mx = y > mx ? y : mx;
+    }
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long m = red[0];
+        for (int i = 1; i < 8; i++) m = red[i] > m ? red[i] : m;
+        jb.e[slot] = exponent_of_max(m);
+    }
+}
+
+// The slices of every job: slice4_kernel's work (vector jobs) or
+// slice_kernel's (the others) for the job's block (bx, by).
+template <int S>
+__global__ void __launch_bounds__(256) slice_group_kernel(const __grid_constant__ SliceGroup g) {
+    const int ji = job_of_block(g, blockIdx.x, false);
+    const SliceJob &jb = g.j[ji];
+    const int lb = blockIdx.x - jb.sb0;
+    const int by = lb / jb.nbx, bx = lb - by * jb.nbx;
+    const Src src = jb.src;
+    const int rows = jb.rows, K = jb.K, Kpad = jb.Kpad, rpe = jb.rpe, nsc = jb.nsc;
+    const int *e = jb.e;
+    if (jb.vec) {
+        const int kk = 4 * (bx * 256 + threadIdx.x);
+        if (kk >= Kpad) return;
+        uint2 *out = static_cast<uint2 *>(jb.out);
+        long long koff = 0;
+        if (kk < K) {
+            const int ko = kk / src.kin, ki = kk - ko * src.kin;
+            koff = static_cast<long long>(ko) * src.sko + ki;
+        }
+        for (int rb = by * 8; rb < rows; rb += jb.nby * 8) {
+            const int rend = min(rows, rb + 8);
+            for (int r = rb; r < rend; r++) {
+                int q[4][S];
+                if (kk < K) {
+                    const double2 *p2 = reinterpret_cast<const double2 *>(src_row(src, r) + koff);
+                    const double2 a = p2[0], b = p2[1];
+                    const int er = e[(r / rpe) * nsc + kk / SUPER];
+                    element_digits<S>(a.x, er, q[0]);
+                    element_digits<S>(a.y, er, q[1]);
+                    element_digits<S>(b.x, er, q[2]);
+                    element_digits<S>(b.y, er, q[3]);
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 4; i++)
+#pragma unroll
+                        for (int j = 0; j < S; j++) q[i][j] = 0;
+                }
+                const long long o = (static_cast<long long>(r) * Kpad + kk) >> 2;
+                float sc = 0.00390625f;
+#pragma unroll
+                for (int j = 0; j < S; j++) {
+                    uint2 w;
+                    w.x = qbf16(q[0][j], sc) | (qbf16(q[1][j], sc) << 16);
+                    w.y = qbf16(q[2][j], sc) | (qbf16(q[3][j], sc) << 16);
+                    out[j * jb.sstride + o] = w;
+                    sc *= 0.00390625f;
+                }
+            }
+        }
+    } else {
+        const int kk = bx * 256 + threadIdx.x;
+        if (kk >= Kpad) return;
+        unsigned short *out = static_cast<unsigned short *>(jb.out);
+        long long koff = 0;
+        if (kk < K) {
+            const int ko = kk / src.kin, ki = kk - ko * src.kin;
+            koff = static_cast<long long>(ko) * src.sko + static_cast<long long>(ki) * src.ski;
+        }
+        for (int rb = by * SLICE_ROWS; rb < rows; rb += jb.nby * SLICE_ROWS) {
+            const int rend = min(rows, rb + SLICE_ROWS);
+            for (int r = rb; r < rend; r++) {
+                int q[S];
+#pragma unroll
+                for (int j = 0; j < S; j++) q[j] = 0;
+                if (kk < K) element_digits<S>(src_row(src, r)[koff], e[(r / rpe) * nsc + kk / SUPER], q);
+                const long long o = static_cast<long long>(r) * Kpad + kk;
+                float sc = 0.00390625f;
+#pragma unroll
+                for (int j = 0; j < S; j++) {
+                    out[j * jb.sstride + o] = static_cast<unsigned short>(qbf16(q[j], sc));
+                    sc *= 0.00390625f;
+                }
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // The tcgen05 sliced GEMM:  C[m][n] = sum_k A[m][k] B[n][k]
 // ---------------------------------------------------------------------------
 struct OzArgs {
@@ -891,6 +1061,52 @@ reduce_partials_kernel(const long long *P, long long pz, long long ldp, int nz, 
     *o = accumulate ? (*o + v) : v;
 }
 
+// Many split-K reductions in one launch (the batched build's rank updates):
+// each job is one reduce_partials_kernel call, its elements numbered from e0
+// in the launch.
+struct ReduceJob {
+    const long long *P;
+    long long pz, ldp;
+    const int *eA, *eB;
+    double *out;
+    long long ldo;
+    long long e0;          // first element of this job in the launch
+    int nz, M, N, arpe, brpe, accumulate, frac;
+};
+constexpr int MAXRED = 240;
+struct ReduceGroup {
+    ReduceJob j[MAXRED];
+    int njob;
+};
+
+__global__ void __launch_bounds__(256) reduce_group_kernel(const __grid_constant__ ReduceGroup g, long long total) {
+    const long long t = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
+    if (t >= total) return;
+    int lo = 0, hi = g.njob - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (g.j[mid].e0 <= t) lo = mid;
+        else hi = mid - 1;
+    }
+    const ReduceJob &jb = g.j[lo];
+    const long long e = t - jb.e0;
+    const int N = jb.N, nz = jb.nz;
+    const int r = static_cast<int>(e / N), c = static_cast<int>(e % N);
+    const long long off = static_cast<long long>(r) * jb.ldp + c;
+    const int *ea = jb.eA + static_cast<long long>(r / jb.arpe) * nz;
+    const int *eb = jb.eB + static_cast<long long>(c / jb.brpe) * nz;
+    int emax = -(1 << 30);
+    for (int zz = 0; zz < nz; zz++) emax = max(emax, ea[zz] + eb[zz]);
+    __int128 s = 0;
+    for (int zz = 0; zz < nz; zz++) {
+        const int d = emax - (ea[zz] + eb[zz]);
+        if (d < 100) s += (static_cast<__int128>(jb.P[zz * jb.pz + off]) << 52) >> d;
+    }
+    const double v = i128_to_f64_scaled(s, emax - jb.frac - 52);
+    double *o = jb.out + static_cast<long long>(r) * jb.ldo + c;
+    *o = jb.accumulate ? (*o + v) : v;
+}
+
 // K[r][c] = K[c][r] for the entries a blocked symmetric rank update leaves
 // unformed: c < bm * (r / bm), left of row r's diagonal block (those (c, r)
 // all lie in the formed blocks, so no entry is both read and written).
@@ -1177,6 +1393,124 @@ static jk_status reduce_partials(jk_ctx *h, const long long *P, int nz, const Sl
     return JK_OK;
 }
 
+// ---- grouped slicing and reductions (batched builds) -------------------------
+static_assert(sizeof(oz::SliceGroup) <= 32764 && sizeof(oz::ReduceGroup) + 8 <= 32764,
+              "grouped launches fit the kernel parameter space");
+
+// Operands to slice with grouped launches: each added operand becomes one
+// job of the same slicing slice_operand does (exponents, then digits).
+struct SliceBatch {
+    std::vector<oz::SliceJob> jobs;
+};
+
+static void slice_add(SliceBatch &sb, const oz::Src &src, int rows, int K, int rpe, Sliced &out) {
+    out.rows = rows;
+    out.K = K;
+    out.Kpad = kpad_of(K);
+    out.rpe = rpe;
+    oz::SliceJob j;
+    std::memset(&j, 0, sizeof j);
+    j.src = src;
+    j.e = out.e;
+    j.out = out.s;
+    j.rows = rows;
+    j.K = K;
+    j.Kpad = out.Kpad;
+    j.rpe = rpe;
+    j.nsc = (K + oz::SUPER - 1) / oz::SUPER;
+    const bool aligned = (reinterpret_cast<uintptr_t>(src.p) & 15u) == 0;
+    j.flat = j.nsc == 1 && aligned && src.rin == 1 && src.ski == 1 && src.kin == K && src.sr == K &&
+             ((static_cast<long long>(rpe) * K) % 2) == 0 && rows % rpe == 0;
+    j.vec = aligned && src.ski == 1 && (src.kin % 4) == 0 && (K % 4) == 0 && (src.sr % 2) == 0 &&
+            (src.sri % 2) == 0 && (src.sko % 2) == 0;
+    j.sstride = j.vec ? static_cast<long long>(rows) * out.Kpad / 4 : static_cast<long long>(rows) * out.Kpad;
+    const int rblocks = (rows + oz::SLICE_ROWS - 1) / oz::SLICE_ROWS;
+    j.nbx = j.vec ? (out.Kpad / 4 + 255) / 256 : (out.Kpad + 255) / 256;
+    j.nby = rblocks < 65535 ? rblocks : 65535;
+    sb.jobs.push_back(j);
+    (void)out.S;
+}
+
+// Slice every collected operand (all six-slice) with one exponent launch and
+// one slicer launch per MAXJOB jobs; the batch is emptied.
+static jk_status slice_flush(jk_ctx *h, SliceBatch &sb, cudaStream_t st) {
+    static thread_local oz::SliceGroup grp;
+    for (size_t i0 = 0; i0 < sb.jobs.size(); i0 += oz::MAXJOB) {
+        const int nj = static_cast<int>(std::min<size_t>(oz::MAXJOB, sb.jobs.size() - i0));
+        long long eb = 0, sbk = 0;
+        for (int i = 0; i < nj; i++) {
+            oz::SliceJob &j = grp.j[i];
+            j = sb.jobs[i0 + i];
+            j.eb0 = static_cast<int>(eb);
+            j.sb0 = static_cast<int>(sbk);
+            const int groups = (j.rows + j.rpe - 1) / j.rpe;
+            eb += j.flat ? groups : static_cast<long long>(groups) * j.nsc;
+            sbk += static_cast<long long>(j.nbx) * j.nby;
+        }
+        if (eb > 0x7fffffffLL || sbk > 0x7fffffffLL) return set_error(h, JK_ERR_SHAPE, "too many slicer blocks");
+        grp.njob = nj;
+        {
+            LaunchScope ls(h, KK_SLICE, st);
+            oz::expo_group_kernel<<<static_cast<unsigned>(eb), 256, 0, st>>>(grp);
+        }
+        JK_LAUNCH_CHECK(h);
+        {
+            LaunchScope ls(h, KK_SLICE, st);
+            oz::slice_group_kernel<6><<<static_cast<unsigned>(sbk), 256, 0, st>>>(grp);
+        }
+        JK_LAUNCH_CHECK(h);
+    }
+    sb.jobs.clear();
+    return JK_OK;
+}
+
+// Split-K reductions collected for grouped launches (reduce_partials' work).
+struct ReduceBatch {
+    std::vector<oz::ReduceJob> jobs;
+};
+
+static void reduce_add(ReduceBatch &rb, const long long *P, int nz, const Sliced &A, const Sliced &B, double *out,
+                       long long ldo, bool accumulate) {
+    oz::ReduceJob j;
+    std::memset(&j, 0, sizeof j);
+    j.ldp = even_ld(B.rows);
+    j.P = P;
+    j.pz = part_rows(A.rows) * j.ldp;
+    j.eA = A.e;
+    j.eB = B.e;
+    j.out = out;
+    j.ldo = ldo;
+    j.nz = nz;
+    j.M = A.rows;
+    j.N = B.rows;
+    j.arpe = A.rpe;
+    j.brpe = B.rpe;
+    j.accumulate = accumulate ? 1 : 0;
+    j.frac = A.S == 7 ? oz::Cfg7::FRAC : oz::Cfg6::FRAC;
+    rb.jobs.push_back(j);
+}
+
+static jk_status reduce_flush(jk_ctx *h, ReduceBatch &rb, cudaStream_t st) {
+    static thread_local oz::ReduceGroup grp;
+    for (size_t i0 = 0; i0 < rb.jobs.size(); i0 += oz::MAXRED) {
+        const int nj = static_cast<int>(std::min<size_t>(oz::MAXRED, rb.jobs.size() - i0));
+        long long tot = 0;
+        for (int i = 0; i < nj; i++) {
+            grp.j[i] = rb.jobs[i0 + i];
+            grp.j[i].e0 = tot;
+            tot += static_cast<long long>(grp.j[i].M) * grp.j[i].N;
+        }
+        grp.njob = nj;
+        {
+            LaunchScope ls(h, KK_OZREDUCE, st);
+            oz::reduce_group_kernel<<<static_cast<unsigned>((tot + 255) / 256), 256, 0, st>>>(grp, tot);
+        }
+        JK_LAUNCH_CHECK(h);
+    }
+    rb.jobs.clear();
+    return JK_OK;
+}
+
 // ---- symmetric rank updates (JK_OPT_SYRK) -----------------------------------
 // K_s = T_X T_X^T of a symmetric density is symmetric.  Row block i (rows
 // [r0, r1) = [BM i, BM (i+1)) of T_X) is multiplied by rows [r0, n) only: one
@@ -1381,20 +1715,32 @@ jk_status split_build(jk_ctx *h, const Problem &pb, cudaStream_t st) {
             JK_TRY(fp64_jstream(h, pb, gamma, h->aux_stream));
         }
         if (!pb.wantK) continue;
-        // Rank update per density over this chunk's (p, i) pairs.
+        // The rank-update operands of every density (grouped launches unless
+        // the FP32-digit slicer is asked for), then the rank update per
+        // density over this chunk's (p, i) pairs.
+        {
+            const bool grouped = h->slicer == 0;
+            SliceBatch sb;
+            for (int s = 0; s < nd; s++) {
+                const int k = pb.k[s];
+                const int Kr = np * k;
+                oz::Src xs{T + pb.offX[s], ldT, static_cast<long long>(n) * ldT, 1, k};
+                if (grouped) slice_add(sb, xs, n, Kr, 1, TX[s]);
+                else JK_TRY(slice_operand(h, xs, n, Kr, 1, TX[s], st));
+                if (!pb.sym[s]) {
+                    oz::Src ys{T + pb.offY[s], ldT, static_cast<long long>(n) * ldT, 1, k};
+                    if (grouped) slice_add(sb, ys, n, Kr, 1, TY[s]);
+                    else JK_TRY(slice_operand(h, ys, n, Kr, 1, TY[s], st));
+                }
+            }
+            JK_TRY(slice_flush(h, sb, st));
+        }
+        ReduceBatch rb;
         long long *Pcur = Pbuf;
         for (int s = 0; s < nd; s++) {
             const int k = pb.k[s];
             const int Kr = np * k;
-            oz::Src xs{T + pb.offX[s], ldT, static_cast<long long>(n) * ldT, 1, k};
-            TX[s].rows = n;
-            JK_TRY(slice_operand(h, xs, n, Kr, 1, TX[s], st));
-            Sliced *B = &TX[s];
-            if (!pb.sym[s]) {
-                oz::Src ys{T + pb.offY[s], ldT, static_cast<long long>(n) * ldT, 1, k};
-                JK_TRY(slice_operand(h, ys, n, Kr, 1, TY[s], st));
-                B = &TY[s];
-            }
+            Sliced *B = pb.sym[s] ? &TX[s] : &TY[s];
             double *Kout = pb.K[s];
             const int ns = nsuper_of(Kr);
             if (pb.sym[s] && h->syrk) {
@@ -1422,10 +1768,11 @@ jk_status split_build(jk_ctx *h, const Problem &pb, cudaStream_t st) {
                 }
             } else {
                 JK_TRY(ozgemm(h, TX[s], *B, nullptr, 0, Pcur, st));
-                JK_TRY(reduce_partials(h, Pcur, ns, TX[s], *B, Kout, n, P0 > 0, st));
+                reduce_add(rb, Pcur, ns, TX[s], *B, Kout, n, P0 > 0);
                 Pcur += static_cast<size_t>(ns) * part_rows(n) * even_ld(n);
             }
         }
+        JK_TRY(reduce_flush(h, rb, st));
     }
     if (pb.wantK && h->syrk)
         for (int s = 0; s < nd; s++)
@@ -1843,7 +2190,10 @@ jk_status split_batched(jk_ctx *h, int nmol, const Problem *pbs, cudaStream_t st
             ++w1;
         }
         if (items.empty()) return set_error(h, JK_ERR_OOM, "workspace too small for one batched work item");
-        // 1. slice the factor chunks
+        // 1. slice the factor chunks (grouped launches, unless the FP32-digit
+        // slicer is asked for: that one slices operand by operand)
+        const bool grouped = h->slicer == 0;
+        SliceBatch sb;
         for (auto &it : items) {
             const Problem &pb = pbs[it.mol];
             const long long n2 = static_cast<long long>(pb.n) * pb.n;
@@ -1851,8 +2201,10 @@ jk_status split_batched(jk_ctx *h, int nmol, const Problem *pbs, cudaStream_t st
                 JK_TRY(fp64_unpack_sym(h, pb.L + it.P0 * packed::tri_count(pb.n), pb.n, it.np, it.Lx, st));
             const double *Lc = pb.packed ? it.Lx : pb.L + it.P0 * n2;
             oz::Src lsrc{Lc, pb.n, 0, 1, pb.n};
-            JK_TRY(slice_operand(h, lsrc, it.np * pb.n, pb.n, pb.n, it.Ls, st));
+            if (grouped) slice_add(sb, lsrc, it.np * pb.n, pb.n, pb.n, it.Ls);
+            else JK_TRY(slice_operand(h, lsrc, it.np * pb.n, pb.n, pb.n, it.Ls, st));
         }
+        JK_TRY(slice_flush(h, sb, st));
         // 2. all panels of the wave: grouped persistent launches
         std::vector<oz::OzProb> probs;
         for (auto &it : items) {
@@ -1885,13 +2237,16 @@ jk_status split_batched(jk_ctx *h, int nmol, const Problem *pbs, cudaStream_t st
             for (int s = 0; s < pb.nd; s++) {
                 const int k = pb.k[s], Kr = it.np * k;
                 oz::Src xs{it.T + pb.offX[s], ldT, static_cast<long long>(pb.n) * ldT, 1, k};
-                JK_TRY(slice_operand(h, xs, pb.n, Kr, 1, it.TX[s], st));
+                if (grouped) slice_add(sb, xs, pb.n, Kr, 1, it.TX[s]);
+                else JK_TRY(slice_operand(h, xs, pb.n, Kr, 1, it.TX[s], st));
                 if (!pb.sym[s]) {
                     oz::Src ys{it.T + pb.offY[s], ldT, static_cast<long long>(pb.n) * ldT, 1, k};
-                    JK_TRY(slice_operand(h, ys, pb.n, Kr, 1, it.TY[s], st));
+                    if (grouped) slice_add(sb, ys, pb.n, Kr, 1, it.TY[s]);
+                    else JK_TRY(slice_operand(h, ys, pb.n, Kr, 1, it.TY[s], st));
                 }
             }
         }
+        JK_TRY(slice_flush(h, sb, st));
         // 4. every rank update of the wave: grouped persistent launches
         probs.clear();
         struct Red { const ItemBufs *it; int s; long long *P; double *tmp; };
@@ -1929,7 +2284,8 @@ jk_status split_batched(jk_ctx *h, int nmol, const Problem *pbs, cudaStream_t st
             }
         }
         JK_TRY(oz_launch(h, probs, st));
-        // 5. reductions into K
+        // 5. reductions into K (the split-K ones in grouped launches)
+        ReduceBatch rb;
         for (auto &r : reds) {
             const Problem &pb = pbs[r.it->mol];
             const long long n2 = static_cast<long long>(pb.n) * pb.n;
@@ -1937,12 +2293,13 @@ jk_status split_batched(jk_ctx *h, int nmol, const Problem *pbs, cudaStream_t st
             if (r.P && pb.sym[r.s] && h->syrk) {
                 JK_TRY(sym_rank_reduce(h, r.it->TX[r.s], pb.n, r.P, pb.K[r.s], r.it->P0 > 0, st));
             } else if (r.P) {
-                JK_TRY(reduce_partials(h, r.P, nsuper_of(r.it->np * pb.k[r.s]), r.it->TX[r.s], B, pb.K[r.s], pb.n,
-                                       r.it->P0 > 0, st));
+                reduce_add(rb, r.P, nsuper_of(r.it->np * pb.k[r.s]), r.it->TX[r.s], B, pb.K[r.s], pb.n,
+                           r.it->P0 > 0);
             } else {
                 JK_TRY(fp64_axpy(h, pb.K[r.s], r.tmp, n2, st));
             }
         }
+        JK_TRY(reduce_flush(h, rb, st));
         w0 = w1;
     }
     if (h->syrk)

@@ -91,6 +91,25 @@ class Src(ct.Structure):
     _fields_ = [("p", VP), ("sr", I64), ("sko", I64), ("ski", I64), ("kin", I32), ("rin", I32), ("sri", I64)]
 
 
+class SliceJob(ct.Structure):
+    _fields_ = [("src", Src), ("e", VP), ("out", VP), ("sstride", I64), ("rows", I32), ("K", I32), ("Kpad", I32),
+                ("rpe", I32), ("nsc", I32), ("vec", I32), ("flat", I32), ("eb0", I32), ("sb0", I32), ("nbx", I32),
+                ("nby", I32)]
+
+
+class SliceGroup(ct.Structure):
+    _fields_ = [("j", SliceJob * 200), ("njob", I32)]
+
+
+class ReduceJob(ct.Structure):
+    _fields_ = [("P", VP), ("pz", I64), ("ldp", I64), ("eA", VP), ("eB", VP), ("out", VP), ("ldo", I64), ("e0", I64),
+                ("nz", I32), ("M", I32), ("N", I32), ("arpe", I32), ("brpe", I32), ("accumulate", I32), ("frac", I32)]
+
+
+class ReduceGroup(ct.Structure):
+    _fields_ = [("j", ReduceJob * 240), ("njob", I32)]
+
+
 class GOp(ct.Structure):
     _fields_ = [("p", VP), ("sb", I64), ("sr", I64), ("sko", I64), ("ski", I64), ("kin", I32)]
 
@@ -186,6 +205,66 @@ def dec_slice4(grid, args, name):
     src = _a(args, 0, Src)
     assert src.ski == 1 and src.kin % 4 == 0 and _v(args, 2, I32) % 4 == 0 and src.p % 16 == 0
     return _slice(grid, args, 8, 4, _slices_of(name))
+
+
+def _group_jobs(g, key, blocks_of):
+    """The jobs of a grouped launch, checked to tile the launch's blocks in order."""
+    assert 1 <= g.njob <= len(g.j), g.njob
+    b = 0
+    for i in range(g.njob):
+        jb = g.j[i]
+        assert getattr(jb, key) == b, (i, getattr(jb, key), b)
+        b += blocks_of(jb)
+    return [g.j[i] for i in range(g.njob)], b
+
+
+def _expo_blocks(jb):
+    groups = (jb.rows - 1) // jb.rpe + 1
+    return groups if jb.flat else groups * jb.nsc
+
+
+def dec_expo_group(grid, args):
+    jobs, nb = _group_jobs(SliceGroup.from_address(args[0]), "eb0", _expo_blocks)
+    assert grid[0] == nb, (grid, nb)
+    res = []
+    for jb in jobs:
+        assert jb.nsc == (jb.K + SUPER - 1) // SUPER and jb.Kpad % 16 == 0 and jb.K <= jb.Kpad
+        groups = (jb.rows - 1) // jb.rpe + 1
+        if jb.flat:
+            assert jb.nsc == 1 and jb.src.p % 16 == 0 and (jb.rpe * jb.K) % 2 == 0 and jb.rows % jb.rpe == 0
+        res += [_src_range(jb.src, jb.rows, jb.K), (jb.e, jb.e + 4 * groups * jb.nsc, "e")]
+    return res
+
+
+def dec_slice_group(grid, args, name):
+    jobs, nb = _group_jobs(SliceGroup.from_address(args[0]), "sb0", lambda jb: jb.nbx * jb.nby)
+    assert grid[0] == nb, (grid, nb)
+    nslice = _slices_of(name)
+    res = []
+    for jb in jobs:
+        per, esize = (4, 8) if jb.vec else (1, 2)
+        if jb.vec:
+            assert jb.src.ski == 1 and jb.src.kin % 4 == 0 and jb.K % 4 == 0 and jb.src.p % 16 == 0
+        assert jb.nbx * 256 * per >= jb.Kpad and jb.nby >= 1 and jb.sstride * per == jb.rows * jb.Kpad
+        ne = ((jb.rows - 1) // jb.rpe) * jb.nsc + (jb.K - 1) // SUPER + 1
+        nout = (nslice - 1) * jb.sstride + (jb.rows * jb.Kpad) // per
+        res += [_src_range(jb.src, jb.rows, jb.K), (jb.e, jb.e + 4 * ne, "e"), (jb.out, jb.out + esize * nout, "slices")]
+    return res
+
+
+def dec_reduce_group(grid, args):
+    g = ReduceGroup.from_address(args[0])
+    total = _v(args, 1, I64)
+    jobs, nel = _group_jobs(g, "e0", lambda jb: jb.M * jb.N)
+    assert nel == total and grid[0] * 256 >= total, (grid, total, nel)
+    res = []
+    for jb in jobs:
+        assert jb.frac in (48, 51)
+        res += [(jb.P, jb.P + 8 * ((jb.nz - 1) * jb.pz + (jb.M - 1) * jb.ldp + jb.N), "P"),
+                (jb.eA, jb.eA + 4 * ((jb.M - 1) // jb.arpe + 1) * jb.nz, "eA"),
+                (jb.eB, jb.eB + 4 * ((jb.N - 1) // jb.brpe + 1) * jb.nz, "eB"),
+                (jb.out, jb.out + 8 * ((jb.M - 1) * jb.ldo + jb.N), "out")]
+    return res
 
 
 def dec_dgemm(grid, args):
@@ -618,15 +697,25 @@ def _expo_of(m):
     return np.where(m > 0, e, -1000)
 
 
-def ex_expo(grid, args):
-    src, rows, K, rpe, e = _a(args, 0, Src), _v(args, 1, I32), _v(args, 2, I32), _v(args, 3, I32), _v(args, 4, VP)
+def _expo_job(src, rows, K, rpe, e, ngroups, nsc):
     X = np.abs(_src_gather(src, rows, K))
-    nsc = grid[1]
-    ev = uv(e, grid[0] * nsc, np.int32)
-    for g in range(grid[0]):
+    ev = uv(e, ngroups * nsc, np.int32)
+    for g in range(ngroups):
         for z in range(nsc):
             blk = X[g * rpe:min(rows, g * rpe + rpe), z * SUPER:min(K, (z + 1) * SUPER)]
             ev[g * nsc + z] = _expo_of(blk.max() if blk.size else 0.0)
+
+
+def ex_expo(grid, args):
+    src, rows, K, rpe, e = _a(args, 0, Src), _v(args, 1, I32), _v(args, 2, I32), _v(args, 3, I32), _v(args, 4, VP)
+    _expo_job(src, rows, K, rpe, e, grid[0], grid[1])
+
+
+def ex_expo_group(grid, args):
+    g = SliceGroup.from_address(args[0])
+    for i in range(g.njob):
+        jb = g.j[i]
+        _expo_job(jb.src, jb.rows, jb.K, jb.rpe, jb.e, (jb.rows - 1) // jb.rpe + 1, jb.nsc)
 
 
 def ex_expo_flat(grid, args):
@@ -656,7 +745,17 @@ def _digits_bf16(x, e, nslice=6):
 def ex_slice(grid, args, name):
     src, rows, K, Kpad = _a(args, 0, Src), _v(args, 1, I32), _v(args, 2, I32), _v(args, 3, I32)
     e, rpe, nsc, out = _v(args, 4, VP), _v(args, 5, I32), _v(args, 6, I32), _v(args, 7, VP)
-    nslice = _slices_of(name)
+    _slice_job(src, rows, K, Kpad, e, rpe, nsc, out, _slices_of(name))
+
+
+def ex_slice_group(grid, args, name):
+    g = SliceGroup.from_address(args[0])
+    for i in range(g.njob):
+        jb = g.j[i]
+        _slice_job(jb.src, jb.rows, jb.K, jb.Kpad, jb.e, jb.rpe, jb.nsc, jb.out, _slices_of(name))
+
+
+def _slice_job(src, rows, K, Kpad, e, rpe, nsc, out, nslice):
     X = _src_gather(src, rows, K)
     ev = uv(e, ((rows - 1) // rpe + 1) * nsc, np.int32)
     E = ev[(np.arange(rows)[:, None] // rpe) * nsc + np.arange(K)[None, :] // SUPER]
@@ -718,6 +817,18 @@ def ex_reduce(grid, args):
     eA, arpe, eB, brpe, out, ldo, acc, frac = (_v(args, 6, VP), _v(args, 7, I32), _v(args, 8, VP), _v(args, 9, I32),
                                                _v(args, 10, VP), _v(args, 11, I64), _v(args, 12, I32),
                                                _v(args, 13, I32))
+    _reduce_job(P, pz, ldp, nz, M, N, eA, arpe, eB, brpe, out, ldo, acc, frac)
+
+
+def ex_reduce_group(grid, args):
+    g = ReduceGroup.from_address(args[0])
+    for i in range(g.njob):
+        jb = g.j[i]
+        _reduce_job(jb.P, jb.pz, jb.ldp, jb.nz, jb.M, jb.N, jb.eA, jb.arpe, jb.eB, jb.brpe, jb.out, jb.ldo,
+                    jb.accumulate, jb.frac)
+
+
+def _reduce_job(P, pz, ldp, nz, M, N, eA, arpe, eB, brpe, out, ldo, acc, frac):
     ea = uv(eA, ((M - 1) // arpe + 1) * nz, np.int32).reshape(-1, nz)[np.arange(M) // arpe]
     eb = uv(eB, ((N - 1) // brpe + 1) * nz, np.int32).reshape(-1, nz)[np.arange(N) // brpe]
     tot = np.zeros((M, N))
@@ -771,6 +882,8 @@ EXECUTORS = [
     ("sum_parts_kernel", ex_sum_parts), ("pair_dot_kernel", ex_pair_dot), ("laplace_scale_kernel", ex_laplace_scale),
     ("weighted_sum_kernel", ex_weighted_sum), ("unpack_sym_kernel", ex_unpack_sym), ("gterms_kernel", ex_gterms),
     ("symmetrize_kernel", ex_symmetrize), ("fold_sym_split_kernel", ex_fold), ("fold_sym_kernel", ex_fold),
+    ("expo_group_kernel", ex_expo_group), ("slice_group_kernel", ex_slice_group),
+    ("reduce_group_kernel", ex_reduce_group),
     ("expo_flat_kernel", ex_expo_flat), ("expo_kernel", ex_expo), ("slice4f_kernel", ex_slice),
     ("slice4_kernel", ex_slice), ("slice_kernel", ex_slice), ("ozgemm_kernel", ex_ozgemm),
     ("reduce_partials_kernel", ex_reduce), ("pack_ag_kernel", ex_pack_ag), ("pack_bg_kernel", ex_pack_bg),
@@ -779,6 +892,8 @@ EXECUTORS = [
 ]
 
 DECODERS = [
+    ("expo_group_kernel", dec_expo_group), ("slice_group_kernel", dec_slice_group),
+    ("reduce_group_kernel", dec_reduce_group),
     ("expo_flat_kernel", dec_expo_flat), ("expo_kernel", dec_expo), ("slice4_kernel", dec_slice4),
     ("slice_kernel", dec_slice), ("dgemm_nt_kernel", dec_dgemm), ("pack_cols_kernel", dec_pack_cols),
     ("frob_stream_kernel", dec_frob), ("gamma_panel_kernel", dec_gamma_panel), ("axpy_kernel", dec_axpy),
@@ -820,7 +935,8 @@ def on_launch(name, grid, block, args):
     for key, fn in DECODERS:
         if key in name:
             try:
-                ranges = fn(g, args, name) if fn in (dec_jstream_sym, dec_slice, dec_slice4) else fn(g, args)
+                ranges = (fn(g, args, name) if fn in (dec_jstream_sym, dec_slice, dec_slice4, dec_slice_group)
+                          else fn(g, args))
             except AssertionError as e:
                 violations.append(f"{key}: inconsistent arguments {e}")
                 return
@@ -833,7 +949,7 @@ def on_launch(name, grid, block, args):
             if EXEC[0] and not bad:
                 for ekey, ex in EXECUTORS:
                     if ekey in name:
-                        ex(g, args, name) if ex in (ex_jstream_sym, ex_slice) else ex(g, args)
+                        ex(g, args, name) if ex in (ex_jstream_sym, ex_slice, ex_slice_group) else ex(g, args)
                         break
             return
     undecoded.add(name)

@@ -111,9 +111,10 @@ def test_full_size_case(full_records, name):
 
 
 def test_full_size_tuned_build_launch_count(full_records):
-    """The tuned multi-state build issues the launches bench.py counts on the
-    B300 (61 per build: grouped persistent GEMMs, slicers, FP64 J streams)."""
-    assert len(full_records["full_multi_state_tuned"]["launches"]) == 61
+    """The tuned multi-state build (grouped schedule) issues 26 launches per
+    build: grouped persistent GEMMs, grouped exponent/slicer/reduction
+    launches, the FP64 J stream and the column packing of the densities."""
+    assert len(full_records["full_multi_state_tuned"]["launches"]) == 26
 
 
 def _check(rec):
@@ -239,18 +240,18 @@ def test_grouped_schedule_collapses_gemm_launches(full_records):
 
 
 def test_tuned_build_matches_the_measured_launch_list(full_records):
-    """Kernel by kernel, the tuned multi-state build records the launches the
-    ncu launch list of the same configuration counted on the B300 (183
-    launches for 3 builds, profiles/multistate_split_launches.md)."""
+    """Kernel by kernel, the tuned multi-state build's launches: in the grouped
+    schedule every operand of a wave is sliced by one exponent launch and one
+    slicer launch (the factor chunk before the panel GEMM, all densities'
+    panel operands after it) and every split-K reduction by one launch."""
     from collections import Counter
-    per_build = {"ozgemm_kernel": 2, "slice4_kernel": 16, "expo_kernel": 16, "expo_flat_kernel": 1,
-                 "jstream_sym_kernel": 1, "gamma_panel_kernel": 1, "reduce_partials_kernel": 8,
-                 "pack_cols_kernel": 15, "slice_kernel": 1}
+    per_build = {"ozgemm_kernel": 2, "expo_group_kernel": 2, "slice_group_kernel": 2, "expo_kernel": 1,
+                 "slice_kernel": 1, "jstream_sym_kernel": 1, "gamma_panel_kernel": 1, "reduce_group_kernel": 1,
+                 "pack_cols_kernel": 15}
     got = Counter()
     for k in full_records["full_multi_state_tuned"]["launches"]:
-        got[next(key for key in per_build if key in k[0] and not (key == "slice_kernel" and "slice4" in k[0])
-                 and not (key == "expo_kernel" and "expo_flat" in k[0]))] += 1
-    assert dict(got) == per_build and sum(per_build.values()) * 3 == 183
+        got[next(key for key in per_build if key in k[0])] += 1
+    assert dict(got) == per_build and sum(per_build.values()) == 26
 
 
 EXEC_CASES = [n for n in NAMES if not n.startswith("autotune")]
