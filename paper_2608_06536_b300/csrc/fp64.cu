@@ -12,6 +12,9 @@
 // by HBM; it exists to be correct, deterministic and a fair baseline.
 #include <cstdarg>
 
+#include <algorithm>
+#include <vector>
+
 #include "jk_internal.h"
 #include "packed.cuh"
 
@@ -361,20 +364,69 @@ __global__ void fold_sym_kernel(double *dX, double *dY, long long cnt) {
     dY[e] = 0.0;
 }
 
-static jk_status pack_z(jk_ctx *h, const Problem &pb, double *Z, cudaStream_t st) {
-    for (int s = 0; s < pb.nd; s++) {
-        long long cnt = (long long)pb.n * pb.k[s];
-        int blocks = (int)((cnt + 255) / 256);
-        { LaunchScope ls(h, KK_PACK, st);
-        pack_cols_kernel<<<blocks, 256, 0, st>>>(pb.X[s], pb.n, pb.k[s], Z, pb.ctot, pb.offX[s]); }
-        JK_LAUNCH_CHECK(h);
-        if (!pb.sym[s]) {
-            LaunchScope ls(h, KK_PACK, st);
-            pack_cols_kernel<<<blocks, 256, 0, st>>>(pb.Y[s], pb.n, pb.k[s], Z, pb.ctot, pb.offY[s]);
-            JK_LAUNCH_CHECK(h);
+// Many column blocks packed by one launch: job j copies src [n][k] into the
+// columns off..off+k-1 of Z [n][ctot]; its elements are numbered from e0 in
+// the launch.  The jobs travel in the parameter space.
+struct PackJob {
+    const double *src;
+    double *Z;
+    long long e0;
+    int n, k, ctot, off;
+};
+constexpr int MAXPACK = 600;
+struct PackGroup {
+    PackJob j[MAXPACK];
+    int njob;
+};
+static_assert(sizeof(PackGroup) + 8 <= 32764, "the pack group fits the kernel parameter space");
+
+__global__ void __launch_bounds__(256) pack_group_kernel(const __grid_constant__ PackGroup g, long long total) {
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= total) return;
+    int lo = 0, hi = g.njob - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (g.j[mid].e0 <= t) lo = mid;
+        else hi = mid - 1;
+    }
+    const PackJob &jb = g.j[lo];
+    const long long e = t - jb.e0;
+    const int lam = (int)(e / jb.k), i = (int)(e % jb.k);
+    jb.Z[(long long)lam * jb.ctot + jb.off + i] = jb.src[e];
+}
+
+// Z_m = [X_0 | Y_0 | X_1 | ...] of every molecule m (Y omitted for symmetric
+// densities): every density block of every molecule in grouped launches.
+jk_status pack_z_multi(jk_ctx *h, int nmol, const Problem *pbs, double *const *Z, cudaStream_t st) {
+    static thread_local PackGroup grp;
+    std::vector<PackJob> jobs;
+    for (int m = 0; m < nmol; m++) {
+        const Problem &pb = pbs[m];
+        for (int s = 0; s < pb.nd; s++) {
+            jobs.push_back(PackJob{pb.X[s], Z[m], 0, pb.n, pb.k[s], pb.ctot, pb.offX[s]});
+            if (!pb.sym[s]) jobs.push_back(PackJob{pb.Y[s], Z[m], 0, pb.n, pb.k[s], pb.ctot, pb.offY[s]});
         }
     }
+    for (size_t i0 = 0; i0 < jobs.size(); i0 += MAXPACK) {
+        const int nj = (int)std::min<size_t>(MAXPACK, jobs.size() - i0);
+        long long tot = 0;
+        for (int i = 0; i < nj; i++) {
+            grp.j[i] = jobs[i0 + i];
+            grp.j[i].e0 = tot;
+            tot += (long long)grp.j[i].n * grp.j[i].k;
+        }
+        grp.njob = nj;
+        {
+            LaunchScope ls(h, KK_PACK, st);
+            pack_group_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(grp, tot);
+        }
+        JK_LAUNCH_CHECK(h);
+    }
     return JK_OK;
+}
+
+static jk_status pack_z(jk_ctx *h, const Problem &pb, double *Z, cudaStream_t st) {
+    return pack_z_multi(h, 1, &pb, &Z, st);
 }
 
 // F[p][mu][nu] = P[p][t(min(mu,nu), max(mu,nu))] for p < np: symmetric L^P

@@ -212,6 +212,8 @@ jk_status split_dense(jk_ctx *h, const DenseProb &dp, cudaStream_t st);
 jk_status fp64_pair_contract(jk_ctx *h, const Problem &left, const double *ZL, const double *M, int nr, double *U,
                              double *out, cudaStream_t st);
 jk_status split_pack_z(jk_ctx *h, const Problem &pb, double *Z, cudaStream_t st);
+// Z[m] = the packed density columns of molecule m, for nmol molecules (grouped launches).
+jk_status pack_z_multi(jk_ctx *h, int nmol, const Problem *pbs, double *const *Z, cudaStream_t st);
 
 // ---- Laplace (LT-AO) builds -------------------------------------------------
 // out[k][mu][p] = C[mu][p] exp(sign alpha[k] eps[p] / 2), k < nq <= kMaxDens

@@ -2156,9 +2156,19 @@ jk_status split_batched(jk_ctx *h, int nmol, const Problem *pbs, cudaStream_t st
         if (!mb[m].Z || !mb[m].gamma || !take_sliced(ar, pb.ctot, pb.n, 1, mb[m].Zs))
             return set_error(h, JK_ERR_OOM, "workspace too small for the batched build");
         mb[m].pc = split_pchunk(pb);
-        JK_TRY(split_pack_z(h, pb, mb[m].Z, st));
-        oz::Src zsrc{mb[m].Z, 1, 0, pb.ctot, pb.n};
-        JK_TRY(slice_operand(h, zsrc, pb.ctot, pb.n, 1, mb[m].Zs, st));
+    }
+    {
+        // every molecule's packed densities and their slices, in grouped launches
+        std::vector<double *> zs(nmol);
+        for (int m = 0; m < nmol; m++) zs[m] = mb[m].Z;
+        JK_TRY(pack_z_multi(h, nmol, pbs, zs.data(), st));
+        SliceBatch zb;
+        for (int m = 0; m < nmol; m++) {
+            oz::Src zsrc{mb[m].Z, 1, 0, pbs[m].ctot, pbs[m].n};
+            if (h->slicer == 0) slice_add(zb, zsrc, pbs[m].ctot, pbs[m].n, 1, mb[m].Zs);
+            else JK_TRY(slice_operand(h, zsrc, pbs[m].ctot, pbs[m].n, 1, mb[m].Zs, st));
+        }
+        JK_TRY(slice_flush(h, zb, st));
     }
     const size_t persist = ar.off;
     bool forked = false;   // J streams running on the second stream

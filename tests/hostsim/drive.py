@@ -110,6 +110,14 @@ class ReduceGroup(ct.Structure):
     _fields_ = [("j", ReduceJob * 240), ("njob", I32)]
 
 
+class PackJob(ct.Structure):
+    _fields_ = [("src", VP), ("Z", VP), ("e0", I64), ("n", I32), ("k", I32), ("ctot", I32), ("off", I32)]
+
+
+class PackGroup(ct.Structure):
+    _fields_ = [("j", PackJob * 600), ("njob", I32)]
+
+
 class GOp(ct.Structure):
     _fields_ = [("p", VP), ("sb", I64), ("sr", I64), ("sko", I64), ("ski", I64), ("kin", I32)]
 
@@ -281,6 +289,17 @@ def dec_pack_cols(grid, args):
                                _v(args, 4, I32), _v(args, 5, I32))
     assert off + k <= ctot
     return [(src, src + 8 * n * k, "src"), (Z, Z + 8 * ((n - 1) * ctot + off + k), "Z")]
+
+
+def dec_pack_group(grid, args):
+    total = _v(args, 1, I64)
+    jobs, nel = _group_jobs(PackGroup.from_address(args[0]), "e0", lambda jb: jb.n * jb.k)
+    assert nel == total and grid[0] * 256 >= total, (grid, total, nel)
+    res = []
+    for jb in jobs:
+        assert jb.off + jb.k <= jb.ctot
+        res += [(jb.src, jb.src + 8 * jb.n * jb.k, "src"), (jb.Z, jb.Z + 8 * ((jb.n - 1) * jb.ctot + jb.off + jb.k), "Z")]
+    return res
 
 
 def dec_frob(grid, args):
@@ -510,6 +529,14 @@ def ex_pack_cols(grid, args):
                                _v(args, 4, I32), _v(args, 5, I32))
     idx = np.arange(n)[:, None] * ctot + off + np.arange(k)[None, :]
     dv(Z, int(idx.max()) + 1)[idx] = dv(src, n * k).reshape(n, k)
+
+
+def ex_pack_group(grid, args):
+    g = PackGroup.from_address(args[0])
+    for i in range(g.njob):
+        jb = g.j[i]
+        idx = np.arange(jb.n)[:, None] * jb.ctot + jb.off + np.arange(jb.k)[None, :]
+        dv(jb.Z, int(idx.max()) + 1)[idx] = dv(jb.src, jb.n * jb.k).reshape(jb.n, jb.k)
 
 
 def ex_frob(grid, args):
@@ -882,6 +909,7 @@ EXECUTORS = [
     ("sum_parts_kernel", ex_sum_parts), ("pair_dot_kernel", ex_pair_dot), ("laplace_scale_kernel", ex_laplace_scale),
     ("weighted_sum_kernel", ex_weighted_sum), ("unpack_sym_kernel", ex_unpack_sym), ("gterms_kernel", ex_gterms),
     ("symmetrize_kernel", ex_symmetrize), ("fold_sym_split_kernel", ex_fold), ("fold_sym_kernel", ex_fold),
+    ("pack_group_kernel", ex_pack_group),
     ("expo_group_kernel", ex_expo_group), ("slice_group_kernel", ex_slice_group),
     ("reduce_group_kernel", ex_reduce_group),
     ("expo_flat_kernel", ex_expo_flat), ("expo_kernel", ex_expo), ("slice4f_kernel", ex_slice),
@@ -892,6 +920,7 @@ EXECUTORS = [
 ]
 
 DECODERS = [
+    ("pack_group_kernel", dec_pack_group),
     ("expo_group_kernel", dec_expo_group), ("slice_group_kernel", dec_slice_group),
     ("reduce_group_kernel", dec_reduce_group),
     ("expo_flat_kernel", dec_expo_flat), ("expo_kernel", dec_expo), ("slice4_kernel", dec_slice4),

@@ -111,10 +111,10 @@ def test_full_size_case(full_records, name):
 
 
 def test_full_size_tuned_build_launch_count(full_records):
-    """The tuned multi-state build (grouped schedule) issues 26 launches per
-    build: grouped persistent GEMMs, grouped exponent/slicer/reduction
-    launches, the FP64 J stream and the column packing of the densities."""
-    assert len(full_records["full_multi_state_tuned"]["launches"]) == 26
+    """The tuned multi-state build (grouped schedule) issues 12 launches per
+    build: grouped persistent GEMMs, grouped packing, exponent, slicer and
+    reduction launches, the FP64 metric dot and J stream."""
+    assert len(full_records["full_multi_state_tuned"]["launches"]) == 12
 
 
 def _check(rec):
@@ -245,13 +245,12 @@ def test_tuned_build_matches_the_measured_launch_list(full_records):
     slicer launch (the factor chunk before the panel GEMM, all densities'
     panel operands after it) and every split-K reduction by one launch."""
     from collections import Counter
-    per_build = {"ozgemm_kernel": 2, "expo_group_kernel": 2, "slice_group_kernel": 2, "expo_kernel": 1,
-                 "slice_kernel": 1, "jstream_sym_kernel": 1, "gamma_panel_kernel": 1, "reduce_group_kernel": 1,
-                 "pack_cols_kernel": 15}
+    per_build = {"ozgemm_kernel": 2, "expo_group_kernel": 3, "slice_group_kernel": 3, "jstream_sym_kernel": 1,
+                 "gamma_panel_kernel": 1, "reduce_group_kernel": 1, "pack_group_kernel": 1}
     got = Counter()
     for k in full_records["full_multi_state_tuned"]["launches"]:
         got[next(key for key in per_build if key in k[0])] += 1
-    assert dict(got) == per_build and sum(per_build.values()) == 26
+    assert dict(got) == per_build and sum(per_build.values()) == 12
 
 
 EXEC_CASES = [n for n in NAMES if not n.startswith("autotune")]
