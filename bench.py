@@ -65,7 +65,7 @@ FP64_GATE = 1e-12        # relative to max |output| (FP64 engine)
 # + dram__bytes_write.sum of the capture, scaled by aux indices),
 # sm__pipe_tensor_cycles_active (% of peak, elapsed) and the capture's command.
 NCU_GEMM = {}
-KERNEL_SOURCES = ("split.cu", "tc.cuh", "fixed.cuh", "digits.cuh")
+KERNEL_SOURCES = ("ozgemm.cuh", "ozcfg.cuh", "tc.cuh", "fixed.cuh")
 
 
 def kernel_source_hash() -> str:

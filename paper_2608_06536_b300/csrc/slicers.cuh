@@ -1,0 +1,415 @@
+// Slicers of the split-precision engine: FP64 operands to S BF16 digit
+// planes under a per-row (per super-chunk) power-of-two scale, one operand per
+// launch or many operands per grouped launch.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include "digits.cuh"
+#include "fixed.cuh"
+#include "ozcfg.cuh"
+
+namespace jk {
+namespace oz {
+
+// ---------------------------------------------------------------------------
+// Integer helpers
+// ---------------------------------------------------------------------------
+
+using fixed::exponent_of_max;
+using fixed::i128_to_f64_scaled;
+using fixed::i64_to_f64_scaled;
+using fixed::to_fixed;
+
+// ---------------------------------------------------------------------------
+// Slicers
+// ---------------------------------------------------------------------------
+
+// Source addressing: element (row r, reduction index kk) is at
+// p + (r / rin)*sr + (r % rin)*sri + (kk / kin)*sko + (kk % kin)*ski
+// (two-level row and reduction indices, e.g. rows (P, i) or K = (P, lam)).
+struct Src {
+    const double *p;
+    long long sr, sko, ski;
+    int kin;
+    int rin = 1;
+    long long sri = 0;
+};
+
+__device__ __forceinline__ const double *src_row(const Src &s, int r) {
+    const int ro = r / s.rin, ri = r - ro * s.rin;
+    return s.p + static_cast<long long>(ro) * s.sr + static_cast<long long>(ri) * s.sri;
+}
+
+// e[g * gridDim.y + z] for row groups g of `rpe` rows and super-chunks z of
+// the reduction index: max|x| over the group's rows and kk in
+// [z*SUPER, (z+1)*SUPER).  Each thread walks kk = k0 + tid, + 256, ... keeping
+// (ko, ki) incrementally, so the hot loop has no integer division.
+__global__ void __launch_bounds__(256) expo_kernel(Src src, int rows, int K, int rpe, int *e) {
+    __shared__ unsigned long long red[8];
+    const int g = blockIdx.x, z = blockIdx.y;
+    const int r0 = g * rpe, r1 = min(rows, r0 + rpe);
+    const int k0 = z * SUPER, k1 = min(K, k0 + SUPER);
+    const int step_o = 256 / src.kin, step_i = 256 % src.kin;
+    unsigned long long mx = 0;
+    for (int r = r0; r < r1; r++) {
+        const double *row = src_row(src, r);
+        int ko = (k0 + threadIdx.x) / src.kin, ki = k0 + threadIdx.x - ko * src.kin;
+        for (int kk = k0 + threadIdx.x; kk < k1; kk += 256) {
+            const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(
+                                             row[static_cast<long long>(ko) * src.sko +
+                                                 static_cast<long long>(ki) * src.ski])) &
+                                         0x7FFFFFFFFFFFFFFFull;
+            mx = b > mx ? b : mx;
+            ko += step_o;
+            ki += step_i;
+            if (ki >= src.kin) { ki -= src.kin; ko++; }
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long y = __shfl_down_sync(0xffffffffu, mx, o);
+        mx = y > mx ? y : mx;
+    }
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long m = red[0];
+        for (int i = 1; i < 8; i++) m = red[i] > m ? red[i] : m;
+        e[g * gridDim.y + z] = exponent_of_max(m);
+    }
+}
+
+using digits::digits6;
+using digits::qbf16;
+
+// The S digits of an element under its scale: the 32-bit split for six
+// slices, the 64-bit one for seven.
+template <int S>
+__device__ __forceinline__ void element_digits(double x, int e, int q[S]) {
+    const long long F = to_fixed(x, e, 8 * S);
+    if constexpr (S == 6) digits6(F, q);
+    else digits::digits_n<S>(F, q);
+}
+
+// Vector slicer: 4 consecutive reduction elements per thread.  Requires
+// src.ski == 1, src.kin % 4 == 0, K % 4 == 0 and 16-byte aligned pairs
+// (checked on the host).
+template <int S>
+__global__ void __launch_bounds__(256) slice4_kernel(Src src, int rows, int K, int Kpad, const int *e, int rpe,
+                                                     int nsc, uint2 *out, long long sstride4) {
+    const int kk = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
+    if (kk >= Kpad) return;
+    long long koff = 0;
+    if (kk < K) {
+        const int ko = kk / src.kin, ki = kk - ko * src.kin;
+        koff = static_cast<long long>(ko) * src.sko + ki;
+    }
+    for (int rb = blockIdx.y * 8; rb < rows; rb += gridDim.y * 8) {
+        const int rend = min(rows, rb + 8);
+        for (int r = rb; r < rend; r++) {
+            int q[4][S];
+            if (kk < K) {
+                const double2 *p2 = reinterpret_cast<const double2 *>(src_row(src, r) + koff);
+                const double2 a = p2[0], b = p2[1];
+                const int er = e[(r / rpe) * nsc + kk / SUPER];
+                element_digits<S>(a.x, er, q[0]);
+                element_digits<S>(a.y, er, q[1]);
+                element_digits<S>(b.x, er, q[2]);
+                element_digits<S>(b.y, er, q[3]);
+            } else {
+#pragma unroll
+                for (int i = 0; i < 4; i++)
+#pragma unroll
+                    for (int j = 0; j < S; j++) q[i][j] = 0;
+            }
+            const long long o = (static_cast<long long>(r) * Kpad + kk) >> 2;
+            float sc = 0.00390625f;
+#pragma unroll
+            for (int j = 0; j < S; j++) {
+                uint2 w;
+                w.x = qbf16(q[0][j], sc) | (qbf16(q[1][j], sc) << 16);
+                w.y = qbf16(q[2][j], sc) | (qbf16(q[3][j], sc) << 16);
+                out[j * sstride4 + o] = w;
+                sc *= 0.00390625f;
+            }
+        }
+    }
+}
+
+// Vector slicer with the digits formed by FP32 additions (digits.cuh, six
+// slices): the same layout and requirements as slice4_kernel; the slices are
+// an equally exact split of the same 48-bit values (digits may differ from the
+// integer path only where a digit rounds a tie, to even here).  The BF16 words
+// are the upper halves of the FP32 digits, paired with one byte permute.
+__global__ void __launch_bounds__(256) slice4f_kernel(Src src, int rows, int K, int Kpad, const int *e, int rpe,
+                                                      int nsc, uint2 *out, long long sstride4) {
+    constexpr int S = 6;
+    const int kk = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
+    if (kk >= Kpad) return;
+    long long koff = 0;
+    if (kk < K) {
+        const int ko = kk / src.kin, ki = kk - ko * src.kin;
+        koff = static_cast<long long>(ko) * src.sko + ki;
+    }
+    for (int rb = blockIdx.y * 8; rb < rows; rb += gridDim.y * 8) {
+        const int rend = min(rows, rb + 8);
+        for (int r = rb; r < rend; r++) {
+            float v[4][S];
+            if (kk < K) {
+                const double2 *p2 = reinterpret_cast<const double2 *>(src_row(src, r) + koff);
+                const double2 a = p2[0], b = p2[1];
+                const int er = e[(r / rpe) * nsc + kk / SUPER];
+                digits::split48(to_fixed(a.x, er, 48), v[0]);
+                digits::split48(to_fixed(a.y, er, 48), v[1]);
+                digits::split48(to_fixed(b.x, er, 48), v[2]);
+                digits::split48(to_fixed(b.y, er, 48), v[3]);
+            } else {
+#pragma unroll
+                for (int i = 0; i < 4; i++)
+#pragma unroll
+                    for (int j = 0; j < S; j++) v[i][j] = 0.0f;
+            }
+            const long long o = (static_cast<long long>(r) * Kpad + kk) >> 2;
+#pragma unroll
+            for (int j = 0; j < S; j++) {
+                uint2 w;
+                w.x = __byte_perm(__float_as_uint(v[0][j]), __float_as_uint(v[1][j]), 0x7632);
+                w.y = __byte_perm(__float_as_uint(v[2][j]), __float_as_uint(v[3][j]), 0x7632);
+                out[j * sstride4 + o] = w;
+            }
+        }
+    }
+}
+
+// e[g] for groups that are contiguous runs of `len` doubles starting at p + g*len
+// (len even, p 16-byte aligned): 16-byte loads.
+__global__ void __launch_bounds__(256) expo_flat_kernel(const double *p, long long len, int *e) {
+    __shared__ unsigned long long red[8];
+    const double2 *q = reinterpret_cast<const double2 *>(p + blockIdx.x * len);
+    unsigned long long mx = 0;
+    for (long long t = threadIdx.x; t < len / 2; t += 256) {
+        const double2 v = q[t];
+        const unsigned long long a = static_cast<unsigned long long>(__double_as_longlong(v.x)) & 0x7FFFFFFFFFFFFFFFull;
+        const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(v.y)) & 0x7FFFFFFFFFFFFFFFull;
+        mx = a > mx ? a : mx;
+        mx = b > mx ? b : mx;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long y = __shfl_down_sync(0xffffffffu, mx, o);
+        mx = y > mx ? y : mx;
+    }
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long m = red[0];
+        for (int i = 1; i < 8; i++) m = red[i] > m ? red[i] : m;
+        e[blockIdx.x] = exponent_of_max(m);
+    }
+}
+
+constexpr int SLICE_ROWS = 8;   // rows per block of the slicer
+
+// out[j][r][kk] = q_j(r, kk) * 2^(-8(j+1)) for j = 0..S-1 (bf16), zero for kk >= K.
+template <int S>
+__global__ void __launch_bounds__(256) slice_kernel(Src src, int rows, int K, int Kpad, const int *e,
+                                                    int rpe, int nsc, unsigned short *out, long long sstride) {
+    const int kk = blockIdx.x * blockDim.x + threadIdx.x;
+    if (kk >= Kpad) return;
+    long long koff = 0;
+    if (kk < K) {
+        const int ko = kk / src.kin, ki = kk - ko * src.kin;
+        koff = static_cast<long long>(ko) * src.sko + static_cast<long long>(ki) * src.ski;
+    }
+    for (int rb = blockIdx.y * SLICE_ROWS; rb < rows; rb += gridDim.y * SLICE_ROWS) {
+        const int rend = min(rows, rb + SLICE_ROWS);
+        for (int r = rb; r < rend; r++) {
+            int q[S];
+#pragma unroll
+            for (int j = 0; j < S; j++) q[j] = 0;
+            if (kk < K) element_digits<S>(src_row(src, r)[koff], e[(r / rpe) * nsc + kk / SUPER], q);
+            const long long o = static_cast<long long>(r) * Kpad + kk;
+            float sc = 0.00390625f;
+#pragma unroll
+            for (int j = 0; j < S; j++) {
+                out[j * sstride + o] = static_cast<unsigned short>(qbf16(q[j], sc));
+                sc *= 0.00390625f;
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Grouped slicing: many operands in one launch
+// ---------------------------------------------------------------------------
+// A batched build slices the factor chunk and both panel operands of every
+// density of every molecule in a wave; one exponent launch and one slicer
+// launch take them all, their jobs carried in the parameter space (no device
+// table to upload, so the launch stays capturable in a CUDA graph).  Each job
+// is one operand as slice_operand would slice it; block b of a launch belongs
+// to the job whose block range [b0, b0 + blocks) holds it.
+struct SliceJob {
+    Src src;
+    int *e;                // exponents: written by the exponent launch, read by the slicer
+    void *out;             // S planes, rows x Kpad each
+    long long sstride;     // plane stride in units of the output words (uint2 when vec, else ushort)
+    int rows, K, Kpad, rpe, nsc;
+    int vec;               // 4-element vector path (alignment checked on the host)
+    int flat;              // exponent groups are contiguous runs of rpe * K doubles
+    int eb0, sb0;          // first block of this job in the exponent and the slicer launch
+    int nbx, nby;          // slicer blocks along K (x) and rows (y)
+};
+constexpr int MAXJOB = 200;
+struct SliceGroup {
+    SliceJob j[MAXJOB];
+    int njob;
+};
+
+__device__ __forceinline__ int job_of_block(const SliceGroup &g, int b, bool expo) {
+    int lo = 0, hi = g.njob - 1;
+    while (lo < hi) {   // the last job whose first block is <= b
+        const int mid = (lo + hi + 1) >> 1;
+        if ((expo ? g.j[mid].eb0 : g.j[mid].sb0) <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// The exponents of every job: expo_kernel's (or expo_flat_kernel's) work for
+// the job's row group g and super-chunk z.
+__global__ void __launch_bounds__(256) expo_group_kernel(const __grid_constant__ SliceGroup g) {
+    __shared__ unsigned long long red[8];
+    const int ji = job_of_block(g, blockIdx.x, true);
+    const SliceJob &jb = g.j[ji];
+    const int lb = blockIdx.x - jb.eb0;
+    unsigned long long mx = 0;
+    int slot;
+    if (jb.flat) {
+        const long long len = static_cast<long long>(jb.rpe) * jb.K;
+        const double2 *q = reinterpret_cast<const double2 *>(jb.src.p + lb * len);
+        for (long long t = threadIdx.x; t < len / 2; t += 256) {
+            const double2 v = q[t];
+            const unsigned long long a = static_cast<unsigned long long>(__double_as_longlong(v.x)) & 0x7FFFFFFFFFFFFFFFull;
+            const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(v.y)) & 0x7FFFFFFFFFFFFFFFull;
+            mx = a > mx ? a : mx;
+            mx = b > mx ? b : mx;
+        }
+        slot = lb;
+    } else {
+        const Src src = jb.src;
+        const int gi = lb / jb.nsc, z = lb - gi * jb.nsc;
+        const int r0 = gi * jb.rpe, r1 = min(jb.rows, r0 + jb.rpe);
+        const int k0 = z * SUPER, k1 = min(jb.K, k0 + SUPER);
+        const int step_o = 256 / src.kin, step_i = 256 % src.kin;
+        for (int r = r0; r < r1; r++) {
+            const double *row = src_row(src, r);
+            int ko = (k0 + threadIdx.x) / src.kin, ki = k0 + threadIdx.x - ko * src.kin;
+            for (int kk = k0 + threadIdx.x; kk < k1; kk += 256) {
+                const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(
+                                                 row[static_cast<long long>(ko) * src.sko +
+                                                     static_cast<long long>(ki) * src.ski])) &
+                                             0x7FFFFFFFFFFFFFFFull;
+                mx = b > mx ? b : mx;
+                ko += step_o;
+                ki += step_i;
+                if (ki >= src.kin) { ki -= src.kin; ko++; }
+            }
+        }
+        slot = gi * jb.nsc + z;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long y = __shfl_down_sync(0xffffffffu, mx, o);
+        mx = y > mx ? y : mx;
+    }
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long m = red[0];
+        for (int i = 1; i < 8; i++) m = red[i] > m ? red[i] : m;
+        jb.e[slot] = exponent_of_max(m);
+    }
+}
+
+// The slices of every job: slice4_kernel's work (vector jobs) or
+// slice_kernel's (the others) for the job's block (bx, by).
+template <int S>
+__global__ void __launch_bounds__(256) slice_group_kernel(const __grid_constant__ SliceGroup g) {
+    const int ji = job_of_block(g, blockIdx.x, false);
+    const SliceJob &jb = g.j[ji];
+    const int lb = blockIdx.x - jb.sb0;
+    const int by = lb / jb.nbx, bx = lb - by * jb.nbx;
+    const Src src = jb.src;
+    const int rows = jb.rows, K = jb.K, Kpad = jb.Kpad, rpe = jb.rpe, nsc = jb.nsc;
+    const int *e = jb.e;
+    if (jb.vec) {
+        const int kk = 4 * (bx * 256 + threadIdx.x);
+        if (kk >= Kpad) return;
+        uint2 *out = static_cast<uint2 *>(jb.out);
+        long long koff = 0;
+        if (kk < K) {
+            const int ko = kk / src.kin, ki = kk - ko * src.kin;
+            koff = static_cast<long long>(ko) * src.sko + ki;
+        }
+        for (int rb = by * 8; rb < rows; rb += jb.nby * 8) {
+            const int rend = min(rows, rb + 8);
+            for (int r = rb; r < rend; r++) {
+                int q[4][S];
+                if (kk < K) {
+                    const double2 *p2 = reinterpret_cast<const double2 *>(src_row(src, r) + koff);
+                    const double2 a = p2[0], b = p2[1];
+                    const int er = e[(r / rpe) * nsc + kk / SUPER];
+                    element_digits<S>(a.x, er, q[0]);
+                    element_digits<S>(a.y, er, q[1]);
+                    element_digits<S>(b.x, er, q[2]);
+                    element_digits<S>(b.y, er, q[3]);
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 4; i++)
+#pragma unroll
+                        for (int j = 0; j < S; j++) q[i][j] = 0;
+                }
+                const long long o = (static_cast<long long>(r) * Kpad + kk) >> 2;
+                float sc = 0.00390625f;
+#pragma unroll
+                for (int j = 0; j < S; j++) {
+                    uint2 w;
+                    w.x = qbf16(q[0][j], sc) | (qbf16(q[1][j], sc) << 16);
+                    w.y = qbf16(q[2][j], sc) | (qbf16(q[3][j], sc) << 16);
+                    out[j * jb.sstride + o] = w;
+                    sc *= 0.00390625f;
+                }
+            }
+        }
+    } else {
+        const int kk = bx * 256 + threadIdx.x;
+        if (kk >= Kpad) return;
+        unsigned short *out = static_cast<unsigned short *>(jb.out);
+        long long koff = 0;
+        if (kk < K) {
+            const int ko = kk / src.kin, ki = kk - ko * src.kin;
+            koff = static_cast<long long>(ko) * src.sko + static_cast<long long>(ki) * src.ski;
+        }
+        for (int rb = by * SLICE_ROWS; rb < rows; rb += jb.nby * SLICE_ROWS) {
+            const int rend = min(rows, rb + SLICE_ROWS);
+            for (int r = rb; r < rend; r++) {
+                int q[S];
+#pragma unroll
+                for (int j = 0; j < S; j++) q[j] = 0;
+                if (kk < K) element_digits<S>(src_row(src, r)[koff], e[(r / rpe) * nsc + kk / SUPER], q);
+                const long long o = static_cast<long long>(r) * Kpad + kk;
+                float sc = 0.00390625f;
+#pragma unroll
+                for (int j = 0; j < S; j++) {
+                    out[j * jb.sstride + o] = static_cast<unsigned short>(qbf16(q[j], sc));
+                    sc *= 0.00390625f;
+                }
+            }
+        }
+    }
+}
+
+}  // namespace oz
+}  // namespace jk
