@@ -454,22 +454,19 @@ ozgemm_kernel(const __grid_constant__ OzGroup g) {
                     __syncwarp();
                     if (lane == 0) tc::mbar_arrive(&accempty[d]);
                     // An exact accumulator d holds integers in units of 2^-(8d+16)
-                    // below 2^24; a tile-long one stays far below one unit of the
-                    // output's 2^-FRAC.  Scale to the unit and convert with one
-                    // FFMA against 1.5*2^23 (exact below 2^22; the rare larger
-                    // value falls back to F2I), then add into the 2^-FRAC fixed
-                    // point of acc64 (shifted by FRAC - 16 - 8d for the exact
-                    // diagonals).  No 64-bit float conversions: those run on the
-                    // scarce FP64 pipe.
+                    // below 2^24; a tile-long one stays far below 2^31 units of the
+                    // output's 2^-FRAC.  Scale to the unit (exact: a power of two),
+                    // convert to int32 (F2I, round to nearest: exact for the exact
+                    // diagonals), then add into the 2^-FRAC fixed point of acc64
+                    // (shifted by FRAC - 16 - 8d for the exact diagonals).  No
+                    // branches and no 64-bit float conversions (those run on the
+                    // scarce FP64 pipe).
                     const bool exact = d < C::NEXACT;
                     const float unit = exact ? __int_as_float((127 + 16 + 8 * d) << 23) : __int_as_float((127 + C::FRAC) << 23);
-                    const float vmax = exact ? __int_as_float((127 + 22 - 16 - 8 * d) << 23)
-                                             : __int_as_float((127 + 22 - C::FRAC) << 23);
                     const int sh = exact ? C::FRAC - 16 - 8 * d : 0;
 #pragma unroll
                     for (int i = 0; i < OUT_COLS; i++) {
-                        int xi = __float_as_int(__fmaf_rn(v[i], unit, 12582912.0f)) - 0x4B400000;
-                        if (fabsf(v[i]) > vmax) xi = __float2int_rn(v[i] * unit);
+                        const int xi = __float2int_rn(v[i] * unit);
                         acc64[i] += static_cast<long long>(static_cast<unsigned long long>(static_cast<long long>(xi)) << sh);
                     }
                 }
