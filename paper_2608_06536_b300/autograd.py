@@ -39,11 +39,28 @@ class _JKFunction(torch.autograd.Function):
                 grads += [dX[s], torch.zeros_like(dY[s])]
             else:
                 grads += [dX[s], dY[s]]
+        if want_dl and L.dim() == 2:
+            dL = fold_packed_grad(dL)
         return (None, None, None, dL if want_dl else None, *grads)
+
+
+def fold_packed_grad(dL):
+    """The gradient with respect to a packed factor ([naux][n(n+1)/2], the
+    row-major upper triangles of the symmetric L^P) from the dense one
+    ([naux][n][n]): an off-diagonal packed entry stands for both L^P_ij and
+    L^P_ji, so it collects dL_ij + dL_ji; a diagonal entry collects dL_ii once."""
+    n = int(dL.shape[-1])
+    iu = torch.triu_indices(n, n, device=dL.device)
+    off = (iu[0] != iu[1]).to(dL.dtype)
+    return (dL[:, iu[0], iu[1]] + off * dL[:, iu[1], iu[0]]).contiguous()
 
 
 def jk(L, X, Y=None, sym=None, precision="fp64", engine=None):
     """Differentiable (J, K), each [nd][n][n], for D_s = X_s Y_s^T.
+
+    L is the dense factor [naux][n][n], or the packed one [naux][n(n+1)/2]
+    when the engine runs with the packed_factor option; its gradient has L's
+    own layout (folded onto the upper triangles for a packed factor).
 
     For a symmetric density pass Y_s = None (or sym[s] = True); its gradient
     then arrives entirely on X_s.

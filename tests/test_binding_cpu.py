@@ -321,3 +321,28 @@ def test_packed_factor_through_the_binding(rec):
     assert calls[3][1][1]._obj.nbf == n
     opt = [c for c in rec.lib.calls if c[0] == "jk_set_option"]
     assert opt and opt[0][1][1:] == (jk.OPTIONS["packed_factor"], 1)
+
+
+def test_packed_factor_gradient_fold():
+    """The packed factor's gradient is the dense one pulled back through the
+    unpacking map p -> L (L_ij = L_ji = p_k): autograd through an explicit
+    unpacking of random packed entries gives the fold, diagonal entries once."""
+    from paper_2608_06536_b300.autograd import fold_packed_grad
+    rng = np.random.default_rng(3)
+    naux, n = 3, 7
+    G = torch.tensor(rng.standard_normal((naux, n, n)))
+    p = torch.tensor(rng.standard_normal((naux, n * (n + 1) // 2)), requires_grad=True)
+    pos = {}
+    k = 0
+    for i in range(n):
+        for j in range(i, n):
+            pos[i, j] = pos[j, i] = k
+            k += 1
+    idx = torch.tensor([[pos[i, j] for j in range(n)] for i in range(n)])
+    L = p[:, idx.reshape(-1)].reshape(naux, n, n)
+    assert torch.equal(L, L.transpose(1, 2))
+    (gp,) = torch.autograd.grad((G * L).sum(), [p])
+    assert torch.equal(fold_packed_grad(G), gp)
+    # by hand for one off-diagonal and one diagonal entry of aux index 1
+    assert fold_packed_grad(G)[1, pos[2, 5]] == G[1, 2, 5] + G[1, 5, 2]
+    assert fold_packed_grad(G)[1, pos[4, 4]] == G[1, 4, 4]

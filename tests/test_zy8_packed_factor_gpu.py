@@ -202,3 +202,36 @@ def test_packed_factor_adjoint(precision):
     assert err(dXp[1], dXd[1]) < tol and err(dXp[1], dXo[1] + dYo[1]) < tol
     assert np.all(dYp[1] == 0) and np.all(dYd[1] == 0)
     assert err(dLp, dLd) < tol and err(dLp, dLo) < tol
+
+
+@pytest.mark.parametrize("precision", ["fp64", "split"])
+def test_packed_factor_autograd(precision):
+    """Through the autograd wrapper a packed factor gets its gradient in its
+    own layout: the dense factor's dL folded onto the upper triangles."""
+    from paper_2608_06536_b300.autograd import fold_packed_grad, jk as jk_fn
+    m = inputs.custom(40, 30, 9.0, [4, 3], [False, True])
+    rng = np.random.default_rng(11)
+    W = torch.tensor(rng.standard_normal((2, 40, 40))).cuda()
+    V = torch.tensor(rng.standard_normal((2, 40, 40))).cuda()
+    grads = []
+    for packed in (0, 1):
+        eng = jk.Engine("cuda:0")
+        eng.set_option("packed_factor", packed)
+        fac = jk.pack_factor(m.L) if packed else torch.from_numpy(m.L)
+        L = fac.cuda().requires_grad_(True)
+        X = [torch.from_numpy(x).cuda().requires_grad_(True) for x in m.X]
+        Y = [torch.from_numpy(m.Y[0]).cuda().requires_grad_(True), None]
+        J, K = jk_fn(L, X, Y, precision=precision, engine=eng)
+        E = (W * K).sum() + (V * J).sum()
+        g = torch.autograd.grad(E, [L, X[0], X[1], Y[0]])
+        eng.sync_status()
+        grads.append(g)
+        eng.close()
+    (gLd, *gd), (gLp, *gp) = grads
+    assert tuple(gLp.shape) == (30, 40 * 41 // 2)
+    err, tol = (abs_err, SPLIT_ABS) if precision == "split" else (rel_err, FP64_REL)
+    assert err(to_np(gLp), to_np(fold_packed_grad(gLd))) < tol
+    for a, b in zip(gp, gd):
+        assert err(to_np(a), to_np(b)) < tol
+    _, _, dLo = oracle.adjoint(m.L, m.X, m.Y, list(to_np(W)), list(to_np(V)))
+    assert err(to_np(gLp), to_np(fold_packed_grad(torch.from_numpy(dLo)))) < tol
