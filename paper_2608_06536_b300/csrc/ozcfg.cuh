@@ -13,7 +13,7 @@ constexpr int KB = 16;              // reduction elements per pipeline stage (on
 constexpr int KBPC = 8;             // K-blocks of a 128-element exact window
 constexpr int WPERIOD = 2 * KBPC;   // the window pattern repeats every 16 K-blocks
 constexpr int SUPER = 2048;         // reduction elements per int64 partial
-constexpr int NSTAGE = 3;
+constexpr int SMEM_MAX = 227 * 1024;   // opt-in shared memory per CTA
 constexpr int THREADS = 320;        // producer warp, MMA warp, 8 epilogue warps
 constexpr int MAXMMA = 12;          // most merged MMAs per K-block of any configuration
 
@@ -50,12 +50,15 @@ struct Cfg {
     static constexpr int OUT_BLK = 8;
     static constexpr int OUT_WARP_BYTES = 32 * OUT_COLS * 8;
     static constexpr int OUT_BYTES = 8 * OUT_WARP_BYTES;
+    // operand stages: as many as fit beside the output staging, at most 4
+    static constexpr int NST_FIT = (SMEM_MAX - OUT_BYTES - 1024 - 256) / STAGE_BYTES;
+    static constexpr int NSTAGE = NST_FIT < 4 ? NST_FIT : 4;
     static constexpr int SMEM_BYTES = NSTAGE * STAGE_BYTES + OUT_BYTES + 1024 /*align slack*/ + 256 /*barriers*/;
     static_assert(S * BN <= 512, "the accumulators fit tensor memory");
     static_assert(BN % 16 == 0 && OUT_COLS % OUT_BLK == 0, "tile width");
     static_assert(NEXACT >= 1 && NEXACT <= 5, "window schedule");
     static_assert(FRAC >= 16 + 8 * (NEXACT - 1) && FRAC + 11 <= 62, "exact drains and the int64 range");
-    static_assert(SMEM_BYTES <= 227 * 1024, "shared memory");
+    static_assert(NSTAGE >= 2 && SMEM_BYTES <= SMEM_MAX, "shared memory");
 };
 using Cfg6 = Cfg<6, 80>;
 using Cfg6n = Cfg<6, 64>;

@@ -119,25 +119,38 @@ __host__ __device__ constexpr MmaList make_mma_list() {
 }
 
 // Issue order per window residue r: the MMAs that touch an accumulator whose
-// window restarts at r go last (each group keeps the list's order), so the
-// MMA thread has the most work queued before it must wait for that
-// accumulator's drain.
+// window ends at r go first, so that its drain can be signalled (committed)
+// as soon as they finish and overlaps the rest of the K-block; the MMAs that
+// touch an accumulator whose window restarts at r go last, so the MMA thread
+// has the most work queued before it must wait for that accumulator's drain
+// (each group keeps the list's order; window starts and ends never share a
+// residue).  nend[r] counts the first group.
 struct MmaOrder {
     int v[WPERIOD][MAXMMA];
+    int nend[WPERIOD];
 };
 template <class C>
 __host__ __device__ constexpr MmaOrder make_mma_order(const MmaList &L) {
     MmaOrder t{};
     for (int r = 0; r < WPERIOD; r++) {
-        const unsigned m = ws_mask<C>(r);
+        const unsigned ms = ws_mask<C>(r), me = we_mask<C>(r);
         int c = 0;
-        for (int pass = 0; pass < 2; pass++)
+        for (int pass = 0; pass < 3; pass++) {
             for (int j = 0; j < L.n; j++) {
                 const unsigned mj = ((1u << L.nb[j]) - 1u) << (L.a[j] + L.b0[j]);
-                if (((mj & m) != 0) == (pass == 1)) t.v[r][c++] = j;
+                const int grp = (mj & me) ? 0 : (mj & ms) ? 2 : 1;
+                if (grp == pass) t.v[r][c++] = j;
             }
+            if (pass == 0) t.nend[r] = c;
+        }
     }
     return t;
+}
+template <class C>
+__host__ __device__ constexpr bool starts_and_ends_apart() {
+    for (int r = 0; r < WPERIOD; r++)
+        if (ws_mask<C>(r) & we_mask<C>(r)) return false;
+    return true;
 }
 
 template <class C>
@@ -161,6 +174,8 @@ __host__ __device__ constexpr bool mma_list_covers_pairs() {
 }
 static_assert(mma_list_covers_pairs<Cfg6>() && mma_list_covers_pairs<Cfg6n>() && mma_list_covers_pairs<Cfg7>(),
               "every slice pair with a + b < S exactly once");
+static_assert(starts_and_ends_apart<Cfg6>() && starts_and_ends_apart<Cfg7>(),
+              "no accumulator window both starts and ends at one residue");
 
 // Drain order at a tile end: the first MMAs of the next tile need the
 // tile-long accumulators, then the exact ones from the lowest diagonal up.
@@ -229,7 +244,17 @@ __device__ __forceinline__ TileCoord tile_of(const OzProb &pr, int u, int raster
 // zeroed it.  Returns false if a wait gave up.
 template <class C, int R, int I>
 __device__ __forceinline__ bool issue_mmas(uint32_t tmem, uint64_t ad0, uint64_t bd0, unsigned &pend,
-                                           int (&wcnt)[C::NACC], uint64_t *accempty, volatile int *abort_flag) {
+                                           int (&wcnt)[C::NACC], uint64_t *accfull, uint64_t *accempty,
+                                           bool early, volatile int *abort_flag) {
+    if constexpr (I == Tabs<C>::order.nend[R] && I > 0) {
+        // the windows ending at this residue have all their MMAs issued
+        if (early) {
+            constexpr unsigned kEnds = we_mask<C>(R);
+#pragma unroll
+            for (int d = 0; d < C::NACC; d++)
+                if (kEnds & (1u << d)) tc::mma_commit(&accfull[d]);
+        }
+    }
     if constexpr (I == Tabs<C>::list.n) {
         return true;
     } else {
@@ -253,7 +278,7 @@ __device__ __forceinline__ bool issue_mmas(uint32_t tmem, uint64_t ad0, uint64_t
         // descriptor start addresses are in 16-byte units
         tc::mma_bf16(tmem + d0 * C::BN, ad0 + static_cast<uint64_t>(a * (BM * 32 / 16)),
                      bd0 + static_cast<uint64_t>(b0 * (C::BN * 32 / 16)), tc::idesc_bf16_f32(BM, C::BN * nb), 1u);
-        return issue_mmas<C, R, I + 1>(tmem, ad0, bd0, pend, wcnt, accempty, abort_flag);
+        return issue_mmas<C, R, I + 1>(tmem, ad0, bd0, pend, wcnt, accfull, accempty, early, abort_flag);
     }
 }
 
@@ -278,13 +303,16 @@ __device__ __forceinline__ bool issue_period(uint8_t *smem, uint32_t tmem, int k
         unsigned pend = kStarts | ((R == 0 && kb0 == 0) ? kAll : 0u);
         const uint64_t ad0 = tc::sdesc_kmajor_sw32(tc::smem_u32(smem + stage * C::STAGE_BYTES));
         const uint64_t bd0 = ad0 + static_cast<uint64_t>(C::A_BYTES / 16);
-        if (!issue_mmas<C, R, 0>(tmem, ad0, bd0, pend, wcnt, accempty, abort_flag)) return false;
+        // the residue's window ends are committed right after their MMAs,
+        // except in the tile's last K-block, which ends every window at once
+        const bool last = kb == nkb - 1;
+        if (!issue_mmas<C, R, 0>(tmem, ad0, bd0, pend, wcnt, accfull, accempty, !last, abort_flag)) return false;
         tc::mma_commit(&empty[stage]);
-        const unsigned ends = kEnds | (kb == nkb - 1 ? kAll : 0u);
+        if (last) {
 #pragma unroll
-        for (int d = 0; d < C::NACC; d++)
-            if (ends & (1u << d)) tc::mma_commit(&accfull[d]);
-        if (++stage == NSTAGE) {
+            for (int d = 0; d < C::NACC; d++) tc::mma_commit(&accfull[d]);
+        }
+        if (++stage == C::NSTAGE) {
             stage = 0;
             phase ^= 1u;
         }
@@ -319,10 +347,10 @@ ozgemm_kernel(const __grid_constant__ OzGroup g) {
     constexpr int OUT_COLS = C::OUT_COLS;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    uint8_t *outbuf = smem + NSTAGE * C::STAGE_BYTES;
+    uint8_t *outbuf = smem + C::NSTAGE * C::STAGE_BYTES;
     uint64_t *full = reinterpret_cast<uint64_t *>(outbuf + C::OUT_BYTES);
-    uint64_t *empty = full + NSTAGE;
-    uint64_t *accfull = empty + NSTAGE;
+    uint64_t *empty = full + C::NSTAGE;
+    uint64_t *accfull = empty + C::NSTAGE;
     uint64_t *accempty = accfull + NACC;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(accempty + NACC);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
@@ -333,7 +361,7 @@ ozgemm_kernel(const __grid_constant__ OzGroup g) {
     const int ustep = static_cast<int>(gridDim.x);
 
     if (threadIdx.x == 0) {
-        for (int i = 0; i < NSTAGE; i++) { tc::mbar_init(&full[i], 1); tc::mbar_init(&empty[i], 1); }
+        for (int i = 0; i < C::NSTAGE; i++) { tc::mbar_init(&full[i], 1); tc::mbar_init(&empty[i], 1); }
         for (int i = 0; i < NACC; i++) { tc::mbar_init(&accfull[i], 1); tc::mbar_init(&accempty[i], 8); }
         *abort_flag = 0;
         tc::fence_barrier_init();
@@ -370,7 +398,7 @@ ozgemm_kernel(const __grid_constant__ OzGroup g) {
                     tc::mbar_expect_tx(&full[stage], C::STAGE_BYTES);
                     tc::tma_load_3d(sa, &pr.tmA, &full[stage], kc, tc_.m * BM, 0);
                     tc::tma_load_3d(sa + C::A_BYTES, &pr.tmB, &full[stage], kc, tc_.n * BN, 0);
-                    if (++stage == NSTAGE) { stage = 0; phase ^= 1u; }
+                    if (++stage == C::NSTAGE) { stage = 0; phase ^= 1u; }
                 }
             }
         }
