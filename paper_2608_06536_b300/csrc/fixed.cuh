@@ -100,13 +100,23 @@ JK_HD double round_top(bool neg, uint64_t top, bool sticky, int x2) {
 }
 
 // v * 2^e2 rounded once to FP64 (ties to even); the result must be a normal
-// double (true for every value the GEMM forms).
+// double (true for every value the GEMM forms).  Branch-free: the GEMM's
+// epilogue converts whole tiles with it.  With the leading one of |v| moved to
+// bit 63 (top), the 53 kept bits are top >> 11 and the 11 dropped ones decide
+// the rounding; adding the rounded significand (implicit bit included) to the
+// exponent field one below the leading bit's carries a rounding overflow
+// (2^53) into the exponent by itself.
 JK_HD double i64_to_f64_scaled(long long v, int e2) {
-    if (v == 0) return 0.0;
-    const bool neg = v < 0;
-    const uint64_t a = neg ? 0ull - static_cast<uint64_t>(v) : static_cast<uint64_t>(v);
-    const int lz = clz64(a);
-    return round_top(neg, a << lz, false, e2 + 63 - lz);
+    const uint64_t u = static_cast<uint64_t>(v);
+    const uint64_t a = v < 0 ? 0ull - u : u;
+    const int lz = clz64(a | 1ull);
+    const uint64_t top = a << lz;
+    const uint64_t mant = top >> 11;
+    const uint64_t rest = top & 0x7FFull;
+    const uint64_t up = (rest + (mant & 1ull)) > 0x400ull ? 1ull : 0ull;
+    const uint64_t bits = (u & 0x8000000000000000ull) +
+                          (static_cast<uint64_t>(e2 + 63 - lz + 1022) << 52) + mant + up;
+    return a == 0 ? 0.0 : bits_f64(bits);
 }
 
 // The same for a 128-bit accumulator (the exactly aligned sum of split-K

@@ -41,6 +41,10 @@ struct OzArgs {
 // partial sum below 2^24.  Window starts are spread over the even K-blocks of
 // the 16-block period (d0: 0; d1: 8; d2: 2, 10; d3: 6, 14; d4: 4, 12) so that
 // drains do not coincide and no two consecutive K-blocks both start one.
+// Every window restarts with the tile, which would make diagonal 2's first
+// window two K-blocks long and its drain due while the epilogue is still
+// finishing the previous tile; instead that window runs on to the second
+// one's end (K-blocks 0..9, 160 elements, still below 2^24 units).
 __host__ __device__ constexpr int wper(int d) { return d < 2 ? WPERIOD : KBPC; }
 __host__ __device__ constexpr int woff(int d) { return d == 0 ? 0 : d == 1 ? KBPC : d == 2 ? 2 : d == 3 ? 6 : 4; }
 __host__ __device__ constexpr bool ws_r(int d, int r) { return (r - woff(d) + WPERIOD) % wper(d) == 0; }
@@ -53,6 +57,12 @@ __host__ __device__ constexpr unsigned ws_mask(int r) {
 }
 template <class C>
 __host__ __device__ constexpr unsigned we_mask(int r) { return ws_mask<C>((r + 1) % WPERIOD); }
+// The window boundary that a tile's first period skips (see above).
+constexpr int kMergedDiag = 2;
+constexpr int kMergedEnd = 1;   // K-block of the skipped end; the skipped start is the next one
+static_assert(woff(kMergedDiag) == kMergedEnd + 1 &&
+                  (kMergedEnd + 1 + wper(kMergedDiag)) * KB * (65536 + 16384) < (1 << 24),
+              "diagonal 2's merged first window stays exact");
 // The window ends of K-block residue r, at run time.
 template <class C>
 __device__ __forceinline__ unsigned we_mask_rt(int r) {
@@ -174,6 +184,8 @@ __host__ __device__ constexpr bool mma_list_covers_pairs() {
 }
 static_assert(mma_list_covers_pairs<Cfg6>() && mma_list_covers_pairs<Cfg6n>() && mma_list_covers_pairs<Cfg7>(),
               "every slice pair with a + b < S exactly once");
+static_assert(we_mask<Cfg6>(kMergedEnd) == (1u << kMergedDiag) && we_mask<Cfg7>(kMergedEnd) == (1u << kMergedDiag),
+              "the skipped window end is the only one at its residue");
 static_assert(starts_and_ends_apart<Cfg6>() && starts_and_ends_apart<Cfg7>(),
               "no accumulator window both starts and ends at one residue");
 
@@ -299,14 +311,19 @@ __device__ __forceinline__ bool issue_period(uint8_t *smem, uint32_t tmem, int k
         constexpr unsigned kAll = (1u << C::NACC) - 1u;
         constexpr unsigned kStarts = ws_mask<C>(R);
         constexpr unsigned kEnds = we_mask<C>(R);
-        // the tile's first K-block opens every accumulator
+        // the tile's first K-block opens every accumulator; its first period
+        // keeps diagonal 2's first window open through K-block 9
         unsigned pend = kStarts | ((R == 0 && kb0 == 0) ? kAll : 0u);
+        if constexpr (R == kMergedEnd + 1) {
+            if (kb0 == 0) pend &= ~(1u << kMergedDiag);
+        }
         const uint64_t ad0 = tc::sdesc_kmajor_sw32(tc::smem_u32(smem + stage * C::STAGE_BYTES));
         const uint64_t bd0 = ad0 + static_cast<uint64_t>(C::A_BYTES / 16);
         // the residue's window ends are committed right after their MMAs,
         // except in the tile's last K-block, which ends every window at once
         const bool last = kb == nkb - 1;
-        if (!issue_mmas<C, R, 0>(tmem, ad0, bd0, pend, wcnt, accfull, accempty, !last, abort_flag)) return false;
+        const bool early = !last && !(R == kMergedEnd && kb0 == 0);
+        if (!issue_mmas<C, R, 0>(tmem, ad0, bd0, pend, wcnt, accfull, accempty, early, abort_flag)) return false;
         tc::mma_commit(&empty[stage]);
         if (last) {
 #pragma unroll
@@ -458,7 +475,8 @@ ozgemm_kernel(const __grid_constant__ OzGroup g) {
                 if (lane < OUT_COLS - 32 && c0 + 32 + lane < a.N) eb_hi = a.eB[(c0 + 32 + lane) / a.b_rpe];
             }
             for (int kb = 0; kb < tc_.nkb && ok; kb++) {
-                const unsigned ends = we_mask_rt<C>(kb & (WPERIOD - 1)) | (kb == tc_.nkb - 1 ? (1u << NACC) - 1u : 0u);
+                const unsigned wends = we_mask_rt<C>(kb & (WPERIOD - 1)) & (kb == kMergedEnd ? ~(1u << kMergedDiag) : ~0u);
+                const unsigned ends = wends | (kb == tc_.nkb - 1 ? (1u << NACC) - 1u : 0u);
                 if (!ends) continue;
                 // one copy of the drain-and-convert code for all accumulators
                 // (per-accumulator unrolled copies cost instruction-cache misses)
@@ -505,25 +523,35 @@ ozgemm_kernel(const __grid_constant__ OzGroup g) {
                 uint8_t *wbuf = outbuf + ew * C::OUT_WARP_BYTES;
                 if (lane == 0) tc::bulk_wait_read();   // previous tile's store has read the buffer
                 __syncwarp();
+                // the int64 accumulators as they are (the split-K partials' form) ...
 #pragma unroll
                 for (int b = 0; b < OUT_COLS / OUT_BLK; b++) {
-                    uint8_t *blk = wbuf + b * (32 * OUT_BLK * 8);
 #pragma unroll
                     for (int j = 0; j < OUT_BLK / 2; j++) {   // 16-byte chunks of this row
                         const int i0 = b * OUT_BLK + 2 * j;
-                        long long w0 = acc64[i0], w1 = acc64[i0 + 1];
-                        if (a.nsuper == 1) {
-                            const int col = c0 + i0;
-                            const int eb0 = __shfl_sync(0xffffffffu, i0 < 32 ? eb_lo : eb_hi, i0 & 31);
-                            const int eb1 = __shfl_sync(0xffffffffu, i0 + 1 < 32 ? eb_lo : eb_hi, (i0 + 1) & 31);
-                            const double d0 = col < a.N && row < a.M ? i64_to_f64_scaled(w0, ea + eb0) : 0.0;
-                            const double d1 = col + 1 < a.N && row < a.M ? i64_to_f64_scaled(w1, ea + eb1) : 0.0;
-                            w0 = __double_as_longlong(d0);
-                            w1 = __double_as_longlong(d1);
-                        }
                         const int chunk = j ^ ((lane >> 1) & 3);   // 64-byte swizzle
-                        longlong2 *dst = reinterpret_cast<longlong2 *>(blk + lane * 64 + chunk * 16);
-                        *dst = make_longlong2(w0, w1);
+                        *reinterpret_cast<longlong2 *>(wbuf + b * (32 * OUT_BLK * 8) + lane * 64 + chunk * 16) =
+                            make_longlong2(acc64[i0], acc64[i0 + 1]);
+                    }
+                }
+                // ... or rounded to FP64 in place: a loop unrolled four times,
+                // enough independent conversions to hide their latency while
+                // the integer-heavy code stays short (fully unrolled copies
+                // cost instruction fetches on every tile)
+                if (a.nsuper == 1) {
+#pragma unroll 4
+                    for (int i0 = 0; i0 < OUT_COLS; i0 += 2) {
+                        const int j = (i0 % OUT_BLK) / 2;
+                        const int chunk = j ^ ((lane >> 1) & 3);
+                        longlong2 *p = reinterpret_cast<longlong2 *>(wbuf + (i0 / OUT_BLK) * (32 * OUT_BLK * 8) + lane * 64 +
+                                                                     chunk * 16);
+                        const longlong2 w = *p;
+                        const int eb0 = __shfl_sync(0xffffffffu, i0 < 32 ? eb_lo : eb_hi, i0 & 31);
+                        const int eb1 = __shfl_sync(0xffffffffu, i0 + 1 < 32 ? eb_lo : eb_hi, (i0 + 1) & 31);
+                        const int col = c0 + i0;
+                        const double d0 = col < a.N && row < a.M ? i64_to_f64_scaled(w.x, ea + eb0) : 0.0;
+                        const double d1 = col + 1 < a.N && row < a.M ? i64_to_f64_scaled(w.y, ea + eb1) : 0.0;
+                        *p = make_longlong2(__double_as_longlong(d0), __double_as_longlong(d1));
                     }
                 }
                 tc::fence_proxy_async_smem();
