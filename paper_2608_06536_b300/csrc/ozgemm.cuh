@@ -86,14 +86,15 @@ template <class C>
 __host__ __device__ constexpr MmaList make_mma_list() {
     MmaList L{};
     if (C::S == 6 && C::BN == 80) {
-        // 21 pairs as 10 MMAs: those touching only the tile-long accumulators
-        // 4, 5 first, the one touching accumulator 0 last (the accumulator
-        // whose window just restarted is needed as late as possible)
-        const int a[10] = {0, 1, 2, 4, 5, 3, 2, 1, 0, 0};
-        const int b0[10] = {4, 3, 3, 0, 0, 0, 0, 0, 3, 0};
-        const int nb[10] = {2, 2, 1, 2, 1, 3, 3, 3, 1, 3};
-        L.n = 10;
-        for (int i = 0; i < 10; i++) {
+        // 21 pairs as 9 MMAs, the fewest with N <= 240 (every MMA reads its
+        // whole A slice from shared memory, whose bandwidth the operand
+        // reads and the TMA writes share): those touching only the tile-long
+        // accumulators 4, 5 first, the one touching accumulator 0 last
+        const int a[9] = {1, 2, 4, 5, 0, 3, 2, 1, 0};
+        const int b0[9] = {3, 3, 0, 0, 3, 0, 0, 0, 0};
+        const int nb[9] = {2, 1, 2, 1, 3, 3, 3, 3, 3};
+        L.n = 9;
+        for (int i = 0; i < 9; i++) {
             L.a[i] = a[i];
             L.b0[i] = b0[i];
             L.nb[i] = nb[i];

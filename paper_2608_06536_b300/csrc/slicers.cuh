@@ -42,30 +42,68 @@ __device__ __forceinline__ const double *src_row(const Src &s, int r) {
     return s.p + static_cast<long long>(ro) * s.sr + static_cast<long long>(ri) * s.sri;
 }
 
+// max|x| bits over one row's reduction indices kk in [k0, k1) (k1 - k0 <=
+// SUPER), for a block of 256 threads: thread t takes kk = k0 + t + 256 i.  The
+// (ko, ki) split of kk is advanced incrementally (no integer division in the
+// loop) and all of a thread's addresses are formed before any load, so its
+// SUPER / 256 loads are in flight together.
+__device__ __forceinline__ unsigned long long row_chunk_max(const double *row, const Src &src, int k0, int k1) {
+    constexpr int U = SUPER / 256;
+    const int step_o = 256 / src.kin, step_i = 256 % src.kin;
+    int ko = (k0 + static_cast<int>(threadIdx.x)) / src.kin, ki = k0 + static_cast<int>(threadIdx.x) - ko * src.kin;
+    long long off[U];
+#pragma unroll
+    for (int i = 0; i < U; i++) {
+        off[i] = static_cast<long long>(ko) * src.sko + static_cast<long long>(ki) * src.ski;
+        ko += step_o;
+        ki += step_i;
+        if (ki >= src.kin) { ki -= src.kin; ko++; }
+    }
+    unsigned long long v[U];
+#pragma unroll
+    for (int i = 0; i < U; i++)
+        v[i] = k0 + static_cast<int>(threadIdx.x) + 256 * i < k1
+                   ? static_cast<unsigned long long>(__double_as_longlong(row[off[i]])) & 0x7FFFFFFFFFFFFFFFull
+                   : 0ull;
+    unsigned long long mx = 0;
+#pragma unroll
+    for (int i = 0; i < U; i++) mx = v[i] > mx ? v[i] : mx;
+    return mx;
+}
+
+// max|x| bits over a contiguous run of len doubles (p 16-byte aligned, len
+// even), for a block of 256 threads: four 16-byte loads in flight per thread.
+__device__ __forceinline__ unsigned long long run_max(const double *p, long long len) {
+    const double2 *q = reinterpret_cast<const double2 *>(p);
+    const long long n2 = len / 2;
+    unsigned long long mx = 0;
+    for (long long t = threadIdx.x; t < n2; t += 4 * 256) {
+        double2 v[4];
+#pragma unroll
+        for (int i = 0; i < 4; i++) v[i] = t + 256 * i < n2 ? q[t + 256 * i] : make_double2(0.0, 0.0);
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+            const unsigned long long a = static_cast<unsigned long long>(__double_as_longlong(v[i].x)) & 0x7FFFFFFFFFFFFFFFull;
+            const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(v[i].y)) & 0x7FFFFFFFFFFFFFFFull;
+            mx = a > mx ? a : mx;
+            mx = b > mx ? b : mx;
+        }
+    }
+    return mx;
+}
+
 // e[g * gridDim.y + z] for row groups g of `rpe` rows and super-chunks z of
 // the reduction index: max|x| over the group's rows and kk in
-// [z*SUPER, (z+1)*SUPER).  Each thread walks kk = k0 + tid, + 256, ... keeping
-// (ko, ki) incrementally, so the hot loop has no integer division.
+// [z*SUPER, (z+1)*SUPER).
 __global__ void __launch_bounds__(256) expo_kernel(Src src, int rows, int K, int rpe, int *e) {
     __shared__ unsigned long long red[8];
     const int g = blockIdx.x, z = blockIdx.y;
     const int r0 = g * rpe, r1 = min(rows, r0 + rpe);
     const int k0 = z * SUPER, k1 = min(K, k0 + SUPER);
-    const int step_o = 256 / src.kin, step_i = 256 % src.kin;
     unsigned long long mx = 0;
     for (int r = r0; r < r1; r++) {
-        const double *row = src_row(src, r);
-        int ko = (k0 + threadIdx.x) / src.kin, ki = k0 + threadIdx.x - ko * src.kin;
-        for (int kk = k0 + threadIdx.x; kk < k1; kk += 256) {
-            const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(
-                                             row[static_cast<long long>(ko) * src.sko +
-                                                 static_cast<long long>(ki) * src.ski])) &
-                                         0x7FFFFFFFFFFFFFFFull;
-            mx = b > mx ? b : mx;
-            ko += step_o;
-            ki += step_i;
-            if (ki >= src.kin) { ki -= src.kin; ko++; }
-        }
+        const unsigned long long m = row_chunk_max(src_row(src, r), src, k0, k1);
+        mx = m > mx ? m : mx;
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -187,15 +225,7 @@ __global__ void __launch_bounds__(256) slice4f_kernel(Src src, int rows, int K, 
 // (len even, p 16-byte aligned): 16-byte loads.
 __global__ void __launch_bounds__(256) expo_flat_kernel(const double *p, long long len, int *e) {
     __shared__ unsigned long long red[8];
-    const double2 *q = reinterpret_cast<const double2 *>(p + blockIdx.x * len);
-    unsigned long long mx = 0;
-    for (long long t = threadIdx.x; t < len / 2; t += 256) {
-        const double2 v = q[t];
-        const unsigned long long a = static_cast<unsigned long long>(__double_as_longlong(v.x)) & 0x7FFFFFFFFFFFFFFFull;
-        const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(v.y)) & 0x7FFFFFFFFFFFFFFFull;
-        mx = a > mx ? a : mx;
-        mx = b > mx ? b : mx;
-    }
+    unsigned long long mx = run_max(p + blockIdx.x * len, len);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         const unsigned long long y = __shfl_down_sync(0xffffffffu, mx, o);
@@ -288,34 +318,16 @@ __global__ void __launch_bounds__(256) expo_group_kernel(const __grid_constant__
     int slot;
     if (jb.flat) {
         const long long len = static_cast<long long>(jb.rpe) * jb.K;
-        const double2 *q = reinterpret_cast<const double2 *>(jb.src.p + lb * len);
-        for (long long t = threadIdx.x; t < len / 2; t += 256) {
-            const double2 v = q[t];
-            const unsigned long long a = static_cast<unsigned long long>(__double_as_longlong(v.x)) & 0x7FFFFFFFFFFFFFFFull;
-            const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(v.y)) & 0x7FFFFFFFFFFFFFFFull;
-            mx = a > mx ? a : mx;
-            mx = b > mx ? b : mx;
-        }
+        mx = run_max(jb.src.p + lb * len, len);
         slot = lb;
     } else {
         const Src src = jb.src;
         const int gi = lb / jb.nsc, z = lb - gi * jb.nsc;
         const int r0 = gi * jb.rpe, r1 = min(jb.rows, r0 + jb.rpe);
         const int k0 = z * SUPER, k1 = min(jb.K, k0 + SUPER);
-        const int step_o = 256 / src.kin, step_i = 256 % src.kin;
         for (int r = r0; r < r1; r++) {
-            const double *row = src_row(src, r);
-            int ko = (k0 + threadIdx.x) / src.kin, ki = k0 + threadIdx.x - ko * src.kin;
-            for (int kk = k0 + threadIdx.x; kk < k1; kk += 256) {
-                const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(
-                                                 row[static_cast<long long>(ko) * src.sko +
-                                                     static_cast<long long>(ki) * src.ski])) &
-                                             0x7FFFFFFFFFFFFFFFull;
-                mx = b > mx ? b : mx;
-                ko += step_o;
-                ki += step_i;
-                if (ki >= src.kin) { ki -= src.kin; ko++; }
-            }
+            const unsigned long long m = row_chunk_max(src_row(src, r), src, k0, k1);
+            mx = m > mx ? m : mx;
         }
         slot = gi * jb.nsc + z;
     }
