@@ -255,7 +255,14 @@ __device__ __forceinline__ TileCoord tile_of(const OzProb &pr, int u, int raster
 // (compile-time tables): before the first MMA into an accumulator whose window
 // starts here (bit set in pend), wait until the epilogue has drained and
 // zeroed it.  Returns false if a wait gave up.
-template <class C, int R, int I>
+// The MMAs of one K-block of window residue R, in the residue's issue order
+// (compile-time tables): before the first MMA into an accumulator whose window
+// starts here (bit set in pend, a subset of PMAX), wait until the epilogue has
+// drained and zeroed it.  PMAX is the residue's window starts, or every
+// accumulator in a tile's first K-block, so that steady-state K-blocks carry
+// no wait code for accumulators that cannot be pending.  Returns false if a
+// wait gave up.
+template <class C, int R, unsigned PMAX, int I>
 __device__ __forceinline__ bool issue_mmas(uint32_t tmem, uint64_t ad0, uint64_t bd0, unsigned &pend,
                                            int (&wcnt)[C::NACC], uint64_t *accfull, uint64_t *accempty,
                                            bool early, volatile int *abort_flag) {
@@ -276,28 +283,70 @@ __device__ __forceinline__ bool issue_mmas(uint32_t tmem, uint64_t ad0, uint64_t
         constexpr int b0 = Tabs<C>::list.b0[i];
         constexpr int nb = Tabs<C>::list.nb[i];
         constexpr int d0 = a + b0;
-        constexpr unsigned mask = ((1u << nb) - 1u) << d0;
-        const unsigned need = pend & mask;
-        if (need) {
+        constexpr unsigned mask = (((1u << nb) - 1u) << d0) & PMAX;
+        if constexpr (mask != 0) {
+            const unsigned need = pend & mask;
+            if (need) {
 #pragma unroll
-            for (int d = 0; d < C::NACC; d++) {
-                if (!(need & (1u << d))) continue;
-                if (!tc::mbar_wait(&accempty[d], static_cast<uint32_t>(wcnt[d]) & 1u, abort_flag)) return false;
-                wcnt[d]++;
+                for (int d = 0; d < C::NACC; d++) {
+                    if (!(mask & (1u << d)) || !(need & (1u << d))) continue;
+                    if (!tc::mbar_wait(&accempty[d], static_cast<uint32_t>(wcnt[d]) & 1u, abort_flag)) return false;
+                    wcnt[d]++;
+                }
+                pend &= ~need;
+                tc::fence_after_sync();
             }
-            pend &= ~need;
-            tc::fence_after_sync();
         }
         // descriptor start addresses are in 16-byte units
         tc::mma_bf16(tmem + d0 * C::BN, ad0 + static_cast<uint64_t>(a * (BM * 32 / 16)),
                      bd0 + static_cast<uint64_t>(b0 * (C::BN * 32 / 16)), tc::idesc_bf16_f32(BM, C::BN * nb), 1u);
-        return issue_mmas<C, R, I + 1>(tmem, ad0, bd0, pend, wcnt, accfull, accempty, early, abort_flag);
+        return issue_mmas<C, R, PMAX, I + 1>(tmem, ad0, bd0, pend, wcnt, accfull, accempty, early, abort_flag);
     }
 }
 
+// One K-block (kb) of residue R: wait for its operand stage, issue its MMAs,
+// release the stage, and in the tile's last K-block signal every drain.
+template <class C, int R, unsigned PMAX>
+__device__ __forceinline__ bool issue_kblock(uint8_t *smem, uint32_t tmem, int kb, int nkb, unsigned pend, bool early,
+                                             int &stage, uint32_t &phase, int (&wcnt)[C::NACC], uint64_t *full,
+                                             uint64_t *empty, uint64_t *accfull, uint64_t *accempty,
+                                             volatile int *abort_flag) {
+    if (!tc::mbar_wait(&full[stage], phase, abort_flag)) return false;
+    tc::fence_after_sync();
+    const uint64_t ad0 = tc::sdesc_kmajor_sw32(tc::smem_u32(smem + stage * C::STAGE_BYTES));
+    const uint64_t bd0 = ad0 + static_cast<uint64_t>(C::A_BYTES / 16);
+    // the residue's window ends are committed right after their MMAs,
+    // except in the tile's last K-block, which ends every window at once
+    const bool last = kb == nkb - 1;
+    if (!issue_mmas<C, R, PMAX, 0>(tmem, ad0, bd0, pend, wcnt, accfull, accempty, early && !last, abort_flag))
+        return false;
+    tc::mma_commit(&empty[stage]);
+    if (last) {
+#pragma unroll
+        for (int d = 0; d < C::NACC; d++) tc::mma_commit(&accfull[d]);
+    }
+    if (++stage == C::NSTAGE) {
+        stage = 0;
+        phase ^= 1u;
+    }
+    return true;
+}
+
+// A tile's first K-block: every accumulator opens a window.
+template <class C>
+__device__ __forceinline__ bool issue_first(uint8_t *smem, uint32_t tmem, int nkb, int &stage, uint32_t &phase,
+                                            int (&wcnt)[C::NACC], uint64_t *full, uint64_t *empty, uint64_t *accfull,
+                                            uint64_t *accempty, volatile int *abort_flag) {
+    constexpr unsigned kAll = (1u << C::NACC) - 1u;
+    static_assert(we_mask<Cfg6>(0) == 0 && we_mask<Cfg7>(0) == 0, "no window ends in a tile's first K-block");
+    return issue_kblock<C, 0, kAll>(smem, tmem, 0, nkb, kAll, false, stage, phase, wcnt, full, empty, accfull,
+                                    accempty, abort_flag);
+}
+
 // K-blocks kb0 + R .. kb0 + 15 of a tile (one window period, unrolled so that
-// the window bookkeeping is compile-time except for the tile's first and last
-// K-block).  Returns false if a wait gave up.
+// the window bookkeeping is compile-time except for the tile's first period
+// and last K-block); in the first period, K-block 0 has been issued already.
+// Returns false if a wait gave up.
 template <class C, int R>
 __device__ __forceinline__ bool issue_period(uint8_t *smem, uint32_t tmem, int kb0, int nkb, int &stage,
                                              uint32_t &phase, int (&wcnt)[C::NACC], uint64_t *full, uint64_t *empty,
@@ -307,32 +356,18 @@ __device__ __forceinline__ bool issue_period(uint8_t *smem, uint32_t tmem, int k
     } else {
         const int kb = kb0 + R;
         if (kb >= nkb) return true;
-        if (!tc::mbar_wait(&full[stage], phase, abort_flag)) return false;
-        tc::fence_after_sync();
-        constexpr unsigned kAll = (1u << C::NACC) - 1u;
-        constexpr unsigned kStarts = ws_mask<C>(R);
-        constexpr unsigned kEnds = we_mask<C>(R);
-        // the tile's first K-block opens every accumulator; its first period
-        // keeps diagonal 2's first window open through K-block 9
-        unsigned pend = kStarts | ((R == 0 && kb0 == 0) ? kAll : 0u);
-        if constexpr (R == kMergedEnd + 1) {
-            if (kb0 == 0) pend &= ~(1u << kMergedDiag);
-        }
-        const uint64_t ad0 = tc::sdesc_kmajor_sw32(tc::smem_u32(smem + stage * C::STAGE_BYTES));
-        const uint64_t bd0 = ad0 + static_cast<uint64_t>(C::A_BYTES / 16);
-        // the residue's window ends are committed right after their MMAs,
-        // except in the tile's last K-block, which ends every window at once
-        const bool last = kb == nkb - 1;
-        const bool early = !last && !(R == kMergedEnd && kb0 == 0);
-        if (!issue_mmas<C, R, 0>(tmem, ad0, bd0, pend, wcnt, accfull, accempty, early, abort_flag)) return false;
-        tc::mma_commit(&empty[stage]);
-        if (last) {
-#pragma unroll
-            for (int d = 0; d < C::NACC; d++) tc::mma_commit(&accfull[d]);
-        }
-        if (++stage == C::NSTAGE) {
-            stage = 0;
-            phase ^= 1u;
+        if (R != 0 || kb0 != 0) {
+            constexpr unsigned kStarts = ws_mask<C>(R);
+            // the tile's first period keeps diagonal 2's first window open
+            // through K-block 9
+            unsigned pend = kStarts;
+            if constexpr (R == kMergedEnd + 1) {
+                if (kb0 == 0) pend &= ~(1u << kMergedDiag);
+            }
+            const bool early = !(R == kMergedEnd && kb0 == 0);
+            if (!issue_kblock<C, R, kStarts>(smem, tmem, kb, nkb, pend, early, stage, phase, wcnt, full, empty,
+                                             accfull, accempty, abort_flag))
+                return false;
         }
         return issue_period<C, R + 1>(smem, tmem, kb0, nkb, stage, phase, wcnt, full, empty, accfull, accempty,
                                       abort_flag);
@@ -432,6 +467,9 @@ ozgemm_kernel(const __grid_constant__ OzGroup g) {
             for (int u = u0; u < nunits && ok; u += ustep) {
                 const OzProb &pr = g.p[prob_of(g, u)];
                 const TileCoord tc_ = tile_of(pr, u - pr.tile0, g.raster);
+                if (tc_.nkb > 0)
+                    ok = issue_first<C>(smem, tmem, tc_.nkb, stage, phase, wcnt, full, empty, accfull, accempty,
+                                        abort_flag);
                 for (int kb0 = 0; kb0 < tc_.nkb && ok; kb0 += WPERIOD)
                     ok = issue_period<C, 0>(smem, tmem, kb0, tc_.nkb, stage, phase, wcnt, full, empty, accfull,
                                             accempty, abort_flag);
