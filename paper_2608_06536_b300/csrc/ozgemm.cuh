@@ -263,7 +263,7 @@ __device__ __forceinline__ TileCoord tile_of(const OzProb &pr, int u, int raster
 // no wait code for accumulators that cannot be pending.  Returns false if a
 // wait gave up.
 template <class C, int R, unsigned PMAX, int I>
-__device__ __forceinline__ bool issue_mmas(uint32_t tmem, uint64_t ad0, uint64_t bd0, unsigned &pend,
+__device__ __forceinline__ bool issue_mmas(uint32_t tmem, uint32_t a_lo, uint32_t b_lo, unsigned &pend,
                                            int (&wcnt)[C::NACC], uint64_t *accfull, uint64_t *accempty,
                                            bool early, volatile int *abort_flag) {
     if constexpr (I == Tabs<C>::order.nend[R] && I > 0) {
@@ -298,9 +298,9 @@ __device__ __forceinline__ bool issue_mmas(uint32_t tmem, uint64_t ad0, uint64_t
             }
         }
         // descriptor start addresses are in 16-byte units
-        tc::mma_bf16(tmem + d0 * C::BN, ad0 + static_cast<uint64_t>(a * (BM * 32 / 16)),
-                     bd0 + static_cast<uint64_t>(b0 * (C::BN * 32 / 16)), tc::idesc_bf16_f32(BM, C::BN * nb), 1u);
-        return issue_mmas<C, R, PMAX, I + 1>(tmem, ad0, bd0, pend, wcnt, accfull, accempty, early, abort_flag);
+        tc::mma_bf16_acc(tmem + d0 * C::BN, a_lo + a * (BM * 32 / 16), b_lo + b0 * (C::BN * 32 / 16), tc::kSw32DescHi,
+                         tc::idesc_bf16_f32(BM, C::BN * nb));
+        return issue_mmas<C, R, PMAX, I + 1>(tmem, a_lo, b_lo, pend, wcnt, accfull, accempty, early, abort_flag);
     }
 }
 
@@ -313,12 +313,12 @@ __device__ __forceinline__ bool issue_kblock(uint8_t *smem, uint32_t tmem, int k
                                              volatile int *abort_flag) {
     if (!tc::mbar_wait(&full[stage], phase, abort_flag)) return false;
     tc::fence_after_sync();
-    const uint64_t ad0 = tc::sdesc_kmajor_sw32(tc::smem_u32(smem + stage * C::STAGE_BYTES));
-    const uint64_t bd0 = ad0 + static_cast<uint64_t>(C::A_BYTES / 16);
+    const uint32_t a_lo = tc::sdesc_kmajor_sw32_lo(tc::smem_u32(smem + stage * C::STAGE_BYTES));
+    const uint32_t b_lo = a_lo + C::A_BYTES / 16;
     // the residue's window ends are committed right after their MMAs,
     // except in the tile's last K-block, which ends every window at once
     const bool last = kb == nkb - 1;
-    if (!issue_mmas<C, R, PMAX, 0>(tmem, ad0, bd0, pend, wcnt, accfull, accempty, early && !last, abort_flag))
+    if (!issue_mmas<C, R, PMAX, 0>(tmem, a_lo, b_lo, pend, wcnt, accfull, accempty, early && !last, abort_flag))
         return false;
     tc::mma_commit(&empty[stage]);
     if (last) {

@@ -143,6 +143,20 @@ __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64
         : "memory");
 }
 
+// The same MMA, accumulating, from the descriptors' split words (a_lo, b_lo
+// lower words, hi the common upper word).
+__device__ __forceinline__ void mma_bf16_acc(uint32_t d_tmem, uint32_t a_lo, uint32_t b_lo, uint32_t hi,
+                                             uint32_t idesc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t.reg .b64 da, db;\n\t"
+        "mov.b64 da, {%1, %3};\n\t"
+        "mov.b64 db, {%2, %3};\n\t"
+        "setp.ne.b32 p, 1, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], da, db, %4, p;\n\t}" ::"r"(d_tmem),
+        "r"(a_lo), "r"(b_lo), "r"(hi), "r"(idesc)
+        : "memory");
+}
+
 // Arrive on `bar` once every tcgen05 operation issued so far by this thread has completed.
 __device__ __forceinline__ void mma_commit(uint64_t *bar) {
     asm volatile(
@@ -233,6 +247,15 @@ __device__ __forceinline__ uint64_t sdesc_kmajor_sw32(uint32_t saddr) {
     d |= static_cast<uint64_t>(1u) << 46;   // descriptor version for tcgen05
     d |= static_cast<uint64_t>(6u) << 61;   // swizzle mode: 32 B
     return d;
+}
+
+// The same descriptor in its two 32-bit words: the upper one is a constant
+// (SBO, version, swizzle mode), the lower one holds the start address, so a
+// descriptor for an offset inside the tile is one 32-bit add (the 14-bit
+// address field does not overflow: shared addresses stay below 2^18).
+constexpr uint32_t kSw32DescHi = (256u >> 4) | (1u << 14) | (6u << 29);
+__device__ __forceinline__ uint32_t sdesc_kmajor_sw32_lo(uint32_t saddr) {
+    return ((saddr >> 4) & 0x3FFFu) | (1u << 16);
 }
 
 // K-major descriptors for 128-byte (8-row groups 1024 B apart) and 64-byte
