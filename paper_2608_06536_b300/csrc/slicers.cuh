@@ -423,5 +423,81 @@ __global__ void __launch_bounds__(256) slice_group_kernel(const __grid_constant_
     }
 }
 
+// ---------------------------------------------------------------------------
+// Exponents of the rank-update operands taken from a panel
+// ---------------------------------------------------------------------------
+// The split build cuts each density's rank-update operands T_X, T_Y (rows mu,
+// reduction index (p, j)) out of the panel T (rows (p, mu), one column per
+// column of X_s or Y_s).  Their exponent groups (row mu, super-chunk z of
+// (p, j)) gather 100-element runs from rows far apart, which a per-group
+// exponent pass reads as scattered short pieces.  Instead, one block reads
+// one whole T row (contiguous) and each warp folds one operand's columns into
+// that operand's exponents by an atomic maximum: exponents are monotone in
+// |x|, so the maximum of per-element exponents is the exponent of the
+// maximum, and -1000 (an all-zero group) is the neutral start.
+struct PanelSeg {
+    int *e;          // the operand's exponents, e[mu * nsc + z]
+    int c0, k, nsc;  // its columns c0 .. c0 + k - 1 of T; super-chunks per row
+    int n;           // rows mu per p of its panel
+};
+struct PanelItem {   // one panel: its rows (p, mu) and its operands' segments
+    const double *T;
+    long long ldT;
+    int n, rows;
+    int seg0, nseg;  // segments seg0 .. seg0 + nseg - 1
+    int b0;          // first block of this panel in the launch (one block per row)
+};
+constexpr int MAXPITEM = 64;
+constexpr int MAXSEG = 800;
+struct PanelExpo {
+    int nitem;
+    int nseg;
+    PanelItem it[MAXPITEM];
+    PanelSeg s[MAXSEG];
+};
+
+// Every segment's exponents set to -1000 (blockIdx.y = segment).
+__global__ void __launch_bounds__(256) int_fill_kernel(const __grid_constant__ PanelExpo g) {
+    const PanelSeg &sg = g.s[blockIdx.y];
+    const int cnt = sg.n * sg.nsc;
+    for (int i = blockIdx.x * 256 + threadIdx.x; i < cnt; i += gridDim.x * 256) sg.e[i] = -1000;
+}
+
+// One block per panel row r = p * n + mu; warp w takes the panel's segments
+// w, w + 8, ...
+__global__ void __launch_bounds__(256) panel_colmax_kernel(const __grid_constant__ PanelExpo g) {
+    int lo = 0, hi = g.nitem - 1;
+    while (lo < hi) {   // the last panel whose first block is <= blockIdx.x
+        const int mid = (lo + hi + 1) >> 1;
+        if (g.it[mid].b0 <= static_cast<int>(blockIdx.x)) lo = mid;
+        else hi = mid - 1;
+    }
+    const PanelItem &pi = g.it[lo];
+    const int r = static_cast<int>(blockIdx.x) - pi.b0;
+    const int p = r / pi.n, mu = r - p * pi.n;
+    const double *row = pi.T + static_cast<long long>(r) * pi.ldT;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int si = pi.seg0 + warp; si < pi.seg0 + pi.nseg; si += 8) {
+        const PanelSeg &sg = g.s[si];
+        const int kk0 = p * sg.k;            // reduction index of the run's first element
+        const int z0 = kk0 / SUPER;
+        const int jb = (z0 + 1) * SUPER - kk0;   // first j of the next super-chunk
+        // the exponent needs only the upper word of |x| (sign cleared)
+        unsigned m0 = 0, m1 = 0;
+        for (int j = lane; j < sg.k; j += 32) {
+            const unsigned hw = static_cast<unsigned>(__double2hiint(row[sg.c0 + j])) & 0x7FFFFFFFu;
+            if (j < jb) m0 = hw > m0 ? hw : m0;
+            else m1 = hw > m1 ? hw : m1;
+        }
+        m0 = __reduce_max_sync(0xffffffffu, m0);
+        if (jb < sg.k) m1 = __reduce_max_sync(0xffffffffu, m1);
+        if (lane == 0) {
+            if (m0) atomicMax(&sg.e[mu * sg.nsc + z0], exponent_of_max(static_cast<unsigned long long>(m0) << 32));
+            if (jb < sg.k && m1)
+                atomicMax(&sg.e[mu * sg.nsc + z0 + 1], exponent_of_max(static_cast<unsigned long long>(m1) << 32));
+        }
+    }
+}
+
 }  // namespace oz
 }  // namespace jk

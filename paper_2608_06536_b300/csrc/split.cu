@@ -378,7 +378,8 @@ static void slice_add(SliceBatch &sb, const oz::Src &src, int rows, int K, int r
 
 // Slice every collected operand (all six-slice) with one exponent launch and
 // one slicer launch per MAXJOB jobs; the batch is emptied.
-static jk_status slice_flush(jk_ctx *h, SliceBatch &sb, cudaStream_t st) {
+// expo = false: the jobs' exponents are already in place (panel_expo).
+static jk_status slice_flush(jk_ctx *h, SliceBatch &sb, cudaStream_t st, bool expo = true) {
     static thread_local oz::SliceGroup grp;
     for (size_t i0 = 0; i0 < sb.jobs.size(); i0 += oz::MAXJOB) {
         const int nj = static_cast<int>(std::min<size_t>(oz::MAXJOB, sb.jobs.size() - i0));
@@ -394,11 +395,11 @@ static jk_status slice_flush(jk_ctx *h, SliceBatch &sb, cudaStream_t st) {
         }
         if (eb > 0x7fffffffLL || sbk > 0x7fffffffLL) return set_error(h, JK_ERR_SHAPE, "too many slicer blocks");
         grp.njob = nj;
-        {
+        if (expo) {
             LaunchScope ls(h, KK_SLICE, st);
             oz::expo_group_kernel<<<static_cast<unsigned>(eb), 256, 0, st>>>(grp);
         }
-        JK_LAUNCH_CHECK(h);
+        if (expo) JK_LAUNCH_CHECK(h);
         {
             LaunchScope ls(h, KK_SLICE, st);
             oz::slice_group_kernel<6><<<static_cast<unsigned>(sbk), 256, 0, st>>>(grp);
@@ -406,6 +407,83 @@ static jk_status slice_flush(jk_ctx *h, SliceBatch &sb, cudaStream_t st) {
         JK_LAUNCH_CHECK(h);
     }
     sb.jobs.clear();
+    return JK_OK;
+}
+
+// The exponents of the rank-update operands of whole panels (every density
+// of one aux chunk of one or several molecules), from whole rows of each panel
+// T (oz::panel_colmax_kernel), in grouped launches.  Usable when every k <=
+// SUPER (a run of one p spans at most two super-chunks).
+static bool panel_expo_fits(const Problem &pb) {
+    for (int s = 0; s < pb.nd; s++)
+        if (pb.k[s] > oz::SUPER) return false;
+    return 2 * pb.nd <= oz::MAXSEG;
+}
+struct PanelBatch {
+    struct Item {
+        const Problem *pb;
+        const double *T;
+        long long ldT;
+        int np;
+        Sliced *TX, *TY;
+    };
+    std::vector<Item> items;
+};
+static void panel_add(PanelBatch &pbt, const Problem &pb, const double *T, long long ldT, int np, Sliced *TX,
+                      Sliced *TY) {
+    pbt.items.push_back({&pb, T, ldT, np, TX, TY});
+}
+static jk_status panel_launch(jk_ctx *h, oz::PanelExpo &g, int nscmax, long long blocks, cudaStream_t st) {
+    if (blocks > 0x7fffffffLL) return set_error(h, JK_ERR_SHAPE, "too many panel rows");
+    {
+        LaunchScope ls(h, KK_SLICE, st);
+        int nmax = 1;
+        for (int i = 0; i < g.nitem; i++) nmax = std::max(nmax, g.it[i].n);
+        const int bx = std::min(1024, (nmax * nscmax + 255) / 256);
+        oz::int_fill_kernel<<<dim3(bx, g.nseg), 256, 0, st>>>(g);
+    }
+    JK_LAUNCH_CHECK(h);
+    {
+        LaunchScope ls(h, KK_SLICE, st);
+        oz::panel_colmax_kernel<<<static_cast<unsigned>(blocks), 256, 0, st>>>(g);
+    }
+    JK_LAUNCH_CHECK(h);
+    return JK_OK;
+}
+static jk_status panel_flush(jk_ctx *h, PanelBatch &pbt, cudaStream_t st) {
+    static thread_local oz::PanelExpo g;
+    g.nitem = 0;
+    g.nseg = 0;
+    int nscmax = 1;
+    long long blocks = 0;
+    for (const auto &itm : pbt.items) {
+        const Problem &pb = *itm.pb;
+        int want = 0;
+        for (int s = 0; s < pb.nd; s++) want += pb.sym[s] ? 1 : 2;
+        if (g.nitem == oz::MAXPITEM || g.nseg + want > oz::MAXSEG) {
+            JK_TRY(panel_launch(h, g, nscmax, blocks, st));
+            g.nitem = g.nseg = 0;
+            nscmax = 1;
+            blocks = 0;
+        }
+        oz::PanelItem &pi = g.it[g.nitem++];
+        pi.T = itm.T;
+        pi.ldT = itm.ldT;
+        pi.n = pb.n;
+        pi.rows = itm.np * pb.n;
+        pi.seg0 = g.nseg;
+        pi.b0 = static_cast<int>(blocks);
+        for (int s = 0; s < pb.nd; s++) {
+            const int nsc = (itm.np * pb.k[s] + oz::SUPER - 1) / oz::SUPER;
+            nscmax = std::max(nscmax, nsc);
+            g.s[g.nseg++] = oz::PanelSeg{itm.TX[s].e, pb.offX[s], pb.k[s], nsc, pb.n};
+            if (!pb.sym[s]) g.s[g.nseg++] = oz::PanelSeg{itm.TY[s].e, pb.offY[s], pb.k[s], nsc, pb.n};
+        }
+        pi.nseg = g.nseg - pi.seg0;
+        blocks += pi.rows;
+    }
+    if (g.nitem > 0) JK_TRY(panel_launch(h, g, nscmax, blocks, st));
+    pbt.items.clear();
     return JK_OK;
 }
 
@@ -678,7 +756,14 @@ jk_status split_build(jk_ctx *h, const Problem &pb, cudaStream_t st) {
                     else JK_TRY(slice_operand(h, ys, n, Kr, 1, TY[s], st));
                 }
             }
-            JK_TRY(slice_flush(h, sb, st));
+            if (grouped && panel_expo_fits(pb)) {
+                PanelBatch pbt;
+                panel_add(pbt, pb, T, ldT, np, TX, TY);
+                JK_TRY(panel_flush(h, pbt, st));
+                JK_TRY(slice_flush(h, sb, st, false));
+            } else {
+                JK_TRY(slice_flush(h, sb, st));
+            }
         }
         ReduceBatch rb;
         long long *Pcur = Pbuf;
@@ -1185,10 +1270,15 @@ jk_status split_batched(jk_ctx *h, int nmol, const Problem *pbs, cudaStream_t st
                 if (pbs[it.mol].wantJ && it.P0 + it.np >= pbs[it.mol].naux)
                     JK_TRY(fp64_jstream(h, pbs[it.mol], mb[it.mol].gamma, h->aux_stream));
         }
+        bool rowwise = grouped;   // exponents from whole panel rows when every molecule allows it
+        for (auto &it : items)
+            if (pbs[it.mol].wantK && !panel_expo_fits(pbs[it.mol])) rowwise = false;
+        PanelBatch pbt;
         for (auto &it : items) {
             const Problem &pb = pbs[it.mol];
             const long long ldT = even_ld(pb.ctot);
             if (!pb.wantK) continue;
+            if (rowwise) panel_add(pbt, pb, it.T, ldT, it.np, it.TX, it.TY);
             for (int s = 0; s < pb.nd; s++) {
                 const int k = pb.k[s], Kr = it.np * k;
                 oz::Src xs{it.T + pb.offX[s], ldT, static_cast<long long>(pb.n) * ldT, 1, k};
@@ -1201,7 +1291,8 @@ jk_status split_batched(jk_ctx *h, int nmol, const Problem *pbs, cudaStream_t st
                 }
             }
         }
-        JK_TRY(slice_flush(h, sb, st));
+        if (rowwise) JK_TRY(panel_flush(h, pbt, st));
+        JK_TRY(slice_flush(h, sb, st, !rowwise));
         // 4. every rank update of the wave: grouped persistent launches
         probs.clear();
         struct Red { const ItemBufs *it; int s; long long *P; double *tmp; };

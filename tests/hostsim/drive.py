@@ -101,6 +101,18 @@ class SliceGroup(ct.Structure):
     _fields_ = [("j", SliceJob * 200), ("njob", I32)]
 
 
+class PanelSeg(ct.Structure):
+    _fields_ = [("e", VP), ("c0", I32), ("k", I32), ("nsc", I32), ("n", I32)]
+
+
+class PanelItem(ct.Structure):
+    _fields_ = [("T", VP), ("ldT", I64), ("n", I32), ("rows", I32), ("seg0", I32), ("nseg", I32), ("b0", I32)]
+
+
+class PanelExpo(ct.Structure):
+    _fields_ = [("nitem", I32), ("nseg", I32), ("it", PanelItem * 64), ("s", PanelSeg * 800)]
+
+
 class ReduceJob(ct.Structure):
     _fields_ = [("P", VP), ("pz", I64), ("ldp", I64), ("eA", VP), ("eB", VP), ("out", VP), ("ldo", I64), ("e0", I64),
                 ("nz", I32), ("M", I32), ("N", I32), ("arpe", I32), ("brpe", I32), ("accumulate", I32), ("frac", I32)]
@@ -241,6 +253,45 @@ def dec_expo_group(grid, args):
         if jb.flat:
             assert jb.nsc == 1 and jb.src.p % 16 == 0 and (jb.rpe * jb.K) % 2 == 0 and jb.rows % jb.rpe == 0
         res += [_src_range(jb.src, jb.rows, jb.K), (jb.e, jb.e + 4 * groups * jb.nsc, "e")]
+    return res
+
+
+def _panel_items(g):
+    """The panels of a row-wise exponent launch, checked to tile its blocks and
+    its segments in order."""
+    assert 1 <= g.nitem <= 64 and 1 <= g.nseg <= 800, (g.nitem, g.nseg)
+    b = seg = 0
+    out = []
+    for i in range(g.nitem):
+        pi = g.it[i]
+        assert pi.b0 == b and pi.seg0 == seg and pi.n >= 1 and pi.rows % pi.n == 0 and pi.nseg >= 1, (i, pi.b0, b)
+        np_ = pi.rows // pi.n
+        segs = [g.s[j] for j in range(pi.seg0, pi.seg0 + pi.nseg)]
+        for sg in segs:
+            assert sg.n == pi.n and 1 <= sg.k <= SUPER and sg.nsc == (np_ * sg.k + SUPER - 1) // SUPER
+            assert sg.c0 >= 0 and sg.c0 + sg.k <= pi.ldT
+        out.append((pi, segs))
+        b += pi.rows
+        seg += pi.nseg
+    assert seg == g.nseg
+    return out, b
+
+
+def dec_int_fill(grid, args):
+    g = PanelExpo.from_address(args[0])
+    items, _ = _panel_items(g)
+    assert grid[1] == g.nseg
+    return [(sg.e, sg.e + 4 * sg.n * sg.nsc, "e") for _, segs in items for sg in segs]
+
+
+def dec_panel_colmax(grid, args):
+    g = PanelExpo.from_address(args[0])
+    items, nb = _panel_items(g)
+    assert grid[0] == nb, (grid, nb)
+    res = []
+    for pi, segs in items:
+        res.append((pi.T, pi.T + 8 * ((pi.rows - 1) * pi.ldT + max(sg.c0 + sg.k for sg in segs)), "T"))
+        res += [(sg.e, sg.e + 4 * sg.n * sg.nsc, "e") for sg in segs]
     return res
 
 
@@ -745,6 +796,29 @@ def ex_expo_group(grid, args):
         _expo_job(jb.src, jb.rows, jb.K, jb.rpe, jb.e, (jb.rows - 1) // jb.rpe + 1, jb.nsc)
 
 
+def ex_int_fill(grid, args):
+    g = PanelExpo.from_address(args[0])
+    for i in range(g.nseg):
+        uv(g.s[i].e, g.s[i].n * g.s[i].nsc, np.int32)[:] = -1000
+
+
+def ex_panel_colmax(grid, args):
+    """Each operand's exponent of (row mu, super-chunk z) from the panel rows
+    (p, mu): the exponent of the maximum over that group of its columns."""
+    g = PanelExpo.from_address(args[0])
+    for i in range(g.nitem):
+        pi = g.it[i]
+        n, np_ = pi.n, pi.rows // pi.n
+        T = np.abs(dv(pi.T, pi.rows * pi.ldT).reshape(pi.rows, pi.ldT))
+        for j in range(pi.seg0, pi.seg0 + pi.nseg):
+            sg = g.s[j]
+            blk = T[:, sg.c0:sg.c0 + sg.k].reshape(np_, n, sg.k).transpose(1, 0, 2).reshape(n, np_ * sg.k)
+            ev = uv(sg.e, n * sg.nsc, np.int32).reshape(n, sg.nsc)
+            for z in range(sg.nsc):
+                part = blk[:, z * SUPER:(z + 1) * SUPER]
+                ev[:, z] = np.maximum(ev[:, z], _expo_of(part.max(axis=1)))
+
+
 def ex_expo_flat(grid, args):
     p, ln, e = _v(args, 0, VP), _v(args, 1, I64), _v(args, 2, VP)
     X = np.abs(dv(p, grid[0] * ln).reshape(grid[0], ln))
@@ -909,7 +983,7 @@ EXECUTORS = [
     ("sum_parts_kernel", ex_sum_parts), ("pair_dot_kernel", ex_pair_dot), ("laplace_scale_kernel", ex_laplace_scale),
     ("weighted_sum_kernel", ex_weighted_sum), ("unpack_sym_kernel", ex_unpack_sym), ("gterms_kernel", ex_gterms),
     ("symmetrize_kernel", ex_symmetrize), ("fold_sym_split_kernel", ex_fold), ("fold_sym_kernel", ex_fold),
-    ("pack_group_kernel", ex_pack_group),
+    ("pack_group_kernel", ex_pack_group), ("int_fill_kernel", ex_int_fill), ("panel_colmax_kernel", ex_panel_colmax),
     ("expo_group_kernel", ex_expo_group), ("slice_group_kernel", ex_slice_group),
     ("reduce_group_kernel", ex_reduce_group),
     ("expo_flat_kernel", ex_expo_flat), ("expo_kernel", ex_expo), ("slice4f_kernel", ex_slice),
@@ -920,7 +994,7 @@ EXECUTORS = [
 ]
 
 DECODERS = [
-    ("pack_group_kernel", dec_pack_group),
+    ("pack_group_kernel", dec_pack_group), ("int_fill_kernel", dec_int_fill), ("panel_colmax_kernel", dec_panel_colmax),
     ("expo_group_kernel", dec_expo_group), ("slice_group_kernel", dec_slice_group),
     ("reduce_group_kernel", dec_reduce_group),
     ("expo_flat_kernel", dec_expo_flat), ("expo_kernel", dec_expo), ("slice4_kernel", dec_slice4),

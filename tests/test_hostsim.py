@@ -111,10 +111,11 @@ def test_full_size_case(full_records, name):
 
 
 def test_full_size_tuned_build_launch_count(full_records):
-    """The tuned multi-state build (grouped schedule) issues 12 launches per
+    """The tuned multi-state build (grouped schedule) issues 13 launches per
     build: grouped persistent GEMMs, grouped packing, exponent, slicer and
-    reduction launches, the FP64 metric dot and J stream."""
-    assert len(full_records["full_multi_state_tuned"]["launches"]) == 12
+    reduction launches, the panel operands' row-wise exponent pass (a fill
+    and a row launch), the FP64 metric dot and J stream."""
+    assert len(full_records["full_multi_state_tuned"]["launches"]) == 13
 
 
 def _check(rec):
@@ -241,16 +242,18 @@ def test_grouped_schedule_collapses_gemm_launches(full_records):
 
 def test_tuned_build_matches_the_measured_launch_list(full_records):
     """Kernel by kernel, the tuned multi-state build's launches: in the grouped
-    schedule every operand of a wave is sliced by one exponent launch and one
-    slicer launch (the factor chunk before the panel GEMM, all densities'
-    panel operands after it) and every split-K reduction by one launch."""
+    schedule every operand of a wave is sliced by one slicer launch (the
+    packed densities and the factor chunk after one exponent launch each,
+    all densities' panel operands after the row-wise exponent pass over the
+    panel) and every split-K reduction by one launch."""
     from collections import Counter
-    per_build = {"ozgemm_kernel": 2, "expo_group_kernel": 3, "slice_group_kernel": 3, "jstream_sym_kernel": 1,
-                 "gamma_panel_kernel": 1, "reduce_group_kernel": 1, "pack_group_kernel": 1}
+    per_build = {"ozgemm_kernel": 2, "expo_group_kernel": 2, "int_fill_kernel": 1, "panel_colmax_kernel": 1,
+                 "slice_group_kernel": 3, "jstream_sym_kernel": 1, "gamma_panel_kernel": 1, "reduce_group_kernel": 1,
+                 "pack_group_kernel": 1}
     got = Counter()
     for k in full_records["full_multi_state_tuned"]["launches"]:
         got[next(key for key in per_build if key in k[0])] += 1
-    assert dict(got) == per_build and sum(per_build.values()) == 12
+    assert dict(got) == per_build and sum(per_build.values()) == 13
 
 
 EXEC_CASES = [n for n in NAMES if not n.startswith("autotune")]
