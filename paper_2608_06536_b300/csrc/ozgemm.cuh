@@ -388,6 +388,46 @@ __device__ __forceinline__ void tmem_zero_cols(uint32_t taddr) {
     if constexpr (N % 16 != 0) tc::tmem_zero8(taddr + (N / 16) * 16);
 }
 
+// A finished FP64 tile whose conversion and store are pending: its int64
+// accumulators sit in this warp's staging block; the epilogue converts them
+// pair by pair while it would otherwise wait for the next drain, and stores
+// each 32 x 8 block as soon as it is complete.
+struct PendingStore {
+    int pi_i0;            // its problem in the launch (bits 8..) and the next column pair
+                          // (bits 0..7; OUT_COLS when nothing is pending)
+    int c0, r0;           // its first column and the warp's first row
+    int ea, eb_lo, eb_hi; // row exponent (minus FRAC); column exponents of columns lane, 32 + lane
+};
+
+template <int OUT_COLS>
+__device__ __forceinline__ void pending_step(PendingStore &ps, const OzGroup &g, uint8_t *wbuf, int lane) {
+    const int pi = ps.pi_i0 >> 8, i0 = ps.pi_i0 & 255;
+    const int N = g.p[pi].a.N, M = g.p[pi].a.M;
+    const int row = ps.r0 + lane;
+    const int j = (i0 % OUT_BLK) / 2;
+    const int chunk = j ^ ((lane >> 1) & 3);
+    longlong2 *p = reinterpret_cast<longlong2 *>(wbuf + (i0 / OUT_BLK) * (32 * OUT_BLK * 8) + lane * 64 + chunk * 16);
+    const longlong2 w = *p;
+    const int eb0 = __shfl_sync(0xffffffffu, i0 < 32 ? ps.eb_lo : ps.eb_hi, i0 & 31);
+    const int eb1 = __shfl_sync(0xffffffffu, i0 + 1 < 32 ? ps.eb_lo : ps.eb_hi, (i0 + 1) & 31);
+    const int col = ps.c0 + i0;
+    const double d0 = col < N && row < M ? i64_to_f64_scaled(w.x, ps.ea + eb0) : 0.0;
+    const double d1 = col + 1 < N && row < M ? i64_to_f64_scaled(w.y, ps.ea + eb1) : 0.0;
+    *p = make_longlong2(__double_as_longlong(d0), __double_as_longlong(d1));
+    ps.pi_i0 += 2;
+    if ((i0 + 2) % OUT_BLK == 0) {
+        // block complete: hand it to the TMA
+        tc::fence_proxy_async_smem();
+        __syncwarp();
+        const int b = i0 / OUT_BLK;
+        const int cc = ps.c0 + b * OUT_BLK;
+        if (lane == 0 && cc < N) {
+            tc::tma_store_2d(&g.p[pi].tmC, wbuf + b * (32 * OUT_BLK * 8), cc, ps.r0);
+            tc::bulk_commit();
+        }
+    }
+}
+
 // Persistent, warp-specialized sliced GEMM.  Warp 0 streams operand stages
 // with TMA, warp 1 issues the slice-pair MMAs per stage, warps 2..9 drain the
 // TMEM accumulators after every window into int64 registers and write the
@@ -491,6 +531,9 @@ ozgemm_kernel(const __grid_constant__ OzGroup g) {
             for (int d = 0; d < NACC; d++) tc::mbar_arrive(&accempty[d]);
         uint32_t epar = 0;   // bit d: parity of the windows drained from accumulator d
         bool ok = true;
+        uint8_t *wbuf = outbuf + ew * C::OUT_WARP_BYTES;   // this warp's staging block
+        PendingStore ps;
+        ps.pi_i0 = OUT_COLS;
         for (int u = u0; u < nunits && ok; u += ustep) {
             // Copy the tile's problem out of parameter space once: the stores
             // below go through generic pointers and would otherwise force a
@@ -507,12 +550,6 @@ ozgemm_kernel(const __grid_constant__ OzGroup g) {
             // exponents of columns l and 32 + l of its OUT_COLS (shared by shuffles).
             const int c0 = tc_.n * BN + half * OUT_COLS;
             const int row = tc_.m * BM + q * 32 + lane;
-            int ea = 0, eb_lo = 0, eb_hi = 0;
-            if (a.nsuper == 1) {
-                if (row < a.M) ea = a.eA[row / a.a_rpe] - C::FRAC;
-                if (c0 + lane < a.N) eb_lo = a.eB[(c0 + lane) / a.b_rpe];
-                if (lane < OUT_COLS - 32 && c0 + 32 + lane < a.N) eb_hi = a.eB[(c0 + 32 + lane) / a.b_rpe];
-            }
             for (int kb = 0; kb < tc_.nkb && ok; kb++) {
                 const unsigned wends = we_mask_rt<C>(kb & (WPERIOD - 1)) & (kb == kMergedEnd ? ~(1u << kMergedDiag) : ~0u);
                 const unsigned ends = wends | (kb == tc_.nkb - 1 ? (1u << NACC) - 1u : 0u);
@@ -523,6 +560,10 @@ ozgemm_kernel(const __grid_constant__ OzGroup g) {
                 for (int j = 0; j < NACC; j++) {
                     const int d = drain_acc<C>(j);
                     if (!(ends & (1u << d))) continue;
+                    // the previous tile's pending store progresses while this
+                    // accumulator is still being written
+                    while ((ps.pi_i0 & 255) < OUT_COLS && !tc::mbar_test_wait(&accfull[d], (epar >> d) & 1u))
+                        pending_step<OUT_COLS>(ps, g, wbuf, lane);
                     if (!tc::mbar_wait(&accfull[d], (epar >> d) & 1u, abort_flag)) {
                         ok = false;
                         break;
@@ -559,10 +600,10 @@ ozgemm_kernel(const __grid_constant__ OzGroup g) {
             if (!ok) break;
             if (a.use_tma_store) {
                 // This warp's 32 x OUT_COLS block: lane = row, swizzled 32 x 8 sub-blocks.
-                uint8_t *wbuf = outbuf + ew * C::OUT_WARP_BYTES;
-                if (lane == 0) tc::bulk_wait_read();   // previous tile's store has read the buffer
+                while ((ps.pi_i0 & 255) < OUT_COLS) pending_step<OUT_COLS>(ps, g, wbuf, lane);   // the previous tile's rest
+                if (lane == 0) tc::bulk_wait_read();   // earlier stores have read the buffer
                 __syncwarp();
-                // the int64 accumulators as they are (the split-K partials' form) ...
+                // the int64 accumulators as they are (the split-K partials' form)
 #pragma unroll
                 for (int b = 0; b < OUT_COLS / OUT_BLK; b++) {
 #pragma unroll
@@ -573,38 +614,30 @@ ozgemm_kernel(const __grid_constant__ OzGroup g) {
                             make_longlong2(acc64[i0], acc64[i0 + 1]);
                     }
                 }
-                // ... or rounded to FP64 in place: a loop unrolled four times,
-                // enough independent conversions to hide their latency while
-                // the integer-heavy code stays short (fully unrolled copies
-                // cost instruction fetches on every tile)
+                const int r0 = tc_.m * BM + q * 32;
                 if (a.nsuper == 1) {
-#pragma unroll 4
-                    for (int i0 = 0; i0 < OUT_COLS; i0 += 2) {
-                        const int j = (i0 % OUT_BLK) / 2;
-                        const int chunk = j ^ ((lane >> 1) & 3);
-                        longlong2 *p = reinterpret_cast<longlong2 *>(wbuf + (i0 / OUT_BLK) * (32 * OUT_BLK * 8) + lane * 64 +
-                                                                     chunk * 16);
-                        const longlong2 w = *p;
-                        const int eb0 = __shfl_sync(0xffffffffu, i0 < 32 ? eb_lo : eb_hi, i0 & 31);
-                        const int eb1 = __shfl_sync(0xffffffffu, i0 + 1 < 32 ? eb_lo : eb_hi, (i0 + 1) & 31);
-                        const int col = c0 + i0;
-                        const double d0 = col < a.N && row < a.M ? i64_to_f64_scaled(w.x, ea + eb0) : 0.0;
-                        const double d1 = col + 1 < a.N && row < a.M ? i64_to_f64_scaled(w.y, ea + eb1) : 0.0;
-                        *p = make_longlong2(__double_as_longlong(d0), __double_as_longlong(d1));
-                    }
-                }
-                tc::fence_proxy_async_smem();
-                __syncwarp();
-                if (lane == 0) {
-                    const int r0 = tc_.m * BM + q * 32;
+                    // FP64 out: rounding every element is deferred into the
+                    // next tile's waits for its accumulators (PendingStore);
+                    // the exponents' load latency hides there too
+                    ps.pi_i0 = pi << 8;
+                    ps.c0 = c0;
+                    ps.r0 = r0;
+                    ps.ea = row < a.M ? a.eA[row / a.a_rpe] - C::FRAC : 0;
+                    ps.eb_lo = c0 + lane < a.N ? a.eB[(c0 + lane) / a.b_rpe] : 0;
+                    ps.eb_hi = lane < OUT_COLS - 32 && c0 + 32 + lane < a.N ? a.eB[(c0 + 32 + lane) / a.b_rpe] : 0;
+                } else {
+                    tc::fence_proxy_async_smem();
+                    __syncwarp();
+                    if (lane == 0) {
 #pragma unroll
-                    for (int b = 0; b < OUT_COLS / OUT_BLK; b++) {
-                        const int cc = c0 + b * OUT_BLK;
-                        // rows of the partial for super-chunk z follow the M rows of z-1
-                        const int rr = a.nsuper == 1 ? r0 : r0 + tc_.z * static_cast<int>(a.pz / a.ldp);
-                        if (cc < a.N) tc::tma_store_2d(tmC, wbuf + b * (32 * OUT_BLK * 8), cc, rr);
+                        for (int b = 0; b < OUT_COLS / OUT_BLK; b++) {
+                            const int cc = c0 + b * OUT_BLK;
+                            // rows of the partial for super-chunk z follow the M rows of z-1
+                            const int rr = r0 + tc_.z * static_cast<int>(a.pz / a.ldp);
+                            if (cc < a.N) tc::tma_store_2d(tmC, wbuf + b * (32 * OUT_BLK * 8), cc, rr);
+                        }
+                        tc::bulk_commit();
                     }
-                    tc::bulk_commit();
                 }
             } else if (row < a.M) {
                 if (a.nsuper == 1) {
@@ -625,6 +658,8 @@ ozgemm_kernel(const __grid_constant__ OzGroup g) {
                 }
             }
         }
+        if (ok)
+            while ((ps.pi_i0 & 255) < OUT_COLS) pending_step<OUT_COLS>(ps, g, wbuf, lane);
         if (lane == 0) tc::bulk_wait_all();
     }
     tc::fence_before_sync();
