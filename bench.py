@@ -65,13 +65,13 @@ FP64_GATE = 1e-12        # relative to max |output| (FP64 engine)
 # + dram__bytes_write.sum of the capture, scaled by aux indices),
 # sm__pipe_tensor_cycles_active (% of peak, elapsed) and the capture's command.
 NCU_GEMM = {
-    "7112195a5f87a4a0": {
-        # profile case (naux=400, one aux chunk): panel launch 15.87 + 10.22 GB,
-        # rank-update launch 56.81 + 2.62 GB; scaled to the headline's 338-index
+    "5c4421038faf8689": {
+        # profile case (naux=400, one aux chunk): panel launch 14.49 + 10.26 GB,
+        # rank-update launch 52.66 + 2.65 GB; scaled to the headline's 338-index
         # chunks (x 338/400) and averaged over its two launches per chunk
-        "traffic": 0.5 * (26.09 + 59.43) * 338 / 400 * 1e9,
-        # sm__pipe_tensor_cycles_active: panel 55.7 %, rank update 56.7 %, time-weighted
-        "tensor_pipe_active": 0.560,
+        "traffic": 0.5 * (24.75 + 55.31) * 338 / 400 * 1e9,
+        # sm__pipe_tensor_cycles_active: panel 56.8 %, rank update 56.3 %, time-weighted
+        "tensor_pipe_active": 0.566,
         "capture": "ncu --set full --clock-control none -k regex:ozgemm -c 1 (panel) and -s 1 -c 1 (rank update) "
                    "python bench.py --case profile --quick --steps 1 --warmup 1 --config 400,1,0,0",
     },
