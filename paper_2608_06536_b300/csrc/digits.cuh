@@ -1,10 +1,14 @@
 // Digit splits of a fixed-point value F into BF16 slices, the slicer's ways of
 // forming them:
-//   digits6 + qbf16   six digits of a 48-bit F (|F| <= 2^48) in 32-bit integer
-//                     arithmetic, then one exact FP32 conversion per digit
-//                     (the default slicer);
-//   digits_n<7>       seven digits of a 56-bit F in 64-bit arithmetic (the
-//                     seven-slice operands of the split adjoint);
+//   digit_values<S>   the S balanced digits of an 8S-bit F (S = 6: 48 bits,
+//                     the builds; S = 7: 56 bits, the split adjoint's
+//                     seven-slice operands), already scaled to their slices'
+//                     values, read off the bytes of F plus a bias (the
+//                     default slicer);
+//   digits6 + qbf16,  the same digits by per-digit integer arithmetic and
+//   digits_n<7>       one exact FP32 conversion each (a second statement of
+//                     the split that the host test checks digit_values
+//                     against);
 //   split48           six digits of a 48-bit F by FP32 additions only
 //                     (JK_OPT_SLICER = 1), below.
 //
@@ -27,6 +31,7 @@
 
 #include <stdint.h>
 #if !defined(__CUDA_ARCH__)
+#include <math.h>
 #include <string.h>
 #endif
 
@@ -104,6 +109,85 @@ JK_HD uint32_t bits_of_f32(float f) {
 JK_HD uint32_t qbf16(int q, float scale) {
     const float f = (f32_of_bits(static_cast<uint32_t>(0x4B400000 + q)) - 12582912.0f) * scale;
     return bits_of_f32(f) >> 16;
+}
+
+// Byte select of two words (CUDA's __byte_perm): result byte i is byte
+// (s >> 4i) & 7 of the eight bytes x (0..3), y (4..7).
+JK_HD uint32_t byte_perm(uint32_t x, uint32_t y, uint32_t s) {
+#if defined(__CUDA_ARCH__)
+    return __byte_perm(x, y, s);
+#else
+    const uint64_t b = (static_cast<uint64_t>(y) << 32) | x;
+    uint32_t r = 0;
+    for (int i = 0; i < 4; i++) r |= static_cast<uint32_t>((b >> (8 * ((s >> (4 * i)) & 7))) & 0xFF) << (8 * i);
+    return r;
+#endif
+}
+
+// a * b + c rounded once (fused).
+JK_HD float fma_rn(float a, float b, float c) {
+#if defined(__CUDA_ARCH__)
+    return __fmaf_rn(a, b, c);
+#else
+    return fmaf(a, b, c);
+#endif
+}
+
+// The S balanced base-256 digits of F (|F| <= 2^(8S)) as the values
+// v_j = q_j * 2^(-8(j+1)), j = 0..S-1: the digits of digits6 / digits_n<S>.
+// With the bias B = 0x80 in each of the S-1 low bytes, G = F + B holds
+// q_j + 128 as its byte S-1-j for j >= 1 (balanced digits in [-128, 127] add
+// no carries), and q_0 = G >> 8(S-1).  A byte dropped into the low byte of
+// 0x4B400000 (1.5 * 2^23) is the FP32 value 1.5 * 2^23 + byte, so one fused
+// multiply-add q_j * sc = f * sc - (1.5 * 2^23 + 128) * sc gives the slice
+// value exactly (both products exact, the result an FP32 value; a zero digit
+// gives +0).  biased_words forms G once per element; digit_value reads one
+// slice's value off it, so a slicer keeps two words per element live, not S
+// values.
+template <int S>
+JK_HD void biased_words(long long F, uint32_t &lo, uint32_t &hi) {
+    static_assert(S == 6 || S == 7, "six or seven slices");
+    constexpr unsigned long long kBias = S == 6 ? 0x8080808080ull : 0x808080808080ull;
+    const unsigned long long G = static_cast<unsigned long long>(F) + kBias;
+    lo = static_cast<uint32_t>(G);
+    hi = static_cast<uint32_t>(G >> 32);
+}
+
+JK_HD float slice_scale(int j) {   // 2^(-8(j+1))
+    float sc = 0.00390625f;
+    for (int i = 0; i < j; i++) sc *= 0.00390625f;
+    return sc;
+}
+
+template <int S>
+JK_HD float digit_value(uint32_t lo, uint32_t hi, int j) {
+    const float sc = slice_scale(j);
+    if (j == 0) {
+        const int q0 = static_cast<int>(hi) >> (8 * (S - 1) - 32);   // G >> 8(S-1), arithmetic
+        return fma_rn(f32_of_bits(0x4B400000u + static_cast<uint32_t>(q0)), sc, -12582912.0f * sc);
+    }
+    const int b = S - 1 - j;   // byte of G holding q_j + 128
+    const uint32_t f = byte_perm(b < 4 ? lo : hi, 0x4B400000u, 0x7650u | static_cast<uint32_t>(b & 3));
+    return fma_rn(f32_of_bits(f), sc, -12583040.0f * sc);
+}
+
+template <int S>
+JK_HD void digit_values(long long F, float v[S]) {
+    uint32_t lo, hi;
+    biased_words<S>(F, lo, hi);
+    for (int j = 0; j < S; j++) v[j] = digit_value<S>(lo, hi, j);   // a constant trip count: unrolled
+}
+
+// Two exact BF16 values (FP32 v_lo, v_hi whose low 16 bits are zero) as one
+// word, v_lo in the low half.
+JK_HD uint32_t pack_bf16x2(float v_lo, float v_hi) {
+#if defined(__CUDA_ARCH__)
+    uint32_t d;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(v_hi), "f"(v_lo));
+    return d;
+#else
+    return (bits_of_f32(v_hi) & 0xFFFF0000u) | (bits_of_f32(v_lo) >> 16);
+#endif
 }
 
 // x rounded to a multiple of 2^k, M = 1.5 * 2^(k+23); exact for |x| <= 2^(k+22).

@@ -71,20 +71,33 @@ __device__ __forceinline__ unsigned long long row_chunk_max(const double *row, c
     return mx;
 }
 
-// max|x| bits over a contiguous run of len doubles (p 16-byte aligned, len
-// even), for a block of 256 threads: four 16-byte loads in flight per thread.
+// max|x| bits over a contiguous run of len doubles (p 8-byte aligned), for a
+// block of 256 threads: four 16-byte loads in flight per thread over the
+// 16-byte aligned body, one scalar load for an unaligned first or odd last
+// element.
 __device__ __forceinline__ unsigned long long run_max(const double *p, long long len) {
+    constexpr unsigned long long kAbs = 0x7FFFFFFFFFFFFFFFull;
+    unsigned long long mx = 0;
+    if (len <= 0) return mx;
+    if (reinterpret_cast<uintptr_t>(p) & 15u) {
+        if (threadIdx.x == 0) mx = static_cast<unsigned long long>(__double_as_longlong(p[0])) & kAbs;
+        ++p;
+        --len;
+    }
+    if ((len & 1) && threadIdx.x == 1) {
+        const unsigned long long a = static_cast<unsigned long long>(__double_as_longlong(p[len - 1])) & kAbs;
+        mx = a > mx ? a : mx;
+    }
     const double2 *q = reinterpret_cast<const double2 *>(p);
     const long long n2 = len / 2;
-    unsigned long long mx = 0;
     for (long long t = threadIdx.x; t < n2; t += 4 * 256) {
         double2 v[4];
 #pragma unroll
         for (int i = 0; i < 4; i++) v[i] = t + 256 * i < n2 ? q[t + 256 * i] : make_double2(0.0, 0.0);
 #pragma unroll
         for (int i = 0; i < 4; i++) {
-            const unsigned long long a = static_cast<unsigned long long>(__double_as_longlong(v[i].x)) & 0x7FFFFFFFFFFFFFFFull;
-            const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(v[i].y)) & 0x7FFFFFFFFFFFFFFFull;
+            const unsigned long long a = static_cast<unsigned long long>(__double_as_longlong(v[i].x)) & kAbs;
+            const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(v[i].y)) & kAbs;
             mx = a > mx ? a : mx;
             mx = b > mx ? b : mx;
         }
@@ -119,61 +132,96 @@ __global__ void __launch_bounds__(256) expo_kernel(Src src, int rows, int K, int
     }
 }
 
-using digits::digits6;
-using digits::qbf16;
-
-// The S digits of an element under its scale: the 32-bit split for six
-// slices, the 64-bit one for seven.
+// The biased words of an element under its scale (digits.cuh biased_words:
+// its 8S-bit fixed-point value plus the digit bias), from which digit_value
+// reads each slice's value.
 template <int S>
-__device__ __forceinline__ void element_digits(double x, int e, int q[S]) {
-    const long long F = to_fixed(x, e, 8 * S);
-    if constexpr (S == 6) digits6(F, q);
-    else digits::digits_n<S>(F, q);
+__device__ __forceinline__ void element_words(double x, int e, uint32_t &lo, uint32_t &hi) {
+    digits::biased_words<S>(to_fixed(x, e, 8 * S), lo, hi);
 }
 
-// Vector slicer: 4 consecutive reduction elements per thread.  Requires
-// src.ski == 1, src.kin % 4 == 0, K % 4 == 0 and 16-byte aligned pairs
-// (checked on the host).
-template <int S>
-__global__ void __launch_bounds__(256) slice4_kernel(Src src, int rows, int K, int Kpad, const int *e, int rpe,
-                                                     int nsc, uint2 *out, long long sstride4) {
-    const int kk = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
+constexpr int SLICE_ROWS = 8;   // rows per block pass of the slicers
+
+// The S digit planes of one operand's rows by*8 .. (rows step nby*8), four
+// consecutive reduction indices kk .. kk+3 per thread (kk = 4 (bx*256 + tid)),
+// one 8-byte word per plane and row (Kpad is a multiple of 4).  AL: the four
+// sources are two 16-byte aligned pairs (src.ski == 1, src.kin % 4 == 0,
+// K % 4 == 0 and even strides from a 16-byte aligned base, checked on the
+// host).  Otherwise each of the four is loaded on its own, so any strides, a
+// run boundary of the (ko, ki) split or the end of K may fall inside the four;
+// the indices past K hold zero digits.  SUPER is a multiple of 4, so the four
+// share one exponent.
+template <int S, bool AL>
+__device__ __forceinline__ void slice_rows4(const Src &src, int rows, int K, int Kpad, const int *e, int rpe,
+                                            int nsc, uint2 *out, long long sstride4, int bx, int by, int nby) {
+    const int kk = 4 * (bx * 256 + static_cast<int>(threadIdx.x));
     if (kk >= Kpad) return;
-    long long koff = 0;
-    if (kk < K) {
-        const int ko = kk / src.kin, ki = kk - ko * src.kin;
-        koff = static_cast<long long>(ko) * src.sko + ki;
-    }
-    for (int rb = blockIdx.y * 8; rb < rows; rb += gridDim.y * 8) {
-        const int rend = min(rows, rb + 8);
-        for (int r = rb; r < rend; r++) {
-            int q[4][S];
-            if (kk < K) {
-                const double2 *p2 = reinterpret_cast<const double2 *>(src_row(src, r) + koff);
-                const double2 a = p2[0], b = p2[1];
-                const int er = e[(r / rpe) * nsc + kk / SUPER];
-                element_digits<S>(a.x, er, q[0]);
-                element_digits<S>(a.y, er, q[1]);
-                element_digits<S>(b.x, er, q[2]);
-                element_digits<S>(b.y, er, q[3]);
-            } else {
+    long long off[4];
+    bool ok[4];
+    {
+        int ko = kk / src.kin, ki = kk - ko * src.kin;
 #pragma unroll
-                for (int i = 0; i < 4; i++)
-#pragma unroll
-                    for (int j = 0; j < S; j++) q[i][j] = 0;
-            }
-            const long long o = (static_cast<long long>(r) * Kpad + kk) >> 2;
-            float sc = 0.00390625f;
-#pragma unroll
-            for (int j = 0; j < S; j++) {
-                uint2 w;
-                w.x = qbf16(q[0][j], sc) | (qbf16(q[1][j], sc) << 16);
-                w.y = qbf16(q[2][j], sc) | (qbf16(q[3][j], sc) << 16);
-                out[j * sstride4 + o] = w;
-                sc *= 0.00390625f;
+        for (int i = 0; i < 4; i++) {
+            ok[i] = kk + i < K;
+            off[i] = static_cast<long long>(ko) * src.sko + static_cast<long long>(ki) * src.ski;
+            if (!AL && ++ki == src.kin) {
+                ki = 0;
+                ++ko;
             }
         }
     }
+    const int zc = kk / SUPER;
+    for (int rb = by * SLICE_ROWS; rb < rows; rb += nby * SLICE_ROWS) {
+        const int rend = min(rows, rb + SLICE_ROWS);
+        for (int r = rb; r < rend; r++) {
+            uint32_t glo[4], ghi[4];   // the biased words; zero elements give zero digits
+            if (kk < K) {
+                const double *row = src_row(src, r);
+                double x[4];
+                if constexpr (AL) {
+                    const double2 *p2 = reinterpret_cast<const double2 *>(row + off[0]);
+                    const double2 a = p2[0], b = p2[1];
+                    x[0] = a.x;
+                    x[1] = a.y;
+                    x[2] = b.x;
+                    x[3] = b.y;
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 4; i++) x[i] = ok[i] ? row[off[i]] : 0.0;
+                }
+                const int er = e[(r / rpe) * nsc + zc];
+#pragma unroll
+                for (int i = 0; i < 4; i++) element_words<S>(x[i], er, glo[i], ghi[i]);
+            } else {
+#pragma unroll
+                for (int i = 0; i < 4; i++) digits::biased_words<S>(0, glo[i], ghi[i]);
+            }
+            const long long o = (static_cast<long long>(r) * Kpad + kk) >> 2;
+#pragma unroll
+            for (int j = 0; j < S; j++) {
+                uint2 w;
+                w.x = digits::pack_bf16x2(digits::digit_value<S>(glo[0], ghi[0], j),
+                                          digits::digit_value<S>(glo[1], ghi[1], j));
+                w.y = digits::pack_bf16x2(digits::digit_value<S>(glo[2], ghi[2], j),
+                                          digits::digit_value<S>(glo[3], ghi[3], j));
+                out[j * sstride4 + o] = w;
+            }
+        }
+    }
+}
+
+// Slicer of one operand whose rows are aligned runs (slice_rows4, AL).
+template <int S>
+__global__ void __launch_bounds__(256) slice4_kernel(Src src, int rows, int K, int Kpad, const int *e, int rpe,
+                                                     int nsc, uint2 *out, long long sstride4) {
+    slice_rows4<S, true>(src, rows, K, Kpad, e, rpe, nsc, out, sstride4, blockIdx.x, blockIdx.y, gridDim.y);
+}
+
+// Slicer of any one operand (slice_rows4, element loads).
+template <int S>
+__global__ void __launch_bounds__(256) slice_kernel(Src src, int rows, int K, int Kpad, const int *e, int rpe,
+                                                    int nsc, uint2 *out, long long sstride4) {
+    slice_rows4<S, false>(src, rows, K, Kpad, e, rpe, nsc, out, sstride4, blockIdx.x, blockIdx.y, gridDim.y);
 }
 
 // Vector slicer with the digits formed by FP32 additions (digits.cuh, six
@@ -240,37 +288,6 @@ __global__ void __launch_bounds__(256) expo_flat_kernel(const double *p, long lo
     }
 }
 
-constexpr int SLICE_ROWS = 8;   // rows per block of the slicer
-
-// out[j][r][kk] = q_j(r, kk) * 2^(-8(j+1)) for j = 0..S-1 (bf16), zero for kk >= K.
-template <int S>
-__global__ void __launch_bounds__(256) slice_kernel(Src src, int rows, int K, int Kpad, const int *e,
-                                                    int rpe, int nsc, unsigned short *out, long long sstride) {
-    const int kk = blockIdx.x * blockDim.x + threadIdx.x;
-    if (kk >= Kpad) return;
-    long long koff = 0;
-    if (kk < K) {
-        const int ko = kk / src.kin, ki = kk - ko * src.kin;
-        koff = static_cast<long long>(ko) * src.sko + static_cast<long long>(ki) * src.ski;
-    }
-    for (int rb = blockIdx.y * SLICE_ROWS; rb < rows; rb += gridDim.y * SLICE_ROWS) {
-        const int rend = min(rows, rb + SLICE_ROWS);
-        for (int r = rb; r < rend; r++) {
-            int q[S];
-#pragma unroll
-            for (int j = 0; j < S; j++) q[j] = 0;
-            if (kk < K) element_digits<S>(src_row(src, r)[koff], e[(r / rpe) * nsc + kk / SUPER], q);
-            const long long o = static_cast<long long>(r) * Kpad + kk;
-            float sc = 0.00390625f;
-#pragma unroll
-            for (int j = 0; j < S; j++) {
-                out[j * sstride + o] = static_cast<unsigned short>(qbf16(q[j], sc));
-                sc *= 0.00390625f;
-            }
-        }
-    }
-}
-
 // ---------------------------------------------------------------------------
 // Grouped slicing: many operands in one launch
 // ---------------------------------------------------------------------------
@@ -284,9 +301,9 @@ struct SliceJob {
     Src src;
     int *e;                // exponents: written by the exponent launch, read by the slicer
     void *out;             // S planes, rows x Kpad each
-    long long sstride;     // plane stride in units of the output words (uint2 when vec, else ushort)
+    long long sstride;     // plane stride in 8-byte output words (four BF16 values)
     int rows, K, Kpad, rpe, nsc;
-    int vec;               // 4-element vector path (alignment checked on the host)
+    int vec;               // aligned 16-byte source loads (alignment checked on the host)
     int flat;              // exponent groups are contiguous runs of rpe * K doubles
     int eb0, sb0;          // first block of this job in the exponent and the slicer launch
     int nbx, nby;          // slicer blocks along K (x) and rows (y)
@@ -309,7 +326,7 @@ __device__ __forceinline__ int job_of_block(const SliceGroup &g, int b, bool exp
 
 // The exponents of every job: expo_kernel's (or expo_flat_kernel's) work for
 // the job's row group g and super-chunk z.
-__global__ void __launch_bounds__(256) expo_group_kernel(const __grid_constant__ SliceGroup g) {
+__global__ void __launch_bounds__(256, 6) expo_group_kernel(const __grid_constant__ SliceGroup g) {
     __shared__ unsigned long long red[8];
     const int ji = job_of_block(g, blockIdx.x, true);
     const SliceJob &jb = g.j[ji];
@@ -345,82 +362,19 @@ __global__ void __launch_bounds__(256) expo_group_kernel(const __grid_constant__
     }
 }
 
-// The slices of every job: slice4_kernel's work (vector jobs) or
+// The slices of every job: slice4_kernel's work (aligned jobs) or
 // slice_kernel's (the others) for the job's block (bx, by).
 template <int S>
-__global__ void __launch_bounds__(256) slice_group_kernel(const __grid_constant__ SliceGroup g) {
+__global__ void __launch_bounds__(256, 8) slice_group_kernel(const __grid_constant__ SliceGroup g) {
     const int ji = job_of_block(g, blockIdx.x, false);
     const SliceJob &jb = g.j[ji];
     const int lb = blockIdx.x - jb.sb0;
     const int by = lb / jb.nbx, bx = lb - by * jb.nbx;
-    const Src src = jb.src;
-    const int rows = jb.rows, K = jb.K, Kpad = jb.Kpad, rpe = jb.rpe, nsc = jb.nsc;
-    const int *e = jb.e;
-    if (jb.vec) {
-        const int kk = 4 * (bx * 256 + threadIdx.x);
-        if (kk >= Kpad) return;
-        uint2 *out = static_cast<uint2 *>(jb.out);
-        long long koff = 0;
-        if (kk < K) {
-            const int ko = kk / src.kin, ki = kk - ko * src.kin;
-            koff = static_cast<long long>(ko) * src.sko + ki;
-        }
-        for (int rb = by * 8; rb < rows; rb += jb.nby * 8) {
-            const int rend = min(rows, rb + 8);
-            for (int r = rb; r < rend; r++) {
-                int q[4][S];
-                if (kk < K) {
-                    const double2 *p2 = reinterpret_cast<const double2 *>(src_row(src, r) + koff);
-                    const double2 a = p2[0], b = p2[1];
-                    const int er = e[(r / rpe) * nsc + kk / SUPER];
-                    element_digits<S>(a.x, er, q[0]);
-                    element_digits<S>(a.y, er, q[1]);
-                    element_digits<S>(b.x, er, q[2]);
-                    element_digits<S>(b.y, er, q[3]);
-                } else {
-#pragma unroll
-                    for (int i = 0; i < 4; i++)
-#pragma unroll
-                        for (int j = 0; j < S; j++) q[i][j] = 0;
-                }
-                const long long o = (static_cast<long long>(r) * Kpad + kk) >> 2;
-                float sc = 0.00390625f;
-#pragma unroll
-                for (int j = 0; j < S; j++) {
-                    uint2 w;
-                    w.x = qbf16(q[0][j], sc) | (qbf16(q[1][j], sc) << 16);
-                    w.y = qbf16(q[2][j], sc) | (qbf16(q[3][j], sc) << 16);
-                    out[j * jb.sstride + o] = w;
-                    sc *= 0.00390625f;
-                }
-            }
-        }
-    } else {
-        const int kk = bx * 256 + threadIdx.x;
-        if (kk >= Kpad) return;
-        unsigned short *out = static_cast<unsigned short *>(jb.out);
-        long long koff = 0;
-        if (kk < K) {
-            const int ko = kk / src.kin, ki = kk - ko * src.kin;
-            koff = static_cast<long long>(ko) * src.sko + static_cast<long long>(ki) * src.ski;
-        }
-        for (int rb = by * SLICE_ROWS; rb < rows; rb += jb.nby * SLICE_ROWS) {
-            const int rend = min(rows, rb + SLICE_ROWS);
-            for (int r = rb; r < rend; r++) {
-                int q[S];
-#pragma unroll
-                for (int j = 0; j < S; j++) q[j] = 0;
-                if (kk < K) element_digits<S>(src_row(src, r)[koff], e[(r / rpe) * nsc + kk / SUPER], q);
-                const long long o = static_cast<long long>(r) * Kpad + kk;
-                float sc = 0.00390625f;
-#pragma unroll
-                for (int j = 0; j < S; j++) {
-                    out[j * jb.sstride + o] = static_cast<unsigned short>(qbf16(q[j], sc));
-                    sc *= 0.00390625f;
-                }
-            }
-        }
-    }
+    uint2 *out = static_cast<uint2 *>(jb.out);
+    if (jb.vec)
+        slice_rows4<S, true>(jb.src, jb.rows, jb.K, jb.Kpad, jb.e, jb.rpe, jb.nsc, out, jb.sstride, bx, by, jb.nby);
+    else
+        slice_rows4<S, false>(jb.src, jb.rows, jb.K, jb.Kpad, jb.e, jb.rpe, jb.nsc, out, jb.sstride, bx, by, jb.nby);
 }
 
 // ---------------------------------------------------------------------------
@@ -429,12 +383,16 @@ __global__ void __launch_bounds__(256) slice_group_kernel(const __grid_constant_
 // The split build cuts each density's rank-update operands T_X, T_Y (rows mu,
 // reduction index (p, j)) out of the panel T (rows (p, mu), one column per
 // column of X_s or Y_s).  Their exponent groups (row mu, super-chunk z of
-// (p, j)) gather 100-element runs from rows far apart, which a per-group
-// exponent pass reads as scattered short pieces.  Instead, one block reads
-// one whole T row (contiguous) and each warp folds one operand's columns into
-// that operand's exponents by an atomic maximum: exponents are monotone in
-// |x|, so the maximum of per-element exponents is the exponent of the
-// maximum, and -1000 (an all-zero group) is the neutral start.
+// (p, j)) gather k-element runs from rows far apart, which a per-group
+// exponent pass reads as scattered short pieces.  Instead, each lane group
+// reads whole T rows, and folds each operand's k columns of the row into that
+// operand's exponents by an atomic maximum: exponents are monotone in |x|, so
+// the maximum of per-element exponents is the exponent of the maximum, and
+// -1000 (an all-zero group) is the neutral start.  Only the upper word of |x|
+// is read: it fixes the exponent.  A warp splits into G = 32 / W groups of W
+// lanes, one row per group, and takes PANEL_U operands of its rows at a time,
+// so each lane has up to PANEL_U * PANEL_V loads in flight and a warp G rows,
+// however short the rows and however small k is.
 struct PanelSeg {
     int *e;          // the operand's exponents, e[mu * nsc + z]
     int c0, k, nsc;  // its columns c0 .. c0 + k - 1 of T; super-chunks per row
@@ -444,11 +402,16 @@ struct PanelItem {   // one panel: its rows (p, mu) and its operands' segments
     const double *T;
     long long ldT;
     int n, rows;
-    int seg0, nseg;  // segments seg0 .. seg0 + nseg - 1
-    int b0;          // first block of this panel in the launch (one block per row)
+    int seg0, nseg;  // segments seg0 .. seg0 + nseg - 1 (nseg <= PANEL_SEG_ITEM)
+    int b0;          // first block of this panel in the launch
+    int rpb;         // panel rows per block
+    int lanes;       // W: lanes per operand, 4, 8, 16 or 32 (W * PANEL_V >= k where possible)
 };
 constexpr int MAXPITEM = 64;
 constexpr int MAXSEG = 800;
+constexpr int PANEL_SEG_ITEM = 128;   // operands of one panel
+constexpr int PANEL_U = 4;            // operands per lane group at a time
+constexpr int PANEL_V = 4;            // words per lane and operand at a time
 struct PanelExpo {
     int nitem;
     int nseg;
@@ -463,9 +426,86 @@ __global__ void __launch_bounds__(256) int_fill_kernel(const __grid_constant__ P
     for (int i = blockIdx.x * 256 + threadIdx.x; i < cnt; i += gridDim.x * 256) sg.e[i] = -1000;
 }
 
-// One block per panel row r = p * n + mu; warp w takes the panel's segments
-// w, w + 8, ...
+// Rows r0 .. r0 + R - 1 of panel item pi with lane groups of W lanes: group
+// gi of warp w takes the rows r0 + w G + gi, then 8 G rows further on.  A run
+// that crosses into the next super-chunk (at j = jb) folds into two
+// exponents; a batch of operands without one (the common case: a crossing
+// happens once per SUPER / k rows p) keeps one maximum per operand.
+template <int W>
+__device__ __forceinline__ void colmax_rows(const PanelItem &pi, const int2 *sc, const int *snsc, int *const *se,
+                                            int r0, int R) {
+    constexpr int G = 32 / W;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, gi = lane / W, sl = lane % W;
+    const unsigned gmask = (W == 32 ? 0xffffffffu : (1u << W) - 1u) << (gi * W % 32);
+    const int nseg = pi.nseg;
+    for (int rbase = warp * G; rbase < R; rbase += 8 * G) {   // warp-uniform
+        const int row = rbase + gi;
+        const bool ract = row < R;
+        const int r = r0 + (ract ? row : 0), p = r / pi.n, mu = r - p * pi.n;
+        const unsigned *hw = reinterpret_cast<const unsigned *>(pi.T + static_cast<long long>(r) * pi.ldT) + 1;
+        for (int s0 = 0; s0 < nseg; s0 += PANEL_U) {
+            int c0[PANEL_U], k[PANEL_U], jb[PANEL_U], kmax = 0;
+            bool cross = false;
+#pragma unroll
+            for (int u = 0; u < PANEL_U; u++) {
+                const int2 ck = ract && s0 + u < nseg ? sc[s0 + u] : make_int2(0, 0);
+                c0[u] = ck.x;
+                k[u] = ck.y;
+                const int kk0 = p * ck.y;                         // reduction index of the run's first element
+                jb[u] = (kk0 / SUPER + 1) * SUPER - kk0;          // first j of the next super-chunk
+                kmax = max(kmax, ck.y);
+                cross = cross || jb[u] < ck.y;
+            }
+            kmax = __reduce_max_sync(0xffffffffu, kmax);
+            cross = __any_sync(0xffffffffu, cross);
+            unsigned m0[PANEL_U], m1[PANEL_U];
+#pragma unroll
+            for (int u = 0; u < PANEL_U; u++) m0[u] = m1[u] = 0;
+            for (int jw = 0; jw < kmax; jw += W * PANEL_V) {   // warp-uniform
+                const int j0 = jw + sl;
+                unsigned x[PANEL_U][PANEL_V];
+#pragma unroll
+                for (int u = 0; u < PANEL_U; u++) {
+                    const unsigned *q = hw + 2 * (c0[u] + j0);
+#pragma unroll
+                    for (int v = 0; v < PANEL_V; v++) x[u][v] = j0 + v * W < k[u] ? q[2 * v * W] : 0u;
+                }
+                if (!cross) {
+#pragma unroll
+                    for (int u = 0; u < PANEL_U; u++)
+#pragma unroll
+                        for (int v = 0; v < PANEL_V; v++) m0[u] = max(m0[u], x[u][v] & 0x7FFFFFFFu);
+                } else {
+#pragma unroll
+                    for (int u = 0; u < PANEL_U; u++)
+#pragma unroll
+                        for (int v = 0; v < PANEL_V; v++) {
+                            const unsigned a = x[u][v] & 0x7FFFFFFFu;
+                            if (j0 + v * W < jb[u]) m0[u] = max(m0[u], a);
+                            else m1[u] = max(m1[u], a);
+                        }
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < PANEL_U; u++) {
+                m0[u] = __reduce_max_sync(gmask, m0[u]);
+                if (cross) m1[u] = __reduce_max_sync(gmask, m1[u]);
+                if (sl == 0 && k[u] > 0) {
+                    const int si = s0 + u, z0 = (p * k[u]) / SUPER, nsc = snsc[si];
+                    if (m0[u]) atomicMax(&se[si][mu * nsc + z0], exponent_of_max(static_cast<unsigned long long>(m0[u]) << 32));
+                    if (m1[u] && jb[u] < k[u])
+                        atomicMax(&se[si][mu * nsc + z0 + 1], exponent_of_max(static_cast<unsigned long long>(m1[u]) << 32));
+                }
+            }
+        }
+    }
+}
+
+// Block b of panel item i takes its rows r0 = (b - b0) rpb .. r0 + R - 1.
 __global__ void __launch_bounds__(256) panel_colmax_kernel(const __grid_constant__ PanelExpo g) {
+    __shared__ int2 sc[PANEL_SEG_ITEM];        // (c0, k) of the item's operands
+    __shared__ int snsc[PANEL_SEG_ITEM];
+    __shared__ int *se[PANEL_SEG_ITEM];
     int lo = 0, hi = g.nitem - 1;
     while (lo < hi) {   // the last panel whose first block is <= blockIdx.x
         const int mid = (lo + hi + 1) >> 1;
@@ -473,29 +513,20 @@ __global__ void __launch_bounds__(256) panel_colmax_kernel(const __grid_constant
         else hi = mid - 1;
     }
     const PanelItem &pi = g.it[lo];
-    const int r = static_cast<int>(blockIdx.x) - pi.b0;
-    const int p = r / pi.n, mu = r - p * pi.n;
-    const double *row = pi.T + static_cast<long long>(r) * pi.ldT;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int si = pi.seg0 + warp; si < pi.seg0 + pi.nseg; si += 8) {
-        const PanelSeg &sg = g.s[si];
-        const int kk0 = p * sg.k;            // reduction index of the run's first element
-        const int z0 = kk0 / SUPER;
-        const int jb = (z0 + 1) * SUPER - kk0;   // first j of the next super-chunk
-        // the exponent needs only the upper word of |x| (sign cleared)
-        unsigned m0 = 0, m1 = 0;
-        for (int j = lane; j < sg.k; j += 32) {
-            const unsigned hw = static_cast<unsigned>(__double2hiint(row[sg.c0 + j])) & 0x7FFFFFFFu;
-            if (j < jb) m0 = hw > m0 ? hw : m0;
-            else m1 = hw > m1 ? hw : m1;
-        }
-        m0 = __reduce_max_sync(0xffffffffu, m0);
-        if (jb < sg.k) m1 = __reduce_max_sync(0xffffffffu, m1);
-        if (lane == 0) {
-            if (m0) atomicMax(&sg.e[mu * sg.nsc + z0], exponent_of_max(static_cast<unsigned long long>(m0) << 32));
-            if (jb < sg.k && m1)
-                atomicMax(&sg.e[mu * sg.nsc + z0 + 1], exponent_of_max(static_cast<unsigned long long>(m1) << 32));
-        }
+    for (int i = threadIdx.x; i < pi.nseg; i += 256) {
+        const PanelSeg &sg = g.s[pi.seg0 + i];
+        sc[i] = make_int2(sg.c0, sg.k);
+        snsc[i] = sg.nsc;
+        se[i] = sg.e;
+    }
+    __syncthreads();
+    const int r0 = (static_cast<int>(blockIdx.x) - pi.b0) * pi.rpb;
+    const int R = min(pi.rpb, pi.rows - r0);
+    switch (pi.lanes) {   // block-uniform
+    case 4: colmax_rows<4>(pi, sc, snsc, se, r0, R); break;
+    case 8: colmax_rows<8>(pi, sc, snsc, se, r0, R); break;
+    case 16: colmax_rows<16>(pi, sc, snsc, se, r0, R); break;
+    default: colmax_rows<32>(pi, sc, snsc, se, r0, R); break;
     }
 }
 

@@ -173,8 +173,7 @@ static jk_status slice_operand(jk_ctx *h, const oz::Src &src, int rows, int K, i
     const int nsc = (K + oz::SUPER - 1) / oz::SUPER;   // one exponent per row group and super-chunk
     const bool aligned = (reinterpret_cast<uintptr_t>(src.p) & 15u) == 0;
     // A group of rows that is one contiguous run of doubles (e.g. one L^P).
-    const bool flat = nsc == 1 && aligned && src.rin == 1 && src.ski == 1 && src.kin == K && src.sr == K &&
-                      ((static_cast<long long>(rpe) * K) % 2) == 0 && rows % rpe == 0;
+    const bool flat = nsc == 1 && src.rin == 1 && src.ski == 1 && src.kin == K && src.sr == K && rows % rpe == 0;
     {
         LaunchScope ls(h, KK_SLICE, st);
         if (flat)
@@ -183,15 +182,16 @@ static jk_status slice_operand(jk_ctx *h, const oz::Src &src, int rows, int K, i
             oz::expo_kernel<<<dim3(groups, nsc), 256, 0, st>>>(src, rows, K, rpe, out.e);
     }
     JK_LAUNCH_CHECK(h);
+    // aligned 16-byte loads of four consecutive elements, else element loads
     const bool vec = aligned && src.ski == 1 && (src.kin % 4) == 0 && (K % 4) == 0 && (src.sr % 2) == 0 &&
                      (src.sri % 2) == 0 && (src.sko % 2) == 0;
     const int rblocks = (rows + oz::SLICE_ROWS - 1) / oz::SLICE_ROWS;
     {
         LaunchScope ls(h, KK_SLICE, st);
+        dim3 grid((out.Kpad / 4 + 255) / 256, rblocks < 65535 ? rblocks : 65535);
+        uint2 *o4 = reinterpret_cast<uint2 *>(out.s);
+        const long long ss4 = static_cast<long long>(rows) * out.Kpad / 4;
         if (vec) {
-            dim3 grid((out.Kpad / 4 + 255) / 256, rblocks < 65535 ? rblocks : 65535);
-            uint2 *o4 = reinterpret_cast<uint2 *>(out.s);
-            const long long ss4 = static_cast<long long>(rows) * out.Kpad / 4;
             if (out.S == 7)
                 oz::slice4_kernel<7><<<grid, 256, 0, st>>>(src, rows, K, out.Kpad, out.e, rpe, nsc, o4, ss4);
             else if (h->slicer == 1)
@@ -199,13 +199,10 @@ static jk_status slice_operand(jk_ctx *h, const oz::Src &src, int rows, int K, i
             else
                 oz::slice4_kernel<6><<<grid, 256, 0, st>>>(src, rows, K, out.Kpad, out.e, rpe, nsc, o4, ss4);
         } else {
-            dim3 grid((out.Kpad + 255) / 256, rblocks < 65535 ? rblocks : 65535);
-            unsigned short *o1 = reinterpret_cast<unsigned short *>(out.s);
-            const long long ss1 = static_cast<long long>(rows) * out.Kpad;
             if (out.S == 7)
-                oz::slice_kernel<7><<<grid, 256, 0, st>>>(src, rows, K, out.Kpad, out.e, rpe, nsc, o1, ss1);
+                oz::slice_kernel<7><<<grid, 256, 0, st>>>(src, rows, K, out.Kpad, out.e, rpe, nsc, o4, ss4);
             else
-                oz::slice_kernel<6><<<grid, 256, 0, st>>>(src, rows, K, out.Kpad, out.e, rpe, nsc, o1, ss1);
+                oz::slice_kernel<6><<<grid, 256, 0, st>>>(src, rows, K, out.Kpad, out.e, rpe, nsc, o4, ss4);
         }
     }
     JK_LAUNCH_CHECK(h);
@@ -364,13 +361,12 @@ static void slice_add(SliceBatch &sb, const oz::Src &src, int rows, int K, int r
     j.rpe = rpe;
     j.nsc = (K + oz::SUPER - 1) / oz::SUPER;
     const bool aligned = (reinterpret_cast<uintptr_t>(src.p) & 15u) == 0;
-    j.flat = j.nsc == 1 && aligned && src.rin == 1 && src.ski == 1 && src.kin == K && src.sr == K &&
-             ((static_cast<long long>(rpe) * K) % 2) == 0 && rows % rpe == 0;
+    j.flat = j.nsc == 1 && src.rin == 1 && src.ski == 1 && src.kin == K && src.sr == K && rows % rpe == 0;
     j.vec = aligned && src.ski == 1 && (src.kin % 4) == 0 && (K % 4) == 0 && (src.sr % 2) == 0 &&
             (src.sri % 2) == 0 && (src.sko % 2) == 0;
-    j.sstride = j.vec ? static_cast<long long>(rows) * out.Kpad / 4 : static_cast<long long>(rows) * out.Kpad;
+    j.sstride = static_cast<long long>(rows) * out.Kpad / 4;
     const int rblocks = (rows + oz::SLICE_ROWS - 1) / oz::SLICE_ROWS;
-    j.nbx = j.vec ? (out.Kpad / 4 + 255) / 256 : (out.Kpad + 255) / 256;
+    j.nbx = (out.Kpad / 4 + 255) / 256;
     j.nby = rblocks < 65535 ? rblocks : 65535;
     sb.jobs.push_back(j);
     (void)out.S;
@@ -413,12 +409,15 @@ static jk_status slice_flush(jk_ctx *h, SliceBatch &sb, cudaStream_t st, bool ex
 // The exponents of the rank-update operands of whole panels (every density
 // of one aux chunk of one or several molecules), from whole rows of each panel
 // T (oz::panel_colmax_kernel), in grouped launches.  Usable when every k <=
-// SUPER (a run of one p spans at most two super-chunks).
+// SUPER (a run of one p spans at most two super-chunks) and a panel row's
+// upper words fit the block's shared memory.
 static bool panel_expo_fits(const Problem &pb) {
     for (int s = 0; s < pb.nd; s++)
         if (pb.k[s] > oz::SUPER) return false;
-    return 2 * pb.nd <= oz::MAXSEG;
+    return 2 * pb.nd <= oz::PANEL_SEG_ITEM;
 }
+static_assert(2 * kMaxDens <= oz::PANEL_SEG_ITEM && oz::PANEL_SEG_ITEM <= oz::MAXSEG,
+              "one panel's operands fit the row-wise exponent launch");
 struct PanelBatch {
     struct Item {
         const Problem *pb;
@@ -458,8 +457,14 @@ static jk_status panel_flush(jk_ctx *h, PanelBatch &pbt, cudaStream_t st) {
     long long blocks = 0;
     for (const auto &itm : pbt.items) {
         const Problem &pb = *itm.pb;
-        int want = 0;
-        for (int s = 0; s < pb.nd; s++) want += pb.sym[s] ? 1 : 2;
+        int want = 0, ncol = 1, kmax = 1;
+        for (int s = 0; s < pb.nd; s++) {
+            want += pb.sym[s] ? 1 : 2;
+            ncol = std::max(ncol, pb.offX[s] + pb.k[s]);
+            if (!pb.sym[s]) ncol = std::max(ncol, pb.offY[s] + pb.k[s]);
+            kmax = std::max(kmax, pb.k[s]);
+        }
+        if (want > oz::PANEL_SEG_ITEM) return set_error(h, JK_ERR_SHAPE, "too many operands in one panel");
         if (g.nitem == oz::MAXPITEM || g.nseg + want > oz::MAXSEG) {
             JK_TRY(panel_launch(h, g, nscmax, blocks, st));
             g.nitem = g.nseg = 0;
@@ -473,6 +478,13 @@ static jk_status panel_flush(jk_ctx *h, PanelBatch &pbt, cudaStream_t st) {
         pi.rows = itm.np * pb.n;
         pi.seg0 = g.nseg;
         pi.b0 = static_cast<int>(blocks);
+        int lanes = 4;   // the fewest lanes (4 .. 32) that cover k in PANEL_V words each
+        while (lanes < 32 && lanes * oz::PANEL_V < kmax) lanes *= 2;
+        pi.lanes = lanes;
+        // one row per lane group (8 warps of 32 / lanes groups), more for
+        // short rows: about 8192 elements per block, at most 8 rows per group
+        const int gr = 8 * (32 / lanes);
+        pi.rpb = gr * std::max(1, std::min(8, 8192 / (gr * ncol)));
         for (int s = 0; s < pb.nd; s++) {
             const int nsc = (itm.np * pb.k[s] + oz::SUPER - 1) / oz::SUPER;
             nscmax = std::max(nscmax, nsc);
@@ -480,7 +492,7 @@ static jk_status panel_flush(jk_ctx *h, PanelBatch &pbt, cudaStream_t st) {
             if (!pb.sym[s]) g.s[g.nseg++] = oz::PanelSeg{itm.TY[s].e, pb.offY[s], pb.k[s], nsc, pb.n};
         }
         pi.nseg = g.nseg - pi.seg0;
-        blocks += pi.rows;
+        blocks += (pi.rows + pi.rpb - 1) / pi.rpb;
     }
     if (g.nitem > 0) JK_TRY(panel_launch(h, g, nscmax, blocks, st));
     pbt.items.clear();

@@ -7,6 +7,9 @@
 //   digits6 + qbf16: the same bounds and exact sum for the integer digits,
 //   and qbf16(q_j, 2^-8(j+1)) is the BF16 encoding of q_j * 2^-8(j+1).
 //   digits_n<7>: the same for seven digits of 56-bit values.
+//   digit_values<6> / <7> (the slicer kernels' byte form): every value equal
+//   to the integer path's q_j * 2^-8(j+1), bit for bit, and an exact BF16
+//   value, so pack_bf16x2 of two of them is the pair of qbf16 words.
 // Prints "ok <count>" and exits 0, or the first violation and exits 1.
 #include <cmath>
 #include <cstdint>
@@ -15,6 +18,34 @@
 #include <random>
 
 #include "../../paper_2608_06536_b300/csrc/digits.cuh"
+
+// digit_values<S>(F) against the integer digits q of the same F: equal FP32
+// words (q_j * 2^-8(j+1) is exact; a zero digit is +0), low halves zero, and
+// pack_bf16x2 of slices j and j+1 giving the qbf16 words of q_j and q_j+1.
+template <int S>
+static int check_values(long long F, const int q[S]) {
+    float v[S];
+    jk::digits::digit_values<S>(F, v);
+    float sc = 0.00390625f;
+    for (int j = 0; j < S; j++) {
+        const double want = std::ldexp(static_cast<double>(q[j]), -8 * (j + 1));
+        uint32_t bits;
+        std::memcpy(&bits, &v[j], 4);
+        if (static_cast<double>(v[j]) != want || (bits & 0xFFFFu) || bits == 0x80000000u) {
+            std::printf("F=%lld: digit_values<%d> slice %d is %a, want %a\n", F, S, j, v[j], want);
+            return 1;
+        }
+        if (j + 1 == S) break;
+        const uint32_t w = jk::digits::pack_bf16x2(v[j], v[j + 1]);
+        const uint32_t ref = jk::digits::qbf16(q[j], sc) | (jk::digits::qbf16(q[j + 1], sc * 0.00390625f) << 16);
+        if (w != ref) {
+            std::printf("F=%lld: pack_bf16x2 of slice %d is %08x, want %08x\n", F, j, w, ref);
+            return 1;
+        }
+        sc *= 0.00390625f;
+    }
+    return 0;
+}
 
 static int check(long long F) {
     float v[6];
@@ -62,7 +93,7 @@ static int check(long long F) {
         std::printf("F=%lld: integer digits sum to %lld\n", F, static_cast<long long>(isum));
         return 1;
     }
-    return 0;
+    return check_values<6>(F, q);
 }
 
 // The seven-digit split of a 56-bit value: exact sum, digit bounds, and
@@ -91,7 +122,7 @@ static int check7(long long F) {
         std::printf("F=%lld: seven digits sum to %lld\n", F, static_cast<long long>(sum));
         return 1;
     }
-    return 0;
+    return check_values<7>(F, q);
 }
 
 int main() {

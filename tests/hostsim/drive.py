@@ -106,7 +106,8 @@ class PanelSeg(ct.Structure):
 
 
 class PanelItem(ct.Structure):
-    _fields_ = [("T", VP), ("ldT", I64), ("n", I32), ("rows", I32), ("seg0", I32), ("nseg", I32), ("b0", I32)]
+    _fields_ = [("T", VP), ("ldT", I64), ("n", I32), ("rows", I32), ("seg0", I32), ("nseg", I32), ("b0", I32),
+                ("rpb", I32), ("lanes", I32)]
 
 
 class PanelExpo(ct.Structure):
@@ -204,7 +205,7 @@ def dec_expo(grid, args):
 
 def dec_expo_flat(grid, args):
     p, ln, e = _v(args, 0, VP), _v(args, 1, I64), _v(args, 2, VP)
-    assert ln % 2 == 0 and p % 16 == 0
+    assert ln >= 1 and p % 8 == 0
     return [(p, p + 8 * grid[0] * ln, "p"), (e, e + 4 * grid[0], "e")]
 
 
@@ -218,7 +219,7 @@ def _slice(grid, args, esize_out, per, nslice):
 
 
 def dec_slice(grid, args, name):
-    return _slice(grid, args, 2, 1, _slices_of(name))
+    return _slice(grid, args, 8, 4, _slices_of(name))
 
 
 def dec_slice4(grid, args, name):
@@ -251,7 +252,9 @@ def dec_expo_group(grid, args):
         assert jb.nsc == (jb.K + SUPER - 1) // SUPER and jb.Kpad % 16 == 0 and jb.K <= jb.Kpad
         groups = (jb.rows - 1) // jb.rpe + 1
         if jb.flat:
-            assert jb.nsc == 1 and jb.src.p % 16 == 0 and (jb.rpe * jb.K) % 2 == 0 and jb.rows % jb.rpe == 0
+            # contiguous runs of rpe * K doubles (any alignment and parity)
+            assert jb.nsc == 1 and jb.src.p % 8 == 0 and jb.rows % jb.rpe == 0
+            assert jb.src.rin == 1 and jb.src.ski == 1 and jb.src.kin == jb.K and jb.src.sr == jb.K
         res += [_src_range(jb.src, jb.rows, jb.K), (jb.e, jb.e + 4 * groups * jb.nsc, "e")]
     return res
 
@@ -265,13 +268,16 @@ def _panel_items(g):
     for i in range(g.nitem):
         pi = g.it[i]
         assert pi.b0 == b and pi.seg0 == seg and pi.n >= 1 and pi.rows % pi.n == 0 and pi.nseg >= 1, (i, pi.b0, b)
+        # rows per block, lane groups that tile a warp, the panel's operands
+        # staged in the block's shared table
+        assert 1 <= pi.rpb and pi.lanes in (4, 8, 16, 32) and pi.nseg <= 128, (pi.rpb, pi.lanes, pi.nseg)
         np_ = pi.rows // pi.n
         segs = [g.s[j] for j in range(pi.seg0, pi.seg0 + pi.nseg)]
         for sg in segs:
             assert sg.n == pi.n and 1 <= sg.k <= SUPER and sg.nsc == (np_ * sg.k + SUPER - 1) // SUPER
             assert sg.c0 >= 0 and sg.c0 + sg.k <= pi.ldT
         out.append((pi, segs))
-        b += pi.rows
+        b += (pi.rows + pi.rpb - 1) // pi.rpb
         seg += pi.nseg
     assert seg == g.nseg
     return out, b
@@ -301,7 +307,7 @@ def dec_slice_group(grid, args, name):
     nslice = _slices_of(name)
     res = []
     for jb in jobs:
-        per, esize = (4, 8) if jb.vec else (1, 2)
+        per, esize = 4, 8   # four BF16 values per 8-byte word
         if jb.vec:
             assert jb.src.ski == 1 and jb.src.kin % 4 == 0 and jb.K % 4 == 0 and jb.src.p % 16 == 0
         assert jb.nbx * 256 * per >= jb.Kpad and jb.nby >= 1 and jb.sstride * per == jb.rows * jb.Kpad

@@ -1,10 +1,12 @@
-"""Both digit splits of the slicer (csrc/digits.cuh: the integer digits6 with
-its BF16 encoding qbf16, and the FP32-addition split48), compiled as host C++
-and checked on the CPU over random and edge-case 48-bit values: the six
+"""The digit splits of the slicer (csrc/digits.cuh: the byte form
+digit_values with pack_bf16x2, the integer digits6 / digits_n<7> with their
+BF16 encoding qbf16, and the FP32-addition split48), compiled as host C++ and
+checked on the CPU over random and edge-case 48-bit (and 56-bit) values: the
 digits sum exactly to the value, stay within the bounds the GEMM's exact
-accumulation windows assume (|q_0| <= 256, |q_j| <= 128), and are exact BF16
-values.  The same source compiles into the device kernels (slice_kernel,
-slice4_kernel, slice4f_kernel)."""
+accumulation windows assume (|q_0| <= 256, |q_j| <= 128), are exact BF16
+values, and the byte form equals the integer digits bit for bit.  The same
+source compiles into the device kernels (slice_kernel, slice4_kernel,
+slice_group_kernel, slice4f_kernel)."""
 import os
 import subprocess
 
