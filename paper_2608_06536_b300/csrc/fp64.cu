@@ -276,10 +276,12 @@ jstream_kernel(const double *L, long long n2, int naux, const double *g,
 // n(n+1)/2 upper-triangle entries are formed (one per thread, consecutive
 // threads on consecutive columns of a row), then mirrored: half the FP64 work.
 // PK: L is stored as packed upper triangles ([naux][n(n+1)/2]), read at the
-// thread's own position t (contiguous across the threads of a warp).
+// thread's own position t (contiguous across the threads of a warp).  The
+// sum runs over P = P0 .. P0 + np - 1 in order; acc adds it to Out (a build
+// that takes the aux indices chunk by chunk), else Out is overwritten.
 template <int NS, bool PK>
 __global__ void __launch_bounds__(64)
-jstream_sym_kernel(const double *L, int n, int naux, const double *g, int ldg, OutTab Out) {
+jstream_sym_kernel(const double *L, int n, int P0, int np, const double *g, int ldg, int acc, OutTab Out) {
     const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (t >= packed::tri_count(n)) return;
     int mu, nu;
@@ -291,23 +293,25 @@ jstream_sym_kernel(const double *L, int n, int naux, const double *g, int ldg, O
     for (int j = 0; j < NS; j++) a[j] = 0.0;
     const double *Lp = PK ? L + t : L + e;
     const long long pstride = PK ? packed::tri_count(n) : n2;
-    for (int P = 0; P < naux; P++) {
+    for (int P = P0; P < P0 + np; P++) {
         const double l = __ldg(Lp + (long long)P * pstride);
 #pragma unroll
         for (int j = 0; j < NS; j++) a[j] = fma(__ldg(g + (long long)j * ldg + P), l, a[j]);
     }
 #pragma unroll
     for (int j = 0; j < NS; j++) {
-        Out.p[j][e] = a[j];
-        if (nu != mu) Out.p[j][(long long)nu * n + mu] = a[j];
+        const double v = acc ? Out.p[j][e] + a[j] : a[j];
+        Out.p[j][e] = v;
+        if (nu != mu) Out.p[j][(long long)nu * n + mu] = v;
     }
 }
 
-// Out[s] = sum_P g[s][P] L^P for s < nd (Out[s] are [n][n] device arrays);
-// pk: L holds packed upper triangles.
-static jk_status jstream(jk_ctx *h, const double *L, int n, int naux,
+// Out[s] (+)= sum_P g[s][P] L^P, P = P0 .. P0 + np - 1, for s < nd (Out[s]
+// are [n][n] device arrays; acc: added to them); pk: L holds packed upper
+// triangles.
+static jk_status jstream(jk_ctx *h, const double *L, int n, int P0, int np,
                          const double *g, int ldg, int nd, double *const *Out,
-                         cudaStream_t st, bool pk = false) {
+                         cudaStream_t st, bool pk = false, bool acc = false) {
     const long long ntri = (long long)n * (n + 1) / 2;
     const int blocks = (int)((ntri + 63) / 64);
     for (int s0 = 0; s0 < nd; s0 += 8) {
@@ -319,8 +323,8 @@ static jk_status jstream(jk_ctx *h, const double *L, int n, int naux,
         switch (ns) {
 #define JS(N)                                                                              \
     case N:                                                                                \
-        if (pk) jstream_sym_kernel<N, true><<<blocks, 64, 0, st>>>(L, n, naux, gs, ldg, o);  \
-        else jstream_sym_kernel<N, false><<<blocks, 64, 0, st>>>(L, n, naux, gs, ldg, o);    \
+        if (pk) jstream_sym_kernel<N, true><<<blocks, 64, 0, st>>>(L, n, P0, np, gs, ldg, acc, o);  \
+        else jstream_sym_kernel<N, false><<<blocks, 64, 0, st>>>(L, n, P0, np, gs, ldg, acc, o);    \
         break;
             JS(1) JS(2) JS(3) JS(4) JS(5) JS(6) JS(7) JS(8)
 #undef JS
@@ -535,11 +539,17 @@ jk_status fp64_jstream_dense(jk_ctx *h, const double *L, int n, int naux, const 
                              cudaStream_t st, bool pk) {
     double *ptrs[kMaxDens];
     for (int s = 0; s < nd; s++) ptrs[s] = out + (long long)s * n * n;
-    return jstream(h, L, n, naux, g, naux, nd, ptrs, st, pk);
+    return jstream(h, L, n, 0, naux, g, naux, nd, ptrs, st, pk);
 }
 
 jk_status fp64_jstream(jk_ctx *h, const Problem &pb, const double *gamma, cudaStream_t st) {
-    return jstream(h, pb.L, pb.n, pb.naux, gamma, pb.naux, pb.nd, pb.J, st, pb.packed);
+    return jstream(h, pb.L, pb.n, 0, pb.naux, gamma, pb.naux, pb.nd, pb.J, st, pb.packed);
+}
+
+// J_s (+)= sum_P gamma_{P,s} L^P over the aux chunk P0 .. P0 + np - 1 (added
+// to J unless P0 == 0): a split build's J, one chunk at a time.
+jk_status fp64_jstream_chunk(jk_ctx *h, const Problem &pb, const double *gamma, int P0, int np, cudaStream_t st) {
+    return jstream(h, pb.L, pb.n, P0, np, gamma, pb.naux, pb.nd, pb.J, st, pb.packed, P0 > 0);
 }
 
 int fp64_default_pchunk(const Problem &pb) {
@@ -728,7 +738,7 @@ jk_status fp64_build(jk_ctx *h, const Problem &pb, cudaStream_t st) {
     if (K && h->syrk)
         for (int s = 0; s < nd; s++)
             if (pb.sym[s]) JK_TRY(mirror_sym_blocks(h, pb.K[s], n, st));
-    if (J) JK_TRY(jstream(h, pb.L, n, naux, gamma, naux, nd, pb.J, st, pb.packed));
+    if (J) JK_TRY(jstream(h, pb.L, n, 0, naux, gamma, naux, nd, pb.J, st, pb.packed));
     return JK_OK;
 }
 
@@ -968,7 +978,7 @@ jk_status fp64_adjoint(jk_ctx *h, const Problem &pb, const double *W,
         }
         double *jv[kMaxDens];
         for (int s = 0; s < nd; s++) jv[s] = JV + (long long)s * n2;
-        JK_TRY(jstream(h, pb.L, n, naux, cps, naux, nd, jv, st, pb.packed));
+        JK_TRY(jstream(h, pb.L, n, 0, naux, cps, naux, nd, jv, st, pb.packed));
         if (dL && pb.packed) {
             JK_TRY(fp64_frob_all(h, pb.L, n, naux, D, nd, gamma, st, true));
         } else if (dL) {

@@ -44,7 +44,7 @@ struct DeviceFlags {
 // Kernel kinds for launch accounting / event timing.
 enum KernelKind {
     KK_DGEMM = 0, KK_JSTREAM, KK_FROB, KK_GAMMA, KK_PACK, KK_MISC,
-    KK_SLICE, KK_OZGEMM, KK_OZREDUCE, KK_COUNT
+    KK_SLICE, KK_OZGEMM, KK_OZREDUCE, KK_EXPO, KK_COUNT
 };
 
 struct Profiler {

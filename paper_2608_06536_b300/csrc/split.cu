@@ -175,7 +175,7 @@ static jk_status slice_operand(jk_ctx *h, const oz::Src &src, int rows, int K, i
     // A group of rows that is one contiguous run of doubles (e.g. one L^P).
     const bool flat = nsc == 1 && src.rin == 1 && src.ski == 1 && src.kin == K && src.sr == K && rows % rpe == 0;
     {
-        LaunchScope ls(h, KK_SLICE, st);
+        LaunchScope ls(h, KK_EXPO, st);
         if (flat)
             oz::expo_flat_kernel<<<groups, 256, 0, st>>>(src.p, static_cast<long long>(rpe) * K, out.e);
         else
@@ -392,7 +392,7 @@ static jk_status slice_flush(jk_ctx *h, SliceBatch &sb, cudaStream_t st, bool ex
         if (eb > 0x7fffffffLL || sbk > 0x7fffffffLL) return set_error(h, JK_ERR_SHAPE, "too many slicer blocks");
         grp.njob = nj;
         if (expo) {
-            LaunchScope ls(h, KK_SLICE, st);
+            LaunchScope ls(h, KK_EXPO, st);
             oz::expo_group_kernel<<<static_cast<unsigned>(eb), 256, 0, st>>>(grp);
         }
         if (expo) JK_LAUNCH_CHECK(h);
@@ -435,7 +435,7 @@ static void panel_add(PanelBatch &pbt, const Problem &pb, const double *T, long 
 static jk_status panel_launch(jk_ctx *h, oz::PanelExpo &g, int nscmax, long long blocks, cudaStream_t st) {
     if (blocks > 0x7fffffffLL) return set_error(h, JK_ERR_SHAPE, "too many panel rows");
     {
-        LaunchScope ls(h, KK_SLICE, st);
+        LaunchScope ls(h, KK_EXPO, st);
         int nmax = 1;
         for (int i = 0; i < g.nitem; i++) nmax = std::max(nmax, g.it[i].n);
         const int bx = std::min(1024, (nmax * nscmax + 255) / 256);
@@ -443,7 +443,7 @@ static jk_status panel_launch(jk_ctx *h, oz::PanelExpo &g, int nscmax, long long
     }
     JK_LAUNCH_CHECK(h);
     {
-        LaunchScope ls(h, KK_SLICE, st);
+        LaunchScope ls(h, KK_EXPO, st);
         oz::panel_colmax_kernel<<<static_cast<unsigned>(blocks), 256, 0, st>>>(g);
     }
     JK_LAUNCH_CHECK(h);
@@ -676,11 +676,15 @@ jk_status fp64_unpack_sym(jk_ctx *h, const double *packed, int n, long long np, 
 jk_status fp64_gamma_panel(jk_ctx *h, const Problem &pb, const double *T, long long ldT, int np, double *gamma,
                            int P0, cudaStream_t st);
 jk_status fp64_jstream(jk_ctx *h, const Problem &pb, const double *gamma, cudaStream_t st);
+jk_status fp64_jstream_chunk(jk_ctx *h, const Problem &pb, const double *gamma, int P0, int np, cudaStream_t st);
 
 // The FP64 J back-contraction needs only the factor and gamma, and runs on the
 // FP64 pipe: it is forked onto a second stream as soon as gamma is complete
 // and overlaps the rank updates on the tensor pipe (join at the end of the
-// build, so the call stays ordered on the caller's stream).
+// build, so the call stays ordered on the caller's stream).  A single
+// molecule's build forks it once per aux chunk (J accumulated chunk by chunk
+// in order), so it runs beside every chunk's rank updates, not only the
+// last's.
 static jk_status fork_jstream(jk_ctx *h, cudaStream_t st) {
     if (!h->aux_stream) {
         JK_CUDA_TRY(h, cudaStreamCreateWithFlags(&h->aux_stream, cudaStreamNonBlocking));
@@ -744,10 +748,10 @@ jk_status split_build(jk_ctx *h, const Problem &pb, cudaStream_t st) {
         } else {
             JK_TRY(ozgemm(h, Lc, Zs, T, ldT, nullptr, st));
         }
-        if (pb.wantJ) JK_TRY(fp64_gamma_panel(h, pb, T, ldT, np, gamma, P0, st));
-        if (pb.wantJ && P0 + np >= naux) {
+        if (pb.wantJ) {
+            JK_TRY(fp64_gamma_panel(h, pb, T, ldT, np, gamma, P0, st));
             JK_TRY(fork_jstream(h, st));
-            JK_TRY(fp64_jstream(h, pb, gamma, h->aux_stream));
+            JK_TRY(fp64_jstream_chunk(h, pb, gamma, P0, np, h->aux_stream));
         }
         if (!pb.wantK) continue;
         // The rank-update operands of every density (grouped launches unless

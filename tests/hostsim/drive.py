@@ -388,13 +388,17 @@ def dec_gamma_panel(grid, args):
     return out
 
 
+def _jstream_args(args):
+    return (_v(args, 0, VP), _v(args, 1, I32), _v(args, 2, I32), _v(args, 3, I32), _v(args, 4, VP),
+            _v(args, 5, I32), _v(args, 6, I32), _a(args, 7, OutTab))
+
+
 def dec_jstream_sym(grid, args, name):
     ns = int(name.split("ILi")[1].split("E")[0])
-    L, n, naux, g, ldg, o = (_v(args, 0, VP), _v(args, 1, I32), _v(args, 2, I32), _v(args, 3, VP),
-                             _v(args, 4, I32), _a(args, 5, OutTab))
-    assert grid[0] * 64 >= n * (n + 1) // 2
+    L, n, P0, np_, g, ldg, acc, o = _jstream_args(args)
+    assert grid[0] * 64 >= n * (n + 1) // 2 and P0 >= 0 and np_ >= 1 and acc in (0, 1)
     per = n * (n + 1) // 2 if "Lb1E" in name else n * n          # packed factor: upper triangles
-    out = [(L, L + 8 * naux * per, "L"), (g, g + 8 * ((ns - 1) * ldg + naux), "g")]
+    out = [(L + 8 * P0 * per, L + 8 * (P0 + np_) * per, "L"), (g, g + 8 * ((ns - 1) * ldg + P0 + np_), "g")]
     out += [(o.p[j], o.p[j] + 8 * n * n, "J") for j in range(ns)]
     return out
 
@@ -635,21 +639,25 @@ def ex_gamma_panel(grid, args):
 
 def ex_jstream_sym(grid, args, name):
     ns = int(name.split("ILi")[1].split("E")[0])
-    L, n, naux, g, ldg, o = (_v(args, 0, VP), _v(args, 1, I32), _v(args, 2, I32), _v(args, 3, VP),
-                             _v(args, 4, I32), _a(args, 5, OutTab))
+    L, n, P0, np_, g, ldg, acc, o = _jstream_args(args)
+    naux = P0 + np_
     if "Lb1E" in name:                                            # packed upper triangles
         iu = np.triu_indices(n)
-        P = dv(L, naux * len(iu[0])).reshape(naux, -1)
-        full = np.zeros((naux, n, n))
+        P = dv(L, naux * len(iu[0])).reshape(naux, -1)[P0:]
+        full = np.zeros((np_, n, n))
         full[:, iu[0], iu[1]] = P
         full[:, iu[1], iu[0]] = P
-        Lm = full.reshape(naux, n * n)
+        Lm = full.reshape(np_, n * n)
     else:
-        Lm = dv(L, naux * n * n).reshape(naux, n * n)
+        Lm = dv(L, naux * n * n).reshape(naux, n * n)[P0:]
     for j in range(ns):
-        out = dv(g + 8 * j * ldg, naux) @ Lm
+        out = dv(g + 8 * j * ldg, naux)[P0:] @ Lm
         out = out.reshape(n, n)
-        dv(o.p[j], n * n)[:] = np.triu(out).ravel() + np.triu(out, 1).T.ravel()   # upper triangle, mirrored
+        sym = np.triu(out).ravel() + np.triu(out, 1).T.ravel()   # upper triangle, mirrored
+        if acc:
+            dv(o.p[j], n * n)[:] += sym
+        else:
+            dv(o.p[j], n * n)[:] = sym
 
 
 def ex_axpy(grid, args):
