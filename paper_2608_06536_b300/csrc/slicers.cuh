@@ -9,6 +9,7 @@
 #include "digits.cuh"
 #include "fixed.cuh"
 #include "ozcfg.cuh"
+#include "packed.cuh"
 
 namespace jk {
 namespace oz {
@@ -527,6 +528,111 @@ __global__ void __launch_bounds__(256) panel_colmax_kernel(const __grid_constant
     case 8: colmax_rows<8>(pi, sc, snsc, se, r0, R); break;
     case 16: colmax_rows<16>(pi, sc, snsc, se, r0, R); break;
     default: colmax_rows<32>(pi, sc, snsc, se, r0, R); break;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// The J back-contraction's operand: the factor chunk, transposed
+// ---------------------------------------------------------------------------
+// J_s = sum_P gamma_{P,s} L^P is symmetric, so it is formed on the upper
+// triangle as the sliced GEMM C[t][s] = sum_kk A[t][kk] G[s][kk] with
+// A[t][kk] = L^{P0+kk}[mu][nu] (t = t(mu, nu), mu <= nu, the packed-triangle
+// position) and G[s][kk] = gamma_{P0+kk,s}.  The factor is stored P-major, so
+// A's rows are strided columns of it: an exponent pass with one thread per
+// row t (the threads of a warp on consecutive positions, i.e. consecutive
+// addresses of each L^P), then a slicer that stages 64 x 64 tiles of L in
+// shared memory and writes each row's digits along kk.  PK: the factor holds
+// packed upper triangles (position t is the row's offset in L^P).
+constexpr int TRI_TILE = 64;
+
+template <bool PK>
+__device__ __forceinline__ long long tri_offset(int n, long long t) {
+    if (PK) return t;
+    int mu, nu;
+    packed::tri_row_col(n, t, &mu, &nu);
+    return static_cast<long long>(mu) * n + nu;
+}
+
+// e[t * nsc + z] = exponent of max |A[t][kk]| over kk in super-chunk z
+// (blockIdx.y = z).  pstride: doubles between consecutive L^P.
+template <bool PK>
+__global__ void __launch_bounds__(256) expo_tri_kernel(const double *L, int n, long long pstride, int P0, int np,
+                                                       int nsc, int *e) {
+    const long long t = blockIdx.x * 256LL + threadIdx.x;
+    if (t >= packed::tri_count(n)) return;
+    const int z = blockIdx.y, k0 = z * SUPER, k1 = min(np, k0 + SUPER);
+    const double *p = L + static_cast<long long>(P0 + k0) * pstride + tri_offset<PK>(n, t);
+    constexpr unsigned long long kAbs = 0x7FFFFFFFFFFFFFFFull;
+    unsigned long long mx = 0;
+    int kk = 0;
+    for (; kk + 8 <= k1 - k0; kk += 8) {
+        unsigned long long v[8];
+#pragma unroll
+        for (int u = 0; u < 8; u++)
+            v[u] = static_cast<unsigned long long>(__double_as_longlong(p[static_cast<long long>(kk + u) * pstride])) & kAbs;
+#pragma unroll
+        for (int u = 0; u < 8; u++) mx = v[u] > mx ? v[u] : mx;
+    }
+    for (; kk < k1 - k0; kk++) {
+        const unsigned long long v = static_cast<unsigned long long>(__double_as_longlong(p[static_cast<long long>(kk) * pstride])) & kAbs;
+        mx = v > mx ? v : mx;
+    }
+    e[t * nsc + z] = exponent_of_max(mx);
+}
+
+// The six digit planes of A: out[j][t][kk] (Kpad columns, zero for kk >= np).
+// Block (bx, by) takes rows t0 = 64 bx .. t0 + 63 and kk0 = 64 by .. kk0 + 63.
+template <bool PK>
+__global__ void __launch_bounds__(256) slice_tri_kernel(const double *L, int n, long long pstride, int P0, int np,
+                                                        int Kpad, int nsc, const int *e, uint2 *out,
+                                                        long long sstride4) {
+    constexpr int S = 6;
+    __shared__ double tile[TRI_TILE][TRI_TILE + 1];   // [kk - kk0][t - t0]
+    __shared__ long long soff[TRI_TILE];
+    const long long ntri = packed::tri_count(n);
+    const long long t0 = blockIdx.x * static_cast<long long>(TRI_TILE);
+    const int kk0 = blockIdx.y * TRI_TILE;
+    if (threadIdx.x < TRI_TILE) {
+        const long long t = t0 + threadIdx.x;
+        soff[threadIdx.x] = t < ntri ? tri_offset<PK>(n, t) : -1;
+    }
+    __syncthreads();
+    {
+        const int tc = threadIdx.x & (TRI_TILE - 1), kr0 = threadIdx.x >> 6;   // 4 rows kk per pass
+        const long long off = soff[tc];
+        double v[TRI_TILE / 4];
+#pragma unroll
+        for (int i = 0; i < TRI_TILE / 4; i++) {
+            const int kk = kk0 + kr0 + 4 * i;
+            v[i] = kk < np && off >= 0 ? L[static_cast<long long>(P0 + kk) * pstride + off] : 0.0;
+        }
+#pragma unroll
+        for (int i = 0; i < TRI_TILE / 4; i++) tile[kr0 + 4 * i][tc] = v[i];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < TRI_TILE * TRI_TILE / 4 / 256; i++) {
+        const int task = i * 256 + static_cast<int>(threadIdx.x), tr = task >> 4, g = task & 15;
+        const long long t = t0 + tr;
+        const int kk = kk0 + 4 * g;
+        if (t >= ntri || kk >= Kpad) continue;
+        uint32_t glo[4], ghi[4];
+        if (kk < np) {
+            const int er = e[t * nsc + kk / SUPER];
+#pragma unroll
+            for (int u = 0; u < 4; u++) digits::biased_words<S>(to_fixed(tile[4 * g + u][tr], er, 8 * S), glo[u], ghi[u]);
+        } else {
+#pragma unroll
+            for (int u = 0; u < 4; u++) digits::biased_words<S>(0, glo[u], ghi[u]);
+        }
+        const long long o = (t * Kpad + kk) >> 2;
+#pragma unroll
+        for (int j = 0; j < S; j++) {
+            uint2 w;
+            w.x = digits::pack_bf16x2(digits::digit_value<S>(glo[0], ghi[0], j), digits::digit_value<S>(glo[1], ghi[1], j));
+            w.y = digits::pack_bf16x2(digits::digit_value<S>(glo[2], ghi[2], j), digits::digit_value<S>(glo[3], ghi[3], j));
+            out[j * sstride4 + o] = w;
+        }
     }
 }
 

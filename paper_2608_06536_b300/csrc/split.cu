@@ -1,7 +1,8 @@
 // Split-precision engine: FP64-accurate J/K from BF16 tensor-core products.
 //
-// Every dense contraction of the build (panels T = L Z and the rank update
-// K_s = sum_P T_X T_Y^T) is computed as an error-free-split product:
+// Every dense contraction of the build (panels T = L Z, the rank update
+// K_s = sum_P T_X T_Y^T and the J back-contraction J_s = sum_P gamma_{P,s}
+// L^P on the upper triangle) is computed as an error-free-split product:
 //
 //  * Slicing.  Each operand row r is scaled by 2^-e_r (e_r from the row's
 //    largest magnitude) and rounded once to a 48-bit fixed-point integer F,
@@ -60,6 +61,26 @@ __global__ void __launch_bounds__(256) mirror_blocks_kernel(double *K, int n, in
     if (e >= static_cast<long long>(n) * n) return;
     const int r = static_cast<int>(e / n), c = static_cast<int>(e - static_cast<long long>(r) * n);
     if (c < bm * (r / bm)) K[e] = K[static_cast<long long>(c) * n + r];
+}
+
+// J_s[mu][nu] = J_s[nu][mu] (+)= C[t][s] for every upper-triangle position
+// t = t(mu, nu) (the sliced GEMM's J back-contraction of one aux chunk; acc:
+// added to J, the chunks in order).
+struct JOut {
+    double *p[kMaxDens];
+};
+__global__ void __launch_bounds__(256) j_tri_add_kernel(const double *C, long long ldc, int n, int nd, int acc,
+                                                        JOut J) {
+    const long long t = blockIdx.x * 256LL + threadIdx.x;
+    if (t >= packed::tri_count(n)) return;
+    int mu, nu;
+    packed::tri_row_col(n, t, &mu, &nu);
+    const long long e = static_cast<long long>(mu) * n + nu, em = static_cast<long long>(nu) * n + mu;
+    for (int s = 0; s < nd; s++) {
+        const double v = acc ? J.p[s][e] + C[t * ldc + s] : C[t * ldc + s];
+        J.p[s][e] = v;
+        if (mu != nu) J.p[s][em] = v;
+    }
 }
 
 }  // namespace oz
@@ -330,6 +351,89 @@ static jk_status reduce_partials(jk_ctx *h, const long long *P, int nz, const Sl
         oz::reduce_partials_kernel<<<static_cast<unsigned>((tot + 255) / 256), 256, 0, st>>>(
             P, part_rows(A.rows) * ldp, ldp, nz, A.rows, B.rows, A.e, A.rpe, B.e, B.rpe, out, ldo,
             accumulate ? 1 : 0, A.S == 7 ? oz::Cfg7::FRAC : oz::Cfg6::FRAC);
+    }
+    JK_LAUNCH_CHECK(h);
+    return JK_OK;
+}
+
+// ---- the J back-contraction on the tensor cores ------------------------------
+// Buffers of one build's J: the transposed factor chunk's slices (rows: the
+// n(n+1)/2 upper-triangle positions, K: the chunk's aux indices), gamma's
+// slices, the chunk's C[t][s] and, for chunks longer than SUPER, its split-K
+// partials.
+struct JBufs {
+    Sliced A, G;
+    double *C = nullptr;
+    long long ldc = 0;
+    long long *P = nullptr;
+};
+
+static long long tri_rows(int n) { return packed::tri_count(n); }
+
+static size_t jbufs_bytes(const Problem &pb, int pc) {
+    const long long nt = tri_rows(pb.n);
+    size_t b = sliced_bytes(static_cast<int>(nt), pc, 1) + sliced_bytes(pb.nd, pc, 1) +
+               align_up(static_cast<size_t>(nt) * even_ld(pb.nd) * 8);
+    if (nsuper_of(pc) > 1) b += align_up(static_cast<size_t>(nsuper_of(pc)) * part_rows(nt) * even_ld(pb.nd) * 8);
+    return b + 4 * kArenaAlign;
+}
+
+static bool take_jbufs(Arena &ar, const Problem &pb, int pc, JBufs &jb) {
+    const long long nt = tri_rows(pb.n);
+    bool ok = take_sliced(ar, static_cast<int>(nt), pc, 1, jb.A) && take_sliced(ar, pb.nd, pc, 1, jb.G);
+    jb.ldc = even_ld(pb.nd);
+    jb.C = ar.take<double>(static_cast<size_t>(nt) * jb.ldc);
+    if (nsuper_of(pc) > 1) jb.P = ar.take<long long>(static_cast<size_t>(nsuper_of(pc)) * part_rows(nt) * jb.ldc);
+    return ok && jb.C && (nsuper_of(pc) == 1 || jb.P);
+}
+
+// J_s (+)= sum_{P in P0 .. P0+np-1} gamma_{P,s} L^P (added unless P0 == 0):
+// the chunk's factor sliced transposed, gamma's chunk sliced, one sliced GEMM
+// C[t][s] = sum_kk A[t][kk] G[s][kk] and its scatter onto both triangles.
+static jk_status split_j_chunk(jk_ctx *h, const Problem &pb, const double *gamma, int P0, int np, JBufs &jb,
+                               cudaStream_t st) {
+    const int n = pb.n;
+    const long long nt = tri_rows(n);
+    const long long pstride = pb.packed ? nt : static_cast<long long>(n) * n;
+    Sliced &A = jb.A;
+    A.rows = static_cast<int>(nt);
+    A.K = np;
+    A.Kpad = kpad_of(np);
+    A.rpe = 1;
+    const int nsc = nsuper_of(np);
+    {
+        LaunchScope ls(h, KK_EXPO, st);
+        const dim3 grid(static_cast<unsigned>((nt + 255) / 256), nsc);
+        if (pb.packed) oz::expo_tri_kernel<true><<<grid, 256, 0, st>>>(pb.L, n, pstride, P0, np, nsc, A.e);
+        else oz::expo_tri_kernel<false><<<grid, 256, 0, st>>>(pb.L, n, pstride, P0, np, nsc, A.e);
+    }
+    JK_LAUNCH_CHECK(h);
+    {
+        LaunchScope ls(h, KK_SLICE, st);
+        const dim3 grid(static_cast<unsigned>((nt + oz::TRI_TILE - 1) / oz::TRI_TILE),
+                        (A.Kpad + oz::TRI_TILE - 1) / oz::TRI_TILE);
+        uint2 *o4 = reinterpret_cast<uint2 *>(A.s);
+        const long long ss4 = nt * A.Kpad / 4;
+        if (pb.packed)
+            oz::slice_tri_kernel<true><<<grid, 256, 0, st>>>(pb.L, n, pstride, P0, np, A.Kpad, nsc, A.e, o4, ss4);
+        else
+            oz::slice_tri_kernel<false><<<grid, 256, 0, st>>>(pb.L, n, pstride, P0, np, A.Kpad, nsc, A.e, o4, ss4);
+    }
+    JK_LAUNCH_CHECK(h);
+    oz::Src gsrc{gamma + P0, pb.naux, 0, 1, np};   // row s: gamma[s][P0 ..]
+    JK_TRY(slice_operand(h, gsrc, pb.nd, np, 1, jb.G, st));
+    if (nsc == 1) {
+        JK_TRY(ozgemm(h, A, jb.G, jb.C, jb.ldc, nullptr, st));
+    } else {
+        JK_TRY(ozgemm(h, A, jb.G, nullptr, 0, jb.P, st));
+        JK_TRY(reduce_partials(h, jb.P, nsc, A, jb.G, jb.C, jb.ldc, false, st));
+    }
+    oz::JOut jo;
+    for (int s = 0; s < kMaxDens; s++) jo.p[s] = s < pb.nd ? pb.J[s] : nullptr;
+    {
+        LaunchScope ls(h, KK_MISC, st);
+        oz::j_tri_add_kernel<<<static_cast<unsigned>((nt + 255) / 256), 256, 0, st>>>(jb.C, jb.ldc, n, pb.nd,
+                                                                                       P0 > 0 ? 1 : 0, jo);
     }
     JK_LAUNCH_CHECK(h);
     return JK_OK;
@@ -622,6 +726,7 @@ static int split_pchunk(const Problem &pb) {
     const size_t n = pb.n;
     size_t per = n * n * (6 * 2) + n * pb.ctot * 8 + n * pb.ctot * (6 * 2);
     if (pb.packed) per += n * n * 8;               // the expanded factor chunk
+    per += n * (n + 1) / 2 * (6 * 2);              // the transposed chunk's slices (J)
     size_t budget = static_cast<size_t>(12) << 30;
     size_t pc = per ? budget / per : 1;
     if (pc < 1) pc = 1;
@@ -667,6 +772,7 @@ size_t split_build_workspace(const Problem &pb) {
     if (pb.n > oz::SUPER)
         b += align_up(static_cast<size_t>(nsuper_of(pb.n)) * part_rows(static_cast<long long>(pc) * n) * even_ld(pb.ctot) * 8);
     if (pb.packed) b += align_up(static_cast<size_t>(pc) * n * n * 8);   // expanded factor chunk
+    b += jbufs_bytes(pb, pc);   // J on the tensor cores (counted whether or not J is asked for: queries do not say)
     return b;
 }
 
@@ -676,15 +782,13 @@ jk_status fp64_unpack_sym(jk_ctx *h, const double *packed, int n, long long np, 
 jk_status fp64_gamma_panel(jk_ctx *h, const Problem &pb, const double *T, long long ldT, int np, double *gamma,
                            int P0, cudaStream_t st);
 jk_status fp64_jstream(jk_ctx *h, const Problem &pb, const double *gamma, cudaStream_t st);
-jk_status fp64_jstream_chunk(jk_ctx *h, const Problem &pb, const double *gamma, int P0, int np, cudaStream_t st);
 
-// The FP64 J back-contraction needs only the factor and gamma, and runs on the
-// FP64 pipe: it is forked onto a second stream as soon as gamma is complete
-// and overlaps the rank updates on the tensor pipe (join at the end of the
-// build, so the call stays ordered on the caller's stream).  A single
-// molecule's build forks it once per aux chunk (J accumulated chunk by chunk
-// in order), so it runs beside every chunk's rank updates, not only the
-// last's.
+// The FP64 J back-contraction of a batched build needs only the factor and
+// gamma, and runs on the FP64 pipe: it is forked onto a second stream as soon
+// as a molecule's gamma is complete and overlaps the rank updates on the
+// tensor pipe (join at the end of the build, so the call stays ordered on the
+// caller's stream).  A single molecule's build forms J on the tensor cores
+// instead (split_j_chunk).
 static jk_status fork_jstream(jk_ctx *h, cudaStream_t st) {
     if (!h->aux_stream) {
         JK_CUDA_TRY(h, cudaStreamCreateWithFlags(&h->aux_stream, cudaStreamNonBlocking));
@@ -724,6 +828,8 @@ jk_status split_build(jk_ctx *h, const Problem &pb, cudaStream_t st) {
     if (n > oz::SUPER)
         Ppanel = ar.take<long long>(static_cast<size_t>(nsuper_of(n)) * part_rows(static_cast<long long>(pc) * n) * ldT);
     double *Lx = pb.packed ? ar.take<double>(static_cast<size_t>(pc) * n2) : nullptr;
+    JBufs jb;
+    if (pb.wantJ) ok = ok && take_jbufs(ar, pb, pc, jb);
     if (!ok || !T || !gamma || !Pbuf || !Kacc || (n > oz::SUPER && !Ppanel) || (pb.packed && !Lx))
         return set_error(h, JK_ERR_OOM, "workspace too small for the split build");
 
@@ -750,8 +856,7 @@ jk_status split_build(jk_ctx *h, const Problem &pb, cudaStream_t st) {
         }
         if (pb.wantJ) {
             JK_TRY(fp64_gamma_panel(h, pb, T, ldT, np, gamma, P0, st));
-            JK_TRY(fork_jstream(h, st));
-            JK_TRY(fp64_jstream_chunk(h, pb, gamma, P0, np, h->aux_stream));
+            JK_TRY(split_j_chunk(h, pb, gamma, P0, np, jb, st));
         }
         if (!pb.wantK) continue;
         // The rank-update operands of every density (grouped launches unless
@@ -823,7 +928,6 @@ jk_status split_build(jk_ctx *h, const Problem &pb, cudaStream_t st) {
     if (pb.wantK && h->syrk)
         for (int s = 0; s < nd; s++)
             if (pb.sym[s]) JK_TRY(mirror_sym_blocks(h, pb.K[s], n, st));
-    if (pb.wantJ) JK_TRY(join_jstream(h, st));
     return JK_OK;
 }
 

@@ -143,6 +143,10 @@ class OutTab(ct.Structure):
     _fields_ = [("p", VP * 8)]
 
 
+class JOut(ct.Structure):
+    _fields_ = [("p", VP * 64)]
+
+
 class PairTab(ct.Structure):
     _fields_ = [("offA", I32 * MAXD), ("offB", I32 * MAXD), ("k", I32 * MAXD)]
 
@@ -403,6 +407,39 @@ def dec_jstream_sym(grid, args, name):
     return out
 
 
+def _tri_args(args, name):
+    """(packed?, L, n, pstride, P0, np) of a transposed-factor slicing launch."""
+    pk = "ILb1E" in name
+    L, n, ps, P0, np_ = _v(args, 0, VP), _v(args, 1, I32), _v(args, 2, I64), _v(args, 3, I32), _v(args, 4, I32)
+    ntri = n * (n + 1) // 2
+    assert ps == (ntri if pk else n * n) and P0 >= 0 and np_ >= 1, (pk, ps, n, P0, np_)
+    return pk, L, n, ps, P0, np_, ntri
+
+
+def dec_expo_tri(grid, args, name):
+    pk, L, n, ps, P0, np_, ntri = _tri_args(args, name)
+    nsc, e = _v(args, 5, I32), _v(args, 6, VP)
+    assert nsc == (np_ + SUPER - 1) // SUPER and grid[1] == nsc and grid[0] * 256 >= ntri, (grid, nsc, ntri)
+    return [(L + 8 * P0 * ps, L + 8 * (P0 + np_) * ps, "L"), (e, e + 4 * ntri * nsc, "e")]
+
+
+def dec_slice_tri(grid, args, name):
+    pk, L, n, ps, P0, np_, ntri = _tri_args(args, name)
+    Kpad, nsc, e, out, ss4 = _v(args, 5, I32), _v(args, 6, I32), _v(args, 7, VP), _v(args, 8, VP), _v(args, 9, I64)
+    assert Kpad == (np_ + 15) // 16 * 16 and nsc == (np_ + SUPER - 1) // SUPER and ss4 * 4 == ntri * Kpad
+    assert grid[0] * 64 >= ntri and grid[1] * 64 >= Kpad and out % 16 == 0, (grid, ntri, Kpad)
+    return [(L + 8 * P0 * ps, L + 8 * (P0 + np_) * ps, "L"), (e, e + 4 * ntri * nsc, "e"),
+            (out, out + 8 * 6 * ss4, "slices")]
+
+
+def dec_j_tri_add(grid, args):
+    C, ldc, n, nd, acc, jo = _v(args, 0, VP), _v(args, 1, I64), _v(args, 2, I32), _v(args, 3, I32), \
+        _v(args, 4, I32), _a(args, 5, JOut)
+    ntri = n * (n + 1) // 2
+    assert 1 <= nd <= 64 and ldc >= nd and acc in (0, 1) and grid[0] * 256 >= ntri
+    return [(C, C + 8 * ((ntri - 1) * ldc + nd), "C")] + [(jo.p[s], jo.p[s] + 8 * n * n, "J") for s in range(nd)]
+
+
 def dec_axpy(grid, args):
     y, x, cnt = _v(args, 0, VP), _v(args, 1, VP), _v(args, 2, I64)
     return [(y, y + 8 * cnt, "y"), (x, x + 8 * cnt, "x")]
@@ -658,6 +695,51 @@ def ex_jstream_sym(grid, args, name):
             dv(o.p[j], n * n)[:] += sym
         else:
             dv(o.p[j], n * n)[:] = sym
+
+
+def _tri_columns(L, n, ps, P0, np_, pk):
+    """A[t][kk] = L^{P0+kk}[mu][nu] over the upper-triangle positions t."""
+    ntri = n * (n + 1) // 2
+    F = dv(L, (P0 + np_) * ps).reshape(P0 + np_, ps)[P0:]
+    if pk:
+        return F.T.copy()
+    iu = np.triu_indices(n)
+    return F[:, iu[0] * n + iu[1]].T.copy()
+
+
+def ex_expo_tri(grid, args, name):
+    pk, L, n, ps, P0, np_, ntri = _tri_args(args, name)
+    nsc, e = _v(args, 5, I32), _v(args, 6, VP)
+    A = np.abs(_tri_columns(L, n, ps, P0, np_, pk))
+    ev = uv(e, ntri * nsc, np.int32).reshape(ntri, nsc)
+    for z in range(nsc):
+        ev[:, z] = _expo_of(A[:, z * SUPER:(z + 1) * SUPER].max(axis=1))
+
+
+def ex_slice_tri(grid, args, name):
+    pk, L, n, ps, P0, np_, ntri = _tri_args(args, name)
+    Kpad, nsc, e, out = _v(args, 5, I32), _v(args, 6, I32), _v(args, 7, VP), _v(args, 8, VP)
+    A = _tri_columns(L, n, ps, P0, np_, pk)
+    ev = uv(e, ntri * nsc, np.int32).reshape(ntri, nsc)
+    E = ev[:, np.arange(np_) // SUPER]
+    planes = _digits_bf16(A, E, 6)
+    o = uv(out, 6 * ntri * Kpad, np.uint16).reshape(6, ntri, Kpad)
+    o[:] = 0
+    for j in range(6):
+        o[j, :, :np_] = planes[j]
+
+
+def ex_j_tri_add(grid, args):
+    C, ldc, n, nd, acc, jo = _v(args, 0, VP), _v(args, 1, I64), _v(args, 2, I32), _v(args, 3, I32), \
+        _v(args, 4, I32), _a(args, 5, JOut)
+    ntri = n * (n + 1) // 2
+    Cm = dv(C, ntri * ldc).reshape(ntri, ldc)
+    iu = np.triu_indices(n)
+    for s in range(nd):
+        J = dv(jo.p[s], n * n).reshape(n, n)
+        v = Cm[:, s] + (J[iu] if acc else 0.0)
+        J[iu] = v
+        J[iu[1], iu[0]] = v
 
 
 def ex_axpy(grid, args):
@@ -994,6 +1076,7 @@ def ex_sym_dl(grid, args):
 EXECUTORS = [
     ("dgemm_nt_kernel", ex_dgemm), ("pack_cols_kernel", ex_pack_cols), ("frob_stream_kernel", ex_frob),
     ("gamma_panel_kernel", ex_gamma_panel), ("jstream_sym_kernel", ex_jstream_sym), ("axpy_kernel", ex_axpy),
+    ("expo_tri_kernel", ex_expo_tri), ("slice_tri_kernel", ex_slice_tri), ("j_tri_add_kernel", ex_j_tri_add),
     ("sum_parts_kernel", ex_sum_parts), ("pair_dot_kernel", ex_pair_dot), ("laplace_scale_kernel", ex_laplace_scale),
     ("weighted_sum_kernel", ex_weighted_sum), ("unpack_sym_kernel", ex_unpack_sym), ("gterms_kernel", ex_gterms),
     ("symmetrize_kernel", ex_symmetrize), ("fold_sym_split_kernel", ex_fold), ("fold_sym_kernel", ex_fold),
@@ -1008,6 +1091,7 @@ EXECUTORS = [
 ]
 
 DECODERS = [
+    ("expo_tri_kernel", dec_expo_tri), ("slice_tri_kernel", dec_slice_tri), ("j_tri_add_kernel", dec_j_tri_add),
     ("pack_group_kernel", dec_pack_group), ("int_fill_kernel", dec_int_fill), ("panel_colmax_kernel", dec_panel_colmax),
     ("expo_group_kernel", dec_expo_group), ("slice_group_kernel", dec_slice_group),
     ("reduce_group_kernel", dec_reduce_group),
@@ -1052,7 +1136,8 @@ def on_launch(name, grid, block, args):
     for key, fn in DECODERS:
         if key in name:
             try:
-                ranges = (fn(g, args, name) if fn in (dec_jstream_sym, dec_slice, dec_slice4, dec_slice_group)
+                ranges = (fn(g, args, name) if fn in (dec_jstream_sym, dec_slice, dec_slice4, dec_slice_group,
+                                                      dec_expo_tri, dec_slice_tri)
                           else fn(g, args))
             except AssertionError as e:
                 violations.append(f"{key}: inconsistent arguments {e}")
@@ -1066,7 +1151,8 @@ def on_launch(name, grid, block, args):
             if EXEC[0] and not bad:
                 for ekey, ex in EXECUTORS:
                     if ekey in name:
-                        ex(g, args, name) if ex in (ex_jstream_sym, ex_slice, ex_slice_group) else ex(g, args)
+                        ex(g, args, name) if ex in (ex_jstream_sym, ex_slice, ex_slice_group, ex_expo_tri,
+                                                    ex_slice_tri) else ex(g, args)
                         break
             return
     undecoded.add(name)

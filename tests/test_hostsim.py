@@ -232,11 +232,12 @@ def test_grouped_schedule_collapses_gemm_launches(full_records):
     """Launch collapse, counted on the CPU: the tuned multi-state build issues
     one sliced-GEMM launch for the panels of all densities and one for all
     eight rank updates; the per-density schedule (two aux chunks at this size)
-    issues a panel launch and eight rank-update launches per chunk."""
+    issues a panel launch, eight rank-update launches and the J
+    back-contraction's launch per chunk."""
     def gemms(name):
         return sum("ozgemm_kernel" in k[0] for k in full_records[name]["launches"])
     assert gemms("full_multi_state_tuned") == 2
-    assert gemms("full_multi_state_default") == 2 * (1 + 8)
+    assert gemms("full_multi_state_default") == 2 * (1 + 8 + 1)
     assert sum("jstream_sym_kernel" in k[0] for k in full_records["full_multi_state_tuned"]["launches"]) == 1
 
 
