@@ -214,21 +214,54 @@ struct DensTab {
     int k[kMaxDens];
 };
 
-__global__ void __launch_bounds__(256)
-gamma_panel_kernel(const double *T, int n, long long ctot, DensTab tab,
-                   double *gamma, int ldg, int P0) {
-    __shared__ double red[8];
-    const int p = blockIdx.x, s = blockIdx.y;
-    const int k = tab.k[s], off = tab.offX[s];
-    const double *Tp = T + (long long)p * n * ctot;
-    const double *Ys = tab.Y[s];
+__device__ __forceinline__ double gamma_dot(const double *Tp, int n, long long ctot, const double *Ys, int off, int k,
+                                            double *red) {
     double acc = 0.0;
     for (int e = threadIdx.x; e < n * k; e += 256) {
         int sig = e / k, i = e - sig * k;
         acc = fma(Tp[(long long)sig * ctot + off + i], Ys[e], acc);
     }
-    double t = block_sum_256(acc, red);
+    return block_sum_256(acc, red);
+}
+
+__global__ void __launch_bounds__(256)
+gamma_panel_kernel(const double *T, int n, long long ctot, DensTab tab,
+                   double *gamma, int ldg, int P0) {
+    __shared__ double red[8];
+    const int p = blockIdx.x, s = blockIdx.y;
+    const double t = gamma_dot(T + (long long)p * n * ctot, n, ctot, tab.Y[s], tab.offX[s], tab.k[s], red);
     if (threadIdx.x == 0) gamma[(long long)s * ldg + P0 + p] = t;
+}
+
+// The same for the chunks of many molecules (a batched build's wave) in one
+// launch: job i covers blocks b0 .. b0 + np nd - 1 (block (p, s) at
+// b0 + s np + p); the densities of all jobs in one table (job i's at d0 ..).
+struct GammaJob {
+    const double *T;
+    double *gamma;
+    long long ldT;
+    int n, np, nd, P0, ldg, d0, b0;
+};
+constexpr int MAXGJOB = 64, MAXGDENS = 1024;
+struct GammaGroup {
+    GammaJob j[MAXGJOB];
+    const double *Y[MAXGDENS];
+    int offX[MAXGDENS], k[MAXGDENS];
+    int njob;
+};
+__global__ void __launch_bounds__(256) gamma_group_kernel(const __grid_constant__ GammaGroup g) {
+    __shared__ double red[8];
+    int lo = 0, hi = g.njob - 1;
+    while (lo < hi) {   // the last job whose first block is <= blockIdx.x
+        const int mid = (lo + hi + 1) >> 1;
+        if (g.j[mid].b0 <= static_cast<int>(blockIdx.x)) lo = mid;
+        else hi = mid - 1;
+    }
+    const GammaJob &jb = g.j[lo];
+    const int lb = static_cast<int>(blockIdx.x) - jb.b0, s = lb / jb.np, p = lb - s * jb.np;
+    const int d = jb.d0 + s;
+    const double t = gamma_dot(jb.T + (long long)p * jb.n * jb.ldT, jb.n, jb.ldT, g.Y[d], g.offX[d], g.k[d], red);
+    if (threadIdx.x == 0) jb.gamma[(long long)s * jb.ldg + jb.P0 + p] = t;
 }
 
 // Out_s[e] = sum_P g[s][P] L^P[e]: one pass over L for up to 8 densities.
@@ -501,6 +534,52 @@ jk_status fp64_gemm_nt(jk_ctx *h, int M, int N, int K, const double *A, long lon
 
 jk_status split_pack_z(jk_ctx *h, const Problem &pb, double *Z, cudaStream_t st) {
     return pack_z(h, pb, Z, st);
+}
+
+static_assert(sizeof(GammaGroup) <= 32764, "grouped launches fit the kernel parameter space");
+
+// gamma of every listed panel chunk (fp64_gamma_panel's work) in grouped
+// launches of up to MAXGJOB chunks and MAXGDENS densities.
+jk_status fp64_gamma_group(jk_ctx *h, const std::vector<GammaItem> &items, cudaStream_t st) {
+    static thread_local GammaGroup grp;
+    size_t i0 = 0;
+    while (i0 < items.size()) {
+        int nj = 0, nden = 0;
+        long long blocks = 0;
+        while (i0 + nj < items.size() && nj < MAXGJOB && nden + items[i0 + nj].pb->nd <= MAXGDENS) {
+            const GammaItem &it = items[i0 + nj];
+            const Problem &pb = *it.pb;
+            GammaJob &j = grp.j[nj];
+            j.T = it.T;
+            j.gamma = it.gamma;
+            j.ldT = it.ldT;
+            j.n = pb.n;
+            j.np = it.np;
+            j.nd = pb.nd;
+            j.P0 = it.P0;
+            j.ldg = pb.naux;
+            j.d0 = nden;
+            j.b0 = static_cast<int>(blocks);
+            for (int s = 0; s < pb.nd; s++) {
+                grp.Y[nden + s] = pb.sym[s] ? pb.X[s] : pb.Y[s];
+                grp.offX[nden + s] = pb.offX[s];
+                grp.k[nden + s] = pb.k[s];
+            }
+            nden += pb.nd;
+            blocks += static_cast<long long>(it.np) * pb.nd;
+            if (blocks > 0x7fffffffLL) return set_error(h, JK_ERR_SHAPE, "too many gamma blocks");
+            nj++;
+        }
+        if (nj == 0) return set_error(h, JK_ERR_SHAPE, "a molecule with more densities than one gamma launch takes");
+        grp.njob = nj;
+        {
+            LaunchScope ls(h, KK_GAMMA, st);
+            gamma_group_kernel<<<static_cast<unsigned>(blocks), 256, 0, st>>>(grp);
+        }
+        JK_LAUNCH_CHECK(h);
+        i0 += nj;
+    }
+    return JK_OK;
 }
 
 // gamma[s][P0 + p] = sum_{sig,i} T^p[sig][offX_s + i] Y_s[sig][i] for p < np.

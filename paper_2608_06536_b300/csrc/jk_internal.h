@@ -214,6 +214,16 @@ jk_status fp64_pair_contract(jk_ctx *h, const Problem &left, const double *ZL, c
 jk_status split_pack_z(jk_ctx *h, const Problem &pb, double *Z, cudaStream_t st);
 // Z[m] = the packed density columns of molecule m, for nmol molecules (grouped launches).
 jk_status pack_z_multi(jk_ctx *h, int nmol, const Problem *pbs, double *const *Z, cudaStream_t st);
+// gamma[s][P0 + p] = sum_{sig,i} T^p[sig][offX_s + i] Y_s[sig][i], p < np, for
+// panel chunks of several molecules (grouped launches).
+struct GammaItem {
+    const Problem *pb;
+    const double *T;
+    long long ldT;
+    int np, P0;
+    double *gamma;
+};
+jk_status fp64_gamma_group(jk_ctx *h, const std::vector<GammaItem> &items, cudaStream_t st);
 
 // ---- Laplace (LT-AO) builds -------------------------------------------------
 // out[k][mu][p] = C[mu][p] exp(sign alpha[k] eps[p] / 2), k < nq <= kMaxDens

@@ -553,14 +553,14 @@ __device__ __forceinline__ long long tri_offset(int n, long long t) {
     return static_cast<long long>(mu) * n + nu;
 }
 
-// e[t * nsc + z] = exponent of max |A[t][kk]| over kk in super-chunk z
-// (blockIdx.y = z).  pstride: doubles between consecutive L^P.
+// e[t * nsc + z] = exponent of max |A[t][kk]| over kk in super-chunk z, for
+// the 256 rows t = 256 bx + thread.  pstride: doubles between consecutive L^P.
 template <bool PK>
-__global__ void __launch_bounds__(256) expo_tri_kernel(const double *L, int n, long long pstride, int P0, int np,
-                                                       int nsc, int *e) {
-    const long long t = blockIdx.x * 256LL + threadIdx.x;
+__device__ __forceinline__ void expo_tri_body(const double *L, int n, long long pstride, int P0, int np, int nsc,
+                                              int *e, long long bx, int z) {
+    const long long t = bx * 256 + threadIdx.x;
     if (t >= packed::tri_count(n)) return;
-    const int z = blockIdx.y, k0 = z * SUPER, k1 = min(np, k0 + SUPER);
+    const int k0 = z * SUPER, k1 = min(np, k0 + SUPER);
     const double *p = L + static_cast<long long>(P0 + k0) * pstride + tri_offset<PK>(n, t);
     constexpr unsigned long long kAbs = 0x7FFFFFFFFFFFFFFFull;
     unsigned long long mx = 0;
@@ -580,26 +580,35 @@ __global__ void __launch_bounds__(256) expo_tri_kernel(const double *L, int n, l
     e[t * nsc + z] = exponent_of_max(mx);
 }
 
-// The six digit planes of A: out[j][t][kk] (Kpad columns, zero for kk >= np).
-// Block (bx, by) takes rows t0 = 64 bx .. t0 + 63 and kk0 = 64 by .. kk0 + 63.
 template <bool PK>
-__global__ void __launch_bounds__(256) slice_tri_kernel(const double *L, int n, long long pstride, int P0, int np,
-                                                        int Kpad, int nsc, const int *e, uint2 *out,
-                                                        long long sstride4) {
+__global__ void __launch_bounds__(256) expo_tri_kernel(const double *L, int n, long long pstride, int P0, int np,
+                                                       int nsc, int *e) {
+    expo_tri_body<PK>(L, n, pstride, P0, np, nsc, e, blockIdx.x, blockIdx.y);
+}
+
+// The six digit planes of A: out[j][t][kk] (Kpad columns, zero for kk >= np),
+// for rows t0 = 64 bx .. t0 + 63 and kk0 = 64 by .. kk0 + 63.
+struct TriTile {
+    double v[TRI_TILE][TRI_TILE + 1];   // [kk - kk0][t - t0]
+    long long off[TRI_TILE];
+};
+
+template <bool PK>
+__device__ __forceinline__ void slice_tri_body(TriTile &sm, const double *L, int n, long long pstride, int P0, int np,
+                                               int Kpad, int nsc, const int *e, uint2 *out, long long sstride4,
+                                               long long bx, int by) {
     constexpr int S = 6;
-    __shared__ double tile[TRI_TILE][TRI_TILE + 1];   // [kk - kk0][t - t0]
-    __shared__ long long soff[TRI_TILE];
     const long long ntri = packed::tri_count(n);
-    const long long t0 = blockIdx.x * static_cast<long long>(TRI_TILE);
-    const int kk0 = blockIdx.y * TRI_TILE;
+    const long long t0 = bx * TRI_TILE;
+    const int kk0 = by * TRI_TILE;
     if (threadIdx.x < TRI_TILE) {
         const long long t = t0 + threadIdx.x;
-        soff[threadIdx.x] = t < ntri ? tri_offset<PK>(n, t) : -1;
+        sm.off[threadIdx.x] = t < ntri ? tri_offset<PK>(n, t) : -1;
     }
     __syncthreads();
     {
         const int tc = threadIdx.x & (TRI_TILE - 1), kr0 = threadIdx.x >> 6;   // 4 rows kk per pass
-        const long long off = soff[tc];
+        const long long off = sm.off[tc];
         double v[TRI_TILE / 4];
 #pragma unroll
         for (int i = 0; i < TRI_TILE / 4; i++) {
@@ -607,7 +616,7 @@ __global__ void __launch_bounds__(256) slice_tri_kernel(const double *L, int n, 
             v[i] = kk < np && off >= 0 ? L[static_cast<long long>(P0 + kk) * pstride + off] : 0.0;
         }
 #pragma unroll
-        for (int i = 0; i < TRI_TILE / 4; i++) tile[kr0 + 4 * i][tc] = v[i];
+        for (int i = 0; i < TRI_TILE / 4; i++) sm.v[kr0 + 4 * i][tc] = v[i];
     }
     __syncthreads();
 #pragma unroll
@@ -620,7 +629,7 @@ __global__ void __launch_bounds__(256) slice_tri_kernel(const double *L, int n, 
         if (kk < np) {
             const int er = e[t * nsc + kk / SUPER];
 #pragma unroll
-            for (int u = 0; u < 4; u++) digits::biased_words<S>(to_fixed(tile[4 * g + u][tr], er, 8 * S), glo[u], ghi[u]);
+            for (int u = 0; u < 4; u++) digits::biased_words<S>(to_fixed(sm.v[4 * g + u][tr], er, 8 * S), glo[u], ghi[u]);
         } else {
 #pragma unroll
             for (int u = 0; u < 4; u++) digits::biased_words<S>(0, glo[u], ghi[u]);
@@ -634,6 +643,60 @@ __global__ void __launch_bounds__(256) slice_tri_kernel(const double *L, int n, 
             out[j * sstride4 + o] = w;
         }
     }
+}
+
+template <bool PK>
+__global__ void __launch_bounds__(256) slice_tri_kernel(const double *L, int n, long long pstride, int P0, int np,
+                                                        int Kpad, int nsc, const int *e, uint2 *out,
+                                                        long long sstride4) {
+    __shared__ TriTile sm;
+    slice_tri_body<PK>(sm, L, n, pstride, P0, np, Kpad, nsc, e, out, sstride4, blockIdx.x, blockIdx.y);
+}
+
+// The same for many operands (the molecules of a batched build's wave) in one
+// exponent and one slicer launch, the jobs in the parameter space; block b
+// belongs to the job whose block range holds it.
+struct TriJob {
+    const double *L;
+    long long pstride;
+    int *e;
+    uint2 *out;
+    long long ss4;
+    int n, P0, np, Kpad, nsc, pk;
+    int ebx, sbx, sby;   // exponent blocks per super-chunk; slicer blocks along t and kk
+    int eb0, sb0;        // first block of this job in the exponent and the slicer launch
+};
+constexpr int MAXTRI = 64;
+struct TriGroup {
+    TriJob j[MAXTRI];
+    int njob;
+};
+
+__device__ __forceinline__ int tri_job_of_block(const TriGroup &g, int b, bool expo) {
+    int lo = 0, hi = g.njob - 1;
+    while (lo < hi) {   // the last job whose first block is <= b
+        const int mid = (lo + hi + 1) >> 1;
+        if ((expo ? g.j[mid].eb0 : g.j[mid].sb0) <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(256) expo_tri_group_kernel(const __grid_constant__ TriGroup g) {
+    const TriJob &jb = g.j[tri_job_of_block(g, blockIdx.x, true)];
+    const int lb = static_cast<int>(blockIdx.x) - jb.eb0, z = lb / jb.ebx, bx = lb - z * jb.ebx;
+    if (jb.pk) expo_tri_body<true>(jb.L, jb.n, jb.pstride, jb.P0, jb.np, jb.nsc, jb.e, bx, z);
+    else expo_tri_body<false>(jb.L, jb.n, jb.pstride, jb.P0, jb.np, jb.nsc, jb.e, bx, z);
+}
+
+__global__ void __launch_bounds__(256) slice_tri_group_kernel(const __grid_constant__ TriGroup g) {
+    __shared__ TriTile sm;
+    const TriJob &jb = g.j[tri_job_of_block(g, blockIdx.x, false)];
+    const int lb = static_cast<int>(blockIdx.x) - jb.sb0, by = lb / jb.sbx, bx = lb - by * jb.sbx;
+    if (jb.pk)
+        slice_tri_body<true>(sm, jb.L, jb.n, jb.pstride, jb.P0, jb.np, jb.Kpad, jb.nsc, jb.e, jb.out, jb.ss4, bx, by);
+    else
+        slice_tri_body<false>(sm, jb.L, jb.n, jb.pstride, jb.P0, jb.np, jb.Kpad, jb.nsc, jb.e, jb.out, jb.ss4, bx, by);
 }
 
 }  // namespace oz

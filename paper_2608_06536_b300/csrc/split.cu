@@ -83,6 +83,43 @@ __global__ void __launch_bounds__(256) j_tri_add_kernel(const double *C, long lo
     }
 }
 
+// The same for many molecules in one launch (a batched build's wave): thread
+// e0 + t of job i takes position t of job i's triangle; the J pointers of all
+// jobs sit in one table (job i's densities at ptr[p0 ..]).
+struct JAddJob {
+    const double *C;
+    long long ldc, e0;
+    int n, nd, acc, p0;
+};
+constexpr int MAXJADD = 64, MAXJPTR = 1024;
+struct JAddGroup {
+    JAddJob j[MAXJADD];
+    double *ptr[MAXJPTR];
+    int njob;
+};
+__global__ void __launch_bounds__(256) j_tri_add_group_kernel(const __grid_constant__ JAddGroup g, long long total) {
+    const long long x = blockIdx.x * 256LL + threadIdx.x;
+    if (x >= total) return;
+    int lo = 0, hi = g.njob - 1;
+    while (lo < hi) {   // the last job whose first element is <= x
+        const int mid = (lo + hi + 1) >> 1;
+        if (g.j[mid].e0 <= x) lo = mid;
+        else hi = mid - 1;
+    }
+    const JAddJob &jb = g.j[lo];
+    const long long t = x - jb.e0;
+    const int n = jb.n;
+    int mu, nu;
+    packed::tri_row_col(n, t, &mu, &nu);
+    const long long e = static_cast<long long>(mu) * n + nu, em = static_cast<long long>(nu) * n + mu;
+    for (int s = 0; s < jb.nd; s++) {
+        double *J = g.ptr[jb.p0 + s];
+        const double v = jb.acc ? J[e] + jb.C[t * jb.ldc + s] : jb.C[t * jb.ldc + s];
+        J[e] = v;
+        if (mu != nu) J[em] = v;
+    }
+}
+
 }  // namespace oz
 
 // ---------------------------------------------------------------------------
@@ -439,6 +476,117 @@ static jk_status split_j_chunk(jk_ctx *h, const Problem &pb, const double *gamma
     return JK_OK;
 }
 
+// ---- the J back-contraction in grouped launches (batched builds) -------------
+static_assert(sizeof(oz::TriGroup) <= 32764 && sizeof(oz::JAddGroup) + 8 <= 32764,
+              "grouped launches fit the kernel parameter space");
+
+struct TriBatch {
+    std::vector<oz::TriJob> jobs;
+};
+
+// One operand A of split_j_chunk as a job of the grouped transposed slicing.
+static void tri_add(TriBatch &tb, const Problem &pb, int P0, int np, Sliced &A) {
+    const int n = pb.n;
+    const long long nt = tri_rows(n);
+    A.rows = static_cast<int>(nt);
+    A.K = np;
+    A.Kpad = kpad_of(np);
+    A.rpe = 1;
+    oz::TriJob j;
+    std::memset(&j, 0, sizeof j);
+    j.L = pb.L;
+    j.pstride = pb.packed ? nt : static_cast<long long>(n) * n;
+    j.e = A.e;
+    j.out = reinterpret_cast<uint2 *>(A.s);
+    j.ss4 = nt * A.Kpad / 4;
+    j.n = n;
+    j.P0 = P0;
+    j.np = np;
+    j.Kpad = A.Kpad;
+    j.nsc = nsuper_of(np);
+    j.pk = pb.packed ? 1 : 0;
+    j.ebx = static_cast<int>((nt + 255) / 256);
+    j.sbx = static_cast<int>((nt + oz::TRI_TILE - 1) / oz::TRI_TILE);
+    j.sby = (A.Kpad + oz::TRI_TILE - 1) / oz::TRI_TILE;
+    tb.jobs.push_back(j);
+}
+
+static jk_status tri_flush(jk_ctx *h, TriBatch &tb, cudaStream_t st) {
+    static thread_local oz::TriGroup grp;
+    for (size_t i0 = 0; i0 < tb.jobs.size(); i0 += oz::MAXTRI) {
+        const int nj = static_cast<int>(std::min<size_t>(oz::MAXTRI, tb.jobs.size() - i0));
+        long long eb = 0, sbk = 0;
+        for (int i = 0; i < nj; i++) {
+            oz::TriJob &j = grp.j[i];
+            j = tb.jobs[i0 + i];
+            j.eb0 = static_cast<int>(eb);
+            j.sb0 = static_cast<int>(sbk);
+            eb += static_cast<long long>(j.ebx) * j.nsc;
+            sbk += static_cast<long long>(j.sbx) * j.sby;
+            if (eb > 0x7fffffffLL || sbk > 0x7fffffffLL) return set_error(h, JK_ERR_SHAPE, "too many J slicer blocks");
+        }
+        grp.njob = nj;
+        {
+            LaunchScope ls(h, KK_EXPO, st);
+            oz::expo_tri_group_kernel<<<static_cast<unsigned>(eb), 256, 0, st>>>(grp);
+        }
+        JK_LAUNCH_CHECK(h);
+        {
+            LaunchScope ls(h, KK_SLICE, st);
+            oz::slice_tri_group_kernel<<<static_cast<unsigned>(sbk), 256, 0, st>>>(grp);
+        }
+        JK_LAUNCH_CHECK(h);
+    }
+    tb.jobs.clear();
+    return JK_OK;
+}
+
+struct JAddBatch {
+    std::vector<oz::JAddJob> jobs;
+    std::vector<double *const *> outs;
+};
+
+static void jadd_add(JAddBatch &ab, const Problem &pb, const JBufs &jb, bool acc) {
+    oz::JAddJob j;
+    std::memset(&j, 0, sizeof j);
+    j.C = jb.C;
+    j.ldc = jb.ldc;
+    j.n = pb.n;
+    j.nd = pb.nd;
+    j.acc = acc ? 1 : 0;
+    ab.jobs.push_back(j);
+    ab.outs.push_back(pb.J);
+}
+
+static jk_status jadd_flush(jk_ctx *h, JAddBatch &ab, cudaStream_t st) {
+    static thread_local oz::JAddGroup grp;
+    size_t i0 = 0;
+    while (i0 < ab.jobs.size()) {
+        int nj = 0, np = 0;
+        long long tot = 0;
+        while (i0 + nj < ab.jobs.size() && nj < oz::MAXJADD && np + ab.jobs[i0 + nj].nd <= oz::MAXJPTR) {
+            oz::JAddJob &j = grp.j[nj];
+            j = ab.jobs[i0 + nj];
+            j.e0 = tot;
+            j.p0 = np;
+            for (int s = 0; s < j.nd; s++) grp.ptr[np + s] = ab.outs[i0 + nj][s];
+            np += j.nd;
+            tot += tri_rows(j.n);
+            nj++;
+        }
+        grp.njob = nj;
+        {
+            LaunchScope ls(h, KK_MISC, st);
+            oz::j_tri_add_group_kernel<<<static_cast<unsigned>((tot + 255) / 256), 256, 0, st>>>(grp, tot);
+        }
+        JK_LAUNCH_CHECK(h);
+        i0 += nj;
+    }
+    ab.jobs.clear();
+    ab.outs.clear();
+    return JK_OK;
+}
+
 // ---- grouped slicing and reductions (batched builds) -------------------------
 static_assert(sizeof(oz::SliceGroup) <= 32764 && sizeof(oz::ReduceGroup) + 8 <= 32764,
               "grouped launches fit the kernel parameter space");
@@ -721,13 +869,15 @@ jk_status mirror_sym_blocks(jk_ctx *h, double *K, int n, cudaStream_t st) {
 // The split build
 // ---------------------------------------------------------------------------
 
-// P-chunk so that the per-chunk workspace stays below ~12 GB.
-static int split_pchunk(const Problem &pb) {
+// P-chunk so that the per-chunk workspace stays below ~12 GB (a single
+// molecule's build) or ~6 GB (a work item of a batch of several molecules,
+// so that several fit one wave of the batched arena).
+static int split_pchunk(const Problem &pb, bool batched = false) {
     const size_t n = pb.n;
     size_t per = n * n * (6 * 2) + n * pb.ctot * 8 + n * pb.ctot * (6 * 2);
     if (pb.packed) per += n * n * 8;               // the expanded factor chunk
     per += n * (n + 1) / 2 * (6 * 2);              // the transposed chunk's slices (J)
-    size_t budget = static_cast<size_t>(12) << 30;
+    size_t budget = static_cast<size_t>(batched ? 6 : 12) << 30;
     size_t pc = per ? budget / per : 1;
     if (pc < 1) pc = 1;
     if (pb.aux_chunk > 0) pc = pb.aux_chunk;       // explicit or tuned chunk
@@ -781,14 +931,13 @@ jk_status split_pack_z(jk_ctx *h, const Problem &pb, double *Z, cudaStream_t st)
 jk_status fp64_unpack_sym(jk_ctx *h, const double *packed, int n, long long np, double *full, cudaStream_t st);
 jk_status fp64_gamma_panel(jk_ctx *h, const Problem &pb, const double *T, long long ldT, int np, double *gamma,
                            int P0, cudaStream_t st);
-jk_status fp64_jstream(jk_ctx *h, const Problem &pb, const double *gamma, cudaStream_t st);
 
-// The FP64 J back-contraction of a batched build needs only the factor and
-// gamma, and runs on the FP64 pipe: it is forked onto a second stream as soon
-// as a molecule's gamma is complete and overlaps the rank updates on the
-// tensor pipe (join at the end of the build, so the call stays ordered on the
-// caller's stream).  A single molecule's build forms J on the tensor cores
-// instead (split_j_chunk).
+// The FP64 J of a dense-density build (its metric dots and back-contraction)
+// needs only the factor and the densities, and runs on the FP64 pipe: it is
+// forked onto a second stream and overlaps the K products on the tensor pipe
+// (join at the end of the build, so the call stays ordered on the caller's
+// stream).  The factored builds form J on the tensor cores instead
+// (split_j_chunk and its grouped form).
 static jk_status fork_jstream(jk_ctx *h, cudaStream_t st) {
     if (!h->aux_stream) {
         JK_CUDA_TRY(h, cudaStreamCreateWithFlags(&h->aux_stream, cudaStreamNonBlocking));
@@ -1242,6 +1391,7 @@ struct ItemBufs {
     double *T = nullptr, *tmp = nullptr;
     long long *P = nullptr;
     double *Lx = nullptr;     // packed factor: the chunk expanded to [np][n][n]
+    JBufs jb;                 // the chunk's J back-contraction
 };
 
 size_t item_bytes(const Problem &pb, int pc) {
@@ -1254,6 +1404,7 @@ size_t item_bytes(const Problem &pb, int pc) {
     b += align_up(partial_count(pb, pc) * 8 + 8);
     b += align_up(static_cast<size_t>(pb.nd) * n * n * 8);   // per-density tmp for chunk accumulation
     if (pb.packed) b += align_up(static_cast<size_t>(pc) * n * n * 8);   // expanded factor chunk
+    b += jbufs_bytes(pb, pc);                                              // J on the tensor cores
     return b + 16 * kArenaAlign;
 }
 
@@ -1274,6 +1425,7 @@ bool take_item(Arena &ar, const Problem &pb, int pc, ItemBufs &it) {
     it.P = ar.take<long long>(partial_count(pb, pc) + 1);
     it.tmp = ar.take<double>(static_cast<size_t>(pb.nd) * n * n);
     if (pb.packed) it.Lx = ar.take<double>(static_cast<size_t>(pc) * n * n);
+    ok = ok && (!pb.wantJ || take_jbufs(ar, pb, pc, it.jb));
     return ok && it.P && it.tmp && (!pb.packed || it.Lx);
 }
 
@@ -1284,14 +1436,14 @@ size_t split_batched_workspace(int nmol, const Problem *pbs) {
     for (int m = 0; m < nmol; m++) {
         const Problem &pb = pbs[m];
         mols += mol_bytes(pb);
-        const int pc = split_pchunk(pb);
+        const int pc = split_pchunk(pb, nmol > 1);
         const size_t ib = item_bytes(pb, pc);
         maxitem = std::max(maxitem, ib);
         items += ib * ((pb.naux + pc - 1) / pc);
     }
     // enough for every molecule's persistent buffers and at least the largest
-    // work item; more (up to everything, capped at 24 GB) lets waves hold more items
-    const size_t cap = static_cast<size_t>(24) << 30;
+    // work item; more (up to everything, capped at 40 GB) lets waves hold more items
+    const size_t cap = static_cast<size_t>(40) << 30;
     return mols + std::max(maxitem, std::min(items, cap));
 }
 
@@ -1305,7 +1457,7 @@ jk_status split_batched(jk_ctx *h, int nmol, const Problem *pbs, cudaStream_t st
         mb[m].gamma = ar.take<double>(static_cast<size_t>(pb.nd) * pb.naux);
         if (!mb[m].Z || !mb[m].gamma || !take_sliced(ar, pb.ctot, pb.n, 1, mb[m].Zs))
             return set_error(h, JK_ERR_OOM, "workspace too small for the batched build");
-        mb[m].pc = split_pchunk(pb);
+        mb[m].pc = split_pchunk(pb, nmol > 1);
     }
     {
         // every molecule's packed densities and their slices, in grouped launches
@@ -1321,11 +1473,21 @@ jk_status split_batched(jk_ctx *h, int nmol, const Problem *pbs, cudaStream_t st
         JK_TRY(slice_flush(h, zb, st));
     }
     const size_t persist = ar.off;
-    bool forked = false;   // J streams running on the second stream
-    // Work items (molecule, aux chunk) in order.
+    // Work items (molecule, aux chunk), chunk-major: the first chunk of every
+    // molecule, then the second ..., so that a wave (at most one chunk per
+    // molecule, as many as the arena holds) takes many molecules at once and
+    // each molecule's chunks still come in order.
     std::vector<std::pair<int, int>> work;
-    for (int m = 0; m < nmol; m++)
-        for (int P0 = 0; P0 < pbs[m].naux; P0 += mb[m].pc) work.push_back({m, P0});
+    for (int c = 0;; c++) {
+        bool any = false;
+        for (int m = 0; m < nmol; m++) {
+            const long long P0 = static_cast<long long>(c) * mb[m].pc;
+            if (P0 >= pbs[m].naux) continue;
+            work.push_back({m, static_cast<int>(P0)});
+            any = true;
+        }
+        if (!any) break;
+    }
     size_t w0 = 0;
     while (w0 < work.size()) {
         ar.reset(persist);
@@ -1374,21 +1536,26 @@ jk_status split_batched(jk_ctx *h, int nmol, const Problem *pbs, cudaStream_t st
             JK_TRY(oz_problem(h, it.Ls, mb[it.mol].Zs, it.T, even_ld(pb.ctot), nullptr, probs.back()));
         }
         JK_TRY(oz_launch(h, probs, st));
-        // 3. gamma; the J streams of molecules whose last chunk this is go to the
-        // second stream; then the rank-update operands
-        bool fork = false;
-        for (auto &it : items) {
-            const Problem &pb = pbs[it.mol];
-            if (!pb.wantJ) continue;
-            JK_TRY(fp64_gamma_panel(h, pb, it.T, even_ld(pb.ctot), it.np, mb[it.mol].gamma, it.P0, st));
-            fork = fork || it.P0 + it.np >= pb.naux;
-        }
-        if (fork) {
-            JK_TRY(fork_jstream(h, st));
-            forked = true;
+        // 3. gamma, and the J back-contraction's operands of every chunk of the
+        // wave (the transposed factor chunks, gamma's chunks); then the
+        // rank-update operands
+        {
+            std::vector<GammaItem> gi;
             for (auto &it : items)
-                if (pbs[it.mol].wantJ && it.P0 + it.np >= pbs[it.mol].naux)
-                    JK_TRY(fp64_jstream(h, pbs[it.mol], mb[it.mol].gamma, h->aux_stream));
+                if (pbs[it.mol].wantJ)
+                    gi.push_back({&pbs[it.mol], it.T, even_ld(pbs[it.mol].ctot), it.np, it.P0, mb[it.mol].gamma});
+            JK_TRY(fp64_gamma_group(h, gi, st));
+            TriBatch tb;
+            SliceBatch gb;
+            for (auto &it : items) {
+                const Problem &pb = pbs[it.mol];
+                if (!pb.wantJ) continue;
+                tri_add(tb, pb, it.P0, it.np, it.jb.A);
+                oz::Src gsrc{mb[it.mol].gamma + it.P0, pb.naux, 0, 1, it.np};   // row s: gamma[s][P0 ..]
+                slice_add(gb, gsrc, pb.nd, it.np, 1, it.jb.G);
+            }
+            JK_TRY(tri_flush(h, tb, st));
+            JK_TRY(slice_flush(h, gb, st));
         }
         bool rowwise = grouped;   // exponents from whole panel rows when every molecule allows it
         for (auto &it : items)
@@ -1413,8 +1580,21 @@ jk_status split_batched(jk_ctx *h, int nmol, const Problem *pbs, cudaStream_t st
         }
         if (rowwise) JK_TRY(panel_flush(h, pbt, st));
         JK_TRY(slice_flush(h, sb, st, !rowwise));
-        // 4. every rank update of the wave: grouped persistent launches
+        // 4. every rank update and J back-contraction of the wave: grouped
+        // persistent launches
         probs.clear();
+        ReduceBatch rb;
+        JAddBatch ab;
+        for (auto &it : items) {
+            const Problem &pb = pbs[it.mol];
+            if (!pb.wantJ) continue;
+            const int nsc = nsuper_of(it.np);
+            probs.emplace_back();
+            JK_TRY(oz_problem(h, it.jb.A, it.jb.G, nsc == 1 ? it.jb.C : nullptr, it.jb.ldc,
+                              nsc == 1 ? nullptr : it.jb.P, probs.back()));
+            if (nsc > 1) reduce_add(rb, it.jb.P, nsc, it.jb.A, it.jb.G, it.jb.C, it.jb.ldc, false);
+            jadd_add(ab, pb, it.jb, it.P0 > 0);
+        }
         struct Red { const ItemBufs *it; int s; long long *P; double *tmp; };
         std::vector<Red> reds;
         for (auto &it : items) {
@@ -1450,8 +1630,7 @@ jk_status split_batched(jk_ctx *h, int nmol, const Problem *pbs, cudaStream_t st
             }
         }
         JK_TRY(oz_launch(h, probs, st));
-        // 5. reductions into K (the split-K ones in grouped launches)
-        ReduceBatch rb;
+        // 5. reductions into K and J's C (the split-K ones in grouped launches)
         for (auto &r : reds) {
             const Problem &pb = pbs[r.it->mol];
             const long long n2 = static_cast<long long>(pb.n) * pb.n;
@@ -1466,6 +1645,8 @@ jk_status split_batched(jk_ctx *h, int nmol, const Problem *pbs, cudaStream_t st
             }
         }
         JK_TRY(reduce_flush(h, rb, st));
+        // 6. J_s (+)= C of every chunk of the wave (chunks of a molecule in order)
+        JK_TRY(jadd_flush(h, ab, st));
         w0 = w1;
     }
     if (h->syrk)
@@ -1473,7 +1654,6 @@ jk_status split_batched(jk_ctx *h, int nmol, const Problem *pbs, cudaStream_t st
             if (pbs[m].wantK)
                 for (int s = 0; s < pbs[m].nd; s++)
                     if (pbs[m].sym[s]) JK_TRY(mirror_sym_blocks(h, pbs[m].K[s], pbs[m].n, st));
-    if (forked) JK_TRY(join_jstream(h, st));
     return JK_OK;
 }
 

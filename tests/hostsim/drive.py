@@ -147,6 +147,33 @@ class JOut(ct.Structure):
     _fields_ = [("p", VP * 64)]
 
 
+class GammaJob(ct.Structure):
+    _fields_ = [("T", VP), ("gamma", VP), ("ldT", I64), ("n", I32), ("np", I32), ("nd", I32), ("P0", I32),
+                ("ldg", I32), ("d0", I32), ("b0", I32)]
+
+
+class GammaGroup(ct.Structure):
+    _fields_ = [("j", GammaJob * 64), ("Y", VP * 1024), ("offX", I32 * 1024), ("k", I32 * 1024), ("njob", I32)]
+
+
+class TriJob(ct.Structure):
+    _fields_ = [("L", VP), ("pstride", I64), ("e", VP), ("out", VP), ("ss4", I64), ("n", I32), ("P0", I32),
+                ("np", I32), ("Kpad", I32), ("nsc", I32), ("pk", I32), ("ebx", I32), ("sbx", I32), ("sby", I32),
+                ("eb0", I32), ("sb0", I32)]
+
+
+class TriGroup(ct.Structure):
+    _fields_ = [("j", TriJob * 64), ("njob", I32)]
+
+
+class JAddJob(ct.Structure):
+    _fields_ = [("C", VP), ("ldc", I64), ("e0", I64), ("n", I32), ("nd", I32), ("acc", I32), ("p0", I32)]
+
+
+class JAddGroup(ct.Structure):
+    _fields_ = [("j", JAddJob * 64), ("ptr", VP * 1024), ("njob", I32)]
+
+
 class PairTab(ct.Structure):
     _fields_ = [("offA", I32 * MAXD), ("offB", I32 * MAXD), ("k", I32 * MAXD)]
 
@@ -392,6 +419,23 @@ def dec_gamma_panel(grid, args):
     return out
 
 
+def dec_gamma_group(grid, args):
+    g = GammaGroup.from_address(args[0])
+    jobs, nb = _group_jobs(g, "b0", lambda jb: jb.np * jb.nd)
+    assert grid[0] == nb, (grid, nb)
+    out, d = [], 0
+    for jb in jobs:
+        assert jb.d0 == d and jb.nd >= 1 and jb.np >= 1 and d + jb.nd <= 1024, (jb.d0, d)
+        out.append((jb.gamma, jb.gamma + 8 * ((jb.nd - 1) * jb.ldg + jb.P0 + jb.np), "gamma"))
+        for s in range(jb.nd):
+            k, off = g.k[d + s], g.offX[d + s]
+            assert off + k <= jb.ldT
+            out.append((jb.T, jb.T + 8 * ((jb.np - 1) * jb.n * jb.ldT + (jb.n - 1) * jb.ldT + off + k), "T"))
+            out.append((g.Y[d + s], g.Y[d + s] + 8 * jb.n * k, "Y"))
+        d += jb.nd
+    return out
+
+
 def _jstream_args(args):
     return (_v(args, 0, VP), _v(args, 1, I32), _v(args, 2, I32), _v(args, 3, I32), _v(args, 4, VP),
             _v(args, 5, I32), _v(args, 6, I32), _a(args, 7, OutTab))
@@ -430,6 +474,51 @@ def dec_slice_tri(grid, args, name):
     assert grid[0] * 64 >= ntri and grid[1] * 64 >= Kpad and out % 16 == 0, (grid, ntri, Kpad)
     return [(L + 8 * P0 * ps, L + 8 * (P0 + np_) * ps, "L"), (e, e + 4 * ntri * nsc, "e"),
             (out, out + 8 * 6 * ss4, "slices")]
+
+
+def _tri_job_check(jb):
+    ntri = jb.n * (jb.n + 1) // 2
+    assert jb.pstride == (ntri if jb.pk else jb.n * jb.n) and jb.P0 >= 0 and jb.np >= 1, (jb.pk, jb.pstride)
+    assert jb.Kpad == (jb.np + 15) // 16 * 16 and jb.nsc == (jb.np + SUPER - 1) // SUPER and jb.ss4 * 4 == ntri * jb.Kpad
+    assert jb.ebx * 256 >= ntri and jb.sbx * 64 >= ntri and jb.sby * 64 >= jb.Kpad and jb.out % 16 == 0
+    return ntri
+
+
+def dec_expo_tri_group(grid, args):
+    jobs, nb = _group_jobs(TriGroup.from_address(args[0]), "eb0", lambda jb: jb.ebx * jb.nsc)
+    assert grid[0] == nb, (grid, nb)
+    res = []
+    for jb in jobs:
+        ntri = _tri_job_check(jb)
+        res += [(jb.L + 8 * jb.P0 * jb.pstride, jb.L + 8 * (jb.P0 + jb.np) * jb.pstride, "L"),
+                (jb.e, jb.e + 4 * ntri * jb.nsc, "e")]
+    return res
+
+
+def dec_slice_tri_group(grid, args):
+    jobs, nb = _group_jobs(TriGroup.from_address(args[0]), "sb0", lambda jb: jb.sbx * jb.sby)
+    assert grid[0] == nb, (grid, nb)
+    res = []
+    for jb in jobs:
+        ntri = _tri_job_check(jb)
+        res += [(jb.L + 8 * jb.P0 * jb.pstride, jb.L + 8 * (jb.P0 + jb.np) * jb.pstride, "L"),
+                (jb.e, jb.e + 4 * ntri * jb.nsc, "e"), (jb.out, jb.out + 8 * 6 * jb.ss4, "slices")]
+    return res
+
+
+def dec_j_tri_add_group(grid, args):
+    g = JAddGroup.from_address(args[0])
+    total = _v(args, 1, I64)
+    jobs, nel = _group_jobs(g, "e0", lambda jb: jb.n * (jb.n + 1) // 2)
+    assert nel == total and grid[0] * 256 >= total, (grid, total, nel)
+    res, p = [], 0
+    for jb in jobs:
+        ntri = jb.n * (jb.n + 1) // 2
+        assert jb.p0 == p and 1 <= jb.nd and jb.ldc >= jb.nd and jb.acc in (0, 1) and p + jb.nd <= 1024
+        res.append((jb.C, jb.C + 8 * ((ntri - 1) * jb.ldc + jb.nd), "C"))
+        res += [(g.ptr[p + s], g.ptr[p + s] + 8 * jb.n * jb.n, "J") for s in range(jb.nd)]
+        p += jb.nd
+    return res
 
 
 def dec_j_tri_add(grid, args):
@@ -674,6 +763,19 @@ def ex_gamma_panel(grid, args):
         gv[s * ldg + P0:s * ldg + P0 + np_] = np.einsum("pik,ik->p", Tm[:, :, off:off + k], Ys)
 
 
+def ex_gamma_group(grid, args):
+    g = GammaGroup.from_address(args[0])
+    for i in range(g.njob):
+        jb = g.j[i]
+        n, ctot, np_ = jb.n, jb.ldT, jb.np
+        Tm = dv(jb.T, np_ * n * ctot).reshape(np_, n, ctot)
+        gv = dv(jb.gamma, (jb.nd - 1) * jb.ldg + jb.P0 + np_)
+        for s in range(jb.nd):
+            k, off = g.k[jb.d0 + s], g.offX[jb.d0 + s]
+            Ys = dv(g.Y[jb.d0 + s], n * k).reshape(n, k)
+            gv[s * jb.ldg + jb.P0:s * jb.ldg + jb.P0 + np_] = np.einsum("pik,ik->p", Tm[:, :, off:off + k], Ys)
+
+
 def ex_jstream_sym(grid, args, name):
     ns = int(name.split("ILi")[1].split("E")[0])
     L, n, P0, np_, g, ldg, acc, o = _jstream_args(args)
@@ -727,6 +829,57 @@ def ex_slice_tri(grid, args, name):
     o[:] = 0
     for j in range(6):
         o[j, :, :np_] = planes[j]
+
+
+def _expo_tri_exec(L, n, ps, P0, np_, pk, nsc, e):
+    ntri = n * (n + 1) // 2
+    A = np.abs(_tri_columns(L, n, ps, P0, np_, pk))
+    ev = uv(e, ntri * nsc, np.int32).reshape(ntri, nsc)
+    for z in range(nsc):
+        ev[:, z] = _expo_of(A[:, z * SUPER:(z + 1) * SUPER].max(axis=1))
+
+
+def _slice_tri_exec(L, n, ps, P0, np_, pk, Kpad, nsc, e, out):
+    ntri = n * (n + 1) // 2
+    A = _tri_columns(L, n, ps, P0, np_, pk)
+    ev = uv(e, ntri * nsc, np.int32).reshape(ntri, nsc)
+    planes = _digits_bf16(A, ev[:, np.arange(np_) // SUPER], 6)
+    o = uv(out, 6 * ntri * Kpad, np.uint16).reshape(6, ntri, Kpad)
+    o[:] = 0
+    for j in range(6):
+        o[j, :, :np_] = planes[j]
+
+
+def ex_expo_tri_group(grid, args):
+    g = TriGroup.from_address(args[0])
+    for i in range(g.njob):
+        jb = g.j[i]
+        _expo_tri_exec(jb.L, jb.n, jb.pstride, jb.P0, jb.np, jb.pk, jb.nsc, jb.e)
+
+
+def ex_slice_tri_group(grid, args):
+    g = TriGroup.from_address(args[0])
+    for i in range(g.njob):
+        jb = g.j[i]
+        _slice_tri_exec(jb.L, jb.n, jb.pstride, jb.P0, jb.np, jb.pk, jb.Kpad, jb.nsc, jb.e, jb.out)
+
+
+def _j_tri_add_exec(C, ldc, n, nd, acc, ptrs):
+    ntri = n * (n + 1) // 2
+    Cm = dv(C, ntri * ldc).reshape(ntri, ldc)
+    iu = np.triu_indices(n)
+    for s in range(nd):
+        J = dv(ptrs[s], n * n).reshape(n, n)
+        v = Cm[:, s] + (J[iu] if acc else 0.0)
+        J[iu] = v
+        J[iu[1], iu[0]] = v
+
+
+def ex_j_tri_add_group(grid, args):
+    g = JAddGroup.from_address(args[0])
+    for i in range(g.njob):
+        jb = g.j[i]
+        _j_tri_add_exec(jb.C, jb.ldc, jb.n, jb.nd, jb.acc, [g.ptr[jb.p0 + s] for s in range(jb.nd)])
 
 
 def ex_j_tri_add(grid, args):
@@ -1077,6 +1230,8 @@ EXECUTORS = [
     ("dgemm_nt_kernel", ex_dgemm), ("pack_cols_kernel", ex_pack_cols), ("frob_stream_kernel", ex_frob),
     ("gamma_panel_kernel", ex_gamma_panel), ("jstream_sym_kernel", ex_jstream_sym), ("axpy_kernel", ex_axpy),
     ("expo_tri_kernel", ex_expo_tri), ("slice_tri_kernel", ex_slice_tri), ("j_tri_add_kernel", ex_j_tri_add),
+    ("expo_tri_group_kernel", ex_expo_tri_group), ("slice_tri_group_kernel", ex_slice_tri_group),
+    ("j_tri_add_group_kernel", ex_j_tri_add_group), ("gamma_group_kernel", ex_gamma_group),
     ("sum_parts_kernel", ex_sum_parts), ("pair_dot_kernel", ex_pair_dot), ("laplace_scale_kernel", ex_laplace_scale),
     ("weighted_sum_kernel", ex_weighted_sum), ("unpack_sym_kernel", ex_unpack_sym), ("gterms_kernel", ex_gterms),
     ("symmetrize_kernel", ex_symmetrize), ("fold_sym_split_kernel", ex_fold), ("fold_sym_kernel", ex_fold),
@@ -1092,6 +1247,8 @@ EXECUTORS = [
 
 DECODERS = [
     ("expo_tri_kernel", dec_expo_tri), ("slice_tri_kernel", dec_slice_tri), ("j_tri_add_kernel", dec_j_tri_add),
+    ("expo_tri_group_kernel", dec_expo_tri_group), ("slice_tri_group_kernel", dec_slice_tri_group),
+    ("j_tri_add_group_kernel", dec_j_tri_add_group), ("gamma_group_kernel", dec_gamma_group),
     ("pack_group_kernel", dec_pack_group), ("int_fill_kernel", dec_int_fill), ("panel_colmax_kernel", dec_panel_colmax),
     ("expo_group_kernel", dec_expo_group), ("slice_group_kernel", dec_slice_group),
     ("reduce_group_kernel", dec_reduce_group),

@@ -111,11 +111,13 @@ def test_full_size_case(full_records, name):
 
 
 def test_full_size_tuned_build_launch_count(full_records):
-    """The tuned multi-state build (grouped schedule) issues 13 launches per
+    """The tuned multi-state build (grouped schedule) issues 17 launches per
     build: grouped persistent GEMMs, grouped packing, exponent, slicer and
     reduction launches, the panel operands' row-wise exponent pass (a fill
-    and a row launch), the FP64 metric dot and J stream."""
-    assert len(full_records["full_multi_state_tuned"]["launches"]) == 13
+    and a row launch), the FP64 metric dot, and the J back-contraction's
+    transposed factor slicing (exponents and digits), gamma's slicing
+    (exponents and digits) and the scatter of its product onto J."""
+    assert len(full_records["full_multi_state_tuned"]["launches"]) == 17
 
 
 def _check(rec):
@@ -238,7 +240,7 @@ def test_grouped_schedule_collapses_gemm_launches(full_records):
         return sum("ozgemm_kernel" in k[0] for k in full_records[name]["launches"])
     assert gemms("full_multi_state_tuned") == 2
     assert gemms("full_multi_state_default") == 2 * (1 + 8 + 1)
-    assert sum("jstream_sym_kernel" in k[0] for k in full_records["full_multi_state_tuned"]["launches"]) == 1
+    assert not any("jstream_sym_kernel" in k[0] for k in full_records["full_multi_state_tuned"]["launches"])
 
 
 def test_tuned_build_matches_the_measured_launch_list(full_records):
@@ -246,15 +248,18 @@ def test_tuned_build_matches_the_measured_launch_list(full_records):
     schedule every operand of a wave is sliced by one slicer launch (the
     packed densities and the factor chunk after one exponent launch each,
     all densities' panel operands after the row-wise exponent pass over the
-    panel) and every split-K reduction by one launch."""
+    panel, gamma for the J back-contraction) and every split-K reduction,
+    the J product's included, by one launch; J's GEMM shares the rank
+    updates' launch."""
     from collections import Counter
-    per_build = {"ozgemm_kernel": 2, "expo_group_kernel": 2, "int_fill_kernel": 1, "panel_colmax_kernel": 1,
-                 "slice_group_kernel": 3, "jstream_sym_kernel": 1, "gamma_panel_kernel": 1, "reduce_group_kernel": 1,
-                 "pack_group_kernel": 1}
+    per_build = {"ozgemm_kernel": 2, "expo_group_kernel": 3, "int_fill_kernel": 1, "panel_colmax_kernel": 1,
+                 "slice_group_kernel": 4, "gamma_group_kernel": 1, "reduce_group_kernel": 1,
+                 "pack_group_kernel": 1, "expo_tri_group_kernel": 1, "slice_tri_group_kernel": 1,
+                 "j_tri_add_group_kernel": 1}
     got = Counter()
     for k in full_records["full_multi_state_tuned"]["launches"]:
         got[next(key for key in per_build if key in k[0])] += 1
-    assert dict(got) == per_build and sum(per_build.values()) == 13
+    assert dict(got) == per_build and sum(per_build.values()) == 17
 
 
 EXEC_CASES = [n for n in NAMES if not n.startswith("autotune")]
