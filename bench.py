@@ -22,9 +22,13 @@ not counted) with every input resident in HBM.  In the same line:
   roofline       the dominant kernel (the tcgen05 sliced GEMM): algorithmic
                  TFLOP/s against the measured BF16 peak, beside the issued
                  BF16 MMA rate;
-  j_stream       the FP64 J back-contraction: HBM GB/s and FP64 TFLOP/s
-                 against the measured HBM peak and the FP64 FMA rate this run
-                 measures with the library's probe kernel;
+  j_stream       the J back-contraction: on the tensor cores its own
+                 kernels (the transposed factor slicing and the scatter onto
+                 J; its sliced GEMM runs inside the GEMM kind): time, HBM GB/s
+                 of their algorithmic bytes against the measured HBM peak;
+                 the FP64 form (dense-density builds) as HBM GB/s and FP64
+                 TFLOP/s against the FP64 FMA rate this run measures with
+                 the library's probe kernel;
   cpu_baseline   the oracle on a bounded, named sample of the same workload;
   configs        the other workloads (one molecule small, multi-state,
                  adjoint, uneven batch replayed as a CUDA graph), unless
@@ -109,6 +113,16 @@ def jstream_bytes_flops(n, naux, nd):
     one FMA per upper-triangle entry, aux index and density."""
     tri = n * (n + 1) // 2
     return 8.0 * tri * naux + 8.0 * nd * n * n, 2.0 * tri * naux * nd
+
+
+def jtri_bytes(n, naux, nd, nchunks):
+    """Algorithmic HBM bytes of the tensor-core J back-contraction's own
+    kernels: the upper triangle of every L^P read twice (exponents, then
+    digits) and written as six BF16 planes; per aux chunk the FP64 product
+    C [n(n+1)/2][nd] read and J written over both triangles (read too after
+    the first chunk)."""
+    tri = n * (n + 1) // 2
+    return (8.0 + 8.0 + 12.0) * tri * naux + nchunks * 8.0 * (tri * nd + 2.0 * nd * n * n) - 8.0 * nd * n * n
 
 
 def adjoint_flops(n, naux, ks, sym):
@@ -383,10 +397,20 @@ def gemm_roofline(prof, flops_alg_per_step, issued, steps, peaks, peak_src):
             "kernel_sources": h, "avg_launch_ms": ms / cnt, "launches": cnt}
 
 
-def jstream_roofline(prof, n, naux, nd, steps, peaks, fp64_tflops):
+def jstream_roofline(prof, n, naux, nd, steps, peaks, fp64_tflops, nchunks=1):
     ms, cnt = prof.get("jstream_fp64", (0.0, 0))
     if not cnt:
-        return None
+        ms, cnt = prof.get("j_tri", (0.0, 0))
+        if not cnt:
+            return None
+        by = jtri_bytes(n, naux, nd, nchunks)
+        per = ms / steps
+        gbs = by / (per * 1e-3) / 1e9
+        hbm = peaks.get("hbm_gbs")
+        return {"kernel": "expo_tri_kernel, slice_tri_kernel, j_tri_add_kernel (J on the tensor cores: the "
+                          "transposed factor slicing and the scatter; its sliced GEMM is in the GEMM kind)",
+                "ms_per_step": per, "launches": cnt, "aux_chunks": nchunks, "algorithmic_bytes": by,
+                "achieved_gbs": gbs, "hbm_peak_gbs": hbm, "hbm_frac": gbs / hbm, "bound": "hbm"}
     by, fl = jstream_bytes_flops(n, naux, nd)
     per = ms / steps
     gbs = by / (per * 1e-3) / 1e9
@@ -569,7 +593,9 @@ def run_ours(args, rank, world, local):
     # ---- rooflines ----------------------------------------------------------
     fp64_tf = fp64_peak(eng, st)
     roofline = gemm_roofline(prof, panel_rank_flops(n, naux, ks, sym), issued, args.steps, peaks, peak_src)
-    jstream = jstream_roofline(prof, n, naux, len(ks), args.steps, peaks, fp64_tf)
+    # three J kernels per aux chunk (exponents, digits, scatter)
+    nchunks = max(1, round(prof.get("j_tri", (0.0, 0))[1] / (3 * args.steps)))
+    jstream = jstream_roofline(prof, n, naux, len(ks), args.steps, peaks, fp64_tf, nchunks)
     if fp64 is not None:
         fp64["fp64_pipe_peak_tflops"] = fp64_tf
         fp64["fp64_pipe_frac"] = fp64["value"] / fp64_tf

@@ -334,7 +334,7 @@ typedef enum {
                                64 (more, narrower tiles; a tuning candidate).
                                Results are identical: the tile only changes
                                which outputs a CTA forms, not how            */
-    JK_OPT_ADJOINT_SLICES = 10 /* split jk_adjoint: BF16 slices per operand of
+    JK_OPT_ADJOINT_SLICES = 10, /* split jk_adjoint: BF16 slices per operand of
                                every product, 7 (default: 56-bit operands, 28
                                slice pairs, 128 x 64 tiles) or 6 (48-bit, 21
                                pairs, about a quarter fewer tensor-core flops).
@@ -343,6 +343,18 @@ typedef enum {
                                where 48-bit operands leave errors of ~1e-14
                                relative to max |dX|; 56 bits bring them below
                                the FP64 engine's own                          */
+    JK_OPT_J_PATH = 11      /* split builds: how J_s = sum_P gamma_{P,s} L^P is
+                               formed (Eq. 4's J term; every value gives the
+                               same J to within the split engine's error).
+                               -1 (default) = automatic: on the tensor cores
+                               when n(n+1)/2 * naux * nd >= 4e9, else as 0;
+                               0 = an FP64 pass over the factor on a second
+                               stream, overlapping the rank updates; 1 = on the
+                               tensor cores: each aux chunk of the factor
+                               sliced transposed over the upper triangle and
+                               multiplied by gamma's slices (one sliced GEMM),
+                               the result added onto both triangles in chunk
+                               order                                           */
 } jk_option;
 /* Options set explicitly on a handle override tuned configurations. */
 jk_status jk_set_option(jk_handle h, jk_option opt, int64_t value);

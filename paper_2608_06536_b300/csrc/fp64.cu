@@ -625,6 +625,12 @@ jk_status fp64_jstream(jk_ctx *h, const Problem &pb, const double *gamma, cudaSt
     return jstream(h, pb.L, pb.n, 0, pb.naux, gamma, pb.naux, pb.nd, pb.J, st, pb.packed);
 }
 
+// J_s (+)= sum_P gamma_{P,s} L^P over the aux chunk P0 .. P0 + np - 1 (added
+// to J unless P0 == 0): a split build's FP64 J, one chunk at a time.
+jk_status fp64_jstream_chunk(jk_ctx *h, const Problem &pb, const double *gamma, int P0, int np, cudaStream_t st) {
+    return jstream(h, pb.L, pb.n, P0, np, gamma, pb.naux, pb.nd, pb.J, st, pb.packed, P0 > 0);
+}
+
 
 int fp64_default_pchunk(const Problem &pb) {
     // Panel chunk of at most ~256 MB of FP64 (T^P for pc aux indices, and the

@@ -50,6 +50,7 @@ static jk_status make_problem(jk_ctx *h, const jk_factor *f, int nd,
     pb.nd = nd;
     pb.L = f->L;
     pb.packed = h && h->packed_factor;
+    pb.jpath = h ? h->jpath : -1;
     int c = 0, ks = 0, km = 0;
     for (int s = 0; s < nd; s++) {
         if (d[s].k < 1 || d[s].k > f->nbf * 4)
@@ -644,6 +645,7 @@ static jk_status query_impl(const jk_ctx *h, jk_op op, int32_t nmol, const jk_fa
     if (p != JK_FP64 && p != JK_SPLIT_BF16) return JK_ERR_ARG;
     // a packed factor (handle option) is taken by the ordinary builds only
     const bool pk = h && h->packed_factor;
+    const int jp = h ? h->jpath : -1;   // the split J path (JK_OPT_J_PATH)
     if (pk && (op == JK_OP_BUILD_HOST || op == JK_OP_BUILD_HOST_PACKED))
         return JK_ERR_UNSUPPORTED;
     if (op == JK_OP_BUILD_DENSE || op == JK_OP_DENSITY_GRAD) {
@@ -665,6 +667,7 @@ static jk_status query_impl(const jk_ctx *h, jk_op op, int32_t nmol, const jk_fa
         Problem pb;
         JK_TRY(make_problem(nullptr, f, nd, dl.data(), false, pb));
         pb.packed = pk;
+        pb.jpath = jp;
         Problem q = pb;
         apply_config(pb, resolve_config(h, JK_OP_BUILD, p, sms, 1, &pb));
         apply_config(q, jk_tune_config{0, 0, 0});
@@ -678,7 +681,10 @@ static jk_status query_impl(const jk_ctx *h, jk_op op, int32_t nmol, const jk_fa
         if (nmol != 2 || !nd_per_mol) return JK_ERR_SHAPE;
         std::vector<Problem> pp;
         JK_TRY(host_batched_problems(2, f, nd_per_mol, nd, d, pp, true));
-        for (auto &q : pp) q.packed = pk;
+        for (auto &q : pp) {
+            q.packed = pk;
+            q.jpath = jp;
+        }
         size_t need = 0;
         const jk_tune_config cfgs[2] = {resolve_config(h, JK_OP_BUILD, p, sms, 1, &pp[1]),
                                         jk_tune_config{0, 0, 0}};
@@ -694,12 +700,16 @@ static jk_status query_impl(const jk_ctx *h, jk_op op, int32_t nmol, const jk_fa
     std::vector<Problem> pbs;
     if (op == JK_OP_BATCHED) {
         JK_TRY(host_batched_problems(nmol, f, nd_per_mol, nd, d, pbs));
-        for (auto &q : pbs) q.packed = pk;
+        for (auto &q : pbs) {
+            q.packed = pk;
+            q.jpath = jp;
+        }
     } else if (op == JK_OP_BUILD || op == JK_OP_ADJOINT || op == JK_OP_BUILD_HOST || op == JK_OP_BUILD_HOST_PACKED) {
         pbs.resize(1);
         jk_status s = make_problem(nullptr, f, nd, d, false, pbs[0]);
         if (s != JK_OK) return s;
         pbs[0].packed = pk;
+        pbs[0].jpath = jp;
         pbs[0].slices = h ? h->adj_slices : 7;   // the split adjoint's operands (the default without a handle)
         nmol = 1;
         if (op == JK_OP_BUILD_HOST || op == JK_OP_BUILD_HOST_PACKED) {
@@ -1163,6 +1173,11 @@ jk_status jk_set_option(jk_handle h, jk_option opt, int64_t value) {
     if (opt == JK_OPT_ADJOINT_SLICES) {
         if (value != 6 && value != 7) return set_error(h, JK_ERR_ARG, "JK_OPT_ADJOINT_SLICES takes 6 or 7");
         h->adj_slices = static_cast<int>(value);
+        return JK_OK;
+    }
+    if (opt == JK_OPT_J_PATH) {
+        if (value < -1 || value > 1) return set_error(h, JK_ERR_ARG, "JK_OPT_J_PATH takes -1, 0 or 1");
+        h->jpath = static_cast<int>(value);
         return JK_OK;
     }
     if (opt == JK_OPT_USE_TUNED) {

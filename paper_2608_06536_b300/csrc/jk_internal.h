@@ -44,7 +44,7 @@ struct DeviceFlags {
 // Kernel kinds for launch accounting / event timing.
 enum KernelKind {
     KK_DGEMM = 0, KK_JSTREAM, KK_FROB, KK_GAMMA, KK_PACK, KK_MISC,
-    KK_SLICE, KK_OZGEMM, KK_OZREDUCE, KK_EXPO, KK_COUNT
+    KK_SLICE, KK_OZGEMM, KK_OZREDUCE, KK_EXPO, KK_JTRI, KK_COUNT
 };
 
 struct Profiler {
@@ -80,6 +80,7 @@ struct jk_ctx {
     int slicer = 0;          // digit extraction of the vector slicer: 0 integer, 1 FP32 additions
     int syrk = 0;            // split engine: symmetric rank updates by row blocks, rest mirrored
     int packed_factor = 0;   // factors passed to builds hold packed upper triangles
+    int jpath = -1;          // split J back-contraction (JK_OPT_J_PATH): -1 automatic, 0 FP64, 1 tensor
     cudaStream_t copy_stream = nullptr;   // host builds: uploads of the factor, created on first use
     cudaEvent_t ev_fork = nullptr, ev_up[2] = {nullptr, nullptr}, ev_used[2] = {nullptr, nullptr};
     cudaStream_t aux_stream = nullptr;    // FP64 J streams overlapped with the rank updates
@@ -112,7 +113,18 @@ struct Problem {
     bool packed = false; // L holds packed upper triangles [naux][n(n+1)/2]; each aux
                          // chunk is expanded into a dense workspace copy before use
     int slices = 6;      // split adjoint: slices per operand (6: 48-bit, 7: 56-bit)
+    int jpath = -1;      // split J back-contraction: -1 automatic, 0 FP64 stream, 1 tensor cores
 };
+
+// The split engine forms J on the tensor cores (sliced GEMM over the upper
+// triangle) when asked, or automatically once the FP64 form's work,
+// n(n+1)/2 * naux * nd multiply-adds, reaches kJTensorMin: below that the
+// FP64 stream is short and overlaps the rank updates on a second stream.
+constexpr double kJTensorMin = 4e9;
+inline bool j_on_tensor(const Problem &pb) {
+    if (pb.jpath >= 0) return pb.jpath == 1;
+    return 0.5 * pb.n * (pb.n + 1.0) * pb.naux * pb.nd >= kJTensorMin;
+}
 
 jk_status set_error(jk_ctx *h, jk_status s, const char *fmt, ...);
 

@@ -5,7 +5,7 @@ namespace jk {
 
 static const char *kKindNames[KK_COUNT] = {
     "dgemm_fp64", "jstream_fp64", "frob_stream_fp64", "gamma_panel_fp64", "pack",
-    "misc", "slice", "ozgemm_tcgen05", "oz_reduce", "expo"};
+    "misc", "slice", "ozgemm_tcgen05", "oz_reduce", "expo", "j_tri"};
 
 static cudaEvent_t take_event(Profiler &p) {
     if (p.used == p.pool.size()) {

@@ -439,14 +439,14 @@ static jk_status split_j_chunk(jk_ctx *h, const Problem &pb, const double *gamma
     A.rpe = 1;
     const int nsc = nsuper_of(np);
     {
-        LaunchScope ls(h, KK_EXPO, st);
+        LaunchScope ls(h, KK_JTRI, st);
         const dim3 grid(static_cast<unsigned>((nt + 255) / 256), nsc);
         if (pb.packed) oz::expo_tri_kernel<true><<<grid, 256, 0, st>>>(pb.L, n, pstride, P0, np, nsc, A.e);
         else oz::expo_tri_kernel<false><<<grid, 256, 0, st>>>(pb.L, n, pstride, P0, np, nsc, A.e);
     }
     JK_LAUNCH_CHECK(h);
     {
-        LaunchScope ls(h, KK_SLICE, st);
+        LaunchScope ls(h, KK_JTRI, st);
         const dim3 grid(static_cast<unsigned>((nt + oz::TRI_TILE - 1) / oz::TRI_TILE),
                         (A.Kpad + oz::TRI_TILE - 1) / oz::TRI_TILE);
         uint2 *o4 = reinterpret_cast<uint2 *>(A.s);
@@ -468,7 +468,7 @@ static jk_status split_j_chunk(jk_ctx *h, const Problem &pb, const double *gamma
     oz::JOut jo;
     for (int s = 0; s < kMaxDens; s++) jo.p[s] = s < pb.nd ? pb.J[s] : nullptr;
     {
-        LaunchScope ls(h, KK_MISC, st);
+        LaunchScope ls(h, KK_JTRI, st);
         oz::j_tri_add_kernel<<<static_cast<unsigned>((nt + 255) / 256), 256, 0, st>>>(jb.C, jb.ldc, n, pb.nd,
                                                                                        P0 > 0 ? 1 : 0, jo);
     }
@@ -527,12 +527,12 @@ static jk_status tri_flush(jk_ctx *h, TriBatch &tb, cudaStream_t st) {
         }
         grp.njob = nj;
         {
-            LaunchScope ls(h, KK_EXPO, st);
+            LaunchScope ls(h, KK_JTRI, st);
             oz::expo_tri_group_kernel<<<static_cast<unsigned>(eb), 256, 0, st>>>(grp);
         }
         JK_LAUNCH_CHECK(h);
         {
-            LaunchScope ls(h, KK_SLICE, st);
+            LaunchScope ls(h, KK_JTRI, st);
             oz::slice_tri_group_kernel<<<static_cast<unsigned>(sbk), 256, 0, st>>>(grp);
         }
         JK_LAUNCH_CHECK(h);
@@ -576,7 +576,7 @@ static jk_status jadd_flush(jk_ctx *h, JAddBatch &ab, cudaStream_t st) {
         }
         grp.njob = nj;
         {
-            LaunchScope ls(h, KK_MISC, st);
+            LaunchScope ls(h, KK_JTRI, st);
             oz::j_tri_add_group_kernel<<<static_cast<unsigned>((tot + 255) / 256), 256, 0, st>>>(grp, tot);
         }
         JK_LAUNCH_CHECK(h);
@@ -876,7 +876,7 @@ static int split_pchunk(const Problem &pb, bool batched = false) {
     const size_t n = pb.n;
     size_t per = n * n * (6 * 2) + n * pb.ctot * 8 + n * pb.ctot * (6 * 2);
     if (pb.packed) per += n * n * 8;               // the expanded factor chunk
-    per += n * (n + 1) / 2 * (6 * 2);              // the transposed chunk's slices (J)
+    if (j_on_tensor(pb)) per += n * (n + 1) / 2 * (6 * 2);   // the transposed chunk's slices (J)
     size_t budget = static_cast<size_t>(batched ? 6 : 12) << 30;
     size_t pc = per ? budget / per : 1;
     if (pc < 1) pc = 1;
@@ -922,7 +922,7 @@ size_t split_build_workspace(const Problem &pb) {
     if (pb.n > oz::SUPER)
         b += align_up(static_cast<size_t>(nsuper_of(pb.n)) * part_rows(static_cast<long long>(pc) * n) * even_ld(pb.ctot) * 8);
     if (pb.packed) b += align_up(static_cast<size_t>(pc) * n * n * 8);   // expanded factor chunk
-    b += jbufs_bytes(pb, pc);   // J on the tensor cores (counted whether or not J is asked for: queries do not say)
+    if (j_on_tensor(pb)) b += jbufs_bytes(pb, pc);   // J on the tensor cores (counted whether or not J is asked for: queries do not say)
     return b;
 }
 
@@ -931,13 +931,18 @@ jk_status split_pack_z(jk_ctx *h, const Problem &pb, double *Z, cudaStream_t st)
 jk_status fp64_unpack_sym(jk_ctx *h, const double *packed, int n, long long np, double *full, cudaStream_t st);
 jk_status fp64_gamma_panel(jk_ctx *h, const Problem &pb, const double *T, long long ldT, int np, double *gamma,
                            int P0, cudaStream_t st);
+jk_status fp64_jstream(jk_ctx *h, const Problem &pb, const double *gamma, cudaStream_t st);
+jk_status fp64_jstream_chunk(jk_ctx *h, const Problem &pb, const double *gamma, int P0, int np, cudaStream_t st);
 
-// The FP64 J of a dense-density build (its metric dots and back-contraction)
-// needs only the factor and the densities, and runs on the FP64 pipe: it is
-// forked onto a second stream and overlaps the K products on the tensor pipe
-// (join at the end of the build, so the call stays ordered on the caller's
-// stream).  The factored builds form J on the tensor cores instead
-// (split_j_chunk and its grouped form).
+// The FP64 form of J (the factored builds' J when it is small, see
+// j_on_tensor; a dense-density build's metric dots and J) needs only the
+// factor and gamma or the densities, and runs on the FP64 pipe: it is forked
+// onto a second stream and overlaps the products on the tensor pipe (join at
+// the end of the build, so the call stays ordered on the caller's stream).
+// A single molecule's build forks it once per aux chunk (J accumulated chunk
+// by chunk in order), a batched build once per molecule, after its last
+// chunk.  Larger builds form J on the tensor cores (split_j_chunk and its
+// grouped form).
 static jk_status fork_jstream(jk_ctx *h, cudaStream_t st) {
     if (!h->aux_stream) {
         JK_CUDA_TRY(h, cudaStreamCreateWithFlags(&h->aux_stream, cudaStreamNonBlocking));
@@ -978,7 +983,8 @@ jk_status split_build(jk_ctx *h, const Problem &pb, cudaStream_t st) {
         Ppanel = ar.take<long long>(static_cast<size_t>(nsuper_of(n)) * part_rows(static_cast<long long>(pc) * n) * ldT);
     double *Lx = pb.packed ? ar.take<double>(static_cast<size_t>(pc) * n2) : nullptr;
     JBufs jb;
-    if (pb.wantJ) ok = ok && take_jbufs(ar, pb, pc, jb);
+    const bool jt = pb.wantJ && j_on_tensor(pb);
+    if (jt) ok = ok && take_jbufs(ar, pb, pc, jb);
     if (!ok || !T || !gamma || !Pbuf || !Kacc || (n > oz::SUPER && !Ppanel) || (pb.packed && !Lx))
         return set_error(h, JK_ERR_OOM, "workspace too small for the split build");
 
@@ -1005,7 +1011,12 @@ jk_status split_build(jk_ctx *h, const Problem &pb, cudaStream_t st) {
         }
         if (pb.wantJ) {
             JK_TRY(fp64_gamma_panel(h, pb, T, ldT, np, gamma, P0, st));
-            JK_TRY(split_j_chunk(h, pb, gamma, P0, np, jb, st));
+            if (jt) {
+                JK_TRY(split_j_chunk(h, pb, gamma, P0, np, jb, st));
+            } else {
+                JK_TRY(fork_jstream(h, st));
+                JK_TRY(fp64_jstream_chunk(h, pb, gamma, P0, np, h->aux_stream));
+            }
         }
         if (!pb.wantK) continue;
         // The rank-update operands of every density (grouped launches unless
@@ -1077,6 +1088,7 @@ jk_status split_build(jk_ctx *h, const Problem &pb, cudaStream_t st) {
     if (pb.wantK && h->syrk)
         for (int s = 0; s < nd; s++)
             if (pb.sym[s]) JK_TRY(mirror_sym_blocks(h, pb.K[s], n, st));
+    if (pb.wantJ && !jt) JK_TRY(join_jstream(h, st));
     return JK_OK;
 }
 
@@ -1404,7 +1416,7 @@ size_t item_bytes(const Problem &pb, int pc) {
     b += align_up(partial_count(pb, pc) * 8 + 8);
     b += align_up(static_cast<size_t>(pb.nd) * n * n * 8);   // per-density tmp for chunk accumulation
     if (pb.packed) b += align_up(static_cast<size_t>(pc) * n * n * 8);   // expanded factor chunk
-    b += jbufs_bytes(pb, pc);                                              // J on the tensor cores
+    if (j_on_tensor(pb)) b += jbufs_bytes(pb, pc);                         // J on the tensor cores
     return b + 16 * kArenaAlign;
 }
 
@@ -1425,7 +1437,7 @@ bool take_item(Arena &ar, const Problem &pb, int pc, ItemBufs &it) {
     it.P = ar.take<long long>(partial_count(pb, pc) + 1);
     it.tmp = ar.take<double>(static_cast<size_t>(pb.nd) * n * n);
     if (pb.packed) it.Lx = ar.take<double>(static_cast<size_t>(pc) * n * n);
-    ok = ok && (!pb.wantJ || take_jbufs(ar, pb, pc, it.jb));
+    ok = ok && (!(pb.wantJ && j_on_tensor(pb)) || take_jbufs(ar, pb, pc, it.jb));
     return ok && it.P && it.tmp && (!pb.packed || it.Lx);
 }
 
@@ -1473,6 +1485,7 @@ jk_status split_batched(jk_ctx *h, int nmol, const Problem *pbs, cudaStream_t st
         JK_TRY(slice_flush(h, zb, st));
     }
     const size_t persist = ar.off;
+    bool forked = false;   // FP64 J passes running on the second stream
     // Work items (molecule, aux chunk), chunk-major: the first chunk of every
     // molecule, then the second ..., so that a wave (at most one chunk per
     // molecule, as many as the arena holds) takes many molecules at once and
@@ -1547,9 +1560,19 @@ jk_status split_batched(jk_ctx *h, int nmol, const Problem *pbs, cudaStream_t st
             JK_TRY(fp64_gamma_group(h, gi, st));
             TriBatch tb;
             SliceBatch gb;
+            bool fork = false;
             for (auto &it : items) {
                 const Problem &pb = pbs[it.mol];
                 if (!pb.wantJ) continue;
+                if (!j_on_tensor(pb)) {
+                    // the FP64 form, once the molecule's gamma is complete
+                    if (it.P0 + it.np >= pb.naux) {
+                        if (!fork) JK_TRY(fork_jstream(h, st));
+                        fork = forked = true;
+                        JK_TRY(fp64_jstream(h, pb, mb[it.mol].gamma, h->aux_stream));
+                    }
+                    continue;
+                }
                 tri_add(tb, pb, it.P0, it.np, it.jb.A);
                 oz::Src gsrc{mb[it.mol].gamma + it.P0, pb.naux, 0, 1, it.np};   // row s: gamma[s][P0 ..]
                 slice_add(gb, gsrc, pb.nd, it.np, 1, it.jb.G);
@@ -1587,7 +1610,7 @@ jk_status split_batched(jk_ctx *h, int nmol, const Problem *pbs, cudaStream_t st
         JAddBatch ab;
         for (auto &it : items) {
             const Problem &pb = pbs[it.mol];
-            if (!pb.wantJ) continue;
+            if (!pb.wantJ || !j_on_tensor(pb)) continue;
             const int nsc = nsuper_of(it.np);
             probs.emplace_back();
             JK_TRY(oz_problem(h, it.jb.A, it.jb.G, nsc == 1 ? it.jb.C : nullptr, it.jb.ldc,
@@ -1654,6 +1677,7 @@ jk_status split_batched(jk_ctx *h, int nmol, const Problem *pbs, cudaStream_t st
             if (pbs[m].wantK)
                 for (int s = 0; s < pbs[m].nd; s++)
                     if (pbs[m].sym[s]) JK_TRY(mirror_sym_blocks(h, pbs[m].K[s], pbs[m].n, st));
+    if (forked) JK_TRY(join_jstream(h, st));
     return JK_OK;
 }
 

@@ -41,10 +41,10 @@ class jk_tune_config(ct.Structure):
 
 
 OPTIONS = {"aux_chunk": 0, "schedule": 1, "raster": 2, "use_tuned": 3, "host_chunk": 5, "slicer": 6,
-           "syrk": 7, "packed_factor": 8, "tile": 9, "adjoint_slices": 10}
+           "syrk": 7, "packed_factor": 8, "tile": 9, "adjoint_slices": 10, "j_path": 11}
 # each option's value on a fresh handle (-1: not set, tuned or default configuration)
 OPTION_DEFAULTS = {"aux_chunk": -1, "schedule": -1, "raster": -1, "use_tuned": 1, "host_chunk": 0,
-                   "slicer": 0, "syrk": 0, "packed_factor": 0, "tile": -1, "adjoint_slices": 7}
+                   "slicer": 0, "syrk": 0, "packed_factor": 0, "tile": -1, "adjoint_slices": 7, "j_path": -1}
 
 
 class JKError(RuntimeError):
@@ -372,8 +372,9 @@ class Engine:
         density_grad, pairs, build_laplace, autotune*) is pack_factor(L),
         [naux][n(n+1)/2] on the device; half the memory), "tile" (0: sliced
         GEMM tiles of 128 x 80 outputs, 1: 128 x 64), "adjoint_slices" (6 or
-        7, default 7: BF16 slices per operand of the split adjoint's products).
-        Kept across arena growth."""
+        7, default 7: BF16 slices per operand of the split adjoint's products),
+        "j_path" (split builds' J: -1 automatic, 0 FP64 pass on a second
+        stream, 1 tensor cores).  Kept across arena growth."""
         code = OPTIONS[name]
         self._opts[code] = int(value)
         if self._h:

@@ -72,7 +72,7 @@ shim.shim_launch.restype = ct.c_char_p
 assert hasattr(shim, "shim_reset"), "the stand-in runtime is not the one loaded"
 
 OPT = {"aux_chunk": 0, "schedule": 1, "raster": 2, "use_tuned": 3, "host_chunk": 5, "slicer": 6,
-       "syrk": 7, "packed_factor": 8, "tile": 9, "adjoint_slices": 10}
+       "syrk": 7, "packed_factor": 8, "tile": 9, "adjoint_slices": 10, "j_path": 11}
 
 # ---- kernel arguments ----------------------------------------------------------
 # Each decoder reads one kernel's arguments (layouts as in the CUDA sources)
@@ -1786,6 +1786,19 @@ CASES = {
     "build_split_nbf_above_superchunk": build_case(2100, 3, [2], [False], SPLIT, {}),
     "build_split_fp32_digits": build_case(400, 60, [40, 40], [True, False], SPLIT, {"slicer": 1, "schedule": 1}),
     "build_split_j_only": build_case(37, 53, [5, 13], [False, True], SPLIT, {}, want="J"),
+    "build_split_j_tensor": build_case(37, 53, [5, 1, 13], [False, True, False], SPLIT, {"j_path": 1}),
+    "build_split_j_tensor_chunks": build_case(130, 70, [9, 3, 20], [False, True, False], SPLIT,
+                                              {"j_path": 1, "aux_chunk": 17}),
+    "build_split_j_tensor_grouped": build_case(130, 70, [9, 3, 20], [False, True, False], SPLIT,
+                                               {"j_path": 1, "schedule": 1, "aux_chunk": 30}),
+    "build_split_j_tensor_superchunks": build_case(20, 2100, [3, 2], [False, True], SPLIT, {"j_path": 1}),
+    "build_split_j_tensor_j_only": build_case(37, 53, [5, 13], [False, True], SPLIT, {"j_path": 1}, want="J"),
+    "build_split_j_tensor_packed": packed(build_case(130, 70, [9, 3, 20], [False, True, False], SPLIT,
+                                                     {"j_path": 1, "packed_factor": 1, "aux_chunk": 30})),
+    "batched_split_j_tensor": batched_case([(60, 150, [6, 6]), (111, 222, [11]), (33, 99, [3, 3, 3])], SPLIT,
+                                           {"j_path": 1}),
+    "batched_split_j_tensor_packed": packed(batched_case([(60, 150, [6, 6]), (140, 222, [11])], SPLIT,
+                                                         {"j_path": 1, "packed_factor": 1}, sym=True)),
     "build_split_syrk": build_case(300, 70, [20, 9, 33], [True, False, True], SPLIT,
                                    {"syrk": 1, "schedule": 0, "aux_chunk": 30}),
     "build_split_syrk_partials": build_case(300, 120, [40, 7], [True, True], SPLIT,
@@ -1903,7 +1916,7 @@ def fuzz_cases(count, seed):
         opts = {}
         if g.random() < 0.5:
             opts["aux_chunk"] = int(g.integers(1, naux + 3))
-        for name in ("schedule", "raster", "slicer", "syrk"):
+        for name in ("schedule", "raster", "slicer", "syrk", "j_path"):
             if g.random() < 0.5:
                 opts[name] = int(g.integers(0, 2))
         kind = g.choice(["build", "adjoint", "dense", "grad", "pairs", "laplace", "batched", "host"])
