@@ -461,6 +461,7 @@ def run_ours(args, rank, world, local):
     eng.set_option("slicer", args.slicer)
     eng.set_option("syrk", args.syrk)
     eng.set_option("packed_factor", 1 if args.packed_factor else 0)
+    eng.set_option("j_path", args.j_path)
 
     # run-time configuration: fixed (--config), or the autotuner's pick for
     # this shape (untimed; the cached pick is used by every build below)
@@ -504,7 +505,7 @@ def run_ours(args, rank, world, local):
         if rank == 0:
             print(json.dumps({"case": case, "ms_per_step": ms_max, "value": value, "kernels_ms": kernels_ms,
                               "launches_per_step": launches / args.steps, "tuned": tuned, "slicer": args.slicer,
-                              "syrk": args.syrk, "packed_factor": bool(args.packed_factor),
+                              "syrk": args.syrk, "packed_factor": bool(args.packed_factor), "j_path": args.j_path,
                               "issued_tensor_tflops": issued / args.steps / (ms_max * 1e-3) / 1e12,
                               "clocks": clk}), flush=True)
         return
@@ -621,7 +622,7 @@ def run_ours(args, rank, world, local):
         "config": {"workload": WORKLOADS[case], "engine": "split", "nbf": n, "naux": naux, "nd": len(ks),
                    "k": ks[0], "l2": "inputs larger than L2 (factor %.1f GB FP64), no flush" % (8e-9 * n * n * naux),
                    "parallelism": f"replicas x{world}", "tuned": tuned, "slicer": args.slicer,
-                   "syrk": args.syrk, "packed_factor": bool(args.packed_factor)},
+                   "syrk": args.syrk, "packed_factor": bool(args.packed_factor), "j_path": args.j_path},
         "e2e": e2e,
         "gpu_launches": int(launches),
         "launches_per_step": launches / args.steps,
@@ -845,6 +846,8 @@ def main():
                     help="digit extraction of the vector slicer: 0 integer, 1 FP32 additions")
     ap.add_argument("--syrk", type=int, choices=[0, 1], default=0,
                     help="symmetric densities: 0 full rank update, 1 blocked symmetric rank update")
+    ap.add_argument("--j-path", dest="j_path", type=int, choices=[-1, 0, 1], default=-1,
+                    help="split builds' J: -1 automatic, 0 FP64 pass on a second stream, 1 tensor cores")
     ap.add_argument("--packed-factor", dest="packed_factor", action="store_true",
                     help="device factor stored as packed upper triangles (half the memory)")
     ap.add_argument("--e2e-link", dest="e2e_link", choices=["packed", "full"], default="packed",
