@@ -540,10 +540,13 @@ __global__ void __launch_bounds__(256) panel_colmax_kernel(const __grid_constant
 // position) and G[s][kk] = gamma_{P0+kk,s}.  The factor is stored P-major, so
 // A's rows are strided columns of it: an exponent pass with one thread per
 // row t (the threads of a warp on consecutive positions, i.e. consecutive
-// addresses of each L^P), then a slicer that stages 64 x 64 tiles of L in
+// addresses of each L^P), then a slicer that stages TRI_TK x TRI_TT tiles of L in
 // shared memory and writes each row's digits along kk.  PK: the factor holds
 // packed upper triangles (position t is the row's offset in L^P).
-constexpr int TRI_TILE = 64;
+constexpr int TRI_TT = 128;  // rows t per tile of the transposed slicer (a power of two, 8 .. 256)
+constexpr int TRI_TK = 32;   // aux indices kk per tile (a multiple of 256 / TRI_TT and of 16)
+static_assert(256 % TRI_TT == 0 && TRI_TK % (256 / TRI_TT) == 0 && TRI_TK % 16 == 0 &&
+                  (TRI_TT * TRI_TK / 4) % 256 == 0, "transposed slicer tile");
 
 template <bool PK>
 __device__ __forceinline__ long long tri_offset(int n, long long t) {
@@ -587,10 +590,15 @@ __global__ void __launch_bounds__(256) expo_tri_kernel(const double *L, int n, l
 }
 
 // The six digit planes of A: out[j][t][kk] (Kpad columns, zero for kk >= np),
-// for rows t0 = 64 bx .. t0 + 63 and kk0 = 64 by .. kk0 + 63.
+// for rows t0 = TRI_TT bx .. t0 + TRI_TT - 1 and kk0 = TRI_TK by .. kk0 +
+// TRI_TK - 1.  The tile's rows of L (one per kk, TRI_TT positions each:
+// contiguous runs of the row mu) are staged in shared memory; then each
+// thread forms four consecutive kk of one row t.  Consecutive blocks take
+// consecutive kk tiles of the same rows t, so a row's planes are written out
+// close together in time.
 struct TriTile {
-    double v[TRI_TILE][TRI_TILE + 1];   // [kk - kk0][t - t0]
-    long long off[TRI_TILE];
+    double v[TRI_TK][TRI_TT + 1];   // [kk - kk0][t - t0]
+    long long off[TRI_TT];
 };
 
 template <bool PK>
@@ -598,30 +606,32 @@ __device__ __forceinline__ void slice_tri_body(TriTile &sm, const double *L, int
                                                int Kpad, int nsc, const int *e, uint2 *out, long long sstride4,
                                                long long bx, int by) {
     constexpr int S = 6;
+    constexpr int RPP = 256 / TRI_TT;              // rows kk per load pass
+    constexpr int GPR = TRI_TK / 4;                // groups of four kk per row t
     const long long ntri = packed::tri_count(n);
-    const long long t0 = bx * TRI_TILE;
-    const int kk0 = by * TRI_TILE;
-    if (threadIdx.x < TRI_TILE) {
+    const long long t0 = bx * TRI_TT;
+    const int kk0 = by * TRI_TK;
+    if (threadIdx.x < TRI_TT) {
         const long long t = t0 + threadIdx.x;
         sm.off[threadIdx.x] = t < ntri ? tri_offset<PK>(n, t) : -1;
     }
     __syncthreads();
     {
-        const int tc = threadIdx.x & (TRI_TILE - 1), kr0 = threadIdx.x >> 6;   // 4 rows kk per pass
+        const int tc = threadIdx.x % TRI_TT, kr0 = threadIdx.x / TRI_TT;
         const long long off = sm.off[tc];
-        double v[TRI_TILE / 4];
+        double v[TRI_TK / RPP];
 #pragma unroll
-        for (int i = 0; i < TRI_TILE / 4; i++) {
-            const int kk = kk0 + kr0 + 4 * i;
+        for (int i = 0; i < TRI_TK / RPP; i++) {
+            const int kk = kk0 + kr0 + RPP * i;
             v[i] = kk < np && off >= 0 ? L[static_cast<long long>(P0 + kk) * pstride + off] : 0.0;
         }
 #pragma unroll
-        for (int i = 0; i < TRI_TILE / 4; i++) sm.v[kr0 + 4 * i][tc] = v[i];
+        for (int i = 0; i < TRI_TK / RPP; i++) sm.v[kr0 + RPP * i][tc] = v[i];
     }
     __syncthreads();
 #pragma unroll
-    for (int i = 0; i < TRI_TILE * TRI_TILE / 4 / 256; i++) {
-        const int task = i * 256 + static_cast<int>(threadIdx.x), tr = task >> 4, g = task & 15;
+    for (int i = 0; i < TRI_TT * GPR / 256; i++) {
+        const int task = i * 256 + static_cast<int>(threadIdx.x), tr = task / GPR, g = task % GPR;
         const long long t = t0 + tr;
         const int kk = kk0 + 4 * g;
         if (t >= ntri || kk >= Kpad) continue;
@@ -645,12 +655,15 @@ __device__ __forceinline__ void slice_tri_body(TriTile &sm, const double *L, int
     }
 }
 
+// One operand: a 1-D grid of sbx * sby blocks, block b at kk tile b % sby
+// and row tile b / sby.
 template <bool PK>
 __global__ void __launch_bounds__(256) slice_tri_kernel(const double *L, int n, long long pstride, int P0, int np,
                                                         int Kpad, int nsc, const int *e, uint2 *out,
-                                                        long long sstride4) {
+                                                        long long sstride4, int sby) {
     __shared__ TriTile sm;
-    slice_tri_body<PK>(sm, L, n, pstride, P0, np, Kpad, nsc, e, out, sstride4, blockIdx.x, blockIdx.y);
+    const int b = static_cast<int>(blockIdx.x), by = b % sby, bx = b / sby;
+    slice_tri_body<PK>(sm, L, n, pstride, P0, np, Kpad, nsc, e, out, sstride4, bx, by);
 }
 
 // The same for many operands (the molecules of a batched build's wave) in one
@@ -692,7 +705,7 @@ __global__ void __launch_bounds__(256) expo_tri_group_kernel(const __grid_consta
 __global__ void __launch_bounds__(256) slice_tri_group_kernel(const __grid_constant__ TriGroup g) {
     __shared__ TriTile sm;
     const TriJob &jb = g.j[tri_job_of_block(g, blockIdx.x, false)];
-    const int lb = static_cast<int>(blockIdx.x) - jb.sb0, by = lb / jb.sbx, bx = lb - by * jb.sbx;
+    const int lb = static_cast<int>(blockIdx.x) - jb.sb0, by = lb % jb.sby, bx = lb / jb.sby;
     if (jb.pk)
         slice_tri_body<true>(sm, jb.L, jb.n, jb.pstride, jb.P0, jb.np, jb.Kpad, jb.nsc, jb.e, jb.out, jb.ss4, bx, by);
     else

@@ -447,14 +447,16 @@ static jk_status split_j_chunk(jk_ctx *h, const Problem &pb, const double *gamma
     JK_LAUNCH_CHECK(h);
     {
         LaunchScope ls(h, KK_JTRI, st);
-        const dim3 grid(static_cast<unsigned>((nt + oz::TRI_TILE - 1) / oz::TRI_TILE),
-                        (A.Kpad + oz::TRI_TILE - 1) / oz::TRI_TILE);
+        const int sby = (A.Kpad + oz::TRI_TK - 1) / oz::TRI_TK;
+        const long long blocks = (nt + oz::TRI_TT - 1) / oz::TRI_TT * sby;
+        if (blocks > 0x7fffffffLL) return set_error(h, JK_ERR_SHAPE, "too many J slicer blocks");
+        const unsigned grid = static_cast<unsigned>(blocks);
         uint2 *o4 = reinterpret_cast<uint2 *>(A.s);
         const long long ss4 = nt * A.Kpad / 4;
         if (pb.packed)
-            oz::slice_tri_kernel<true><<<grid, 256, 0, st>>>(pb.L, n, pstride, P0, np, A.Kpad, nsc, A.e, o4, ss4);
+            oz::slice_tri_kernel<true><<<grid, 256, 0, st>>>(pb.L, n, pstride, P0, np, A.Kpad, nsc, A.e, o4, ss4, sby);
         else
-            oz::slice_tri_kernel<false><<<grid, 256, 0, st>>>(pb.L, n, pstride, P0, np, A.Kpad, nsc, A.e, o4, ss4);
+            oz::slice_tri_kernel<false><<<grid, 256, 0, st>>>(pb.L, n, pstride, P0, np, A.Kpad, nsc, A.e, o4, ss4, sby);
     }
     JK_LAUNCH_CHECK(h);
     oz::Src gsrc{gamma + P0, pb.naux, 0, 1, np};   // row s: gamma[s][P0 ..]
@@ -506,8 +508,8 @@ static void tri_add(TriBatch &tb, const Problem &pb, int P0, int np, Sliced &A) 
     j.nsc = nsuper_of(np);
     j.pk = pb.packed ? 1 : 0;
     j.ebx = static_cast<int>((nt + 255) / 256);
-    j.sbx = static_cast<int>((nt + oz::TRI_TILE - 1) / oz::TRI_TILE);
-    j.sby = (A.Kpad + oz::TRI_TILE - 1) / oz::TRI_TILE;
+    j.sbx = static_cast<int>((nt + oz::TRI_TT - 1) / oz::TRI_TT);
+    j.sby = (A.Kpad + oz::TRI_TK - 1) / oz::TRI_TK;
     tb.jobs.push_back(j);
 }
 

@@ -467,11 +467,16 @@ def dec_expo_tri(grid, args, name):
     return [(L + 8 * P0 * ps, L + 8 * (P0 + np_) * ps, "L"), (e, e + 4 * ntri * nsc, "e")]
 
 
+TRI_TT, TRI_TK = 128, 32  # the transposed slicer's tile (rows t, aux indices kk)
+
+
 def dec_slice_tri(grid, args, name):
     pk, L, n, ps, P0, np_, ntri = _tri_args(args, name)
     Kpad, nsc, e, out, ss4 = _v(args, 5, I32), _v(args, 6, I32), _v(args, 7, VP), _v(args, 8, VP), _v(args, 9, I64)
+    sby = _v(args, 10, I32)
     assert Kpad == (np_ + 15) // 16 * 16 and nsc == (np_ + SUPER - 1) // SUPER and ss4 * 4 == ntri * Kpad
-    assert grid[0] * 64 >= ntri and grid[1] * 64 >= Kpad and out % 16 == 0, (grid, ntri, Kpad)
+    assert sby == -(-Kpad // TRI_TK) and grid[0] == -(-ntri // TRI_TT) * sby and grid[1] == 1 and out % 16 == 0, \
+        (grid, ntri, Kpad, sby)
     return [(L + 8 * P0 * ps, L + 8 * (P0 + np_) * ps, "L"), (e, e + 4 * ntri * nsc, "e"),
             (out, out + 8 * 6 * ss4, "slices")]
 
@@ -480,7 +485,7 @@ def _tri_job_check(jb):
     ntri = jb.n * (jb.n + 1) // 2
     assert jb.pstride == (ntri if jb.pk else jb.n * jb.n) and jb.P0 >= 0 and jb.np >= 1, (jb.pk, jb.pstride)
     assert jb.Kpad == (jb.np + 15) // 16 * 16 and jb.nsc == (jb.np + SUPER - 1) // SUPER and jb.ss4 * 4 == ntri * jb.Kpad
-    assert jb.ebx * 256 >= ntri and jb.sbx * 64 >= ntri and jb.sby * 64 >= jb.Kpad and jb.out % 16 == 0
+    assert jb.ebx * 256 >= ntri and jb.sbx == -(-ntri // TRI_TT) and jb.sby == -(-jb.Kpad // TRI_TK) and jb.out % 16 == 0
     return ntri
 
 
