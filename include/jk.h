@@ -22,9 +22,10 @@
  *    sub-allocated by bump, as the paper's engine does, Sec. IV).
  *  - All work is enqueued asynchronously on the caller's stream
  *    (a cudaStream_t passed as void*; NULL = legacy default stream).
- *    Split builds run their FP64 J back-contraction, and jk_build_host its
- *    uploads, on streams the handle owns; those fork from and join the
- *    caller's stream inside the call, so every result is ordered on it.
+ *    Split builds run the FP64 form of their J back-contraction (see
+ *    JK_OPT_J_PATH), and jk_build_host its uploads, on streams the handle
+ *    owns; those fork from and join the caller's stream inside the call, so
+ *    every result is ordered on it.
  *  - Outputs are overwritten, never accumulated into.
  *  - Arguments are validated on the host before anything is launched; a
  *    failing check returns a status and stores a message retrievable with
@@ -317,9 +318,9 @@ typedef enum {
                                (position a*nbf - a(a-1)/2 + b - a for a <= b):
                                half the device memory.  Each aux chunk is
                                expanded into the workspace before its
-                               products; the FP64 J back-contraction reads the
-                               packed form (and so do the dense calls' metric
-                               dots).  Results equal the dense factor's
+                               products; the J back-contraction reads the
+                               packed form (both of its forms, JK_OPT_J_PATH;
+                               and so do the dense calls' metric dots).  Results equal the dense factor's
                                bit for bit at the same aux chunk (the automatic
                                chunk can be smaller, as the expanded copy counts
                                against its budget: then they differ by
