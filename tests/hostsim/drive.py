@@ -1753,6 +1753,34 @@ def packed_refused_case():
     return fn
 
 
+def j_path_threshold_case():
+    """The workspace queries follow the split builds' J path: the automatic
+    choice equals the tensor-core form's size above 4e9 multiply-adds of J's
+    FP64 work (the headline workload) and the FP64 form's below it (the
+    multi-state workload), and the two forms' sizes differ (the tensor-core
+    form takes the transposed chunk's slices, and its aux chunk is smaller
+    where the workspace budget bounds it).  Only sizes are queried: the factor
+    is never touched."""
+    def fn():
+        got = {}
+        for label, n, naux, ks in (("headline", 1000, 5000, [100] * 16), ("multi_state", 400, 2400, [40] * 8)):
+            f = jk_factor(n, naux, ct.c_void_p(1 << 20))
+            d = (jk_density * len(ks))()
+            for s_, k in enumerate(ks):
+                d[s_].k, d[s_].symmetric, d[s_].X, d[s_].Y = k, 0, 1 << 20, 1 << 20
+            q = {"auto": query(0, f, d, len(ks), SPLIT)}
+            for jp in (-1, 0, 1):
+                h = handle(1 << 20, {"j_path": jp}, scaled=False)
+                q[jp] = query(0, f, d, len(ks), SPLIT, h=h)
+                lib.jk_destroy(h)
+            got[label] = q
+        hd, ms = got["headline"], got["multi_state"]
+        assert hd["auto"] == hd[-1] == hd[1] != hd[0], hd
+        assert ms["auto"] == ms[-1] == ms[0] != ms[1], ms
+        return 0, None
+    return fn
+
+
 def noalloc_case(n, naux, ks):
     def fn():
         f, d, L, X, Y = mol(n, naux, ks, [False] * len(ks))
@@ -1897,9 +1925,11 @@ FULL_CASES = {
                                                  {"packed_factor": 1, "schedule": 1})),
 }
 
-# Calls that must be refused before any device work (run by name only).
+# Calls that must be refused before any device work, and query-only checks
+# (run by name only).
 REFUSE_CASES = {
     "packed_refused": packed_refused_case(),
+    "j_path_threshold": j_path_threshold_case(),
 }
 
 # ---- random cases ----------------------------------------------------------------

@@ -110,6 +110,16 @@ def test_full_size_case(full_records, name):
     _check(full_records[name])
 
 
+def test_j_path_threshold_in_workspace_queries(shim_dir):
+    """The split builds take J on the tensor cores above 4e9 multiply-adds of
+    J's FP64 work: the queried workspace of the headline workload (automatic
+    choice) equals that of the forced tensor-core form, the multi-state
+    workload's that of the FP64 form, and nothing is launched."""
+    rec = _drive(shim_dir, ["j_path_threshold"])["j_path_threshold"]
+    assert rec["status"] == 0 and not rec["violations"], (rec["error"], rec["violations"])
+    assert not rec["launches"]
+
+
 def test_full_size_tuned_build_launch_count(full_records):
     """The tuned multi-state build (grouped schedule) issues 13 launches per
     build: grouped persistent GEMMs, grouped packing, exponent, slicer and
