@@ -224,6 +224,7 @@ static size_t host_persist_bytes(const Problem &pb, int chunk, bool wantJ, bool 
 static Problem host_chunk_problem(const Problem &pb, const HostBufs &b, int np, int buf) {
     Problem q = pb;
     q.naux = np;
+    if (q.jpath < 0) q.jpath = j_on_tensor(pb) ? 1 : 0;   // J's form chosen for the whole problem
     q.L = b.stage[buf];
     size_t off = 0;
     for (int s = 0; s < pb.nd; s++) {
@@ -262,6 +263,7 @@ static size_t host_build_bytes(const jk_ctx *h, const Problem &pb, jk_precision 
     const int chunk = host_chunk_of(h, pb);
     Problem q = pb;
     q.naux = chunk;
+    if (q.jpath < 0) q.jpath = j_on_tensor(pb) ? 1 : 0;   // as the chunk builds take it
     jk_tune_config c{0, 1, 0};
     if (h) c = host_config(h, p, q);
     apply_config(q, c);
